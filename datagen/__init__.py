@@ -1,0 +1,125 @@
+"""Seeded synthetic inputs shaped like the workloads of arXiv 1701.08475, Sec. 5.
+
+This module only draws inputs.  It holds none of the graph-construction
+arithmetic, so both the CUDA path and the CPU oracle can use it.
+
+The paper evaluates on SIFT1M (128-d, integer values 0..255) and GIST1M
+(960-d, non-negative) (Sec. 5).  Those datasets are not available here; the
+generators below produce stand-ins with the same dimensionality, value range
+and clustered structure.  No item of either dataset is reproduced.
+"""
+import numpy as np
+
+__all__ = ["gaussian_mixture", "sift_like", "gist_like", "unit_mixture",
+           "WORKLOADS", "make", "sample_rows"]
+
+
+def gaussian_mixture(n, D, n_centres, seed, lo=-10.0, hi=10.0, sigma=1.0):
+    """Isotropic Gaussian mixture: centres ~ U[lo, hi]^D, point = centre + N(0, sigma^2)."""
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(lo, hi, size=(n_centres, D)).astype(np.float32)
+    lab = rng.integers(0, n_centres, size=n)
+    X = rng.standard_normal(size=(n, D), dtype=np.float32)
+    X *= np.float32(sigma)
+    X += centres[lab]
+    return np.ascontiguousarray(X, dtype=np.float32)
+
+
+def sift_like(n, D=128, n_centres=1000, seed=0, zero_frac=0.3, spread=25.0, chunk=1 << 18):
+    """Non-negative integers 0..255 stored as FP32, clustered.
+
+    Centres ~ U[0, 120]^D; point = centre + N(0, spread^2); a Bernoulli(zero_frac)
+    mask zeroes coordinates; then clip to [0, 255] and round.
+    """
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0.0, 120.0, size=(n_centres, D)).astype(np.float32)
+    lab = rng.integers(0, n_centres, size=n)
+    X = np.empty((n, D), np.float32)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        v = rng.standard_normal(size=(b - a, D), dtype=np.float32)
+        v *= np.float32(spread)
+        v += centres[lab[a:b]]
+        v[rng.random(size=(b - a, D), dtype=np.float32) < zero_frac] = 0.0
+        np.clip(v, 0.0, 255.0, out=v)
+        np.rint(v, out=v)
+        X[a:b] = v
+    return X
+
+
+def gist_like(n, D=960, n_centres=1000, seed=0, block=32, alpha=0.3, conc=50.0, chunk=1 << 15):
+    """Values in [0, 1], non-negative, L1-normalised per `block`-dim block.
+
+    Each centre has a Dirichlet(alpha) profile per block; a point draws
+    Gamma(conc * profile) per coordinate around its centre and L1-normalises
+    every block.
+    """
+    assert D % block == 0
+    rng = np.random.default_rng(seed)
+    prof = rng.gamma(alpha, size=(n_centres, D)).astype(np.float32) + np.float32(1e-3)
+    prof = prof.reshape(n_centres, D // block, block)
+    prof /= prof.sum(axis=2, keepdims=True)
+    prof = prof.reshape(n_centres, D)
+    lab = rng.integers(0, n_centres, size=n)
+    X = np.empty((n, D), np.float32)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        v = rng.gamma(conc * prof[lab[a:b]] + np.float32(1e-3)).astype(np.float32)
+        v = v.reshape(b - a, D // block, block)
+        v /= np.maximum(v.sum(axis=2, keepdims=True), np.float32(1e-30))
+        X[a:b] = v.reshape(b - a, D)
+    return X
+
+
+def unit_mixture(n, D=96, n_centres=10000, seed=0, sigma=0.1, chunk=1 << 20):
+    """Unit-normalised mixture: centres ~ N(0, I) normalised; point = centre + N(0, sigma^2), normalised."""
+    rng = np.random.default_rng(seed)
+    c = rng.standard_normal(size=(n_centres, D), dtype=np.float32)
+    c /= np.linalg.norm(c, axis=1, keepdims=True)
+    lab = rng.integers(0, n_centres, size=n)
+    X = np.empty((n, D), np.float32)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        v = rng.standard_normal(size=(b - a, D), dtype=np.float32)
+        v *= np.float32(sigma)
+        v += c[lab[a:b]]
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        X[a:b] = v
+    return X
+
+
+# Workload recipes: sizes and build parameters of the graph workloads.
+WORKLOADS = {
+    "gmm-10k-d32": dict(gen="gaussian_mixture", n=10_000, D=32, n_centres=50, seed=1235,
+                        k=10, leaf_max=64, passes=1, rounds=2),
+    "sift-like-1m-d128": dict(gen="sift_like", n=1_000_000, D=128, n_centres=1000, seed=1236,
+                              k=20, leaf_max=128, passes=3, rounds=4),
+    "gist-like-1m-d960": dict(gen="gist_like", n=1_000_000, D=960, n_centres=1000, seed=1237,
+                              k=20, leaf_max=256, passes=3, rounds=4),
+    "unit-10m-d96": dict(gen="unit_mixture", n=10_000_000, D=96, n_centres=10000, seed=1239,
+                         k=16, leaf_max=128, passes=3, rounds=4),
+}
+
+
+def make(name, n=None):
+    """Draw the input of workload `name` (optionally only its first `n` rows' recipe at size n)."""
+    w = dict(WORKLOADS[name])
+    n = w["n"] if n is None else n
+    g = w["gen"]
+    if g == "gaussian_mixture":
+        return gaussian_mixture(n, w["D"], w["n_centres"], w["seed"])
+    if g == "sift_like":
+        return sift_like(n, w["D"], w["n_centres"], w["seed"])
+    if g == "gist_like":
+        return gist_like(n, w["D"], w["n_centres"], w["seed"])
+    if g == "unit_mixture":
+        return unit_mixture(n, w["D"], w["n_centres"], w["seed"])
+    raise KeyError(g)
+
+
+def sample_rows(n, s, seed):
+    """A sorted seeded sample of s distinct row indices (all rows if s >= n)."""
+    if s >= n:
+        return np.arange(n, dtype=np.int32)
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(n, size=s, replace=False)).astype(np.int32)

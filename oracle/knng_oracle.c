@@ -1,0 +1,428 @@
+/*
+ * knng_oracle.c -- CPU oracle for kNN-graph construction by two-means-tree
+ * partitioning, exhaustive comparison inside each cluster, and
+ * neighbour-of-neighbour refinement (Zhao, Yang, Deng, "Scalable Nearest
+ * Neighbor Search based on kNN Graph", arXiv 1701.08475, Sec. 3.1, Alg. 1;
+ * refinement: the nearest-neighbour-descent prior art cited in Sec. 1).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark load this library.  It shares no code,
+ * header, table or helper with the CUDA library and never calls it.
+ *
+ * Plain, slow and single-threaded on purpose.  Build with
+ *   gcc -O2 -ffp-contract=off -fPIC -shared
+ * so every floating-point operation is the one written here; a fused
+ * multiply-add appears only where fmaf() is called explicitly.
+ *
+ * Readings of the paper used here (the paper leaves these open):
+ *  - metric: squared l2 (Sec. 1 allows l1 or l2; squared l2 orders pairs
+ *    exactly as l2 does);
+ *  - canonical FP32 distance: acc = 0; for j ascending: t = x_j - y_j;
+ *    acc = fmaf(t, t, acc).  Symmetric bit for bit, since (x-y)^2 == (y-x)^2;
+ *  - ties are broken by the smaller id; lists hold unique ids, sorted by
+ *    (d, id); empty slots hold id -1 with d = +inf and sort last;
+ *  - two-means split (Sec. 3.1, Alg. 1 "apply two means clustering") is a
+ *    balanced Lloyd 2-means: the first floor(m/2) points by (s, id) go left,
+ *    where s = x . (c1 - c0) orders points exactly as
+ *    ||x - c0||^2 - ||x - c1||^2 does (the two differ by a factor 2 and a
+ *    per-segment constant, which a median cut cannot see);
+ *  - centroids are FP64 means of FP32 points (summed in ascending id order),
+ *    rounded to FP32;
+ *  - uniform depth: every segment at a level splits, so leaf sizes are
+ *    floor/ceil(n / 2^L), L the least level with ceil(n / 2^L) <= leaf_max;
+ *  - initial centroids: the points at positions h and h' of the segment
+ *    (segments hold their ids in ascending order), h and h' drawn from a
+ *    SplitMix64 hash of (pass seed, level, segment index);
+ *  - "visited" pairs (Alg. 1) are not skipped: re-evaluating a pair gives the
+ *    same canonical distance and cannot change a list;
+ *  - refinement round (Jacobi): reverse lists R[i] capped at the k closest by
+ *    (d, id); N_i = G_old[i] (mode 0) or G_old[i] + R[i] (mode 1); every
+ *    unordered pair {u, v} of N_i with u != v offers v to u and u to v with
+ *    the canonical distance; G_new[u] = first k unique of G_old[u] + offers.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): one output step for  */
+/* state z, i.e. advance by the golden-ratio increment, then mix.     */
+/* ------------------------------------------------------------------ */
+uint64_t orc_splitmix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Seed of tree pass p. */
+uint64_t orc_pass_seed(uint64_t seed, int pass)
+{
+    return orc_splitmix64(seed ^ (uint64_t)pass);
+}
+
+/* Positions (h, h2) of the two initial centroids of segment `seg` at
+ * `level`, for a segment of m >= 2 points.  h2 != h. */
+void orc_init_positions(uint64_t pass_seed, int level, int64_t seg, int64_t m,
+                        int64_t *h, int64_t *h2)
+{
+    uint64_t a = orc_splitmix64(orc_splitmix64(orc_splitmix64(pass_seed) ^ (uint64_t)level) ^ (uint64_t)seg);
+    uint64_t b = orc_splitmix64(a);
+    *h = (int64_t)(a % (uint64_t)m);
+    *h2 = (*h + 1 + (int64_t)(b % (uint64_t)(m - 1))) % m;
+}
+
+/* ------------------------------------------------------------------ */
+/* Distances                                                          */
+/* ------------------------------------------------------------------ */
+float orc_dist_f32(const float *x, const float *y, int D)
+{
+    float acc = 0.0f;
+    for (int j = 0; j < D; ++j) {
+        float t = x[j] - y[j];
+        acc = fmaf(t, t, acc);
+    }
+    return acc;
+}
+
+double orc_dist_f64(const float *x, const float *y, int D)
+{
+    double acc = 0.0;
+    for (int j = 0; j < D; ++j) {
+        double t = (double)x[j] - (double)y[j];
+        acc += t * t;
+    }
+    return acc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sorted, unique, bounded (d, id) lists                              */
+/* ------------------------------------------------------------------ */
+/* (d, id) order; an empty slot (id -1, d +inf) is greater than every entry
+ * because ids compare as unsigned. */
+static int key_less(float da, int32_t ia, float db, int32_t ib)
+{
+    if (da < db) return 1;
+    if (da > db) return 0;
+    return (uint32_t)ia < (uint32_t)ib;
+}
+
+static void list_clear(int32_t *ids, float *d, int k)
+{
+    for (int t = 0; t < k; ++t) { ids[t] = -1; d[t] = INFINITY; }
+}
+
+/* Offer (cd, cid) to the list: keep the k smallest unique ids by (d, id). */
+void orc_list_insert(int32_t *ids, float *d, int k, float cd, int32_t cid)
+{
+    if (cid < 0) return;
+    if (!key_less(cd, cid, d[k - 1], ids[k - 1])) return;
+    for (int t = 0; t < k; ++t)
+        if (ids[t] == cid) return;
+    int pos = 0;
+    while (!key_less(cd, cid, d[pos], ids[pos])) ++pos;
+    for (int t = k - 1; t > pos; --t) { ids[t] = ids[t - 1]; d[t] = d[t - 1]; }
+    ids[pos] = cid;
+    d[pos] = cd;
+}
+
+static int key_less64(double da, int32_t ia, double db, int32_t ib)
+{
+    if (da < db) return 1;
+    if (da > db) return 0;
+    return (uint32_t)ia < (uint32_t)ib;
+}
+
+static void list_insert64(int32_t *ids, double *d, int k, double cd, int32_t cid)
+{
+    if (!key_less64(cd, cid, d[k - 1], ids[k - 1])) return;
+    int pos = 0;
+    while (!key_less64(cd, cid, d[pos], ids[pos])) ++pos;
+    for (int t = k - 1; t > pos; --t) { ids[t] = ids[t - 1]; d[t] = d[t - 1]; }
+    ids[pos] = cid;
+    d[pos] = cd;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact kNN graph (the problem statement of Sec. 1, every point as a  */
+/* query against the other n - 1).                                    */
+/* ------------------------------------------------------------------ */
+/* Rows of `sample` (or all n rows when sample == NULL), canonical FP32
+ * distances, ties by id.  out: s x k. */
+int orc_exact_f32(const float *X, int64_t n, int D, int k,
+                  const int32_t *sample, int64_t s,
+                  int32_t *out_ids, float *out_d)
+{
+    if (!sample) s = n;
+    for (int64_t r = 0; r < s; ++r) {
+        int64_t i = sample ? sample[r] : r;
+        int32_t *li = out_ids + r * k;
+        float *ld = out_d + r * k;
+        list_clear(li, ld, k);
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            orc_list_insert(li, ld, k, orc_dist_f32(X + i * D, X + j * D, D), (int32_t)j);
+        }
+    }
+    return 0;
+}
+
+/* Same with FP64 distances (the error reference). */
+int orc_exact_f64(const float *X, int64_t n, int D, int k,
+                  const int32_t *sample, int64_t s,
+                  int32_t *out_ids, double *out_d)
+{
+    if (!sample) s = n;
+    for (int64_t r = 0; r < s; ++r) {
+        int64_t i = sample ? sample[r] : r;
+        int32_t *li = out_ids + r * k;
+        double *ld = out_d + r * k;
+        for (int t = 0; t < k; ++t) { li[t] = -1; ld[t] = INFINITY; }
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            list_insert64(li, ld, k, orc_dist_f64(X + i * D, X + j * D, D), (int32_t)j);
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Two-means tree (Sec. 3.1: bisect repeatedly with two-means until    */
+/* every cluster is below the threshold; Alg. 1 "apply two means").    */
+/* ------------------------------------------------------------------ */
+int orc_tree_depth(int64_t n, int leaf_max)
+{
+    int L = 0;
+    while ((n + ((int64_t)1 << L) - 1) / ((int64_t)1 << L) > leaf_max) ++L;
+    return L;
+}
+
+typedef struct { float s; int32_t id; } proj_t;
+
+static int proj_cmp(const void *a, const void *b)
+{
+    const proj_t *x = a, *y = b;
+    if (x->s < y->s) return -1;
+    if (x->s > y->s) return 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+static int id_cmp(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* FP64 mean of the listed points, rounded to FP32. */
+static void mean_of(const float *X, int D, const int32_t *ids, int64_t cnt,
+                    double *acc, float *c)
+{
+    for (int j = 0; j < D; ++j) acc[j] = 0.0;
+    for (int64_t t = 0; t < cnt; ++t)
+        for (int j = 0; j < D; ++j) acc[j] += (double)X[(int64_t)ids[t] * D + j];
+    for (int j = 0; j < D; ++j) c[j] = (float)(acc[j] / (double)cnt);
+}
+
+/* Split one segment (ids ascending, m >= 2) into its left half
+ * (floor(m/2) ids) and right half, each written back in ascending order. */
+static void split_segment(const float *X, int D, int32_t *seg_ids, int64_t m,
+                          int iters, uint64_t pass_seed, int level, int64_t seg,
+                          proj_t *pr, float *c0, float *c1, float *w, double *acc,
+                          int32_t *tmp)
+{
+    int64_t K = m / 2, h, h2;
+    orc_init_positions(pass_seed, level, seg, m, &h, &h2);
+    memcpy(c0, X + (int64_t)seg_ids[h] * D, sizeof(float) * D);
+    memcpy(c1, X + (int64_t)seg_ids[h2] * D, sizeof(float) * D);
+    for (int it = 0; it <= iters; ++it) {
+        for (int j = 0; j < D; ++j) w[j] = c1[j] - c0[j];
+        for (int64_t t = 0; t < m; ++t) {
+            const float *x = X + (int64_t)seg_ids[t] * D;
+            float a = 0.0f;
+            for (int j = 0; j < D; ++j) a = fmaf(x[j], w[j], a);
+            pr[t].s = a + 0.0f;   /* -0 and +0 are one key */
+            pr[t].id = seg_ids[t];
+        }
+        qsort(pr, (size_t)m, sizeof(proj_t), proj_cmp);
+        for (int64_t t = 0; t < m; ++t) tmp[t] = pr[t].id;
+        qsort(tmp, (size_t)K, sizeof(int32_t), id_cmp);
+        qsort(tmp + K, (size_t)(m - K), sizeof(int32_t), id_cmp);
+        if (it == iters) break;
+        mean_of(X, D, tmp, K, acc, c0);
+        mean_of(X, D, tmp + K, m - K, acc, c1);
+    }
+    memcpy(seg_ids, tmp, sizeof(int32_t) * (size_t)m);
+}
+
+/* Partition of tree pass `pass`: out_perm (n ids, leaves contiguous, ids
+ * ascending inside a leaf), out_leaf_offsets (2^L + 1 offsets).
+ * Returns the depth L, or -1 on bad arguments / allocation failure. */
+int orc_partition(const float *X, int64_t n, int D, int leaf_max, int iters,
+                  uint64_t seed, int pass, int32_t *out_perm, int64_t *out_leaf_offsets)
+{
+    if (n < 1 || D < 1 || leaf_max < 2 || iters < 0) return -1;
+    int L = orc_tree_depth(n, leaf_max);
+    uint64_t ps = orc_pass_seed(seed, pass);
+    int64_t nleaf = (int64_t)1 << L;
+    int64_t *off = malloc(sizeof(int64_t) * (size_t)(nleaf + 1));
+    int64_t *nxt = malloc(sizeof(int64_t) * (size_t)(nleaf + 1));
+    proj_t *pr = malloc(sizeof(proj_t) * (size_t)n);
+    int32_t *tmp = malloc(sizeof(int32_t) * (size_t)n);
+    float *c0 = malloc(sizeof(float) * (size_t)D), *c1 = malloc(sizeof(float) * (size_t)D);
+    float *w = malloc(sizeof(float) * (size_t)D);
+    double *acc = malloc(sizeof(double) * (size_t)D);
+    if (!off || !nxt || !pr || !tmp || !c0 || !c1 || !w || !acc) {
+        free(off); free(nxt); free(pr); free(tmp); free(c0); free(c1); free(w); free(acc);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; ++i) out_perm[i] = (int32_t)i;
+    off[0] = 0;
+    off[1] = n;
+    for (int level = 0; level < L; ++level) {
+        int64_t nseg = (int64_t)1 << level;
+        for (int64_t sg = 0; sg < nseg; ++sg) {
+            int64_t a = off[sg], m = off[sg + 1] - off[sg];
+            split_segment(X, D, out_perm + a, m, iters, ps, level, sg, pr, c0, c1, w, acc, tmp);
+            nxt[2 * sg] = a;
+            nxt[2 * sg + 1] = a + m / 2;
+        }
+        nxt[2 * nseg] = n;
+        memcpy(off, nxt, sizeof(int64_t) * (size_t)(2 * nseg + 1));
+    }
+    memcpy(out_leaf_offsets, off, sizeof(int64_t) * (size_t)(nleaf + 1));
+    free(off); free(nxt); free(pr); free(tmp); free(c0); free(c1); free(w); free(acc);
+    return L;
+}
+
+/* ------------------------------------------------------------------ */
+/* Leaf stage (Alg. 1, inner loops): every pair <i, j>, i != j, of a   */
+/* cluster updates G[i] and G[j] with d(x_i, x_j).                     */
+/* ------------------------------------------------------------------ */
+int orc_leaf_update(const float *X, int64_t n, int D, int k,
+                    const int32_t *perm, const int64_t *leaf_offsets, int64_t n_leaves,
+                    int32_t *ids, float *dists)
+{
+    (void)n;
+    for (int64_t l = 0; l < n_leaves; ++l) {
+        for (int64_t a = leaf_offsets[l]; a < leaf_offsets[l + 1]; ++a) {
+            for (int64_t b = a + 1; b < leaf_offsets[l + 1]; ++b) {
+                int32_t i = perm[a], j = perm[b];
+                float d = orc_dist_f32(X + (int64_t)i * D, X + (int64_t)j * D, D);
+                orc_list_insert(ids + (int64_t)i * k, dists + (int64_t)i * k, k, d, j);
+                orc_list_insert(ids + (int64_t)j * k, dists + (int64_t)j * k, k, d, i);
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Refinement round (neighbour-of-neighbour local join, Jacobi form).  */
+/* mode 0: N_i = G_old[i];  mode 1: N_i = G_old[i] + R[i].            */
+/* ------------------------------------------------------------------ */
+int orc_reverse_lists(int64_t n, int k, const int32_t *ids, const float *dists,
+                      int32_t *rev_ids, float *rev_d)
+{
+    for (int64_t i = 0; i < n; ++i) list_clear(rev_ids + i * k, rev_d + i * k, k);
+    for (int64_t j = 0; j < n; ++j)
+        for (int t = 0; t < k; ++t) {
+            int32_t i = ids[j * k + t];
+            if (i < 0) continue;
+            orc_list_insert(rev_ids + (int64_t)i * k, rev_d + (int64_t)i * k, k,
+                            dists[j * k + t], (int32_t)j);
+        }
+    return 0;
+}
+
+int orc_refine_round(const float *X, int64_t n, int D, int k, int mode,
+                     int32_t *ids, float *dists)
+{
+    size_t nk = (size_t)n * (size_t)k;
+    int32_t *old_ids = malloc(sizeof(int32_t) * nk);
+    float *old_d = malloc(sizeof(float) * nk);
+    int32_t *rev_ids = mode ? malloc(sizeof(int32_t) * nk) : NULL;
+    float *rev_d = mode ? malloc(sizeof(float) * nk) : NULL;
+    int32_t *memb = malloc(sizeof(int32_t) * (size_t)(2 * k));
+    if (!old_ids || !old_d || !memb || (mode && (!rev_ids || !rev_d))) {
+        free(old_ids); free(old_d); free(rev_ids); free(rev_d); free(memb);
+        return -1;
+    }
+    memcpy(old_ids, ids, sizeof(int32_t) * nk);
+    memcpy(old_d, dists, sizeof(float) * nk);
+    if (mode) orc_reverse_lists(n, k, old_ids, old_d, rev_ids, rev_d);
+    for (int64_t i = 0; i < n; ++i) {
+        int cnt = 0;
+        for (int t = 0; t < k; ++t)
+            if (old_ids[i * k + t] >= 0) memb[cnt++] = old_ids[i * k + t];
+        if (mode)
+            for (int t = 0; t < k; ++t)
+                if (rev_ids[i * k + t] >= 0) memb[cnt++] = rev_ids[i * k + t];
+        for (int a = 0; a < cnt; ++a)
+            for (int b = a + 1; b < cnt; ++b) {
+                int32_t u = memb[a], v = memb[b];
+                if (u == v) continue;
+                float d = orc_dist_f32(X + (int64_t)u * D, X + (int64_t)v * D, D);
+                orc_list_insert(ids + (int64_t)u * k, dists + (int64_t)u * k, k, d, v);
+                orc_list_insert(ids + (int64_t)v * k, dists + (int64_t)v * k, k, d, u);
+            }
+    }
+    free(old_ids); free(old_d); free(rev_ids); free(rev_d); free(memb);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Whole build: "Initialize G", I_0 tree passes (Alg. 1), then the     */
+/* refinement rounds.                                                 */
+/* ------------------------------------------------------------------ */
+int orc_build(const float *X, int64_t n, int D, int k, int leaf_max, int passes,
+              int rounds, int iters, int mode, uint64_t seed,
+              int32_t *out_ids, float *out_d)
+{
+    if (n < 2 || k < 1 || D < 1 || leaf_max < 2) return -1;
+    for (int64_t i = 0; i < n; ++i) list_clear(out_ids + i * k, out_d + i * k, k);
+    int L = orc_tree_depth(n, leaf_max);
+    int64_t nleaf = (int64_t)1 << L;
+    int32_t *perm = malloc(sizeof(int32_t) * (size_t)n);
+    int64_t *off = malloc(sizeof(int64_t) * (size_t)(nleaf + 1));
+    if (!perm || !off) { free(perm); free(off); return -1; }
+    for (int p = 0; p < passes; ++p) {
+        if (orc_partition(X, n, D, leaf_max, iters, seed, p, perm, off) < 0) {
+            free(perm); free(off); return -1;
+        }
+        orc_leaf_update(X, n, D, k, perm, off, nleaf, out_ids, out_d);
+    }
+    free(perm); free(off);
+    for (int r = 0; r < rounds; ++r)
+        if (orc_refine_round(X, n, D, k, mode, out_ids, out_d) != 0) return -1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Recall of a graph against exact lists on sampled rows.             */
+/* ids: n x k graph; gt_ids/gt_d: s x k exact lists of sample rows.   */
+/* recall_ids: mean over rows of |G[i] & GT[i]| / k.                  */
+/* recall_tie: mean over rows of #{real entries of G[i] with          */
+/*             d <= d_k of GT[i]} / k.                                */
+/* ------------------------------------------------------------------ */
+int orc_recall(const int32_t *ids, const float *dists, const int32_t *gt_ids,
+               const float *gt_d, const int32_t *sample, int64_t s, int k,
+               double *recall_ids, double *recall_tie)
+{
+    int64_t hit = 0, tie = 0;
+    for (int64_t r = 0; r < s; ++r) {
+        int64_t i = sample[r];
+        float kth = gt_d[r * k + k - 1];
+        for (int a = 0; a < k; ++a) {
+            int32_t g = ids[i * k + a];
+            if (g < 0) continue;
+            for (int b = 0; b < k; ++b)
+                if (gt_ids[r * k + b] == g) { ++hit; break; }
+            if (dists[i * k + a] <= kth) ++tie;
+        }
+    }
+    *recall_ids = s ? (double)hit / ((double)s * k) : 0.0;
+    *recall_tie = s ? (double)tie / ((double)s * k) : 0.0;
+    return 0;
+}
