@@ -1,0 +1,190 @@
+/*
+ * knng.h -- C ABI of the GB300 (sm_103a) kNN-graph builder.
+ *
+ * The library builds an approximate k-nearest-neighbour graph of n points in
+ * R^D by the method of Zhao, Yang and Deng, "Scalable Nearest Neighbor Search
+ * based on kNN Graph" (arXiv 1701.08475):
+ *   - Sec. 3.1 / Alg. 1: I_0 rounds ("tree passes"), each partitioning the
+ *     points by recursive two-means bisection into clusters no bigger than a
+ *     threshold (leaf_max), then comparing every pair inside each cluster and
+ *     updating both endpoints' k-lists;
+ *   - Sec. 1 (prior art cited there, nearest-neighbour descent): optional
+ *     neighbour-of-neighbour refinement rounds (local join).
+ *
+ * Conventions shared by every call:
+ *   - data is n x D FP32, row-major, rows contiguous (row i at data + i*D).
+ *   - A graph is two n x k row-major arrays: ids (int32) and dists (FP32,
+ *     squared l2).  Row i is sorted ascending by (dist, id), holds unique ids,
+ *     never i itself; an empty slot is (id -1, dist +inf) and sorts last.
+ *   - Distances are the canonical FP32 squared l2: acc = 0; for j = 0..D-1:
+ *     t = x_j - y_j; acc = fmaf(t, t, acc).  Equal pairs give equal bits.
+ *   - Ties are broken by the smaller id.
+ *   - Pointers may be device pointers or host pointers (pageable or pinned);
+ *     the library detects which.  Host inputs are copied to the device inside
+ *     the call and host outputs are copied back before it returns.  The caller
+ *     owns every buffer it passes; the library allocates only its own
+ *     workspace (stream-ordered, from a library memory pool) and releases it
+ *     before returning.
+ *   - stream: a cudaStream_t (NULL = the legacy default stream).  Every call
+ *     is synchronous: it returns after its work on `stream` has finished.
+ *   - Return value: KNNG_OK or a negative KNNG_E* code; knng_last_error()
+ *     gives a message (thread-local, valid until the next call on the thread).
+ *   - n < 2^31 (ids are int32).  Limits: 1 <= k <= 64, 1 <= D <= 4096,
+ *     2 (k + 1) <= leaf_max <= 256.
+ */
+#ifndef KNNG_H
+#define KNNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KNNG_API __attribute__((visibility("default")))
+#else
+#define KNNG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KNNG_OK 0
+#define KNNG_EINVAL (-1)   /* bad argument (message says which) */
+#define KNNG_ENOMEM (-2)   /* device allocation failed */
+#define KNNG_ECUDA (-3)    /* a CUDA call or kernel failed */
+#define KNNG_ETIMEOUT (-4) /* a bounded device wait gave up */
+
+enum knng_join_mode {
+    KNNG_JOIN_FWD = 0,     /* N_i = G[i] */
+    KNNG_JOIN_FWD_REV = 1  /* N_i = G[i] + R[i], R[i] the k closest reverse neighbours */
+};
+
+enum knng_precision {
+    KNNG_FP32 = 0          /* canonical FP32 everywhere */
+};
+
+typedef struct knng_params {
+    int k;               /* neighbours per point (Alg. 1 "k: scale of k-NN Graph") */
+    int leaf_max;        /* cluster-size threshold (Sec. 3.1, e.g. 50) */
+    int tree_passes;     /* I_0, the rounds of Alg. 1; each uses a new partition */
+    int refine_rounds;   /* neighbour-of-neighbour rounds after the passes */
+    int join_mode;       /* enum knng_join_mode */
+    int precision;       /* enum knng_precision */
+    int twomeans_iters;  /* Lloyd iterations T per two-means split (>= 0) */
+    uint64_t seed;       /* partition seed; pass p uses SplitMix64(seed ^ p) */
+} knng_params;
+
+/* Defaults: k 10, leaf_max 64, tree_passes 1, refine_rounds 0,
+ * join_mode FWD_REV, precision FP32, twomeans_iters 4, seed 0. */
+KNNG_API void knng_default_params(knng_params *p);
+
+/*
+ * Build the kNN graph of `data` (Alg. 1, Sec. 3.1): `rounds` tree passes
+ * (I_0; the paper calls one partition-and-compare cycle a "round"), each a
+ * balanced two-means tree with clusters of at most leaf_max points followed by
+ * the all-pairs update inside every cluster; no refinement; FP32; default
+ * stream; `seed` fixes the partitions.
+ * out_ids, out_dists: n x k, written in full.
+ * Errors: KNNG_EINVAL if n <= k, k or D or leaf_max out of range, rounds < 1,
+ * a NULL pointer, or non-finite input.
+ */
+KNNG_API int knng_build(const float *data, int64_t n, int D, int k, int leaf_max, int rounds,
+               uint64_t seed, int32_t *out_ids, float *out_dists);
+
+/*
+ * Build with every parameter (Sec. 3.1 / Alg. 1, then p->refine_rounds
+ * neighbour-of-neighbour rounds, Sec. 1 prior art) on `stream`.
+ * Same outputs and errors as knng_build; tree_passes may be 0 only when
+ * refine_rounds is 0 too (the graph is then all empty slots).
+ */
+KNNG_API int knng_build_ex(const float *data, int64_t n, int D, const knng_params *p,
+                  int32_t *out_ids, float *out_dists, void *stream);
+
+/*
+ * Refinement only: p->refine_rounds local-join rounds (Jacobi: every offer of
+ * a round comes from the graph as it stood before the round) applied to the
+ * graph (ids_inout, dists_inout), which must satisfy the graph conventions and
+ * hold canonical distances.  Uses p->k (must equal the graph's k) and
+ * p->join_mode.  Also serves to resume a saved graph.
+ */
+KNNG_API int knng_refine(const float *data, int64_t n, int D, const knng_params *p,
+                int32_t *ids_inout, float *dists_inout, void *stream);
+
+/*
+ * The partition of tree pass `pass` (Sec. 3.1: recursive two-means
+ * bisection), exactly as knng_build_ex computes it for the same seed,
+ * leaf_max and twomeans_iters.  out_perm: n ids, the clusters contiguous,
+ * ids ascending inside a cluster.  out_leaf_offsets: 2^L + 1 offsets into
+ * out_perm, L = the least depth with ceil(n / 2^L) <= leaf_max; cluster c is
+ * out_perm[off[c] .. off[c+1]).  Use knng_tree_depth to size it.
+ */
+KNNG_API int knng_partition(const float *data, int64_t n, int D, int leaf_max, int twomeans_iters,
+                   uint64_t seed, int pass, int32_t *out_perm, int64_t *out_leaf_offsets,
+                   void *stream);
+
+/* Depth L of the balanced tree for n points and threshold leaf_max (-1 if invalid). */
+KNNG_API int knng_tree_depth(int64_t n, int leaf_max);
+
+/*
+ * The leaf stage of Alg. 1 on a given partition: for every cluster and every
+ * pair <i, j> in it, i != j, update G[i] and G[j] with d(x_i, x_j).
+ * perm / leaf_offsets as knng_partition returns them (any partition into
+ * clusters of 2..256 points is accepted).  (ids_inout, dists_inout) is the
+ * graph G, updated in place.
+ */
+KNNG_API int knng_leaf_update(const float *data, int64_t n, int D, int k, const int32_t *perm,
+                     const int64_t *leaf_offsets, int64_t n_leaves, int32_t *ids_inout,
+                     float *dists_inout, void *stream);
+
+/*
+ * Exact k nearest neighbours (the problem statement of Sec. 1, each listed
+ * point as a query against the other n - 1) of the s rows listed in `sample`
+ * (all rows in order when sample is NULL, then s must equal n), canonical FP32
+ * distances, ties by id.  out_ids, out_dists: s x k.  Ground truth for recall.
+ */
+KNNG_API int knng_exact(const float *data, int64_t n, int D, int k, const int32_t *sample, int64_t s,
+               int32_t *out_ids, float *out_dists, void *stream);
+
+/*
+ * Recall of a graph (ids, dists: n x k) on the sampled rows against their
+ * exact lists (gt_ids, gt_dists: s x k, as knng_exact returns them).
+ * out_recall_ids: mean over rows of |G[i] & GT[i]| / k.
+ * out_recall_tie: mean over rows of the share of real entries of G[i] whose
+ * distance is <= the k-th exact distance of row i (counts any correct
+ * neighbour among equal distances).  out_* are host pointers.
+ */
+KNNG_API int knng_recall(const int32_t *ids, const float *dists, const int32_t *gt_ids,
+                const float *gt_dists, const int32_t *sample, int64_t s, int k,
+                double *out_recall_ids, double *out_recall_tie, void *stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+KNNG_API const char *knng_last_error(void);
+
+/* Peak device workspace (bytes) knng_build_ex allocates for these arguments. */
+KNNG_API size_t knng_workspace_bytes(int64_t n, int D, const knng_params *p);
+
+/*
+ * Kernel statistics (process-wide).  While enabled, every kernel launch is
+ * counted per kernel name together with its algorithmic bytes and flops (the
+ * data the method must move or compute, not what the hardware moved); with
+ * timing on, CUDA events on the launching stream bracket each launch and the
+ * summed device time is recorded too.
+ */
+typedef struct knng_kernel_stat {
+    char name[32];
+    uint64_t launches;
+    double ms;       /* summed device time, 0 when timing is off */
+    double bytes;    /* summed algorithmic bytes */
+    double flops;    /* summed algorithmic flops */
+} knng_kernel_stat;
+
+KNNG_API int knng_stats_enable(int on, int timing);
+KNNG_API void knng_stats_reset(void);
+KNNG_API int knng_stats_count(void);
+KNNG_API int knng_stats_get(int index, knng_kernel_stat *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KNNG_H */

@@ -1,0 +1,30 @@
+"""GB300 (sm_103a) kNN-graph construction by two-means trees
+(Zhao, Yang, Deng, arXiv 1701.08475, Sec. 3.1, Alg. 1) with neighbour-of-
+neighbour refinement.
+
+A thin binding of the C ABI declared in include/knng.h: every function has
+the name of its C entry point, marshals tensors to plain pointers and sizes,
+and calls the CUDA library.  No step of the method runs in Python.
+"""
+from ._lib import (  # noqa: F401
+    KNNG_FP32,
+    KNNG_JOIN_FWD,
+    KNNG_JOIN_FWD_REV,
+    KnngError,
+    Params,
+    default_params,
+    knng_build,
+    knng_build_ex,
+    knng_exact,
+    knng_leaf_update,
+    knng_partition,
+    knng_recall,
+    knng_refine,
+    knng_tree_depth,
+    knng_workspace_bytes,
+    library_path,
+    load,
+    stats,
+    stats_enable,
+    stats_reset,
+)

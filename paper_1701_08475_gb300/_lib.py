@@ -1,0 +1,284 @@
+"""ctypes binding of libknng.so (the C ABI of include/knng.h).
+
+Argument marshalling only: tensors and arrays become pointers and sizes,
+outputs are allocated like the input (same device; numpy in, numpy out), and
+errors become KnngError.  If the CUDA library is missing the import of a
+function fails loudly; there is no fallback.
+"""
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libknng.so")
+_lock = threading.Lock()
+_lib = None
+
+KNNG_JOIN_FWD = 0
+KNNG_JOIN_FWD_REV = 1
+KNNG_FP32 = 0
+
+_CODES = {-1: "KNNG_EINVAL", -2: "KNNG_ENOMEM", -3: "KNNG_ECUDA", -4: "KNNG_ETIMEOUT"}
+
+
+class KnngError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_CODES.get(code, "error"), code, msg))
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("leaf_max", ctypes.c_int), ("tree_passes", ctypes.c_int),
+                ("refine_rounds", ctypes.c_int), ("join_mode", ctypes.c_int), ("precision", ctypes.c_int),
+                ("twomeans_iters", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def load():
+    """Load libknng.so (built by __graft_entry__.build() or build.py)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError("libknng.so is not built (run __graft_entry__.build()); no fallback exists")
+        lib = ctypes.CDLL(_LIB_PATH)
+        P, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64
+        PP = ctypes.POINTER(Params)
+        sig = {
+            "knng_default_params": (None, [PP]),
+            "knng_build": (i32, [P, i64, i32, i32, i32, i32, u64, P, P]),
+            "knng_build_ex": (i32, [P, i64, i32, PP, P, P, P]),
+            "knng_refine": (i32, [P, i64, i32, PP, P, P, P]),
+            "knng_partition": (i32, [P, i64, i32, i32, i32, u64, i32, P, P, P]),
+            "knng_tree_depth": (i32, [i64, i32]),
+            "knng_leaf_update": (i32, [P, i64, i32, i32, P, P, i64, P, P, P]),
+            "knng_exact": (i32, [P, i64, i32, i32, P, i64, P, P, P]),
+            "knng_recall": (i32, [P, P, P, P, P, i64, i32, P, P, P]),
+            "knng_last_error": (ctypes.c_char_p, []),
+            "knng_workspace_bytes": (ctypes.c_size_t, [i64, i32, PP]),
+            "knng_stats_enable": (i32, [i32, i32]),
+            "knng_stats_reset": (None, []),
+            "knng_stats_count": (i32, []),
+            "knng_stats_get": (i32, [i32, ctypes.POINTER(KernelStat)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(code):
+    if code != 0:
+        raise KnngError(code, load().knng_last_error().decode())
+
+
+# ---------------------------------------------------------------- marshalling
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        return ctypes.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _contig(x, dtype_name):
+    """x as a C-contiguous array of the named dtype (torch stays torch)."""
+    if _is_torch(x):
+        import torch
+        dt = {"float32": torch.float32, "int32": torch.int32, "int64": torch.int64}[dtype_name]
+        if x.dtype != dt:
+            raise TypeError("expected %s, got %s" % (dt, x.dtype))
+        return x.contiguous()
+    a = np.ascontiguousarray(x)
+    if a.dtype != np.dtype(dtype_name):
+        raise TypeError("expected %s, got %s" % (dtype_name, a.dtype))
+    return a
+
+
+def _empty_like_input(x, shape, dtype_name):
+    if _is_torch(x):
+        import torch
+        dt = {"float32": torch.float32, "int32": torch.int32, "int64": torch.int64}[dtype_name]
+        return torch.empty(shape, dtype=dt, device=x.device, pin_memory=False)
+    return np.empty(shape, dtype=dtype_name)
+
+
+class _DeviceCtx:
+    """Make x's CUDA device current and pick its current stream."""
+
+    def __init__(self, x, stream):
+        self.x, self.stream, self.ctx = x, stream, None
+
+    def __enter__(self):
+        s = self.stream
+        if _is_torch(self.x) and self.x.is_cuda:
+            import torch
+            self.ctx = torch.cuda.device(self.x.device)
+            self.ctx.__enter__()
+            if s is None:
+                s = torch.cuda.current_stream(self.x.device).cuda_stream
+        elif s is not None and hasattr(s, "cuda_stream"):
+            s = s.cuda_stream
+        if s is not None and hasattr(s, "cuda_stream"):
+            s = s.cuda_stream
+        return ctypes.c_void_p(s) if s else None
+
+    def __exit__(self, *a):
+        if self.ctx is not None:
+            self.ctx.__exit__(*a)
+
+
+def default_params(**kw):
+    p = Params()
+    load().knng_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+# ---------------------------------------------------------------- entry points
+def knng_build(data, k, leaf_max, rounds=1, seed=0):
+    """Alg. 1 with `rounds` tree passes, FP32, no refinement; returns (ids, dists)."""
+    data = _contig(data, "float32")
+    n, D = data.shape
+    ids = _empty_like_input(data, (n, k), "int32")
+    d = _empty_like_input(data, (n, k), "float32")
+    with _DeviceCtx(data, None):
+        if _is_torch(data) and data.is_cuda:
+            import torch
+            torch.cuda.current_stream(data.device).synchronize()   # knng_build runs on the default stream
+        _check(load().knng_build(_ptr(data), n, D, k, leaf_max, rounds, seed & (2**64 - 1), _ptr(ids), _ptr(d)))
+    return ids, d
+
+
+def knng_build_ex(data, params, stream=None, out=None):
+    """The whole build with explicit params; returns (ids, dists)."""
+    data = _contig(data, "float32")
+    n, D = data.shape
+    k = params.k
+    if out is None:
+        ids = _empty_like_input(data, (n, k), "int32")
+        d = _empty_like_input(data, (n, k), "float32")
+    else:
+        ids, d = out
+    with _DeviceCtx(data, stream) as s:
+        _check(load().knng_build_ex(_ptr(data), n, D, ctypes.byref(params), _ptr(ids), _ptr(d), s))
+    return ids, d
+
+
+def knng_refine(data, ids, dists, params, stream=None):
+    """Refinement rounds on (ids, dists), in place; returns them."""
+    data = _contig(data, "float32")
+    n, D = data.shape
+    assert ids.shape == (n, params.k) and dists.shape == (n, params.k)
+    ids = _contig(ids, "int32")
+    dists = _contig(dists, "float32")
+    with _DeviceCtx(data, stream) as s:
+        _check(load().knng_refine(_ptr(data), n, D, ctypes.byref(params), _ptr(ids), _ptr(dists), s))
+    return ids, dists
+
+
+def knng_tree_depth(n, leaf_max):
+    return int(load().knng_tree_depth(n, leaf_max))
+
+
+def knng_partition(data, leaf_max, twomeans_iters=4, seed=0, pass_=0, stream=None):
+    """(perm, leaf_offsets) of tree pass `pass_`."""
+    data = _contig(data, "float32")
+    n, D = data.shape
+    L = knng_tree_depth(n, leaf_max)
+    if L < 0:
+        raise KnngError(-1, "bad leaf_max")
+    perm = _empty_like_input(data, (n,), "int32")
+    off = _empty_like_input(data, ((1 << L) + 1,), "int64")
+    with _DeviceCtx(data, stream) as s:
+        _check(load().knng_partition(_ptr(data), n, D, leaf_max, twomeans_iters, seed & (2**64 - 1), pass_,
+                                     _ptr(perm), _ptr(off), s))
+    return perm, off
+
+
+def knng_leaf_update(data, k, perm, leaf_offsets, ids, dists, stream=None):
+    """Leaf stage of Alg. 1 on a given partition, in place on (ids, dists)."""
+    data = _contig(data, "float32")
+    n, D = data.shape
+    perm = _contig(perm, "int32")
+    leaf_offsets = _contig(leaf_offsets, "int64")
+    ids = _contig(ids, "int32")
+    dists = _contig(dists, "float32")
+    with _DeviceCtx(data, stream) as s:
+        _check(load().knng_leaf_update(_ptr(data), n, D, k, _ptr(perm), _ptr(leaf_offsets), len(leaf_offsets) - 1,
+                                       _ptr(ids), _ptr(dists), s))
+    return ids, dists
+
+
+def knng_exact(data, k, sample=None, stream=None):
+    """Exact k-NN lists of the sampled rows (all rows if sample is None)."""
+    data = _contig(data, "float32")
+    n, D = data.shape
+    if sample is not None:
+        sample = _contig(sample, "int32")
+    s_rows = n if sample is None else len(sample)
+    ids = _empty_like_input(data, (s_rows, k), "int32")
+    d = _empty_like_input(data, (s_rows, k), "float32")
+    with _DeviceCtx(data, stream) as s:
+        _check(load().knng_exact(_ptr(data), n, D, k, _ptr(sample), s_rows, _ptr(ids), _ptr(d), s))
+    return ids, d
+
+
+def knng_recall(ids, dists, gt_ids, gt_dists, sample, stream=None):
+    """(recall by id set, tie-tolerant recall) of a graph on sampled rows."""
+    ids = _contig(ids, "int32")
+    dists = _contig(dists, "float32")
+    gt_ids = _contig(gt_ids, "int32")
+    gt_dists = _contig(gt_dists, "float32")
+    sample = _contig(sample, "int32")
+    k = ids.shape[1]
+    ri = ctypes.c_double()
+    rt = ctypes.c_double()
+    with _DeviceCtx(ids, stream) as s:
+        _check(load().knng_recall(_ptr(ids), _ptr(dists), _ptr(gt_ids), _ptr(gt_dists), _ptr(sample), len(sample), k,
+                                  ctypes.byref(ri), ctypes.byref(rt), s))
+    return ri.value, rt.value
+
+
+def knng_workspace_bytes(n, D, params):
+    return int(load().knng_workspace_bytes(n, D, ctypes.byref(params)))
+
+
+def stats_enable(on=True, timing=False):
+    load().knng_stats_enable(1 if on else 0, 1 if timing else 0)
+
+
+def stats_reset():
+    load().knng_stats_reset()
+
+
+def stats():
+    """{kernel name: dict(launches, ms, bytes, flops)} summed since the last reset."""
+    lib = load()
+    out = {}
+    st = KernelStat()
+    for i in range(lib.knng_stats_count()):
+        if lib.knng_stats_get(i, ctypes.byref(st)) == 0:
+            out[st.name.decode()] = dict(launches=int(st.launches), ms=float(st.ms), bytes=float(st.bytes),
+                                         flops=float(st.flops))
+    return out

@@ -1,0 +1,872 @@
+// api.cu -- the C ABI (include/knng.h): argument checks, pointer marshalling,
+// workspace, the build schedule of Alg. 1 (Sec. 3.1) plus refinement rounds,
+// and kernel statistics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace knng {
+
+size_t join_smem_bytes(int D, int mcap);
+int join_blocks_per_lane(int mcap);
+
+// ---------------------------------------------------------------- errors
+namespace {
+thread_local std::string g_last_error;
+
+struct Error {
+    int code;
+};
+
+[[noreturn]] void fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    throw Error{code};
+}
+
+void cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return;
+    if (e == cudaErrorMemoryAllocation) fail(KNNG_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    fail(KNNG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+template <class F>
+int guarded(F&& f) {
+    g_last_error.clear();
+    try {
+        f();
+        return KNNG_OK;
+    } catch (const Error& e) {
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        return KNNG_ENOMEM;
+    }
+}
+}  // namespace
+
+// ---------------------------------------------------------------- stats
+namespace {
+struct StatRegistry {
+    std::mutex mu;
+    bool on = false, timing = false;
+    std::map<std::string, knng_kernel_stat> stats;
+    struct Pending {
+        std::string name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> free_events;
+
+    cudaEvent_t event() {
+        if (!free_events.empty()) {
+            cudaEvent_t e = free_events.back();
+            free_events.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    // called after the stream has been synchronised
+    void flush() {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto& p : pending) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) stats[p.name].ms += ms;
+            free_events.push_back(p.a);
+            free_events.push_back(p.b);
+        }
+        pending.clear();
+        cudaGetLastError();
+    }
+};
+StatRegistry& reg() {
+    static StatRegistry* r = new StatRegistry();
+    return *r;
+}
+}  // namespace
+
+LaunchScope::LaunchScope(const char* name, cudaStream_t s, double bytes, double flops)
+    : name_(name), s_(s), bytes_(bytes), flops_(flops), slot_(-1) {
+    StatRegistry& r = reg();
+    std::lock_guard<std::mutex> lk(r.mu);
+    if (!r.on) return;
+    knng_kernel_stat& st = r.stats[name];
+    if (st.name[0] == 0) snprintf(st.name, sizeof st.name, "%s", name);
+    st.launches += 1;
+    st.bytes += bytes;
+    st.flops += flops;
+    if (r.timing) {
+        StatRegistry::Pending p{name, r.event(), r.event()};
+        cudaEventRecord(p.a, s);
+        r.pending.push_back(p);
+        slot_ = (int)r.pending.size() - 1;
+    }
+}
+
+LaunchScope::~LaunchScope() {
+    StatRegistry& r = reg();
+    std::lock_guard<std::mutex> lk(r.mu);
+    if (slot_ >= 0 && slot_ < (int)r.pending.size()) cudaEventRecord(r.pending[slot_].b, s_);
+}
+
+// ---------------------------------------------------------------- memory
+namespace {
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+cudaMemPool_t device_pool() {
+    int dev = 0;
+    cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) return it->second;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    cuda_check(cudaMemPoolCreate(&pool, &props), "cudaMemPoolCreate");
+    uint64_t keep = ~0ull;  // keep freed memory for the next call
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+    return pool;
+}
+
+// One stream-ordered allocation carved into aligned pieces.
+struct Workspace {
+    cudaStream_t s = nullptr;
+    char* base = nullptr;
+    size_t size = 0, used = 0;
+
+    template <class T>
+    T* take(size_t count) {
+        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        size_t off = used;
+        used += bytes;
+        return base ? reinterpret_cast<T*>(base + off) : nullptr;
+    }
+    void allocate(cudaStream_t stream) {
+        s = stream;
+        size = used;
+        used = 0;
+        if (size == 0) return;
+        void* p = nullptr;
+        cuda_check(cudaMallocFromPoolAsync(&p, size, device_pool(), s), "workspace allocation");
+        base = static_cast<char*>(p);
+    }
+    ~Workspace() {
+        if (base) cudaFreeAsync(base, s);
+    }
+};
+
+bool is_device_ptr(const void* p) {
+    if (p == nullptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// A caller buffer as the kernels see it: the caller's device pointer, or a
+// workspace copy of a host buffer.
+template <class T>
+struct DevBuf {
+    T* host = nullptr;  // non-null when the caller passed host memory
+    T* dev = nullptr;
+    size_t count = 0;
+};
+
+template <class T>
+void bind(Workspace& ws, DevBuf<T>& b, const T* caller, size_t count, bool pass) {
+    b.count = count;
+    if (is_device_ptr(caller)) {
+        b.dev = const_cast<T*>(caller);
+        b.host = nullptr;
+    } else {
+        b.host = const_cast<T*>(caller);
+        b.dev = ws.take<T>(count);
+        (void)pass;
+    }
+}
+
+template <class T>
+void upload(DevBuf<T>& b, cudaStream_t s) {
+    if (b.host && b.count)
+        cuda_check(cudaMemcpyAsync(b.dev, b.host, b.count * sizeof(T), cudaMemcpyHostToDevice, s), "H2D copy");
+}
+template <class T>
+void download(DevBuf<T>& b, cudaStream_t s) {
+    if (b.host && b.count)
+        cuda_check(cudaMemcpyAsync(b.host, b.dev, b.count * sizeof(T), cudaMemcpyDeviceToHost, s), "D2H copy");
+}
+
+__global__ void k_iota(int32_t* p, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        p[e] = (int32_t)e;
+}
+}  // namespace
+
+// ---------------------------------------------------------------- tree plan
+namespace {
+int tree_depth(int64_t n, int leaf_max) {
+    int L = 0;
+    while ((n + ((int64_t)1 << L) - 1) / ((int64_t)1 << L) > leaf_max) ++L;
+    return L;
+}
+
+int bits_for(int64_t v) {  // bits to hold values 0..v
+    int b = 0;
+    while (((int64_t)1 << b) <= v) ++b;
+    return b;
+}
+
+// Offsets of every level, the tiles of every sweep, and where they live in
+// one device array.
+struct TreePlan {
+    int L = 0;
+    int64_t n = 0;
+    std::vector<std::vector<int32_t>> off;  // per level (L + 1 levels; off[L] = leaves)
+    std::vector<LevelPlan> levels;
+    std::vector<int32_t> host;               // packed device image
+    struct Idx {
+        size_t seg_off, tiles, seg_tile0;        // element offsets into the image
+    };
+    std::vector<Idx> idx;
+    size_t leaf_off_at = 0;
+    int nseg_max = 0, ntiles_max = 0, nseg_large_max = 0, max_leaf = 0;
+
+    void make(int64_t n_, int leaf_max) {
+        n = n_;
+        L = tree_depth(n, leaf_max);
+        off.assign(L + 1, {});
+        off[0] = {0, (int32_t)n};
+        for (int l = 0; l < L; ++l) {
+            auto& o = off[l];
+            auto& nx = off[l + 1];
+            nx.clear();
+            for (size_t sgi = 0; sgi + 1 < o.size(); ++sgi) {
+                nx.push_back(o[sgi]);
+                nx.push_back(o[sgi] + (o[sgi + 1] - o[sgi]) / 2);
+            }
+            nx.push_back((int32_t)n);
+        }
+        host.clear();
+        levels.assign(L, {});
+        idx.assign(L, {});
+        nseg_max = ntiles_max = nseg_large_max = 0;
+        for (int l = 0; l < L; ++l) {
+            const auto& o = off[l];
+            const int nseg = (int)o.size() - 1;
+            std::vector<int32_t> tiles, tile0;
+            int max_m = 0;
+            for (int sgi = 0; sgi < nseg; ++sgi) {
+                tile0.push_back((int32_t)(tiles.size() / 4));
+                const int a = o[sgi], b = o[sgi + 1];
+                max_m = std::max(max_m, b - a);
+                for (int t = a; t < b; t += kTile) {
+                    tiles.push_back(sgi);
+                    tiles.push_back(t);
+                    tiles.push_back(std::min(b, t + kTile));
+                    tiles.push_back(t == a ? 1 : 0);
+                }
+            }
+            tile0.push_back((int32_t)(tiles.size() / 4));
+            LevelPlan& lp = levels[l];
+            lp.level = l;
+            lp.n = (int)n;
+            lp.nseg = nseg;
+            lp.ntiles = (int)tiles.size() / 4;
+            lp.max_m = max_m;
+            lp.pos_bits = bits_for(max_m - 1);
+            lp.small = max_m <= kSmallMax;
+            nseg_max = std::max(nseg_max, nseg);
+            ntiles_max = std::max(ntiles_max, lp.ntiles);
+            if (!lp.small) nseg_large_max = std::max(nseg_large_max, nseg);
+            // int4 tiles need 16-byte alignment in the packed image
+            while (host.size() % 4) host.push_back(0);
+            idx[l].tiles = host.size();
+            host.insert(host.end(), tiles.begin(), tiles.end());
+            idx[l].seg_off = host.size();
+            host.insert(host.end(), o.begin(), o.end());
+            idx[l].seg_tile0 = host.size();
+            host.insert(host.end(), tile0.begin(), tile0.end());
+        }
+        leaf_off_at = host.size();
+        host.insert(host.end(), off[L].begin(), off[L].end());
+        max_leaf = 0;
+        for (size_t i = 0; i + 1 < off[L].size(); ++i) max_leaf = std::max(max_leaf, off[L][i + 1] - off[L][i]);
+    }
+    // point the level plans into the uploaded image
+    void rebase(const int32_t* dev) {
+        for (int l = 0; l < L; ++l) {
+            levels[l].tiles = reinterpret_cast<const int4*>(dev + idx[l].tiles);
+            levels[l].seg_off = dev + idx[l].seg_off;
+            levels[l].seg_tile0 = dev + idx[l].seg_tile0;
+        }
+    }
+};
+}  // namespace
+
+// ---------------------------------------------------------------- the build
+namespace {
+
+struct Args {
+    int64_t n;
+    int D;
+    knng_params p;
+};
+
+void validate_common(const void* data, int64_t n, int D, int k) {
+    if (!data) fail(KNNG_EINVAL, "data is NULL");
+    if (D < 1 || D > 4096) fail(KNNG_EINVAL, "D = %d out of range [1, 4096]", D);
+    if (k < 1 || k > 64) fail(KNNG_EINVAL, "k = %d out of range [1, 64]", k);
+    if (n <= k) fail(KNNG_EINVAL, "n = %lld must exceed k = %d", (long long)n, k);
+    if (n >= ((int64_t)1 << 31)) fail(KNNG_EINVAL, "n = %lld must be below 2^31", (long long)n);
+    if (n * (int64_t)k >= ((int64_t)1 << 31)) fail(KNNG_EINVAL, "n * k must be below 2^31");
+}
+
+void validate_params(const knng_params* p, int64_t n) {
+    if (!p) fail(KNNG_EINVAL, "params is NULL");
+    if (p->tree_passes < 0) fail(KNNG_EINVAL, "tree_passes = %d < 0", p->tree_passes);
+    if (p->refine_rounds < 0) fail(KNNG_EINVAL, "refine_rounds = %d < 0", p->refine_rounds);
+    if (p->tree_passes == 0 && p->refine_rounds > 0)
+        fail(KNNG_EINVAL, "refine_rounds > 0 needs tree_passes >= 1");
+    if (p->tree_passes > 0 && (p->leaf_max < 2 * (p->k + 1) || p->leaf_max > 256))
+        fail(KNNG_EINVAL, "leaf_max = %d out of range [2(k+1) = %d, 256]", p->leaf_max, 2 * (p->k + 1));
+    if (p->join_mode != KNNG_JOIN_FWD && p->join_mode != KNNG_JOIN_FWD_REV)
+        fail(KNNG_EINVAL, "join_mode = %d unknown", p->join_mode);
+    if (p->precision != KNNG_FP32) fail(KNNG_EINVAL, "precision = %d unsupported", p->precision);
+    if (p->twomeans_iters < 0 || p->twomeans_iters > 64)
+        fail(KNNG_EINVAL, "twomeans_iters = %d out of range [0, 64]", p->twomeans_iters);
+    const int m = p->join_mode == KNNG_JOIN_FWD_REV ? 2 * p->k : p->k;
+    if (p->refine_rounds > 0 && m > 64) fail(KNNG_EINVAL, "refinement supports k <= 32 with reverse lists");
+    (void)n;
+}
+
+constexpr size_t kOfferBudgetBytes = size_t(8) << 30;
+
+struct BuildLayout {
+    // sizes only; filled twice (layout, then real pointers)
+    SplitBuffers sb{};
+    JoinBuffers jb{};
+    int32_t *perm_a = nullptr, *perm_b = nullptr, *plan_dev = nullptr;
+    uint64_t *G = nullptr, *G2 = nullptr;
+    int* status = nullptr;
+    int64_t nodes_per_chunk = 0;
+};
+
+void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, bool tree, bool join) {
+    const int64_t n = a.n;
+    const int k = a.p.k, D = a.D;
+    b.status = ws.take<int>(4);
+    b.G = ws.take<uint64_t>((size_t)n * k);
+    if (tree) {
+        b.perm_a = ws.take<int32_t>(n);
+        b.perm_b = ws.take<int32_t>(n);
+        b.plan_dev = ws.take<int32_t>(tp.host.size());
+        const int ns = std::max(tp.nseg_max, 1), nt = std::max(tp.ntiles_max, 1);
+        const int nl = std::max(tp.nseg_large_max, 1);
+        b.sb.W = ws.take<float>((size_t)ns * D);
+        b.sb.S = ws.take<float>(n);
+        b.sb.thr = ws.take<uint64_t>(ns);
+        b.sb.st = ws.take<SelState>(ns);
+        b.sb.ghist = ws.take<uint32_t>((size_t)nl << kRadixBits);
+        b.sb.ticket = ws.take<uint32_t>(nl);
+        b.sb.partial = ws.take<double>((size_t)nt * 2 * D);
+        b.sb.tile_left = ws.take<int32_t>(nt);
+        b.sb.status = b.status;
+    }
+    if (join) {
+        const bool rev = a.p.join_mode == KNNG_JOIN_FWD_REV;
+        const int64_t m = rev ? 2 * k : k;
+        const int64_t per_node = std::max<int64_t>(m * (m - 1), 1);
+        int64_t cap = (int64_t)(kOfferBudgetBytes / 20);
+        cap = std::min<int64_t>(cap, per_node * n);
+        cap = std::min<int64_t>(cap, ((int64_t)1 << 31) - 1);
+        b.nodes_per_chunk = std::max<int64_t>(cap / per_node, 1);
+        cap = b.nodes_per_chunk * per_node;
+        b.G2 = ws.take<uint64_t>((size_t)n * k);
+        if (rev) {
+            b.jb.deg = ws.take<int32_t>(n + 1);
+            b.jb.roff = ws.take<int32_t>(n + 1);
+            b.jb.cur = ws.take<int32_t>(n);
+            b.jb.rbuf = ws.take<uint64_t>((size_t)n * k);
+            b.jb.R = ws.take<uint64_t>((size_t)n * k);
+        }
+        b.jb.pcnt = ws.take<int32_t>(n + 1);
+        b.jb.poff = ws.take<int32_t>(n + 1);
+        b.jb.pcur = ws.take<int32_t>(n);
+        b.jb.ptgt = ws.take<uint32_t>(cap);
+        b.jb.pkey = ws.take<uint64_t>(cap);
+        b.jb.grouped = ws.take<uint64_t>(cap);
+        b.jb.cap = cap;
+        b.jb.counter = ws.take<uint32_t>(4);
+        b.jb.scan_tmp = ws.take<int32_t>(scan_tmp_ints(n));
+    }
+}
+
+int grid_1d(int64_t count) {
+    int64_t g = (count + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+}
+
+void check_status(const int* dstatus, cudaStream_t s) {
+    int st = 0;
+    cuda_check(cudaMemcpyAsync(&st, dstatus, sizeof(int), cudaMemcpyDeviceToHost, s), "status read");
+    cuda_check(cudaStreamSynchronize(s), "stream synchronize");
+    reg().flush();
+    if (st & kStatusNonFinite) fail(KNNG_EINVAL, "data holds a non-finite value");
+    if (st & kStatusBadInput) fail(KNNG_EINVAL, "an id or offset given by the caller is out of range");
+    if (st & kStatusOverflow) fail(KNNG_ECUDA, "internal offer buffer overflow");
+    if (st & kStatusInternal) fail(KNNG_ECUDA, "internal consistency check failed");
+}
+
+// Partition of one pass into perm_a (leaves contiguous).  Returns the buffer
+// holding the result.
+int32_t* run_partition(const float* X, const Args& a, const TreePlan& tp, BuildLayout& b, int pass, cudaStream_t s) {
+    const uint64_t ps = splitmix64(a.p.seed ^ (uint64_t)pass);
+    int32_t* pin = b.perm_a;
+    int32_t* pout = b.perm_b;
+    k_iota<<<grid_1d(a.n), 256, 0, s>>>(pin, a.n);
+    for (int l = 0; l < tp.L; ++l) {
+        run_split_level(X, a.D, tp.levels[l], a.p.twomeans_iters, ps, pin, pout, b.sb, s);
+        std::swap(pin, pout);
+    }
+    return pin;
+}
+
+void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& tp, cudaStream_t s) {
+    const int64_t n = a.n;
+    const int k = a.p.k;
+    launch_check_finite(X, n * (int64_t)a.D, b.status, s);
+    launch_fill_empty(b.G, n * k, s);
+    if (a.p.tree_passes > 0)
+        cuda_check(cudaMemcpyAsync(b.plan_dev, tp.host.data(), tp.host.size() * 4, cudaMemcpyHostToDevice, s),
+                   "plan upload");
+    for (int pass = 0; pass < a.p.tree_passes; ++pass) {
+        int32_t* perm = run_partition(X, a, tp, b, pass, s);
+        launch_leaf_fp32(X, a.D, perm, b.plan_dev + tp.leaf_off_at, (int)(tp.off[tp.L].size() - 1), tp.max_leaf, k,
+                         b.G, b.status, s);
+    }
+    for (int r = 0; r < a.p.refine_rounds; ++r) {
+        run_join_round(X, n, a.D, k, a.p.join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, b.jb, b.nodes_per_chunk,
+                       b.status, s);
+        std::swap(b.G, b.G2);
+    }
+}
+
+}  // namespace
+}  // namespace knng
+
+using namespace knng;
+
+extern "C" {
+
+void knng_default_params(knng_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->k = 10;
+    p->leaf_max = 64;
+    p->tree_passes = 1;
+    p->refine_rounds = 0;
+    p->join_mode = KNNG_JOIN_FWD_REV;
+    p->precision = KNNG_FP32;
+    p->twomeans_iters = 4;
+    p->seed = 0;
+}
+
+const char* knng_last_error(void) { return g_last_error.c_str(); }
+
+int knng_tree_depth(int64_t n, int leaf_max) {
+    if (n < 1 || leaf_max < 1) return -1;
+    return tree_depth(n, leaf_max);
+}
+
+int knng_build_ex(const float* data, int64_t n, int D, const knng_params* p, int32_t* out_ids, float* out_dists,
+                  void* stream) {
+    return guarded([&] {
+        if (!p) fail(KNNG_EINVAL, "params is NULL");
+        validate_common(data, n, D, p->k);
+        validate_params(p, n);
+        if (!out_ids || !out_dists) fail(KNNG_EINVAL, "output pointer is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        Args a{n, D, *p};
+        TreePlan tp;
+        if (p->tree_passes > 0) tp.make(n, p->leaf_max);
+        Workspace ws;
+        BuildLayout b;
+        DevBuf<float> X;
+        DevBuf<int32_t> oi;
+        DevBuf<float> od;
+        const size_t nk = (size_t)n * p->k;
+        for (int pass = 0; pass < 2; ++pass) {  // layout, then real pointers
+            ws.used = 0;
+            bind(ws, X, data, (size_t)n * D, pass);
+            bind(ws, oi, out_ids, nk, pass);
+            bind(ws, od, out_dists, nk, pass);
+            carve(ws, b, a, tp, p->tree_passes > 0, p->refine_rounds > 0);
+            if (pass == 0) ws.allocate(s);
+        }
+        if (p->tree_passes > 0) tp.rebase(b.plan_dev);
+        cuda_check(cudaMemsetAsync(b.status, 0, sizeof(int), s), "status clear");
+        upload(X, s);
+        build_core(X.dev, a, b, tp, s);
+        launch_unpack(b.G, oi.dev, od.dev, (int64_t)nk, s);
+        download(oi, s);
+        download(od, s);
+        cuda_check(cudaGetLastError(), "kernel launch");
+        check_status(b.status, s);
+    });
+}
+
+int knng_build(const float* data, int64_t n, int D, int k, int leaf_max, int rounds, uint64_t seed,
+               int32_t* out_ids, float* out_dists) {
+    knng_params p;
+    knng_default_params(&p);
+    p.k = k;
+    p.leaf_max = leaf_max;
+    p.tree_passes = rounds;
+    p.refine_rounds = 0;
+    p.seed = seed;
+    if (rounds < 1) {
+        g_last_error = "rounds must be >= 1";
+        return KNNG_EINVAL;
+    }
+    return knng_build_ex(data, n, D, &p, out_ids, out_dists, nullptr);
+}
+
+int knng_refine(const float* data, int64_t n, int D, const knng_params* p, int32_t* ids_inout,
+                float* dists_inout, void* stream) {
+    return guarded([&] {
+        if (!p) fail(KNNG_EINVAL, "params is NULL");
+        validate_common(data, n, D, p->k);
+        knng_params q = *p;
+        q.tree_passes = 1;  // validation of the join parameters only
+        q.leaf_max = std::max(q.leaf_max, 2 * (q.k + 1));
+        q.leaf_max = std::min(q.leaf_max, 256);
+        validate_params(&q, n);
+        if (!ids_inout || !dists_inout) fail(KNNG_EINVAL, "graph pointer is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        Args a{n, D, *p};
+        a.p.tree_passes = 0;
+        TreePlan tp;
+        Workspace ws;
+        BuildLayout b;
+        DevBuf<float> X;
+        DevBuf<int32_t> gi;
+        DevBuf<float> gd;
+        const size_t nk = (size_t)n * p->k;
+        for (int pass = 0; pass < 2; ++pass) {
+            ws.used = 0;
+            bind(ws, X, data, (size_t)n * D, pass);
+            bind(ws, gi, ids_inout, nk, pass);
+            bind(ws, gd, dists_inout, nk, pass);
+            carve(ws, b, a, tp, false, p->refine_rounds > 0);
+            if (pass == 0) ws.allocate(s);
+        }
+        cuda_check(cudaMemsetAsync(b.status, 0, sizeof(int), s), "status clear");
+        upload(X, s);
+        upload(gi, s);
+        upload(gd, s);
+        launch_check_finite(X.dev, n * (int64_t)D, b.status, s);
+        launch_pack(gi.dev, gd.dev, b.G, (int64_t)nk, n, b.status, s);
+        for (int r = 0; r < p->refine_rounds; ++r) {
+            run_join_round(X.dev, n, D, p->k, p->join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, b.jb,
+                           b.nodes_per_chunk, b.status, s);
+            std::swap(b.G, b.G2);
+        }
+        launch_unpack(b.G, gi.dev, gd.dev, (int64_t)nk, s);
+        download(gi, s);
+        download(gd, s);
+        cuda_check(cudaGetLastError(), "kernel launch");
+        check_status(b.status, s);
+    });
+}
+
+int knng_partition(const float* data, int64_t n, int D, int leaf_max, int twomeans_iters, uint64_t seed, int pass,
+                   int32_t* out_perm, int64_t* out_leaf_offsets, void* stream) {
+    return guarded([&] {
+        if (!data || !out_perm || !out_leaf_offsets) fail(KNNG_EINVAL, "NULL pointer");
+        if (D < 1 || D > 4096) fail(KNNG_EINVAL, "D = %d out of range [1, 4096]", D);
+        if (n < 1 || n >= ((int64_t)1 << 31)) fail(KNNG_EINVAL, "n = %lld out of range", (long long)n);
+        if (leaf_max < 2) fail(KNNG_EINVAL, "leaf_max = %d < 2", leaf_max);
+        if (twomeans_iters < 0 || twomeans_iters > 64) fail(KNNG_EINVAL, "twomeans_iters out of range");
+        if (pass < 0) fail(KNNG_EINVAL, "pass < 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        Args a{n, D, {}};
+        knng_default_params(&a.p);
+        a.p.k = 1;
+        a.p.leaf_max = leaf_max;
+        a.p.twomeans_iters = twomeans_iters;
+        a.p.seed = seed;
+        TreePlan tp;
+        tp.make(n, leaf_max);
+        Workspace ws;
+        BuildLayout b;
+        DevBuf<float> X;
+        DevBuf<int32_t> op;
+        const size_t noff = tp.off[tp.L].size();
+        for (int ps = 0; ps < 2; ++ps) {
+            ws.used = 0;
+            bind(ws, X, data, (size_t)n * D, ps);
+            bind(ws, op, out_perm, (size_t)n, ps);
+            carve(ws, b, a, tp, true, false);
+            if (ps == 0) ws.allocate(s);
+        }
+        tp.rebase(b.plan_dev);
+        cuda_check(cudaMemsetAsync(b.status, 0, sizeof(int), s), "status clear");
+        upload(X, s);
+        launch_check_finite(X.dev, n * (int64_t)D, b.status, s);
+        cuda_check(cudaMemcpyAsync(b.plan_dev, tp.host.data(), tp.host.size() * 4, cudaMemcpyHostToDevice, s),
+                   "plan upload");
+        int32_t* perm = run_partition(X.dev, a, tp, b, pass, s);
+        cuda_check(cudaMemcpyAsync(op.dev, perm, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s), "perm copy");
+        download(op, s);
+        std::vector<int64_t> off(tp.off[tp.L].begin(), tp.off[tp.L].end());
+        if (is_device_ptr(out_leaf_offsets))
+            cuda_check(cudaMemcpyAsync(out_leaf_offsets, off.data(), noff * 8, cudaMemcpyHostToDevice, s),
+                       "offsets copy");
+        else
+            memcpy(out_leaf_offsets, off.data(), noff * 8);
+        cuda_check(cudaGetLastError(), "kernel launch");
+        check_status(b.status, s);
+    });
+}
+
+int knng_leaf_update(const float* data, int64_t n, int D, int k, const int32_t* perm, const int64_t* leaf_offsets,
+                     int64_t n_leaves, int32_t* ids_inout, float* dists_inout, void* stream) {
+    return guarded([&] {
+        validate_common(data, n, D, k);
+        if (!perm || !leaf_offsets || !ids_inout || !dists_inout) fail(KNNG_EINVAL, "NULL pointer");
+        if (n_leaves < 0) fail(KNNG_EINVAL, "n_leaves < 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        std::vector<int64_t> off((size_t)n_leaves + 1);
+        if (is_device_ptr(leaf_offsets)) {
+            cuda_check(cudaMemcpyAsync(off.data(), leaf_offsets, off.size() * 8, cudaMemcpyDeviceToHost, s),
+                       "offsets read");
+            cuda_check(cudaStreamSynchronize(s), "stream synchronize");
+        } else {
+            memcpy(off.data(), leaf_offsets, off.size() * 8);
+        }
+        int max_leaf = 0;
+        for (int64_t l = 0; l < n_leaves; ++l) {
+            const int64_t m = off[l + 1] - off[l];
+            if (m < 0 || m > 256 || off[l] < 0 || off[l + 1] > n)
+                fail(KNNG_EINVAL, "leaf %lld has bad offsets", (long long)l);
+            max_leaf = std::max<int>(max_leaf, (int)m);
+        }
+        std::vector<int32_t> off32(off.begin(), off.end());
+        Workspace ws;
+        DevBuf<float> X;
+        DevBuf<int32_t> pm, gi;
+        DevBuf<float> gd;
+        uint64_t* G = nullptr;
+        int32_t* doff = nullptr;
+        int* status = nullptr;
+        const size_t nk = (size_t)n * k;
+        for (int ps = 0; ps < 2; ++ps) {
+            ws.used = 0;
+            bind(ws, X, data, (size_t)n * D, ps);
+            bind(ws, pm, perm, (size_t)n, ps);
+            bind(ws, gi, ids_inout, nk, ps);
+            bind(ws, gd, dists_inout, nk, ps);
+            G = ws.take<uint64_t>(nk);
+            doff = ws.take<int32_t>(off32.size());
+            status = ws.take<int>(4);
+            if (ps == 0) ws.allocate(s);
+        }
+        cuda_check(cudaMemsetAsync(status, 0, sizeof(int), s), "status clear");
+        upload(X, s);
+        upload(pm, s);
+        upload(gi, s);
+        upload(gd, s);
+        cuda_check(cudaMemcpyAsync(doff, off32.data(), off32.size() * 4, cudaMemcpyHostToDevice, s), "offsets");
+        launch_check_finite(X.dev, n * (int64_t)D, status, s);
+        launch_pack(gi.dev, gd.dev, G, (int64_t)nk, n, status, s);
+        launch_check_ids(pm.dev, n, 0, n, status, s);
+        if (n_leaves > 0 && max_leaf >= 2)
+            launch_leaf_fp32(X.dev, D, pm.dev, doff, (int)n_leaves, max_leaf, k, G, status, s);
+        launch_unpack(G, gi.dev, gd.dev, (int64_t)nk, s);
+        download(gi, s);
+        download(gd, s);
+        cuda_check(cudaGetLastError(), "kernel launch");
+        check_status(status, s);
+    });
+}
+
+int knng_exact(const float* data, int64_t n, int D, int k, const int32_t* sample, int64_t s_rows, int32_t* out_ids,
+               float* out_dists, void* stream) {
+    return guarded([&] {
+        validate_common(data, n, D, k);
+        if (!out_ids || !out_dists) fail(KNNG_EINVAL, "output pointer is NULL");
+        if (!sample && s_rows != n) fail(KNNG_EINVAL, "without a sample s must equal n");
+        if (s_rows < 0) fail(KNNG_EINVAL, "s < 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        Workspace ws;
+        DevBuf<float> X;
+        DevBuf<int32_t> smp, oi;
+        DevBuf<float> od;
+        uint64_t* keys = nullptr;
+        int* status = nullptr;
+        const size_t sk = (size_t)s_rows * k;
+        for (int ps = 0; ps < 2; ++ps) {
+            ws.used = 0;
+            bind(ws, X, data, (size_t)n * D, ps);
+            if (sample) bind(ws, smp, sample, (size_t)s_rows, ps);
+            bind(ws, oi, out_ids, sk, ps);
+            bind(ws, od, out_dists, sk, ps);
+            keys = ws.take<uint64_t>(std::max<size_t>(sk, 1));
+            status = ws.take<int>(4);
+            if (ps == 0) ws.allocate(s);
+        }
+        cuda_check(cudaMemsetAsync(status, 0, sizeof(int), s), "status clear");
+        upload(X, s);
+        if (sample) upload(smp, s);
+        launch_check_finite(X.dev, n * (int64_t)D, status, s);
+        if (s_rows > 0) {
+            if (sample) launch_check_ids(smp.dev, s_rows, 0, n, status, s);
+            launch_exact(X.dev, n, D, k, sample ? smp.dev : nullptr, s_rows, keys, status, s);
+            launch_unpack(keys, oi.dev, od.dev, (int64_t)sk, s);
+        }
+        download(oi, s);
+        download(od, s);
+        cuda_check(cudaGetLastError(), "kernel launch");
+        check_status(status, s);
+    });
+}
+
+int knng_recall(const int32_t* ids, const float* dists, const int32_t* gt_ids, const float* gt_dists,
+                const int32_t* sample, int64_t s_rows, int k, double* out_recall_ids, double* out_recall_tie,
+                void* stream) {
+    return guarded([&] {
+        if (!ids || !dists || !gt_ids || !gt_dists || !sample || !out_recall_ids || !out_recall_tie)
+            fail(KNNG_EINVAL, "NULL pointer");
+        if (k < 1 || k > 64) fail(KNNG_EINVAL, "k out of range");
+        if (s_rows < 0) fail(KNNG_EINVAL, "s < 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t sk = (size_t)s_rows * k;
+        // host graphs: gather the sampled rows on the host (marshalling only)
+        std::vector<int32_t> hids, hsmp;
+        std::vector<float> hd;
+        const bool dev = is_device_ptr(ids);
+        if (!dev) {
+            std::vector<int32_t> sm((size_t)s_rows);
+            if (is_device_ptr(sample)) {
+                cuda_check(cudaMemcpy(sm.data(), sample, s_rows * 4, cudaMemcpyDeviceToHost), "sample read");
+            } else {
+                memcpy(sm.data(), sample, s_rows * 4);
+            }
+            hids.resize(sk);
+            hd.resize(sk);
+            hsmp.resize((size_t)s_rows);
+            for (int64_t r = 0; r < s_rows; ++r) {
+                memcpy(&hids[r * k], ids + (size_t)sm[r] * k, 4 * k);
+                memcpy(&hd[r * k], dists + (size_t)sm[r] * k, 4 * k);
+                hsmp[r] = (int32_t)r;
+            }
+        }
+        Workspace ws;
+        DevBuf<int32_t> di, gi, smp;
+        DevBuf<float> dd, gd;
+        unsigned long long* counts = nullptr;
+        for (int ps = 0; ps < 2; ++ps) {
+            ws.used = 0;
+            if (dev) {
+                di.dev = const_cast<int32_t*>(ids);
+                dd.dev = const_cast<float*>(dists);
+                bind(ws, smp, sample, (size_t)s_rows, ps);
+            } else {
+                bind(ws, di, hids.data(), sk, ps);
+                bind(ws, dd, hd.data(), sk, ps);
+                bind(ws, smp, hsmp.data(), (size_t)s_rows, ps);
+            }
+            bind(ws, gi, gt_ids, sk, ps);
+            bind(ws, gd, gt_dists, sk, ps);
+            counts = ws.take<unsigned long long>(2);
+            if (ps == 0) ws.allocate(s);
+        }
+        if (!dev) {
+            upload(di, s);
+            upload(dd, s);
+        }
+        upload(smp, s);
+        upload(gi, s);
+        upload(gd, s);
+        launch_recall(di.dev, dd.dev, gi.dev, gd.dev, smp.dev, s_rows, k, counts, s);
+        unsigned long long hc[2] = {0, 0};
+        cuda_check(cudaMemcpyAsync(hc, counts, sizeof hc, cudaMemcpyDeviceToHost, s), "counts read");
+        cuda_check(cudaGetLastError(), "kernel launch");
+        cuda_check(cudaStreamSynchronize(s), "stream synchronize");
+        reg().flush();
+        const double denom = (double)s_rows * k;
+        *out_recall_ids = s_rows ? hc[0] / denom : 0.0;
+        *out_recall_tie = s_rows ? hc[1] / denom : 0.0;
+    });
+}
+
+size_t knng_workspace_bytes(int64_t n, int D, const knng_params* p) {
+    size_t out = 0;
+    guarded([&] {
+        validate_common((const void*)1, n, D, p ? p->k : 0);
+        validate_params(p, n);
+        Args a{n, D, *p};
+        TreePlan tp;
+        if (p->tree_passes > 0) tp.make(n, p->leaf_max);
+        Workspace ws;
+        BuildLayout b;
+        carve(ws, b, a, tp, p->tree_passes > 0, p->refine_rounds > 0);
+        out = ws.used;
+    });
+    return out;
+}
+
+int knng_stats_enable(int on, int timing) {
+    StatRegistry& r = reg();
+    std::lock_guard<std::mutex> lk(r.mu);
+    r.on = on != 0;
+    r.timing = on != 0 && timing != 0;
+    return KNNG_OK;
+}
+
+void knng_stats_reset(void) {
+    StatRegistry& r = reg();
+    std::lock_guard<std::mutex> lk(r.mu);
+    r.stats.clear();
+}
+
+int knng_stats_count(void) {
+    StatRegistry& r = reg();
+    std::lock_guard<std::mutex> lk(r.mu);
+    return (int)r.stats.size();
+}
+
+int knng_stats_get(int index, knng_kernel_stat* out) {
+    StatRegistry& r = reg();
+    std::lock_guard<std::mutex> lk(r.mu);
+    if (!out || index < 0 || index >= (int)r.stats.size()) return KNNG_EINVAL;
+    auto it = r.stats.begin();
+    std::advance(it, index);
+    *out = it->second;
+    return KNNG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// common.cuh -- device helpers shared by the kNN-graph kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/knng.h"
+
+namespace knng {
+
+// A graph entry is one 64-bit key: the order-preserving image of the FP32
+// distance in the high word and the id in the low word, so that unsigned
+// comparison of keys is the (dist, id) order used everywhere.  The empty slot
+// (id -1, dist +inf) is the all-ones key and sorts after every real entry.
+constexpr uint64_t kEmptyKey = ~0ull;
+
+// Order-preserving map of an FP32 value to uint32 (valid for every non-NaN,
+// with -0 mapped like +0 by the caller adding +0.0f first).
+__host__ __device__ __forceinline__ uint32_t f2u(float f) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(f);
+#else
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ float u2f(uint32_t u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+__host__ __device__ __forceinline__ uint32_t ord32(float f) {
+    uint32_t b = f2u(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__host__ __device__ __forceinline__ float unord32(uint32_t o) {
+    uint32_t b = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    return u2f(b);
+}
+__host__ __device__ __forceinline__ uint64_t make_key(float d, uint32_t id) {
+    return ((uint64_t)ord32(d) << 32) | id;
+}
+__host__ __device__ __forceinline__ uint32_t key_id(uint64_t k) { return (uint32_t)k; }
+__host__ __device__ __forceinline__ float key_dist(uint64_t k) { return unord32((uint32_t)(k >> 32)); }
+
+// SplitMix64 output for state z (Steele, Lea & Flood 2014).
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
+    uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
+    uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
+    return ((uint64_t)hi << 32) | lo;
+}
+__device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+        uint64_t o = shfl_xor64(v, m);
+        v = o < v ? o : v;
+    }
+    return v;
+}
+
+// Sort NS keys held in registers ascending (odd-even transposition; NS small).
+template <int NS>
+__device__ __forceinline__ void sort_regs(uint64_t (&a)[NS]) {
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+#pragma unroll
+        for (int i = (r & 1); i + 1 < NS; i += 2) {
+            uint64_t x = a[i], y = a[i + 1];
+            a[i] = x < y ? x : y;
+            a[i + 1] = x < y ? y : x;
+        }
+    }
+}
+
+// Warp-cooperative selection.  Every lane holds NS keys sorted ascending
+// (kEmptyKey pads).  Produces, in order, the first `k` distinct keys of the
+// multiset of all 32*NS keys (equal keys are one graph entry seen twice).
+// Lane r % 32 keeps output r in out[r / 32].  All 32 lanes must call it.
+template <int NS, int NO>
+__device__ __forceinline__ void warp_select_unique(uint64_t (&a)[NS], int k, uint64_t (&out)[NO]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) out[o] = kEmptyKey;
+    for (int r = 0; r < k; ++r) {
+        uint64_t m = warp_min64(a[0]);
+        if ((r & 31) == lane) {
+#pragma unroll
+            for (int o = 0; o < NO; ++o)
+                if (o == (r >> 5)) out[o] = m;
+        }
+        if (m == kEmptyKey) break;
+        // drop every copy of m: only heads can equal the minimum (lanes are
+        // sorted), and a lane can hold several copies in a row
+        for (int t = 0; t < NS && a[0] == m; ++t) {
+#pragma unroll
+            for (int i = 0; i + 1 < NS; ++i) a[i] = a[i + 1];
+            a[NS - 1] = kEmptyKey;
+        }
+    }
+}
+
+// Status word written by kernels that detect a bad input or an internal
+// limit; the host reads it once per call.
+enum DevStatus : int {
+    kStatusOk = 0,
+    kStatusNonFinite = 1,   // input holds NaN or Inf
+    kStatusOverflow = 2,    // an internal buffer would overflow: later stages skip
+    kStatusBadInput = 4,    // an id or offset given by the caller is out of range
+    kStatusInternal = 8,    // a consistency check failed: the write was skipped
+};
+constexpr int kStatusStop = kStatusOverflow | kStatusBadInput | kStatusInternal;
+
+}  // namespace knng

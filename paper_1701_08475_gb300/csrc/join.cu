@@ -1,0 +1,561 @@
+// join.cu -- neighbour-of-neighbour refinement (the nearest-neighbour-descent
+// prior art cited in Sec. 1), in Jacobi form: every offer of a round is made
+// from the graph as it stood before the round, so the result does not depend
+// on the order in which offers arrive.
+//
+//   K6 reverse lists  R[i] = the k closest j with i in G[j], by (d, j)
+//   K5 local join     for every node i and every pair {u, v} of
+//                     N_i = G[i] (+ R[i]), u != v: offer v to u and u to v
+//                     with the canonical distance; an offer that cannot beat
+//                     the target's k-th entry is dropped at the source (it
+//                     could never enter the target's list)
+//   scatter           group the offers by target (counts, prefix sum)
+//   K4 merge          G_new[u] = first k unique of G_old[u] + offers to u
+#include "common.cuh"
+#include "kernels.h"
+
+namespace knng {
+
+namespace {
+
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+__device__ __forceinline__ int warp_incl_scan(int x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_partial(const int32_t* __restrict__ cnt, int64_t n,
+                                                             int32_t* __restrict__ bsum) {
+    __shared__ int wt[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int s = 0;
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t) {
+        const int64_t e = base + (int64_t)threadIdx.x * kScanItems + t;
+        if (e < n) s += cnt[e];
+    }
+    s = warp_incl_scan(s);
+    if ((threadIdx.x & 31) == 31) wt[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int w = warp_incl_scan(wt[threadIdx.x]);
+        if (threadIdx.x == 31) bsum[blockIdx.x] = w;
+    }
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_blocks(int32_t* __restrict__ bsum, int nb) {
+    __shared__ int wt[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += kScanBlock) {
+        const int e = base + threadIdx.x;
+        const int v = e < nb ? bsum[e] : 0;
+        int x = warp_incl_scan(v);
+        if ((threadIdx.x & 31) == 31) wt[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) wt[threadIdx.x] = warp_incl_scan(wt[threadIdx.x]);
+        __syncthreads();
+        const int before = (threadIdx.x >= 32 ? wt[(threadIdx.x >> 5) - 1] : 0) + carry;
+        if (e < nb) bsum[e] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == kScanBlock - 1) carry = before + x;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_final(const int32_t* __restrict__ cnt, int64_t n,
+                                                           const int32_t* __restrict__ bsum,
+                                                           int32_t* __restrict__ off) {
+    __shared__ int wt[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t) {
+        const int64_t e = base + (int64_t)threadIdx.x * kScanItems + t;
+        v[t] = e < n ? cnt[e] : 0;
+        s += v[t];
+    }
+    const int x = warp_incl_scan(s);
+    if ((threadIdx.x & 31) == 31) wt[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) wt[threadIdx.x] = warp_incl_scan(wt[threadIdx.x]);
+    __syncthreads();
+    int run = bsum[blockIdx.x] + (threadIdx.x >= 32 ? wt[(threadIdx.x >> 5) - 1] : 0) + x - s;
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t) {
+        const int64_t e = base + (int64_t)threadIdx.x * kScanItems + t;
+        if (e < n) off[e] = run;
+        run += v[t];
+        if (e == n - 1) off[n] = run;
+    }
+}
+
+__global__ void k_fill_empty(uint64_t* __restrict__ G, int64_t count) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        G[e] = kEmptyKey;
+}
+
+__global__ void k_pack(const int32_t* __restrict__ ids, const float* __restrict__ d, uint64_t* __restrict__ G,
+                       int64_t count, int64_t n, int* __restrict__ status) {
+    bool bad = false;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t id = ids[e];
+        bad |= id < -1 || id >= n;
+        G[e] = (id < 0 || id >= n) ? kEmptyKey : make_key(__fadd_rn(d[e], 0.f), (uint32_t)id);
+    }
+    if (bad) atomicOr(status, kStatusBadInput);
+}
+
+__global__ void k_check_ids(const int32_t* __restrict__ ids, int64_t count, int64_t lo, int64_t hi,
+                            int* __restrict__ status) {
+    bool bad = false;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        bad |= ids[e] < lo || ids[e] >= hi;
+    if (bad) atomicOr(status, kStatusBadInput);
+}
+
+__global__ void k_unpack(const uint64_t* __restrict__ G, int32_t* __restrict__ ids, float* __restrict__ d,
+                         int64_t count) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = G[e];
+        if (key == kEmptyKey) {
+            ids[e] = -1;
+            d[e] = __int_as_float(0x7f800000);
+        } else {
+            ids[e] = (int32_t)key_id(key);
+            d[e] = key_dist(key);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- K6
+__global__ void k6_count(const uint64_t* __restrict__ G, int64_t nk, int32_t* __restrict__ deg) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = G[e];
+        if (key != kEmptyKey) atomicAdd(&deg[key_id(key)], 1);
+    }
+}
+
+__global__ void k6_fill(const uint64_t* __restrict__ G, int64_t nk, int k, const int32_t* __restrict__ roff,
+                        int32_t* __restrict__ cur, uint64_t* __restrict__ rbuf) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = G[e];
+        if (key == kEmptyKey) continue;
+        const uint32_t i = key_id(key);
+        const uint32_t j = (uint32_t)(e / k);
+        const int pos = roff[i] + atomicAdd(&cur[i], 1);
+        rbuf[pos] = (key & 0xFFFFFFFF00000000ull) | j;
+    }
+}
+
+// k best keys of list[beg, end) merged with `run` (NO slots per lane, sorted
+// list of k keys spread lane-major); duplicates merged.  Warp-wide.
+template <int NO>
+__device__ __forceinline__ void warp_merge_list(const uint64_t* __restrict__ list, int beg, int end, int k,
+                                                uint64_t (&run)[NO]) {
+    const int lane = threadIdx.x & 31;
+    constexpr int NC = 4;
+    for (int c = beg; c < end; c += 32 * NC) {
+        uint64_t a[NC + NO];
+#pragma unroll
+        for (int s = 0; s < NC; ++s) {
+            const int e = c + lane + 32 * s;
+            a[s] = e < end ? list[e] : kEmptyKey;
+        }
+        // skip the merge when nothing can enter: compare with the k-th key
+        uint64_t mine = run[0];
+#pragma unroll
+        for (int o = 1; o < NO; ++o)
+            if (o == ((k - 1) >> 5)) mine = run[o];
+        const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)mine, (k - 1) & 31);
+        const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(mine >> 32), (k - 1) & 31);
+        const uint64_t last = ((uint64_t)hi << 32) | lo;
+        bool any = false;
+#pragma unroll
+        for (int s = 0; s < NC; ++s) any |= a[s] < last;
+        if (!__any_sync(0xffffffffu, any)) continue;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) a[NC + o] = run[o];
+        sort_regs<NC + NO>(a);
+        warp_select_unique<NC + NO, NO>(a, k, run);
+    }
+}
+
+template <int NO>
+__global__ void __launch_bounds__(256) k6_select(const uint64_t* __restrict__ rbuf, const int32_t* __restrict__ roff,
+                                                 int64_t n, int k, uint64_t* __restrict__ R) {
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const int lane = threadIdx.x & 31;
+    uint64_t run[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) run[o] = kEmptyKey;
+    warp_merge_list<NO>(rbuf, roff[i], roff[i + 1], k, run);
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+        if (lane + 32 * o < k) R[i * k + lane + 32 * o] = run[o];
+}
+
+// ---------------------------------------------------------------- K5
+// One warp per node i.  Members N_i in shared memory; the upper triangle of
+// member pairs is cut into 4 x 4 blocks, BPL blocks per lane; distances are
+// canonical (dims ascending, fmaf); surviving offers are appended to the
+// chunk's buffer.
+constexpr int kJoinWarps = 4;
+
+__host__ __device__ inline void join_chunk(int D, int mcap, int* dch, int* stride) {
+    const int d4 = (D + 3) & ~3;
+    int cap = (24 * 1024 / (mcap * 4) - 4) & ~3;
+    if (cap < 4) cap = 4;
+    const int c = d4 < cap ? d4 : cap;
+    *dch = c;
+    *stride = ((c / 4) & 1) ? c : c + 4;
+}
+
+template <int BPL>
+__global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restrict__ X, int D, int k, int rev,
+                                                          int mcap, const uint64_t* __restrict__ Gold,
+                                                          const uint64_t* __restrict__ R, int64_t node0,
+                                                          int64_t node1, uint32_t* __restrict__ counter,
+                                                          int64_t cap, uint32_t* __restrict__ ptgt,
+                                                          uint64_t* __restrict__ pkey,
+                                                          int32_t* __restrict__ pcnt, int* __restrict__ status) {
+    extern __shared__ float4 smem4[];
+    int dch, stride;
+    join_chunk(D, mcap, &dch, &stride);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    char* base = reinterpret_cast<char*>(smem4) + (size_t)warp * ((size_t)mcap * (stride * 4 + 12) + 16);
+    float* xs = reinterpret_cast<float*>(base);                                   // [mcap][stride]
+    uint64_t* thr = reinterpret_cast<uint64_t*>(xs + (size_t)mcap * stride);      // [mcap]
+    int32_t* mem = reinterpret_cast<int32_t*>(thr + mcap);                        // [mcap]
+
+    const int64_t i = node0 + (int64_t)blockIdx.x * kJoinWarps + warp;
+    if (i >= node1 || (*status & kStatusStop)) return;
+    // members: real ids of G_old[i], then of R[i]
+    int M = 0;
+    for (int src = 0; src < (rev ? 2 : 1); ++src) {
+        const uint64_t* row = (src == 0 ? Gold : R) + i * k;
+        for (int e0 = 0; e0 < k; e0 += 32) {
+            const int e = e0 + lane;
+            const uint64_t key = e < k ? row[e] : kEmptyKey;
+            const bool real = key != kEmptyKey;
+            const unsigned bal = __ballot_sync(0xffffffffu, real);
+            if (real) {
+                const int pos = M + __popc(bal & ((1u << lane) - 1u));
+                const uint32_t u = key_id(key);
+                mem[pos] = (int32_t)u;
+                thr[pos] = Gold[(int64_t)u * k + k - 1];
+            }
+            M += __popc(bal);
+        }
+    }
+    __syncwarp();
+    if (M < 2) return;
+    const int RGN = (M + 3) >> 2;
+    const int nb = RGN * (RGN + 1) / 2;
+    int brg[BPL], bcg[BPL];
+#pragma unroll
+    for (int q = 0; q < BPL; ++q) {
+        int b = lane + 32 * q;
+        brg[q] = -1;
+        bcg[q] = 0;
+        if (b < nb) {
+            int rg = 0;
+            while (b >= RGN - rg) {
+                b -= RGN - rg;
+                ++rg;
+            }
+            brg[q] = rg;
+            bcg[q] = rg + b;
+        }
+    }
+    float acc[BPL][4][4];
+#pragma unroll
+    for (int q = 0; q < BPL; ++q)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[q][a][b] = 0.f;
+    const bool vec = (D % 4 == 0);
+    for (int d0 = 0; d0 < D; d0 += dch) {
+        const int dl = min(dch, D - d0);
+        // gather the members' dims [d0, d0 + dch)
+        if (vec) {
+            const int q4 = dch >> 2;
+            for (int e = lane; e < M * q4; e += 32) {
+                const int r = e / q4, c4 = e - r * q4;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (c4 * 4 < dl) v = __ldg(reinterpret_cast<const float4*>(X + (int64_t)mem[r] * D + d0) + c4);
+                *reinterpret_cast<float4*>(xs + r * stride + c4 * 4) = v;
+            }
+        } else {
+            for (int e = lane; e < M * dch; e += 32) {
+                const int r = e / dch, c = e - r * dch;
+                xs[r * stride + c] = c < dl ? __ldg(X + (int64_t)mem[r] * D + d0 + c) : 0.f;
+            }
+        }
+        // rows M .. 4*RGN-1 read as zeros
+        for (int e = lane; e < (RGN * 4 - M) * dch; e += 32) {
+            const int r = M + e / dch, c = e % dch;
+            xs[r * stride + c] = 0.f;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < BPL; ++q) {
+            if (brg[q] < 0) continue;
+            const float* rp = xs + brg[q] * 4 * stride;
+            const float* cp = xs + bcg[q] * 4 * stride;
+            for (int dq = 0; dq < dch; dq += 4) {
+                float4 rv[4], cv[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) rv[a] = *reinterpret_cast<const float4*>(rp + a * stride + dq);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) cv[b] = *reinterpret_cast<const float4*>(cp + b * stride + dq);
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        float t = __fsub_rn(rv[a].x, cv[b].x);
+                        acc[q][a][b] = __fmaf_rn(t, t, acc[q][a][b]);
+                        t = __fsub_rn(rv[a].y, cv[b].y);
+                        acc[q][a][b] = __fmaf_rn(t, t, acc[q][a][b]);
+                        t = __fsub_rn(rv[a].z, cv[b].z);
+                        acc[q][a][b] = __fmaf_rn(t, t, acc[q][a][b]);
+                        t = __fsub_rn(rv[a].w, cv[b].w);
+                        acc[q][a][b] = __fmaf_rn(t, t, acc[q][a][b]);
+                    }
+            }
+        }
+        __syncwarp();
+    }
+    // offers: count, reserve, write
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < BPL; ++q) {
+        if (brg[q] < 0) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int ia = brg[q] * 4 + a, ib = bcg[q] * 4 + b;
+                if (ia < ib && ib < M) {
+                    const uint32_t u = (uint32_t)mem[ia], v = (uint32_t)mem[ib];
+                    if (u != v) {
+                        cnt += make_key(acc[q][a][b], v) < thr[ia];
+                        cnt += make_key(acc[q][a][b], u) < thr[ib];
+                    }
+                }
+            }
+    }
+    const int incl = warp_incl_scan(cnt);
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    uint32_t at = 0;
+    if (lane == 31) at = atomicAdd(counter, (uint32_t)total);
+    at = __shfl_sync(0xffffffffu, at, 31);
+    if ((int64_t)at + total > cap) {
+        if (lane == 0) atomicOr(status, kStatusOverflow);
+        return;
+    }
+    uint32_t w = at + incl - cnt;
+#pragma unroll
+    for (int q = 0; q < BPL; ++q) {
+        if (brg[q] < 0) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int ia = brg[q] * 4 + a, ib = bcg[q] * 4 + b;
+                if (ia < ib && ib < M) {
+                    const uint32_t u = (uint32_t)mem[ia], v = (uint32_t)mem[ib];
+                    if (u != v) {
+                        const uint64_t ku = make_key(acc[q][a][b], v);
+                        if (ku < thr[ia]) {
+                            ptgt[w] = u;
+                            pkey[w] = ku;
+                            ++w;
+                            atomicAdd(&pcnt[u], 1);
+                        }
+                        const uint64_t kv = make_key(acc[q][a][b], u);
+                        if (kv < thr[ib]) {
+                            ptgt[w] = v;
+                            pkey[w] = kv;
+                            ++w;
+                            atomicAdd(&pcnt[v], 1);
+                        }
+                    }
+                }
+            }
+    }
+}
+
+__global__ void k5_scatter(const uint32_t* __restrict__ ptgt, const uint64_t* __restrict__ pkey,
+                           const uint32_t* __restrict__ counter, int64_t cap, const int32_t* __restrict__ poff,
+                           int32_t* __restrict__ pcur, uint64_t* __restrict__ grouped,
+                           const int* __restrict__ status) {
+    // after an overflow some reserved slots were never written: group nothing
+    if (*status & kStatusStop) return;
+    const int64_t total = min((int64_t)*counter, cap);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = ptgt[q];
+        const int pos = poff[t] + atomicAdd(&pcur[t], 1);
+        grouped[pos] = pkey[q];
+    }
+}
+
+template <int NO>
+__global__ void __launch_bounds__(256) k4_merge(uint64_t* __restrict__ Gnew, const uint64_t* __restrict__ grouped,
+                                                const int32_t* __restrict__ poff, int64_t n, int k,
+                                                const int* __restrict__ status) {
+    const int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (u >= n || (*status & kStatusStop)) return;
+    const int beg = poff[u], end = poff[u + 1];
+    if (beg == end) return;
+    const int lane = threadIdx.x & 31;
+    uint64_t* row = Gnew + u * k;
+    uint64_t run[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) run[o] = lane + 32 * o < k ? row[lane + 32 * o] : kEmptyKey;
+    warp_merge_list<NO>(grouped, beg, end, k, run);
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+        if (lane + 32 * o < k) row[lane + 32 * o] = run[o];
+}
+
+inline int grid_for(int64_t count, int block) {
+    int64_t g = (count + block - 1) / block;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+size_t scan_tmp_ints(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1; }
+
+void launch_scan(const int32_t* cnt, int32_t* off, int64_t n, int32_t* tmp, cudaStream_t s) {
+    const int nb = (int)((n + kScanTile - 1) / kScanTile);
+    LaunchScope ls("k_scan", s, n * 8.0, 0);
+    if (nb == 0) {
+        cudaMemsetAsync(off, 0, sizeof(int32_t), s);
+        return;
+    }
+    k_scan_partial<<<nb, kScanBlock, 0, s>>>(cnt, n, tmp);
+    k_scan_blocks<<<1, kScanBlock, 0, s>>>(tmp, nb);
+    k_scan_final<<<nb, kScanBlock, 0, s>>>(cnt, n, tmp, off);
+}
+
+void launch_fill_empty(uint64_t* G, int64_t count, cudaStream_t s) {
+    LaunchScope ls("k_fill_empty", s, count * 8.0, 0);
+    k_fill_empty<<<grid_for(count, 256), 256, 0, s>>>(G, count);
+}
+
+void launch_pack(const int32_t* ids, const float* d, uint64_t* G, int64_t count, int64_t n, int* status,
+                 cudaStream_t s) {
+    LaunchScope ls("k_pack", s, count * 16.0, 0);
+    k_pack<<<grid_for(count, 256), 256, 0, s>>>(ids, d, G, count, n, status);
+}
+
+void launch_check_ids(const int32_t* ids, int64_t count, int64_t lo, int64_t hi, int* status, cudaStream_t s) {
+    if (count <= 0) return;
+    LaunchScope ls("k_check_ids", s, count * 4.0, 0);
+    k_check_ids<<<grid_for(count, 256), 256, 0, s>>>(ids, count, lo, hi, status);
+}
+
+void launch_unpack(const uint64_t* G, int32_t* ids, float* d, int64_t count, cudaStream_t s) {
+    LaunchScope ls("k_unpack", s, count * 16.0, 0);
+    k_unpack<<<grid_for(count, 256), 256, 0, s>>>(G, ids, d, count);
+}
+
+void launch_reverse_lists(const uint64_t* G, int64_t n, int k, const JoinBuffers& b, cudaStream_t s) {
+    const int64_t nk = n * k;
+    cudaMemsetAsync(b.deg, 0, sizeof(int32_t) * (n + 1), s);
+    cudaMemsetAsync(b.cur, 0, sizeof(int32_t) * n, s);
+    {
+        LaunchScope ls("k6_count", s, nk * 8.0 + nk * 4.0, 0);
+        k6_count<<<grid_for(nk, 256), 256, 0, s>>>(G, nk, b.deg);
+    }
+    launch_scan(b.deg, b.roff, n, b.scan_tmp, s);
+    {
+        LaunchScope ls("k6_fill", s, nk * (8.0 + 8.0 + 8.0), 0);
+        k6_fill<<<grid_for(nk, 256), 256, 0, s>>>(G, nk, k, b.roff, b.cur, b.rbuf);
+    }
+    LaunchScope ls("k6_select", s, nk * 16.0 + n * 8.0, 0);
+    const int grid = (int)((n * 32 + 255) / 256);
+    if (k > 32)
+        k6_select<2><<<grid, 256, 0, s>>>(b.rbuf, b.roff, n, k, b.R);
+    else
+        k6_select<1><<<grid, 256, 0, s>>>(b.rbuf, b.roff, n, k, b.R);
+}
+
+int join_blocks_per_lane(int mcap) {
+    const int rgn = (mcap + 3) / 4;
+    const int nb = rgn * (rgn + 1) / 2;
+    return (nb + 31) / 32;
+}
+
+// shared memory of one join CTA: per warp the member rows (mcap, a multiple
+// of 4, rows of one dim chunk), their thresholds and their ids
+size_t join_smem_bytes(int D, int mcap) {
+    int dch, stride;
+    join_chunk(D, mcap, &dch, &stride);
+    return (size_t)kJoinWarps * ((size_t)mcap * (stride * 4 + 12) + 16);
+}
+
+void run_join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold, uint64_t* Gnew,
+                    const JoinBuffers& b, int64_t nodes_per_chunk, int* status, cudaStream_t s) {
+    cudaMemcpyAsync(Gnew, Gold, sizeof(uint64_t) * n * k, cudaMemcpyDeviceToDevice, s);
+    if (rev) launch_reverse_lists(Gold, n, k, b, s);
+    const int mcap = ((rev ? 2 * k : k) + 3) & ~3;
+    const int bpl = join_blocks_per_lane(mcap);
+    const size_t smem = join_smem_bytes(D, mcap);
+    for (int64_t c0 = 0; c0 < n; c0 += nodes_per_chunk) {
+        const int64_t c1 = c0 + nodes_per_chunk < n ? c0 + nodes_per_chunk : n;
+        cudaMemsetAsync(b.pcnt, 0, sizeof(int32_t) * (n + 1), s);
+        cudaMemsetAsync(b.pcur, 0, sizeof(int32_t) * n, s);
+        cudaMemsetAsync(b.counter, 0, sizeof(uint32_t), s);
+        {
+            const double m = rev ? 2.0 * k : (double)k;
+            LaunchScope ls("k5_join", s, (double)(c1 - c0) * (m * D * 4.0 + 2 * k * 8.0 + m * 8.0),
+                           (double)(c1 - c0) * m * (m - 1) / 2 * 3.0 * D);
+            const int grid = (int)((c1 - c0 + kJoinWarps - 1) / kJoinWarps);
+#define KNNG_JOIN(BPL)                                                                                     \
+    do {                                                                                                   \
+        cudaFuncSetAttribute(k5_join<BPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
+        k5_join<BPL><<<grid, 32 * kJoinWarps, smem, s>>>(X, D, k, rev ? 1 : 0, mcap, Gold, b.R, c0, c1,     \
+                                                         b.counter, b.cap, b.ptgt, b.pkey, b.pcnt, status); \
+    } while (0)
+            if (bpl <= 1) KNNG_JOIN(1);
+            else if (bpl <= 2) KNNG_JOIN(2);
+            else if (bpl <= 3) KNNG_JOIN(3);
+            else if (bpl <= 4) KNNG_JOIN(4);
+            else KNNG_JOIN(5);
+#undef KNNG_JOIN
+        }
+        launch_scan(b.pcnt, b.poff, n, b.scan_tmp, s);
+        {
+            LaunchScope ls("k5_scatter", s, 0, 0);
+            k5_scatter<<<152 * 16, 256, 0, s>>>(b.ptgt, b.pkey, b.counter, b.cap, b.poff, b.pcur, b.grouped,
+                                                status);
+        }
+        {
+            LaunchScope ls("k4_merge", s, n * (4.0 + 16.0 * k), 0);
+            const int grid = (int)((n * 32 + 255) / 256);
+            if (k > 32)
+                k4_merge<2><<<grid, 256, 0, s>>>(Gnew, b.grouped, b.poff, n, k, status);
+            else
+                k4_merge<1><<<grid, 256, 0, s>>>(Gnew, b.grouped, b.poff, n, k, status);
+        }
+    }
+}
+
+}  // namespace knng

@@ -1,0 +1,118 @@
+// kernels.h -- host-side launchers of the kNN-graph kernels (one .cu per stage).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace knng {
+
+// ---------------------------------------------------------------- stats
+// Every launcher reports its launch through this hook so that launches,
+// algorithmic bytes/flops and (optionally) event-timed device time can be
+// summed per kernel name.
+struct LaunchScope {
+    LaunchScope(const char* name, cudaStream_t s, double bytes, double flops);
+    ~LaunchScope();
+    const char* name_;
+    cudaStream_t s_;
+    double bytes_, flops_;
+    int slot_;
+};
+
+// ---------------------------------------------------------------- prepare (K0)
+// Sets *status |= kStatusNonFinite if any of the n*D values is not finite.
+void launch_check_finite(const float* X, int64_t count, int* status, cudaStream_t s);
+
+// ---------------------------------------------------------------- two-means split (K1)
+struct SelState {
+    uint64_t prefix;  // known high bits of the selected key
+    uint32_t krem;    // rank still to select among keys matching prefix
+    uint32_t pad;
+};
+
+struct LevelPlan {
+    int level;
+    int n;            // points covered by the level (all of them)
+    int nseg;
+    int ntiles;
+    int max_m;        // largest segment size at this level
+    int pos_bits;     // bits of a position inside a segment
+    bool small;       // one CTA per segment selects and partitions
+    const int32_t* seg_off;    // device [nseg + 1]
+    const int4* tiles;         // device [ntiles] {seg, begin, end, first_of_seg}
+    const int32_t* seg_tile0;  // device [nseg + 1]
+};
+
+struct SplitBuffers {
+    float* W;             // [nseg_max][D]  c1 - c0 per segment
+    float* S;             // [n] projections
+    uint64_t* thr;        // [nseg_max] selected key (first key of the right side)
+    SelState* st;         // [nseg_max]
+    uint32_t* ghist;      // [nseg_max][2048], zero between uses
+    uint32_t* ticket;     // [nseg_max], zero between uses
+    double* partial;      // [ntiles_max][2][D]
+    int32_t* tile_left;   // [ntiles_max]
+    int* status;          // device status word
+};
+
+constexpr int kTile = 2048;         // positions per tile of a sweep
+constexpr int kSmallMax = 8192;     // segments up to this size select in one CTA
+constexpr int kRadixBits = 11;
+
+// One level of the balanced two-means tree: T Lloyd iterations, then the
+// final cut that writes perm_out.
+void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint64_t pass_seed,
+                     const int32_t* perm_in, int32_t* perm_out, const SplitBuffers& b,
+                     cudaStream_t s);
+
+// ---------------------------------------------------------------- leaf stage (K2)
+// For every leaf l (perm[leaf_off[l] .. leaf_off[l+1]), 2..256 points): all
+// pairs, canonical FP32 distances, merged into the key graph G (n x k).
+void launch_leaf_fp32(const float* X, int D, const int32_t* perm, const int32_t* leaf_off,
+                      int nleaf, int max_leaf, int k, uint64_t* G, const int* status, cudaStream_t s);
+
+// ---------------------------------------------------------------- refinement (K4-K6)
+struct JoinBuffers {
+    int32_t* deg;        // [n + 1]
+    int32_t* roff;       // [n + 1]
+    int32_t* cur;        // [n]
+    uint64_t* rbuf;      // [n * k]
+    uint64_t* R;         // [n * k]
+    int32_t* pcnt;       // [n + 1]
+    int32_t* poff;       // [n + 1]
+    int32_t* pcur;       // [n]
+    uint32_t* ptgt;      // [cap]
+    uint64_t* pkey;      // [cap]
+    uint64_t* grouped;   // [cap]
+    int64_t cap;         // proposal capacity of one chunk
+    uint32_t* counter;   // [1] proposals appended
+    int32_t* scan_tmp;   // scan scratch
+};
+
+void launch_reverse_lists(const uint64_t* G, int64_t n, int k, const JoinBuffers& b, cudaStream_t s);
+// One refinement round: reads Gold (and R when rev), writes Gnew.
+void run_join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold,
+                    uint64_t* Gnew, const JoinBuffers& b, int64_t nodes_per_chunk, int* status,
+                    cudaStream_t s);
+
+// Exclusive scan of cnt[0..n) into off[0..n], off[n] = total.
+void launch_scan(const int32_t* cnt, int32_t* off, int64_t n, int32_t* tmp, cudaStream_t s);
+size_t scan_tmp_ints(int64_t n);
+
+// ---------------------------------------------------------------- graph I/O
+void launch_fill_empty(uint64_t* G, int64_t count, cudaStream_t s);
+// ids outside [-1, n) set kStatusBadInput (and are stored as empty slots)
+void launch_pack(const int32_t* ids, const float* d, uint64_t* G, int64_t count, int64_t n, int* status,
+                 cudaStream_t s);
+// Sets kStatusBadInput if any of ids[0 .. count) lies outside [lo, hi).
+void launch_check_ids(const int32_t* ids, int64_t count, int64_t lo, int64_t hi, int* status, cudaStream_t s);
+void launch_unpack(const uint64_t* G, int32_t* ids, float* d, int64_t count, cudaStream_t s);
+
+// ---------------------------------------------------------------- exact / recall (K7)
+void launch_exact(const float* X, int64_t n, int D, int k, const int32_t* sample, int64_t s_rows,
+                  uint64_t* out, const int* status, cudaStream_t s);
+void launch_recall(const int32_t* ids, const float* d, const int32_t* gt_ids, const float* gt_d,
+                   const int32_t* sample, int64_t s_rows, int k, unsigned long long* counts,
+                   cudaStream_t s);
+
+}  // namespace knng

@@ -1,0 +1,444 @@
+// split.cu -- K1: one level of the balanced two-means tree (Sec. 3.1: the
+// reference set is bisected repeatedly by two-means clustering; Alg. 1
+// "apply two means clustering").
+//
+// Every segment of a level is split at once.  A segment holds its ids in
+// ascending order; a split keeps that order on both sides.  One Lloyd
+// iteration is
+//   project  s_p = x_p . (c1 - c0)          canonical FP32 order (one thread
+//                                           per point, dims ascending, fmaf)
+//   select   the floor(m/2)-th smallest key (s_p, position) by radix select
+//   sums     FP64 sums of the left and right points (fixed reduction order)
+//   centroid c0 = mean(left), c1 = mean(right), FP64 divided then rounded
+// and the level ends with a final project + select + stable partition.
+// With a balanced cut only the order of ||x-c0||^2 - ||x-c1||^2 matters, and
+// x . (c1 - c0) has the same order.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace knng {
+
+namespace {
+
+__device__ __forceinline__ uint64_t sel_key(float s, int pos, int pos_bits) {
+    return ((uint64_t)ord32(s) << pos_bits) | (uint32_t)pos;
+}
+
+// Inclusive/exclusive block scan of one int per thread (blockDim multiple of 32).
+__device__ __forceinline__ int block_excl_scan(int v, int* warp_tot, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    const int before = warp ? warp_tot[warp - 1] : 0;
+    *total = warp_tot[nw - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__device__ __forceinline__ int block_sum(int v, int* warp_tot) {
+    int total;
+    block_excl_scan(v, warp_tot, &total);
+    return total;
+}
+
+// Warp 0: digit b with below(b) <= krem < below(b) + hist[b].
+__device__ __forceinline__ void find_digit(const uint32_t* hist, int nb, uint32_t krem, int* out_digit,
+                                           uint32_t* out_below) {
+    const int lane = threadIdx.x & 31;
+    const int per = nb >= 32 ? nb / 32 : 1;
+    const int b0 = lane * per;
+    uint32_t sum = 0;
+    for (int b = b0; b < b0 + per && b < nb; ++b) sum += hist[b];
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t excl = incl - sum;
+    if (excl <= krem && krem < incl) {
+        uint32_t run = excl;
+        for (int b = b0; b < b0 + per && b < nb; ++b) {
+            if (krem < run + hist[b]) {
+                *out_digit = b;
+                *out_below = run;
+                break;
+            }
+            run += hist[b];
+        }
+    }
+}
+
+__global__ void k1_init(const float* __restrict__ X, int D, const int32_t* __restrict__ perm,
+                        const int32_t* __restrict__ seg_off, int level, uint64_t pass_seed,
+                        float* __restrict__ W) {
+    const int seg = blockIdx.x;
+    const int a = seg_off[seg];
+    const int m = seg_off[seg + 1] - a;
+    // initial centroids: the points at positions h, h2 of the segment, drawn
+    // from SplitMix64 of (pass seed, level, segment index); h2 != h
+    const uint64_t r1 = splitmix64(splitmix64(splitmix64(pass_seed) ^ (uint64_t)level) ^ (uint64_t)seg);
+    const uint64_t r2 = splitmix64(r1);
+    const int64_t h = (int64_t)(r1 % (uint64_t)m);
+    const int64_t h2 = (h + 1 + (int64_t)(r2 % (uint64_t)(m - 1))) % m;
+    const float* c0 = X + (int64_t)perm[a + h] * D;
+    const float* c1 = X + (int64_t)perm[a + h2] * D;
+    for (int j = threadIdx.x; j < D; j += blockDim.x) W[(int64_t)seg * D + j] = __fsub_rn(c1[j], c0[j]);
+}
+
+// s_p = x_{perm[p]} . w_seg in the canonical order: one thread owns a point
+// and accumulates its dims in ascending order with fmaf.  Rows are staged in
+// shared memory 32 dims at a time so that global loads stay coalesced.
+__global__ void __launch_bounds__(256) k1_project(const float* __restrict__ X, int D,
+                                                  const int32_t* __restrict__ perm,
+                                                  const int4* __restrict__ tiles,
+                                                  const int32_t* __restrict__ seg_off,
+                                                  const float* __restrict__ W, float* __restrict__ S,
+                                                  SelState* __restrict__ st) {
+    __shared__ float xs[256][33];
+    __shared__ float ws[32];
+    const int4 t = tiles[blockIdx.x];
+    const int seg = t.x, begin = t.y, end = t.z;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (st != nullptr && t.w && threadIdx.x == 0) {
+        const int m = seg_off[seg + 1] - seg_off[seg];
+        st[seg].prefix = 0;
+        st[seg].krem = (uint32_t)(m / 2);
+    }
+    const float* w = W + (int64_t)seg * D;
+    for (int base = begin; base < end; base += 256) {
+        const int cnt = min(256, end - base);
+        const int my_row = threadIdx.x < cnt ? perm[base + threadIdx.x] : 0;
+        float acc = 0.f;
+        for (int d0 = 0; d0 < D; d0 += 32) {
+            const int dl = min(32, D - d0);
+            if (warp == 0) ws[lane] = lane < dl ? w[d0 + lane] : 0.f;
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) {
+                const int row = __shfl_sync(0xffffffffu, my_row, q);
+                const int pt = warp * 32 + q;
+                float v = 0.f;
+                if (pt < cnt && lane < dl) v = __ldg(X + (int64_t)row * D + d0 + lane);
+                xs[pt][lane] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < cnt)
+                for (int dd = 0; dd < dl; ++dd) acc = __fmaf_rn(xs[threadIdx.x][dd], ws[dd], acc);
+            __syncthreads();
+        }
+        if (threadIdx.x < cnt) S[base + threadIdx.x] = __fadd_rn(acc, 0.f);  // -0 -> +0
+    }
+}
+
+// Small segments: one CTA per segment keeps all keys in shared memory,
+// selects the floor(m/2)-th key, and either records it (thr) or, on the
+// final cut, partitions the segment stably into perm_out.
+__global__ void __launch_bounds__(1024) k1_select_small(const float* __restrict__ S,
+                                                        const int32_t* __restrict__ seg_off, int pos_bits,
+                                                        uint64_t* __restrict__ thr,
+                                                        const int32_t* __restrict__ perm_in,
+                                                        int32_t* __restrict__ perm_out, int* __restrict__ status) {
+    extern __shared__ uint64_t keys[];
+    __shared__ uint32_t hist[1 << kRadixBits];
+    __shared__ int sh_digit;
+    __shared__ uint32_t sh_below;
+    __shared__ int warp_tot[32];
+    const int seg = blockIdx.x, a = seg_off[seg], m = seg_off[seg + 1] - a;
+    for (int p = threadIdx.x; p < m; p += blockDim.x) keys[p] = sel_key(S[a + p], p, pos_bits);
+    uint64_t prefix = 0;
+    uint32_t krem = (uint32_t)(m / 2);
+    for (int hi = 32 + pos_bits; hi > 0; hi -= kRadixBits) {
+        const int lo = max(hi - kRadixBits, 0), width = hi - lo;
+        const uint32_t mask = (1u << width) - 1u;
+        for (int b = threadIdx.x; b < (1 << width); b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        for (int p = threadIdx.x; p < m; p += blockDim.x) {
+            const uint64_t kk = keys[p];
+            if ((kk >> hi) == (prefix >> hi)) atomicAdd(&hist[(uint32_t)(kk >> lo) & mask], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) find_digit(hist, 1 << width, krem, &sh_digit, &sh_below);
+        __syncthreads();
+        prefix |= (uint64_t)sh_digit << lo;
+        krem -= sh_below;
+        __syncthreads();
+    }
+    if (perm_out == nullptr) {
+        if (threadIdx.x == 0) thr[seg] = prefix;
+        return;
+    }
+    const int K = m / 2;
+    int left_before = 0;
+    for (int base = 0; base < m; base += blockDim.x) {
+        const int p = base + threadIdx.x;
+        const int isl = (p < m) && keys[p] < prefix;
+        int tot;
+        const int ex = block_excl_scan(isl, warp_tot, &tot);
+        if (p < m) {
+            const int lb = left_before + ex;
+            const int np = isl ? lb : K + (p - lb);
+            if ((isl ? np < K : np < m) && np >= 0)
+                perm_out[a + np] = perm_in[a + p];
+            else
+                atomicOr(status, kStatusInternal);
+        }
+        left_before += tot;
+    }
+}
+
+// Large segments: one radix pass over bits [hi-11, hi) of the keys.  Every
+// tile adds its histogram to the segment's global one; the last tile of the
+// segment to finish (ticket) picks the digit and clears the histogram.
+__global__ void __launch_bounds__(256) k1_select_pass(const float* __restrict__ S,
+                                                      const int4* __restrict__ tiles,
+                                                      const int32_t* __restrict__ seg_off,
+                                                      const int32_t* __restrict__ seg_tile0, int pos_bits,
+                                                      int hi, SelState* __restrict__ st,
+                                                      uint32_t* __restrict__ ghist,
+                                                      uint32_t* __restrict__ ticket,
+                                                      uint64_t* __restrict__ thr, int last_pass) {
+    __shared__ uint32_t hist[1 << kRadixBits];
+    __shared__ int sh_last, sh_digit;
+    __shared__ uint32_t sh_below;
+    const int4 t = tiles[blockIdx.x];
+    const int seg = t.x, begin = t.y, end = t.z;
+    const int a = seg_off[seg];
+    const int lo = max(hi - kRadixBits, 0), width = hi - lo, nb = 1 << width;
+    const uint32_t mask = (uint32_t)nb - 1u;
+    const uint64_t prefix = st[seg].prefix;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    for (int p = begin + threadIdx.x; p < end; p += blockDim.x) {
+        const uint64_t kk = sel_key(S[p], p - a, pos_bits);
+        if ((kk >> hi) == (prefix >> hi)) atomicAdd(&hist[(uint32_t)(kk >> lo) & mask], 1u);
+    }
+    __syncthreads();
+    uint32_t* gh = ghist + (size_t)seg * (1 << kRadixBits);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        if (hist[b]) atomicAdd(&gh[b], hist[b]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t ntile = (uint32_t)(seg_tile0[seg + 1] - seg_tile0[seg]);
+        sh_last = atomicAdd(&ticket[seg], 1u) == ntile - 1u;
+    }
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = atomicExch(&gh[b], 0u);
+    __syncthreads();
+    if (threadIdx.x < 32) find_digit(hist, nb, st[seg].krem, &sh_digit, &sh_below);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t np = prefix | ((uint64_t)sh_digit << lo);
+        st[seg].prefix = np;
+        st[seg].krem -= sh_below;
+        ticket[seg] = 0;
+        if (last_pass) thr[seg] = np;
+    }
+}
+
+// FP64 sums of the left and right points of each tile, 128 dims per CTA
+// (blockIdx.y).  Order: per warp ascending positions, then warps 0..7.
+template <bool VEC>
+__global__ void __launch_bounds__(256) k1_sums(const float* __restrict__ X, int D,
+                                               const int32_t* __restrict__ perm,
+                                               const int4* __restrict__ tiles, const float* __restrict__ S,
+                                               const int32_t* __restrict__ seg_off,
+                                               const uint64_t* __restrict__ thr, int pos_bits,
+                                               double* __restrict__ partial) {
+    __shared__ double red[8][2][128];
+    const int4 t = tiles[blockIdx.x];
+    const int seg = t.x, begin = t.y, end = t.z;
+    const int dbase = blockIdx.y * 128;
+    const int a = seg_off[seg];
+    const uint64_t T = thr[seg];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double aL[4] = {0.0, 0.0, 0.0, 0.0}, aR[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int p = begin + warp; p < end; p += 8) {
+        const bool left = sel_key(S[p], p - a, pos_bits) < T;
+        const float* x = X + (int64_t)perm[p] * D + dbase;
+        float v[4];
+        if (VEC) {
+            if (dbase + lane * 4 < D) {
+                const float4 f = __ldg(reinterpret_cast<const float4*>(x) + lane);
+                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+            } else {
+                v[0] = v[1] = v[2] = v[3] = 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = (dbase + lane + 32 * j < D) ? __ldg(x + lane + 32 * j) : 0.f;
+        }
+        if (left) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) aL[j] += (double)v[j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) aR[j] += (double)v[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int dl = VEC ? lane * 4 + j : lane + 32 * j;
+        red[warp][0][dl] = aL[j];
+        red[warp][1][dl] = aR[j];
+    }
+    __syncthreads();
+    if (threadIdx.x < 128 && dbase + threadIdx.x < D) {
+        double sL = 0.0, sR = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            sL += red[w][0][threadIdx.x];
+            sR += red[w][1][threadIdx.x];
+        }
+        partial[((int64_t)blockIdx.x * 2 + 0) * D + dbase + threadIdx.x] = sL;
+        partial[((int64_t)blockIdx.x * 2 + 1) * D + dbase + threadIdx.x] = sR;
+    }
+}
+
+// New centroids of each segment from its tiles' partial sums (tile order),
+// FP64 mean rounded to FP32; stores w = c1 - c0.
+__global__ void k1_centroids(const double* __restrict__ partial, const int32_t* __restrict__ seg_off,
+                             const int32_t* __restrict__ seg_tile0, int D, float* __restrict__ W) {
+    const int seg = blockIdx.x;
+    const int m = seg_off[seg + 1] - seg_off[seg];
+    const int K = m / 2;
+    const int t0 = seg_tile0[seg], t1 = seg_tile0[seg + 1];
+    for (int d = threadIdx.x; d < D; d += blockDim.x) {
+        double sL = 0.0, sR = 0.0;
+        for (int t = t0; t < t1; ++t) {
+            sL += partial[((int64_t)t * 2 + 0) * D + d];
+            sR += partial[((int64_t)t * 2 + 1) * D + d];
+        }
+        const float c0 = (float)(sL / (double)K);
+        const float c1 = (float)(sR / (double)(m - K));
+        W[(int64_t)seg * D + d] = __fsub_rn(c1, c0);
+    }
+}
+
+__global__ void __launch_bounds__(256) k1_part_count(const float* __restrict__ S, const int4* __restrict__ tiles,
+                                                     const int32_t* __restrict__ seg_off,
+                                                     const uint64_t* __restrict__ thr, int pos_bits,
+                                                     int32_t* __restrict__ tile_left) {
+    __shared__ int warp_tot[32];
+    const int4 t = tiles[blockIdx.x];
+    const int a = seg_off[t.x];
+    const uint64_t T = thr[t.x];
+    int c = 0;
+    for (int p = t.y + threadIdx.x; p < t.z; p += blockDim.x) c += sel_key(S[p], p - a, pos_bits) < T;
+    c = block_sum(c, warp_tot);
+    if (threadIdx.x == 0) tile_left[blockIdx.x] = c;
+}
+
+__global__ void __launch_bounds__(256) k1_part_scatter(const float* __restrict__ S, const int4* __restrict__ tiles,
+                                                       const int32_t* __restrict__ seg_off,
+                                                       const int32_t* __restrict__ seg_tile0,
+                                                       const uint64_t* __restrict__ thr, int pos_bits,
+                                                       const int32_t* __restrict__ tile_left,
+                                                       const int32_t* __restrict__ perm_in,
+                                                       int32_t* __restrict__ perm_out, int* __restrict__ status) {
+    __shared__ int warp_tot[32];
+    const int4 t = tiles[blockIdx.x];
+    const int seg = t.x;
+    const int a = seg_off[seg], m = seg_off[seg + 1] - a, K = m / 2;
+    const uint64_t T = thr[seg];
+    int lb = 0;
+    for (int q = seg_tile0[seg] + threadIdx.x; q < (int)blockIdx.x; q += blockDim.x) lb += tile_left[q];
+    lb = block_sum(lb, warp_tot);
+    for (int base = t.y; base < t.z; base += blockDim.x) {
+        const int p = base + threadIdx.x;
+        const int isl = p < t.z && sel_key(S[p], p - a, pos_bits) < T;
+        int tot;
+        const int ex = block_excl_scan(isl, warp_tot, &tot);
+        if (p < t.z) {
+            const int l = lb + ex;
+            const int np = isl ? l : K + (p - a - l);
+            if ((isl ? np < K : np < m) && np >= 0)
+                perm_out[a + np] = perm_in[p];
+            else
+                atomicOr(status, kStatusInternal);
+        }
+        lb += tot;
+    }
+}
+
+}  // namespace
+
+void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint64_t pass_seed,
+                     const int32_t* perm_in, int32_t* perm_out, const SplitBuffers& b, cudaStream_t s) {
+    // algorithmic bytes: a sweep reads every row once plus its id and key
+    const double n = lp.n, rows = n * D * 4.0;
+    const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    const int dchunks = (D + 127) / 128;
+    {
+        LaunchScope ls("k1_init", s, (double)lp.nseg * 3 * D * 4, 0);
+        k1_init<<<lp.nseg, 128, 0, s>>>(X, D, perm_in, lp.seg_off, lp.level, pass_seed, b.W);
+    }
+    for (int it = 0; it <= iters; ++it) {
+        const bool last = it == iters;
+        {
+            LaunchScope ls("k1_project", s, rows + n * 8, 2.0 * n * D);
+            k1_project<<<lp.ntiles, 256, 0, s>>>(X, D, perm_in, lp.tiles, lp.seg_off, b.W, b.S,
+                                                 lp.small ? nullptr : b.st);
+        }
+        if (lp.small) {
+            const size_t smem = (size_t)lp.max_m * sizeof(uint64_t);
+            LaunchScope ls("k1_select_small", s, n * 4 + (last ? n * 8 : 0), 0);
+            cudaFuncSetAttribute(k1_select_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k1_select_small<<<lp.nseg, 1024, smem, s>>>(b.S, lp.seg_off, lp.pos_bits, b.thr, perm_in,
+                                                        last ? perm_out : nullptr, b.status);
+            if (last) break;
+        } else {
+            const int TB = 32 + lp.pos_bits;
+            for (int hi = TB; hi > 0; hi -= kRadixBits) {
+                LaunchScope ls("k1_select_pass", s, n * 4, 0);
+                k1_select_pass<<<lp.ntiles, 256, 0, s>>>(b.S, lp.tiles, lp.seg_off, lp.seg_tile0, lp.pos_bits, hi,
+                                                         b.st, b.ghist, b.ticket, b.thr, hi - kRadixBits <= 0);
+            }
+            if (last) {
+                {
+                    LaunchScope ls("k1_part_count", s, n * 4, 0);
+                    k1_part_count<<<lp.ntiles, 256, 0, s>>>(b.S, lp.tiles, lp.seg_off, b.thr, lp.pos_bits,
+                                                            b.tile_left);
+                }
+                LaunchScope ls("k1_part_scatter", s, n * 12, 0);
+                k1_part_scatter<<<lp.ntiles, 256, 0, s>>>(b.S, lp.tiles, lp.seg_off, lp.seg_tile0, b.thr,
+                                                          lp.pos_bits, b.tile_left, perm_in, perm_out, b.status);
+                break;
+            }
+        }
+        {
+            LaunchScope ls("k1_sums", s, rows + n * 8, n * D);
+            dim3 grid(lp.ntiles, dchunks);
+            if (vec)
+                k1_sums<true><<<grid, 256, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr, lp.pos_bits,
+                                                   b.partial);
+            else
+                k1_sums<false><<<grid, 256, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr, lp.pos_bits,
+                                                    b.partial);
+        }
+        {
+            LaunchScope ls("k1_centroids", s, (double)lp.ntiles * 2 * D * 8 + (double)lp.nseg * D * 4, 0);
+            k1_centroids<<<lp.nseg, 128, 0, s>>>(b.partial, lp.seg_off, lp.seg_tile0, D, b.W);
+        }
+    }
+}
+
+}  // namespace knng

@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bar (from the graph conventions): ids bit-exact; distances bit-exact (the
+canonical FP32 distance is computed in the same order on both sides, so the
+1e-5 relative bound is met with zero error).  Where floating point decides
+the partition (FP64 centroid sums of non-integer data, summed in another
+order), the later stages are compared on the GPU's own partition, and the
+partition itself is compared on integer data, where the sums are exact.
+"""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def knng():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1701_08475_gb300 as m
+    m.load()
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def _np(t):
+    return t.cpu().numpy() if hasattr(t, "cpu") else np.asarray(t)
+
+
+def _assert_graph_equal(g_ids, g_d, o_ids, o_d):
+    g_ids, g_d = _np(g_ids), _np(g_d)
+    bad = np.argwhere(g_ids != o_ids)
+    assert bad.size == 0, "ids differ at %s: gpu %s oracle %s" % (
+        bad[:3].tolist(), g_ids[tuple(bad[0])], o_ids[tuple(bad[0])])
+    assert np.array_equal(g_d.view(np.uint32), o_d.view(np.uint32)), "distance bits differ"
+
+
+def _assert_valid(ids, d, full=True):
+    ids, d = _np(ids), _np(d)
+    n, k = ids.shape
+    assert not np.any(ids == np.arange(n)[:, None]), "self loop"
+    real = ids >= 0
+    if full:
+        assert real.all()
+    s = np.sort(np.where(real, ids, -1 - np.arange(k)[None, :]), axis=1)
+    assert not np.any((s[:, 1:] == s[:, :-1]) & (s[:, 1:] >= 0)), "duplicate id"
+    dd = np.where(real, d, np.inf)
+    assert np.all(dd[:, 1:] >= dd[:, :-1]), "row not sorted by distance"
+    tie = dd[:, 1:] == dd[:, :-1]
+    ui = ids.astype(np.int64) & 0xffffffff
+    assert not np.any(tie & (ui[:, 1:] < ui[:, :-1])), "equal distances not ordered by id"
+
+
+# ---------------------------------------------------------------- whole build
+BUILD_CASES = [
+    # n, D, k, leaf_max, passes, rounds, mode, iters
+    (1500, 24, 8, 40, 2, 1, oracle.FWD_REV, 3),
+    (3001, 13, 10, 64, 2, 2, oracle.FWD_REV, 4),      # D not a multiple of 4, ragged n
+    (2500, 32, 16, 128, 2, 1, oracle.FWD, 2),
+    (4097, 8, 12, 256, 1, 1, oracle.FWD_REV, 4),      # largest leaves
+    (700, 130, 5, 12, 3, 2, oracle.FWD_REV, 1),       # two dim chunks in the join
+    (21, 3, 20, 42, 1, 0, oracle.FWD, 4),             # n = k + 1: one leaf, complete lists
+    (900, 16, 33, 68, 1, 0, oracle.FWD, 4),           # k > 32: two list slots per lane
+]
+
+
+@pytest.mark.parametrize("n,D,k,lm,passes,rounds,mode,iters", BUILD_CASES)
+def test_build_matches_oracle_on_integer_data(knng, n, D, k, lm, passes, rounds, mode, iters):
+    X = datagen.sift_like(n, D=D, n_centres=max(2, n // 60), seed=n + D)
+    p = knng.default_params(k=k, leaf_max=lm, tree_passes=passes, refine_rounds=rounds, join_mode=mode,
+                            twomeans_iters=iters, seed=1234 + n)
+    ids, d = knng.knng_build_ex(_dev(X), p)
+    o_ids, o_d = oracle.build_graph(X, k, lm, passes=passes, rounds=rounds, iters=iters, mode=mode, seed=1234 + n)
+    _assert_graph_equal(ids, d, o_ids, o_d)
+    _assert_valid(ids, d)
+
+
+def test_plain_build_entry_point(knng):
+    X = datagen.sift_like(2000, D=16, n_centres=30, seed=3)
+    ids, d = knng.knng_build(_dev(X), k=10, leaf_max=64, rounds=3, seed=99)
+    o_ids, o_d = oracle.build_graph(X, 10, 64, passes=3, rounds=0, iters=4, seed=99)
+    _assert_graph_equal(ids, d, o_ids, o_d)
+
+
+def test_host_pointers_give_the_same_graph(knng):
+    X = datagen.sift_like(1200, D=20, n_centres=15, seed=5)
+    p = knng.default_params(k=6, leaf_max=32, tree_passes=2, refine_rounds=1, seed=8)
+    hi, hd = knng.knng_build_ex(X, p)                        # numpy in, numpy out
+    di, dd = knng.knng_build_ex(_dev(X), p)
+    assert isinstance(hi, np.ndarray)
+    _assert_graph_equal(di, dd, hi, hd)
+
+
+# ---------------------------------------------------------------- partition
+@pytest.mark.parametrize("n,D,lm,iters", [(20000, 12, 64, 3), (5000, 7, 40, 4), (64, 5, 64, 4), (9000, 1, 100, 2)])
+def test_partition_matches_oracle_on_integer_data(knng, n, D, lm, iters):
+    # n = 20000 takes the multi-CTA selection at the top levels
+    X = datagen.sift_like(n, D=D, n_centres=50, seed=n)
+    perm, off = knng.knng_partition(_dev(X), lm, twomeans_iters=iters, seed=77, pass_=1)
+    o_perm, o_off = oracle.partition(X, lm, iters=iters, seed=77, pass_=1)
+    assert np.array_equal(_np(off), o_off)
+    assert np.array_equal(_np(perm), o_perm)
+
+
+def test_partition_invariants_on_float_data(knng):
+    X = datagen.gaussian_mixture(30000, 20, 100, seed=4)
+    perm, off = knng.knng_partition(_dev(X), 100, seed=3)
+    perm, off = _np(perm), _np(off)
+    L = knng.knng_tree_depth(30000, 100)
+    assert len(off) == (1 << L) + 1
+    assert np.array_equal(np.sort(perm), np.arange(30000))
+    for a, b in zip(off[:-1], off[1:]):
+        assert np.all(np.diff(perm[a:b]) > 0)
+    o_perm, o_off = oracle.partition(X, 100, seed=3)
+    assert np.array_equal(off, o_off)
+    # FP64 sums in another order may move a few points at a cut; most leaves agree
+    same = sum(np.array_equal(perm[a:b], o_perm[a:b]) for a, b in zip(off[:-1], off[1:]))
+    assert same >= 0.9 * (len(off) - 1)
+
+
+# ---------------------------------------------------------------- leaf stage
+@pytest.mark.parametrize("n,D,k,lm", [(6000, 32, 10, 64), (3000, 37, 20, 128), (2000, 300, 8, 256)])
+def test_leaf_stage_on_gpu_partition_matches_oracle(knng, n, D, k, lm):
+    X = datagen.gaussian_mixture(n, D, 40, seed=D)
+    perm, off = knng.knng_partition(_dev(X), lm, seed=5)
+    perm_h, off_h = _np(perm), _np(off)
+    o_ids, o_d = oracle.leaf_update(X, k, perm_h, off_h)
+    ids0, d0 = oracle.new_graph(n, k)
+    g_ids, g_d = knng.knng_leaf_update(_dev(X), k, perm, off, _dev(ids0), _dev(d0))
+    _assert_graph_equal(g_ids, g_d, o_ids, o_d)
+    # the build's first pass is the same computation
+    p = knng.default_params(k=k, leaf_max=lm, tree_passes=1, refine_rounds=0, seed=5)
+    b_ids, b_d = knng.knng_build_ex(_dev(X), p)
+    _assert_graph_equal(b_ids, b_d, o_ids, o_d)
+
+
+def test_leaf_update_merges_into_an_existing_graph(knng):
+    X = datagen.gaussian_mixture(4000, 16, 30, seed=9)
+    k = 12
+    g = oracle.build_graph(X, k, 64, passes=1, rounds=0, seed=1)
+    perm, off = knng.knng_partition(_dev(X), 64, seed=2, pass_=3)
+    o_ids, o_d = oracle.leaf_update(X, k, _np(perm), _np(off), *g)
+    g_ids, g_d = knng.knng_leaf_update(_dev(X), k, perm, off, _dev(g[0]), _dev(g[1]))
+    _assert_graph_equal(g_ids, g_d, o_ids, o_d)
+
+
+# ---------------------------------------------------------------- refinement
+@pytest.mark.parametrize("mode", [oracle.FWD, oracle.FWD_REV])
+@pytest.mark.parametrize("n,D,k", [(5000, 24, 10), (3000, 50, 16), (2000, 9, 32)])
+def test_refine_round_matches_oracle(knng, mode, n, D, k):
+    if mode == oracle.FWD_REV and 2 * k > 64:
+        pytest.skip("reverse lists need 2k <= 64")
+    X = datagen.gaussian_mixture(n, D, 25, seed=n + k)
+    g = oracle.build_graph(X, k, max(64, 2 * (k + 1)), passes=2, rounds=0, seed=3)
+    o_ids, o_d = oracle.refine_round(X, *g, mode=mode)
+    p = knng.default_params(k=k, refine_rounds=1, join_mode=mode)
+    g_ids, g_d = knng.knng_refine(_dev(X), _dev(g[0]), _dev(g[1]), p)
+    _assert_graph_equal(g_ids, g_d, o_ids, o_d)
+
+
+def test_refine_from_random_graph_two_rounds(knng):
+    # a random start makes every round propose a lot (stress of the grouping)
+    X = datagen.gaussian_mixture(1500, 12, 10, seed=21)
+    k = 10
+    rng = np.random.default_rng(0)
+    ids, d = oracle.new_graph(1500, k)
+    for i in range(1500):
+        for j in rng.choice(np.delete(np.arange(1500), i), size=k, replace=False):
+            oracle.list_insert(ids[i], d[i], oracle.dist_f32(X[i], X[j]), j)
+    o = (ids, d)
+    for _ in range(2):
+        o = oracle.refine_round(X, *o, mode=oracle.FWD_REV)
+    p = knng.default_params(k=k, refine_rounds=2, join_mode=knng.KNNG_JOIN_FWD_REV)
+    g_ids, g_d = knng.knng_refine(_dev(X), _dev(ids), _dev(d), p)
+    _assert_graph_equal(g_ids, g_d, *o)
+
+
+# ---------------------------------------------------------------- exact, recall
+@pytest.mark.parametrize("n,D,k,s", [(3000, 32, 10, None), (5000, 37, 20, 300), (2000, 200, 50, 150),
+                                     (129, 4, 3, None)])
+def test_exact_matches_oracle(knng, n, D, k, s):
+    X = datagen.gaussian_mixture(n, D, 20, seed=n)
+    smp = None if s is None else datagen.sample_rows(n, s, seed=1)
+    g_ids, g_d = knng.knng_exact(_dev(X), k, None if smp is None else _dev(smp))
+    o_ids, o_d = oracle.exact_f32(X, k, smp)
+    _assert_graph_equal(g_ids, g_d, o_ids, o_d)
+
+
+def test_exact_integer_ties(knng):
+    rng = np.random.default_rng(2)
+    X = rng.integers(0, 3, size=(1000, 4)).astype(np.float32)     # heavy ties
+    g_ids, g_d = knng.knng_exact(_dev(X), 15)
+    o_ids, o_d = oracle.exact_f32(X, 15)
+    _assert_graph_equal(g_ids, g_d, o_ids, o_d)
+
+
+def test_recall_matches_oracle(knng):
+    X = datagen.gaussian_mixture(4000, 16, 40, seed=31)
+    k = 10
+    ids, d = oracle.build_graph(X, k, 64, passes=1, rounds=0, seed=4)
+    smp = datagen.sample_rows(4000, 500, seed=2)
+    gi, gd = oracle.exact_f32(X, k, smp)
+    want = oracle.recall(ids, d, gi, gd, smp)
+    got = knng.knng_recall(_dev(ids), _dev(d), _dev(gi), _dev(gd), _dev(smp))
+    assert got == want
+    got_host = knng.knng_recall(ids, d, gi, gd, smp)
+    assert got_host == want
+
+
+# ---------------------------------------------------------------- edge cases
+def test_duplicate_points_and_zero_vectors(knng):
+    X = np.zeros((600, 8), np.float32)
+    X[300:] = datagen.sift_like(300, D=8, n_centres=3, seed=1)[np.arange(300) % 7]   # many duplicates
+    p = knng.default_params(k=9, leaf_max=32, tree_passes=2, refine_rounds=1, seed=2)
+    ids, d = knng.knng_build_ex(_dev(X), p)
+    o_ids, o_d = oracle.build_graph(X, 9, 32, passes=2, rounds=1, seed=2)
+    _assert_graph_equal(ids, d, o_ids, o_d)
+
+
+def test_non_finite_input_is_rejected(knng):
+    X = datagen.gaussian_mixture(500, 8, 5, seed=1)
+    X[123, 4] = np.nan
+    with pytest.raises(knng.KnngError) as e:
+        knng.knng_build_ex(_dev(X), knng.default_params(k=5, leaf_max=32))
+    assert e.value.code == -1 and "non-finite" in str(e.value)
+    X[123, 4] = np.inf
+    with pytest.raises(knng.KnngError):
+        knng.knng_exact(_dev(X), 5)
+
+
+def test_empty_sample_and_zero_passes(knng):
+    X = datagen.gaussian_mixture(300, 8, 5, seed=1)
+    ids, d = knng.knng_build_ex(_dev(X), knng.default_params(k=4, tree_passes=0))
+    assert np.all(_np(ids) == -1) and np.all(np.isinf(_np(d)))
+    gi, gd = knng.knng_exact(_dev(X), 4, _dev(np.zeros(0, np.int32)))
+    assert _np(gi).shape == (0, 4)

@@ -1,0 +1,80 @@
+"""CPU-side checks of the C ABI library: it builds for sm_103a, loads, and
+exports every entry point include/knng.h declares; host-only entry points
+answer without a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1701_08475_gb300 import build
+    build.build()
+    import paper_1701_08475_gb300 as knng
+    return knng.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "knng.h")).read()
+    return sorted(set(re.findall(r"KNNG_API\s+[\w\s\*]*?\b(knng_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_abi():
+    names = _declared()
+    for want in ("knng_build", "knng_build_ex", "knng_refine", "knng_partition", "knng_leaf_update",
+                 "knng_exact", "knng_recall", "knng_last_error", "knng_workspace_bytes"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", os.path.join(ROOT, "paper_1701_08475_gb300", "libknng.so")],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (knng_\w+)", out))
+    assert set(_declared()) <= exported
+    # nothing but the C ABI is exported
+    assert exported == set(_declared())
+    for name in _declared():
+        assert getattr(lib, name) is not None
+
+
+def test_library_is_built_for_sm103a(lib):
+    out = subprocess.run(["cuobjdump", "--list-elf", os.path.join(ROOT, "paper_1701_08475_gb300", "libknng.so")],
+                         capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_host_only_entry_points(lib):
+    import paper_1701_08475_gb300 as knng
+    p = knng.default_params()
+    assert (p.k, p.leaf_max, p.tree_passes, p.refine_rounds, p.twomeans_iters) == (10, 64, 1, 0, 4)
+    assert knng.knng_tree_depth(1_000_000, 128) == 13
+    assert knng.knng_tree_depth(10_000, 64) == 8
+    assert knng.knng_tree_depth(50, 64) == 0
+    assert knng.knng_tree_depth(0, 64) == -1
+    p2 = knng.default_params(k=20, leaf_max=128, tree_passes=3, refine_rounds=4)
+    ws = knng.knng_workspace_bytes(1_000_000, 128, p2)
+    # graph double buffer + reverse lists at least; bounded offer budget
+    assert 4 * 1_000_000 * 20 * 8 <= ws < 16 << 30
+    bad = knng.default_params(k=20, leaf_max=30)   # leaf_max < 2(k+1)
+    assert knng.knng_workspace_bytes(1000, 8, bad) == 0
+    assert b"leaf_max" in lib.knng_last_error()
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu(lib):
+    import numpy as np
+    import paper_1701_08475_gb300 as knng
+    X = np.zeros((10, 4), np.float32)
+    with pytest.raises(knng.KnngError) as e:
+        knng.knng_build(X, k=10, leaf_max=64)      # n <= k
+    assert e.value.code == -1
+    with pytest.raises(knng.KnngError):
+        knng.knng_build(X, k=3, leaf_max=7)        # leaf_max < 2(k+1)
+    with pytest.raises(knng.KnngError):
+        knng.knng_build_ex(X, knng.default_params(k=3, leaf_max=64, precision=7))
