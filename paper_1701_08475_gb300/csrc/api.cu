@@ -391,6 +391,7 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.sb.st = ws.take<SelState>(ns);
         b.sb.ghist = ws.take<uint32_t>((size_t)nl << kRadixBits);
         b.sb.ticket = ws.take<uint32_t>(nl);
+        b.sb.nseg_large = nl;
         b.sb.partial = ws.take<double>((size_t)nt * 2 * D);
         b.sb.tile_left = ws.take<int32_t>(nt);
         b.sb.status = b.status;
@@ -446,6 +447,10 @@ int32_t* run_partition(const float* X, const Args& a, const TreePlan& tp, BuildL
     const uint64_t ps = splitmix64(a.p.seed ^ (uint64_t)pass);
     int32_t* pin = b.perm_a;
     int32_t* pout = b.perm_b;
+    // the cross-CTA selection accumulates into these and leaves them zero
+    cuda_check(cudaMemsetAsync(b.sb.ghist, 0, sizeof(uint32_t) * ((size_t)b.sb.nseg_large << kRadixBits), s),
+               "histogram clear");
+    cuda_check(cudaMemsetAsync(b.sb.ticket, 0, sizeof(uint32_t) * b.sb.nseg_large, s), "ticket clear");
     k_iota<<<grid_1d(a.n), 256, 0, s>>>(pin, a.n);
     for (int l = 0; l < tp.L; ++l) {
         run_split_level(X, a.D, tp.levels[l], a.p.twomeans_iters, ps, pin, pout, b.sb, s);
@@ -717,9 +722,10 @@ int knng_exact(const float* data, int64_t n, int D, int k, const int32_t* sample
                float* out_dists, void* stream) {
     return guarded([&] {
         validate_common(data, n, D, k);
+        if (s_rows < 0) fail(KNNG_EINVAL, "s < 0");
+        if (s_rows == 0) return;  // nothing to compute (empty buffers may be NULL)
         if (!out_ids || !out_dists) fail(KNNG_EINVAL, "output pointer is NULL");
         if (!sample && s_rows != n) fail(KNNG_EINVAL, "without a sample s must equal n");
-        if (s_rows < 0) fail(KNNG_EINVAL, "s < 0");
         cudaStream_t s = (cudaStream_t)stream;
         Workspace ws;
         DevBuf<float> X;
@@ -758,10 +764,14 @@ int knng_recall(const int32_t* ids, const float* dists, const int32_t* gt_ids, c
                 const int32_t* sample, int64_t s_rows, int k, double* out_recall_ids, double* out_recall_tie,
                 void* stream) {
     return guarded([&] {
-        if (!ids || !dists || !gt_ids || !gt_dists || !sample || !out_recall_ids || !out_recall_tie)
-            fail(KNNG_EINVAL, "NULL pointer");
+        if (!out_recall_ids || !out_recall_tie) fail(KNNG_EINVAL, "NULL output pointer");
         if (k < 1 || k > 64) fail(KNNG_EINVAL, "k out of range");
         if (s_rows < 0) fail(KNNG_EINVAL, "s < 0");
+        if (s_rows == 0) {  // no rows: recall is defined as 0
+            *out_recall_ids = *out_recall_tie = 0.0;
+            return;
+        }
+        if (!ids || !dists || !gt_ids || !gt_dists || !sample) fail(KNNG_EINVAL, "NULL pointer");
         cudaStream_t s = (cudaStream_t)stream;
         const size_t sk = (size_t)s_rows * k;
         // host graphs: gather the sampled rows on the host (marshalling only)

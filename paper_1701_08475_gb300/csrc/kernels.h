@@ -48,8 +48,9 @@ struct SplitBuffers {
     float* S;             // [n] projections
     uint64_t* thr;        // [nseg_max] selected key (first key of the right side)
     SelState* st;         // [nseg_max]
-    uint32_t* ghist;      // [nseg_max][2048], zero between uses
-    uint32_t* ticket;     // [nseg_max], zero between uses
+    uint32_t* ghist;      // [nseg_large][2048]: zeroed once per partition, left zero by each select
+    uint32_t* ticket;     // [nseg_large]: same
+    int nseg_large;       // segments of the widest level that selects across CTAs
     double* partial;      // [ntiles_max][2][D]
     int32_t* tile_left;   // [ntiles_max]
     int* status;          // device status word

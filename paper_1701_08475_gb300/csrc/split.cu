@@ -87,7 +87,8 @@ __device__ __forceinline__ void find_digit(const uint32_t* hist, int nb, uint32_
 
 __global__ void k1_init(const float* __restrict__ X, int D, const int32_t* __restrict__ perm,
                         const int32_t* __restrict__ seg_off, int level, uint64_t pass_seed,
-                        float* __restrict__ W) {
+                        float* __restrict__ W, const int* __restrict__ status) {
+    if (*status & kStatusStop) return;  // perm may hold unwritten slots
     const int seg = blockIdx.x;
     const int a = seg_off[seg];
     const int m = seg_off[seg + 1] - a;
@@ -110,9 +111,10 @@ __global__ void __launch_bounds__(256) k1_project(const float* __restrict__ X, i
                                                   const int4* __restrict__ tiles,
                                                   const int32_t* __restrict__ seg_off,
                                                   const float* __restrict__ W, float* __restrict__ S,
-                                                  SelState* __restrict__ st) {
+                                                  SelState* __restrict__ st, const int* __restrict__ status) {
     __shared__ float xs[256][33];
     __shared__ float ws[32];
+    if (*status & kStatusStop) return;  // perm may hold unwritten slots
     const int4 t = tiles[blockIdx.x];
     const int seg = t.x, begin = t.y, end = t.z;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -262,8 +264,9 @@ __global__ void __launch_bounds__(256) k1_sums(const float* __restrict__ X, int 
                                                const int4* __restrict__ tiles, const float* __restrict__ S,
                                                const int32_t* __restrict__ seg_off,
                                                const uint64_t* __restrict__ thr, int pos_bits,
-                                               double* __restrict__ partial) {
+                                               double* __restrict__ partial, const int* __restrict__ status) {
     __shared__ double red[8][2][128];
+    if (*status & kStatusStop) return;  // perm may hold unwritten slots
     const int4 t = tiles[blockIdx.x];
     const int seg = t.x, begin = t.y, end = t.z;
     const int dbase = blockIdx.y * 128;
@@ -389,14 +392,14 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
     const int dchunks = (D + 127) / 128;
     {
         LaunchScope ls("k1_init", s, (double)lp.nseg * 3 * D * 4, 0);
-        k1_init<<<lp.nseg, 128, 0, s>>>(X, D, perm_in, lp.seg_off, lp.level, pass_seed, b.W);
+        k1_init<<<lp.nseg, 128, 0, s>>>(X, D, perm_in, lp.seg_off, lp.level, pass_seed, b.W, b.status);
     }
     for (int it = 0; it <= iters; ++it) {
         const bool last = it == iters;
         {
             LaunchScope ls("k1_project", s, rows + n * 8, 2.0 * n * D);
             k1_project<<<lp.ntiles, 256, 0, s>>>(X, D, perm_in, lp.tiles, lp.seg_off, b.W, b.S,
-                                                 lp.small ? nullptr : b.st);
+                                                 lp.small ? nullptr : b.st, b.status);
         }
         if (lp.small) {
             const size_t smem = (size_t)lp.max_m * sizeof(uint64_t);
@@ -429,10 +432,10 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
             dim3 grid(lp.ntiles, dchunks);
             if (vec)
                 k1_sums<true><<<grid, 256, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr, lp.pos_bits,
-                                                   b.partial);
+                                                   b.partial, b.status);
             else
                 k1_sums<false><<<grid, 256, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr, lp.pos_bits,
-                                                    b.partial);
+                                                    b.partial, b.status);
         }
         {
             LaunchScope ls("k1_centroids", s, (double)lp.ntiles * 2 * D * 8 + (double)lp.nseg * D * 4, 0);
