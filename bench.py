@@ -1,0 +1,352 @@
+"""Benchmark: kNN-graph build throughput (points/s) with recall@k against exact.
+
+One step = one whole build (tree passes of Alg. 1, Sec. 3.1, then the
+refinement rounds) of the workload's n points, inputs resident in HBM.
+Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+N > 1 (under torchrun): every rank builds its own instance (weak scaling,
+no collective on the data path); the step time is the max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import datagen  # noqa: E402
+
+DEFAULT_WORKLOAD = "sift-like-1m-d128"
+REF_SAMPLE_N = 10_000      # oracle sample size per reference-arm step (~8 s)
+CPU_BASELINE_N = 20_000    # oracle sample size of the cpu_baseline entry (~16 s)
+RECALL_SAMPLE = 10_000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(name):
+    w = dict(datagen.WORKLOADS[name])
+    return dict(workload=name, n=w["n"], D=w["D"], k=w["k"], leaf_max=w["leaf_max"], tree_passes=w["passes"],
+                refine_rounds=w["rounds"], join_mode="fwd_rev", twomeans_iters=4, precision="fp32",
+                generator=w["gen"], seed=w["seed"])
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        if not self.rows:
+            return None
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(self.rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------- roofline
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+KERNEL_SOURCES = {"k1_": "split.cu", "k2_": "leaf.cu", "k4_": "join.cu", "k5_": "join.cu", "k6_": "join.cu",
+                  "k7_": "exact.cu"}
+ALU_KERNELS = ("k5_join", "k2_leaf_fp32", "k7_exact")
+
+
+def kernel_source_hash(kernel):
+    for pre, f in KERNEL_SOURCES.items():
+        if kernel.startswith(pre):
+            path = os.path.join(ROOT, "paper_1701_08475_gb300", "csrc", f)
+            with open(path, "rb") as fh:
+                return hashlib.sha256(fh.read()).hexdigest()[:16]
+    return None
+
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per algorithmic byte from the committed ncu summary of this
+    kernel, or None when there is none or the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("- ") and ":" in line:
+                k_, v = line[2:].split(":", 1)
+                vals[k_.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256_16") != kernel_source_hash(kernel):
+        return None
+    try:
+        return float(vals["dram_bytes_per_alg_byte"])
+    except (KeyError, ValueError):
+        return None
+
+
+def roofline(stats, clocks, workload, steps):
+    peaks, kind = measured_peaks()
+    name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    avg_ms = st["ms"] / st["launches"]
+    per_launch_bytes = st["bytes"] / st["launches"]
+    if name in ALU_KERNELS:
+        # FP32 issue-slot roofline: one FSUB + one FFMA per pair and dim
+        # (flops counted 3 per pair-dim: sub 1, fma 2 -> 2 issue slots)
+        sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        ops = st["flops"] / st["launches"] * 2.0 / 3.0
+        achieved = ops / (avg_ms * 1e-3) / 1e12
+        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+        out = {"kernel": name, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+               "unit": "Top/s", "frac": round(achieved / peak, 4),
+               "peak_source": "derived: 152 SMs x 128 FP32 lanes x median SM clock %.0f MHz" % sm_mhz}
+    else:
+        achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        out = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+               "frac": round(achieved / peak, 4), "peak_source": "%s hbm_gbs" % kind}
+    ratio = profiled_traffic(name, workload)
+    out["traffic"] = None if ratio is None else round(ratio * per_launch_bytes)
+    out["alg_bytes_per_launch"] = round(per_launch_bytes)
+    out["avg_launch_ms"] = round(avg_ms, 4)
+    out["launches_per_step"] = st["launches"] / steps
+    out["share_of_step"] = None
+    return out
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_build_seconds(cfg, n_s):
+    import oracle
+    X = datagen.make(cfg["workload"], n_s)
+    t = time.perf_counter()
+    oracle.build_graph(X, cfg["k"], cfg["leaf_max"], passes=cfg["tree_passes"], rounds=cfg["refine_rounds"],
+                       iters=cfg["twomeans_iters"], mode=oracle.FWD_REV, seed=cfg["seed"])
+    return time.perf_counter() - t
+
+
+def cpu_baseline(cfg):
+    n_s = CPU_BASELINE_N
+    sec = oracle_build_seconds(cfg, n_s)
+    return {"value": round(n_s / sec, 1), "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": "whole build (same k, leaf_max, passes, rounds, iters) of the first recipe draw at "
+                      "n=%d instead of %d points; %.1f s single-threaded" % (n_s, cfg["n"], sec),
+            "host_cpus": os.cpu_count()}
+
+
+def run_reference(args, cfg):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    n_s = REF_SAMPLE_N
+    for _ in range(args.warmup):
+        oracle_build_seconds(cfg, n_s)
+    total = 0.0
+    for _ in range(args.steps):
+        total += oracle_build_seconds(cfg, n_s)
+    value = n_s * args.steps / total
+    line = {"impl": "reference", "metric": "kNN-graph build points/s at recall@k vs exact", "value": round(value, 1),
+            "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": round(value, 1), "unit": "points/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: whole build of n=%d points of the recipe (same parameters)" % n_s},
+            "e2e": {"value": round(value, 1), "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, cfg):
+    import torch
+    import paper_1701_08475_gb300 as knng
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    knng.load()
+
+    X = datagen.make(cfg["workload"])
+    if world > 1:   # independent replica per rank: a different draw
+        X = X[np.random.default_rng(rank).permutation(X.shape[0])]
+    n, D = X.shape
+    Xd = torch.from_numpy(X).to(dev)
+    p = knng.default_params(k=cfg["k"], leaf_max=cfg["leaf_max"], tree_passes=cfg["tree_passes"],
+                            refine_rounds=cfg["refine_rounds"], join_mode=knng.KNNG_JOIN_FWD_REV,
+                            twomeans_iters=cfg["twomeans_iters"], seed=cfg["seed"])
+    stream = torch.cuda.Stream(dev)
+    ids = torch.empty((n, cfg["k"]), dtype=torch.int32, device=dev)
+    dists = torch.empty((n, cfg["k"]), dtype=torch.float32, device=dev)
+
+    def step():
+        knng.knng_build_ex(Xd, p, stream=stream, out=(ids, dists))
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    knng.stats_reset()
+    knng.stats_enable(True, timing=True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    knng.stats_enable(False)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    st = knng.stats()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = sum(v["launches"] for v in st.values())
+    value = world * n * args.steps / (ms * 1e-3)
+
+    # recall of the last graph on sampled rows, against exact lists
+    smp = datagen.sample_rows(n, RECALL_SAMPLE, seed=3)
+    smp_d = torch.from_numpy(smp).to(dev)
+    gi, gd = knng.knng_exact(Xd, cfg["k"], smp_d)
+    rec_ids, rec_tie = knng.knng_recall(ids, dists, gi, gd, smp_d)
+
+    # end to end: host buffers through the C ABI, copies inside the timed region
+    Xh = torch.from_numpy(X).pin_memory()
+    oi = torch.empty((n, cfg["k"]), dtype=torch.int32).pin_memory()
+    od = torch.empty((n, cfg["k"]), dtype=torch.float32).pin_memory()
+    knng.knng_build_ex(Xh, p, stream=stream, out=(oi, od))   # warm
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        knng.knng_build_ex(Xh, p, stream=stream, out=(oi, od))
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": round(world * n * args.e2e_steps / e2e_s, 1), "unit": "points/s",
+           "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(oi.numel() * 4 + od.numel() * 4),
+           "steps": args.e2e_steps, "timer": "host wall clock around synchronous C-ABI calls"}
+    same = bool(torch.equal(oi, ids.cpu()) and torch.equal(od, dists.cpu()))
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    roof = roofline(st, clk, cfg["workload"], args.steps)
+    roof["share_of_step"] = round(st[roof["kernel"]]["ms"] / ms, 4)
+    cfg_out = dict(cfg)
+    cfg_out["l2"] = "inputs larger than L2: X is %.0f MB (L2 129 MB)" % (X.nbytes / 1e6)
+    line = {
+        "metric": "kNN-graph build points/s at recall@k vs exact", "value": round(value, 1), "unit": "points/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": cfg_out,
+        "recall_at_k": {"ids": round(rec_ids, 5), "tie": round(rec_tie, 5), "sample_rows": int(len(smp)),
+                        "exact": "knng_exact canonical FP32"},
+        "roofline": roof, "e2e": e2e, "e2e_graph_equals_device_graph": same, "gpu_launches": int(launches),
+        "clocks": clk,
+        "kernels": {k_: {"ms_per_step": round(v["ms"] / args.steps, 3), "launches_per_step": v["launches"] / args.steps}
+                    for k_, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    cfg = workload_config(args.workload)
+    if args.impl == "reference":
+        run_reference(args, cfg)
+    else:
+        run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    main()
