@@ -157,6 +157,33 @@ KNNG_API int knng_recall(const int32_t *ids, const float *dists, const int32_t *
                 const float *gt_dists, const int32_t *sample, int64_t s, int k,
                 double *out_recall_ids, double *out_recall_tie, void *stream);
 
+/*
+ * knng_exact without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * where they need ground-truth lists -- code running under a memory manager
+ * that owns all device memory (a cudaMalloc would fail or escape its
+ * accounting), or a latency-bound loop where an allocation's implicit
+ * synchronisation is not allowed.
+ *
+ * Same result as knng_exact for the same arguments.  Differences:
+ *   - data, sample, out_ids and out_dists must be device pointers (no host
+ *     staging); sample is required (s >= 1);
+ *   - s * k must not exceed 262144 (KNNG_EINVAL otherwise): the scratch is a
+ *     fixed 2 MiB static device array (plus one status word) that every GPU
+ *     loading the library holds until the process exits;
+ *   - the first call on each device looks up the scratch's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device;
+ *   - every call on a device shares the one scratch: calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race and must
+ *     be serialised by the caller.  The scratch keeps the last call's
+ *     contents; each call clears the status word it needs at zero and
+ *     overwrites the lists in full.
+ * The call is synchronous with respect to `stream`.
+ */
+KNNG_API int knng_exact_noalloc(const float *data, int64_t n, int D, int k, const int32_t *sample,
+                                int64_t s, int32_t *out_ids, float *out_dists, void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 KNNG_API const char *knng_last_error(void);
 

@@ -16,6 +16,7 @@ from ._lib import (  # noqa: F401
     knng_build,
     knng_build_ex,
     knng_exact,
+    knng_exact_noalloc,
     knng_leaf_update,
     knng_partition,
     knng_recall,

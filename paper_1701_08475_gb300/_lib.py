@@ -64,6 +64,7 @@ def load():
             "knng_tree_depth": (i32, [i64, i32]),
             "knng_leaf_update": (i32, [P, i64, i32, i32, P, P, i64, P, P, P]),
             "knng_exact": (i32, [P, i64, i32, i32, P, i64, P, P, P]),
+            "knng_exact_noalloc": (i32, [P, i64, i32, i32, P, i64, P, P, P]),
             "knng_recall": (i32, [P, P, P, P, P, i64, i32, P, P, P]),
             "knng_last_error": (ctypes.c_char_p, []),
             "knng_workspace_bytes": (ctypes.c_size_t, [i64, i32, PP]),
@@ -241,6 +242,27 @@ def knng_exact(data, k, sample=None, stream=None):
     d = _empty_like_input(data, (s_rows, k), "float32")
     with _DeviceCtx(data, stream) as s:
         _check(load().knng_exact(_ptr(data), n, D, k, _ptr(sample), s_rows, _ptr(ids), _ptr(d), s))
+    return ids, d
+
+
+def knng_exact_noalloc(data, k, sample, out=None, stream=None):
+    """knng_exact that allocates no device memory inside the library: for
+    callers that cannot allocate at that point (a memory manager owns the
+    device's memory, or an allocation's implicit synchronisation is not
+    allowed).  Device tensors only; len(sample) * k <= 262144.  Pass `out`
+    (two preallocated device tensors of shape (len(sample), k)) to avoid any
+    allocation on this side too."""
+    data = _contig(data, "float32")
+    sample = _contig(sample, "int32")
+    n, D = data.shape
+    s_rows = len(sample)
+    if out is None:
+        ids = _empty_like_input(data, (s_rows, k), "int32")
+        d = _empty_like_input(data, (s_rows, k), "float32")
+    else:
+        ids, d = out
+    with _DeviceCtx(data, stream) as s:
+        _check(load().knng_exact_noalloc(_ptr(data), n, D, k, _ptr(sample), s_rows, _ptr(ids), _ptr(d), s))
     return ids, d
 
 

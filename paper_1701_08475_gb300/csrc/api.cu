@@ -44,6 +44,12 @@ void cuda_check(cudaError_t e, const char* what) {
     fail(KNNG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+}  // namespace
+
+// Sets the message knng_last_error returns (for entry points outside this file).
+void record_error(const char* msg) { g_last_error = msg; }
+
+namespace {
 template <class F>
 int guarded(F&& f) {
     g_last_error.clear();
