@@ -25,25 +25,47 @@ def gaussian_mixture(n, D, n_centres, seed, lo=-10.0, hi=10.0, sigma=1.0):
     return np.ascontiguousarray(X, dtype=np.float32)
 
 
-def sift_like(n, D=128, n_centres=1000, seed=0, zero_frac=0.3, spread=25.0, chunk=1 << 18):
-    """Non-negative integers 0..255 stored as FP32, clustered.
+def sift_like(n, D=128, n_centres=1000, seed=0, zero_frac=0.3, spread=25.0, latent_dim=16, noise=4.0,
+              chunk=1 << 18):
+    """Non-negative integers 0..255 stored as FP32, clustered, low intrinsic dimension.
 
-    Centres ~ U[0, 120]^D; point = centre + N(0, spread^2); a Bernoulli(zero_frac)
-    mask zeroes coordinates; then clip to [0, 255] and round.
+    Centres ~ U[0, 120]^D, each with its own set of zero coordinates
+    (Bernoulli(zero_frac)).  A point varies around its centre inside the
+    centre's own latent_dim-dimensional subspace (a random D x latent_dim basis
+    scaled so every coordinate has standard deviation `spread`), plus
+    N(0, noise^2) in every coordinate; the centre's zero coordinates stay
+    zero; then clip to [0, 255] and round.  (Descriptors like SIFT's have a
+    low intrinsic dimension; isotropic 128-d noise would make every point of a
+    cluster nearly equidistant, which no real descriptor set does.)
+    With latent_dim=None the variation is isotropic N(0, spread^2) instead.
     """
     rng = np.random.default_rng(seed)
     centres = rng.uniform(0.0, 120.0, size=(n_centres, D)).astype(np.float32)
+    keep = (rng.random(size=(n_centres, D)) >= zero_frac).astype(np.float32)
     lab = rng.integers(0, n_centres, size=n)
+    if latent_dim:
+        basis = rng.standard_normal(size=(n_centres, latent_dim, D), dtype=np.float32)
+        basis *= np.float32(spread / np.sqrt(latent_dim))
     X = np.empty((n, D), np.float32)
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
-        v = rng.standard_normal(size=(b - a, D), dtype=np.float32)
-        v *= np.float32(spread)
-        v += centres[lab[a:b]]
-        v[rng.random(size=(b - a, D), dtype=np.float32) < zero_frac] = 0.0
+        lb = lab[a:b]
+        if latent_dim:
+            z = rng.standard_normal(size=(b - a, latent_dim), dtype=np.float32)
+            v = rng.standard_normal(size=(b - a, D), dtype=np.float32) * np.float32(noise)
+            order = np.argsort(lb, kind="stable")
+            bounds = np.searchsorted(lb[order], np.arange(n_centres + 1))
+            for c in range(n_centres):
+                rows = order[bounds[c]:bounds[c + 1]]
+                if len(rows):
+                    v[rows] += z[rows] @ basis[c]
+        else:
+            v = rng.standard_normal(size=(b - a, D), dtype=np.float32) * np.float32(spread)
+        v += centres[lb]
+        v *= keep[lb]
         np.clip(v, 0.0, 255.0, out=v)
         np.rint(v, out=v)
-        X[a:b] = v
+        X[a:b] = v.astype(np.float32, copy=False)
     return X
 
 

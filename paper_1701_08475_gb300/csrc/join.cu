@@ -213,11 +213,15 @@ __global__ void __launch_bounds__(256) k6_select(const uint64_t* __restrict__ rb
 // chunk's buffer.
 constexpr int kJoinWarps = 4;
 
+// Dims per shared-memory chunk (about 12 KB of member rows per warp, equal
+// chunks) and the row stride (stride / 4 odd: consecutive rows in different
+// banks for float4 reads).
 __host__ __device__ inline void join_chunk(int D, int mcap, int* dch, int* stride) {
     const int d4 = (D + 3) & ~3;
-    int cap = (24 * 1024 / (mcap * 4) - 4) & ~3;
+    int cap = (12 * 1024 / (mcap * 4) - 4) & ~3;
     if (cap < 4) cap = 4;
-    const int c = d4 < cap ? d4 : cap;
+    const int nch = (d4 + cap - 1) / cap;
+    const int c = ((d4 + nch - 1) / nch + 3) & ~3;
     *dch = c;
     *stride = ((c / 4) & 1) ? c : c + 4;
 }
@@ -310,17 +314,21 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
             xs[r * stride + c] = 0.f;
         }
         __syncwarp();
+        // block (rg, cg) holds members {rg + a * RGN} x {cg + b * RGN}: lanes
+        // then read consecutive rows, which the odd stride / 4 puts in
+        // different banks
 #pragma unroll
         for (int q = 0; q < BPL; ++q) {
             if (brg[q] < 0) continue;
-            const float* rp = xs + brg[q] * 4 * stride;
-            const float* cp = xs + bcg[q] * 4 * stride;
+            const float* rp = xs + brg[q] * stride;
+            const float* cp = xs + bcg[q] * stride;
+            const int step = RGN * stride;
             for (int dq = 0; dq < dch; dq += 4) {
                 float4 rv[4], cv[4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) rv[a] = *reinterpret_cast<const float4*>(rp + a * stride + dq);
+                for (int a = 0; a < 4; ++a) rv[a] = *reinterpret_cast<const float4*>(rp + a * step + dq);
 #pragma unroll
-                for (int b = 0; b < 4; ++b) cv[b] = *reinterpret_cast<const float4*>(cp + b * stride + dq);
+                for (int b = 0; b < 4; ++b) cv[b] = *reinterpret_cast<const float4*>(cp + b * step + dq);
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -338,7 +346,8 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
         }
         __syncwarp();
     }
-    // offers: count, reserve, write
+    // offers: count, reserve, write.  Every unordered member pair lies in
+    // exactly one block once diagonal blocks keep only a < b.
     int cnt = 0;
 #pragma unroll
     for (int q = 0; q < BPL; ++q) {
@@ -347,8 +356,8 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int ia = brg[q] * 4 + a, ib = bcg[q] * 4 + b;
-                if (ia < ib && ib < M) {
+                const int ia = brg[q] + a * RGN, ib = bcg[q] + b * RGN;
+                if (ia < M && ib < M && (brg[q] < bcg[q] || a < b)) {
                     const uint32_t u = (uint32_t)mem[ia], v = (uint32_t)mem[ib];
                     if (u != v) {
                         cnt += make_key(acc[q][a][b], v) < thr[ia];
@@ -375,8 +384,8 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int ia = brg[q] * 4 + a, ib = bcg[q] * 4 + b;
-                if (ia < ib && ib < M) {
+                const int ia = brg[q] + a * RGN, ib = bcg[q] + b * RGN;
+                if (ia < M && ib < M && (brg[q] < bcg[q] || a < b)) {
                     const uint32_t u = (uint32_t)mem[ia], v = (uint32_t)mem[ib];
                     if (u != v) {
                         const uint64_t ku = make_key(acc[q][a][b], v);

@@ -273,35 +273,57 @@ __global__ void __launch_bounds__(256) k1_sums(const float* __restrict__ X, int 
     const int a = seg_off[seg];
     const uint64_t T = thr[seg];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double aL[4] = {0.0, 0.0, 0.0, 0.0}, aR[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int p = begin + warp; p < end; p += 8) {
-        const bool left = sel_key(S[p], p - a, pos_bits) < T;
-        const float* x = X + (int64_t)perm[p] * D + dbase;
-        float v[4];
-        if (VEC) {
-            if (dbase + lane * 4 < D) {
-                const float4 f = __ldg(reinterpret_cast<const float4*>(x) + lane);
-                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-            } else {
-                v[0] = v[1] = v[2] = v[3] = 0.f;
+    // Per-lane compensated FP32 sums (Knuth's TwoSum: hi + lo carries the
+    // exact sum of every addition's rounding error), combined in FP64 below.
+    // GB300 issues FP64 at a small fraction of its FP32 rate, so one FP64
+    // add per element would bound this sweep far below HBM speed.  For
+    // integer-valued data every add is exact and lo stays 0.
+    float hL[4] = {0.f, 0.f, 0.f, 0.f}, lL[4] = {0.f, 0.f, 0.f, 0.f};
+    float hR[4] = {0.f, 0.f, 0.f, 0.f}, lR[4] = {0.f, 0.f, 0.f, 0.f};
+    constexpr int U = 4;  // independent rows in flight per warp
+    for (int p0 = begin + warp; p0 < end; p0 += 8 * U) {
+        float v[U][4];
+        bool left[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int p = p0 + 8 * u;
+            left[u] = false;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[u][j] = 0.f;
+            if (p < end) {
+                left[u] = sel_key(S[p], p - a, pos_bits) < T;
+                const float* x = X + (int64_t)perm[p] * D + dbase;
+                if (VEC) {
+                    if (dbase + lane * 4 < D) {
+                        const float4 f = __ldg(reinterpret_cast<const float4*>(x) + lane);
+                        v[u][0] = f.x; v[u][1] = f.y; v[u][2] = f.z; v[u][3] = f.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) v[u][j] = (dbase + lane + 32 * j < D) ? __ldg(x + lane + 32 * j) : 0.f;
+                }
             }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = (dbase + lane + 32 * j < D) ? __ldg(x + lane + 32 * j) : 0.f;
         }
-        if (left) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) aL[j] += (double)v[j];
-        } else {
+        for (int u = 0; u < U; ++u) {
+            if (p0 + 8 * u >= end) break;
+            float* h = left[u] ? hL : hR;
+            float* l = left[u] ? lL : lR;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) aR[j] += (double)v[j];
+            for (int j = 0; j < 4; ++j) {
+                const float s = __fadd_rn(h[j], v[u][j]);
+                const float bp = __fsub_rn(s, h[j]);
+                const float err = __fadd_rn(__fsub_rn(h[j], __fsub_rn(s, bp)), __fsub_rn(v[u][j], bp));
+                h[j] = s;
+                l[j] = __fadd_rn(l[j], err);
+            }
         }
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int dl = VEC ? lane * 4 + j : lane + 32 * j;
-        red[warp][0][dl] = aL[j];
-        red[warp][1][dl] = aR[j];
+        red[warp][0][dl] = (double)hL[j] + (double)lL[j];
+        red[warp][1][dl] = (double)hR[j] + (double)lR[j];
     }
     __syncthreads();
     if (threadIdx.x < 128 && dbase + threadIdx.x < D) {
