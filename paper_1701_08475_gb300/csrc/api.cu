@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -107,14 +108,14 @@ StatRegistry& reg() {
 }
 }  // namespace
 
-LaunchScope::LaunchScope(const char* name, cudaStream_t s, double bytes, double flops)
+LaunchScope::LaunchScope(const char* name, cudaStream_t s, double bytes, double flops, int kernels)
     : name_(name), s_(s), bytes_(bytes), flops_(flops), slot_(-1) {
     StatRegistry& r = reg();
     std::lock_guard<std::mutex> lk(r.mu);
     if (!r.on) return;
     knng_kernel_stat& st = r.stats[name];
     if (st.name[0] == 0) snprintf(st.name, sizeof st.name, "%s", name);
-    st.launches += 1;
+    st.launches += kernels;
     st.bytes += bytes;
     st.flops += flops;
     if (r.timing) {
@@ -368,7 +369,13 @@ void validate_params(const knng_params* p, int64_t n) {
     (void)n;
 }
 
-constexpr size_t kOfferBudgetBytes = size_t(8) << 30;
+// Device bytes for one chunk's offers (target, key, grouped key: 20 B each).
+// KNNG_OFFER_BUDGET_MB overrides it (smaller budgets mean more chunks).
+size_t offer_budget_bytes() {
+    const char* e = getenv("KNNG_OFFER_BUDGET_MB");
+    if (e && atol(e) > 0) return (size_t)atol(e) << 20;
+    return size_t(8) << 30;
+}
 
 struct BuildLayout {
     // sizes only; filled twice (layout, then real pointers)
@@ -406,7 +413,7 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         const bool rev = a.p.join_mode == KNNG_JOIN_FWD_REV;
         const int64_t m = rev ? 2 * k : k;
         const int64_t per_node = std::max<int64_t>(m * (m - 1), 1);
-        int64_t cap = (int64_t)(kOfferBudgetBytes / 20);
+        int64_t cap = (int64_t)(offer_budget_bytes() / 20);
         cap = std::min<int64_t>(cap, per_node * n);
         cap = std::min<int64_t>(cap, ((int64_t)1 << 31) - 1);
         b.nodes_per_chunk = std::max<int64_t>(cap / per_node, 1);
@@ -457,7 +464,10 @@ int32_t* run_partition(const float* X, const Args& a, const TreePlan& tp, BuildL
     cuda_check(cudaMemsetAsync(b.sb.ghist, 0, sizeof(uint32_t) * ((size_t)b.sb.nseg_large << kRadixBits), s),
                "histogram clear");
     cuda_check(cudaMemsetAsync(b.sb.ticket, 0, sizeof(uint32_t) * b.sb.nseg_large, s), "ticket clear");
-    k_iota<<<grid_1d(a.n), 256, 0, s>>>(pin, a.n);
+    {
+        LaunchScope ls("k_iota", s, a.n * 4.0, 0);
+        k_iota<<<grid_1d(a.n), 256, 0, s>>>(pin, a.n);
+    }
     for (int l = 0; l < tp.L; ++l) {
         run_split_level(X, a.D, tp.levels[l], a.p.twomeans_iters, ps, pin, pout, b.sb, s);
         std::swap(pin, pout);

@@ -204,12 +204,12 @@ void launch_recall(const int32_t* ids, const float* d, const int32_t* gt_ids, co
 }
 
 void launch_check_finite(const float* X, int64_t count, int* status, cudaStream_t s) {
-    LaunchScope ls("k0_check_finite", s, count * 4.0, 0);
     // X may start at any 4-byte boundary: handle the head up to 16 B alignment
     // and the tail with scalar loads
     const uintptr_t addr = reinterpret_cast<uintptr_t>(X);
     const int64_t head = (int64_t)(((16 - (addr & 15)) & 15) / 4);
     const int64_t h = head < count ? head : count;
+    LaunchScope ls("k0_check_finite", s, count * 4.0, 0, h > 0 ? 2 : 1);
     if (h > 0) k_check_finite<<<1, 32, 0, s>>>(nullptr, 0, X, (int)h, status);
     const int64_t rest = count - h;
     const int64_t n4 = rest / 4;

@@ -453,7 +453,7 @@ size_t scan_tmp_ints(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTil
 
 void launch_scan(const int32_t* cnt, int32_t* off, int64_t n, int32_t* tmp, cudaStream_t s) {
     const int nb = (int)((n + kScanTile - 1) / kScanTile);
-    LaunchScope ls("k_scan", s, n * 8.0, 0);
+    LaunchScope ls("k_scan", s, n * 8.0, 0, nb == 0 ? 0 : 3);
     if (nb == 0) {
         cudaMemsetAsync(off, 0, sizeof(int32_t), s);
         return;

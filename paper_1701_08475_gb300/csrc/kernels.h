@@ -11,7 +11,8 @@ namespace knng {
 // algorithmic bytes/flops and (optionally) event-timed device time can be
 // summed per kernel name.
 struct LaunchScope {
-    LaunchScope(const char* name, cudaStream_t s, double bytes, double flops);
+    // `kernels`: how many kernel launches the scope encloses
+    LaunchScope(const char* name, cudaStream_t s, double bytes, double flops, int kernels = 1);
     ~LaunchScope();
     const char* name_;
     cudaStream_t s_;
