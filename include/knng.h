@@ -203,6 +203,7 @@ typedef struct knng_kernel_stat {
     double ms;       /* summed device time, 0 when timing is off */
     double bytes;    /* summed algorithmic bytes */
     double flops;    /* summed algorithmic flops */
+    double items;    /* summed work items where counted (k5_join: offers that passed the filter) */
 } knng_kernel_stat;
 
 KNNG_API int knng_stats_enable(int on, int timing);

@@ -37,7 +37,7 @@ class Params(ctypes.Structure):
 
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double),
-                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double), ("items", ctypes.c_double)]
 
 
 def library_path():
@@ -302,5 +302,5 @@ def stats():
     for i in range(lib.knng_stats_count()):
         if lib.knng_stats_get(i, ctypes.byref(st)) == 0:
             out[st.name.decode()] = dict(launches=int(st.launches), ms=float(st.ms), bytes=float(st.bytes),
-                                         flops=float(st.flops))
+                                         flops=float(st.flops), items=float(st.items))
     return out

@@ -126,6 +126,21 @@ LaunchScope::LaunchScope(const char* name, cudaStream_t s, double bytes, double 
     }
 }
 
+void record_items(const char* name, double items) {
+    StatRegistry& r = reg();
+    std::lock_guard<std::mutex> lk(r.mu);
+    if (!r.on) return;
+    knng_kernel_stat& st = r.stats[name];
+    if (st.name[0] == 0) snprintf(st.name, sizeof st.name, "%s", name);
+    st.items += items;
+}
+
+bool stats_on() {
+    StatRegistry& r = reg();
+    std::lock_guard<std::mutex> lk(r.mu);
+    return r.on;
+}
+
 LaunchScope::~LaunchScope() {
     StatRegistry& r = reg();
     std::lock_guard<std::mutex> lk(r.mu);
@@ -255,11 +270,28 @@ struct TreePlan {
     std::vector<LevelPlan> levels;
     std::vector<int32_t> host;               // packed device image
     struct Idx {
-        size_t seg_off, tiles, seg_tile0;        // element offsets into the image
+        size_t seg_off, tiles, seg_tile0, sweep, seg_sweep0;  // element offsets into the image
     };
     std::vector<Idx> idx;
     size_t leaf_off_at = 0;
-    int nseg_max = 0, ntiles_max = 0, nseg_large_max = 0, max_leaf = 0;
+    int nseg_max = 0, ntiles_max = 0, nsweep_max = 0, nseg_large_max = 0, max_leaf = 0;
+
+    // tiles of at most `size` positions inside one segment: {seg, begin, end, first}
+    static void tile_level(const std::vector<int32_t>& o, int size, std::vector<int32_t>& tiles,
+                           std::vector<int32_t>& first) {
+        const int nseg = (int)o.size() - 1;
+        for (int sgi = 0; sgi < nseg; ++sgi) {
+            first.push_back((int32_t)(tiles.size() / 4));
+            const int a = o[sgi], b = o[sgi + 1];
+            for (int t = a; t < b; t += size) {
+                tiles.push_back(sgi);
+                tiles.push_back(t);
+                tiles.push_back(std::min(b, t + size));
+                tiles.push_back(t == a ? 1 : 0);
+            }
+        }
+        first.push_back((int32_t)(tiles.size() / 4));
+    }
 
     void make(int64_t n_, int leaf_max) {
         n = n_;
@@ -279,43 +311,40 @@ struct TreePlan {
         host.clear();
         levels.assign(L, {});
         idx.assign(L, {});
-        nseg_max = ntiles_max = nseg_large_max = 0;
+        nseg_max = ntiles_max = nsweep_max = nseg_large_max = 0;
         for (int l = 0; l < L; ++l) {
             const auto& o = off[l];
             const int nseg = (int)o.size() - 1;
-            std::vector<int32_t> tiles, tile0;
+            std::vector<int32_t> tiles, tile0, sweep, sweep0;
+            tile_level(o, kTile, tiles, tile0);
+            tile_level(o, kSweepTile, sweep, sweep0);
             int max_m = 0;
-            for (int sgi = 0; sgi < nseg; ++sgi) {
-                tile0.push_back((int32_t)(tiles.size() / 4));
-                const int a = o[sgi], b = o[sgi + 1];
-                max_m = std::max(max_m, b - a);
-                for (int t = a; t < b; t += kTile) {
-                    tiles.push_back(sgi);
-                    tiles.push_back(t);
-                    tiles.push_back(std::min(b, t + kTile));
-                    tiles.push_back(t == a ? 1 : 0);
-                }
-            }
-            tile0.push_back((int32_t)(tiles.size() / 4));
+            for (int sgi = 0; sgi < nseg; ++sgi) max_m = std::max(max_m, o[sgi + 1] - o[sgi]);
             LevelPlan& lp = levels[l];
             lp.level = l;
             lp.n = (int)n;
             lp.nseg = nseg;
             lp.ntiles = (int)tiles.size() / 4;
+            lp.nsweep = (int)sweep.size() / 4;
             lp.max_m = max_m;
             lp.pos_bits = bits_for(max_m - 1);
             lp.small = max_m <= kSmallMax;
             nseg_max = std::max(nseg_max, nseg);
             ntiles_max = std::max(ntiles_max, lp.ntiles);
+            nsweep_max = std::max(nsweep_max, lp.nsweep);
             if (!lp.small) nseg_large_max = std::max(nseg_large_max, nseg);
             // int4 tiles need 16-byte alignment in the packed image
             while (host.size() % 4) host.push_back(0);
             idx[l].tiles = host.size();
             host.insert(host.end(), tiles.begin(), tiles.end());
+            idx[l].sweep = host.size();
+            host.insert(host.end(), sweep.begin(), sweep.end());
             idx[l].seg_off = host.size();
             host.insert(host.end(), o.begin(), o.end());
             idx[l].seg_tile0 = host.size();
             host.insert(host.end(), tile0.begin(), tile0.end());
+            idx[l].seg_sweep0 = host.size();
+            host.insert(host.end(), sweep0.begin(), sweep0.end());
         }
         leaf_off_at = host.size();
         host.insert(host.end(), off[L].begin(), off[L].end());
@@ -326,8 +355,10 @@ struct TreePlan {
     void rebase(const int32_t* dev) {
         for (int l = 0; l < L; ++l) {
             levels[l].tiles = reinterpret_cast<const int4*>(dev + idx[l].tiles);
+            levels[l].sweep = reinterpret_cast<const int4*>(dev + idx[l].sweep);
             levels[l].seg_off = dev + idx[l].seg_off;
             levels[l].seg_tile0 = dev + idx[l].seg_tile0;
+            levels[l].seg_sweep0 = dev + idx[l].seg_sweep0;
         }
     }
 };
@@ -405,7 +436,7 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.sb.ghist = ws.take<uint32_t>((size_t)nl << kRadixBits);
         b.sb.ticket = ws.take<uint32_t>(nl);
         b.sb.nseg_large = nl;
-        b.sb.partial = ws.take<double>((size_t)nt * 2 * D);
+        b.sb.partial = ws.take<double>((size_t)std::max(tp.nsweep_max, 1) * 2 * D);
         b.sb.tile_left = ws.take<int32_t>(nt);
         b.sb.status = b.status;
     }
@@ -435,6 +466,7 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.jb.cap = cap;
         b.jb.counter = ws.take<uint32_t>(4);
         b.jb.scan_tmp = ws.take<int32_t>(scan_tmp_ints(n));
+        b.jb.offers_total = ws.take<unsigned long long>(1);
     }
 }
 
@@ -452,6 +484,17 @@ void check_status(const int* dstatus, cudaStream_t s) {
     if (st & kStatusBadInput) fail(KNNG_EINVAL, "an id or offset given by the caller is out of range");
     if (st & kStatusOverflow) fail(KNNG_ECUDA, "internal offer buffer overflow");
     if (st & kStatusInternal) fail(KNNG_ECUDA, "internal consistency check failed");
+}
+
+// Offer counting for the statistics: cleared before a call, read after it.
+void offers_begin(BuildLayout& b, cudaStream_t s) {
+    if (b.jb.offers_total) cuda_check(cudaMemsetAsync(b.jb.offers_total, 0, 8, s), "offer counter clear");
+}
+void offers_end(BuildLayout& b) {
+    if (!b.jb.offers_total || !stats_on()) return;
+    unsigned long long v = 0;
+    cuda_check(cudaMemcpy(&v, b.jb.offers_total, 8, cudaMemcpyDeviceToHost), "offer counter read");
+    record_items("k5_join", (double)v);
 }
 
 // Partition of one pass into perm_a (leaves contiguous).  Returns the buffer
@@ -549,6 +592,7 @@ int knng_build_ex(const float* data, int64_t n, int D, const knng_params* p, int
         }
         if (p->tree_passes > 0) tp.rebase(b.plan_dev);
         cuda_check(cudaMemsetAsync(b.status, 0, sizeof(int), s), "status clear");
+        offers_begin(b, s);
         upload(X, s);
         build_core(X.dev, a, b, tp, s);
         launch_unpack(b.G, oi.dev, od.dev, (int64_t)nk, s);
@@ -556,6 +600,7 @@ int knng_build_ex(const float* data, int64_t n, int D, const knng_params* p, int
         download(od, s);
         cuda_check(cudaGetLastError(), "kernel launch");
         check_status(b.status, s);
+        offers_end(b);
     });
 }
 
@@ -605,6 +650,7 @@ int knng_refine(const float* data, int64_t n, int D, const knng_params* p, int32
             if (pass == 0) ws.allocate(s);
         }
         cuda_check(cudaMemsetAsync(b.status, 0, sizeof(int), s), "status clear");
+        offers_begin(b, s);
         upload(X, s);
         upload(gi, s);
         upload(gd, s);
@@ -620,6 +666,7 @@ int knng_refine(const float* data, int64_t n, int D, const knng_params* p, int32
         download(gd, s);
         cuda_check(cudaGetLastError(), "kernel launch");
         check_status(b.status, s);
+        offers_end(b);
     });
 }
 

@@ -411,10 +411,11 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
 __global__ void k5_scatter(const uint32_t* __restrict__ ptgt, const uint64_t* __restrict__ pkey,
                            const uint32_t* __restrict__ counter, int64_t cap, const int32_t* __restrict__ poff,
                            int32_t* __restrict__ pcur, uint64_t* __restrict__ grouped,
-                           const int* __restrict__ status) {
+                           const int* __restrict__ status, unsigned long long* __restrict__ offers_total) {
     // after an overflow some reserved slots were never written: group nothing
     if (*status & kStatusStop) return;
     const int64_t total = min((int64_t)*counter, cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(offers_total, (unsigned long long)total);
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t t = ptgt[q];
         const int pos = poff[t] + atomicAdd(&pcur[t], 1);
@@ -554,7 +555,7 @@ void run_join_round(const float* X, int64_t n, int D, int k, bool rev, const uin
         {
             LaunchScope ls("k5_scatter", s, 0, 0);
             k5_scatter<<<152 * 16, 256, 0, s>>>(b.ptgt, b.pkey, b.counter, b.cap, b.poff, b.pcur, b.grouped,
-                                                status);
+                                                status, b.offers_total);
         }
         {
             LaunchScope ls("k4_merge", s, n * (4.0 + 16.0 * k), 0);

@@ -39,9 +39,12 @@ struct LevelPlan {
     int max_m;        // largest segment size at this level
     int pos_bits;     // bits of a position inside a segment
     bool small;       // one CTA per segment selects and partitions
+    int nsweep;       // sweep tiles (project, sums)
     const int32_t* seg_off;    // device [nseg + 1]
-    const int4* tiles;         // device [ntiles] {seg, begin, end, first_of_seg}
-    const int32_t* seg_tile0;  // device [nseg + 1]
+    const int4* tiles;         // device [ntiles] select tiles {seg, begin, end, first_of_seg}
+    const int32_t* seg_tile0;  // device [nseg + 1] first select tile of each segment
+    const int4* sweep;         // device [nsweep] sweep tiles, same layout
+    const int32_t* seg_sweep0; // device [nseg + 1] first sweep tile of each segment
 };
 
 struct SplitBuffers {
@@ -52,12 +55,13 @@ struct SplitBuffers {
     uint32_t* ghist;      // [nseg_large][2048]: zeroed once per partition, left zero by each select
     uint32_t* ticket;     // [nseg_large]: same
     int nseg_large;       // segments of the widest level that selects across CTAs
-    double* partial;      // [ntiles_max][2][D]
+    double* partial;      // [nsweep_max][2][D]
     int32_t* tile_left;   // [ntiles_max]
     int* status;          // device status word
 };
 
-constexpr int kTile = 2048;         // positions per tile of a sweep
+constexpr int kTile = 2048;         // positions per select/partition tile
+constexpr int kSweepTile = 512;     // positions per project/sums tile
 constexpr int kSmallMax = 8192;     // segments up to this size select in one CTA
 constexpr int kRadixBits = 11;
 
@@ -89,7 +93,11 @@ struct JoinBuffers {
     int64_t cap;         // proposal capacity of one chunk
     uint32_t* counter;   // [1] proposals appended
     int32_t* scan_tmp;   // scan scratch
+    unsigned long long* offers_total;  // [1] offers grouped over the whole call (statistics)
 };
+
+// Adds `items` to the statistics of kernel `name` (when statistics are on).
+void record_items(const char* name, double items);
 
 void launch_reverse_lists(const uint64_t* G, int64_t n, int k, const JoinBuffers& b, cudaStream_t s);
 // One refinement round: reads Gold (and R when rev), writes Gnew.

@@ -105,15 +105,17 @@ __global__ void k1_init(const float* __restrict__ X, int D, const int32_t* __res
 
 // s_p = x_{perm[p]} . w_seg in the canonical order: one thread owns a point
 // and accumulates its dims in ascending order with fmaf.  Rows are staged in
-// shared memory 32 dims at a time so that global loads stay coalesced.
+// shared memory 64 dims at a time (a warp loads 32 rows' 256-byte pieces,
+// all in flight at once) so that global loads stay coalesced.
+template <bool VEC2>
 __global__ void __launch_bounds__(256) k1_project(const float* __restrict__ X, int D,
                                                   const int32_t* __restrict__ perm,
                                                   const int4* __restrict__ tiles,
                                                   const int32_t* __restrict__ seg_off,
                                                   const float* __restrict__ W, float* __restrict__ S,
                                                   SelState* __restrict__ st, const int* __restrict__ status) {
-    __shared__ float xs[256][33];
-    __shared__ float ws[32];
+    __shared__ float xs[256][65];
+    __shared__ float ws[64];
     if (*status & kStatusStop) return;  // perm may hold unwritten slots
     const int4 t = tiles[blockIdx.x];
     const int seg = t.x, begin = t.y, end = t.z;
@@ -128,16 +130,28 @@ __global__ void __launch_bounds__(256) k1_project(const float* __restrict__ X, i
         const int cnt = min(256, end - base);
         const int my_row = threadIdx.x < cnt ? perm[base + threadIdx.x] : 0;
         float acc = 0.f;
-        for (int d0 = 0; d0 < D; d0 += 32) {
-            const int dl = min(32, D - d0);
-            if (warp == 0) ws[lane] = lane < dl ? w[d0 + lane] : 0.f;
-#pragma unroll 8
+        for (int d0 = 0; d0 < D; d0 += 64) {
+            const int dl = min(64, D - d0);
+            if (threadIdx.x < 64) ws[threadIdx.x] = threadIdx.x < dl ? w[d0 + threadIdx.x] : 0.f;
+            float2 v[32];
+#pragma unroll
             for (int q = 0; q < 32; ++q) {
                 const int row = __shfl_sync(0xffffffffu, my_row, q);
-                const int pt = warp * 32 + q;
-                float v = 0.f;
-                if (pt < cnt && lane < dl) v = __ldg(X + (int64_t)row * D + d0 + lane);
-                xs[pt][lane] = v;
+                const float* src = X + (int64_t)row * D + d0 + 2 * lane;
+                v[q] = make_float2(0.f, 0.f);
+                if (warp * 32 + q < cnt) {
+                    if (VEC2) {
+                        if (2 * lane < dl) v[q] = __ldg(reinterpret_cast<const float2*>(src));
+                    } else {
+                        if (2 * lane < dl) v[q].x = __ldg(src);
+                        if (2 * lane + 1 < dl) v[q].y = __ldg(src + 1);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                xs[warp * 32 + q][2 * lane] = v[q].x;
+                xs[warp * 32 + q][2 * lane + 1] = v[q].y;
             }
             __syncthreads();
             if (threadIdx.x < cnt)
@@ -257,15 +271,20 @@ __global__ void __launch_bounds__(256) k1_select_pass(const float* __restrict__ 
 }
 
 // FP64 sums of the left and right points of each tile, 128 dims per CTA
-// (blockIdx.y).  Order: per warp ascending positions, then warps 0..7.
+// (blockIdx.y).  Warp w owns a contiguous run of the tile's positions; order:
+// per warp ascending positions, then warps 0..15, then tiles.
+constexpr int kSumsWarps = 16;
+
 template <bool VEC>
-__global__ void __launch_bounds__(256) k1_sums(const float* __restrict__ X, int D,
-                                               const int32_t* __restrict__ perm,
-                                               const int4* __restrict__ tiles, const float* __restrict__ S,
-                                               const int32_t* __restrict__ seg_off,
-                                               const uint64_t* __restrict__ thr, int pos_bits,
-                                               double* __restrict__ partial, const int* __restrict__ status) {
-    __shared__ double red[8][2][128];
+__global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restrict__ X, int D,
+                                                          const int32_t* __restrict__ perm,
+                                                          const int4* __restrict__ tiles,
+                                                          const float* __restrict__ S,
+                                                          const int32_t* __restrict__ seg_off,
+                                                          const uint64_t* __restrict__ thr, int pos_bits,
+                                                          double* __restrict__ partial,
+                                                          const int* __restrict__ status) {
+    __shared__ double red[kSumsWarps][2][128];
     if (*status & kStatusStop) return;  // perm may hold unwritten slots
     const int4 t = tiles[blockIdx.x];
     const int seg = t.x, begin = t.y, end = t.z;
@@ -273,6 +292,8 @@ __global__ void __launch_bounds__(256) k1_sums(const float* __restrict__ X, int 
     const int a = seg_off[seg];
     const uint64_t T = thr[seg];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int per = (end - begin + kSumsWarps - 1) / kSumsWarps;
+    const int w0 = begin + warp * per, w1 = min(end, w0 + per);
     // Per-lane compensated FP32 sums (Knuth's TwoSum: hi + lo carries the
     // exact sum of every addition's rounding error), combined in FP64 below.
     // GB300 issues FP64 at a small fraction of its FP32 rate, so one FP64
@@ -280,42 +301,51 @@ __global__ void __launch_bounds__(256) k1_sums(const float* __restrict__ X, int 
     // integer-valued data every add is exact and lo stays 0.
     float hL[4] = {0.f, 0.f, 0.f, 0.f}, lL[4] = {0.f, 0.f, 0.f, 0.f};
     float hR[4] = {0.f, 0.f, 0.f, 0.f}, lR[4] = {0.f, 0.f, 0.f, 0.f};
-    constexpr int U = 4;  // independent rows in flight per warp
-    for (int p0 = begin + warp; p0 < end; p0 += 8 * U) {
-        float v[U][4];
-        bool left[U];
+    constexpr int U = 8;  // independent rows in flight per warp
+    for (int c = w0; c < w1; c += 32) {
+        // ids and sides of the next 32 positions, one per lane
+        const int p = c + lane;
+        int my_row = 0, my_left = 0;
+        if (p < w1) {
+            my_row = perm[p];
+            my_left = sel_key(S[p], p - a, pos_bits) < T;
+        }
+        const int cnt = min(32, w1 - c);
+        for (int q0 = 0; q0 < cnt; q0 += U) {
+            float v[U][4];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int p = p0 + 8 * u;
-            left[u] = false;
+            for (int u = 0; u < U; ++u) {
+                const int row = __shfl_sync(0xffffffffu, my_row, (q0 + u) & 31);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[u][j] = 0.f;
-            if (p < end) {
-                left[u] = sel_key(S[p], p - a, pos_bits) < T;
-                const float* x = X + (int64_t)perm[p] * D + dbase;
-                if (VEC) {
-                    if (dbase + lane * 4 < D) {
-                        const float4 f = __ldg(reinterpret_cast<const float4*>(x) + lane);
-                        v[u][0] = f.x; v[u][1] = f.y; v[u][2] = f.z; v[u][3] = f.w;
+                for (int j = 0; j < 4; ++j) v[u][j] = 0.f;
+                if (q0 + u < cnt) {
+                    const float* x = X + (int64_t)row * D + dbase;
+                    if (VEC) {
+                        if (dbase + lane * 4 < D) {
+                            const float4 f = __ldg(reinterpret_cast<const float4*>(x) + lane);
+                            v[u][0] = f.x; v[u][1] = f.y; v[u][2] = f.z; v[u][3] = f.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            v[u][j] = (dbase + lane + 32 * j < D) ? __ldg(x + lane + 32 * j) : 0.f;
                     }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) v[u][j] = (dbase + lane + 32 * j < D) ? __ldg(x + lane + 32 * j) : 0.f;
                 }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (p0 + 8 * u >= end) break;
-            float* h = left[u] ? hL : hR;
-            float* l = left[u] ? lL : lR;
+            for (int u = 0; u < U; ++u) {
+                const int left = __shfl_sync(0xffffffffu, my_left, (q0 + u) & 31);
+                if (q0 + u >= cnt) break;
+                float* h = left ? hL : hR;
+                float* l = left ? lL : lR;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float s = __fadd_rn(h[j], v[u][j]);
-                const float bp = __fsub_rn(s, h[j]);
-                const float err = __fadd_rn(__fsub_rn(h[j], __fsub_rn(s, bp)), __fsub_rn(v[u][j], bp));
-                h[j] = s;
-                l[j] = __fadd_rn(l[j], err);
+                for (int j = 0; j < 4; ++j) {
+                    const float s = __fadd_rn(h[j], v[u][j]);
+                    const float bp = __fsub_rn(s, h[j]);
+                    const float err = __fadd_rn(__fsub_rn(h[j], __fsub_rn(s, bp)), __fsub_rn(v[u][j], bp));
+                    h[j] = s;
+                    l[j] = __fadd_rn(l[j], err);
+                }
             }
         }
     }
@@ -329,7 +359,7 @@ __global__ void __launch_bounds__(256) k1_sums(const float* __restrict__ X, int 
     if (threadIdx.x < 128 && dbase + threadIdx.x < D) {
         double sL = 0.0, sR = 0.0;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
+        for (int w = 0; w < kSumsWarps; ++w) {
             sL += red[w][0][threadIdx.x];
             sR += red[w][1][threadIdx.x];
         }
@@ -348,6 +378,7 @@ __global__ void k1_centroids(const double* __restrict__ partial, const int32_t* 
     const int t0 = seg_tile0[seg], t1 = seg_tile0[seg + 1];
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
         double sL = 0.0, sR = 0.0;
+#pragma unroll 4
         for (int t = t0; t < t1; ++t) {
             sL += partial[((int64_t)t * 2 + 0) * D + d];
             sR += partial[((int64_t)t * 2 + 1) * D + d];
@@ -411,6 +442,7 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
     // algorithmic bytes: a sweep reads every row once plus its id and key
     const double n = lp.n, rows = n * D * 4.0;
     const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    const bool vec2 = (D % 2 == 0) && ((reinterpret_cast<uintptr_t>(X) & 7) == 0);
     const int dchunks = (D + 127) / 128;
     {
         LaunchScope ls("k1_init", s, (double)lp.nseg * 3 * D * 4, 0);
@@ -420,15 +452,22 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
         const bool last = it == iters;
         {
             LaunchScope ls("k1_project", s, rows + n * 8, 2.0 * n * D);
-            k1_project<<<lp.ntiles, 256, 0, s>>>(X, D, perm_in, lp.tiles, lp.seg_off, b.W, b.S,
-                                                 lp.small ? nullptr : b.st, b.status);
+            SelState* st = lp.small ? nullptr : b.st;
+            if (vec2)
+                k1_project<true><<<lp.nsweep, 256, 0, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S, st,
+                                                           b.status);
+            else
+                k1_project<false><<<lp.nsweep, 256, 0, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S, st,
+                                                            b.status);
         }
         if (lp.small) {
             const size_t smem = (size_t)lp.max_m * sizeof(uint64_t);
+            // one thread per point up to 1024, at least 4 warps
+            const int nt = std::min(1024, std::max(128, (lp.max_m + 31) & ~31));
             LaunchScope ls("k1_select_small", s, n * 4 + (last ? n * 8 : 0), 0);
             cudaFuncSetAttribute(k1_select_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k1_select_small<<<lp.nseg, 1024, smem, s>>>(b.S, lp.seg_off, lp.pos_bits, b.thr, perm_in,
-                                                        last ? perm_out : nullptr, b.status);
+            k1_select_small<<<lp.nseg, nt, smem, s>>>(b.S, lp.seg_off, lp.pos_bits, b.thr, perm_in,
+                                                      last ? perm_out : nullptr, b.status);
             if (last) break;
         } else {
             const int TB = 32 + lp.pos_bits;
@@ -453,11 +492,11 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
             LaunchScope ls("k1_sums", s, rows + n * 8, n * D);
             dim3 grid(lp.ntiles, dchunks);
             if (vec)
-                k1_sums<true><<<grid, 256, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr, lp.pos_bits,
-                                                   b.partial, b.status);
+                k1_sums<true><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr,
+                                                               lp.pos_bits, b.partial, b.status);
             else
-                k1_sums<false><<<grid, 256, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr, lp.pos_bits,
-                                                    b.partial, b.status);
+                k1_sums<false><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr,
+                                                                lp.pos_bits, b.partial, b.status);
         }
         {
             LaunchScope ls("k1_centroids", s, (double)lp.ntiles * 2 * D * 8 + (double)lp.nseg * D * 4, 0);
