@@ -423,20 +423,70 @@ __global__ void k5_scatter(const uint32_t* __restrict__ ptgt, const uint64_t* __
     }
 }
 
+// An offer of `key` to a node whose sorted list is row[0..k) can change the
+// list only if it beats the k-th entry and is not one of the entries already
+// (an id always comes with the same canonical distance, hence the same key).
+__device__ __forceinline__ bool offer_useful(uint64_t key, const uint64_t* row, int k) {
+    if (!(key < row[k - 1])) return false;
+    int lo = 0, len = k;
+    while (len > 0) {
+        const int half = len >> 1;
+        if (row[lo + half] < key) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return row[lo] != key;
+}
+
+// One warp per node: the node's current list sits in shared memory; every
+// lane drops the offers that cannot change it, and only the rest go through
+// the warp selection.
 template <int NO>
 __global__ void __launch_bounds__(256) k4_merge(uint64_t* __restrict__ Gnew, const uint64_t* __restrict__ grouped,
                                                 const int32_t* __restrict__ poff, int64_t n, int k,
                                                 const int* __restrict__ status) {
+    __shared__ uint64_t rows[8][32 * NO];
     const int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (u >= n || (*status & kStatusStop)) return;
     const int beg = poff[u], end = poff[u + 1];
     if (beg == end) return;
     const int lane = threadIdx.x & 31;
+    uint64_t* srow = rows[threadIdx.x >> 5];
     uint64_t* row = Gnew + u * k;
     uint64_t run[NO];
 #pragma unroll
-    for (int o = 0; o < NO; ++o) run[o] = lane + 32 * o < k ? row[lane + 32 * o] : kEmptyKey;
-    warp_merge_list<NO>(grouped, beg, end, k, run);
+    for (int o = 0; o < NO; ++o) {
+        run[o] = lane + 32 * o < k ? row[lane + 32 * o] : kEmptyKey;
+        srow[lane + 32 * o] = run[o];
+    }
+    __syncwarp();
+    constexpr int NC = 4;
+    bool changed = false;
+    for (int c = beg; c < end; c += 32 * NC) {
+        uint64_t a[NC + NO];
+        bool any = false;
+#pragma unroll
+        for (int s = 0; s < NC; ++s) {
+            const int e = c + lane + 32 * s;
+            a[s] = (e < end) ? grouped[e] : kEmptyKey;
+            if (a[s] != kEmptyKey && !offer_useful(a[s], srow, k)) a[s] = kEmptyKey;
+            any |= a[s] != kEmptyKey;
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) a[NC + o] = run[o];
+        sort_regs<NC + NO>(a);
+        warp_select_unique<NC + NO, NO>(a, k, run);
+        __syncwarp();
+#pragma unroll
+        for (int o = 0; o < NO; ++o) srow[lane + 32 * o] = run[o];
+        __syncwarp();
+        changed = true;
+    }
+    if (!changed) return;
 #pragma unroll
     for (int o = 0; o < NO; ++o)
         if (lane + 32 * o < k) row[lane + 32 * o] = run[o];
