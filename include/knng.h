@@ -60,7 +60,12 @@ enum knng_join_mode {
 };
 
 enum knng_precision {
-    KNNG_FP32 = 0          /* canonical FP32 everywhere */
+    KNNG_FP32 = 0,         /* canonical FP32 everywhere */
+    KNNG_BF16 = 1,         /* leaf Gram on tensor cores from a BF16 copy, certified FP32 re-rank */
+    KNNG_FP16 = 2          /* the same from an FP16 copy */
+    /* With BF16/FP16 the graph is identical to the FP32 one: every row whose
+     * low-precision selection cannot be certified by the error bound is
+     * recomputed in FP32.  Leaves above 128 points use the FP32 leaf kernel. */
 };
 
 typedef struct knng_params {

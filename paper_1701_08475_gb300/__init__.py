@@ -7,6 +7,8 @@ the name of its C entry point, marshals tensors to plain pointers and sizes,
 and calls the CUDA library.  No step of the method runs in Python.
 """
 from ._lib import (  # noqa: F401
+    KNNG_BF16,
+    KNNG_FP16,
     KNNG_FP32,
     KNNG_JOIN_FWD,
     KNNG_JOIN_FWD_REV,

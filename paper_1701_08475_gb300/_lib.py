@@ -19,6 +19,8 @@ _lib = None
 KNNG_JOIN_FWD = 0
 KNNG_JOIN_FWD_REV = 1
 KNNG_FP32 = 0
+KNNG_BF16 = 1
+KNNG_FP16 = 2
 
 _CODES = {-1: "KNNG_EINVAL", -2: "KNNG_ENOMEM", -3: "KNNG_ECUDA", -4: "KNNG_ETIMEOUT"}
 

@@ -392,7 +392,8 @@ void validate_params(const knng_params* p, int64_t n) {
         fail(KNNG_EINVAL, "leaf_max = %d out of range [2(k+1) = %d, 256]", p->leaf_max, 2 * (p->k + 1));
     if (p->join_mode != KNNG_JOIN_FWD && p->join_mode != KNNG_JOIN_FWD_REV)
         fail(KNNG_EINVAL, "join_mode = %d unknown", p->join_mode);
-    if (p->precision != KNNG_FP32) fail(KNNG_EINVAL, "precision = %d unsupported", p->precision);
+    if (p->precision != KNNG_FP32 && p->precision != KNNG_BF16 && p->precision != KNNG_FP16)
+        fail(KNNG_EINVAL, "precision = %d unknown", p->precision);
     if (p->twomeans_iters < 0 || p->twomeans_iters > 64)
         fail(KNNG_EINVAL, "twomeans_iters = %d out of range [0, 64]", p->twomeans_iters);
     const int m = p->join_mode == KNNG_JOIN_FWD_REV ? 2 * p->k : p->k;
@@ -414,15 +415,29 @@ struct BuildLayout {
     JoinBuffers jb{};
     int32_t *perm_a = nullptr, *perm_b = nullptr, *plan_dev = nullptr;
     uint64_t *G = nullptr, *G2 = nullptr;
-    int* status = nullptr;
+    int* status = nullptr;  // [0] status bits, [1] rows re-ranked exactly after a failed certificate
     int64_t nodes_per_chunk = 0;
+    // low-precision leaf stage
+    uint16_t* Xl = nullptr;
+    float *lp_nrm = nullptr, *lp_err = nullptr;
+    int* notexact = nullptr;
 };
+
+bool lp_leaf(const Args& a, const TreePlan& tp) {
+    return a.p.precision != KNNG_FP32 && a.p.tree_passes > 0 && tp.max_leaf <= 128;
+}
 
 void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, bool tree, bool join) {
     const int64_t n = a.n;
     const int k = a.p.k, D = a.D;
     b.status = ws.take<int>(4);
     b.G = ws.take<uint64_t>((size_t)n * k);
+    if (tree && lp_leaf(a, tp)) {
+        b.Xl = ws.take<uint16_t>((size_t)n * lp_dim(D));
+        b.lp_nrm = ws.take<float>(n);
+        b.lp_err = ws.take<float>(n);
+        b.notexact = ws.take<int>(4);
+    }
     if (tree) {
         b.perm_a = ws.take<int32_t>(n);
         b.perm_b = ws.take<int32_t>(n);
@@ -475,11 +490,14 @@ int grid_1d(int64_t count) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
 }
 
-void check_status(const int* dstatus, cudaStream_t s) {
-    int st = 0;
-    cuda_check(cudaMemcpyAsync(&st, dstatus, sizeof(int), cudaMemcpyDeviceToHost, s), "status read");
+void check_status(const int* dstatus, cudaStream_t s, const char* fallback_kernel = nullptr) {
+    int hs[2] = {0, 0};
+    cuda_check(cudaMemcpyAsync(hs, dstatus, sizeof hs, cudaMemcpyDeviceToHost, s), "status read");
     cuda_check(cudaStreamSynchronize(s), "stream synchronize");
     reg().flush();
+    if (fallback_kernel) record_items(fallback_kernel, (double)hs[1]);
+    const int st = hs[0];
+    if (st & kStatusTimeout) fail(KNNG_ETIMEOUT, "a bounded device wait ran out");
     if (st & kStatusNonFinite) fail(KNNG_EINVAL, "data holds a non-finite value");
     if (st & kStatusBadInput) fail(KNNG_EINVAL, "an id or offset given by the caller is out of range");
     if (st & kStatusOverflow) fail(KNNG_ECUDA, "internal offer buffer overflow");
@@ -526,10 +544,22 @@ void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& t
     if (a.p.tree_passes > 0)
         cuda_check(cudaMemcpyAsync(b.plan_dev, tp.host.data(), tp.host.size() * 4, cudaMemcpyHostToDevice, s),
                    "plan upload");
+    const bool lp = lp_leaf(a, tp);
+    const bool bf16 = a.p.precision == KNNG_BF16;
+    // re-ranked candidates per row: k plus a margin, at most 63
+    const int kp = std::min(63, k + std::max(k / 2, 8));
+    if (lp) cuda_check(cudaMemsetAsync(b.notexact, 0, sizeof(int), s), "flag clear");
     for (int pass = 0; pass < a.p.tree_passes; ++pass) {
         int32_t* perm = run_partition(X, a, tp, b, pass, s);
-        launch_leaf_fp32(X, a.D, perm, b.plan_dev + tp.leaf_off_at, (int)(tp.off[tp.L].size() - 1), tp.max_leaf, k,
-                         b.G, b.status, s);
+        const int32_t* leaf_off = b.plan_dev + tp.leaf_off_at;
+        const int nleaf = (int)(tp.off[tp.L].size() - 1);
+        bool done = false;
+        if (lp) {
+            launch_quantize(X, n, a.D, perm, bf16, b.Xl, b.lp_nrm, b.lp_err, b.notexact, s);
+            done = launch_leaf_tc(b.Xl, n, X, a.D, perm, leaf_off, nleaf, tp.max_leaf, b.lp_nrm, b.lp_err, k, kp,
+                                  bf16, b.G, b.status, b.notexact, s);
+        }
+        if (!done) launch_leaf_fp32(X, a.D, perm, leaf_off, nleaf, tp.max_leaf, k, b.G, b.status, s);
     }
     for (int r = 0; r < a.p.refine_rounds; ++r) {
         run_join_round(X, n, a.D, k, a.p.join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, b.jb, b.nodes_per_chunk,
@@ -591,7 +621,7 @@ int knng_build_ex(const float* data, int64_t n, int D, const knng_params* p, int
             if (pass == 0) ws.allocate(s);
         }
         if (p->tree_passes > 0) tp.rebase(b.plan_dev);
-        cuda_check(cudaMemsetAsync(b.status, 0, sizeof(int), s), "status clear");
+        cuda_check(cudaMemsetAsync(b.status, 0, 4 * sizeof(int), s), "status clear");
         offers_begin(b, s);
         upload(X, s);
         build_core(X.dev, a, b, tp, s);
@@ -599,7 +629,8 @@ int knng_build_ex(const float* data, int64_t n, int D, const knng_params* p, int
         download(oi, s);
         download(od, s);
         cuda_check(cudaGetLastError(), "kernel launch");
-        check_status(b.status, s);
+        check_status(b.status, s,
+                     lp_leaf(a, tp) ? (p->precision == KNNG_BF16 ? "k2_leaf_bf16" : "k2_leaf_fp16") : nullptr);
         offers_end(b);
     });
 }
@@ -649,7 +680,7 @@ int knng_refine(const float* data, int64_t n, int D, const knng_params* p, int32
             carve(ws, b, a, tp, false, p->refine_rounds > 0);
             if (pass == 0) ws.allocate(s);
         }
-        cuda_check(cudaMemsetAsync(b.status, 0, sizeof(int), s), "status clear");
+        cuda_check(cudaMemsetAsync(b.status, 0, 4 * sizeof(int), s), "status clear");
         offers_begin(b, s);
         upload(X, s);
         upload(gi, s);
@@ -701,7 +732,7 @@ int knng_partition(const float* data, int64_t n, int D, int leaf_max, int twomea
             if (ps == 0) ws.allocate(s);
         }
         tp.rebase(b.plan_dev);
-        cuda_check(cudaMemsetAsync(b.status, 0, sizeof(int), s), "status clear");
+        cuda_check(cudaMemsetAsync(b.status, 0, 4 * sizeof(int), s), "status clear");
         upload(X, s);
         launch_check_finite(X.dev, n * (int64_t)D, b.status, s);
         cuda_check(cudaMemcpyAsync(b.plan_dev, tp.host.data(), tp.host.size() * 4, cudaMemcpyHostToDevice, s),
@@ -762,7 +793,7 @@ int knng_leaf_update(const float* data, int64_t n, int D, int k, const int32_t* 
             status = ws.take<int>(4);
             if (ps == 0) ws.allocate(s);
         }
-        cuda_check(cudaMemsetAsync(status, 0, sizeof(int), s), "status clear");
+        cuda_check(cudaMemsetAsync(status, 0, 4 * sizeof(int), s), "status clear");
         upload(X, s);
         upload(pm, s);
         upload(gi, s);
@@ -807,7 +838,7 @@ int knng_exact(const float* data, int64_t n, int D, int k, const int32_t* sample
             status = ws.take<int>(4);
             if (ps == 0) ws.allocate(s);
         }
-        cuda_check(cudaMemsetAsync(status, 0, sizeof(int), s), "status clear");
+        cuda_check(cudaMemsetAsync(status, 0, 4 * sizeof(int), s), "status clear");
         upload(X, s);
         if (sample) upload(smp, s);
         launch_check_finite(X.dev, n * (int64_t)D, status, s);

@@ -120,7 +120,8 @@ enum DevStatus : int {
     kStatusOverflow = 2,    // an internal buffer would overflow: later stages skip
     kStatusBadInput = 4,    // an id or offset given by the caller is out of range
     kStatusInternal = 8,    // a consistency check failed: the write was skipped
+    kStatusTimeout = 16,    // a bounded device wait ran out
 };
-constexpr int kStatusStop = kStatusOverflow | kStatusBadInput | kStatusInternal;
+constexpr int kStatusStop = kStatusOverflow | kStatusBadInput | kStatusInternal | kStatusTimeout;
 
 }  // namespace knng

@@ -77,6 +77,20 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
 void launch_leaf_fp32(const float* X, int D, const int32_t* perm, const int32_t* leaf_off,
                       int nleaf, int max_leaf, int k, uint64_t* G, const int* status, cudaStream_t s);
 
+// ---------------------------------------------------------------- low precision (K0, K2 tensor cores, K3)
+int lp_dim(int D);  // D rounded up to the 64-element rows of the swizzled tiles
+// Leaf-order 16-bit copy of X (perm: leaf order; NULL = identity), squared
+// norms and quantisation errors; *notexact |= 1 when the 16-bit arithmetic is
+// not exact for this input.
+void launch_quantize(const float* X, int64_t n, int D, const int32_t* perm, bool bf16, uint16_t* Xq, float* nrm,
+                     float* qerr, int* notexact, cudaStream_t s);
+// Leaf stage on tcgen05 from the leaf-order copy; false when it cannot run
+// (leaf above 128 points, no tensor-map encoder) and nothing was launched.
+// status[1] counts the rows that fell back to exact recomputation.
+bool launch_leaf_tc(const uint16_t* Xl, int64_t n, const float* X, int D, const int32_t* perm,
+                    const int32_t* leaf_off, int nleaf, int max_leaf, const float* nrm, const float* qerr, int k,
+                    int kp, bool bf16, uint64_t* G, int* status, const int* notexact, cudaStream_t s);
+
 // ---------------------------------------------------------------- refinement (K4-K6)
 struct JoinBuffers {
     int32_t* deg;        // [n + 1]

@@ -1,0 +1,483 @@
+// leaf_tc.cu -- the low-precision leaf stage on tcgen05 tensor cores.
+//
+//   K0 quantize   a BF16 or FP16 copy x^ of every point in leaf order, its
+//                 squared norm ||x^||^2 (FP32) and its quantisation error
+//                 e = ||x - x^|| (rounded up), plus one flag saying whether
+//                 the low-precision arithmetic is exact for this input
+//   K2 leaf       per leaf (m <= 128 points): the Gram matrix x^_i . x^_j on
+//                 the tensor cores (TMA loads of the leaf's rows into 128-byte
+//                 swizzled shared memory, tcgen05.mma with the FP32
+//                 accumulator in tensor memory), approximate distances
+//                 d^ = ||x^_i||^2 + ||x^_j||^2 - 2 x^_i . x^_j, and per row:
+//   K3 re-rank    the k' best approximate candidates get their canonical FP32
+//                 distance; the row is certified when no excluded candidate
+//                 can beat the row's k-th exact entry by the error bound below,
+//                 else it is recomputed exactly over the whole leaf.
+//
+// With the certificate the graph is identical to the FP32 path's.  When all
+// values are integers that the 16-bit type holds exactly and every norm is
+// below 2^23, products and sums are exact integers in FP32, d^ is the
+// canonical distance itself and no re-rank is needed.
+//
+// Error bound of d^ against the exact distance d of the FP32 points (per row
+// i, against every candidate j of the leaf):
+//   |sqrt(d) - sqrt(d~)| <= e_i + e_j            (d~: exact distance of x^)
+//   |d^ - d~| <= c_D (||x^_i|| + ||x^_j||)^2 + 2^-23 |d^|
+// with c_D = (16 D + 8) 2^-24: four times the textbook bound for the FP32
+// sums (Higham, Ch. 3) because the tensor cores' summation order and internal
+// rounding are not specified.  A candidate excluded with approximate value
+// a >= a* can only beat the k-th exact entry t if
+//   (sqrt(max(0, a* - eps)) - e_i - e_max)^2 <= t.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace knng {
+
+namespace {
+
+// ---------------------------------------------------------------- K0
+template <bool BF16>
+__device__ __forceinline__ uint16_t quantize_bits(float x, float* back) {
+    if (BF16) {
+        const __nv_bfloat16 q = __float2bfloat16_rn(x);
+        *back = __bfloat162float(q);
+        return __bfloat16_as_ushort(q);
+    } else {
+        const __half q = __float2half_rn(x);
+        *back = __half2float(q);
+        return __half_as_ushort(q);
+    }
+}
+
+// One warp per output row p (= leaf-order position): the row of point
+// perm[p], dims padded with zeros to Dp.  Flags in *notexact: 1 = some value
+// is not an integer the 16-bit type holds exactly, or some squared norm is
+// 2^23 or more; 2 = some value is negative; 4 = some squared norm is 2^22 or
+// more.  The 16-bit arithmetic is exact unless flag 1 is set or flags 2 and 4
+// both are: then every norm, Gram entry and distance (and every partial sum
+// of them) is an integer below 2^24.
+template <bool BF16>
+__global__ void __launch_bounds__(256) k0_quantize(const float* __restrict__ X, int64_t n, int D, int Dp,
+                                                   const int32_t* __restrict__ perm, uint16_t* __restrict__ Xq,
+                                                   float* __restrict__ nrm, float* __restrict__ qerr,
+                                                   int* __restrict__ notexact) {
+    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (p >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = perm ? perm[p] : p;
+    const float lim = BF16 ? 256.f : 2048.f;
+    float sq = 0.f;
+    double e2 = 0.0;
+    bool exact = true, neg = false;
+    for (int d = lane; d < Dp; d += 32) {
+        const float x = d < D ? X[i * D + d] : 0.f;
+        float b;
+        Xq[p * Dp + d] = quantize_bits<BF16>(x, &b);
+        sq = __fmaf_rn(b, b, sq);
+        const double t = (double)x - (double)b;
+        e2 += t * t;
+        exact &= (x == rintf(x)) && fabsf(x) <= lim;
+        neg |= x < 0.f;
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+        sq += __shfl_xor_sync(0xffffffffu, sq, m);
+        e2 += __shfl_xor_sync(0xffffffffu, e2, m);
+    }
+    exact = __all_sync(0xffffffffu, exact);
+    neg = __any_sync(0xffffffffu, neg);
+    if (lane == 0) {
+        nrm[p] = sq;
+        // rounded up: the bound must not shrink
+        qerr[p] = e2 > 0.0 ? __double2float_ru(sqrt(e2) * (1.0 + 1e-12)) : 0.f;
+        const int f = ((!exact || sq >= 8388608.f) ? 1 : 0) | (neg ? 2 : 0) | (sq >= 4194304.f ? 4 : 0);
+        if (f) atomicOr(notexact, f);
+    }
+}
+
+__device__ __forceinline__ bool lp_exact(int f) { return (f & 1) == 0 && !((f & 2) && (f & 4)); }
+
+// ---------------------------------------------------------------- K2/K3
+constexpr int kTcRows = 128;             // M = N = 128 tile: leaves up to 128 points
+constexpr int kTcK = 64;                 // 16-bit elements per 128-byte swizzled row
+constexpr int kStageBytes = kTcRows * kTcK * 2;
+constexpr int kDtStride = kTcRows + 1;
+constexpr int kTcThreads = 128;
+
+struct TcSmem {
+    int stages;
+    size_t stage_off, dt_off, bar_off, misc_off, total;
+};
+
+__host__ __device__ inline TcSmem tc_smem(int Dp) {
+    TcSmem L;
+    const int nk = Dp / kTcK;
+    L.stages = nk < 4 ? nk : 4;
+    L.stage_off = 0;
+    L.dt_off = (size_t)L.stages * kStageBytes;
+    L.bar_off = L.dt_off + (size_t)kTcRows * kDtStride * 4;
+    L.misc_off = L.bar_off + (size_t)(2 * L.stages + 1) * 8;
+    // misc: tmem address, abort flag, ids[128], nrm[128], err[128], two maxima
+    L.total = L.misc_off + 16 + 3 * kTcRows * 4 + 16;
+    return L;
+}
+
+// canonical FP32 squared distance between rows a and b of X
+__device__ __forceinline__ float canon_dist(const float* __restrict__ xa, const float* __restrict__ xb, int D,
+                                            bool vec) {
+    float acc = 0.f;
+    if (vec) {
+        for (int d = 0; d < D; d += 4) {
+            const float4 u = __ldg(reinterpret_cast<const float4*>(xa + d));
+            const float4 v = __ldg(reinterpret_cast<const float4*>(xb + d));
+            float t = __fsub_rn(u.x, v.x);
+            acc = __fmaf_rn(t, t, acc);
+            t = __fsub_rn(u.y, v.y);
+            acc = __fmaf_rn(t, t, acc);
+            t = __fsub_rn(u.z, v.z);
+            acc = __fmaf_rn(t, t, acc);
+            t = __fsub_rn(u.w, v.w);
+            acc = __fmaf_rn(t, t, acc);
+        }
+    } else {
+        for (int d = 0; d < D; ++d) {
+            const float t = __fsub_rn(__ldg(xa + d), __ldg(xb + d));
+            acc = __fmaf_rn(t, t, acc);
+        }
+    }
+    return acc;
+}
+
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)v, src);
+    const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(v >> 32), src);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// entry r of a list held lane-major in NO slots (r < 32 * NO)
+template <int NO>
+__device__ __forceinline__ uint64_t list_at(const uint64_t (&v)[NO], int r) {
+    uint64_t mine = v[0];
+#pragma unroll
+    for (int o = 1; o < NO; ++o)
+        if (o == (r >> 5)) mine = v[o];
+    return shfl64(mine, r & 31);
+}
+
+template <bool BF16, int NSG>
+__global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constant__ CUtensorMap tmap, int Dp,
+                                                           const float* __restrict__ X, int D,
+                                                           const int32_t* __restrict__ perm,
+                                                           const int32_t* __restrict__ leaf_off,
+                                                           const float* __restrict__ nrm,
+                                                           const float* __restrict__ qerr, int k, int kp,
+                                                           uint64_t* __restrict__ G, int* __restrict__ status,
+                                                           const int* __restrict__ notexact) {
+    extern __shared__ uint8_t smem_raw[];
+    if (*status & kStatusStop) return;  // whole CTA, before any barrier or tensor memory
+    const TcSmem L = tc_smem(Dp);
+    uint8_t* base = smem_raw + ((1024 - (tc::smem_addr(smem_raw) & 1023)) & 1023);
+    float* dt = reinterpret_cast<float*>(base + L.dt_off);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bar_off);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.misc_off);
+    int* abort_flag = reinterpret_cast<int*>(base + L.misc_off + 4);
+    int32_t* sid = reinterpret_cast<int32_t*>(base + L.misc_off + 16);
+    float* snrm = reinterpret_cast<float*>(sid + kTcRows);
+    float* serr = snrm + kTcRows;
+    float* smax = serr + kTcRows;  // [0] max ||x^||, [1] max e
+
+    const int S = L.stages, nk = Dp / kTcK;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int leaf = blockIdx.x;
+    const int a = leaf_off[leaf];
+    const int m = leaf_off[leaf + 1] - a;
+    const uint32_t full0 = tc::smem_addr(bars), empty0 = full0 + 8 * S, done = full0 + 16 * S;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(full0 + 8 * s, 1);
+            tc::mbar_init(empty0 + 8 * s, 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::mbar_fence_init();
+        *abort_flag = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_addr(tmem_slot), kTcRows);
+        tc::tmem_relinquish();
+    }
+    for (int r = tid; r < kTcRows; r += kTcThreads) {
+        const bool in = r < m;
+        sid[r] = in ? perm[a + r] : 0;
+        snrm[r] = in ? nrm[a + r] : 0.f;
+        serr[r] = in ? qerr[a + r] : 0.f;
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    // ---- producer + MMA issue (one thread)
+    if (tid == 0) {
+        bool ok = true;
+        const uint32_t idesc = tc::idesc_f16(BF16, kTcRows, kTcRows);
+        int issued = 0, consumed = 0;
+        for (; issued < S && issued < nk; ++issued) {
+            const uint32_t fb = full0 + 8 * issued;
+            tc::mbar_expect_tx(fb, kStageBytes);
+            tc::tma_load_2d(tc::smem_addr(base + (size_t)issued * kStageBytes), &tmap, issued * kTcK, a, fb);
+        }
+        for (int c = 0; c < nk; ++c) {
+            const int s = c % S;
+            if (!tc::mbar_wait(full0 + 8 * s, (uint32_t)((c / S) & 1), status)) {
+                ok = false;
+                break;
+            }
+            consumed = c + 1;
+            const uint64_t d0 = tc::sdesc_k128(tc::smem_addr(base + (size_t)s * kStageBytes));
+#pragma unroll
+            for (int kk = 0; kk < kTcK / 16; ++kk)  // K = 16 per instruction: 32 bytes along the row
+                tc::mma_f16(tmem, d0 + 2 * kk, d0 + 2 * kk, idesc, (c | kk) != 0);
+            tc::mma_commit(empty0 + 8 * s);
+            if (c + S < nk) {
+                if (!tc::mbar_wait(empty0 + 8 * s, (uint32_t)((c / S) & 1), status)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t fb = full0 + 8 * s;
+                tc::mbar_expect_tx(fb, kStageBytes);
+                tc::tma_load_2d(tc::smem_addr(base + (size_t)s * kStageBytes), &tmap, (c + S) * kTcK, a, fb);
+                ++issued;
+            }
+        }
+        tc::mma_commit(done);
+        if (!ok) {
+            *abort_flag = 1;
+            // let the loads still in flight land before the CTA can exit
+            for (int c = consumed; c < issued; ++c) tc::mbar_wait(full0 + 8 * (c % S), (uint32_t)((c / S) & 1), status);
+        }
+    }
+    __syncwarp();
+    const int mma_ok = tc::mbar_wait(done, 0, status) ? 1 : 0;
+    // uniform over the CTA: the tensor-memory loads below are warp-collective
+    const bool ok = __syncthreads_and(mma_ok) && *abort_flag == 0;
+    tc::fence_after_sync();
+    if (ok) {
+        // ---- epilogue: row = TMEM lane = thread
+        const int row = warp * 32 + lane;
+#pragma unroll 1
+        for (int cc = 0; cc < kTcRows / 32; ++cc) {
+            float v[32];
+            tc::tmem_ld_32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int col = cc * 32 + j;
+                dt[row * kDtStride + col] = __fsub_rn(__fadd_rn(snrm[row], snrm[col]), __fmul_rn(2.f, v[j]));
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTcRows);
+    if (!ok) return;
+
+    // leaf maxima of ||x^|| and e for the certificate
+    if (warp == 0) {
+        float mn = 0.f, me = 0.f;
+        for (int r = lane; r < m; r += 32) {
+            mn = fmaxf(mn, sqrtf(snrm[r]));
+            me = fmaxf(me, serr[r]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn = fmaxf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            me = fmaxf(me, __shfl_xor_sync(0xffffffffu, me, o));
+        }
+        if (lane == 0) {
+            smax[0] = mn * (1.f + 1e-6f);
+            smax[1] = me;
+        }
+    }
+    __syncthreads();
+
+    const bool exact = lp_exact(*notexact);
+    const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    constexpr int NC = kTcRows / 32;
+    for (int r = warp; r < m; r += kTcThreads / 32) {
+        const int gi = sid[r];
+        uint64_t* grow = G + (int64_t)gi * k;
+        uint64_t old[NSG];
+#pragma unroll
+        for (int s = 0; s < NSG; ++s) old[s] = lane + 32 * s < k ? grow[lane + 32 * s] : kEmptyKey;
+        uint64_t res[NSG];
+        bool done_row = false;
+        if (exact) {
+            // d^ is the canonical distance itself
+            uint64_t cand[NC + NSG];
+#pragma unroll
+            for (int s = 0; s < NC; ++s) {
+                const int c = lane + 32 * s;
+                cand[s] = (c < m && c != r) ? make_key(__fadd_rn(dt[r * kDtStride + c], 0.f), (uint32_t)sid[c])
+                                            : kEmptyKey;
+            }
+#pragma unroll
+            for (int s = 0; s < NSG; ++s) cand[NC + s] = old[s];
+            sort_regs<NC + NSG>(cand);
+            warp_select_unique<NC + NSG, NSG>(cand, k, res);
+            done_row = true;
+        } else if (m - 1 > 0) {
+            // the kp + 1 best approximate candidates (keys unique: distinct ids)
+            uint64_t apx[NC];
+#pragma unroll
+            for (int s = 0; s < NC; ++s) {
+                const int c = lane + 32 * s;
+                apx[s] = (c < m && c != r) ? make_key(__fadd_rn(dt[r * kDtStride + c], 0.f), (uint32_t)sid[c])
+                                           : kEmptyKey;
+            }
+            sort_regs<NC>(apx);
+            uint64_t top[2];
+            const int want = kp + 1 < m - 1 ? kp + 1 : m - 1;
+            warp_select_unique<NC, 2>(apx, want, top);
+            const int nre = want < kp ? want : kp;  // re-ranked candidates
+            // canonical distances of the re-ranked ones; excluded: from rank kp on
+            uint64_t ex[2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int j = lane + 32 * s;
+                ex[s] = kEmptyKey;
+                if (j < nre) {
+                    const uint32_t cid = key_id(top[s]);
+                    const float d = canon_dist(X + (int64_t)gi * D, X + (int64_t)cid * D, D, vec);
+                    ex[s] = make_key(d, cid);
+                }
+            }
+            uint64_t merged[2 + NSG];
+            merged[0] = ex[0];
+            merged[1] = ex[1];
+#pragma unroll
+            for (int s = 0; s < NSG; ++s) merged[2 + s] = old[s];
+            sort_regs<2 + NSG>(merged);
+            warp_select_unique<2 + NSG, NSG>(merged, k, res);
+            if (want <= kp) {
+                done_row = true;  // nothing excluded
+            } else {
+                const uint64_t astar_key = list_at<2>(top, kp);
+                const uint64_t tau_key = list_at<NSG>(res, k - 1);
+                if (tau_key != kEmptyKey) {
+                    const double astar = (double)key_dist(astar_key);
+                    const double tau = (double)key_dist(tau_key);
+                    const double ni = sqrt((double)snrm[r]);
+                    const double cD = (16.0 * Dp + 8.0) * 5.9604644775390625e-8;  // 2^-24
+                    const double eps = cD * (ni + smax[0]) * (ni + smax[0]) + 1.1920928955078125e-7 * fabs(astar);
+                    const double lo = astar - eps;
+                    double root = lo > 0.0 ? sqrt(lo) : 0.0;
+                    root -= (double)serr[r] + (double)smax[1];
+                    const double lower = root > 0.0 ? root * root : 0.0;
+                    done_row = lower * (1.0 - 1e-12) > tau;
+                }
+            }
+        }
+        if (!done_row) {
+            // not certified: exact distances to the whole leaf
+            uint64_t cand[NC + NSG];
+#pragma unroll
+            for (int s = 0; s < NC; ++s) {
+                const int c = lane + 32 * s;
+                cand[s] = kEmptyKey;
+                if (c < m && c != r)
+                    cand[s] = make_key(canon_dist(X + (int64_t)gi * D, X + (int64_t)sid[c] * D, D, vec),
+                                       (uint32_t)sid[c]);
+            }
+#pragma unroll
+            for (int s = 0; s < NSG; ++s) cand[NC + s] = old[s];
+            sort_regs<NC + NSG>(cand);
+            warp_select_unique<NC + NSG, NSG>(cand, k, res);
+            if (lane == 0) atomicAdd(status + 1, 1);  // fallback counter (statistics)
+        }
+#pragma unroll
+        for (int s = 0; s < NSG; ++s)
+            if (lane + 32 * s < k) grow[lane + 32 * s] = res[s];
+    }
+}
+
+// ---------------------------------------------------------------- host
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+}  // namespace
+
+int lp_dim(int D) { return (D + kTcK - 1) / kTcK * kTcK; }
+
+void launch_quantize(const float* X, int64_t n, int D, const int32_t* perm, bool bf16, uint16_t* Xq, float* nrm,
+                     float* qerr, int* notexact, cudaStream_t s) {
+    const int Dp = lp_dim(D);
+    LaunchScope ls("k0_quantize", s, (double)n * (D * 4.0 + Dp * 2.0 + 8.0), 0);
+    const int grid = (int)((n * 32 + 255) / 256);
+    if (bf16)
+        k0_quantize<true><<<grid, 256, 0, s>>>(X, n, D, Dp, perm, Xq, nrm, qerr, notexact);
+    else
+        k0_quantize<false><<<grid, 256, 0, s>>>(X, n, D, Dp, perm, Xq, nrm, qerr, notexact);
+}
+
+bool launch_leaf_tc(const uint16_t* Xl, int64_t n, const float* X, int D, const int32_t* perm,
+                    const int32_t* leaf_off, int nleaf, int max_leaf, const float* nrm, const float* qerr, int k,
+                    int kp, bool bf16, uint64_t* G, int* status, const int* notexact, cudaStream_t s) {
+    if (max_leaf > kTcRows) return false;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const int Dp = lp_dim(D);
+    CUtensorMap tmap;
+    const cuuint64_t gdim[2] = {(cuuint64_t)Dp, (cuuint64_t)n};
+    const cuuint64_t gstride[1] = {(cuuint64_t)Dp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTcRows};
+    const cuuint32_t estride[2] = {1, 1};
+    if (enc(&tmap, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+            const_cast<uint16_t*>(Xl), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const TcSmem L = tc_smem(Dp);
+    const size_t smem = L.total + 1024;
+    const double mm = (double)max_leaf;
+    LaunchScope ls(bf16 ? "k2_leaf_bf16" : "k2_leaf_fp16", s, (double)nleaf * mm * (Dp * 2.0 + 2 * 8.0 * k),
+                   (double)nleaf * 128.0 * 128.0 * 2.0 * Dp);
+#define KNNG_LEAF_TC(B, NS)                                                                                    \
+    do {                                                                                                       \
+        cudaFuncSetAttribute(k2_leaf_tc<B, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+        k2_leaf_tc<B, NS><<<nleaf, kTcThreads, smem, s>>>(tmap, Dp, X, D, perm, leaf_off, nrm, qerr, k, kp, G, \
+                                                          status, notexact);                                  \
+    } while (0)
+    if (bf16) {
+        if (k > 32) KNNG_LEAF_TC(true, 2);
+        else KNNG_LEAF_TC(true, 1);
+    } else {
+        if (k > 32) KNNG_LEAF_TC(false, 2);
+        else KNNG_LEAF_TC(false, 1);
+    }
+#undef KNNG_LEAF_TC
+    return true;
+}
+
+}  // namespace knng

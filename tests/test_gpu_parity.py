@@ -98,6 +98,34 @@ def test_host_pointers_give_the_same_graph(knng):
     _assert_graph_equal(di, dd, hi, hd)
 
 
+# ---------------------------------------------------------------- low precision
+def _lp_data(kind, n, D, seed):
+    if kind == "integer":      # exact in BF16/FP16: products and sums are exact integers
+        return datagen.sift_like(n, D=D, n_centres=max(2, n // 80), seed=seed)
+    if kind == "signed":       # signed integers with large norms: the certificate decides
+        rng = np.random.default_rng(seed)
+        return rng.integers(-250, 250, size=(n, D)).astype(np.float32)
+    return datagen.gaussian_mixture(n, D, 30, seed=seed)   # float: quantised, certified re-rank
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("kind,n,D,k,lm", [("integer", 4000, 128, 20, 128), ("float", 5000, 32, 10, 64),
+                                           ("float", 3000, 200, 16, 100), ("signed", 2000, 64, 12, 60),
+                                           ("integer", 1500, 24, 40, 128)])
+def test_low_precision_build_equals_fp32(knng, precision, kind, n, D, k, lm):
+    # the certified re-rank makes the BF16/FP16 leaf stage return the FP32 graph
+    X = _lp_data(kind, n, D, seed=n + D)
+    prec = knng.KNNG_BF16 if precision == "bf16" else knng.KNNG_FP16
+    mode = oracle.FWD_REV if 2 * k <= 64 else oracle.FWD   # reverse lists need 2k <= 64
+    common = dict(k=k, leaf_max=lm, tree_passes=2, refine_rounds=1, seed=9, join_mode=mode)
+    lp_ids, lp_d = knng.knng_build_ex(_dev(X), knng.default_params(precision=prec, **common))
+    f_ids, f_d = knng.knng_build_ex(_dev(X), knng.default_params(precision=knng.KNNG_FP32, **common))
+    _assert_graph_equal(lp_ids, lp_d, _np(f_ids), _np(f_d))
+    if kind == "integer":
+        o_ids, o_d = oracle.build_graph(X, k, lm, passes=2, rounds=1, seed=9, mode=mode)
+        _assert_graph_equal(lp_ids, lp_d, o_ids, o_d)
+
+
 # ---------------------------------------------------------------- partition
 @pytest.mark.parametrize("n,D,lm,iters", [(20000, 12, 64, 3), (5000, 7, 40, 4), (64, 5, 64, 4), (9000, 1, 100, 2)])
 def test_partition_matches_oracle_on_integer_data(knng, n, D, lm, iters):
