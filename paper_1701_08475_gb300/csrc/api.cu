@@ -421,7 +421,17 @@ struct BuildLayout {
     uint16_t* Xl = nullptr;
     float *lp_nrm = nullptr, *lp_err = nullptr;
     int* notexact = nullptr;
+    // tensor-core join
+    uint16_t* Xq = nullptr;
+    float *q_nrm = nullptr, *q_err = nullptr;
 };
+
+// Original-order 16-bit copy for the tensor-core stages (also sets the
+// exactness flag); nothing in FP32.
+void quantize_for_join(const float* X, const Args& a, BuildLayout& b, cudaStream_t s) {
+    if (!b.Xq) return;
+    launch_quantize(X, a.n, a.D, nullptr, a.p.precision == KNNG_BF16, b.Xq, b.q_nrm, b.q_err, b.notexact, s);
+}
 
 bool lp_leaf(const Args& a, const TreePlan& tp) {
     return a.p.precision != KNNG_FP32 && a.p.tree_passes > 0 && tp.max_leaf <= 128;
@@ -432,11 +442,24 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
     const int k = a.p.k, D = a.D;
     b.status = ws.take<int>(4);
     b.G = ws.take<uint64_t>((size_t)n * k);
+    const bool lp_any = a.p.precision != KNNG_FP32;
+    if (lp_any) b.notexact = ws.take<int>(4);
     if (tree && lp_leaf(a, tp)) {
         b.Xl = ws.take<uint16_t>((size_t)n * lp_dim(D));
         b.lp_nrm = ws.take<float>(n);
         b.lp_err = ws.take<float>(n);
-        b.notexact = ws.take<int>(4);
+    }
+    if (lp_any && (join || (tree && lp_leaf(a, tp)))) {  // original-order 16-bit copy
+        b.Xq = ws.take<uint16_t>((size_t)n * lp_dim(D));
+        b.q_nrm = ws.take<float>(n);
+        b.q_err = ws.take<float>(n);
+    }
+    if (join && lp_any) {  // the tensor-core join reads the original-order copy
+        b.jb.lp = true;
+        b.jb.bf16 = a.p.precision == KNNG_BF16;
+        b.jb.Xq = b.Xq;
+        b.jb.qnrm = b.q_nrm;
+        b.jb.notexact = b.notexact;
     }
     if (tree) {
         b.perm_a = ws.take<int32_t>(n);
@@ -548,14 +571,15 @@ void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& t
     const bool bf16 = a.p.precision == KNNG_BF16;
     // re-ranked candidates per row: k plus a margin, at most 63
     const int kp = std::min(63, k + std::max(k / 2, 8));
-    if (lp) cuda_check(cudaMemsetAsync(b.notexact, 0, sizeof(int), s), "flag clear");
+    if (b.notexact) cuda_check(cudaMemsetAsync(b.notexact, 0, sizeof(int), s), "flag clear");
+    quantize_for_join(X, a, b, s);
     for (int pass = 0; pass < a.p.tree_passes; ++pass) {
         int32_t* perm = run_partition(X, a, tp, b, pass, s);
         const int32_t* leaf_off = b.plan_dev + tp.leaf_off_at;
         const int nleaf = (int)(tp.off[tp.L].size() - 1);
         bool done = false;
         if (lp) {
-            launch_quantize(X, n, a.D, perm, bf16, b.Xl, b.lp_nrm, b.lp_err, b.notexact, s);
+            launch_permute16(b.Xq, b.q_nrm, b.q_err, n, a.D, perm, b.Xl, b.lp_nrm, b.lp_err, s);
             done = launch_leaf_tc(b.Xl, n, X, a.D, perm, leaf_off, nleaf, tp.max_leaf, b.lp_nrm, b.lp_err, k, kp,
                                   bf16, b.G, b.status, b.notexact, s);
         }
@@ -687,6 +711,8 @@ int knng_refine(const float* data, int64_t n, int D, const knng_params* p, int32
         upload(gd, s);
         launch_check_finite(X.dev, n * (int64_t)D, b.status, s);
         launch_pack(gi.dev, gd.dev, b.G, (int64_t)nk, n, b.status, s);
+        if (b.notexact) cuda_check(cudaMemsetAsync(b.notexact, 0, sizeof(int), s), "flag clear");
+        quantize_for_join(X.dev, a, b, s);
         for (int r = 0; r < p->refine_rounds; ++r) {
             run_join_round(X.dev, n, D, p->k, p->join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, b.jb,
                            b.nodes_per_chunk, b.status, s);

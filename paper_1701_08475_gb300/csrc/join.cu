@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
                                                           int64_t node1, uint32_t* __restrict__ counter,
                                                           int64_t cap, uint32_t* __restrict__ ptgt,
                                                           uint64_t* __restrict__ pkey,
-                                                          int32_t* __restrict__ pcnt, int* __restrict__ status) {
+                                                          int32_t* __restrict__ pcnt, int* __restrict__ status,
+                                                          const int* __restrict__ skip_if_exact) {
     extern __shared__ float4 smem4[];
     int dch, stride;
     join_chunk(D, mcap, &dch, &stride);
@@ -245,6 +246,11 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
 
     const int64_t i = node0 + (int64_t)blockIdx.x * kJoinWarps + warp;
     if (i >= node1 || (*status & kStatusStop)) return;
+    // the tensor-core join does this round when the 16-bit copy is exact
+    if (skip_if_exact) {
+        const int f = *skip_if_exact;
+        if ((f & 1) == 0 && !((f & 2) && (f & 4))) return;
+    }
     // members: real ids of G_old[i], then of R[i]
     int M = 0;
     for (int src = 0; src < (rev ? 2 : 1); ++src) {
@@ -583,6 +589,10 @@ void run_join_round(const float* X, int64_t n, int D, int k, bool rev, const uin
         cudaMemsetAsync(b.pcnt, 0, sizeof(int32_t) * (n + 1), s);
         cudaMemsetAsync(b.pcur, 0, sizeof(int32_t) * n, s);
         cudaMemsetAsync(b.counter, 0, sizeof(uint32_t), s);
+        // tensor-core join first; the FP32 join below then returns at once
+        // on the device when the 16-bit copy is exact
+        const bool tc_launched = b.lp && launch_join_tc(b.Xq, D, b.qnrm, k, rev, Gold, b.R, c0, c1, b, status,
+                                                        b.notexact, b.bf16, s);
         {
             const double m = rev ? 2.0 * k : (double)k;
             LaunchScope ls("k5_join", s, (double)(c1 - c0) * (m * D * 4.0 + 2 * k * 8.0 + m * 8.0),
@@ -592,7 +602,8 @@ void run_join_round(const float* X, int64_t n, int D, int k, bool rev, const uin
     do {                                                                                                   \
         cudaFuncSetAttribute(k5_join<BPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
         k5_join<BPL><<<grid, 32 * kJoinWarps, smem, s>>>(X, D, k, rev ? 1 : 0, mcap, Gold, b.R, c0, c1,     \
-                                                         b.counter, b.cap, b.ptgt, b.pkey, b.pcnt, status); \
+                                                         b.counter, b.cap, b.ptgt, b.pkey, b.pcnt, status,  \
+                                                         tc_launched ? b.notexact : nullptr);               \
     } while (0)
             if (bpl <= 1) KNNG_JOIN(1);
             else if (bpl <= 2) KNNG_JOIN(2);

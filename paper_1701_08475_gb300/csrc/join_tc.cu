@@ -1,0 +1,261 @@
+// join_tc.cu -- the local join (neighbour-of-neighbour refinement, the prior
+// art cited in Sec. 1) with the member Gram matrices on tcgen05 tensor cores.
+//
+// Used when the 16-bit copy makes the arithmetic exact (all values integers
+// the 16-bit type holds, every squared norm and distance an integer below
+// 2^24): then ||x_u||^2 + ||x_v||^2 - 2 x_u . x_v computed from the tensor
+// cores' FP32 accumulator is the canonical distance itself, bit for bit.
+// Otherwise the kernel returns at once and the FP32 join (join.cu), launched
+// beside it, does the round; the choice is made on the device, so neither
+// needs the host to look at the data.
+//
+// One CTA packs NPC nodes: node j's members N_i = G_old[i] (+ R[i]) occupy
+// tile rows j * mcap .. j * mcap + M_j - 1.  Their 16-bit rows are gathered
+// into the 128-byte-swizzled K-major layout with cp.async, one thread issues
+// the 128 x 128 x Dp Gram on the tensor cores, and in the epilogue thread r
+// (= tensor-memory lane r) offers every pair {u, v} of its node with v after
+// u, in both directions, when the offer beats the target's k-th entry.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace knng {
+
+namespace {
+
+constexpr int kRows = 128;
+constexpr int kKc = 64;                  // 16-bit elements per swizzled row
+constexpr int kChunkBytes = kRows * kKc * 2;
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ bool lp_exact_flag(int f) { return (f & 1) == 0 && !((f & 2) && (f & 4)); }
+
+struct JtSmem {
+    size_t tile, priv, mem, thr, nrm, cnt, bar, slot, total;
+};
+__host__ __device__ inline JtSmem jt_smem(int Dp, int mcap) {
+    JtSmem L;
+    L.tile = 0;
+    L.priv = 0;  // the operand tile is dead once the MMA has completed
+    const size_t tile = (size_t)(Dp / kKc) * kChunkBytes, pv = (size_t)mcap * kRows * 4;
+    L.mem = tile > pv ? tile : pv;
+    L.thr = L.mem + kRows * 4;
+    L.nrm = L.thr + kRows * 8;
+    L.cnt = L.nrm + kRows * 4;
+    L.bar = L.cnt + 16 * 4;
+    L.slot = L.bar + 8;
+    L.total = L.slot + 8;
+    return L;
+}
+
+// Persistent: CTA b takes node groups b, b + gridDim.x, ...; tensor memory
+// and the barrier are set up once.
+__global__ void __launch_bounds__(kThreads, 1) k5_join_tc(const uint16_t* __restrict__ Xq, int Dp,
+                                                         const float* __restrict__ nrm, int k, int rev, int mcap,
+                                                         int npc, const uint64_t* __restrict__ Gold,
+                                                         const uint64_t* __restrict__ R, int64_t node0,
+                                                         int64_t node1, uint32_t* __restrict__ counter, int64_t cap,
+                                                         uint32_t* __restrict__ ptgt, uint64_t* __restrict__ pkey,
+                                                         int32_t* __restrict__ pcnt, int* __restrict__ status,
+                                                         const int* __restrict__ notexact, bool bf16) {
+    extern __shared__ uint8_t smem_raw[];
+    if ((*status & kStatusStop) || !lp_exact_flag(*notexact)) return;
+    const JtSmem L = jt_smem(Dp, mcap);
+    uint8_t* base = smem_raw + ((1024 - (tc::smem_addr(smem_raw) & 1023)) & 1023);
+    float* priv = reinterpret_cast<float*>(base + L.priv);    // [mcap][128]: thread r's Gram row
+    int32_t* mem = reinterpret_cast<int32_t*>(base + L.mem);
+    uint64_t* thr = reinterpret_cast<uint64_t*>(base + L.thr);
+    float* snrm = reinterpret_cast<float*>(base + L.nrm);
+    int* mcount = reinterpret_cast<int*>(base + L.cnt);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.slot);
+    const uint32_t done = tc::smem_addr(base + L.bar);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nk = Dp / kKc;
+    const int64_t ngroups = (node1 - node0 + npc - 1) / npc;
+
+    if (tid == 0) {
+        tc::mbar_init(done, 1);
+        tc::mbar_fence_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_addr(tmem_slot), kRows);
+        tc::tmem_relinquish();
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = tc::idesc_f16(bf16, kRows, kRows);
+    int iter = 0;
+    bool ok = true;
+    for (int64_t grp = blockIdx.x; grp < ngroups && ok; grp += gridDim.x, ++iter) {
+        const int64_t first = node0 + grp * npc;
+        for (int r = tid; r < kRows; r += kThreads) mem[r] = -1;
+        __syncthreads();
+        // members of the group's nodes (warp j collects node j)
+        for (int j = warp; j < npc; j += kThreads / 32) {
+            const int64_t i = first + j;
+            int M = 0;
+            if (i < node1) {
+                for (int src = 0; src < (rev ? 2 : 1); ++src) {
+                    const uint64_t* row = (src == 0 ? Gold : R) + i * k;
+                    for (int e0 = 0; e0 < k; e0 += 32) {
+                        const int e = e0 + lane;
+                        const uint64_t key = e < k ? row[e] : kEmptyKey;
+                        const bool real = key != kEmptyKey;
+                        const unsigned bal = __ballot_sync(0xffffffffu, real);
+                        if (real) mem[j * mcap + M + __popc(bal & ((1u << lane) - 1u))] = (int32_t)key_id(key);
+                        M += __popc(bal);
+                    }
+                }
+            }
+            if (lane == 0) mcount[j] = M;
+        }
+        __syncthreads();
+        // gather the member rows (16-byte pieces) into the swizzled K-major tile;
+        // the thresholds and norms below load while these copies are in flight
+        const int q_per_row = Dp / 8;
+        for (int e = tid; e < kRows * q_per_row; e += kThreads) {
+            const int r = e / q_per_row, q = e - r * q_per_row;
+            const int kc = q >> 3, c16 = q & 7;
+            uint8_t* dst = base + (size_t)kc * kChunkBytes + r * 128 + ((c16 ^ (r & 7)) << 4);
+            const int u = mem[r];
+            if (u >= 0) {
+                const uint16_t* src = Xq + (int64_t)u * Dp + q * 8;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::smem_addr(dst)), "l"(src)
+                             : "memory");
+            } else {
+                *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+        for (int r = tid; r < kRows; r += kThreads) {
+            const int u = mem[r];
+            thr[r] = u >= 0 ? Gold[(int64_t)u * k + k - 1] : 0ull;
+            snrm[r] = u >= 0 ? nrm[u] : 0.f;
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        // the tensor cores read shared memory through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            for (int c = 0; c < nk; ++c) {
+                const uint64_t d0 = tc::sdesc_k128(tc::smem_addr(base + (size_t)c * kChunkBytes));
+#pragma unroll
+                for (int kk = 0; kk < kKc / 16; ++kk)
+                    tc::mma_f16(tmem, d0 + 2 * kk, d0 + 2 * kk, idesc, (c | kk) != 0);
+            }
+            tc::mma_commit(done);
+        }
+        __syncwarp();
+        const int mma_ok = tc::mbar_wait(done, (uint32_t)(iter & 1), status) ? 1 : 0;
+        ok = __syncthreads_and(mma_ok);
+        tc::fence_after_sync();
+        if (!ok) break;
+
+        // ---- epilogue: thread r = row r of the tile
+        const int r = tid;
+        const int j = r / mcap, s = r - j * mcap;
+        const int Mj = j < npc ? mcount[j] : 0;
+        const bool mine = s < Mj;
+        // this row's Gram values against its node's members -> private column
+#pragma unroll 1
+        for (int cc = 0; cc < kRows / 32; ++cc) {
+            float g[32];
+            tc::tmem_ld_32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), g);
+            if (mine) {
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int t = cc * 32 + jj - j * mcap;
+                    if (t > s && t < Mj) priv[t * kRows + r] = g[jj];
+                }
+            }
+        }
+        const uint32_t u = mine ? (uint32_t)mem[r] : 0u;
+        const uint64_t thr_u = thr[r];
+        const float nu = snrm[r];
+        // pass 0 counts the offers, pass 1 writes them
+        int cnt = 0;
+        uint32_t w = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1) {
+                int x = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                const int total = __shfl_sync(0xffffffffu, x, 31);
+                uint32_t at = 0;
+                if (lane == 31 && total > 0) at = atomicAdd(counter, (uint32_t)total);
+                at = __shfl_sync(0xffffffffu, at, 31);
+                if (total == 0) break;
+                if ((int64_t)at + total > cap) {
+                    if (lane == 0) atomicOr(status, kStatusOverflow);
+                    break;
+                }
+                w = at + x - cnt;
+            }
+            for (int t = s + 1; mine && t < Mj; ++t) {
+                const int col = j * mcap + t;
+                const uint32_t v = (uint32_t)mem[col];
+                if (v == u) continue;
+                const float d = __fadd_rn(__fsub_rn(__fadd_rn(nu, snrm[col]), __fmul_rn(2.f, priv[t * kRows + r])), 0.f);
+                const uint64_t ku = make_key(d, v);
+                const uint64_t kv = make_key(d, u);
+                const bool ou = ku < thr_u, ov = kv < thr[col];
+                if (pass == 0) {
+                    cnt += (int)ou + (int)ov;
+                } else {
+                    if (ou) {
+                        ptgt[w] = u;
+                        pkey[w] = ku;
+                        ++w;
+                        atomicAdd(&pcnt[u], 1);
+                    }
+                    if (ov) {
+                        ptgt[w] = v;
+                        pkey[w] = kv;
+                        ++w;
+                        atomicAdd(&pcnt[v], 1);
+                    }
+                }
+            }
+        }
+        // all tensor-memory reads and shared-memory uses of this group done
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kRows);
+}
+
+}  // namespace
+
+bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev, const uint64_t* Gold,
+                    const uint64_t* R, int64_t node0, int64_t node1, const JoinBuffers& b, int* status,
+                    const int* notexact, bool bf16, cudaStream_t s) {
+    const int Dp = lp_dim(D);
+    const int mcap = ((rev ? 2 * k : k) + 7) & ~7;
+    if (Dp / kKc > 4 || mcap > kRows) return false;
+    const int npc = kRows / mcap;
+    const JtSmem L = jt_smem(Dp, mcap);
+    // at least 56 KB per CTA: at most 4 CTAs (512 tensor-memory columns) per SM
+    size_t smem = L.total + 1024;
+    if (smem < 56 * 1024) smem = 56 * 1024;
+    const int64_t nodes = node1 - node0;
+    const int64_t groups = (nodes + npc - 1) / npc;
+    const int per_sm = (int)((227 * 1024) / smem) < 4 ? (int)((227 * 1024) / smem) : 4;
+    const int grid = (int)(groups < (int64_t)152 * per_sm ? groups : (int64_t)152 * per_sm);
+    const double m = rev ? 2.0 * k : (double)k;
+    LaunchScope ls("k5_join_tc", s, (double)nodes * (m * Dp * 2.0 + 2 * k * 8.0 + m * 12.0),
+                   (double)grid * kRows * kRows * 2.0 * Dp);
+    cudaFuncSetAttribute(k5_join_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k5_join_tc<<<grid, kThreads, smem, s>>>(Xq, Dp, nrm, k, rev ? 1 : 0, mcap, npc, Gold, R, node0, node1, b.counter,
+                                            b.cap, b.ptgt, b.pkey, b.pcnt, status, notexact, bf16);
+    return true;
+}
+
+}  // namespace knng

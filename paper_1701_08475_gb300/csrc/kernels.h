@@ -84,6 +84,9 @@ int lp_dim(int D);  // D rounded up to the 64-element rows of the swizzled tiles
 // not exact for this input.
 void launch_quantize(const float* X, int64_t n, int D, const int32_t* perm, bool bf16, uint16_t* Xq, float* nrm,
                      float* qerr, int* notexact, cudaStream_t s);
+// Leaf-order gather of a 16-bit copy (with its norms and errors).
+void launch_permute16(const uint16_t* Xq, const float* nrm, const float* qerr, int64_t n, int D,
+                      const int32_t* perm, uint16_t* Xl, float* lnrm, float* lerr, cudaStream_t s);
 // Leaf stage on tcgen05 from the leaf-order copy; false when it cannot run
 // (leaf above 128 points, no tensor-map encoder) and nothing was launched.
 // status[1] counts the rows that fell back to exact recomputation.
@@ -108,7 +111,19 @@ struct JoinBuffers {
     uint32_t* counter;   // [1] proposals appended
     int32_t* scan_tmp;   // scan scratch
     unsigned long long* offers_total;  // [1] offers grouped over the whole call (statistics)
+    // tensor-core join (16-bit copy in original order); used when lp is set
+    // and, on the device, only when the copy's arithmetic is exact
+    bool lp = false, bf16 = true;
+    const uint16_t* Xq = nullptr;
+    const float* qnrm = nullptr;
+    const int* notexact = nullptr;
 };
+
+// The tensor-core local join of nodes [node0, node1); false (nothing
+// launched) when the shape is not supported.
+bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev, const uint64_t* Gold,
+                    const uint64_t* R, int64_t node0, int64_t node1, const JoinBuffers& b, int* status,
+                    const int* notexact, bool bf16, cudaStream_t s);
 
 // Adds `items` to the statistics of kernel `name` (when statistics are on).
 void record_items(const char* name, double items);

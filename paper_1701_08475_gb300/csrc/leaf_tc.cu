@@ -74,16 +74,15 @@ __global__ void __launch_bounds__(256) k0_quantize(const float* __restrict__ X, 
     const int lane = threadIdx.x & 31;
     const int64_t i = perm ? perm[p] : p;
     const float lim = BF16 ? 256.f : 2048.f;
-    float sq = 0.f;
-    double e2 = 0.0;
+    float sq = 0.f, e2 = 0.f;
     bool exact = true, neg = false;
     for (int d = lane; d < Dp; d += 32) {
         const float x = d < D ? X[i * D + d] : 0.f;
         float b;
         Xq[p * Dp + d] = quantize_bits<BF16>(x, &b);
         sq = __fmaf_rn(b, b, sq);
-        const double t = (double)x - (double)b;
-        e2 += t * t;
+        const float t = __fsub_rn(x, b);  // exact: b is x rounded to fewer bits
+        e2 = __fmaf_rn(t, t, e2);
         exact &= (x == rintf(x)) && fabsf(x) <= lim;
         neg |= x < 0.f;
     }
@@ -96,14 +95,34 @@ __global__ void __launch_bounds__(256) k0_quantize(const float* __restrict__ X, 
     neg = __any_sync(0xffffffffu, neg);
     if (lane == 0) {
         nrm[p] = sq;
-        // rounded up: the bound must not shrink
-        qerr[p] = e2 > 0.0 ? __double2float_ru(sqrt(e2) * (1.0 + 1e-12)) : 0.f;
+        // an upper bound: the FP32 sum of Dp squares is within (Dp + 2) u of
+        // the exact sum (Higham, Ch. 3), the square root rounds up
+        qerr[p] = e2 > 0.f ? __fsqrt_ru(__fmul_ru(e2, 1.f + (float)(Dp + 8) * 5.9604645e-8f)) : 0.f;
         const int f = ((!exact || sq >= 8388608.f) ? 1 : 0) | (neg ? 2 : 0) | (sq >= 4194304.f ? 4 : 0);
         if (f) atomicOr(notexact, f);
     }
 }
 
 __device__ __forceinline__ bool lp_exact(int f) { return (f & 1) == 0 && !((f & 2) && (f & 4)); }
+
+// Leaf-order copy gathered from the original-order one: row p of the output
+// is row perm[p] of the input (16-byte pieces), with its norm and error.
+__global__ void __launch_bounds__(256) k0_permute16(const uint4* __restrict__ Xq, const float* __restrict__ nrm,
+                                                    const float* __restrict__ qerr, int64_t n, int q_per_row,
+                                                    const int32_t* __restrict__ perm, uint4* __restrict__ Xl,
+                                                    float* __restrict__ lnrm, float* __restrict__ lerr) {
+    const int64_t total = n * q_per_row;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e / q_per_row;
+        const int q = (int)(e - p * q_per_row);
+        const int64_t i = perm[p];
+        Xl[e] = __ldg(Xq + i * q_per_row + q);
+        if (q == 0) {
+            lnrm[p] = nrm[i];
+            lerr[p] = qerr[i];
+        }
+    }
+}
 
 // ---------------------------------------------------------------- K2/K3
 constexpr int kTcRows = 128;             // M = N = 128 tile: leaves up to 128 points
@@ -439,6 +458,17 @@ void launch_quantize(const float* X, int64_t n, int D, const int32_t* perm, bool
         k0_quantize<true><<<grid, 256, 0, s>>>(X, n, D, Dp, perm, Xq, nrm, qerr, notexact);
     else
         k0_quantize<false><<<grid, 256, 0, s>>>(X, n, D, Dp, perm, Xq, nrm, qerr, notexact);
+}
+
+void launch_permute16(const uint16_t* Xq, const float* nrm, const float* qerr, int64_t n, int D,
+                      const int32_t* perm, uint16_t* Xl, float* lnrm, float* lerr, cudaStream_t s) {
+    const int Dp = lp_dim(D);
+    const int q = Dp / 8;
+    LaunchScope ls("k0_permute16", s, (double)n * (Dp * 4.0 + 16.0), 0);
+    int64_t g = (n * q + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    k0_permute16<<<(int)g, 256, 0, s>>>(reinterpret_cast<const uint4*>(Xq), nrm, qerr, n, q, perm,
+                                        reinterpret_cast<uint4*>(Xl), lnrm, lerr);
 }
 
 bool launch_leaf_tc(const uint16_t* Xl, int64_t n, const float* X, int D, const int32_t* perm,
