@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16"])
     return ap.parse_args()
 
 
@@ -116,9 +117,11 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-KERNEL_SOURCES = {"k1_": "split.cu", "k2_": "leaf.cu", "k4_": "join.cu", "k5_": "join.cu", "k6_": "join.cu",
-                  "k7_": "exact.cu"}
+KERNEL_SOURCES = {"k1_": "split.cu", "k2_leaf_fp32": "leaf.cu", "k2_": "leaf_tc.cu", "k4_": "join.cu",
+                  "k5_join_tc": "join_tc.cu", "k5_": "join.cu", "k6_": "join.cu", "k7_": "exact.cu",
+                  "k0_": "leaf_tc.cu"}
 ALU_KERNELS = ("k5_join", "k2_leaf_fp32", "k7_exact")
+TENSOR_KERNELS = ("k2_leaf_bf16", "k2_leaf_fp16")
 
 
 def kernel_source_hash(kernel):
@@ -169,6 +172,12 @@ def roofline(stats, clocks, workload, steps):
         out = {"kernel": name, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
                "unit": "Top/s", "frac": round(achieved / peak, 4),
                "peak_source": "derived: 152 SMs x 128 FP32 lanes x median SM clock %.0f MHz" % sm_mhz}
+    elif name in TENSOR_KERNELS:
+        # dense 16-bit tensor rate; timed inside a long step: the sustained peak
+        achieved = st["flops"] / st["launches"] / (avg_ms * 1e-3) / 1e12
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
+        out = {"kernel": name, "bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+               "frac": round(achieved / peak, 4), "peak_source": "%s bf16_tflops_sustained" % kind}
     else:
         achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
         peak = float(peaks["hbm_gbs"])
@@ -224,6 +233,9 @@ def run_reference(args, cfg):
 
 
 # ---------------------------------------------------------------- our arm
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
+
+
 def run_ours(args, cfg):
     import torch
     import paper_1701_08475_gb300 as knng
@@ -241,50 +253,58 @@ def run_ours(args, cfg):
         X = X[np.random.default_rng(rank).permutation(X.shape[0])]
     n, D = X.shape
     Xd = torch.from_numpy(X).to(dev)
-    p = knng.default_params(k=cfg["k"], leaf_max=cfg["leaf_max"], tree_passes=cfg["tree_passes"],
-                            refine_rounds=cfg["refine_rounds"], join_mode=knng.KNNG_JOIN_FWD_REV,
-                            twomeans_iters=cfg["twomeans_iters"], seed=cfg["seed"])
     stream = torch.cuda.Stream(dev)
-    ids = torch.empty((n, cfg["k"]), dtype=torch.int32, device=dev)
-    dists = torch.empty((n, cfg["k"]), dtype=torch.float32, device=dev)
 
-    def step():
-        knng.knng_build_ex(Xd, p, stream=stream, out=(ids, dists))
-
-    with torch.cuda.stream(stream):
-        for _ in range(max(3, args.warmup)):
-            step()
-    torch.cuda.synchronize()
+    def params(prec):
+        return knng.default_params(k=cfg["k"], leaf_max=cfg["leaf_max"], tree_passes=cfg["tree_passes"],
+                                   refine_rounds=cfg["refine_rounds"], join_mode=knng.KNNG_JOIN_FWD_REV,
+                                   twomeans_iters=cfg["twomeans_iters"], seed=cfg["seed"],
+                                   precision=PRECISIONS[prec])
 
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
 
-    clocks = ClockSampler(local)
-    knng.stats_reset()
-    knng.stats_enable(True, timing=True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    with torch.cuda.stream(stream):
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step()
-        ev1.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    knng.stats_enable(False)
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    st = knng.stats()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    def max_over_ranks(v):
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([v], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            v = float(t.item())
+        return v
+
+    def timed(prec, sample_clocks):
+        """steps whole builds on one stream, CUDA events, after warm-up."""
+        p = params(prec)
+        ids = torch.empty((n, cfg["k"]), dtype=torch.int32, device=dev)
+        dists = torch.empty((n, cfg["k"]), dtype=torch.float32, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(max(3, args.warmup)):
+                knng.knng_build_ex(Xd, p, stream=stream, out=(ids, dists))
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local) if sample_clocks else None
+        knng.stats_reset()
+        knng.stats_enable(True, timing=True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(args.steps):
+                knng.knng_build_ex(Xd, p, stream=stream, out=(ids, dists))
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        knng.stats_enable(False)
+        barrier()
+        ms = max_over_ranks(ev0.elapsed_time(ev1))
+        return ms, knng.stats(), clk, ids, dists
+
+    ms, st, clk, ids, dists = timed(args.precision, True)
     launches = sum(v["launches"] for v in st.values())
     value = world * n * args.steps / (ms * 1e-3)
 
@@ -294,7 +314,17 @@ def run_ours(args, cfg):
     gi, gd = knng.knng_exact(Xd, cfg["k"], smp_d)
     rec_ids, rec_tie = knng.knng_recall(ids, dists, gi, gd, smp_d)
 
+    # the plain FP32 form of the same build, timed the same way
+    fp32 = None
+    if args.precision != "fp32":
+        ms32, st32, _, ids32, d32 = timed("fp32", False)
+        r32 = knng.knng_recall(ids32, d32, gi, gd, smp_d)
+        fp32 = {"value": round(world * n * args.steps / (ms32 * 1e-3), 1), "ms_per_step": round(ms32 / args.steps, 3),
+                "recall_ids": round(r32[0], 5),
+                "graph_identical": bool(torch.equal(ids32, ids) and torch.equal(d32, dists))}
+
     # end to end: host buffers through the C ABI, copies inside the timed region
+    p = params(args.precision)
     Xh = torch.from_numpy(X).pin_memory()
     oi = torch.empty((n, cfg["k"]), dtype=torch.int32).pin_memory()
     od = torch.empty((n, cfg["k"]), dtype=torch.float32).pin_memory()
@@ -303,12 +333,7 @@ def run_ours(args, cfg):
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         knng.knng_build_ex(Xh, p, stream=stream, out=(oi, od))
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": round(world * n * args.e2e_steps / e2e_s, 1), "unit": "points/s",
            "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(oi.numel() * 4 + od.numel() * 4),
            "steps": args.e2e_steps, "timer": "host wall clock around synchronous C-ABI calls"}
@@ -322,18 +347,21 @@ def run_ours(args, cfg):
     roof = roofline(st, clk, cfg["workload"], args.steps)
     roof["share_of_step"] = round(st[roof["kernel"]]["ms"] / ms, 4)
     cfg_out = dict(cfg)
+    cfg_out["precision"] = args.precision
     cfg_out["l2"] = "inputs larger than L2: X is %.0f MB (L2 129 MB)" % (X.nbytes / 1e6)
     line = {
         "metric": "kNN-graph build points/s at recall@k vs exact", "value": round(value, 1), "unit": "points/s",
         "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else args.precision + "+f32", "data": "synthetic",
         "config": cfg_out,
         "recall_at_k": {"ids": round(rec_ids, 5), "tie": round(rec_tie, 5), "sample_rows": int(len(smp)),
                         "exact": "knng_exact canonical FP32"},
+        "fp32_form": fp32,
         "roofline": roof, "e2e": e2e, "e2e_graph_equals_device_graph": same, "gpu_launches": int(launches),
         "clocks": clk,
         "kernels": {k_: {"ms_per_step": round(v["ms"] / args.steps, 3), "launches_per_step": v["launches"] / args.steps}
-                    for k_, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+                    for k_, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])[:10]},
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)

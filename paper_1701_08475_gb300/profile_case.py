@@ -45,6 +45,7 @@ def main():
     ap.add_argument("--workload", default="sift-like-1m-d128")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     a = ap.parse_args()
     import torch
 
@@ -56,7 +57,7 @@ def main():
     for _ in range(a.repeat):
         if a.stage == "build":
             p = knng.default_params(k=k, leaf_max=w["leaf_max"], tree_passes=w["passes"], refine_rounds=w["rounds"],
-                                    seed=w["seed"])
+                                    seed=w["seed"], precision={"fp32": 0, "bf16": 1, "fp16": 2}[a.precision])
             knng.knng_build_ex(Xd, p)
         elif a.stage == "split":
             knng.knng_partition(Xd, w["leaf_max"], seed=w["seed"])
