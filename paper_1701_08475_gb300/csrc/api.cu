@@ -449,7 +449,7 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.lp_nrm = ws.take<float>(n);
         b.lp_err = ws.take<float>(n);
     }
-    if (lp_any && (join || (tree && lp_leaf(a, tp)))) {  // original-order 16-bit copy
+    if (lp_any && (join || tree)) {  // original-order 16-bit copy
         b.Xq = ws.take<uint16_t>((size_t)n * lp_dim(D));
         b.q_nrm = ws.take<float>(n);
         b.q_err = ws.take<float>(n);
@@ -460,6 +460,12 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.jb.Xq = b.Xq;
         b.jb.qnrm = b.q_nrm;
         b.jb.notexact = b.notexact;
+    }
+    if (tree && lp_any) {  // the tree sweeps read the 16-bit copy when it is exact
+        b.sb.Xq = b.Xq;
+        b.sb.Dq = lp_dim(D);
+        b.sb.qtype = a.p.precision == KNNG_BF16 ? 1 : 2;
+        b.sb.qflag = b.notexact;
     }
     if (tree) {
         b.perm_a = ws.take<int32_t>(n);

@@ -58,6 +58,11 @@ struct SplitBuffers {
     double* partial;      // [nsweep_max][2][D]
     int32_t* tile_left;   // [ntiles_max]
     int* status;          // device status word
+    // 16-bit copy of X (original order, rows of Dq); the sweeps read it
+    // instead of X when *qflag says it holds every value exactly
+    const uint16_t* Xq = nullptr;
+    int Dq = 0, qtype = 0;  // qtype 1 = BF16, 2 = FP16
+    const int* qflag = nullptr;
 };
 
 constexpr int kTile = 2048;         // positions per select/partition tile

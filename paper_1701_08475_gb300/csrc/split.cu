@@ -13,6 +13,8 @@
 // and the level ends with a final project + select + stable partition.
 // With a balanced cut only the order of ||x-c0||^2 - ||x-c1||^2 matters, and
 // x . (c1 - c0) has the same order.
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -107,25 +109,29 @@ __global__ void k1_init(const float* __restrict__ X, int D, const int32_t* __res
 // and accumulates its dims in ascending order with fmaf.  Rows are staged in
 // shared memory 64 dims at a time (a warp loads 32 rows' 256-byte pieces,
 // all in flight at once) so that global loads stay coalesced.
-template <bool VEC2>
-__global__ void __launch_bounds__(256) k1_project(const float* __restrict__ X, int D,
-                                                  const int32_t* __restrict__ perm,
-                                                  const int4* __restrict__ tiles,
-                                                  const int32_t* __restrict__ seg_off,
-                                                  const float* __restrict__ W, float* __restrict__ S,
-                                                  SelState* __restrict__ st, const int* __restrict__ status) {
-    __shared__ float xs[256][65];
-    __shared__ float ws[64];
-    if (*status & kStatusStop) return;  // perm may hold unwritten slots
-    const int4 t = tiles[blockIdx.x];
-    const int seg = t.x, begin = t.y, end = t.z;
+// When the 16-bit copy holds every value exactly (flag from the quantize
+// kernel), the sweeps read it instead of X: the same FP32 values, half the
+// bytes.  qtype: 1 = BF16, 2 = FP16.
+__device__ __forceinline__ bool q16_usable(const uint16_t* Xq, const int* qflag) {
+    if (Xq == nullptr) return false;
+    const int f = *qflag;
+    return (f & 1) == 0 && !((f & 2) && (f & 4));
+}
+template <int Q>  // 1 = BF16, 2 = FP16
+__device__ __forceinline__ float q16_to_float(uint32_t h) {
+    if (Q == 1) return __uint_as_float(h << 16);
+    return __half2float(__ushort_as_half((unsigned short)h));
+}
+
+// One sweep tile of the projection.  Q = 0 reads the FP32 rows of X (VEC2:
+// as float2), Q = 1 / 2 the BF16 / FP16 copy; every load of a 64-dim slab is
+// issued before any value is used.
+template <bool VEC2, int Q>
+__device__ __forceinline__ void project_tile(const float* __restrict__ X, int D, const uint16_t* __restrict__ Xq,
+                                             int Dq, const int32_t* __restrict__ perm, int begin, int end,
+                                             const float* __restrict__ w, float* __restrict__ S, float (*xs)[65],
+                                             float* ws) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (st != nullptr && t.w && threadIdx.x == 0) {
-        const int m = seg_off[seg + 1] - seg_off[seg];
-        st[seg].prefix = 0;
-        st[seg].krem = (uint32_t)(m / 2);
-    }
-    const float* w = W + (int64_t)seg * D;
     for (int base = begin; base < end; base += 256) {
         const int cnt = min(256, end - base);
         const int my_row = threadIdx.x < cnt ? perm[base + threadIdx.x] : 0;
@@ -134,22 +140,28 @@ __global__ void __launch_bounds__(256) k1_project(const float* __restrict__ X, i
             const int dl = min(64, D - d0);
             if (threadIdx.x < 64) ws[threadIdx.x] = threadIdx.x < dl ? w[d0 + threadIdx.x] : 0.f;
             float2 v[32];
+            uint32_t h[32];  // Q != 0: two raw 16-bit values
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
                 const int row = __shfl_sync(0xffffffffu, my_row, q);
-                const float* src = X + (int64_t)row * D + d0 + 2 * lane;
+                const bool live = warp * 32 + q < cnt && 2 * lane < dl;
                 v[q] = make_float2(0.f, 0.f);
-                if (warp * 32 + q < cnt) {
+                h[q] = 0u;
+                if (Q != 0) {  // rows padded to Dq: the pair is in bounds
+                    if (live) h[q] = __ldg(reinterpret_cast<const uint32_t*>(Xq + (int64_t)row * Dq + d0 + 2 * lane));
+                } else {
+                    const float* src = X + (int64_t)row * D + d0 + 2 * lane;
                     if (VEC2) {
-                        if (2 * lane < dl) v[q] = __ldg(reinterpret_cast<const float2*>(src));
-                    } else {
-                        if (2 * lane < dl) v[q].x = __ldg(src);
+                        if (live) v[q] = __ldg(reinterpret_cast<const float2*>(src));
+                    } else if (live) {
+                        v[q].x = __ldg(src);
                         if (2 * lane + 1 < dl) v[q].y = __ldg(src + 1);
                     }
                 }
             }
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
+                if (Q != 0) v[q] = make_float2(q16_to_float<Q>(h[q] & 0xFFFFu), q16_to_float<Q>(h[q] >> 16));
                 xs[warp * 32 + q][2 * lane] = v[q].x;
                 xs[warp * 32 + q][2 * lane + 1] = v[q].y;
             }
@@ -160,6 +172,35 @@ __global__ void __launch_bounds__(256) k1_project(const float* __restrict__ X, i
         }
         if (threadIdx.x < cnt) S[base + threadIdx.x] = __fadd_rn(acc, 0.f);  // -0 -> +0
     }
+}
+
+template <bool VEC2>
+__global__ void __launch_bounds__(256) k1_project(const float* __restrict__ X, int D,
+                                                  const int32_t* __restrict__ perm,
+                                                  const int4* __restrict__ tiles,
+                                                  const int32_t* __restrict__ seg_off,
+                                                  const float* __restrict__ W, float* __restrict__ S,
+                                                  SelState* __restrict__ st, const int* __restrict__ status,
+                                                  const uint16_t* __restrict__ Xq, int Dq, int qtype,
+                                                  const int* __restrict__ qflag) {
+    __shared__ float xs[256][65];
+    __shared__ float ws[64];
+    if (*status & kStatusStop) return;  // perm may hold unwritten slots
+    const int q = q16_usable(Xq, qflag) ? qtype : 0;
+    const int4 t = tiles[blockIdx.x];
+    const int seg = t.x, begin = t.y, end = t.z;
+    if (st != nullptr && t.w && threadIdx.x == 0) {
+        const int m = seg_off[seg + 1] - seg_off[seg];
+        st[seg].prefix = 0;
+        st[seg].krem = (uint32_t)(m / 2);
+    }
+    const float* w = W + (int64_t)seg * D;
+    if (q == 1)
+        project_tile<VEC2, 1>(X, D, Xq, Dq, perm, begin, end, w, S, xs, ws);
+    else if (q == 2)
+        project_tile<VEC2, 2>(X, D, Xq, Dq, perm, begin, end, w, S, xs, ws);
+    else
+        project_tile<VEC2, 0>(X, D, Xq, Dq, perm, begin, end, w, S, xs, ws);
 }
 
 // Small segments: one CTA per segment keeps all keys in shared memory,
@@ -275,6 +316,90 @@ __global__ void __launch_bounds__(256) k1_select_pass(const float* __restrict__ 
 // per warp ascending positions, then warps 0..15, then tiles.
 constexpr int kSumsWarps = 16;
 
+// Adds the n rows listed in rows[] (one side of the cut) to the per-lane
+// compensated sums (h, l), with the loads of up to U rows in flight.  Q = 0
+// reads the FP32 rows of X (VEC: lane l owns dims 4l .. 4l+3, else l, l+32,
+// ...), Q = 1 / 2 the BF16 / FP16 copy (dims 4l .. 4l+3).
+template <bool VEC, int Q>
+__device__ __forceinline__ void sums_side(const float* __restrict__ X, int D, const uint16_t* __restrict__ Xq, int Dq,
+                                          const int* rows, int n, int dbase, float* h, float* l) {
+    const int lane = threadIdx.x & 31;
+    constexpr int U = Q != 0 ? 16 : 8;  // 4 KB per warp in flight
+    for (int q0 = 0; q0 < n; q0 += U) {
+        float v[U][4];
+        uint2 hq[U];  // Q != 0: four raw 16-bit values
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[u][j] = 0.f;
+            hq[u] = make_uint2(0u, 0u);
+            if (q0 + u < n) {
+                const int row = rows[q0 + u];
+                const float* x = X + (int64_t)row * D + dbase;
+                if (Q != 0) {  // rows padded to Dq: the four values are in bounds
+                    if (dbase + lane * 4 < D)
+                        hq[u] = __ldg(reinterpret_cast<const uint2*>(Xq + (int64_t)row * Dq + dbase + 4 * lane));
+                } else if (VEC) {
+                    if (dbase + lane * 4 < D) {
+                        const float4 f = __ldg(reinterpret_cast<const float4*>(x) + lane);
+                        v[u][0] = f.x; v[u][1] = f.y; v[u][2] = f.z; v[u][3] = f.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) v[u][j] = (dbase + lane + 32 * j < D) ? __ldg(x + lane + 32 * j) : 0.f;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (q0 + u >= n) break;
+            if (Q != 0) {
+                v[u][0] = q16_to_float<Q>(hq[u].x & 0xFFFFu);
+                v[u][1] = q16_to_float<Q>(hq[u].x >> 16);
+                v[u][2] = q16_to_float<Q>(hq[u].y & 0xFFFFu);
+                v[u][3] = q16_to_float<Q>(hq[u].y >> 16);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {  // TwoSum: s + err == h + v exactly
+                const float s = __fadd_rn(h[j], v[u][j]);
+                const float bp = __fsub_rn(s, h[j]);
+                const float err = __fadd_rn(__fsub_rn(h[j], __fsub_rn(s, bp)), __fsub_rn(v[u][j], bp));
+                h[j] = s;
+                l[j] = __fadd_rn(l[j], err);
+            }
+        }
+    }
+}
+
+// Accumulates the warp's run [w0, w1) of one tile: each chunk of 32
+// positions is split by side (rows[]: the left rows, then the right ones,
+// both in position order) so that each side's sums take its rows in
+// ascending positions without per-row selects.
+template <bool VEC, int Q>
+__device__ __forceinline__ void sums_run(const float* __restrict__ X, int D, const uint16_t* __restrict__ Xq, int Dq,
+                                         const int32_t* __restrict__ perm, const float* __restrict__ S, int a,
+                                         uint64_t T, int pos_bits, int w0, int w1, int dbase, int* rows, float* hL,
+                                         float* lL, float* hR, float* lR) {
+    const int lane = threadIdx.x & 31;
+    for (int c = w0; c < w1; c += 32) {
+        const int p = c + lane;
+        int my_row = 0;
+        bool my_left = false;
+        if (p < w1) {
+            my_row = perm[p];
+            my_left = sel_key(S[p], p - a, pos_bits) < T;
+        }
+        const int cnt = min(32, w1 - c);
+        const unsigned lb = __ballot_sync(0xffffffffu, my_left);
+        const int nl = __popc(lb), before = __popc(lb & ((1u << lane) - 1u));
+        __syncwarp();  // the previous chunk's reads of rows[] are done
+        if (p < w1) rows[my_left ? before : nl + lane - before] = my_row;
+        __syncwarp();
+        sums_side<VEC, Q>(X, D, Xq, Dq, rows, nl, dbase, hL, lL);
+        sums_side<VEC, Q>(X, D, Xq, Dq, rows + nl, cnt - nl, dbase, hR, lR);
+    }
+}
+
 template <bool VEC>
 __global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restrict__ X, int D,
                                                           const int32_t* __restrict__ perm,
@@ -283,9 +408,13 @@ __global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restri
                                                           const int32_t* __restrict__ seg_off,
                                                           const uint64_t* __restrict__ thr, int pos_bits,
                                                           double* __restrict__ partial,
-                                                          const int* __restrict__ status) {
+                                                          const int* __restrict__ status,
+                                                          const uint16_t* __restrict__ Xq, int Dq, int qtype,
+                                                          const int* __restrict__ qflag) {
     __shared__ double red[kSumsWarps][2][128];
+    __shared__ int rows[kSumsWarps][32];
     if (*status & kStatusStop) return;  // perm may hold unwritten slots
+    const int q = q16_usable(Xq, qflag) ? qtype : 0;  // then lane l owns dims 4l .. 4l+3
     const int4 t = tiles[blockIdx.x];
     const int seg = t.x, begin = t.y, end = t.z;
     const int dbase = blockIdx.y * 128;
@@ -301,57 +430,15 @@ __global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restri
     // integer-valued data every add is exact and lo stays 0.
     float hL[4] = {0.f, 0.f, 0.f, 0.f}, lL[4] = {0.f, 0.f, 0.f, 0.f};
     float hR[4] = {0.f, 0.f, 0.f, 0.f}, lR[4] = {0.f, 0.f, 0.f, 0.f};
-    constexpr int U = 8;  // independent rows in flight per warp
-    for (int c = w0; c < w1; c += 32) {
-        // ids and sides of the next 32 positions, one per lane
-        const int p = c + lane;
-        int my_row = 0, my_left = 0;
-        if (p < w1) {
-            my_row = perm[p];
-            my_left = sel_key(S[p], p - a, pos_bits) < T;
-        }
-        const int cnt = min(32, w1 - c);
-        for (int q0 = 0; q0 < cnt; q0 += U) {
-            float v[U][4];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int row = __shfl_sync(0xffffffffu, my_row, (q0 + u) & 31);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) v[u][j] = 0.f;
-                if (q0 + u < cnt) {
-                    const float* x = X + (int64_t)row * D + dbase;
-                    if (VEC) {
-                        if (dbase + lane * 4 < D) {
-                            const float4 f = __ldg(reinterpret_cast<const float4*>(x) + lane);
-                            v[u][0] = f.x; v[u][1] = f.y; v[u][2] = f.z; v[u][3] = f.w;
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            v[u][j] = (dbase + lane + 32 * j < D) ? __ldg(x + lane + 32 * j) : 0.f;
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int left = __shfl_sync(0xffffffffu, my_left, (q0 + u) & 31);
-                if (q0 + u >= cnt) break;
-                float* h = left ? hL : hR;
-                float* l = left ? lL : lR;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float s = __fadd_rn(h[j], v[u][j]);
-                    const float bp = __fsub_rn(s, h[j]);
-                    const float err = __fadd_rn(__fsub_rn(h[j], __fsub_rn(s, bp)), __fsub_rn(v[u][j], bp));
-                    h[j] = s;
-                    l[j] = __fadd_rn(l[j], err);
-                }
-            }
-        }
-    }
+    if (q == 1)
+        sums_run<VEC, 1>(X, D, Xq, Dq, perm, S, a, T, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR, lR);
+    else if (q == 2)
+        sums_run<VEC, 2>(X, D, Xq, Dq, perm, S, a, T, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR, lR);
+    else
+        sums_run<VEC, 0>(X, D, Xq, Dq, perm, S, a, T, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR, lR);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int dl = VEC ? lane * 4 + j : lane + 32 * j;
+        const int dl = (VEC || q != 0) ? lane * 4 + j : lane + 32 * j;
         red[warp][0][dl] = (double)hL[j] + (double)lL[j];
         red[warp][1][dl] = (double)hR[j] + (double)lR[j];
     }
@@ -455,10 +542,10 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
             SelState* st = lp.small ? nullptr : b.st;
             if (vec2)
                 k1_project<true><<<lp.nsweep, 256, 0, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S, st,
-                                                           b.status);
+                                                           b.status, b.Xq, b.Dq, b.qtype, b.qflag);
             else
                 k1_project<false><<<lp.nsweep, 256, 0, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S, st,
-                                                            b.status);
+                                                            b.status, b.Xq, b.Dq, b.qtype, b.qflag);
         }
         if (lp.small) {
             const size_t smem = (size_t)lp.max_m * sizeof(uint64_t);
@@ -493,10 +580,12 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
             dim3 grid(lp.ntiles, dchunks);
             if (vec)
                 k1_sums<true><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr,
-                                                               lp.pos_bits, b.partial, b.status);
+                                                               lp.pos_bits, b.partial, b.status, b.Xq, b.Dq,
+                                                               b.qtype, b.qflag);
             else
                 k1_sums<false><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr,
-                                                                lp.pos_bits, b.partial, b.status);
+                                                                lp.pos_bits, b.partial, b.status, b.Xq, b.Dq,
+                                                                b.qtype, b.qflag);
         }
         {
             LaunchScope ls("k1_centroids", s, (double)lp.ntiles * 2 * D * 8 + (double)lp.nseg * D * 4, 0);
