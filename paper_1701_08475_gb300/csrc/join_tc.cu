@@ -12,9 +12,10 @@
 // One CTA packs NPC nodes: node j's members N_i = G_old[i] (+ R[i]) occupy
 // tile rows j * mcap .. j * mcap + M_j - 1.  Their 16-bit rows are gathered
 // into the 128-byte-swizzled K-major layout with cp.async, one thread issues
-// the 128 x 128 x Dp Gram on the tensor cores, and in the epilogue thread r
-// (= tensor-memory lane r) offers every pair {u, v} of its node with v after
-// u, in both directions, when the offer beats the target's k-th entry.
+// the 128 x 128 x Dp Gram on the tensor cores, and in the epilogue the two
+// threads of tile row r (= tensor-memory lane r) evaluate an equal share of
+// the node's pairs {u, v}, offering each in both directions when the offer
+// beats the target's k-th entry.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -28,7 +29,7 @@ namespace {
 constexpr int kRows = 128;
 constexpr int kKc = 64;                  // 16-bit elements per swizzled row
 constexpr int kChunkBytes = kRows * kKc * 2;
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;  // two threads per tile row in the epilogue
 
 __device__ __forceinline__ bool lp_exact_flag(int f) { return (f & 1) == 0 && !((f & 2) && (f & 4)); }
 
@@ -52,7 +53,7 @@ __host__ __device__ inline JtSmem jt_smem(int Dp, int mcap) {
 
 // Persistent: CTA b takes node groups b, b + gridDim.x, ...; tensor memory
 // and the barrier are set up once.
-__global__ void __launch_bounds__(kThreads, 1) k5_join_tc(const uint16_t* __restrict__ Xq, int Dp,
+__global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __restrict__ Xq, int Dp,
                                                          const float* __restrict__ nrm, int k, int rev, int mcap,
                                                          int npc, const uint64_t* __restrict__ Gold,
                                                          const uint64_t* __restrict__ R, int64_t node0,
@@ -154,74 +155,76 @@ __global__ void __launch_bounds__(kThreads, 1) k5_join_tc(const uint16_t* __rest
         tc::fence_after_sync();
         if (!ok) break;
 
-        // ---- epilogue: thread r = row r of the tile
-        const int r = tid;
+        // ---- epilogue: row r of the tile is member s of node j.  Threads r
+        // and r + 128 (warps w and w + 4 read the same tensor-memory lanes)
+        // share the row: each copies half of its Gram values to priv[t][r].
+        const int r = tid & (kRows - 1), h = tid >> 7;
         const int j = r / mcap, s = r - j * mcap;
         const int Mj = j < npc ? mcount[j] : 0;
         const bool mine = s < Mj;
-        // this row's Gram values against its node's members -> private column
 #pragma unroll 1
-        for (int cc = 0; cc < kRows / 32; ++cc) {
+        for (int cc = 2 * h; cc < 2 * h + 2; ++cc) {
             float g[32];
-            tc::tmem_ld_32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), g);
+            tc::tmem_ld_32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(cc * 32), g);
             if (mine) {
 #pragma unroll
                 for (int jj = 0; jj < 32; ++jj) {
                     const int t = cc * 32 + jj - j * mcap;
-                    if (t > s && t < Mj) priv[t * kRows + r] = g[jj];
+                    if (t >= 0 && t < Mj) priv[t * kRows + r] = g[jj];
                 }
             }
         }
+        tc::fence_before_sync();
+        __syncthreads();
+        // Pair {s, t} of the node belongs to row s when t = s + delta (mod Mj)
+        // with 1 <= delta < Mj / 2, or delta = Mj / 2 (Mj even) and s < Mj / 2:
+        // every pair once, every row (Mj - 1) / 2 or Mj / 2 of them.  Thread h
+        // takes delta = 1 + h, 3 + h, ...; bit 2i (2i + 1) of `hit` says that
+        // its i-th pair offers v to u (u to v).
         const uint32_t u = mine ? (uint32_t)mem[r] : 0u;
         const uint64_t thr_u = thr[r];
         const float nu = snrm[r];
-        // pass 0 counts the offers, pass 1 writes them
-        int cnt = 0;
-        uint32_t w = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            if (pass == 1) {
-                int x = cnt;
+        const int Hs = mine ? (Mj - 1) / 2 + ((Mj % 2 == 0 && 2 * s < Mj) ? 1 : 0) : 0;
+        uint64_t hit = 0;
+        for (int dl = 1 + h, i = 0; dl <= Hs; dl += 2, ++i) {
+            const int t = s + dl < Mj ? s + dl : s + dl - Mj;
+            const int col = j * mcap + t;
+            const uint32_t v = (uint32_t)mem[col];
+            if (v == u) continue;
+            const float d = __fadd_rn(__fsub_rn(__fadd_rn(nu, snrm[col]), __fmul_rn(2.f, priv[t * kRows + r])), 0.f);
+            const bool ou = make_key(d, v) < thr_u, ov = make_key(d, u) < thr[col];
+            hit |= ((uint64_t)ou << (2 * i)) | ((uint64_t)ov << (2 * i + 1));
+        }
+        // one slot range per warp, then the offers themselves
+        const int cnt = __popcll(hit);
+        int x = cnt;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x += y;
-                }
-                const int total = __shfl_sync(0xffffffffu, x, 31);
-                uint32_t at = 0;
-                if (lane == 31 && total > 0) at = atomicAdd(counter, (uint32_t)total);
-                at = __shfl_sync(0xffffffffu, at, 31);
-                if (total == 0) break;
-                if ((int64_t)at + total > cap) {
-                    if (lane == 0) atomicOr(status, kStatusOverflow);
-                    break;
-                }
-                w = at + x - cnt;
-            }
-            for (int t = s + 1; mine && t < Mj; ++t) {
-                const int col = j * mcap + t;
-                const uint32_t v = (uint32_t)mem[col];
-                if (v == u) continue;
-                const float d = __fadd_rn(__fsub_rn(__fadd_rn(nu, snrm[col]), __fmul_rn(2.f, priv[t * kRows + r])), 0.f);
-                const uint64_t ku = make_key(d, v);
-                const uint64_t kv = make_key(d, u);
-                const bool ou = ku < thr_u, ov = kv < thr[col];
-                if (pass == 0) {
-                    cnt += (int)ou + (int)ov;
-                } else {
-                    if (ou) {
-                        ptgt[w] = u;
-                        pkey[w] = ku;
-                        ++w;
-                        atomicAdd(&pcnt[u], 1);
-                    }
-                    if (ov) {
-                        ptgt[w] = v;
-                        pkey[w] = kv;
-                        ++w;
-                        atomicAdd(&pcnt[v], 1);
-                    }
-                }
-            }
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, x, 31);
+        uint32_t at = 0;
+        if (lane == 31 && total > 0) at = atomicAdd(counter, (uint32_t)total);
+        at = __shfl_sync(0xffffffffu, at, 31);
+        if (total > 0 && (int64_t)at + total > cap) {
+            if (lane == 0) atomicOr(status, kStatusOverflow);
+            hit = 0;
+        }
+        uint32_t w = at + x - cnt;
+        while (hit != 0) {
+            const int b = __ffsll((long long)hit) - 1;
+            hit &= hit - 1;
+            const int dl = 1 + h + 2 * (b >> 1);
+            const int t = s + dl < Mj ? s + dl : s + dl - Mj;
+            const int col = j * mcap + t;
+            const uint32_t v = (uint32_t)mem[col];
+            const float d = __fadd_rn(__fsub_rn(__fadd_rn(nu, snrm[col]), __fmul_rn(2.f, priv[t * kRows + r])), 0.f);
+            const uint32_t tgt = (b & 1) ? v : u;
+            ptgt[w] = tgt;
+            pkey[w] = make_key(d, (b & 1) ? u : v);
+            ++w;
+            atomicAdd(&pcnt[tgt], 1);
         }
         // all tensor-memory reads and shared-memory uses of this group done
         tc::fence_before_sync();
