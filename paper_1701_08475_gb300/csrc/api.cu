@@ -500,7 +500,12 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
             b.jb.cur = ws.take<int32_t>(n);
             b.jb.rbuf = ws.take<uint64_t>((size_t)n * k);
             b.jb.R = ws.take<uint64_t>((size_t)n * k);
+            b.jb.R2 = ws.take<uint64_t>((size_t)n * k);
+            b.jb.rnew_buf = ws.take<uint64_t>(n);
         }
+        b.jb.fnew_buf = ws.take<uint64_t>(n);
+        b.jb.active = ws.take<int32_t>(n);
+        b.jb.nactive = ws.take<int32_t>(4);
         b.jb.pcnt = ws.take<int32_t>(n + 1);
         b.jb.poff = ws.take<int32_t>(n + 1);
         b.jb.pcur = ws.take<int32_t>(n);
@@ -591,11 +596,8 @@ void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& t
         }
         if (!done) launch_leaf_fp32(X, a.D, perm, leaf_off, nleaf, tp.max_leaf, k, b.G, b.status, s);
     }
-    for (int r = 0; r < a.p.refine_rounds; ++r) {
-        run_join_round(X, n, a.D, k, a.p.join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, b.jb, b.nodes_per_chunk,
-                       b.status, s);
-        std::swap(b.G, b.G2);
-    }
+    run_refine(X, n, a.D, k, a.p.join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, b.jb, b.nodes_per_chunk,
+               a.p.refine_rounds, b.status, s);
 }
 
 }  // namespace
@@ -719,11 +721,8 @@ int knng_refine(const float* data, int64_t n, int D, const knng_params* p, int32
         launch_pack(gi.dev, gd.dev, b.G, (int64_t)nk, n, b.status, s);
         if (b.notexact) cuda_check(cudaMemsetAsync(b.notexact, 0, sizeof(int), s), "flag clear");
         quantize_for_join(X.dev, a, b, s);
-        for (int r = 0; r < p->refine_rounds; ++r) {
-            run_join_round(X.dev, n, D, p->k, p->join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, b.jb,
-                           b.nodes_per_chunk, b.status, s);
-            std::swap(b.G, b.G2);
-        }
+        run_refine(X.dev, n, D, p->k, p->join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, b.jb, b.nodes_per_chunk,
+                   p->refine_rounds, b.status, s);
         launch_unpack(b.G, gi.dev, gd.dev, (int64_t)nk, s);
         download(gi, s);
         download(gd, s);

@@ -11,6 +11,8 @@
 //                     could never enter the target's list)
 //   scatter           group the offers by target (counts, prefix sum)
 //   K4 merge          G_new[u] = first k unique of G_old[u] + offers to u
+#include <utility>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -206,6 +208,88 @@ __global__ void __launch_bounds__(256) k6_select(const uint64_t* __restrict__ rb
         if (lane + 32 * o < k) R[i * k + lane + 32 * o] = run[o];
 }
 
+// Whether `key` is one of the sorted keys list[0 .. k).
+__device__ __forceinline__ bool sorted_has(const uint64_t* list, int k, uint64_t key) {
+    int lo = 0, len = k;
+    while (len > 0) {
+        const int half = len >> 1;
+        if (list[lo + half] < key) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo < k && list[lo] == key;
+}
+
+// Member flags of one round.  A member of node i (an entry of G_old[i] or of
+// R[i]) is old when the same key was a member of i in the previous round
+// (in G_prev[i] or R_prev[i]): both directions of a pair of old members were
+// offered then, and such an offer is now either in its target's list already
+// or beaten by the target's k-th entry (which never gets worse), so the join
+// may skip the pair without changing the result.  One warp per node; bit e of
+// fnew[i] (rnew[i]) marks entry e of G_old[i] (R[i]) new; nodes with a new
+// member are appended to `active` (one atomic per block).
+constexpr int kFlagWarps = 16;
+template <int NO>
+__global__ void __launch_bounds__(32 * kFlagWarps) k6_flags(const uint64_t* __restrict__ Gcur,
+                                                            const uint64_t* __restrict__ Rcur,
+                                                            const uint64_t* __restrict__ Gprev,
+                                                            const uint64_t* __restrict__ Rprev, int64_t n, int k,
+                                                            uint64_t* __restrict__ fnew, uint64_t* __restrict__ rnew,
+                                                            int32_t* __restrict__ active,
+                                                            int32_t* __restrict__ nactive) {
+    __shared__ uint64_t prev[kFlagWarps][2][32 * NO];
+    __shared__ int act[kFlagWarps];
+    __shared__ int base;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * kFlagWarps + w;
+    int on = 0;
+    if (i < n) {
+        uint64_t* pg = prev[w][0];
+        uint64_t* pr = prev[w][1];
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+            const int e = lane + 32 * o;
+            pg[e] = e < k ? Gprev[i * k + e] : kEmptyKey;
+            pr[e] = (Rprev && e < k) ? Rprev[i * k + e] : kEmptyKey;
+        }
+        __syncwarp();
+        uint64_t fb = 0, rb = 0;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+            const int e = lane + 32 * o;
+            uint64_t key = e < k ? Gcur[i * k + e] : kEmptyKey;
+            bool nw = key != kEmptyKey && !sorted_has(pg, k, key) && !(Rprev && sorted_has(pr, k, key));
+            fb |= (uint64_t)__ballot_sync(0xffffffffu, nw) << (32 * o);
+            if (Rcur) {
+                key = e < k ? Rcur[i * k + e] : kEmptyKey;
+                nw = key != kEmptyKey && !sorted_has(pg, k, key) && !(Rprev && sorted_has(pr, k, key));
+                rb |= (uint64_t)__ballot_sync(0xffffffffu, nw) << (32 * o);
+            }
+        }
+        if (lane == 0) {
+            fnew[i] = fb;
+            if (Rcur) rnew[i] = rb;
+        }
+        on = (fb | rb) != 0;
+    }
+    if (lane == 0) act[w] = on;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int q = 0; q < kFlagWarps; ++q) c += act[q];
+        base = c > 0 ? atomicAdd(nactive, c) : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int at = base;
+        for (int q = 0; q < kFlagWarps; ++q)
+            if (act[q]) active[at++] = (int32_t)((int64_t)blockIdx.x * kFlagWarps + q);
+    }
+}
+
 // ---------------------------------------------------------------- K5
 // One warp per node i.  Members N_i in shared memory; the upper triangle of
 // member pairs is cut into 4 x 4 blocks, BPL blocks per lane; distances are
@@ -226,10 +310,22 @@ __host__ __device__ inline void join_chunk(int D, int mcap, int* dch, int* strid
     *stride = ((c / 4) & 1) ? c : c + 4;
 }
 
+// Whether entry (a, b) of block row ia, column ib is a pair to evaluate:
+// in the rectangle ia is a new member and ib any later member or an old one;
+// in the triangle `upper` says the entry is above the diagonal.  Pairs of
+// two old members (indices >= nn) are skipped.
+__device__ __forceinline__ bool pair_live(bool rect, int ia, int ib, int M, int nn, bool upper) {
+    if (rect) return ia < nn && ib < M && (ib >= nn || ib > ia);
+    return ia < M && ib < M && upper && (ia < nn || ib < nn);
+}
+
 template <int BPL>
 __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restrict__ X, int D, int k, int rev,
                                                           int mcap, const uint64_t* __restrict__ Gold,
-                                                          const uint64_t* __restrict__ R, int64_t node0,
+                                                          const uint64_t* __restrict__ R,
+                                                          const int32_t* __restrict__ list,
+                                                          const uint64_t* __restrict__ fnew,
+                                                          const uint64_t* __restrict__ rnew, int64_t node0,
                                                           int64_t node1, uint32_t* __restrict__ counter,
                                                           int64_t cap, uint32_t* __restrict__ ptgt,
                                                           uint64_t* __restrict__ pkey,
@@ -244,35 +340,49 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
     uint64_t* thr = reinterpret_cast<uint64_t*>(xs + (size_t)mcap * stride);      // [mcap]
     int32_t* mem = reinterpret_cast<int32_t*>(thr + mcap);                        // [mcap]
 
-    const int64_t i = node0 + (int64_t)blockIdx.x * kJoinWarps + warp;
-    if (i >= node1 || (*status & kStatusStop)) return;
+    const int64_t pos = node0 + (int64_t)blockIdx.x * kJoinWarps + warp;
+    if (pos >= node1 || (*status & kStatusStop)) return;
+    const int64_t i = list ? (int64_t)list[pos] : pos;
     // the tensor-core join does this round when the 16-bit copy is exact
     if (skip_if_exact) {
         const int f = *skip_if_exact;
         if ((f & 1) == 0 && !((f & 2) && (f & 4))) return;
     }
-    // members: real ids of G_old[i], then of R[i]
-    int M = 0;
-    for (int src = 0; src < (rev ? 2 : 1); ++src) {
-        const uint64_t* row = (src == 0 ? Gold : R) + i * k;
-        for (int e0 = 0; e0 < k; e0 += 32) {
-            const int e = e0 + lane;
-            const uint64_t key = e < k ? row[e] : kEmptyKey;
-            const bool real = key != kEmptyKey;
-            const unsigned bal = __ballot_sync(0xffffffffu, real);
-            if (real) {
-                const int pos = M + __popc(bal & ((1u << lane) - 1u));
-                const uint32_t u = key_id(key);
-                mem[pos] = (int32_t)u;
-                thr[pos] = Gold[(int64_t)u * k + k - 1];
+    // members: the new ones first (flags from the previous round; none =
+    // all new), then the old ones; each takes ids of G_old[i], then of R[i]
+    int M = 0, nn = 0;
+    const uint64_t fbits = fnew ? fnew[i] : ~0ull, rbits = rnew ? rnew[i] : ~0ull;
+    for (int want = 1; want >= 0; --want) {
+        for (int src = 0; src < (rev ? 2 : 1); ++src) {
+            const uint64_t* row = (src == 0 ? Gold : R) + i * k;
+            const uint64_t bits = src == 0 ? fbits : rbits;
+            for (int e0 = 0; e0 < k; e0 += 32) {
+                const int e = e0 + lane;
+                const uint64_t key = e < k ? row[e] : kEmptyKey;
+                const bool take = key != kEmptyKey && (int)((bits >> e) & 1ull) == want;
+                const unsigned bal = __ballot_sync(0xffffffffu, take);
+                if (take) {
+                    const int at = M + __popc(bal & ((1u << lane) - 1u));
+                    const uint32_t u = key_id(key);
+                    mem[at] = (int32_t)u;
+                    thr[at] = Gold[(int64_t)u * k + k - 1];
+                }
+                M += __popc(bal);
             }
-            M += __popc(bal);
         }
+        if (want == 1) nn = M;
     }
     __syncwarp();
-    if (M < 2) return;
+    if (M < 2 || nn == 0) return;
+    // Pairs with a new member: the upper triangle of all members cut into
+    // 4 x 4 blocks, or, when fewer blocks do, the rectangle new x all (rows
+    // 0 .. nn-1 against every member, each new x new pair kept once).
     const int RGN = (M + 3) >> 2;
-    const int nb = RGN * (RGN + 1) / 2;
+    const int nb_tri = RGN * (RGN + 1) / 2;
+    const int RBN = (nn + 3) >> 2;
+    const bool rect = RBN * RGN < nb_tri;
+    const int nb = rect ? RBN * RGN : nb_tri;
+    const int RSTEP = rect ? RBN : RGN;  // member index step between a block's rows
     int brg[BPL], bcg[BPL];
 #pragma unroll
     for (int q = 0; q < BPL; ++q) {
@@ -280,13 +390,18 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
         brg[q] = -1;
         bcg[q] = 0;
         if (b < nb) {
-            int rg = 0;
-            while (b >= RGN - rg) {
-                b -= RGN - rg;
-                ++rg;
+            if (rect) {
+                brg[q] = b / RGN;
+                bcg[q] = b - brg[q] * RGN;
+            } else {
+                int rg = 0;
+                while (b >= RGN - rg) {
+                    b -= RGN - rg;
+                    ++rg;
+                }
+                brg[q] = rg;
+                bcg[q] = rg + b;
             }
-            brg[q] = rg;
-            bcg[q] = rg + b;
         }
     }
     float acc[BPL][4][4];
@@ -328,13 +443,13 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
             if (brg[q] < 0) continue;
             const float* rp = xs + brg[q] * stride;
             const float* cp = xs + bcg[q] * stride;
-            const int step = RGN * stride;
+            const int rstep = RSTEP * stride, cstep = RGN * stride;
             for (int dq = 0; dq < dch; dq += 4) {
                 float4 rv[4], cv[4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) rv[a] = *reinterpret_cast<const float4*>(rp + a * step + dq);
+                for (int a = 0; a < 4; ++a) rv[a] = *reinterpret_cast<const float4*>(rp + a * rstep + dq);
 #pragma unroll
-                for (int b = 0; b < 4; ++b) cv[b] = *reinterpret_cast<const float4*>(cp + b * step + dq);
+                for (int b = 0; b < 4; ++b) cv[b] = *reinterpret_cast<const float4*>(cp + b * cstep + dq);
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -352,8 +467,9 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
         }
         __syncwarp();
     }
-    // offers: count, reserve, write.  Every unordered member pair lies in
-    // exactly one block once diagonal blocks keep only a < b.
+    // offers: count, reserve, write.  In the triangle every unordered member
+    // pair lies in exactly one block once diagonal blocks keep only a < b;
+    // pairs of two old members are dropped.
     int cnt = 0;
 #pragma unroll
     for (int q = 0; q < BPL; ++q) {
@@ -362,8 +478,8 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int ia = brg[q] + a * RGN, ib = bcg[q] + b * RGN;
-                if (ia < M && ib < M && (brg[q] < bcg[q] || a < b)) {
+                const int ia = brg[q] + a * RSTEP, ib = bcg[q] + b * RGN;
+                if (pair_live(rect, ia, ib, M, nn, brg[q] < bcg[q] || a < b)) {
                     const uint32_t u = (uint32_t)mem[ia], v = (uint32_t)mem[ib];
                     if (u != v) {
                         cnt += make_key(acc[q][a][b], v) < thr[ia];
@@ -390,8 +506,8 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int ia = brg[q] + a * RGN, ib = bcg[q] + b * RGN;
-                if (ia < M && ib < M && (brg[q] < bcg[q] || a < b)) {
+                const int ia = brg[q] + a * RSTEP, ib = bcg[q] + b * RGN;
+                if (pair_live(rect, ia, ib, M, nn, brg[q] < bcg[q] || a < b)) {
                     const uint32_t u = (uint32_t)mem[ia], v = (uint32_t)mem[ib];
                     if (u != v) {
                         const uint64_t ku = make_key(acc[q][a][b], v);
@@ -577,15 +693,18 @@ size_t join_smem_bytes(int D, int mcap) {
     return (size_t)kJoinWarps * ((size_t)mcap * (stride * 4 + 12) + 16);
 }
 
-void run_join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold, uint64_t* Gnew,
-                    const JoinBuffers& b, int64_t nodes_per_chunk, int* status, cudaStream_t s) {
+namespace {
+
+// One refinement round over the nodes at positions [0, count) of b.list
+// (all nodes when b.list is NULL): reads Gold (and b.R), writes Gnew.
+void join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold, uint64_t* Gnew,
+                const JoinBuffers& b, int64_t count, int64_t nodes_per_chunk, int* status, cudaStream_t s) {
     cudaMemcpyAsync(Gnew, Gold, sizeof(uint64_t) * n * k, cudaMemcpyDeviceToDevice, s);
-    if (rev) launch_reverse_lists(Gold, n, k, b, s);
     const int mcap = ((rev ? 2 * k : k) + 3) & ~3;
     const int bpl = join_blocks_per_lane(mcap);
     const size_t smem = join_smem_bytes(D, mcap);
-    for (int64_t c0 = 0; c0 < n; c0 += nodes_per_chunk) {
-        const int64_t c1 = c0 + nodes_per_chunk < n ? c0 + nodes_per_chunk : n;
+    for (int64_t c0 = 0; c0 < count; c0 += nodes_per_chunk) {
+        const int64_t c1 = c0 + nodes_per_chunk < count ? c0 + nodes_per_chunk : count;
         cudaMemsetAsync(b.pcnt, 0, sizeof(int32_t) * (n + 1), s);
         cudaMemsetAsync(b.pcur, 0, sizeof(int32_t) * n, s);
         cudaMemsetAsync(b.counter, 0, sizeof(uint32_t), s);
@@ -601,8 +720,9 @@ void run_join_round(const float* X, int64_t n, int D, int k, bool rev, const uin
 #define KNNG_JOIN(BPL)                                                                                     \
     do {                                                                                                   \
         cudaFuncSetAttribute(k5_join<BPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
-        k5_join<BPL><<<grid, 32 * kJoinWarps, smem, s>>>(X, D, k, rev ? 1 : 0, mcap, Gold, b.R, c0, c1,     \
-                                                         b.counter, b.cap, b.ptgt, b.pkey, b.pcnt, status,  \
+        k5_join<BPL><<<grid, 32 * kJoinWarps, smem, s>>>(X, D, k, rev ? 1 : 0, mcap, Gold, b.R, b.list,     \
+                                                         b.fnew, b.rnew, c0, c1, b.counter, b.cap, b.ptgt,  \
+                                                         b.pkey, b.pcnt, status,                            \
                                                          tc_launched ? b.notexact : nullptr);               \
     } while (0)
             if (bpl <= 1) KNNG_JOIN(1);
@@ -626,6 +746,44 @@ void run_join_round(const float* X, int64_t n, int D, int k, bool rev, const uin
             else
                 k4_merge<1><<<grid, 256, 0, s>>>(Gnew, b.grouped, b.poff, n, k, status);
         }
+    }
+}
+
+}  // namespace
+
+void run_refine(const float* X, int64_t n, int D, int k, bool rev, uint64_t*& G, uint64_t*& G2,
+                const JoinBuffers& jb, int64_t nodes_per_chunk, int rounds, int* status, cudaStream_t s) {
+    JoinBuffers b = jb;
+    for (int r = 0; r < rounds; ++r) {
+        if (rev) launch_reverse_lists(G, n, k, b, s);  // into b.R; b.R2 keeps the previous round's
+        b.list = nullptr;
+        b.fnew = b.rnew = nullptr;
+        int64_t count = n;
+        if (r > 0) {
+            // G2 still holds the previous round's G_old
+            cudaMemsetAsync(b.nactive, 0, sizeof(int32_t), s);
+            {
+                LaunchScope ls("k6_flags", s, n * k * 8.0 * (rev ? 4.0 : 2.0) + n * 20.0, 0);
+                const int grid = (int)((n + kFlagWarps - 1) / kFlagWarps);
+                if (k > 32)
+                    k6_flags<2><<<grid, 32 * kFlagWarps, 0, s>>>(G, rev ? b.R : nullptr, G2, rev ? b.R2 : nullptr,
+                                                                 n, k, b.fnew_buf, b.rnew_buf, b.active, b.nactive);
+                else
+                    k6_flags<1><<<grid, 32 * kFlagWarps, 0, s>>>(G, rev ? b.R : nullptr, G2, rev ? b.R2 : nullptr,
+                                                                 n, k, b.fnew_buf, b.rnew_buf, b.active, b.nactive);
+            }
+            int32_t h = 0;
+            cudaMemcpyAsync(&h, b.nactive, sizeof h, cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            count = h;
+            b.list = b.active;
+            b.fnew = b.fnew_buf;
+            b.rnew = rev ? b.rnew_buf : nullptr;
+            record_items("k6_flags", (double)count);
+        }
+        join_round(X, n, D, k, rev, G, G2, b, count, nodes_per_chunk, status, s);
+        std::swap(G, G2);
+        if (rev) std::swap(b.R, b.R2);
     }
 }
 

@@ -45,10 +45,53 @@ __host__ __device__ inline JtSmem jt_smem(int Dp, int mcap) {
     L.thr = L.mem + kRows * 4;
     L.nrm = L.thr + kRows * 8;
     L.cnt = L.nrm + kRows * 4;
-    L.bar = L.cnt + 16 * 4;
+    L.bar = L.cnt + 32 * 4;  // member counts, then new-member counts
     L.slot = L.bar + 8;
     L.total = L.slot + 8;
     return L;
+}
+
+// Flat enumeration of the pairs of a node whose members are nn new ones
+// (indices 0 .. nn-1) followed by no old ones.  p < nn * no is the new x old
+// pair (p / no, nn + p % no); then the new x new pairs {a, a + 1 + c mod nn}
+// for c < (nn - 1) / 2, row by row; then, for even nn, {a, a + nn / 2} with
+// a < nn / 2.  Every unordered pair with a new member appears once.
+__device__ __forceinline__ int small_div(int p, int d, float rd) {
+    // p < 2^15, d <= 128: the estimate is off by at most one
+    int q = __float2int_rz((float)p * rd);
+    const int rem = p - q * d;
+    if (rem < 0) --q;
+    else if (rem >= d) ++q;
+    return q;
+}
+struct PairMap {
+    int nn, no, H, PO, PC;
+    float rno, rH;
+    __device__ __forceinline__ void decode(int p, int& a, int& b) const {
+        if (p < PO) {
+            a = small_div(p, no, rno);
+            b = nn + (p - a * no);
+        } else if (p - PO < PC) {
+            const int q = p - PO;
+            a = small_div(q, H, rH);
+            const int t = a + 1 + (q - a * H);
+            b = t >= nn ? t - nn : t;
+        } else {
+            a = p - PO - PC;
+            b = a + nn / 2;
+        }
+    }
+};
+__device__ __forceinline__ PairMap pair_map(int nn, int no) {
+    PairMap m;
+    m.nn = nn;
+    m.no = no;
+    m.H = nn > 0 ? (nn - 1) / 2 : 0;
+    m.PO = nn * no;
+    m.PC = nn * m.H;
+    m.rno = no > 0 ? 1.f / (float)no : 0.f;
+    m.rH = m.H > 0 ? 1.f / (float)m.H : 0.f;
+    return m;
 }
 
 // Persistent: CTA b takes node groups b, b + gridDim.x, ...; tensor memory
@@ -56,7 +99,10 @@ __host__ __device__ inline JtSmem jt_smem(int Dp, int mcap) {
 __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __restrict__ Xq, int Dp,
                                                          const float* __restrict__ nrm, int k, int rev, int mcap,
                                                          int npc, const uint64_t* __restrict__ Gold,
-                                                         const uint64_t* __restrict__ R, int64_t node0,
+                                                         const uint64_t* __restrict__ R,
+                                                         const int32_t* __restrict__ list,
+                                                         const uint64_t* __restrict__ fnew,
+                                                         const uint64_t* __restrict__ rnew, int64_t node0,
                                                          int64_t node1, uint32_t* __restrict__ counter, int64_t cap,
                                                          uint32_t* __restrict__ ptgt, uint64_t* __restrict__ pkey,
                                                          int32_t* __restrict__ pcnt, int* __restrict__ status,
@@ -94,24 +140,34 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
         const int64_t first = node0 + grp * npc;
         for (int r = tid; r < kRows; r += kThreads) mem[r] = -1;
         __syncthreads();
-        // members of the group's nodes (warp j collects node j)
+        // members of the group's nodes (warp j collects node j): the new ones
+        // first, then the old ones (flags from the previous round; none = all new)
         for (int j = warp; j < npc; j += kThreads / 32) {
-            const int64_t i = first + j;
-            int M = 0;
-            if (i < node1) {
-                for (int src = 0; src < (rev ? 2 : 1); ++src) {
-                    const uint64_t* row = (src == 0 ? Gold : R) + i * k;
-                    for (int e0 = 0; e0 < k; e0 += 32) {
-                        const int e = e0 + lane;
-                        const uint64_t key = e < k ? row[e] : kEmptyKey;
-                        const bool real = key != kEmptyKey;
-                        const unsigned bal = __ballot_sync(0xffffffffu, real);
-                        if (real) mem[j * mcap + M + __popc(bal & ((1u << lane) - 1u))] = (int32_t)key_id(key);
-                        M += __popc(bal);
+            const int64_t pos = first + j;
+            int M = 0, nn = 0;
+            if (pos < node1) {
+                const int64_t i = list ? (int64_t)list[pos] : pos;
+                const uint64_t fb = fnew ? fnew[i] : ~0ull, rb = rnew ? rnew[i] : ~0ull;
+                for (int want = 1; want >= 0; --want) {
+                    for (int src = 0; src < (rev ? 2 : 1); ++src) {
+                        const uint64_t* row = (src == 0 ? Gold : R) + i * k;
+                        const uint64_t bits = src == 0 ? fb : rb;
+                        for (int e0 = 0; e0 < k; e0 += 32) {
+                            const int e = e0 + lane;
+                            const uint64_t key = e < k ? row[e] : kEmptyKey;
+                            const bool take = key != kEmptyKey && (int)((bits >> e) & 1ull) == want;
+                            const unsigned bal = __ballot_sync(0xffffffffu, take);
+                            if (take) mem[j * mcap + M + __popc(bal & ((1u << lane) - 1u))] = (int32_t)key_id(key);
+                            M += __popc(bal);
+                        }
                     }
+                    if (want == 1) nn = M;
                 }
             }
-            if (lane == 0) mcount[j] = M;
+            if (lane == 0) {
+                mcount[j] = M;
+                mcount[16 + j] = nn;
+            }
         }
         __syncthreads();
         // gather the member rows (16-byte pieces) into the swizzled K-major tile;
@@ -176,24 +232,24 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
         }
         tc::fence_before_sync();
         __syncthreads();
-        // Pair {s, t} of the node belongs to row s when t = s + delta (mod Mj)
-        // with 1 <= delta < Mj / 2, or delta = Mj / 2 (Mj even) and s < Mj / 2:
-        // every pair once, every row (Mj - 1) / 2 or Mj / 2 of them.  Thread h
-        // takes delta = 1 + h, 3 + h, ...; bit 2i (2i + 1) of `hit` says that
-        // its i-th pair offers v to u (u to v).
-        const uint32_t u = mine ? (uint32_t)mem[r] : 0u;
-        const uint64_t thr_u = thr[r];
-        const float nu = snrm[r];
-        const int Hs = mine ? (Mj - 1) / 2 + ((Mj % 2 == 0 && 2 * s < Mj) ? 1 : 0) : 0;
+        // The pairs to evaluate: new x old (nn * no of them) and new x new
+        // (nn (nn - 1) / 2), flattened and dealt round-robin to the node's
+        // 2 * mcap threads.  Bit 2i (2i + 1) of `hit` says that the thread's
+        // i-th pair {a, b} offers b to a (a to b).
+        const int nn = j < npc ? mcount[16 + j] : 0, no = Mj - nn;
+        const int P = nn * no + nn * (nn - 1) / 2;
+        const int T = 2 * mcap, tix = 2 * s + h, base_row = j * mcap;
+        const PairMap pm = pair_map(nn, no);
         uint64_t hit = 0;
-        for (int dl = 1 + h, i = 0; dl <= Hs; dl += 2, ++i) {
-            const int t = s + dl < Mj ? s + dl : s + dl - Mj;
-            const int col = j * mcap + t;
-            const uint32_t v = (uint32_t)mem[col];
-            if (v == u) continue;
-            const float d = __fadd_rn(__fsub_rn(__fadd_rn(nu, snrm[col]), __fmul_rn(2.f, priv[t * kRows + r])), 0.f);
-            const bool ou = make_key(d, v) < thr_u, ov = make_key(d, u) < thr[col];
-            hit |= ((uint64_t)ou << (2 * i)) | ((uint64_t)ov << (2 * i + 1));
+        for (int p = tix, i = 0; p < P; p += T, ++i) {
+            int a, b;
+            pm.decode(p, a, b);
+            const uint32_t ua = (uint32_t)mem[base_row + a], ub = (uint32_t)mem[base_row + b];
+            if (ua == ub) continue;
+            const float d = __fadd_rn(__fsub_rn(__fadd_rn(snrm[base_row + a], snrm[base_row + b]),
+                                                __fmul_rn(2.f, priv[b * kRows + base_row + a])), 0.f);
+            const bool oa = make_key(d, ub) < thr[base_row + a], ob = make_key(d, ua) < thr[base_row + b];
+            hit |= ((uint64_t)oa << (2 * i)) | ((uint64_t)ob << (2 * i + 1));
         }
         // one slot range per warp, then the offers themselves
         const int cnt = __popcll(hit);
@@ -213,16 +269,16 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
         }
         uint32_t w = at + x - cnt;
         while (hit != 0) {
-            const int b = __ffsll((long long)hit) - 1;
+            const int bit = __ffsll((long long)hit) - 1;
             hit &= hit - 1;
-            const int dl = 1 + h + 2 * (b >> 1);
-            const int t = s + dl < Mj ? s + dl : s + dl - Mj;
-            const int col = j * mcap + t;
-            const uint32_t v = (uint32_t)mem[col];
-            const float d = __fadd_rn(__fsub_rn(__fadd_rn(nu, snrm[col]), __fmul_rn(2.f, priv[t * kRows + r])), 0.f);
-            const uint32_t tgt = (b & 1) ? v : u;
+            int a, b;
+            pm.decode(tix + (bit >> 1) * T, a, b);
+            const uint32_t ua = (uint32_t)mem[base_row + a], ub = (uint32_t)mem[base_row + b];
+            const float d = __fadd_rn(__fsub_rn(__fadd_rn(snrm[base_row + a], snrm[base_row + b]),
+                                                __fmul_rn(2.f, priv[b * kRows + base_row + a])), 0.f);
+            const uint32_t tgt = (bit & 1) ? ub : ua;
             ptgt[w] = tgt;
-            pkey[w] = make_key(d, (b & 1) ? u : v);
+            pkey[w] = make_key(d, (bit & 1) ? ua : ub);
             ++w;
             atomicAdd(&pcnt[tgt], 1);
         }
@@ -254,9 +310,10 @@ bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev
     const int grid = (int)(groups < (int64_t)152 * per_sm ? groups : (int64_t)152 * per_sm);
     const double m = rev ? 2.0 * k : (double)k;
     LaunchScope ls("k5_join_tc", s, (double)nodes * (m * Dp * 2.0 + 2 * k * 8.0 + m * 12.0),
-                   (double)grid * kRows * kRows * 2.0 * Dp);
+                   (double)groups * kRows * kRows * 2.0 * Dp);
     cudaFuncSetAttribute(k5_join_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k5_join_tc<<<grid, kThreads, smem, s>>>(Xq, Dp, nrm, k, rev ? 1 : 0, mcap, npc, Gold, R, node0, node1, b.counter,
+    k5_join_tc<<<grid, kThreads, smem, s>>>(Xq, Dp, nrm, k, rev ? 1 : 0, mcap, npc, Gold, R, b.list, b.fnew, b.rnew,
+                                            node0, node1, b.counter,
                                             b.cap, b.ptgt, b.pkey, b.pcnt, status, notexact, bf16);
     return true;
 }

@@ -116,6 +116,18 @@ struct JoinBuffers {
     uint32_t* counter;   // [1] proposals appended
     int32_t* scan_tmp;   // scan scratch
     unsigned long long* offers_total;  // [1] offers grouped over the whole call (statistics)
+    // member flags between rounds: R2 keeps the previous round's reverse
+    // lists; fnew_buf / rnew_buf [n] bit e marks entry e of G_old[i] / R[i]
+    // new; active [n] lists the nodes with a new member, nactive [1] counts them
+    uint64_t* R2 = nullptr;
+    uint64_t* fnew_buf = nullptr;
+    uint64_t* rnew_buf = nullptr;
+    int32_t* active = nullptr;
+    int32_t* nactive = nullptr;
+    // the current round's view of them (NULL: every node, every member new)
+    const int32_t* list = nullptr;
+    const uint64_t* fnew = nullptr;
+    const uint64_t* rnew = nullptr;
     // tensor-core join (16-bit copy in original order); used when lp is set
     // and, on the device, only when the copy's arithmetic is exact
     bool lp = false, bf16 = true;
@@ -124,8 +136,9 @@ struct JoinBuffers {
     const int* notexact = nullptr;
 };
 
-// The tensor-core local join of nodes [node0, node1); false (nothing
-// launched) when the shape is not supported.
+// The tensor-core local join of the nodes at positions [node0, node1) of
+// b.list (of all nodes when it is NULL); false (nothing launched) when the
+// shape is not supported.
 bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev, const uint64_t* Gold,
                     const uint64_t* R, int64_t node0, int64_t node1, const JoinBuffers& b, int* status,
                     const int* notexact, bool bf16, cudaStream_t s);
@@ -134,10 +147,11 @@ bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev
 void record_items(const char* name, double items);
 
 void launch_reverse_lists(const uint64_t* G, int64_t n, int k, const JoinBuffers& b, cudaStream_t s);
-// One refinement round: reads Gold (and R when rev), writes Gnew.
-void run_join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold,
-                    uint64_t* Gnew, const JoinBuffers& b, int64_t nodes_per_chunk, int* status,
-                    cudaStream_t s);
+// `rounds` refinement rounds on G (G2: the second graph buffer); on return
+// G points at the result.  Rounds after the first skip the member pairs that
+// the previous round already offered.
+void run_refine(const float* X, int64_t n, int D, int k, bool rev, uint64_t*& G, uint64_t*& G2,
+                const JoinBuffers& b, int64_t nodes_per_chunk, int rounds, int* status, cudaStream_t s);
 
 // Exclusive scan of cnt[0..n) into off[0..n], off[n] = total.
 void launch_scan(const int32_t* cnt, int32_t* off, int64_t n, int32_t* tmp, cudaStream_t s);

@@ -210,6 +210,43 @@ def test_refine_from_random_graph_two_rounds(knng):
     _assert_graph_equal(g_ids, g_d, *o)
 
 
+@pytest.mark.parametrize("mode,k,start", [(oracle.FWD_REV, 8, "tree"), (oracle.FWD_REV, 20, "tree"),
+                                          (oracle.FWD, 12, "tree"), (oracle.FWD, 40, "tree"),
+                                          (oracle.FWD_REV, 10, "random"), (oracle.FWD, 16, "random")])
+def test_refine_rounds_skipping_old_pairs_match_oracle(knng, mode, k, start):
+    # rounds after the first skip pairs of two members that the previous round
+    # already joined; every round must still equal the oracle's full join
+    n, D = 2600, 20
+    X = datagen.gaussian_mixture(n, D, 25, seed=k + 31)
+    if start == "tree":
+        ids, d = oracle.build_graph(X, k, max(64, 2 * (k + 1)), passes=1, rounds=0, seed=6)
+    else:
+        rng = np.random.default_rng(k)
+        ids, d = oracle.new_graph(n, k)
+        for i in range(n):
+            for j in rng.choice(np.delete(np.arange(n), i), size=k, replace=False):
+                oracle.list_insert(ids[i], d[i], oracle.dist_f32(X[i], X[j]), j)
+    o = (ids, d)
+    for _ in range(4):
+        o = oracle.refine_round(X, *o, mode=mode)
+    p = knng.default_params(k=k, refine_rounds=4, join_mode=mode)
+    g_ids, g_d = knng.knng_refine(_dev(X), _dev(ids), _dev(d), p)
+    _assert_graph_equal(g_ids, g_d, *o)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("k,mode", [(20, oracle.FWD_REV), (12, oracle.FWD), (48, oracle.FWD)])
+def test_low_precision_rounds_match_oracle(knng, precision, k, mode):
+    # the tensor-core join over four rounds (member flags from the second on)
+    n = 3500
+    X = datagen.sift_like(n, D=96, n_centres=40, seed=k)
+    prec = knng.KNNG_BF16 if precision == "bf16" else knng.KNNG_FP16
+    common = dict(k=k, leaf_max=128, tree_passes=1, refine_rounds=4, seed=3, join_mode=mode)
+    lp_ids, lp_d = knng.knng_build_ex(_dev(X), knng.default_params(precision=prec, **common))
+    o_ids, o_d = oracle.build_graph(X, k, 128, passes=1, rounds=4, seed=3, mode=mode)
+    _assert_graph_equal(lp_ids, lp_d, o_ids, o_d)
+
+
 # ---------------------------------------------------------------- exact, recall
 @pytest.mark.parametrize("n,D,k,s", [(3000, 32, 10, None), (5000, 37, 20, 300), (2000, 200, 50, 150),
                                      (129, 4, 3, None)])
