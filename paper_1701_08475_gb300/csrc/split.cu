@@ -203,6 +203,132 @@ __global__ void __launch_bounds__(256) k1_project(const float* __restrict__ X, i
         project_tile<VEC2, 0>(X, D, Xq, Dq, perm, begin, end, w, S, xs, ws);
 }
 
+// The projection with rows staged by cp.async and double-buffered: while one
+// 128-byte slab of 256 rows (64 dims of the 16-bit copy, or 32 dims of X) is
+// summed, the copies of the next slab are in flight.  Staged rows are 144
+// bytes apart, so the 16-byte reads of 8 consecutive threads cover all 32
+// banks once.  Needs 16-byte aligned rows of X (D a multiple of 4).
+constexpr int kPrRows = 256;
+constexpr int kPrStride = 144;
+constexpr int kPrSmem = 2 * kPrRows * kPrStride + 2 * 64 * 4 + kSweepTile * 4;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+template <int Q>
+__device__ __forceinline__ void project_async_tile(const float* __restrict__ X, int D,
+                                                   const uint16_t* __restrict__ Xq, int Dq,
+                                                   const int32_t* __restrict__ perm, int begin, int end,
+                                                   const float* __restrict__ w, float* __restrict__ S,
+                                                   uint8_t* smem) {
+    constexpr int SLAB = Q != 0 ? 64 : 32;  // dims per 128-byte slab
+    float* wsb = reinterpret_cast<float*>(smem + 2 * kPrRows * kPrStride);  // [2][64]
+    int* ids = reinterpret_cast<int*>(wsb + 2 * 64);                        // [kSweepTile]
+    const int tid = threadIdx.x;
+    // the tile's row ids once, so that no copy waits on a global load
+    for (int p = tid; p < end - begin; p += kPrRows) ids[p] = perm[begin + p];
+    __syncthreads();
+    const int nslab = (D + SLAB - 1) / SLAB;
+    const int nstage = ((end - begin + kPrRows - 1) / kPrRows) * nslab;
+    // stage st: rows begin + (st / nslab) * 256 .., dims (st % nslab) * SLAB ..
+    auto issue = [&](int st) {
+        const int c = st / nslab, d0 = (st - c * nslab) * SLAB;
+        const int base = begin + c * kPrRows, cnt = min(kPrRows, end - base);
+        uint8_t* buf = smem + (st & 1) * (kPrRows * kPrStride);
+        for (int e = tid; e < kPrRows * 8; e += kPrRows) {
+            const int r = e >> 3, part = e & 7;
+            if (r >= cnt) break;
+            const int row = ids[base - begin + r];
+            if (Q != 0) {
+                cp_async16(buf + r * kPrStride + part * 16, Xq + (int64_t)row * Dq + d0 + part * 8);
+            } else if (d0 + part * 4 < D) {
+                cp_async16(buf + r * kPrStride + part * 16, X + (int64_t)row * D + d0 + part * 4);
+            }
+        }
+        if (tid < SLAB) wsb[(st & 1) * 64 + tid] = d0 + tid < D ? w[d0 + tid] : 0.f;
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    if (nstage > 0) issue(0);
+    float acc = 0.f;
+    for (int st = 0; st < nstage; ++st) {
+        if (st + 1 < nstage) {
+            issue(st + 1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncthreads();
+        const int c = st / nslab, sl = st - c * nslab, d0 = sl * SLAB;
+        const int base = begin + c * kPrRows, cnt = min(kPrRows, end - base);
+        if (tid < cnt) {
+            const uint8_t* rowp = smem + (st & 1) * (kPrRows * kPrStride) + tid * kPrStride;
+            const float* ws = wsb + (st & 1) * 64;
+            const int dl = min(SLAB, D - d0);
+            if (Q != 0) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (q * 8 >= dl) break;
+                    const uint4 h = *reinterpret_cast<const uint4*>(rowp + q * 16);
+                    const uint32_t hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        if (q * 8 + t < dl) {
+                            const uint32_t bits = t & 1 ? hv[t >> 1] >> 16 : hv[t >> 1] & 0xFFFFu;
+                            acc = __fmaf_rn(q16_to_float<Q>(bits), ws[q * 8 + t], acc);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (q * 4 >= dl) break;
+                    const float4 v = *reinterpret_cast<const float4*>(rowp + q * 16);
+                    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (q * 4 + t < dl) acc = __fmaf_rn(vv[t], ws[q * 4 + t], acc);
+                }
+            }
+            if (sl == nslab - 1) {
+                S[base + tid] = __fadd_rn(acc, 0.f);  // -0 -> +0
+                acc = 0.f;
+            }
+        }
+        __syncthreads();  // buffer st & 1 is refilled by the next issue
+    }
+}
+
+__global__ void __launch_bounds__(kPrRows) k1_project_async(const float* __restrict__ X, int D,
+                                                            const int32_t* __restrict__ perm,
+                                                            const int4* __restrict__ tiles,
+                                                            const int32_t* __restrict__ seg_off,
+                                                            const float* __restrict__ W, float* __restrict__ S,
+                                                            SelState* __restrict__ st,
+                                                            const int* __restrict__ status,
+                                                            const uint16_t* __restrict__ Xq, int Dq, int qtype,
+                                                            const int* __restrict__ qflag) {
+    extern __shared__ __align__(16) uint8_t pr_smem[];
+    if (*status & kStatusStop) return;  // perm may hold unwritten slots
+    const int q = q16_usable(Xq, qflag) ? qtype : 0;
+    const int4 t = tiles[blockIdx.x];
+    const int seg = t.x, begin = t.y, end = t.z;
+    if (st != nullptr && t.w && threadIdx.x == 0) {
+        const int m = seg_off[seg + 1] - seg_off[seg];
+        st[seg].prefix = 0;
+        st[seg].krem = (uint32_t)(m / 2);
+    }
+    const float* w = W + (int64_t)seg * D;
+    if (q == 1)
+        project_async_tile<1>(X, D, Xq, Dq, perm, begin, end, w, S, pr_smem);
+    else if (q == 2)
+        project_async_tile<2>(X, D, Xq, Dq, perm, begin, end, w, S, pr_smem);
+    else
+        project_async_tile<0>(X, D, Xq, Dq, perm, begin, end, w, S, pr_smem);
+}
+
 // Small segments: one CTA per segment keeps all keys in shared memory,
 // selects the floor(m/2)-th key, and either records it (thr) or, on the
 // final cut, partitions the segment stably into perm_out.
@@ -359,6 +485,13 @@ __device__ __forceinline__ void sums_side(const float* __restrict__ X, int D, co
                 v[u][2] = q16_to_float<Q>(hq[u].y & 0xFFFFu);
                 v[u][3] = q16_to_float<Q>(hq[u].y >> 16);
             }
+            if (Q != 0) {
+                // exact-mode values are integers of magnitude <= 2048 and a
+                // lane adds at most 128 of them per tile: FP32 sums are exact
+#pragma unroll
+                for (int j = 0; j < 4; ++j) h[j] = __fadd_rn(h[j], v[u][j]);
+                continue;
+            }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {  // TwoSum: s + err == h + v exactly
                 const float s = __fadd_rn(h[j], v[u][j]);
@@ -381,13 +514,21 @@ __device__ __forceinline__ void sums_run(const float* __restrict__ X, int D, con
                                          uint64_t T, int pos_bits, int w0, int w1, int dbase, int* rows, float* hL,
                                          float* lL, float* hR, float* lR) {
     const int lane = threadIdx.x & 31;
+    // ids and projections of the next 32 positions load while this chunk's
+    // rows are summed
+    int next_row = 0;
+    float next_s = 0.f;
+    if (w0 + lane < w1) {
+        next_row = perm[w0 + lane];
+        next_s = S[w0 + lane];
+    }
     for (int c = w0; c < w1; c += 32) {
         const int p = c + lane;
-        int my_row = 0;
-        bool my_left = false;
-        if (p < w1) {
-            my_row = perm[p];
-            my_left = sel_key(S[p], p - a, pos_bits) < T;
+        const int my_row = next_row;
+        const bool my_left = p < w1 && sel_key(next_s, p - a, pos_bits) < T;
+        if (p + 32 < w1) {
+            next_row = perm[p + 32];
+            next_s = S[p + 32];
         }
         const int cnt = min(32, w1 - c);
         const unsigned lb = __ballot_sync(0xffffffffu, my_left);
@@ -540,7 +681,11 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
         {
             LaunchScope ls("k1_project", s, rows + n * 8, 2.0 * n * D);
             SelState* st = lp.small ? nullptr : b.st;
-            if (vec2)
+            if (vec) {
+                cudaFuncSetAttribute(k1_project_async, cudaFuncAttributeMaxDynamicSharedMemorySize, kPrSmem);
+                k1_project_async<<<lp.nsweep, kPrRows, kPrSmem, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S,
+                                                                     st, b.status, b.Xq, b.Dq, b.qtype, b.qflag);
+            } else if (vec2)
                 k1_project<true><<<lp.nsweep, 256, 0, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S, st,
                                                            b.status, b.Xq, b.Dq, b.qtype, b.qflag);
             else
