@@ -11,6 +11,7 @@
 //                     could never enter the target's list)
 //   scatter           group the offers by target (counts, prefix sum)
 //   K4 merge          G_new[u] = first k unique of G_old[u] + offers to u
+#include <algorithm>
 #include <utility>
 
 #include "common.cuh"
@@ -193,12 +194,42 @@ __device__ __forceinline__ void warp_merge_list(const uint64_t* __restrict__ lis
     }
 }
 
+// Ascending bitonic sort of one key per lane across the warp.
+__device__ __forceinline__ uint64_t warp_sort32(uint64_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, stride);
+            const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), stride);
+            const uint64_t o = ((uint64_t)hi << 32) | lo;
+            // the lower lane of a pair keeps the smaller key in ascending runs
+            const bool up = (lane & size) == 0, lower = (lane & stride) == 0;
+            v = (lower == up) ? (o < v ? o : v) : (o < v ? v : o);
+        }
+    }
+    return v;
+}
+
 template <int NO>
 __global__ void __launch_bounds__(256) k6_select(const uint64_t* __restrict__ rbuf, const int32_t* __restrict__ roff,
                                                  int64_t n, int k, uint64_t* __restrict__ R) {
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
     const int lane = threadIdx.x & 31;
+    const int beg = roff[i], deg = roff[i + 1] - beg;
+    if (deg <= 32) {
+        // the usual case: every candidate fits a lane; the keys are distinct
+        // (one per source list), so the sorted run's first k are the list
+        const uint64_t v = warp_sort32(lane < deg ? rbuf[beg + lane] : kEmptyKey);
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+            const int e = lane + 32 * o;
+            if (e < k) R[i * k + e] = o == 0 ? v : kEmptyKey;
+        }
+        return;
+    }
     uint64_t run[NO];
 #pragma unroll
     for (int o = 0; o < NO; ++o) run[o] = kEmptyKey;
@@ -319,35 +350,17 @@ __device__ __forceinline__ bool pair_live(bool rect, int ia, int ib, int M, int 
     return ia < M && ib < M && upper && (ia < nn || ib < nn);
 }
 
+// The local join of node i by one warp (members, distances, offers).
 template <int BPL>
-__global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restrict__ X, int D, int k, int rev,
-                                                          int mcap, const uint64_t* __restrict__ Gold,
-                                                          const uint64_t* __restrict__ R,
-                                                          const int32_t* __restrict__ list,
-                                                          const uint64_t* __restrict__ fnew,
-                                                          const uint64_t* __restrict__ rnew, int64_t node0,
-                                                          int64_t node1, uint32_t* __restrict__ counter,
-                                                          int64_t cap, uint32_t* __restrict__ ptgt,
-                                                          uint64_t* __restrict__ pkey,
-                                                          int32_t* __restrict__ pcnt, int* __restrict__ status,
-                                                          const int* __restrict__ skip_if_exact) {
-    extern __shared__ float4 smem4[];
-    int dch, stride;
-    join_chunk(D, mcap, &dch, &stride);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    char* base = reinterpret_cast<char*>(smem4) + (size_t)warp * ((size_t)mcap * (stride * 4 + 12) + 16);
-    float* xs = reinterpret_cast<float*>(base);                                   // [mcap][stride]
-    uint64_t* thr = reinterpret_cast<uint64_t*>(xs + (size_t)mcap * stride);      // [mcap]
-    int32_t* mem = reinterpret_cast<int32_t*>(thr + mcap);                        // [mcap]
-
-    const int64_t pos = node0 + (int64_t)blockIdx.x * kJoinWarps + warp;
-    if (pos >= node1 || (*status & kStatusStop)) return;
-    const int64_t i = list ? (int64_t)list[pos] : pos;
-    // the tensor-core join does this round when the 16-bit copy is exact
-    if (skip_if_exact) {
-        const int f = *skip_if_exact;
-        if ((f & 1) == 0 && !((f & 2) && (f & 4))) return;
-    }
+__device__ __forceinline__ void join_node(const float* __restrict__ X, int D, int k, int rev, int mcap,
+                                          const uint64_t* __restrict__ Gold, const uint64_t* __restrict__ R,
+                                          const uint64_t* __restrict__ fnew, const uint64_t* __restrict__ rnew,
+                                          int64_t i, uint32_t* __restrict__ counter, int64_t cap,
+                                          uint32_t* __restrict__ ptgt, uint64_t* __restrict__ pkey,
+                                          int32_t* __restrict__ pcnt, int* __restrict__ status, float* xs,
+                                          uint64_t* thr, int32_t* mem, int dch, int stride) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();  // the warp's previous node is done with xs, thr and mem
     // members: the new ones first (flags from the previous round; none =
     // all new), then the old ones; each takes ids of G_old[i], then of R[i]
     int M = 0, nn = 0;
@@ -530,6 +543,39 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
     }
 }
 
+// Warps stride over the node positions [node0, node1) (of `list` when given).
+template <int BPL>
+__global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restrict__ X, int D, int k, int rev,
+                                                          int mcap, const uint64_t* __restrict__ Gold,
+                                                          const uint64_t* __restrict__ R,
+                                                          const int32_t* __restrict__ list,
+                                                          const uint64_t* __restrict__ fnew,
+                                                          const uint64_t* __restrict__ rnew, int64_t node0,
+                                                          int64_t node1, uint32_t* __restrict__ counter,
+                                                          int64_t cap, uint32_t* __restrict__ ptgt,
+                                                          uint64_t* __restrict__ pkey,
+                                                          int32_t* __restrict__ pcnt, int* __restrict__ status,
+                                                          const int* __restrict__ skip_if_exact) {
+    extern __shared__ float4 smem4[];
+    if (*status & kStatusStop) return;
+    // the tensor-core join does this round when the 16-bit copy is exact
+    if (skip_if_exact) {
+        const int f = *skip_if_exact;
+        if ((f & 1) == 0 && !((f & 2) && (f & 4))) return;
+    }
+    int dch, stride;
+    join_chunk(D, mcap, &dch, &stride);
+    const int warp = threadIdx.x >> 5;
+    char* base = reinterpret_cast<char*>(smem4) + (size_t)warp * ((size_t)mcap * (stride * 4 + 12) + 16);
+    float* xs = reinterpret_cast<float*>(base);                                   // [mcap][stride]
+    uint64_t* thr = reinterpret_cast<uint64_t*>(xs + (size_t)mcap * stride);      // [mcap]
+    int32_t* mem = reinterpret_cast<int32_t*>(thr + mcap);                        // [mcap]
+    for (int64_t pos = node0 + (int64_t)blockIdx.x * kJoinWarps + warp; pos < node1;
+         pos += (int64_t)gridDim.x * kJoinWarps)
+        join_node<BPL>(X, D, k, rev, mcap, Gold, R, fnew, rnew, list ? (int64_t)list[pos] : pos, counter, cap, ptgt,
+                       pkey, pcnt, status, xs, thr, mem, dch, stride);
+}
+
 __global__ void k5_scatter(const uint32_t* __restrict__ ptgt, const uint64_t* __restrict__ pkey,
                            const uint32_t* __restrict__ counter, int64_t cap, const int32_t* __restrict__ poff,
                            int32_t* __restrict__ pcur, uint64_t* __restrict__ grouped,
@@ -563,20 +609,13 @@ __device__ __forceinline__ bool offer_useful(uint64_t key, const uint64_t* row, 
     return row[lo] != key;
 }
 
-// One warp per node: the node's current list sits in shared memory; every
-// lane drops the offers that cannot change it, and only the rest go through
-// the warp selection.
+// Merges one node's offers into its list: the list sits in shared memory;
+// every lane drops the offers that cannot change it, and only the rest go
+// through the warp selection.
 template <int NO>
-__global__ void __launch_bounds__(256) k4_merge(uint64_t* __restrict__ Gnew, const uint64_t* __restrict__ grouped,
-                                                const int32_t* __restrict__ poff, int64_t n, int k,
-                                                const int* __restrict__ status) {
-    __shared__ uint64_t rows[8][32 * NO];
-    const int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (u >= n || (*status & kStatusStop)) return;
-    const int beg = poff[u], end = poff[u + 1];
-    if (beg == end) return;
+__device__ __forceinline__ void merge_node(uint64_t* __restrict__ Gnew, const uint64_t* __restrict__ grouped,
+                                           int64_t u, int beg, int end, int k, uint64_t* srow) {
     const int lane = threadIdx.x & 31;
-    uint64_t* srow = rows[threadIdx.x >> 5];
     uint64_t* row = Gnew + u * k;
     uint64_t run[NO];
 #pragma unroll
@@ -608,10 +647,36 @@ __global__ void __launch_bounds__(256) k4_merge(uint64_t* __restrict__ Gnew, con
         __syncwarp();
         changed = true;
     }
-    if (!changed) return;
+    if (changed) {
 #pragma unroll
-    for (int o = 0; o < NO; ++o)
-        if (lane + 32 * o < k) row[lane + 32 * o] = run[o];
+        for (int o = 0; o < NO; ++o)
+            if (lane + 32 * o < k) row[lane + 32 * o] = run[o];
+    }
+    __syncwarp();  // srow is reused by the warp's next node
+}
+
+// Warps stride over groups of 32 targets; the targets of a group that
+// received offers are merged one after the other.
+template <int NO>
+__global__ void __launch_bounds__(256) k4_merge(uint64_t* __restrict__ Gnew, const uint64_t* __restrict__ grouped,
+                                                const int32_t* __restrict__ poff, int64_t n, int k,
+                                                const int* __restrict__ status) {
+    __shared__ uint64_t rows[8][32 * NO];
+    if (*status & kStatusStop) return;
+    const int lane = threadIdx.x & 31;
+    uint64_t* srow = rows[threadIdx.x >> 5];
+    const int64_t warps = (int64_t)gridDim.x * 8;
+    for (int64_t g0 = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 32; g0 < n; g0 += warps * 32) {
+        const int64_t u = g0 + lane;
+        const int beg = u < n ? poff[u] : 0, end = u < n ? poff[u + 1] : 0;
+        unsigned todo = __ballot_sync(0xffffffffu, end > beg);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            merge_node<NO>(Gnew, grouped, g0 + src, __shfl_sync(0xffffffffu, beg, src),
+                           __shfl_sync(0xffffffffu, end, src), k, srow);
+        }
+    }
 }
 
 inline int grid_for(int64_t count, int block) {
@@ -697,14 +762,54 @@ namespace {
 
 // One refinement round over the nodes at positions [0, count) of b.list
 // (all nodes when b.list is NULL): reads Gold (and b.R), writes Gnew.
+void launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold,
+                       const JoinBuffers& b, int64_t c0, int64_t c1, int mcap, int bpl, size_t smem, int* status,
+                       cudaStream_t s);
+void finish_chunk(int64_t n, int k, uint64_t* Gnew, const JoinBuffers& b, int* status, cudaStream_t s);
+
+// Chunks: a chunk of nodes_per_chunk nodes fits the offer buffer even when
+// every member pair offers both ways.  Larger chunks are sized from `est`
+// (offers per node, updated from each checked chunk); when one overflows,
+// which its offer counter shows after the join, the flag is cleared and the
+// join re-runs on a smaller chunk (the target lists have not been touched).
 void join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold, uint64_t* Gnew,
-                const JoinBuffers& b, int64_t count, int64_t nodes_per_chunk, int* status, cudaStream_t s) {
+                const JoinBuffers& b, int64_t count, int64_t nodes_per_chunk, double& est, int* status,
+                cudaStream_t s) {
     cudaMemcpyAsync(Gnew, Gold, sizeof(uint64_t) * n * k, cudaMemcpyDeviceToDevice, s);
     const int mcap = ((rev ? 2 * k : k) + 3) & ~3;
     const int bpl = join_blocks_per_lane(mcap);
     const size_t smem = join_smem_bytes(D, mcap);
-    for (int64_t c0 = 0; c0 < count; c0 += nodes_per_chunk) {
-        const int64_t c1 = c0 + nodes_per_chunk < count ? c0 + nodes_per_chunk : count;
+    const double m_max = rev ? 2.0 * k : (double)k;
+    // the 32-bit offer counter must not wrap, even in the worst case
+    const int64_t wrap_nodes = (int64_t)(4294967295.0 / std::max(1.0, m_max * (m_max - 1)));
+    for (int64_t c0 = 0, c1 = 0; c0 < count; c0 = c1) {
+        int64_t want = (int64_t)((double)b.cap / std::max(est, 1.0));
+        want = std::max(nodes_per_chunk, std::min(want, wrap_nodes));
+        c1 = std::min(count, c0 + want);
+        for (;;) {
+            launch_join_chunk(X, n, D, k, rev, Gold, b, c0, c1, mcap, bpl, smem, status, s);
+            if (c1 - c0 <= nodes_per_chunk) break;  // cannot overflow
+            uint32_t offers = 0;
+            int st = 0;
+            cudaMemcpyAsync(&offers, b.counter, sizeof offers, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(&st, status, sizeof st, cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            est = std::max((double)offers / (double)(c1 - c0), 1.0);
+            if ((int64_t)offers <= b.cap) break;
+            st &= ~kStatusOverflow;
+            cudaMemcpyAsync(status, &st, sizeof st, cudaMemcpyHostToDevice, s);
+            cudaStreamSynchronize(s);
+            c1 = c0 + std::max(nodes_per_chunk, (int64_t)((double)(c1 - c0) * (double)b.cap / offers * 0.9));
+            record_items("k5_join_retry", 1.0);
+        }
+        finish_chunk(n, k, Gnew, b, status, s);
+    }
+}
+
+void launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold,
+                       const JoinBuffers& b, int64_t c0, int64_t c1, int mcap, int bpl, size_t smem, int* status,
+                       cudaStream_t s) {
+    {
         cudaMemsetAsync(b.pcnt, 0, sizeof(int32_t) * (n + 1), s);
         cudaMemsetAsync(b.pcur, 0, sizeof(int32_t) * n, s);
         cudaMemsetAsync(b.counter, 0, sizeof(uint32_t), s);
@@ -716,7 +821,7 @@ void join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_
             const double m = rev ? 2.0 * k : (double)k;
             LaunchScope ls("k5_join", s, (double)(c1 - c0) * (m * D * 4.0 + 2 * k * 8.0 + m * 8.0),
                            (double)(c1 - c0) * m * (m - 1) / 2 * 3.0 * D);
-            const int grid = (int)((c1 - c0 + kJoinWarps - 1) / kJoinWarps);
+            const int grid = (int)std::min<int64_t>((c1 - c0 + kJoinWarps - 1) / kJoinWarps, 152 * 32);
 #define KNNG_JOIN(BPL)                                                                                     \
     do {                                                                                                   \
         cudaFuncSetAttribute(k5_join<BPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
@@ -732,6 +837,12 @@ void join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_
             else KNNG_JOIN(5);
 #undef KNNG_JOIN
         }
+    }
+}
+
+// Groups the chunk's offers by target and merges them into Gnew.
+void finish_chunk(int64_t n, int k, uint64_t* Gnew, const JoinBuffers& b, int* status, cudaStream_t s) {
+    {
         launch_scan(b.pcnt, b.poff, n, b.scan_tmp, s);
         {
             LaunchScope ls("k5_scatter", s, 0, 0);
@@ -740,7 +851,7 @@ void join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_
         }
         {
             LaunchScope ls("k4_merge", s, n * (4.0 + 16.0 * k), 0);
-            const int grid = (int)((n * 32 + 255) / 256);
+            const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
             if (k > 32)
                 k4_merge<2><<<grid, 256, 0, s>>>(Gnew, b.grouped, b.poff, n, k, status);
             else
@@ -754,6 +865,10 @@ void join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_
 void run_refine(const float* X, int64_t n, int D, int k, bool rev, uint64_t*& G, uint64_t*& G2,
                 const JoinBuffers& jb, int64_t nodes_per_chunk, int rounds, int* status, cudaStream_t s) {
     JoinBuffers b = jb;
+    // offers per node of the first round's chunks: a guess (a quarter of the
+    // worst case); then what the previous chunk measured
+    const double m_max = rev ? 2.0 * k : (double)k;
+    double est = m_max * (m_max - 1) / 4;
     for (int r = 0; r < rounds; ++r) {
         if (rev) launch_reverse_lists(G, n, k, b, s);  // into b.R; b.R2 keeps the previous round's
         b.list = nullptr;
@@ -781,7 +896,7 @@ void run_refine(const float* X, int64_t n, int D, int k, bool rev, uint64_t*& G,
             b.rnew = rev ? b.rnew_buf : nullptr;
             record_items("k6_flags", (double)count);
         }
-        join_round(X, n, D, k, rev, G, G2, b, count, nodes_per_chunk, status, s);
+        join_round(X, n, D, k, rev, G, G2, b, count, nodes_per_chunk, est, status, s);
         std::swap(G, G2);
         if (rev) std::swap(b.R, b.R2);
     }

@@ -490,15 +490,15 @@ __device__ __forceinline__ void sums_side(const float* __restrict__ X, int D, co
                 // lane adds at most 128 of them per tile: FP32 sums are exact
 #pragma unroll
                 for (int j = 0; j < 4; ++j) h[j] = __fadd_rn(h[j], v[u][j]);
-                continue;
-            }
+            } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {  // TwoSum: s + err == h + v exactly
-                const float s = __fadd_rn(h[j], v[u][j]);
-                const float bp = __fsub_rn(s, h[j]);
-                const float err = __fadd_rn(__fsub_rn(h[j], __fsub_rn(s, bp)), __fsub_rn(v[u][j], bp));
-                h[j] = s;
-                l[j] = __fadd_rn(l[j], err);
+                for (int j = 0; j < 4; ++j) {  // TwoSum: s + err == h + v exactly
+                    const float s = __fadd_rn(h[j], v[u][j]);
+                    const float bp = __fsub_rn(s, h[j]);
+                    const float err = __fadd_rn(__fsub_rn(h[j], __fsub_rn(s, bp)), __fsub_rn(v[u][j], bp));
+                    h[j] = s;
+                    l[j] = __fadd_rn(l[j], err);
+                }
             }
         }
     }
@@ -596,24 +596,221 @@ __global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restri
     }
 }
 
-// New centroids of each segment from its tiles' partial sums (tile order),
-// FP64 mean rounded to FP32; stores w = c1 - c0.
-__global__ void k1_centroids(const double* __restrict__ partial, const int32_t* __restrict__ seg_off,
-                             const int32_t* __restrict__ seg_tile0, int D, float* __restrict__ W) {
+// Centroid sums with rows staged like the projection's: a CTA takes one
+// select tile (up to kTile positions), stages 128-byte slabs of 256 rows by
+// cp.async (double-buffered), and each thread sums 4 dims of the slab over a
+// 1/G share of the rows, left and right apart.  Each chunk of 256 positions
+// is first ordered stably by side (left rows first), so that a warp's two row
+// groups are almost always on the same side.  Per thread the rows of a side
+// come in ascending positions; the G partial sums of a dim are combined in
+// FP64 in group order.
+constexpr int kSuThreads = 256;
+constexpr int kSuSmem = 2 * kPrRows * kPrStride + kTile * 4 + kTile * 2 + 8 * 4 + 2 * 1024 * 8;
+
+// Adds 4 dims (quad q) of one staged row to the sums (h, l).
+template <int Q>
+__device__ __forceinline__ void sums_add(const uint8_t* row, int q, float (&h)[4], float (&l)[4]) {
+    float v[4];
+    if (Q != 0) {
+        const uint2 b = *reinterpret_cast<const uint2*>(row + q * 8);
+        v[0] = q16_to_float<Q>(b.x & 0xFFFFu);
+        v[1] = q16_to_float<Q>(b.x >> 16);
+        v[2] = q16_to_float<Q>(b.y & 0xFFFFu);
+        v[3] = q16_to_float<Q>(b.y >> 16);
+        // exact-mode values are integers of magnitude <= 2048 and a thread
+        // adds at most 128 of them per dim and tile: FP32 sums are exact
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[j] = __fadd_rn(h[j], v[j]);
+    } else {
+        const float4 f = *reinterpret_cast<const float4*>(row + q * 16);
+        v[0] = f.x;
+        v[1] = f.y;
+        v[2] = f.z;
+        v[3] = f.w;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {  // TwoSum: s + err == h + v exactly
+            const float s = __fadd_rn(h[j], v[j]);
+            const float bp = __fsub_rn(s, h[j]);
+            const float err = __fadd_rn(__fsub_rn(h[j], __fsub_rn(s, bp)), __fsub_rn(v[j], bp));
+            h[j] = s;
+            l[j] = __fadd_rn(l[j], err);
+        }
+    }
+}
+
+// Issues the copies of stage st of a sums tile: dims (st / nchunk) * SLAB ..
+// of the rows of chunk st % nchunk, into buffer st & 1.
+template <int Q>
+__device__ __forceinline__ void sums_issue(const float* __restrict__ X, int D, const uint16_t* __restrict__ Xq,
+                                           int Dq, const int* ids, int m, int nchunk, int st, uint8_t* smem) {
+    constexpr int SLAB = Q != 0 ? 64 : 32;
+    const int sl = st / nchunk, c = st - sl * nchunk, d0 = sl * SLAB;
+    const int cnt = min(kPrRows, m - c * kPrRows);
+    uint8_t* buf = smem + (st & 1) * (kPrRows * kPrStride);
+    for (int e = threadIdx.x; e < kPrRows * 8; e += kSuThreads) {
+        const int r = e >> 3, piece = e & 7;
+        if (r >= cnt) break;
+        const int row = ids[c * kPrRows + r];
+        if (Q != 0) {
+            cp_async16(buf + r * kPrStride + piece * 16, Xq + (int64_t)row * Dq + d0 + piece * 8);
+        } else if (d0 + piece * 4 < D) {
+            cp_async16(buf + r * kPrStride + piece * 16, X + (int64_t)row * D + d0 + piece * 4);
+        }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int Q>
+__device__ __forceinline__ void sums_async_tile(const float* __restrict__ X, int D, const uint16_t* __restrict__ Xq,
+                                                int Dq, const int32_t* __restrict__ perm,
+                                                const float* __restrict__ S, int a, uint64_t T, int pos_bits,
+                                                int begin, int end, double* __restrict__ part, uint8_t* smem) {
+    constexpr int SLAB = Q != 0 ? 64 : 32;  // dims per 128-byte slab
+    constexpr int QUADS = SLAB / 4;         // threads per row
+    constexpr int G = kSuThreads / QUADS;   // row groups
+    int* ids = reinterpret_cast<int*>(smem + 2 * kPrRows * kPrStride);  // [kTile] row ids by position
+    uint16_t* order = reinterpret_cast<uint16_t*>(ids + kTile);          // [kTile] positions by side
+    int* nleft = reinterpret_cast<int*>(order + kTile);                  // [8] left rows per chunk
+    double* red = reinterpret_cast<double*>(nleft + 8);                  // [2][G][SLAB], G * SLAB = 1024
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m = end - begin, nchunk = (m + kPrRows - 1) / kPrRows;
+    for (int p = tid; p < m; p += kSuThreads) ids[p] = perm[begin + p];
+    // warp c orders chunk c: left rows first, each side by position
+    for (int c = warp; c < nchunk; c += kSuThreads / 32) {
+        unsigned bal[8];
+        int nl = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int p = c * kPrRows + 32 * i + lane;
+            bal[i] = __ballot_sync(0xffffffffu, p < m && sel_key(S[begin + p], begin + p - a, pos_bits) < T);
+            nl += __popc(bal[i]);
+        }
+        int lb = 0;  // left rows before this group of 32
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int p = c * kPrRows + 32 * i + lane;
+            if (p < m) {
+                const int l_rank = lb + __popc(bal[i] & ((1u << lane) - 1u));
+                // rows before p: 32 i + lane, of which l_rank on the left
+                const int rank = (bal[i] >> lane) & 1u ? l_rank : nl + (32 * i + lane - l_rank);
+                order[c * kPrRows + rank] = (uint16_t)(32 * i + lane);
+            }
+            lb += __popc(bal[i]);
+        }
+        if (lane == 0) nleft[c] = nl;
+    }
+    __syncthreads();
+    const int nslab = (D + SLAB - 1) / SLAB, nstage = nslab * nchunk;
+    // stage st: dims (st / nchunk) * SLAB .., rows of chunk st % nchunk
+    const int q = tid % QUADS, g = tid / QUADS;
+    float hL[4] = {0.f, 0.f, 0.f, 0.f}, lL[4] = {0.f, 0.f, 0.f, 0.f};
+    float hR[4] = {0.f, 0.f, 0.f, 0.f}, lR[4] = {0.f, 0.f, 0.f, 0.f};
+    if (nstage > 0) sums_issue<Q>(X, D, Xq, Dq, ids, m, nchunk, 0, smem);
+    for (int st = 0; st < nstage; ++st) {
+        if (st + 1 < nstage) {
+            sums_issue<Q>(X, D, Xq, Dq, ids, m, nchunk, st + 1, smem);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncthreads();
+        const int sl = st / nchunk, c = st - sl * nchunk, d0 = sl * SLAB;
+        const int cnt = min(kPrRows, m - c * kPrRows), nl = nleft[c];
+        const uint8_t* buf = smem + (st & 1) * (kPrRows * kPrStride);
+        if (d0 + 4 * q < D) {
+            int i = g;
+            for (; i < nl; i += G) sums_add<Q>(buf + order[c * kPrRows + i] * kPrStride, q, hL, lL);
+            for (; i < cnt; i += G) sums_add<Q>(buf + order[c * kPrRows + i] * kPrStride, q, hR, lR);
+        }
+        if (c == nchunk - 1) {  // the slab's rows are all in: combine the groups
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                red[(0 * G + g) * SLAB + 4 * q + j] = (double)hL[j] + (double)lL[j];
+                red[(1 * G + g) * SLAB + 4 * q + j] = (double)hR[j] + (double)lR[j];
+                hL[j] = lL[j] = hR[j] = lR[j] = 0.f;
+            }
+            __syncthreads();
+            if (tid < 2 * SLAB) {
+                const int side = tid / SLAB, dd = tid - side * SLAB;
+                if (d0 + dd < D) {
+                    double acc = 0.0;
+                    for (int gg = 0; gg < G; ++gg) acc += red[(side * G + gg) * SLAB + dd];
+                    part[(int64_t)side * D + d0 + dd] = acc;
+                }
+            }
+        }
+        __syncthreads();  // buffer st & 1 and red are reused
+    }
+}
+
+__global__ void __launch_bounds__(kSuThreads) k1_sums_async(const float* __restrict__ X, int D,
+                                                            const int32_t* __restrict__ perm,
+                                                            const int4* __restrict__ tiles,
+                                                            const float* __restrict__ S,
+                                                            const int32_t* __restrict__ seg_off,
+                                                            const uint64_t* __restrict__ thr, int pos_bits,
+                                                            double* __restrict__ partial,
+                                                            const int* __restrict__ status,
+                                                            const uint16_t* __restrict__ Xq, int Dq, int qtype,
+                                                            const int* __restrict__ qflag) {
+    extern __shared__ __align__(16) uint8_t su_smem[];
+    if (*status & kStatusStop) return;  // perm may hold unwritten slots
+    const int q = q16_usable(Xq, qflag) ? qtype : 0;
+    const int4 t = tiles[blockIdx.x];
+    const int seg = t.x, begin = t.y, end = t.z;
+    const int a = seg_off[seg];
+    const uint64_t T = thr[seg];
+    double* part = partial + (int64_t)blockIdx.x * 2 * D;
+    if (q == 1)
+        sums_async_tile<1>(X, D, Xq, Dq, perm, S, a, T, pos_bits, begin, end, part, su_smem);
+    else if (q == 2)
+        sums_async_tile<2>(X, D, Xq, Dq, perm, S, a, T, pos_bits, begin, end, part, su_smem);
+    else
+        sums_async_tile<0>(X, D, Xq, Dq, perm, S, a, T, pos_bits, begin, end, part, su_smem);
+}
+
+// New centroids of each segment from its tiles' partial sums (kCenGroups
+// interleaved groups of tiles, each summed in tile order, then added in group
+// order), FP64 mean rounded to FP32; stores w = c1 - c0.
+constexpr int kCenGroups = 4;  // tile groups of k1_centroids (128 dims each)
+__global__ void __launch_bounds__(128 * kCenGroups) k1_centroids(const double* __restrict__ partial,
+                                                                 const int32_t* __restrict__ seg_off,
+                                                                 const int32_t* __restrict__ seg_tile0, int D,
+                                                                 float* __restrict__ W) {
+    __shared__ double red[kCenGroups][2][128];
     const int seg = blockIdx.x;
     const int m = seg_off[seg + 1] - seg_off[seg];
     const int K = m / 2;
     const int t0 = seg_tile0[seg], t1 = seg_tile0[seg + 1];
-    for (int d = threadIdx.x; d < D; d += blockDim.x) {
+    const int dl = threadIdx.x & 127, g = threadIdx.x >> 7;
+    for (int db = 0; db < D; db += 128) {
+        const int d = db + dl;
+        // group g sums tiles t0 + g, t0 + g + kCenGroups, ...; the groups are
+        // then added in order
         double sL = 0.0, sR = 0.0;
+        if (d < D) {
 #pragma unroll 4
-        for (int t = t0; t < t1; ++t) {
-            sL += partial[((int64_t)t * 2 + 0) * D + d];
-            sR += partial[((int64_t)t * 2 + 1) * D + d];
+            for (int t = t0 + g; t < t1; t += kCenGroups) {
+                sL += partial[((int64_t)t * 2 + 0) * D + d];
+                sR += partial[((int64_t)t * 2 + 1) * D + d];
+            }
         }
-        const float c0 = (float)(sL / (double)K);
-        const float c1 = (float)(sR / (double)(m - K));
-        W[(int64_t)seg * D + d] = __fsub_rn(c1, c0);
+        red[g][0][dl] = sL;
+        red[g][1][dl] = sR;
+        __syncthreads();
+        if (g == 0 && d < D) {
+            sL = red[0][0][dl];
+            sR = red[0][1][dl];
+#pragma unroll
+            for (int q = 1; q < kCenGroups; ++q) {
+                sL += red[q][0][dl];
+                sR += red[q][1][dl];
+            }
+            const float c0 = (float)(sL / (double)K);
+            const float c1 = (float)(sR / (double)(m - K));
+            W[(int64_t)seg * D + d] = __fsub_rn(c1, c0);
+        }
+        __syncthreads();
     }
 }
 
@@ -723,7 +920,12 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
         {
             LaunchScope ls("k1_sums", s, rows + n * 8, n * D);
             dim3 grid(lp.ntiles, dchunks);
-            if (vec)
+            if (vec && b.Xq) {  // the staged sums pay off on the 16-bit copy
+                cudaFuncSetAttribute(k1_sums_async, cudaFuncAttributeMaxDynamicSharedMemorySize, kSuSmem);
+                k1_sums_async<<<lp.ntiles, kSuThreads, kSuSmem, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off,
+                                                                     b.thr, lp.pos_bits, b.partial, b.status, b.Xq,
+                                                                     b.Dq, b.qtype, b.qflag);
+            } else if (vec)
                 k1_sums<true><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr,
                                                                lp.pos_bits, b.partial, b.status, b.Xq, b.Dq,
                                                                b.qtype, b.qflag);
@@ -734,7 +936,7 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
         }
         {
             LaunchScope ls("k1_centroids", s, (double)lp.ntiles * 2 * D * 8 + (double)lp.nseg * D * 4, 0);
-            k1_centroids<<<lp.nseg, 128, 0, s>>>(b.partial, lp.seg_off, lp.seg_tile0, D, b.W);
+            k1_centroids<<<lp.nseg, 128 * kCenGroups, 0, s>>>(b.partial, lp.seg_off, lp.seg_tile0, D, b.W);
         }
     }
 }

@@ -247,6 +247,31 @@ def test_low_precision_rounds_match_oracle(knng, precision, k, mode):
     _assert_graph_equal(lp_ids, lp_d, o_ids, o_d)
 
 
+def test_refine_small_offer_budget_retries_chunks(knng, monkeypatch):
+    # a 1 MB offer buffer: chunks sized from the offer estimate overflow and
+    # are re-run smaller; the result must not change
+    monkeypatch.setenv("KNNG_OFFER_BUDGET_MB", "1")
+    n, k = 3000, 12
+    X = datagen.gaussian_mixture(n, 16, 20, seed=5)
+    rng = np.random.default_rng(2)
+    ids, d = oracle.new_graph(n, k)
+    for i in range(n):
+        for j in rng.choice(np.delete(np.arange(n), i), size=k, replace=False):
+            oracle.list_insert(ids[i], d[i], oracle.dist_f32(X[i], X[j]), j)
+    o = (ids, d)
+    for _ in range(3):
+        o = oracle.refine_round(X, *o, mode=oracle.FWD_REV)
+    p = knng.default_params(k=k, refine_rounds=3, join_mode=knng.KNNG_JOIN_FWD_REV)
+    knng.stats_reset()
+    knng.stats_enable(True, False)
+    try:
+        g_ids, g_d = knng.knng_refine(_dev(X), _dev(ids), _dev(d), p)
+    finally:
+        knng.stats_enable(False)
+    _assert_graph_equal(g_ids, g_d, *o)
+    assert knng.stats().get("k5_join_retry", {}).get("items", 0) > 0, "no chunk overflowed"
+
+
 # ---------------------------------------------------------------- exact, recall
 @pytest.mark.parametrize("n,D,k,s", [(3000, 32, 10, None), (5000, 37, 20, 300), (2000, 200, 50, 150),
                                      (129, 4, 3, None)])
