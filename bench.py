@@ -157,9 +157,12 @@ def profiled_traffic(kernel, workload):
         return None
 
 
-def roofline(stats, clocks, workload, steps):
+def roofline(stats, clocks, workload, steps, name=None):
+    """Roofline of kernel `name` (default: the one with the most device time)."""
     peaks, kind = measured_peaks()
-    name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    if name is None:
+        name = max(stats.items(), key=lambda kv: kv[1]["ms"])[0]
+    st = stats[name]
     avg_ms = st["ms"] / st["launches"]
     per_launch_bytes = st["bytes"] / st["launches"]
     if name in ALU_KERNELS:
@@ -190,6 +193,26 @@ def roofline(stats, clocks, workload, steps):
     out["launches_per_step"] = st["launches"] / steps
     out["share_of_step"] = None
     return out
+
+
+def distance_error(X, ids, dists, rows):
+    """max |d - d64| / d64 over the stored entries of sampled rows, d64 the
+    squared distance in FP64 (numpy, on the host)."""
+    ids_h = ids[rows].cpu().numpy() if hasattr(ids, "cpu") else ids[rows]
+    d_h = dists[rows].cpu().numpy() if hasattr(dists, "cpu") else dists[rows]
+    worst, count = 0.0, 0
+    for r, i in enumerate(rows):
+        real = ids_h[r] >= 0
+        if not real.any():
+            continue
+        diff = X[ids_h[r][real]].astype(np.float64) - X[i].astype(np.float64)
+        d64 = np.einsum("ij,ij->i", diff, diff)
+        pos = d64 > 0
+        if pos.any():
+            worst = max(worst, float(np.max(np.abs(d_h[r][real][pos] - d64[pos]) / d64[pos])))
+        count += int(real.sum())
+    return {"max_rel": worst, "entries": count, "rows": int(len(rows)),
+            "against": "FP64 squared l2 of the stored pairs (numpy)"}
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -283,29 +306,38 @@ def run_ours(args, cfg):
             for _ in range(max(3, args.warmup)):
                 knng.knng_build_ex(Xd, p, stream=stream, out=(ids, dists))
         torch.cuda.synchronize()
+
+        def run(stats):
+            """steps builds between two events; with per-kernel event timing
+            when `stats` (that run only feeds the breakdown and rooflines)."""
+            knng.stats_reset()
+            knng.stats_enable(True, timing=True) if stats else knng.stats_enable(True, timing=False)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            barrier()
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                ev0.record(stream)
+                for _ in range(args.steps):
+                    knng.knng_build_ex(Xd, p, stream=stream, out=(ids, dists))
+                ev1.record(stream)
+            torch.cuda.synchronize()
+            knng.stats_enable(False)
+            barrier()
+            return max_over_ranks(ev0.elapsed_time(ev1)), knng.stats()
+
         clocks = ClockSampler(local) if sample_clocks else None
-        knng.stats_reset()
-        knng.stats_enable(True, timing=True)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        barrier()
-        torch.cuda.synchronize()
         if clocks:
             clocks.start()
-        with torch.cuda.stream(stream):
-            ev0.record(stream)
-            for _ in range(args.steps):
-                knng.knng_build_ex(Xd, p, stream=stream, out=(ids, dists))
-            ev1.record(stream)
-        torch.cuda.synchronize()
+        ms, counted = run(False)     # the timed number: launches counted, no per-kernel events
         clk = clocks.stop() if clocks else None
-        knng.stats_enable(False)
-        barrier()
-        ms = max_over_ranks(ev0.elapsed_time(ev1))
-        return ms, knng.stats(), clk, ids, dists
+        ms_k, st = run(True)
+        for name_, v in st.items():  # launches of the timed run
+            v["launches_timed_run"] = counted.get(name_, {}).get("launches", 0)
+        return ms, st, clk, ids, dists, ms_k
 
-    ms, st, clk, ids, dists = timed(args.precision, True)
-    launches = sum(v["launches"] for v in st.values())
+    ms, st, clk, ids, dists, ms_k = timed(args.precision, True)
+    launches = sum(v["launches_timed_run"] for v in st.values())
     value = world * n * args.steps / (ms * 1e-3)
 
     # recall of the last graph on sampled rows, against exact lists
@@ -313,11 +345,12 @@ def run_ours(args, cfg):
     smp_d = torch.from_numpy(smp).to(dev)
     gi, gd = knng.knng_exact(Xd, cfg["k"], smp_d)
     rec_ids, rec_tie = knng.knng_recall(ids, dists, gi, gd, smp_d)
+    dist_err = distance_error(X, ids, dists, smp[:2000])
 
     # the plain FP32 form of the same build, timed the same way
     fp32 = None
     if args.precision != "fp32":
-        ms32, st32, _, ids32, d32 = timed("fp32", False)
+        ms32, st32, _, ids32, d32, _ = timed("fp32", False)
         r32 = knng.knng_recall(ids32, d32, gi, gd, smp_d)
         fp32 = {"value": round(world * n * args.steps / (ms32 * 1e-3), 1), "ms_per_step": round(ms32 / args.steps, 3),
                 "recall_ids": round(r32[0], 5),
@@ -345,7 +378,16 @@ def run_ours(args, cfg):
             dist.destroy_process_group()
         return
     roof = roofline(st, clk, cfg["workload"], args.steps)
-    roof["share_of_step"] = round(st[roof["kernel"]]["ms"] / ms, 4)
+    roof["share_of_step"] = round(st[roof["kernel"]]["ms"] / ms_k, 4)
+    # the same figures for the other kernels above 2 % of the step
+    others = []
+    for name_, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"]):
+        if name_ == roof["kernel"] or v["ms"] < 0.02 * ms_k or v["launches"] == 0 or v["ms"] <= 0:
+            continue
+        r_ = roofline(st, clk, cfg["workload"], args.steps, name_)
+        r_["share_of_step"] = round(v["ms"] / ms_k, 4)
+        others.append({key: r_[key] for key in ("kernel", "bound", "achieved", "peak", "unit", "frac",
+                                                 "share_of_step", "traffic")})
     cfg_out = dict(cfg)
     cfg_out["precision"] = args.precision
     cfg_out["l2"] = "inputs larger than L2: X is %.0f MB (L2 129 MB)" % (X.nbytes / 1e6)
@@ -358,10 +400,13 @@ def run_ours(args, cfg):
         "recall_at_k": {"ids": round(rec_ids, 5), "tie": round(rec_tie, 5), "sample_rows": int(len(smp)),
                         "exact": "knng_exact canonical FP32"},
         "fp32_form": fp32,
-        "roofline": roof, "e2e": e2e, "e2e_graph_equals_device_graph": same, "gpu_launches": int(launches),
+        "roofline": roof, "roofline_other_kernels": others, "distance_error": dist_err, "e2e": e2e, "e2e_graph_equals_device_graph": same, "gpu_launches": int(launches),
         "clocks": clk,
         "kernels": {k_: {"ms_per_step": round(v["ms"] / args.steps, 3), "launches_per_step": v["launches"] / args.steps}
                     for k_, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])[:10]},
+        "kernel_breakdown_run": {"ms_per_step": round(ms_k / args.steps, 3),
+                                 "note": "a second run of the same steps with CUDA events around every launch; "
+                                         "the per-kernel times, shares and rooflines come from it"},
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)

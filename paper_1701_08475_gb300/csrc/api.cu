@@ -108,8 +108,20 @@ StatRegistry& reg() {
 }
 }  // namespace
 
+// KNNG_LAUNCH_LOG=1: every launch scope (and every later byte count) is
+// written to stderr as "launch <name> <bytes> <flops>", for matching
+// profiler captures to their algorithmic work.
+bool launch_log() {
+    static const bool on = [] {
+        const char* e = getenv("KNNG_LAUNCH_LOG");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+
 LaunchScope::LaunchScope(const char* name, cudaStream_t s, double bytes, double flops, int kernels)
     : name_(name), s_(s), bytes_(bytes), flops_(flops), slot_(-1) {
+    if (launch_log()) fprintf(stderr, "launch %s %.0f %.0f\n", name, bytes, flops);
     StatRegistry& r = reg();
     std::lock_guard<std::mutex> lk(r.mu);
     if (!r.on) return;
@@ -133,6 +145,16 @@ void record_items(const char* name, double items) {
     knng_kernel_stat& st = r.stats[name];
     if (st.name[0] == 0) snprintf(st.name, sizeof st.name, "%s", name);
     st.items += items;
+}
+
+void record_bytes(const char* name, double bytes) {
+    if (launch_log()) fprintf(stderr, "bytes %s %.0f\n", name, bytes);
+    StatRegistry& r = reg();
+    std::lock_guard<std::mutex> lk(r.mu);
+    if (!r.on) return;
+    knng_kernel_stat& st = r.stats[name];
+    if (st.name[0] == 0) snprintf(st.name, sizeof st.name, "%s", name);
+    st.bytes += bytes;
 }
 
 bool stats_on() {
@@ -431,6 +453,12 @@ struct BuildLayout {
 void quantize_for_join(const float* X, const Args& a, BuildLayout& b, cudaStream_t s) {
     if (!b.Xq) return;
     launch_quantize(X, a.n, a.D, nullptr, a.p.precision == KNNG_BF16, b.Xq, b.q_nrm, b.q_err, b.notexact, s);
+    // the kernels pick their path from the device flag; the host copy only
+    // sizes the statistics' algorithmic bytes
+    int f = 0;
+    cuda_check(cudaMemcpyAsync(&f, b.notexact, sizeof f, cudaMemcpyDeviceToHost, s), "flag read");
+    cuda_check(cudaStreamSynchronize(s), "stream synchronize");
+    b.sb.q16_host = b.sb.Xq != nullptr && (f & 1) == 0 && !((f & 2) && (f & 4));
 }
 
 bool lp_leaf(const Args& a, const TreePlan& tp) {

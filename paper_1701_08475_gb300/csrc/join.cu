@@ -762,18 +762,20 @@ namespace {
 
 // One refinement round over the nodes at positions [0, count) of b.list
 // (all nodes when b.list is NULL): reads Gold (and b.R), writes Gnew.
-void launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold,
-                       const JoinBuffers& b, int64_t c0, int64_t c1, int mcap, int bpl, size_t smem, int* status,
-                       cudaStream_t s);
-void finish_chunk(int64_t n, int k, uint64_t* Gnew, const JoinBuffers& b, int* status, cudaStream_t s);
+const char* launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold,
+                              const JoinBuffers& b, bool tc, int64_t c0, int64_t c1, int mcap, int bpl, size_t smem,
+                              int* status, cudaStream_t s);
+void finish_chunk(int64_t n, int k, uint64_t* Gnew, const JoinBuffers& b, double offers, int* status,
+                  cudaStream_t s);
 
-// Chunks: a chunk of nodes_per_chunk nodes fits the offer buffer even when
-// every member pair offers both ways.  Larger chunks are sized from `est`
-// (offers per node, updated from each checked chunk); when one overflows,
-// which its offer counter shows after the join, the flag is cleared and the
-// join re-runs on a smaller chunk (the target lists have not been touched).
+// Chunks are sized from `est` (offers per node, measured on the previous
+// chunk), but never below nodes_per_chunk, which fits the offer buffer even
+// when every member pair offers both ways.  After each join the offer
+// counter is read back; on an overflow the flag is cleared and the join
+// re-runs on a smaller chunk (no target list has been touched yet).  `tc`:
+// the tensor-core join does the work.
 void join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold, uint64_t* Gnew,
-                const JoinBuffers& b, int64_t count, int64_t nodes_per_chunk, double& est, int* status,
+                const JoinBuffers& b, bool tc, int64_t count, int64_t nodes_per_chunk, double& est, int* status,
                 cudaStream_t s) {
     cudaMemcpyAsync(Gnew, Gold, sizeof(uint64_t) * n * k, cudaMemcpyDeviceToDevice, s);
     const int mcap = ((rev ? 2 * k : k) + 3) & ~3;
@@ -786,37 +788,40 @@ void join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_
         int64_t want = (int64_t)((double)b.cap / std::max(est, 1.0));
         want = std::max(nodes_per_chunk, std::min(want, wrap_nodes));
         c1 = std::min(count, c0 + want);
+        uint32_t offers = 0;
         for (;;) {
-            launch_join_chunk(X, n, D, k, rev, Gold, b, c0, c1, mcap, bpl, smem, status, s);
-            if (c1 - c0 <= nodes_per_chunk) break;  // cannot overflow
-            uint32_t offers = 0;
+            const char* who = launch_join_chunk(X, n, D, k, rev, Gold, b, tc, c0, c1, mcap, bpl, smem, status, s);
             int st = 0;
             cudaMemcpyAsync(&offers, b.counter, sizeof offers, cudaMemcpyDeviceToHost, s);
             cudaMemcpyAsync(&st, status, sizeof st, cudaMemcpyDeviceToHost, s);
             cudaStreamSynchronize(s);
             est = std::max((double)offers / (double)(c1 - c0), 1.0);
-            if ((int64_t)offers <= b.cap) break;
+            // a chunk of nodes_per_chunk nodes cannot overflow; should it all
+            // the same, the flag stays and the call reports it
+            if ((int64_t)offers <= b.cap || c1 - c0 <= nodes_per_chunk) {
+                record_bytes(who, std::min<double>(offers, (double)b.cap) * 12.0);  // offers written (id + key)
+                break;
+            }
             st &= ~kStatusOverflow;
             cudaMemcpyAsync(status, &st, sizeof st, cudaMemcpyHostToDevice, s);
             cudaStreamSynchronize(s);
             c1 = c0 + std::max(nodes_per_chunk, (int64_t)((double)(c1 - c0) * (double)b.cap / offers * 0.9));
             record_items("k5_join_retry", 1.0);
         }
-        finish_chunk(n, k, Gnew, b, status, s);
+        finish_chunk(n, k, Gnew, b, (double)offers, status, s);
     }
 }
 
-void launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold,
-                       const JoinBuffers& b, int64_t c0, int64_t c1, int mcap, int bpl, size_t smem, int* status,
-                       cudaStream_t s) {
+// The join of the chunk [c0, c1); returns the name of the kernel that ran.
+const char* launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold,
+                              const JoinBuffers& b, bool tc, int64_t c0, int64_t c1, int mcap, int bpl, size_t smem,
+                              int* status, cudaStream_t s) {
     {
         cudaMemsetAsync(b.pcnt, 0, sizeof(int32_t) * (n + 1), s);
         cudaMemsetAsync(b.pcur, 0, sizeof(int32_t) * n, s);
         cudaMemsetAsync(b.counter, 0, sizeof(uint32_t), s);
-        // tensor-core join first; the FP32 join below then returns at once
-        // on the device when the 16-bit copy is exact
-        const bool tc_launched = b.lp && launch_join_tc(b.Xq, D, b.qnrm, k, rev, Gold, b.R, c0, c1, b, status,
-                                                        b.notexact, b.bf16, s);
+        if (tc && launch_join_tc(b.Xq, D, b.qnrm, k, rev, Gold, b.R, c0, c1, b, status, b.notexact, b.bf16, s))
+            return "k5_join_tc";
         {
             const double m = rev ? 2.0 * k : (double)k;
             LaunchScope ls("k5_join", s, (double)(c1 - c0) * (m * D * 4.0 + 2 * k * 8.0 + m * 8.0),
@@ -827,8 +832,7 @@ void launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev, const 
         cudaFuncSetAttribute(k5_join<BPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
         k5_join<BPL><<<grid, 32 * kJoinWarps, smem, s>>>(X, D, k, rev ? 1 : 0, mcap, Gold, b.R, b.list,     \
                                                          b.fnew, b.rnew, c0, c1, b.counter, b.cap, b.ptgt,  \
-                                                         b.pkey, b.pcnt, status,                            \
-                                                         tc_launched ? b.notexact : nullptr);               \
+                                                         b.pkey, b.pcnt, status, nullptr);                  \
     } while (0)
             if (bpl <= 1) KNNG_JOIN(1);
             else if (bpl <= 2) KNNG_JOIN(2);
@@ -838,19 +842,24 @@ void launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev, const 
 #undef KNNG_JOIN
         }
     }
+    return "k5_join";
 }
 
 // Groups the chunk's offers by target and merges them into Gnew.
-void finish_chunk(int64_t n, int k, uint64_t* Gnew, const JoinBuffers& b, int* status, cudaStream_t s) {
+void finish_chunk(int64_t n, int k, uint64_t* Gnew, const JoinBuffers& b, double offers, int* status,
+                  cudaStream_t s) {
     {
         launch_scan(b.pcnt, b.poff, n, b.scan_tmp, s);
         {
-            LaunchScope ls("k5_scatter", s, 0, 0);
+            // per offer: target and key read, its target's offset, the key written
+            LaunchScope ls("k5_scatter", s, offers * 24.0, 0);
             k5_scatter<<<152 * 16, 256, 0, s>>>(b.ptgt, b.pkey, b.counter, b.cap, b.poff, b.pcur, b.grouped,
                                                 status, b.offers_total);
         }
         {
-            LaunchScope ls("k4_merge", s, n * (4.0 + 16.0 * k), 0);
+            // offsets, every grouped offer, and the list of each target reached
+            // (at most min(n, offers) of them) read and written
+            LaunchScope ls("k4_merge", s, n * 4.0 + offers * 8.0 + std::min((double)n, offers) * 16.0 * k, 0);
             const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
             if (k > 32)
                 k4_merge<2><<<grid, 256, 0, s>>>(Gnew, b.grouped, b.poff, n, k, status);
@@ -869,6 +878,14 @@ void run_refine(const float* X, int64_t n, int D, int k, bool rev, uint64_t*& G,
     // worst case); then what the previous chunk measured
     const double m_max = rev ? 2.0 * k : (double)k;
     double est = m_max * (m_max - 1) / 4;
+    // the tensor-core join runs when the 16-bit copy is exact for this input
+    bool tc = false;
+    if (b.lp) {
+        int f = 0;
+        cudaMemcpyAsync(&f, b.notexact, sizeof f, cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        tc = (f & 1) == 0 && !((f & 2) && (f & 4));
+    }
     for (int r = 0; r < rounds; ++r) {
         if (rev) launch_reverse_lists(G, n, k, b, s);  // into b.R; b.R2 keeps the previous round's
         b.list = nullptr;
@@ -896,7 +913,7 @@ void run_refine(const float* X, int64_t n, int D, int k, bool rev, uint64_t*& G,
             b.rnew = rev ? b.rnew_buf : nullptr;
             record_items("k6_flags", (double)count);
         }
-        join_round(X, n, D, k, rev, G, G2, b, count, nodes_per_chunk, est, status, s);
+        join_round(X, n, D, k, rev, G, G2, b, tc, count, nodes_per_chunk, est, status, s);
         std::swap(G, G2);
         if (rev) std::swap(b.R, b.R2);
     }

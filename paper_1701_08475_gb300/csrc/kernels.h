@@ -63,6 +63,7 @@ struct SplitBuffers {
     const uint16_t* Xq = nullptr;
     int Dq = 0, qtype = 0;  // qtype 1 = BF16, 2 = FP16
     const int* qflag = nullptr;
+    bool q16_host = false;  // the host's copy of that decision (statistics only)
 };
 
 constexpr int kTile = 2048;         // positions per select/partition tile
@@ -143,8 +144,10 @@ bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev
                     const uint64_t* R, int64_t node0, int64_t node1, const JoinBuffers& b, int* status,
                     const int* notexact, bool bf16, cudaStream_t s);
 
-// Adds `items` to the statistics of kernel `name` (when statistics are on).
+// Adds `items` (algorithmic `bytes`) to the statistics of kernel `name`
+// (when statistics are on).
 void record_items(const char* name, double items);
+void record_bytes(const char* name, double bytes);
 
 void launch_reverse_lists(const uint64_t* G, int64_t n, int k, const JoinBuffers& b, cudaStream_t s);
 // `rounds` refinement rounds on G (G2: the second graph buffer); on return

@@ -865,7 +865,7 @@ __global__ void __launch_bounds__(256) k1_part_scatter(const float* __restrict__
 void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint64_t pass_seed,
                      const int32_t* perm_in, int32_t* perm_out, const SplitBuffers& b, cudaStream_t s) {
     // algorithmic bytes: a sweep reads every row once plus its id and key
-    const double n = lp.n, rows = n * D * 4.0;
+    const double n = lp.n, rows = n * (b.q16_host ? b.Dq * 2.0 : D * 4.0);
     const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     const bool vec2 = (D % 2 == 0) && ((reinterpret_cast<uintptr_t>(X) & 7) == 0);
     const int dchunks = (D + 127) / 128;
