@@ -62,6 +62,11 @@ __device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
     uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
     return ((uint64_t)hi << 32) | lo;
 }
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)v, src);
+    const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(v >> 32), src);
+    return ((uint64_t)hi << 32) | lo;
+}
 __device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) {
@@ -110,6 +115,87 @@ __device__ __forceinline__ void warp_select_unique(uint64_t (&a)[NS], int k, uin
             a[NS - 1] = kEmptyKey;
         }
     }
+}
+
+// Ascending bitonic sort of one key per lane across the warp.
+__device__ __forceinline__ uint64_t warp_sort32(uint64_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const uint64_t o = shfl_xor64(v, stride);
+            // the lower lane of a pair keeps the smaller key in ascending runs
+            const bool up = (lane & size) == 0, lower = (lane & stride) == 0;
+            v = (lower == up) ? (o < v ? o : v) : (o < v ? v : o);
+        }
+    }
+    return v;
+}
+
+// Fast path of "first k distinct keys of list U candidates" for k <= 32.
+// `list`: the current sorted list, entry e in lane e (empty slots kEmptyKey);
+// `cand`: NC keys per lane, distinct among themselves (any may equal a list
+// entry).  A candidate not below the list's k-th key cannot enter.  The
+// survivors (at most 32) are sorted, the 32 smallest keys of the union come
+// from one bitonic merge step and a bitonic sort, and duplicates drop out.
+// Returns false, with nothing decided, when more than 32 candidates survive
+// or those 32 keys hold fewer than k distinct ones while more may follow; the
+// caller then takes the general path.  `scratch`: 32 keys of shared memory
+// owned by the warp.  On true, `out` is the new list (entry e in lane e) and
+// `changed` says whether it differs from `list`.
+template <int NC>
+__device__ __forceinline__ bool warp_merge_few(const uint64_t (&cand)[NC], uint64_t list, int k, uint64_t* scratch,
+                                               uint64_t& out, bool& changed) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t klo = __shfl_sync(0xffffffffu, (uint32_t)list, k - 1);
+    const uint32_t khi = __shfl_sync(0xffffffffu, (uint32_t)(list >> 32), k - 1);
+    const uint64_t kth = ((uint64_t)khi << 32) | klo;
+    unsigned bal[NC];
+    int total = 0;
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+        bal[s] = __ballot_sync(0xffffffffu, cand[s] < kth);
+        total += __popc(bal[s]);
+    }
+    if (total == 0) {
+        out = list;
+        changed = false;
+        return true;
+    }
+    if (total > 32) return false;
+    int base = 0;
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+        if (cand[s] < kth) scratch[base + __popc(bal[s] & lt)] = cand[s];
+        base += __popc(bal[s]);
+    }
+    __syncwarp();
+    uint64_t b = lane < total ? scratch[lane] : kEmptyKey;
+    __syncwarp();
+    b = warp_sort32(b);
+    // list ascending and the survivors descending form a bitonic sequence of
+    // 64; its lower half-cleaner holds the 32 smallest, itself bitonic
+    const uint64_t br = shfl64(b, 31 - lane);
+    uint64_t c = list < br ? list : br;
+#pragma unroll
+    for (int stride = 16; stride > 0; stride >>= 1) {
+        const uint64_t o = shfl_xor64(c, stride);
+        c = (lane & stride) == 0 ? (o < c ? o : c) : (o < c ? c : o);
+    }
+    const uint64_t prev = shfl64(c, (lane + 31) & 31);
+    const bool keep = c != kEmptyKey && (lane == 0 || c != prev);
+    const unsigned ub = __ballot_sync(0xffffffffu, keep);
+    const int nu = __popc(ub);
+    const uint64_t last = shfl64(c, 31);
+    if (nu < k && last != kEmptyKey) return false;  // a 33rd key may be needed
+    if (keep) scratch[__popc(ub & lt)] = c;
+    __syncwarp();
+    out = lane < nu ? scratch[lane] : kEmptyKey;
+    __syncwarp();
+    changed = __any_sync(0xffffffffu, lane < k && out != list);
+    return true;
 }
 
 // Status word written by kernels that detect a bad input or an internal

@@ -194,24 +194,6 @@ __device__ __forceinline__ void warp_merge_list(const uint64_t* __restrict__ lis
     }
 }
 
-// Ascending bitonic sort of one key per lane across the warp.
-__device__ __forceinline__ uint64_t warp_sort32(uint64_t v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, stride);
-            const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), stride);
-            const uint64_t o = ((uint64_t)hi << 32) | lo;
-            // the lower lane of a pair keeps the smaller key in ascending runs
-            const bool up = (lane & size) == 0, lower = (lane & stride) == 0;
-            v = (lower == up) ? (o < v ? o : v) : (o < v ? v : o);
-        }
-    }
-    return v;
-}
-
 template <int NO>
 __global__ void __launch_bounds__(256) k6_select(const uint64_t* __restrict__ rbuf, const int32_t* __restrict__ roff,
                                                  int64_t n, int k, uint64_t* __restrict__ R) {
@@ -614,7 +596,7 @@ __device__ __forceinline__ bool offer_useful(uint64_t key, const uint64_t* row, 
 // through the warp selection.
 template <int NO>
 __device__ __forceinline__ void merge_node(uint64_t* __restrict__ Gnew, const uint64_t* __restrict__ grouped,
-                                           int64_t u, int beg, int end, int k, uint64_t* srow) {
+                                           int64_t u, int beg, int end, int k, uint64_t* srow, uint64_t* scratch) {
     const int lane = threadIdx.x & 31;
     uint64_t* row = Gnew + u * k;
     uint64_t run[NO];
@@ -637,6 +619,22 @@ __device__ __forceinline__ void merge_node(uint64_t* __restrict__ Gnew, const ui
             any |= a[s] != kEmptyKey;
         }
         if (!__any_sync(0xffffffffu, any)) continue;
+        if (NO == 1) {  // usually few offers survive: one bitonic merge
+            uint64_t few[NC], out;
+            bool ch;
+#pragma unroll
+            for (int s = 0; s < NC; ++s) few[s] = a[s];
+            if (warp_merge_few<NC>(few, run[0], k, scratch, out, ch)) {
+                if (ch) {
+                    run[0] = lane < k ? out : kEmptyKey;
+                    __syncwarp();
+                    srow[lane] = run[0];
+                    __syncwarp();
+                    changed = true;
+                }
+                continue;
+            }
+        }
 #pragma unroll
         for (int o = 0; o < NO; ++o) a[NC + o] = run[o];
         sort_regs<NC + NO>(a);
@@ -662,6 +660,7 @@ __global__ void __launch_bounds__(256) k4_merge(uint64_t* __restrict__ Gnew, con
                                                 const int32_t* __restrict__ poff, int64_t n, int k,
                                                 const int* __restrict__ status) {
     __shared__ uint64_t rows[8][32 * NO];
+    __shared__ uint64_t scratch[8][32];
     if (*status & kStatusStop) return;
     const int lane = threadIdx.x & 31;
     uint64_t* srow = rows[threadIdx.x >> 5];
@@ -674,7 +673,7 @@ __global__ void __launch_bounds__(256) k4_merge(uint64_t* __restrict__ Gnew, con
             const int src = __ffs(todo) - 1;
             todo &= todo - 1;
             merge_node<NO>(Gnew, grouped, g0 + src, __shfl_sync(0xffffffffu, beg, src),
-                           __shfl_sync(0xffffffffu, end, src), k, srow);
+                           __shfl_sync(0xffffffffu, end, src), k, srow, scratch[threadIdx.x >> 5]);
         }
     }
 }

@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(LeafCfg<MC>::NT) k2_leaf_fp32(const float* __r
     float* xs = reinterpret_cast<float*>(smem4);          // [MC][stride]
     float* dt = xs + MC * stride;                          // [RB][MC + 1]
     int32_t* ids = reinterpret_cast<int32_t*>(dt + C::RB * (MC + 1));  // [MC]
+    uint64_t* wscratch = reinterpret_cast<uint64_t*>(ids + MC) + (threadIdx.x >> 5) * 32;  // 32 keys per warp
 
     const int leaf = blockIdx.x;
     const int a = leaf_off[leaf];
@@ -125,6 +126,17 @@ __global__ void __launch_bounds__(LeafCfg<MC>::NT) k2_leaf_fp32(const float* __r
                 const int c = lane + 32 * s;
                 cand[s] = (c < m && c != row) ? make_key(dt[r * (MC + 1) + c], (uint32_t)ids[c]) : kEmptyKey;
             }
+            if (NSG == 1) {
+                // few candidates beat the row's k-th entry after the first pass
+                uint64_t few[MC / 32], out;
+                bool changed;
+#pragma unroll
+                for (int s = 0; s < MC / 32; ++s) few[s] = cand[s];
+                if (warp_merge_few<MC / 32>(few, lane < k ? grow[lane] : kEmptyKey, k, wscratch, out, changed)) {
+                    if (changed && lane < k) grow[lane] = out;
+                    continue;
+                }
+            }
 #pragma unroll
             for (int s = 0; s < NSG; ++s) {
                 const int e = lane + 32 * s;
@@ -148,7 +160,7 @@ void launch_leaf_t(const float* X, int D, const int32_t* perm, const int32_t* le
     using C = LeafCfg<MC>;
     int dch, stride;
     leaf_chunk(D, MC, &dch, &stride);
-    const size_t smem = (size_t)MC * stride * 4 + (size_t)C::RB * (MC + 1) * 4 + MC * 4;
+    const size_t smem = (size_t)MC * stride * 4 + (size_t)C::RB * (MC + 1) * 4 + MC * 4 + (C::NT / 32) * 32 * 8;
     cudaFuncSetAttribute(k2_leaf_fp32<MC, NSG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k2_leaf_fp32<MC, NSG><<<nleaf, C::NT, smem, s>>>(X, D, perm, leaf_off, k, G, status);
 }

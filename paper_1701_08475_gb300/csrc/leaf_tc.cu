@@ -133,7 +133,7 @@ constexpr int kTcThreads = 128;
 
 struct TcSmem {
     int stages;
-    size_t stage_off, dt_off, bar_off, misc_off, total;
+    size_t stage_off, dt_off, bar_off, misc_off, scratch_off, total;
 };
 
 __host__ __device__ inline TcSmem tc_smem(int Dp) {
@@ -144,8 +144,10 @@ __host__ __device__ inline TcSmem tc_smem(int Dp) {
     L.dt_off = (size_t)L.stages * kStageBytes;
     L.bar_off = L.dt_off + (size_t)kTcRows * kDtStride * 4;
     L.misc_off = L.bar_off + (size_t)(2 * L.stages + 1) * 8;
-    // misc: tmem address, abort flag, ids[128], nrm[128], err[128], two maxima
-    L.total = L.misc_off + 16 + 3 * kTcRows * 4 + 16;
+    // misc: tmem address, abort flag, ids[128], nrm[128], err[128], two maxima;
+    // then 32 keys of merge scratch per warp
+    L.scratch_off = L.misc_off + 16 + 3 * kTcRows * 4 + 16;
+    L.total = L.scratch_off + (kTcThreads / 32) * 32 * 8;
     return L;
 }
 
@@ -175,11 +177,6 @@ __device__ __forceinline__ float canon_dist(const float* __restrict__ xa, const 
     return acc;
 }
 
-__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
-    const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)v, src);
-    const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(v >> 32), src);
-    return ((uint64_t)hi << 32) | lo;
-}
 
 // entry r of a list held lane-major in NO slots (r < 32 * NO)
 template <int NO>
@@ -329,6 +326,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
     const bool exact = lp_exact(*notexact);
     const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     constexpr int NC = kTcRows / 32;
+    uint64_t* wscratch = reinterpret_cast<uint64_t*>(base + L.scratch_off) + warp * 32;
     for (int r = warp; r < m; r += kTcThreads / 32) {
         const int gi = sid[r];
         uint64_t* grow = G + (int64_t)gi * k;
@@ -345,6 +343,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
                 const int c = lane + 32 * s;
                 cand[s] = (c < m && c != r) ? make_key(__fadd_rn(dt[r * kDtStride + c], 0.f), (uint32_t)sid[c])
                                             : kEmptyKey;
+            }
+            if (NSG == 1) {
+                // few candidates beat the row's k-th entry after the first pass
+                uint64_t few[NC];
+#pragma unroll
+                for (int s = 0; s < NC; ++s) few[s] = cand[s];
+                uint64_t out;
+                bool changed;
+                if (warp_merge_few<NC>(few, old[0], k, wscratch, out, changed)) {
+                    if (changed && lane < k) grow[lane] = out;
+                    continue;
+                }
             }
 #pragma unroll
             for (int s = 0; s < NSG; ++s) cand[NC + s] = old[s];
