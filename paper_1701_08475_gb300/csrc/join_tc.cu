@@ -173,8 +173,9 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
         // gather the member rows (16-byte pieces) into the swizzled K-major tile;
         // the thresholds and norms below load while these copies are in flight
         const int q_per_row = Dp / 8;
-        for (int e = tid; e < kRows * q_per_row; e += kThreads) {
-            const int r = e / q_per_row, q = e - r * q_per_row;
+        // piece e = tid + i * kThreads is (row r, piece q); stepped without a division
+        const int r_step = kThreads / q_per_row, q_step = kThreads - r_step * q_per_row;
+        for (int r = tid / q_per_row, q = tid - (tid / q_per_row) * q_per_row; r < kRows;) {
             const int kc = q >> 3, c16 = q & 7;
             uint8_t* dst = base + (size_t)kc * kChunkBytes + r * 128 + ((c16 ^ (r & 7)) << 4);
             const int u = mem[r];
@@ -184,6 +185,12 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                              : "memory");
             } else {
                 *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+            }
+            r += r_step;
+            q += q_step;
+            if (q >= q_per_row) {
+                q -= q_per_row;
+                ++r;
             }
         }
         for (int r = tid; r < kRows; r += kThreads) {
@@ -206,7 +213,8 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
             tc::mma_commit(done);
         }
         __syncwarp();
-        const int mma_ok = tc::mbar_wait(done, (uint32_t)(iter & 1), status) ? 1 : 0;
+        // one thread watches the barrier; the others sleep in __syncthreads
+        const int mma_ok = tid == 0 ? (tc::mbar_wait(done, (uint32_t)(iter & 1), status) ? 1 : 0) : 1;
         ok = __syncthreads_and(mma_ok);
         tc::fence_after_sync();
         if (!ok) break;
@@ -218,15 +226,19 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
         const int j = r / mcap, s = r - j * mcap;
         const int Mj = j < npc ? mcount[j] : 0;
         const bool mine = s < Mj;
+        // the 32-column chunks that hold the windows of this warp's rows (its
+        // first and last row's nodes), alternately to h = 0 and h = 1
+        const int wr0 = (warp & 3) * 32;
+        const int cmin = (wr0 / mcap) * mcap, cmax = min(((wr0 + 31) / mcap + 1) * mcap, kRows);
 #pragma unroll 1
-        for (int cc = 2 * h; cc < 2 * h + 2; ++cc) {
+        for (int cc = (cmin >> 5) + h; cc * 32 < cmax; cc += 2) {
             float g[32];
-            tc::tmem_ld_32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(cc * 32), g);
+            tc::tmem_ld_32(tmem + ((uint32_t)wr0 << 16) + (uint32_t)(cc * 32), g);
             if (mine) {
 #pragma unroll
                 for (int jj = 0; jj < 32; ++jj) {
                     const int t = cc * 32 + jj - j * mcap;
-                    if (t >= 0 && t < Mj) priv[t * kRows + r] = g[jj];
+                    if ((unsigned)t < (unsigned)Mj) priv[t * kRows + r] = g[jj];
                 }
             }
         }

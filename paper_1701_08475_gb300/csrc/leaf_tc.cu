@@ -281,7 +281,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
         }
     }
     __syncwarp();
-    const int mma_ok = tc::mbar_wait(done, 0, status) ? 1 : 0;
+    // one thread watches the barrier; the others sleep in __syncthreads
+    const int mma_ok = tid == 0 ? (tc::mbar_wait(done, 0, status) ? 1 : 0) : 1;
     // uniform over the CTA: the tensor-memory loads below are warp-collective
     const bool ok = __syncthreads_and(mma_ok) && *abort_flag == 0;
     tc::fence_after_sync();
