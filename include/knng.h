@@ -105,6 +105,30 @@ KNNG_API int knng_build(const float *data, int64_t n, int D, int k, int leaf_max
 KNNG_API int knng_build_ex(const float *data, int64_t n, int D, const knng_params *p,
                   int32_t *out_ids, float *out_dists, void *stream);
 
+/* One independent instance of a batched build. */
+typedef struct knng_instance {
+    const float *data;   /* n x D FP32 row-major, host or device */
+    int64_t n;           /* points (> k) */
+    int D;               /* dims (1 .. 4096) */
+    int leaf_max;        /* this instance's cluster bound; 0: p->leaf_max */
+    int32_t *out_ids;    /* n x k, ids local to the instance */
+    float *out_dists;    /* n x k */
+} knng_instance;
+
+/*
+ * Many independent graphs in one build (Sec. 3.1 / Alg. 1 and the
+ * refinement, per instance; the paper builds one graph at a time, so the
+ * batching is this library's).  Instances of equal D run as one forest:
+ * every stage is one launch over all their trees (each stops splitting at its
+ * own depth, with the seeds it would get alone), then one leaf stage and
+ * shared refinement rounds over all their points.  Each instance's result is
+ * exactly the one knng_build_ex gives it alone with the same parameters.
+ * inst[i].data must not overlap any output.  Errors: as knng_build_ex, for
+ * any instance (nothing is written then), or n_inst < 1, or the points of one
+ * D together reach 2^31 rows.
+ */
+KNNG_API int knng_build_batched(int n_inst, const knng_instance *inst, const knng_params *p, void *stream);
+
 /*
  * Refinement only: p->refine_rounds local-join rounds (Jacobi: every offer of
  * a round comes from the graph as it stood before the round) applied to the

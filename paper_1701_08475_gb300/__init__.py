@@ -17,6 +17,7 @@ from ._lib import (  # noqa: F401
     default_params,
     knng_build,
     knng_build_ex,
+    knng_build_batched,
     knng_exact,
     knng_exact_noalloc,
     knng_leaf_update,

@@ -37,6 +37,11 @@ class Params(ctypes.Structure):
                 ("twomeans_iters", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
+class Instance(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("n", ctypes.c_int64), ("D", ctypes.c_int), ("leaf_max", ctypes.c_int),
+                ("out_ids", ctypes.c_void_p), ("out_dists", ctypes.c_void_p)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double),
                 ("bytes", ctypes.c_double), ("flops", ctypes.c_double), ("items", ctypes.c_double)]
@@ -61,6 +66,7 @@ def load():
             "knng_default_params": (None, [PP]),
             "knng_build": (i32, [P, i64, i32, i32, i32, i32, u64, P, P]),
             "knng_build_ex": (i32, [P, i64, i32, PP, P, P, P]),
+            "knng_build_batched": (i32, [i32, ctypes.POINTER(Instance), PP, P]),
             "knng_refine": (i32, [P, i64, i32, PP, P, P, P]),
             "knng_partition": (i32, [P, i64, i32, i32, i32, u64, i32, P, P, P]),
             "knng_tree_depth": (i32, [i64, i32]),
@@ -186,6 +192,27 @@ def knng_build_ex(data, params, stream=None, out=None):
     with _DeviceCtx(data, stream) as s:
         _check(load().knng_build_ex(_ptr(data), n, D, ctypes.byref(params), _ptr(ids), _ptr(d), s))
     return ids, d
+
+
+def knng_build_batched(datas, params, leaf_maxes=None, stream=None):
+    """Independent graphs of several inputs in one build; returns a list of
+    (ids, dists), ids local to each input.  leaf_maxes: per input (0: params')."""
+    datas = [_contig(x, "float32") for x in datas]
+    leaf_maxes = leaf_maxes or [0] * len(datas)
+    k = params.k
+    outs = [(_empty_like_input(x, (x.shape[0], k), "int32"), _empty_like_input(x, (x.shape[0], k), "float32"))
+            for x in datas]
+    arr = (Instance * len(datas))()
+    for i, (x, (ids, d)) in enumerate(zip(datas, outs)):
+        arr[i].data = _ptr(x).value
+        arr[i].n = x.shape[0]
+        arr[i].D = x.shape[1]
+        arr[i].leaf_max = int(leaf_maxes[i])
+        arr[i].out_ids = _ptr(ids).value
+        arr[i].out_dists = _ptr(d).value
+    with _DeviceCtx(datas[0], stream) as s:
+        _check(load().knng_build_batched(len(datas), arr, ctypes.byref(params), s))
+    return outs
 
 
 def knng_refine(data, ids, dists, params, stream=None):

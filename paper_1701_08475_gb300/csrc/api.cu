@@ -292,18 +292,21 @@ struct TreePlan {
     std::vector<LevelPlan> levels;
     std::vector<int32_t> host;               // packed device image
     struct Idx {
-        size_t seg_off, tiles, seg_tile0, sweep, seg_sweep0;  // element offsets into the image
+        size_t seg_off, tiles, seg_tile0, sweep, seg_sweep0, seg_local;  // element offsets into the image
     };
+    bool forest = false;
     std::vector<Idx> idx;
     size_t leaf_off_at = 0;
     int nseg_max = 0, ntiles_max = 0, nsweep_max = 0, nseg_large_max = 0, max_leaf = 0;
 
-    // tiles of at most `size` positions inside one segment: {seg, begin, end, first}
-    static void tile_level(const std::vector<int32_t>& o, int size, std::vector<int32_t>& tiles,
-                           std::vector<int32_t>& first) {
+    // tiles of at most `size` positions inside one segment: {seg, begin, end,
+    // first}; segments with split[sgi] == 0 get none
+    static void tile_level(const std::vector<int32_t>& o, const std::vector<char>& split, int size,
+                           std::vector<int32_t>& tiles, std::vector<int32_t>& first) {
         const int nseg = (int)o.size() - 1;
         for (int sgi = 0; sgi < nseg; ++sgi) {
             first.push_back((int32_t)(tiles.size() / 4));
+            if (!split[sgi]) continue;
             const int a = o[sgi], b = o[sgi + 1];
             for (int t = a; t < b; t += size) {
                 tiles.push_back(sgi);
@@ -315,18 +318,46 @@ struct TreePlan {
         first.push_back((int32_t)(tiles.size() / 4));
     }
 
-    void make(int64_t n_, int leaf_max) {
-        n = n_;
-        L = tree_depth(n, leaf_max);
+    void make(int64_t n_, int leaf_max) { make_forest({n_}, {leaf_max}); }
+
+    // Independent trees side by side (instance i owns positions
+    // [sum of n_j for j < i, + n_i)); tree i stops splitting at its own depth,
+    // and its segments keep their own indices for the seeds.
+    void make_forest(const std::vector<int64_t>& sizes, const std::vector<int>& leaf_maxes) {
+        const int ni = (int)sizes.size();
+        n = 0;
+        for (int64_t v : sizes) n += v;
+        std::vector<int> depth(ni);
+        L = 0;
+        for (int i = 0; i < ni; ++i) {
+            depth[i] = tree_depth(sizes[i], leaf_maxes[i]);
+            L = std::max(L, depth[i]);
+        }
+        forest = ni > 1;
         off.assign(L + 1, {});
-        off[0] = {0, (int32_t)n};
+        std::vector<std::vector<int32_t>> owner(L + 1), local(L + 1);
+        off[0].push_back(0);
+        for (int i = 0; i < ni; ++i) {
+            off[0].push_back(off[0].back() + (int32_t)sizes[i]);
+            owner[0].push_back(i);
+            local[0].push_back(0);
+        }
+        std::vector<std::vector<char>> split(L);
         for (int l = 0; l < L; ++l) {
-            auto& o = off[l];
+            const auto& o = off[l];
             auto& nx = off[l + 1];
-            nx.clear();
             for (size_t sgi = 0; sgi + 1 < o.size(); ++sgi) {
+                const int inst = owner[l][sgi];
+                const bool sp = l < depth[inst];
+                split[l].push_back(sp ? 1 : 0);
                 nx.push_back(o[sgi]);
-                nx.push_back(o[sgi] + (o[sgi + 1] - o[sgi]) / 2);
+                owner[l + 1].push_back(inst);
+                local[l + 1].push_back(sp ? 2 * local[l][sgi] : local[l][sgi]);
+                if (sp) {
+                    nx.push_back(o[sgi] + (o[sgi + 1] - o[sgi]) / 2);
+                    owner[l + 1].push_back(inst);
+                    local[l + 1].push_back(2 * local[l][sgi] + 1);
+                }
             }
             nx.push_back((int32_t)n);
         }
@@ -338,10 +369,14 @@ struct TreePlan {
             const auto& o = off[l];
             const int nseg = (int)o.size() - 1;
             std::vector<int32_t> tiles, tile0, sweep, sweep0;
-            tile_level(o, kTile, tiles, tile0);
-            tile_level(o, kSweepTile, sweep, sweep0);
+            tile_level(o, split[l], kTile, tiles, tile0);
+            tile_level(o, split[l], kSweepTile, sweep, sweep0);
             int max_m = 0;
-            for (int sgi = 0; sgi < nseg; ++sgi) max_m = std::max(max_m, o[sgi + 1] - o[sgi]);
+            bool frozen = false;
+            for (int sgi = 0; sgi < nseg; ++sgi) {
+                if (split[l][sgi]) max_m = std::max(max_m, o[sgi + 1] - o[sgi]);
+                else frozen = true;
+            }
             LevelPlan& lp = levels[l];
             lp.level = l;
             lp.n = (int)n;
@@ -351,6 +386,7 @@ struct TreePlan {
             lp.max_m = max_m;
             lp.pos_bits = bits_for(max_m - 1);
             lp.small = max_m <= kSmallMax;
+            lp.frozen = frozen;
             nseg_max = std::max(nseg_max, nseg);
             ntiles_max = std::max(ntiles_max, lp.ntiles);
             nsweep_max = std::max(nsweep_max, lp.nsweep);
@@ -367,6 +403,8 @@ struct TreePlan {
             host.insert(host.end(), tile0.begin(), tile0.end());
             idx[l].seg_sweep0 = host.size();
             host.insert(host.end(), sweep0.begin(), sweep0.end());
+            idx[l].seg_local = host.size();
+            if (forest) host.insert(host.end(), local[l].begin(), local[l].end());
         }
         leaf_off_at = host.size();
         host.insert(host.end(), off[L].begin(), off[L].end());
@@ -381,6 +419,7 @@ struct TreePlan {
             levels[l].seg_off = dev + idx[l].seg_off;
             levels[l].seg_tile0 = dev + idx[l].seg_tile0;
             levels[l].seg_sweep0 = dev + idx[l].seg_sweep0;
+            levels[l].seg_local = forest ? dev + idx[l].seg_local : nullptr;
         }
     }
 };
@@ -692,6 +731,83 @@ int knng_build_ex(const float* data, int64_t n, int D, const knng_params* p, int
         check_status(b.status, s,
                      lp_leaf(a, tp) ? (p->precision == KNNG_BF16 ? "k2_leaf_bf16" : "k2_leaf_fp16") : nullptr);
         offers_end(b);
+    });
+}
+
+int knng_build_batched(int n_inst, const knng_instance* inst, const knng_params* p, void* stream) {
+    return guarded([&] {
+        if (!p) fail(KNNG_EINVAL, "params is NULL");
+        if (n_inst < 1 || !inst) fail(KNNG_EINVAL, "n_inst = %d (need >= 1 and an instance array)", n_inst);
+        // every instance is checked before any device work
+        std::map<int, std::vector<int>> by_dim;
+        for (int i = 0; i < n_inst; ++i) {
+            const knng_instance& in = inst[i];
+            knng_params q = *p;
+            if (in.leaf_max > 0) q.leaf_max = in.leaf_max;
+            try {
+                validate_common(in.data, in.n, in.D, q.k);
+                validate_params(&q, in.n);
+                if (!in.out_ids || !in.out_dists) fail(KNNG_EINVAL, "output pointer is NULL");
+            } catch (const Error& e) {
+                const std::string msg = g_last_error;
+                fail(e.code, "instance %d: %s", i, msg.c_str());
+            }
+            by_dim[in.D].push_back(i);
+        }
+        cudaStream_t s = (cudaStream_t)stream;
+        const int k = p->k;
+        for (const auto& grp : by_dim) {
+            const int D = grp.first;
+            const std::vector<int>& ids = grp.second;
+            std::vector<int64_t> sizes, first;
+            std::vector<int> leafs;
+            int64_t n = 0;
+            for (int i : ids) {
+                first.push_back(n);
+                sizes.push_back(inst[i].n);
+                leafs.push_back(inst[i].leaf_max > 0 ? inst[i].leaf_max : p->leaf_max);
+                n += inst[i].n;
+            }
+            if (n >= ((int64_t)1 << 31) || n * (int64_t)k >= ((int64_t)1 << 31))
+                fail(KNNG_EINVAL, "the instances of D = %d hold %lld points together (must stay below 2^31, "
+                     "and n * k too)", D, (long long)n);
+            Args a{n, D, *p};
+            TreePlan tp;
+            if (p->tree_passes > 0) tp.make_forest(sizes, leafs);
+            Workspace ws;
+            BuildLayout b;
+            float* X = nullptr;
+            int32_t* oi = nullptr;
+            float* od = nullptr;
+            const size_t nk = (size_t)n * k;
+            for (int pass = 0; pass < 2; ++pass) {  // layout, then real pointers
+                ws.used = 0;
+                X = ws.take<float>((size_t)n * D);
+                oi = ws.take<int32_t>(nk);
+                od = ws.take<float>(nk);
+                carve(ws, b, a, tp, p->tree_passes > 0, p->refine_rounds > 0);
+                if (pass == 0) ws.allocate(s);
+            }
+            if (p->tree_passes > 0) tp.rebase(b.plan_dev);
+            cuda_check(cudaMemsetAsync(b.status, 0, 4 * sizeof(int), s), "status clear");
+            offers_begin(b, s);
+            for (size_t t = 0; t < ids.size(); ++t)
+                cuda_check(cudaMemcpyAsync(X + first[t] * D, inst[ids[t]].data, sizeof(float) * sizes[t] * D,
+                                           cudaMemcpyDefault, s),
+                           "instance copy");
+            build_core(X, a, b, tp, s);
+            for (size_t t = 0; t < ids.size(); ++t) {
+                const knng_instance& in = inst[ids[t]];
+                const size_t off = (size_t)first[t] * k, cnt = (size_t)sizes[t] * k;
+                launch_unpack(b.G + off, oi + off, od + off, (int64_t)cnt, s, first[t]);
+                cuda_check(cudaMemcpyAsync(in.out_ids, oi + off, cnt * 4, cudaMemcpyDefault, s), "ids copy");
+                cuda_check(cudaMemcpyAsync(in.out_dists, od + off, cnt * 4, cudaMemcpyDefault, s), "dists copy");
+            }
+            cuda_check(cudaGetLastError(), "kernel launch");
+            check_status(b.status, s,
+                         lp_leaf(a, tp) ? (p->precision == KNNG_BF16 ? "k2_leaf_bf16" : "k2_leaf_fp16") : nullptr);
+            offers_end(b);
+        }
     });
 }
 

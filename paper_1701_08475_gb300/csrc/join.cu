@@ -128,14 +128,14 @@ __global__ void k_check_ids(const int32_t* __restrict__ ids, int64_t count, int6
 }
 
 __global__ void k_unpack(const uint64_t* __restrict__ G, int32_t* __restrict__ ids, float* __restrict__ d,
-                         int64_t count) {
+                         int64_t count, int64_t id_offset) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = G[e];
         if (key == kEmptyKey) {
             ids[e] = -1;
             d[e] = __int_as_float(0x7f800000);
         } else {
-            ids[e] = (int32_t)key_id(key);
+            ids[e] = (int32_t)((int64_t)key_id(key) - id_offset);
             d[e] = key_dist(key);
         }
     }
@@ -717,9 +717,9 @@ void launch_check_ids(const int32_t* ids, int64_t count, int64_t lo, int64_t hi,
     k_check_ids<<<grid_for(count, 256), 256, 0, s>>>(ids, count, lo, hi, status);
 }
 
-void launch_unpack(const uint64_t* G, int32_t* ids, float* d, int64_t count, cudaStream_t s) {
+void launch_unpack(const uint64_t* G, int32_t* ids, float* d, int64_t count, cudaStream_t s, int64_t id_offset) {
     LaunchScope ls("k_unpack", s, count * 16.0, 0);
-    k_unpack<<<grid_for(count, 256), 256, 0, s>>>(G, ids, d, count);
+    k_unpack<<<grid_for(count, 256), 256, 0, s>>>(G, ids, d, count, id_offset);
 }
 
 void launch_reverse_lists(const uint64_t* G, int64_t n, int k, const JoinBuffers& b, cudaStream_t s) {

@@ -45,6 +45,12 @@ struct LevelPlan {
     const int32_t* seg_tile0;  // device [nseg + 1] first select tile of each segment
     const int4* sweep;         // device [nsweep] sweep tiles, same layout
     const int32_t* seg_sweep0; // device [nseg + 1] first sweep tile of each segment
+    // Forests (independent instances side by side): a segment with no tiles
+    // is a finished tree's leaf and does not split (`frozen`: the level has
+    // one); seg_local[seg] is the segment's index within its own tree at this
+    // level (NULL: the global index, one tree)
+    const int32_t* seg_local = nullptr;
+    bool frozen = false;
 };
 
 struct SplitBuffers {
@@ -167,7 +173,8 @@ void launch_pack(const int32_t* ids, const float* d, uint64_t* G, int64_t count,
                  cudaStream_t s);
 // Sets kStatusBadInput if any of ids[0 .. count) lies outside [lo, hi).
 void launch_check_ids(const int32_t* ids, int64_t count, int64_t lo, int64_t hi, int* status, cudaStream_t s);
-void launch_unpack(const uint64_t* G, int32_t* ids, float* d, int64_t count, cudaStream_t s);
+// ids are written as key id - id_offset (an instance's first row in a forest)
+void launch_unpack(const uint64_t* G, int32_t* ids, float* d, int64_t count, cudaStream_t s, int64_t id_offset = 0);
 
 // ---------------------------------------------------------------- exact / recall (K7)
 void launch_exact(const float* X, int64_t n, int D, int k, const int32_t* sample, int64_t s_rows,

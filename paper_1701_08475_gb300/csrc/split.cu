@@ -88,15 +88,19 @@ __device__ __forceinline__ void find_digit(const uint32_t* hist, int nb, uint32_
 }
 
 __global__ void k1_init(const float* __restrict__ X, int D, const int32_t* __restrict__ perm,
-                        const int32_t* __restrict__ seg_off, int level, uint64_t pass_seed,
+                        const int32_t* __restrict__ seg_off, const int32_t* __restrict__ seg_tile0,
+                        const int32_t* __restrict__ seg_local, int level, uint64_t pass_seed,
                         float* __restrict__ W, const int* __restrict__ status) {
     if (*status & kStatusStop) return;  // perm may hold unwritten slots
     const int seg = blockIdx.x;
+    if (seg_tile0[seg + 1] == seg_tile0[seg]) return;  // a finished tree's leaf: it does not split
     const int a = seg_off[seg];
     const int m = seg_off[seg + 1] - a;
     // initial centroids: the points at positions h, h2 of the segment, drawn
-    // from SplitMix64 of (pass seed, level, segment index); h2 != h
-    const uint64_t r1 = splitmix64(splitmix64(splitmix64(pass_seed) ^ (uint64_t)level) ^ (uint64_t)seg);
+    // from SplitMix64 of (pass seed, level, segment index in its own tree);
+    // h2 != h
+    const uint64_t sl = seg_local ? (uint64_t)seg_local[seg] : (uint64_t)seg;
+    const uint64_t r1 = splitmix64(splitmix64(splitmix64(pass_seed) ^ (uint64_t)level) ^ sl);
     const uint64_t r2 = splitmix64(r1);
     const int64_t h = (int64_t)(r1 % (uint64_t)m);
     const int64_t h2 = (h + 1 + (int64_t)(r2 % (uint64_t)(m - 1))) % m;
@@ -333,7 +337,8 @@ __global__ void __launch_bounds__(kPrRows) k1_project_async(const float* __restr
 // selects the floor(m/2)-th key, and either records it (thr) or, on the
 // final cut, partitions the segment stably into perm_out.
 __global__ void __launch_bounds__(1024) k1_select_small(const float* __restrict__ S,
-                                                        const int32_t* __restrict__ seg_off, int pos_bits,
+                                                        const int32_t* __restrict__ seg_off,
+                                                        const int32_t* __restrict__ seg_tile0, int pos_bits,
                                                         uint64_t* __restrict__ thr,
                                                         const int32_t* __restrict__ perm_in,
                                                         int32_t* __restrict__ perm_out, int* __restrict__ status) {
@@ -342,6 +347,7 @@ __global__ void __launch_bounds__(1024) k1_select_small(const float* __restrict_
     __shared__ int sh_digit;
     __shared__ uint32_t sh_below;
     __shared__ int warp_tot[32];
+    if (seg_tile0[blockIdx.x + 1] == seg_tile0[blockIdx.x]) return;  // a finished tree's leaf
     const int seg = blockIdx.x, a = seg_off[seg], m = seg_off[seg + 1] - a;
     for (int p = threadIdx.x; p < m; p += blockDim.x) keys[p] = sel_key(S[a + p], p, pos_bits);
     uint64_t prefix = 0;
@@ -782,6 +788,7 @@ __global__ void __launch_bounds__(128 * kCenGroups) k1_centroids(const double* _
     const int m = seg_off[seg + 1] - seg_off[seg];
     const int K = m / 2;
     const int t0 = seg_tile0[seg], t1 = seg_tile0[seg + 1];
+    if (t0 == t1) return;  // a finished tree's leaf: no centroids
     const int dl = threadIdx.x & 127, g = threadIdx.x >> 7;
     for (int db = 0; db < D; db += 128) {
         const int d = db + dl;
@@ -869,9 +876,13 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
     const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     const bool vec2 = (D % 2 == 0) && ((reinterpret_cast<uintptr_t>(X) & 7) == 0);
     const int dchunks = (D + 127) / 128;
+    // finished trees' leaves keep their place: the cut below writes only the
+    // segments that split
+    if (lp.frozen) cudaMemcpyAsync(perm_out, perm_in, sizeof(int32_t) * (size_t)lp.n, cudaMemcpyDeviceToDevice, s);
     {
         LaunchScope ls("k1_init", s, (double)lp.nseg * 3 * D * 4, 0);
-        k1_init<<<lp.nseg, 128, 0, s>>>(X, D, perm_in, lp.seg_off, lp.level, pass_seed, b.W, b.status);
+        k1_init<<<lp.nseg, 128, 0, s>>>(X, D, perm_in, lp.seg_off, lp.seg_tile0, lp.seg_local, lp.level, pass_seed,
+                                        b.W, b.status);
     }
     for (int it = 0; it <= iters; ++it) {
         const bool last = it == iters;
@@ -895,7 +906,7 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
             const int nt = std::min(1024, std::max(128, (lp.max_m + 31) & ~31));
             LaunchScope ls("k1_select_small", s, n * 4 + (last ? n * 8 : 0), 0);
             cudaFuncSetAttribute(k1_select_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k1_select_small<<<lp.nseg, nt, smem, s>>>(b.S, lp.seg_off, lp.pos_bits, b.thr, perm_in,
+            k1_select_small<<<lp.nseg, nt, smem, s>>>(b.S, lp.seg_off, lp.seg_tile0, lp.pos_bits, b.thr, perm_in,
                                                       last ? perm_out : nullptr, b.status);
             if (last) break;
         } else {

@@ -331,3 +331,33 @@ def test_empty_sample_and_zero_passes(knng):
     assert np.all(_np(ids) == -1) and np.all(np.isinf(_np(d)))
     gi, gd = knng.knng_exact(_dev(X), 4, _dev(np.zeros(0, np.int32)))
     assert _np(gi).shape == (0, 4)
+
+
+# ---------------------------------------------------------------- batched instances
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_batched_build_equals_single_builds(knng, precision):
+    # instances of several sizes, dims and cluster bounds in one forest build:
+    # each result equals the instance built alone
+    specs = [(2000, 64, 64), (5003, 64, 128), (777, 128, 40), (12000, 64, 64), (3000, 128, 128), (150, 64, 40)]
+    k = 12
+    datas = [datagen.gaussian_mixture(n, D, 20, seed=n + D) if i % 2 else
+             datagen.sift_like(n, D=D, n_centres=30, seed=n) for i, (n, D, _) in enumerate(specs)]
+    prec = {"fp32": knng.KNNG_FP32, "bf16": knng.KNNG_BF16}[precision]
+    p = knng.default_params(k=k, leaf_max=64, tree_passes=2, refine_rounds=2, seed=21, precision=prec)
+    outs = knng.knng_build_batched([_dev(X) for X in datas], p, leaf_maxes=[lm for _, _, lm in specs])
+    for (n, D, lm), X, (ids, d) in zip(specs, datas, outs):
+        q = knng.default_params(k=k, leaf_max=lm, tree_passes=2, refine_rounds=2, seed=21, precision=prec)
+        ids1, d1 = knng.knng_build_ex(_dev(X), q)
+        _assert_graph_equal(ids, d, _np(ids1), _np(d1))
+
+
+def test_batched_build_host_buffers_and_errors(knng):
+    X1 = datagen.gaussian_mixture(1000, 16, 10, seed=1)
+    X2 = datagen.gaussian_mixture(1500, 16, 10, seed=2)
+    p = knng.default_params(k=8, leaf_max=32, tree_passes=1, refine_rounds=1, seed=3)
+    outs = knng.knng_build_batched([X1, X2], p)      # numpy: host buffers through the C ABI
+    for X, (ids, d) in zip([X1, X2], outs):
+        ids1, d1 = knng.knng_build_ex(_dev(X), p)
+        _assert_graph_equal(ids, d, _np(ids1), _np(d1))
+    with pytest.raises(knng.KnngError):
+        knng.knng_build_batched([X1, X2[:5]], p)      # second instance: n <= k
