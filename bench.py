@@ -416,8 +416,82 @@ def run_ours(args, cfg):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """The batched workload: 64 independent instances in one knng_build_batched
+    call per step, leaf_max per D from the autotuner (time not counted)."""
+    import torch
+    import paper_1701_08475_gb300 as knng
+    from paper_1701_08475_gb300.autotune import autotune_leaf_max
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    w = datagen.BATCHED
+    datas = datagen.batched_mixtures(n_inst=w["n_inst"], seed=w["seed"] + rank)
+    n_tot = sum(x.shape[0] for x in datas)
+    dev = [torch.from_numpy(x).cuda() for x in datas]
+    prec = PRECISIONS[args.precision]
+    p = knng.default_params(k=w["k"], leaf_max=128, tree_passes=w["passes"], refine_rounds=w["rounds"],
+                            join_mode=knng.KNNG_JOIN_FWD_REV, seed=w["seed"], precision=prec)
+    leafs, report = autotune_leaf_max(dev, p)
+    stream = torch.cuda.Stream()
+
+    def timed(q):
+        with torch.cuda.stream(stream):
+            for _ in range(max(3, args.warmup)):
+                outs = knng.knng_build_batched(dev, q, leaf_maxes=leafs, stream=stream)
+        torch.cuda.synchronize()
+        knng.stats_reset()
+        knng.stats_enable(True, timing=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(args.steps):
+                outs = knng.knng_build_batched(dev, q, leaf_maxes=leafs, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        launches = sum(v["launches"] for v in knng.stats().values())
+        knng.stats_enable(False)
+        return e0.elapsed_time(e1), outs, launches
+
+    ms, outs, launches = timed(p)
+    # recall on 200 sampled rows of every instance
+    hit = tot = 0
+    for x, (ids, d) in zip(dev, outs):
+        smp = torch.from_numpy(datagen.sample_rows(x.shape[0], 200, seed=5)).cuda()
+        gi, gd = knng.knng_exact(x, w["k"], smp)
+        r = knng.knng_recall(ids, d, gi, gd, smp)[0]
+        hit += r * len(smp)
+        tot += len(smp)
+    q32 = knng.default_params(k=w["k"], leaf_max=128, tree_passes=w["passes"], refine_rounds=w["rounds"],
+                              join_mode=knng.KNNG_JOIN_FWD_REV, seed=w["seed"], precision=knng.KNNG_FP32)
+    ms32, outs32, _ = timed(q32)
+    same = all(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) for a, b in zip(outs, outs32))
+    line = {
+        "metric": "kNN-graph build points/s at recall@k vs exact", "value": round(n_tot * args.steps / (ms * 1e-3), 1),
+        "unit": "points/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else args.precision + "+f32", "data": "synthetic",
+        "config": {"workload": w["name"], "instances": len(datas), "points": int(n_tot), "k": w["k"],
+                   "tree_passes": w["passes"], "refine_rounds": w["rounds"], "precision": args.precision,
+                   "leaf_max_by_D": {str(x.shape[1]): l for x, l in zip(datas, leafs)},
+                   "autotune": {str(D): rows for D, rows in report.items()}},
+        "recall_at_k": {"ids": round(hit / tot, 5), "sample_rows": int(tot)},
+        "fp32_form": {"value": round(n_tot * args.steps / (ms32 * 1e-3), 1), "ms_per_step": round(ms32 / args.steps, 3),
+                      "graph_identical": bool(same)},
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == datagen.BATCHED["name"]:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no reference arm; "
+                              "the oracle arm runs the single-instance workloads"}))
+            return
+        run_batched(args)
+        return
     cfg = workload_config(args.workload)
     if args.impl == "reference":
         run_reference(args, cfg)

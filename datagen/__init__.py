@@ -10,8 +10,8 @@ and clustered structure.  No item of either dataset is reproduced.
 """
 import numpy as np
 
-__all__ = ["gaussian_mixture", "sift_like", "gist_like", "unit_mixture",
-           "WORKLOADS", "make", "sample_rows"]
+__all__ = ["gaussian_mixture", "sift_like", "gist_like", "unit_mixture", "batched_mixtures",
+           "WORKLOADS", "BATCHED", "make", "sample_rows"]
 
 
 def gaussian_mixture(n, D, n_centres, seed, lo=-10.0, hi=10.0, sigma=1.0):
@@ -110,6 +110,10 @@ def unit_mixture(n, D=96, n_centres=10000, seed=0, sigma=0.1, chunk=1 << 20):
     return X
 
 
+# The batched workload: 64 independent Gaussian mixtures of 2,000 - 200,000
+# points, D in {64, 128, 256}, k = 16, leaf_max chosen per D by the autotuner.
+BATCHED = dict(name="batched-64-gmm", n_inst=64, seed=1238, k=16, passes=3, rounds=4)
+
 # Workload recipes: sizes and build parameters of the graph workloads.
 WORKLOADS = {
     "gmm-10k-d32": dict(gen="gaussian_mixture", n=10_000, D=32, n_centres=50, seed=1235,
@@ -121,6 +125,20 @@ WORKLOADS = {
     "unit-10m-d96": dict(gen="unit_mixture", n=10_000_000, D=96, n_centres=10000, seed=1239,
                          k=16, leaf_max=128, passes=3, rounds=4),
 }
+
+
+def batched_mixtures(n_inst=64, seed=1238, n_lo=2000, n_hi=200000, dims=(64, 128, 256), c_lo=20, c_hi=500):
+    """Independent instances for a batched build: n ~ U[n_lo, n_hi], D drawn
+    from `dims`, each an isotropic Gaussian mixture (centres U[-10, 10],
+    sigma 1) with U[c_lo, c_hi] centres.  Returns a list of (n x D) arrays."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_inst):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        D = int(dims[int(rng.integers(0, len(dims)))])
+        c = int(rng.integers(c_lo, c_hi + 1))
+        out.append(gaussian_mixture(n, D, c, seed=seed * 1000 + i))
+    return out
 
 
 def make(name, n=None):

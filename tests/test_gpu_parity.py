@@ -361,3 +361,19 @@ def test_batched_build_host_buffers_and_errors(knng):
         _assert_graph_equal(ids, d, _np(ids1), _np(d1))
     with pytest.raises(knng.KnngError):
         knng.knng_build_batched([X1, X2[:5]], p)      # second instance: n <= k
+
+
+def test_autotune_leaf_max_picks_a_measured_candidate(knng):
+    from paper_1701_08475_gb300.autotune import autotune_leaf_max
+    datas = [_dev(datagen.gaussian_mixture(6000, 32, 30, seed=1)), _dev(datagen.gaussian_mixture(3000, 64, 30, seed=2)),
+             _dev(datagen.gaussian_mixture(4000, 32, 30, seed=3))]
+    p = knng.default_params(k=10, tree_passes=1, refine_rounds=1, seed=4)
+    leafs, report = autotune_leaf_max(datas, p, pilot_rows=4000, sample_rows=200)
+    assert leafs[0] == leafs[2]                   # one choice per D
+    assert set(report) == {32, 64}
+    for D, rows in report.items():
+        assert [r[0] for r in rows] == [64, 128, 256]
+        assert all(r[1] > 0 and 0 <= r[2] <= 1 for r in rows)
+        best = max(r[2] for r in rows)
+        pick = [r for r in rows if r[0] == leafs[0 if D == 32 else 1]][0]
+        assert pick[2] >= best - 0.002
