@@ -144,9 +144,9 @@ __host__ __device__ inline TcSmem tc_smem(int Dp) {
     L.dt_off = (size_t)L.stages * kStageBytes;
     L.bar_off = L.dt_off + (size_t)kTcRows * kDtStride * 4;
     L.misc_off = L.bar_off + (size_t)(2 * L.stages + 1) * 8;
-    // misc: tmem address, abort flag, ids[128], nrm[128], err[128], two maxima;
-    // then 32 keys of merge scratch per warp
-    L.scratch_off = L.misc_off + 16 + 3 * kTcRows * 4 + 16;
+    // misc: tmem address, abort flag, ids[128], nrm[128], err[128], two maxima,
+    // sqrt of the norms (rounded up)[128]; then 32 keys of merge scratch per warp
+    L.scratch_off = L.misc_off + 16 + 3 * kTcRows * 4 + 16 + kTcRows * 4;
     L.total = L.scratch_off + (kTcThreads / 32) * 32 * 8;
     return L;
 }
@@ -177,6 +177,9 @@ __device__ __forceinline__ float canon_dist(const float* __restrict__ xa, const 
     return acc;
 }
 
+
+// the key that lane `src` holds
+__device__ __forceinline__ uint64_t lane_key(uint64_t v, int src) { return shfl64(v, src); }
 
 // entry r of a list held lane-major in NO slots (r < 32 * NO)
 template <int NO>
@@ -209,6 +212,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
     float* snrm = reinterpret_cast<float*>(sid + kTcRows);
     float* serr = snrm + kTcRows;
     float* smax = serr + kTcRows;  // [0] max ||x^||, [1] max e
+    float* srt = smax + 4;         // [128] ||x^|| rounded up
 
     const int S = L.stages, nk = Dp / kTcK;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -305,7 +309,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
     if (warp == 0) tc::tmem_dealloc(tmem, kTcRows);
     if (!ok) return;
 
-    // leaf maxima of ||x^|| and e for the certificate
+    // leaf maxima of ||x^|| and e for the certificate; every ||x^|| rounded up
+    for (int r = tid; r < kTcRows; r += kTcThreads) srt[r] = r < m ? __fsqrt_ru(snrm[r]) : 0.f;
     if (warp == 0) {
         float mn = 0.f, me = 0.f;
         for (int r = lane; r < m; r += 32) {
@@ -363,6 +368,57 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
             warp_select_unique<NC + NSG, NSG>(cand, k, res);
             done_row = true;
         } else if (m - 1 > 0) {
+            if (NSG == 1 && lane_key(old[0], k - 1) != kEmptyKey) {
+                // After the first pass: a candidate whose exact distance provably
+                // exceeds the row's k-th entry cannot enter.  With the bound of
+                // the certificate below, per candidate and rounded so that it
+                // stays a lower bound: d >= (sqrt(a - eps) - e_i - e_j)^2.  The
+                // rest (usually a few) get canonical distances and one merge.
+                const float tau = key_dist(lane_key(old[0], k - 1));
+                const float cD = (16.f * Dp + 8.f) * 5.9604644775390625e-8f;
+                unsigned bal[NC];
+                int total = 0;
+#pragma unroll
+                for (int s = 0; s < NC; ++s) {
+                    const int c = lane + 32 * s;
+                    bool keep = c < m && c != r;
+                    if (keep) {
+                        const float a = dt[r * kDtStride + c];
+                        const float sn = __fadd_ru(srt[r], srt[c]);
+                        const float eps = __fadd_ru(__fmul_ru(cD, __fmul_ru(sn, sn)), __fmul_ru(1.1920928955078125e-7f, fabsf(a)));
+                        const float lo = __fsub_rd(a, eps);
+                        if (lo > 0.f) {
+                            const float root = __fsub_rd(__fsub_rd(__fsqrt_rd(lo), serr[r]), serr[c]);
+                            if (root > 0.f && __fmul_rd(root, root) > tau) keep = false;
+                        }
+                    }
+                    bal[s] = __ballot_sync(0xffffffffu, keep);
+                    total += __popc(bal[s]);
+                }
+                if (total <= 32) {
+                    // survivors' columns to lanes, then their canonical keys
+                    int* cols = reinterpret_cast<int*>(wscratch);
+                    int at = 0;
+#pragma unroll
+                    for (int s = 0; s < NC; ++s) {
+                        if ((bal[s] >> lane) & 1u) cols[at + __popc(bal[s] & ((1u << lane) - 1u))] = lane + 32 * s;
+                        at += __popc(bal[s]);
+                    }
+                    __syncwarp();
+                    const int c = lane < total ? cols[lane] : -1;
+                    __syncwarp();
+                    uint64_t one[1] = {kEmptyKey};
+                    if (c >= 0)
+                        one[0] = make_key(canon_dist(X + (int64_t)gi * D, X + (int64_t)sid[c] * D, D, vec),
+                                          (uint32_t)sid[c]);
+                    uint64_t out;
+                    bool changed;
+                    if (warp_merge_few<1>(one, old[0], k, wscratch, out, changed)) {
+                        if (changed && lane < k) grow[lane] = out;
+                        continue;
+                    }
+                }
+            }
             // the kp + 1 best approximate candidates (keys unique: distinct ids)
             uint64_t apx[NC];
 #pragma unroll
