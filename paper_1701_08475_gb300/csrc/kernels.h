@@ -28,7 +28,7 @@ void launch_check_finite(const float* X, int64_t count, int* status, cudaStream_
 struct SelState {
     uint64_t prefix;  // known high bits of the selected key
     uint32_t krem;    // rank still to select among keys matching prefix
-    uint32_t pad;
+    uint32_t done;    // the selected key is known (thr written)
 };
 
 struct LevelPlan {

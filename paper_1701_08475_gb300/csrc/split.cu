@@ -60,6 +60,17 @@ __device__ __forceinline__ int block_sum(int v, int* warp_tot) {
 }
 
 // Warp 0: digit b with below(b) <= krem < below(b) + hist[b].
+// Radix digits of a selection key (ord32(s) << pos_bits | position), from the
+// top: the 32 value bits in digits of 11, 11 and 10 bits, then the position
+// bits 11 at a time.  `hi` is a digit's upper bound; returns its lower one.
+// Once the value digits are done with krem = 0, the selected key is the first
+// of its value, so (value << pos_bits) is an equivalent threshold (every key
+// of that value goes right) and the position digits are skipped.
+__host__ __device__ inline int digit_lo(int hi, int pos_bits) {
+    return hi > pos_bits ? (hi - kRadixBits > pos_bits ? hi - kRadixBits : pos_bits)
+                         : (hi - kRadixBits > 0 ? hi - kRadixBits : 0);
+}
+
 __device__ __forceinline__ void find_digit(const uint32_t* hist, int nb, uint32_t krem, int* out_digit,
                                            uint32_t* out_below) {
     const int lane = threadIdx.x & 31;
@@ -197,6 +208,7 @@ __global__ void __launch_bounds__(256) k1_project(const float* __restrict__ X, i
         const int m = seg_off[seg + 1] - seg_off[seg];
         st[seg].prefix = 0;
         st[seg].krem = (uint32_t)(m / 2);
+        st[seg].done = 0;  // set once the selection is done
     }
     const float* w = W + (int64_t)seg * D;
     if (q == 1)
@@ -323,6 +335,7 @@ __global__ void __launch_bounds__(kPrRows) k1_project_async(const float* __restr
         const int m = seg_off[seg + 1] - seg_off[seg];
         st[seg].prefix = 0;
         st[seg].krem = (uint32_t)(m / 2);
+        st[seg].done = 0;  // set once the selection is done
     }
     const float* w = W + (int64_t)seg * D;
     if (q == 1)
@@ -352,8 +365,9 @@ __global__ void __launch_bounds__(1024) k1_select_small(const float* __restrict_
     for (int p = threadIdx.x; p < m; p += blockDim.x) keys[p] = sel_key(S[a + p], p, pos_bits);
     uint64_t prefix = 0;
     uint32_t krem = (uint32_t)(m / 2);
-    for (int hi = 32 + pos_bits; hi > 0; hi -= kRadixBits) {
-        const int lo = max(hi - kRadixBits, 0), width = hi - lo;
+    for (int hi = 32 + pos_bits, lo; hi > 0 && !(hi == pos_bits && krem == 0); hi = lo) {
+        lo = digit_lo(hi, pos_bits);
+        const int width = hi - lo;
         const uint32_t mask = (1u << width) - 1u;
         for (int b = threadIdx.x; b < (1 << width); b += blockDim.x) hist[b] = 0;
         __syncthreads();
@@ -401,14 +415,15 @@ __global__ void __launch_bounds__(256) k1_select_pass(const float* __restrict__ 
                                                       int hi, SelState* __restrict__ st,
                                                       uint32_t* __restrict__ ghist,
                                                       uint32_t* __restrict__ ticket,
-                                                      uint64_t* __restrict__ thr, int last_pass) {
+                                                      uint64_t* __restrict__ thr) {
     __shared__ uint32_t hist[1 << kRadixBits];
     __shared__ int sh_last, sh_digit;
     __shared__ uint32_t sh_below;
     const int4 t = tiles[blockIdx.x];
     const int seg = t.x, begin = t.y, end = t.z;
+    if (st[seg].done) return;  // selected already (value digits, no tie to the left)
     const int a = seg_off[seg];
-    const int lo = max(hi - kRadixBits, 0), width = hi - lo, nb = 1 << width;
+    const int lo = digit_lo(hi, pos_bits), width = hi - lo, nb = 1 << width;
     const uint32_t mask = (uint32_t)nb - 1u;
     const uint64_t prefix = st[seg].prefix;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
@@ -436,10 +451,14 @@ __global__ void __launch_bounds__(256) k1_select_pass(const float* __restrict__ 
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint64_t np = prefix | ((uint64_t)sh_digit << lo);
+        const uint32_t kr = st[seg].krem - sh_below;
         st[seg].prefix = np;
-        st[seg].krem -= sh_below;
+        st[seg].krem = kr;
         ticket[seg] = 0;
-        if (last_pass) thr[seg] = np;
+        if (lo == 0 || (lo == pos_bits && kr == 0)) {
+            thr[seg] = np;
+            st[seg].done = 1;
+        }
     }
 }
 
@@ -910,11 +929,11 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
                                                       last ? perm_out : nullptr, b.status);
             if (last) break;
         } else {
-            const int TB = 32 + lp.pos_bits;
-            for (int hi = TB; hi > 0; hi -= kRadixBits) {
-                LaunchScope ls("k1_select_pass", s, n * 4, 0);
+            // every digit is launched; a segment whose key is known returns at once
+            for (int hi = 32 + lp.pos_bits; hi > 0; hi = digit_lo(hi, lp.pos_bits)) {
+                LaunchScope ls("k1_select_pass", s, hi > lp.pos_bits ? n * 4 : 0, 0);
                 k1_select_pass<<<lp.ntiles, 256, 0, s>>>(b.S, lp.tiles, lp.seg_off, lp.seg_tile0, lp.pos_bits, hi,
-                                                         b.st, b.ghist, b.ticket, b.thr, hi - kRadixBits <= 0);
+                                                         b.st, b.ghist, b.ticket, b.thr);
             }
             if (last) {
                 {
