@@ -501,7 +501,7 @@ void quantize_for_join(const float* X, const Args& a, BuildLayout& b, cudaStream
 }
 
 bool lp_leaf(const Args& a, const TreePlan& tp) {
-    return a.p.precision != KNNG_FP32 && a.p.tree_passes > 0 && tp.max_leaf <= 128;
+    return a.p.precision != KNNG_FP32 && a.p.tree_passes > 0 && tp.max_leaf <= 256;
 }
 
 void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, bool tree, bool join) {

@@ -128,7 +128,6 @@ __global__ void __launch_bounds__(256) k0_permute16(const uint4* __restrict__ Xq
 constexpr int kTcRows = 128;             // M = N = 128 tile: leaves up to 128 points
 constexpr int kTcK = 64;                 // 16-bit elements per 128-byte swizzled row
 constexpr int kStageBytes = kTcRows * kTcK * 2;
-constexpr int kDtStride = kTcRows + 1;
 constexpr int kTcThreads = 128;
 
 struct TcSmem {
@@ -136,17 +135,20 @@ struct TcSmem {
     size_t stage_off, dt_off, bar_off, misc_off, scratch_off, total;
 };
 
-__host__ __device__ inline TcSmem tc_smem(int Dp) {
+// MT row tiles of 128 (leaves up to 128 MT points): stages of MT boxes, the
+// d^ rows of one tile, barriers, then misc: tmem address, abort flag,
+// ids / norms / errors / rounded-up sqrt norms [128 MT] each, two maxima; then
+// 32 keys of merge scratch per warp
+__host__ __device__ inline TcSmem tc_smem(int Dp, int MT) {
     TcSmem L;
     const int nk = Dp / kTcK;
-    L.stages = nk < 4 ? nk : 4;
+    const int smax = MT == 1 ? 4 : 2;
+    L.stages = nk < smax ? nk : smax;
     L.stage_off = 0;
-    L.dt_off = (size_t)L.stages * kStageBytes;
-    L.bar_off = L.dt_off + (size_t)kTcRows * kDtStride * 4;
+    L.dt_off = (size_t)L.stages * kStageBytes * MT;
+    L.bar_off = L.dt_off + (size_t)kTcRows * (kTcRows * MT + 1) * 4;
     L.misc_off = L.bar_off + (size_t)(2 * L.stages + 1) * 8;
-    // misc: tmem address, abort flag, ids[128], nrm[128], err[128], two maxima,
-    // sqrt of the norms (rounded up)[128]; then 32 keys of merge scratch per warp
-    L.scratch_off = L.misc_off + 16 + 3 * kTcRows * 4 + 16 + kTcRows * 4;
+    L.scratch_off = L.misc_off + 16 + 4 * (size_t)kTcRows * MT * 4 + 16;
     L.total = L.scratch_off + (kTcThreads / 32) * 32 * 8;
     return L;
 }
@@ -191,7 +193,7 @@ __device__ __forceinline__ uint64_t list_at(const uint64_t (&v)[NO], int r) {
     return shfl64(mine, r & 31);
 }
 
-template <bool BF16, int NSG>
+template <bool BF16, int NSG, int MT>
 __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constant__ CUtensorMap tmap, int Dp,
                                                            const float* __restrict__ X, int D,
                                                            const int32_t* __restrict__ perm,
@@ -200,19 +202,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
                                                            const float* __restrict__ qerr, int k, int kp,
                                                            uint64_t* __restrict__ G, int* __restrict__ status,
                                                            const int* __restrict__ notexact) {
+    constexpr int RW = kTcRows * MT;      // leaf rows (and Gram columns) held
+    constexpr int DTS = RW + 1;           // d^ row stride
+    constexpr int SB = kStageBytes * MT;  // one K chunk of all rows
     extern __shared__ uint8_t smem_raw[];
     if (*status & kStatusStop) return;  // whole CTA, before any barrier or tensor memory
-    const TcSmem L = tc_smem(Dp);
+    const TcSmem L = tc_smem(Dp, MT);
     uint8_t* base = smem_raw + ((1024 - (tc::smem_addr(smem_raw) & 1023)) & 1023);
     float* dt = reinterpret_cast<float*>(base + L.dt_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bar_off);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.misc_off);
     int* abort_flag = reinterpret_cast<int*>(base + L.misc_off + 4);
     int32_t* sid = reinterpret_cast<int32_t*>(base + L.misc_off + 16);
-    float* snrm = reinterpret_cast<float*>(sid + kTcRows);
-    float* serr = snrm + kTcRows;
-    float* smax = serr + kTcRows;  // [0] max ||x^||, [1] max e
-    float* srt = smax + 4;         // [128] ||x^|| rounded up
+    float* snrm = reinterpret_cast<float*>(sid + RW);
+    float* serr = snrm + RW;
+    float* srt = serr + RW;   // ||x^|| rounded up
+    float* smax = srt + RW;   // [0] max ||x^||, [1] max e
 
     const int S = L.stages, nk = Dp / kTcK;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -220,6 +225,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
     const int a = leaf_off[leaf];
     const int m = leaf_off[leaf + 1] - a;
     const uint32_t full0 = tc::smem_addr(bars), empty0 = full0 + 8 * S, done = full0 + 16 * S;
+    constexpr uint32_t kCols = kTcRows * MT * MT;  // tensor-memory columns: MT tiles of RW
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
@@ -231,10 +237,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
         *abort_flag = 0;
     }
     if (warp == 0) {
-        tc::tmem_alloc(tc::smem_addr(tmem_slot), kTcRows);
+        tc::tmem_alloc(tc::smem_addr(tmem_slot), kCols);
         tc::tmem_relinquish();
     }
-    for (int r = tid; r < kTcRows; r += kTcThreads) {
+    for (int r = tid; r < RW; r += kTcThreads) {
         const bool in = r < m;
         sid[r] = in ? perm[a + r] : 0;
         snrm[r] = in ? nrm[a + r] : 0.f;
@@ -244,16 +250,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    // ---- producer + MMA issue (one thread)
+    // ---- producer + MMA issue (one thread): per K chunk, row tile t of the
+    // Gram is A = rows 128 t .., B = all RW rows (N = RW), into columns t RW ..
     if (tid == 0) {
         bool ok = true;
-        const uint32_t idesc = tc::idesc_f16(BF16, kTcRows, kTcRows);
+        const uint32_t idesc = tc::idesc_f16(BF16, kTcRows, RW);
         int issued = 0, consumed = 0;
-        for (; issued < S && issued < nk; ++issued) {
-            const uint32_t fb = full0 + 8 * issued;
-            tc::mbar_expect_tx(fb, kStageBytes);
-            tc::tma_load_2d(tc::smem_addr(base + (size_t)issued * kStageBytes), &tmap, issued * kTcK, a, fb);
-        }
+        auto load_stage = [&](int s, int c) {
+            const uint32_t fb = full0 + 8 * s;
+            tc::mbar_expect_tx(fb, SB);
+#pragma unroll
+            for (int t = 0; t < MT; ++t)
+                tc::tma_load_2d(tc::smem_addr(base + (size_t)s * SB + (size_t)t * kStageBytes), &tmap, c * kTcK,
+                                a + t * kTcRows, fb);
+        };
+        for (; issued < S && issued < nk; ++issued) load_stage(issued, issued);
         for (int c = 0; c < nk; ++c) {
             const int s = c % S;
             if (!tc::mbar_wait(full0 + 8 * s, (uint32_t)((c / S) & 1), status)) {
@@ -261,19 +272,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
                 break;
             }
             consumed = c + 1;
-            const uint64_t d0 = tc::sdesc_k128(tc::smem_addr(base + (size_t)s * kStageBytes));
+            const uint64_t d0 = tc::sdesc_k128(tc::smem_addr(base + (size_t)s * SB));
 #pragma unroll
-            for (int kk = 0; kk < kTcK / 16; ++kk)  // K = 16 per instruction: 32 bytes along the row
-                tc::mma_f16(tmem, d0 + 2 * kk, d0 + 2 * kk, idesc, (c | kk) != 0);
+            for (int t = 0; t < MT; ++t)
+#pragma unroll
+                for (int kk = 0; kk < kTcK / 16; ++kk)  // K = 16 per instruction: 32 bytes along the row
+                    tc::mma_f16(tmem + (uint32_t)(t * RW), d0 + (uint64_t)(t * (kStageBytes >> 4)) + 2 * kk,
+                                d0 + 2 * kk, idesc, (c | kk) != 0);
             tc::mma_commit(empty0 + 8 * s);
             if (c + S < nk) {
                 if (!tc::mbar_wait(empty0 + 8 * s, (uint32_t)((c / S) & 1), status)) {
                     ok = false;
                     break;
                 }
-                const uint32_t fb = full0 + 8 * s;
-                tc::mbar_expect_tx(fb, kStageBytes);
-                tc::tma_load_2d(tc::smem_addr(base + (size_t)s * kStageBytes), &tmap, (c + S) * kTcK, a, fb);
+                load_stage(s, c + S);
                 ++issued;
             }
         }
@@ -290,27 +302,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
     // uniform over the CTA: the tensor-memory loads below are warp-collective
     const bool ok = __syncthreads_and(mma_ok) && *abort_flag == 0;
     tc::fence_after_sync();
-    if (ok) {
-        // ---- epilogue: row = TMEM lane = thread
-        const int row = warp * 32 + lane;
-#pragma unroll 1
-        for (int cc = 0; cc < kTcRows / 32; ++cc) {
-            float v[32];
-            tc::tmem_ld_32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int col = cc * 32 + j;
-                dt[row * kDtStride + col] = __fsub_rn(__fadd_rn(snrm[row], snrm[col]), __fmul_rn(2.f, v[j]));
-            }
-        }
+    if (!ok) {
+        tc::fence_before_sync();
+        __syncthreads();
+        if (warp == 0) tc::tmem_dealloc(tmem, kCols);
+        return;
     }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kTcRows);
-    if (!ok) return;
 
     // leaf maxima of ||x^|| and e for the certificate; every ||x^|| rounded up
-    for (int r = tid; r < kTcRows; r += kTcThreads) srt[r] = r < m ? __fsqrt_ru(snrm[r]) : 0.f;
+    for (int r = tid; r < RW; r += kTcThreads) srt[r] = r < m ? __fsqrt_ru(snrm[r]) : 0.f;
     if (warp == 0) {
         float mn = 0.f, me = 0.f;
         for (int r = lane; r < m; r += 32) {
@@ -327,14 +327,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
             smax[1] = me;
         }
     }
-    __syncthreads();
 
     const bool exact = lp_exact(*notexact);
     const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-    constexpr int NC = kTcRows / 32;
+    constexpr int NC = RW / 32;
     uint64_t* wscratch = reinterpret_cast<uint64_t*>(base + L.scratch_off) + warp * 32;
-    for (int r = warp; r < m; r += kTcThreads / 32) {
-        const int gi = sid[r];
+    for (int t = 0; t < MT; ++t) {
+    // ---- this tile's d^ rows: thread = TMEM lane = row 128 t + warp * 32 + lane
+    {
+        const int rl = warp * 32 + lane, R = t * kTcRows + rl;
+#pragma unroll 1
+        for (int cc = 0; cc < RW / 32; ++cc) {
+            float v[32];
+            tc::tmem_ld_32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * RW + cc * 32), v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int col = cc * 32 + j;
+                dt[rl * DTS + col] = __fsub_rn(__fadd_rn(snrm[R], snrm[col]), __fmul_rn(2.f, v[j]));
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (t == MT - 1 && warp == 0) tc::tmem_dealloc(tmem, kCols);
+    const int rows_t = min(kTcRows, m - t * kTcRows);
+    for (int r = warp; r < rows_t; r += kTcThreads / 32) {
+        const int R = t * kTcRows + r;  // the row in the leaf; r: its d^ row
+        const int gi = sid[R];
         uint64_t* grow = G + (int64_t)gi * k;
         uint64_t old[NSG];
 #pragma unroll
@@ -347,7 +366,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
 #pragma unroll
             for (int s = 0; s < NC; ++s) {
                 const int c = lane + 32 * s;
-                cand[s] = (c < m && c != r) ? make_key(__fadd_rn(dt[r * kDtStride + c], 0.f), (uint32_t)sid[c])
+                cand[s] = (c < m && c != R) ? make_key(__fadd_rn(dt[r * DTS + c], 0.f), (uint32_t)sid[c])
                                             : kEmptyKey;
             }
             if (NSG == 1) {
@@ -381,14 +400,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
 #pragma unroll
                 for (int s = 0; s < NC; ++s) {
                     const int c = lane + 32 * s;
-                    bool keep = c < m && c != r;
+                    bool keep = c < m && c != R;
                     if (keep) {
-                        const float a = dt[r * kDtStride + c];
-                        const float sn = __fadd_ru(srt[r], srt[c]);
+                        const float a = dt[r * DTS + c];
+                        const float sn = __fadd_ru(srt[R], srt[c]);
                         const float eps = __fadd_ru(__fmul_ru(cD, __fmul_ru(sn, sn)), __fmul_ru(1.1920928955078125e-7f, fabsf(a)));
                         const float lo = __fsub_rd(a, eps);
                         if (lo > 0.f) {
-                            const float root = __fsub_rd(__fsub_rd(__fsqrt_rd(lo), serr[r]), serr[c]);
+                            const float root = __fsub_rd(__fsub_rd(__fsqrt_rd(lo), serr[R]), serr[c]);
                             if (root > 0.f && __fmul_rd(root, root) > tau) keep = false;
                         }
                     }
@@ -424,7 +443,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
 #pragma unroll
             for (int s = 0; s < NC; ++s) {
                 const int c = lane + 32 * s;
-                apx[s] = (c < m && c != r) ? make_key(__fadd_rn(dt[r * kDtStride + c], 0.f), (uint32_t)sid[c])
+                apx[s] = (c < m && c != R) ? make_key(__fadd_rn(dt[r * DTS + c], 0.f), (uint32_t)sid[c])
                                            : kEmptyKey;
             }
             sort_regs<NC>(apx);
@@ -459,12 +478,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
                 if (tau_key != kEmptyKey) {
                     const double astar = (double)key_dist(astar_key);
                     const double tau = (double)key_dist(tau_key);
-                    const double ni = sqrt((double)snrm[r]);
+                    const double ni = sqrt((double)snrm[R]);
                     const double cD = (16.0 * Dp + 8.0) * 5.9604644775390625e-8;  // 2^-24
                     const double eps = cD * (ni + smax[0]) * (ni + smax[0]) + 1.1920928955078125e-7 * fabs(astar);
                     const double lo = astar - eps;
                     double root = lo > 0.0 ? sqrt(lo) : 0.0;
-                    root -= (double)serr[r] + (double)smax[1];
+                    root -= (double)serr[R] + (double)smax[1];
                     const double lower = root > 0.0 ? root * root : 0.0;
                     done_row = lower * (1.0 - 1e-12) > tau;
                 }
@@ -477,7 +496,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
             for (int s = 0; s < NC; ++s) {
                 const int c = lane + 32 * s;
                 cand[s] = kEmptyKey;
-                if (c < m && c != r)
+                if (c < m && c != R)
                     cand[s] = make_key(canon_dist(X + (int64_t)gi * D, X + (int64_t)sid[c] * D, D, vec),
                                        (uint32_t)sid[c]);
             }
@@ -490,6 +509,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
 #pragma unroll
         for (int s = 0; s < NSG; ++s)
             if (lane + 32 * s < k) grow[lane + 32 * s] = res[s];
+    }
+    __syncthreads();  // the next tile's d^ rows overwrite dt
     }
 }
 
@@ -541,7 +562,8 @@ void launch_permute16(const uint16_t* Xq, const float* nrm, const float* qerr, i
 bool launch_leaf_tc(const uint16_t* Xl, int64_t n, const float* X, int D, const int32_t* perm,
                     const int32_t* leaf_off, int nleaf, int max_leaf, const float* nrm, const float* qerr, int k,
                     int kp, bool bf16, uint64_t* G, int* status, const int* notexact, cudaStream_t s) {
-    if (max_leaf > kTcRows) return false;
+    if (max_leaf > 2 * kTcRows) return false;
+    const int MT = max_leaf > kTcRows ? 2 : 1;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     const int Dp = lp_dim(D);
@@ -555,24 +577,31 @@ bool launch_leaf_tc(const uint16_t* Xl, int64_t n, const float* X, int D, const 
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
-    const TcSmem L = tc_smem(Dp);
+    const TcSmem L = tc_smem(Dp, MT);
     const size_t smem = L.total + 1024;
-    const double mm = (double)max_leaf;
+    if (smem > 227 * 1024) return false;
+    const double mm = (double)max_leaf, rw = 128.0 * MT;
     LaunchScope ls(bf16 ? "k2_leaf_bf16" : "k2_leaf_fp16", s, (double)nleaf * mm * (Dp * 2.0 + 2 * 8.0 * k),
-                   (double)nleaf * 128.0 * 128.0 * 2.0 * Dp);
-#define KNNG_LEAF_TC(B, NS)                                                                                    \
-    do {                                                                                                       \
-        cudaFuncSetAttribute(k2_leaf_tc<B, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
-        k2_leaf_tc<B, NS><<<nleaf, kTcThreads, smem, s>>>(tmap, Dp, X, D, perm, leaf_off, nrm, qerr, k, kp, G, \
-                                                          status, notexact);                                  \
+                   (double)nleaf * rw * rw * 2.0 * Dp);
+#define KNNG_LEAF_TC(B, NS, T)                                                                                  \
+    do {                                                                                                        \
+        cudaFuncSetAttribute(k2_leaf_tc<B, NS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+        k2_leaf_tc<B, NS, T><<<nleaf, kTcThreads, smem, s>>>(tmap, Dp, X, D, perm, leaf_off, nrm, qerr, k, kp, \
+                                                             G, status, notexact);                              \
+    } while (0)
+#define KNNG_LEAF_TC_K(B, T)              \
+    do {                                  \
+        if (k > 32) KNNG_LEAF_TC(B, 2, T); \
+        else KNNG_LEAF_TC(B, 1, T);        \
     } while (0)
     if (bf16) {
-        if (k > 32) KNNG_LEAF_TC(true, 2);
-        else KNNG_LEAF_TC(true, 1);
+        if (MT == 2) KNNG_LEAF_TC_K(true, 2);
+        else KNNG_LEAF_TC_K(true, 1);
     } else {
-        if (k > 32) KNNG_LEAF_TC(false, 2);
-        else KNNG_LEAF_TC(false, 1);
+        if (MT == 2) KNNG_LEAF_TC_K(false, 2);
+        else KNNG_LEAF_TC_K(false, 1);
     }
+#undef KNNG_LEAF_TC_K
 #undef KNNG_LEAF_TC
     return true;
 }

@@ -111,7 +111,9 @@ def _lp_data(kind, n, D, seed):
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 @pytest.mark.parametrize("kind,n,D,k,lm", [("integer", 4000, 128, 20, 128), ("float", 5000, 32, 10, 64),
                                            ("float", 3000, 200, 16, 100), ("signed", 2000, 64, 12, 60),
-                                           ("integer", 1500, 24, 40, 128)])
+                                           ("integer", 1500, 24, 40, 128),
+                                           ("integer", 5000, 64, 16, 256), ("float", 4000, 96, 12, 200),
+                                           ("float", 3000, 320, 10, 160)])   # two 128-row tiles per leaf
 def test_low_precision_build_equals_fp32(knng, precision, kind, n, D, k, lm):
     # the certified re-rank makes the BF16/FP16 leaf stage return the FP32 graph
     X = _lp_data(kind, n, D, seed=n + D)
