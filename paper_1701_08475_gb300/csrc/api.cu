@@ -526,6 +526,7 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.jb.bf16 = a.p.precision == KNNG_BF16;
         b.jb.Xq = b.Xq;
         b.jb.qnrm = b.q_nrm;
+        b.jb.qerr = b.q_err;
         b.jb.notexact = b.notexact;
     }
     if (tree && lp_any) {  // the tree sweeps read the 16-bit copy when it is exact

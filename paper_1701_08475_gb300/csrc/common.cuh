@@ -198,6 +198,34 @@ __device__ __forceinline__ bool warp_merge_few(const uint64_t (&cand)[NC], uint6
     return true;
 }
 
+// canonical FP32 squared distance between rows xa and xb (dims ascending,
+// fmaf); vec: D % 4 == 0 and 16-byte aligned rows
+__device__ __forceinline__ float canon_dist(const float* __restrict__ xa, const float* __restrict__ xb, int D,
+                                            bool vec) {
+    float acc = 0.f;
+    if (vec) {
+        for (int d = 0; d < D; d += 4) {
+            const float4 u = __ldg(reinterpret_cast<const float4*>(xa + d));
+            const float4 v = __ldg(reinterpret_cast<const float4*>(xb + d));
+            float t = __fsub_rn(u.x, v.x);
+            acc = __fmaf_rn(t, t, acc);
+            t = __fsub_rn(u.y, v.y);
+            acc = __fmaf_rn(t, t, acc);
+            t = __fsub_rn(u.z, v.z);
+            acc = __fmaf_rn(t, t, acc);
+            t = __fsub_rn(u.w, v.w);
+            acc = __fmaf_rn(t, t, acc);
+        }
+    } else {
+        for (int d = 0; d < D; ++d) {
+            const float t = __fsub_rn(__ldg(xa + d), __ldg(xb + d));
+            acc = __fmaf_rn(t, t, acc);
+        }
+    }
+    return acc;
+}
+
+
 // Status word written by kernels that detect a bad input or an internal
 // limit; the host reads it once per call.
 enum DevStatus : int {

@@ -12,6 +12,7 @@
 //   scatter           group the offers by target (counts, prefix sum)
 //   K4 merge          G_new[u] = first k unique of G_old[u] + offers to u
 #include <algorithm>
+#include <cstdlib>
 #include <utility>
 
 #include "common.cuh"
@@ -767,6 +768,14 @@ const char* launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev,
 void finish_chunk(int64_t n, int k, uint64_t* Gnew, const JoinBuffers& b, double offers, int* status,
                   cudaStream_t s);
 
+// KNNG_JOIN_SCREEN=1: with a 16-bit copy that is not exact, the join screens
+// pairs on the tensor cores and computes canonical distances only for those
+// the screen cannot exclude (k5_join_tc_cert) instead of running the FP32 join.
+bool join_screen() {
+    const char* e = getenv("KNNG_JOIN_SCREEN");
+    return e && e[0] == '1';
+}
+
 // Chunks are sized from `est` (offers per node, measured on the previous
 // chunk), but never below nodes_per_chunk, which fits the offer buffer even
 // when every member pair offers both ways.  After each join the offer
@@ -821,6 +830,11 @@ const char* launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev,
         cudaMemsetAsync(b.counter, 0, sizeof(uint32_t), s);
         if (tc && launch_join_tc(b.Xq, D, b.qnrm, k, rev, Gold, b.R, c0, c1, b, status, b.notexact, b.bf16, s))
             return "k5_join_tc";
+        // not exact: the tensor cores screen the pairs and canonical distances
+        // decide (on request: it pays only when few pairs survive the screen)
+        if (!tc && b.lp && join_screen() &&
+            launch_join_tc(b.Xq, D, b.qnrm, k, rev, Gold, b.R, c0, c1, b, status, b.notexact, b.bf16, s, true, X))
+            return "k5_join_tc_cert";
         {
             const double m = rev ? 2.0 * k : (double)k;
             LaunchScope ls("k5_join", s, (double)(c1 - c0) * (m * D * 4.0 + 2 * k * 8.0 + m * 8.0),

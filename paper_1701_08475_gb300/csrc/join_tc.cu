@@ -33,18 +33,29 @@ constexpr int kThreads = 256;  // two threads per tile row in the epilogue
 
 __device__ __forceinline__ bool lp_exact_flag(int f) { return (f & 1) == 0 && !((f & 2) && (f & 4)); }
 
+// pairs a thread evaluates per group at most: ceil of mcap (mcap - 1) / 2
+// pairs over 2 mcap threads
+__host__ __device__ inline int jt_iters(int mcap) { return (mcap - 1) / 4 + 1; }
+
+// The operand tile, reused after the product for the Gram rows (and, when
+// certifying, each thread's exact distances); then member ids, thresholds,
+// norms, errors and rounded-up norm roots, counts, the barrier, the slot.
 struct JtSmem {
-    size_t tile, priv, mem, thr, nrm, cnt, bar, slot, total;
+    size_t tile, priv, dist, mem, thr, nrm, err, srt, cnt, bar, slot, total;
 };
-__host__ __device__ inline JtSmem jt_smem(int Dp, int mcap) {
+__host__ __device__ inline JtSmem jt_smem(int Dp, int mcap, bool cert) {
     JtSmem L;
     L.tile = 0;
     L.priv = 0;  // the operand tile is dead once the MMA has completed
     const size_t tile = (size_t)(Dp / kKc) * kChunkBytes, pv = (size_t)mcap * kRows * 4;
-    L.mem = tile > pv ? tile : pv;
+    const size_t ds = cert ? (size_t)kThreads * jt_iters(mcap) * 4 : 0;
+    L.dist = pv;
+    L.mem = tile > pv + ds ? tile : pv + ds;
     L.thr = L.mem + kRows * 4;
     L.nrm = L.thr + kRows * 8;
-    L.cnt = L.nrm + kRows * 4;
+    L.err = L.nrm + kRows * 4;
+    L.srt = L.err + (cert ? kRows * 4 : 0);
+    L.cnt = L.srt + (cert ? kRows * 4 : 0);
     L.bar = L.cnt + 32 * 4;  // member counts, then new-member counts
     L.slot = L.bar + 8;
     L.total = L.slot + 8;
@@ -96,6 +107,14 @@ __device__ __forceinline__ PairMap pair_map(int nn, int no) {
 
 // Persistent: CTA b takes node groups b, b + gridDim.x, ...; tensor memory
 // and the barrier are set up once.
+//
+// CERT (the 16-bit copy is not exact): d^ from the Gram only decides which
+// pairs need their canonical distance.  With the leaf certificate's bound,
+// rounded so that it stays a lower bound, d >= (sqrt(d^ - eps) - e_a - e_b)^2;
+// a direction whose target's k-th entry is below that cannot be offered.
+// Every other pair gets its canonical FP32 distance from X, and the offers
+// are decided on exact keys: the same offers as the FP32 join.
+template <bool CERT>
 __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __restrict__ Xq, int Dp,
                                                          const float* __restrict__ nrm, int k, int rev, int mcap,
                                                          int npc, const uint64_t* __restrict__ Gold,
@@ -106,16 +125,22 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                                                          int64_t node1, uint32_t* __restrict__ counter, int64_t cap,
                                                          uint32_t* __restrict__ ptgt, uint64_t* __restrict__ pkey,
                                                          int32_t* __restrict__ pcnt, int* __restrict__ status,
-                                                         const int* __restrict__ notexact, bool bf16) {
+                                                         const int* __restrict__ notexact, bool bf16,
+                                                         const float* __restrict__ X, int D,
+                                                         const float* __restrict__ qerr) {
     extern __shared__ uint8_t smem_raw[];
-    if ((*status & kStatusStop) || !lp_exact_flag(*notexact)) return;
-    const JtSmem L = jt_smem(Dp, mcap);
+    if ((*status & kStatusStop) || (!CERT && !lp_exact_flag(*notexact))) return;
+    const JtSmem L = jt_smem(Dp, mcap, CERT);
     uint8_t* base = smem_raw + ((1024 - (tc::smem_addr(smem_raw) & 1023)) & 1023);
     float* priv = reinterpret_cast<float*>(base + L.priv);    // [mcap][128]: thread r's Gram row
     int32_t* mem = reinterpret_cast<int32_t*>(base + L.mem);
     uint64_t* thr = reinterpret_cast<uint64_t*>(base + L.thr);
     float* snrm = reinterpret_cast<float*>(base + L.nrm);
+    float* serr = reinterpret_cast<float*>(base + L.err);  // CERT: quantisation errors
+    float* srt = reinterpret_cast<float*>(base + L.srt);   // CERT: norm roots, rounded up
+    float* dist = reinterpret_cast<float*>(base + L.dist) + threadIdx.x * jt_iters(mcap);  // CERT
     int* mcount = reinterpret_cast<int*>(base + L.cnt);
+    const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.slot);
     const uint32_t done = tc::smem_addr(base + L.bar);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -197,6 +222,10 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
             const int u = mem[r];
             thr[r] = u >= 0 ? Gold[(int64_t)u * k + k - 1] : 0ull;
             snrm[r] = u >= 0 ? nrm[u] : 0.f;
+            if (CERT) {
+                serr[r] = u >= 0 ? qerr[u] : 0.f;
+                srt[r] = u >= 0 ? __fsqrt_ru(nrm[u]) : 0.f;
+            }
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         // the tensor cores read shared memory through the async proxy
@@ -258,9 +287,27 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
             pm.decode(p, a, b);
             const uint32_t ua = (uint32_t)mem[base_row + a], ub = (uint32_t)mem[base_row + b];
             if (ua == ub) continue;
-            const float d = __fadd_rn(__fsub_rn(__fadd_rn(snrm[base_row + a], snrm[base_row + b]),
-                                                __fmul_rn(2.f, priv[b * kRows + base_row + a])), 0.f);
-            const bool oa = make_key(d, ub) < thr[base_row + a], ob = make_key(d, ua) < thr[base_row + b];
+            float d = __fadd_rn(__fsub_rn(__fadd_rn(snrm[base_row + a], snrm[base_row + b]),
+                                          __fmul_rn(2.f, priv[b * kRows + base_row + a])), 0.f);
+            const uint64_t ta = thr[base_row + a], tb = thr[base_row + b];
+            if (CERT) {
+                const float cD = (16.f * Dp + 8.f) * 5.9604644775390625e-8f;  // 2^-24
+                const float sn = __fadd_ru(srt[base_row + a], srt[base_row + b]);
+                const float eps = __fadd_ru(__fmul_ru(cD, __fmul_ru(sn, sn)), __fmul_ru(1.1920928955078125e-7f, fabsf(d)));
+                const float lo = __fsub_rd(d, eps);
+                float lb = 0.f;
+                if (lo > 0.f) {
+                    const float root = __fsub_rd(__fsub_rd(__fsqrt_rd(lo), serr[base_row + a]), serr[base_row + b]);
+                    if (root > 0.f) lb = __fmul_rd(root, root);
+                }
+                // an empty slot's key accepts everything
+                const bool na = ta == kEmptyKey || !(lb > key_dist(ta));
+                const bool nb = tb == kEmptyKey || !(lb > key_dist(tb));
+                if (!na && !nb) continue;
+                d = canon_dist(X + (int64_t)ua * D, X + (int64_t)ub * D, D, vec);
+                dist[i] = d;
+            }
+            const bool oa = make_key(d, ub) < ta, ob = make_key(d, ua) < tb;
             hit |= ((uint64_t)oa << (2 * i)) | ((uint64_t)ob << (2 * i + 1));
         }
         // one slot range per warp, then the offers themselves
@@ -286,8 +333,9 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
             int a, b;
             pm.decode(tix + (bit >> 1) * T, a, b);
             const uint32_t ua = (uint32_t)mem[base_row + a], ub = (uint32_t)mem[base_row + b];
-            const float d = __fadd_rn(__fsub_rn(__fadd_rn(snrm[base_row + a], snrm[base_row + b]),
-                                                __fmul_rn(2.f, priv[b * kRows + base_row + a])), 0.f);
+            const float d = CERT ? dist[bit >> 1]
+                                 : __fadd_rn(__fsub_rn(__fadd_rn(snrm[base_row + a], snrm[base_row + b]),
+                                                       __fmul_rn(2.f, priv[b * kRows + base_row + a])), 0.f);
             const uint32_t tgt = (bit & 1) ? ub : ua;
             ptgt[w] = tgt;
             pkey[w] = make_key(d, (bit & 1) ? ua : ub);
@@ -307,12 +355,13 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
 
 bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev, const uint64_t* Gold,
                     const uint64_t* R, int64_t node0, int64_t node1, const JoinBuffers& b, int* status,
-                    const int* notexact, bool bf16, cudaStream_t s) {
+                    const int* notexact, bool bf16, cudaStream_t s, bool cert, const float* X) {
     const int Dp = lp_dim(D);
     const int mcap = ((rev ? 2 * k : k) + 7) & ~7;
     if (Dp / kKc > 4 || mcap > kRows) return false;
+    if (cert && (!X || !b.qerr)) return false;
     const int npc = kRows / mcap;
-    const JtSmem L = jt_smem(Dp, mcap);
+    const JtSmem L = jt_smem(Dp, mcap, cert);
     // at least 56 KB per CTA: at most 4 CTAs (512 tensor-memory columns) per SM
     size_t smem = L.total + 1024;
     if (smem < 56 * 1024) smem = 56 * 1024;
@@ -321,12 +370,22 @@ bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev
     const int per_sm = (int)((227 * 1024) / smem) < 4 ? (int)((227 * 1024) / smem) : 4;
     const int grid = (int)(groups < (int64_t)152 * per_sm ? groups : (int64_t)152 * per_sm);
     const double m = rev ? 2.0 * k : (double)k;
-    LaunchScope ls("k5_join_tc", s, (double)nodes * (m * Dp * 2.0 + 2 * k * 8.0 + m * 12.0),
+    // certifying: the canonical distances' rows of X are counted per offer
+    // written (record_bytes), not here
+    LaunchScope ls(cert ? "k5_join_tc_cert" : "k5_join_tc", s,
+                   (double)nodes * (m * Dp * 2.0 + 2 * k * 8.0 + m * (cert ? 20.0 : 12.0)),
                    (double)groups * kRows * kRows * 2.0 * Dp);
-    cudaFuncSetAttribute(k5_join_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k5_join_tc<<<grid, kThreads, smem, s>>>(Xq, Dp, nrm, k, rev ? 1 : 0, mcap, npc, Gold, R, b.list, b.fnew, b.rnew,
-                                            node0, node1, b.counter,
-                                            b.cap, b.ptgt, b.pkey, b.pcnt, status, notexact, bf16);
+    if (cert) {
+        cudaFuncSetAttribute(k5_join_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k5_join_tc<true><<<grid, kThreads, smem, s>>>(Xq, Dp, nrm, k, rev ? 1 : 0, mcap, npc, Gold, R, b.list, b.fnew,
+                                                      b.rnew, node0, node1, b.counter, b.cap, b.ptgt, b.pkey, b.pcnt,
+                                                      status, notexact, bf16, X, D, b.qerr);
+    } else {
+        cudaFuncSetAttribute(k5_join_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k5_join_tc<false><<<grid, kThreads, smem, s>>>(Xq, Dp, nrm, k, rev ? 1 : 0, mcap, npc, Gold, R, b.list,
+                                                       b.fnew, b.rnew, node0, node1, b.counter, b.cap, b.ptgt, b.pkey,
+                                                       b.pcnt, status, notexact, bf16, nullptr, 0, nullptr);
+    }
     return true;
 }
 

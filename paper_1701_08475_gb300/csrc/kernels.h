@@ -140,15 +140,18 @@ struct JoinBuffers {
     bool lp = false, bf16 = true;
     const uint16_t* Xq = nullptr;
     const float* qnrm = nullptr;
+    const float* qerr = nullptr;
     const int* notexact = nullptr;
 };
 
 // The tensor-core local join of the nodes at positions [node0, node1) of
 // b.list (of all nodes when it is NULL); false (nothing launched) when the
 // shape is not supported.
+// cert: the 16-bit copy is not exact; the Gram only screens pairs and the
+// offers use canonical distances from X (b.qerr: quantisation errors).
 bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev, const uint64_t* Gold,
                     const uint64_t* R, int64_t node0, int64_t node1, const JoinBuffers& b, int* status,
-                    const int* notexact, bool bf16, cudaStream_t s);
+                    const int* notexact, bool bf16, cudaStream_t s, bool cert = false, const float* X = nullptr);
 
 // Adds `items` (algorithmic `bytes`) to the statistics of kernel `name`
 // (when statistics are on).

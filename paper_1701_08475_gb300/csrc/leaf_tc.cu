@@ -153,33 +153,6 @@ __host__ __device__ inline TcSmem tc_smem(int Dp, int MT) {
     return L;
 }
 
-// canonical FP32 squared distance between rows a and b of X
-__device__ __forceinline__ float canon_dist(const float* __restrict__ xa, const float* __restrict__ xb, int D,
-                                            bool vec) {
-    float acc = 0.f;
-    if (vec) {
-        for (int d = 0; d < D; d += 4) {
-            const float4 u = __ldg(reinterpret_cast<const float4*>(xa + d));
-            const float4 v = __ldg(reinterpret_cast<const float4*>(xb + d));
-            float t = __fsub_rn(u.x, v.x);
-            acc = __fmaf_rn(t, t, acc);
-            t = __fsub_rn(u.y, v.y);
-            acc = __fmaf_rn(t, t, acc);
-            t = __fsub_rn(u.z, v.z);
-            acc = __fmaf_rn(t, t, acc);
-            t = __fsub_rn(u.w, v.w);
-            acc = __fmaf_rn(t, t, acc);
-        }
-    } else {
-        for (int d = 0; d < D; ++d) {
-            const float t = __fsub_rn(__ldg(xa + d), __ldg(xb + d));
-            acc = __fmaf_rn(t, t, acc);
-        }
-    }
-    return acc;
-}
-
-
 // the key that lane `src` holds
 __device__ __forceinline__ uint64_t lane_key(uint64_t v, int src) { return shfl64(v, src); }
 

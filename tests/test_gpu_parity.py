@@ -237,11 +237,15 @@ def test_refine_rounds_skipping_old_pairs_match_oracle(knng, mode, k, start):
 
 
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
-@pytest.mark.parametrize("k,mode", [(20, oracle.FWD_REV), (12, oracle.FWD), (48, oracle.FWD)])
-def test_low_precision_rounds_match_oracle(knng, precision, k, mode):
-    # the tensor-core join over four rounds (member flags from the second on)
+@pytest.mark.parametrize("k,mode,kind", [(20, oracle.FWD_REV, "integer"), (12, oracle.FWD, "integer"),
+                                         (48, oracle.FWD, "integer"), (16, oracle.FWD_REV, "float"),
+                                         (24, oracle.FWD, "float")])
+def test_low_precision_rounds_match_oracle(knng, precision, k, mode, kind):
+    # the tensor-core join over four rounds (member flags from the second on):
+    # exact on integer data; screening plus canonical distances on float data
     n = 3500
-    X = datagen.sift_like(n, D=96, n_centres=40, seed=k)
+    X = (datagen.sift_like(n, D=96, n_centres=40, seed=k) if kind == "integer"
+         else datagen.gaussian_mixture(n, 96, 40, seed=k))
     prec = knng.KNNG_BF16 if precision == "bf16" else knng.KNNG_FP16
     common = dict(k=k, leaf_max=128, tree_passes=1, refine_rounds=4, seed=3, join_mode=mode)
     lp_ids, lp_d = knng.knng_build_ex(_dev(X), knng.default_params(precision=prec, **common))
@@ -379,3 +383,22 @@ def test_autotune_leaf_max_picks_a_measured_candidate(knng):
         best = max(r[2] for r in rows)
         pick = [r for r in rows if r[0] == leafs[0 if D == 32 else 1]][0]
         assert pick[2] >= best - 0.002
+
+
+@pytest.mark.parametrize("k,mode", [(16, oracle.FWD_REV), (24, oracle.FWD)])
+def test_screening_join_matches_oracle(knng, monkeypatch, k, mode):
+    # KNNG_JOIN_SCREEN=1: with a copy that is not exact the join screens pairs
+    # on the tensor cores and decides offers on canonical distances
+    monkeypatch.setenv("KNNG_JOIN_SCREEN", "1")
+    n = 3500
+    X = datagen.gaussian_mixture(n, 96, 40, seed=k + 1)
+    common = dict(k=k, leaf_max=128, tree_passes=1, refine_rounds=4, seed=5, join_mode=mode)
+    knng.stats_reset()
+    knng.stats_enable(True, False)
+    try:
+        ids, d = knng.knng_build_ex(_dev(X), knng.default_params(precision=knng.KNNG_BF16, **common))
+    finally:
+        knng.stats_enable(False)
+    assert knng.stats().get("k5_join_tc_cert", {}).get("launches", 0) > 0
+    o_ids, o_d = oracle.build_graph(X, k, 128, passes=1, rounds=4, seed=5, mode=mode)
+    _assert_graph_equal(ids, d, o_ids, o_d)
