@@ -263,17 +263,17 @@ def run_ours(args, cfg):
     import torch
     import paper_1701_08475_gb300 as knng
 
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    from paper_1701_08475_gb300 import replicas
+
+    rank, world, local = replicas.rank_env()
     torch.cuda.set_device(local)
+    replicas.init("nccl")
     dev = torch.device("cuda", local)
     knng.load()
 
     X = datagen.make(cfg["workload"])
     if world > 1:   # independent replica per rank: a different draw
-        X = X[np.random.default_rng(rank).permutation(X.shape[0])]
+        X = np.ascontiguousarray(X[replicas.replica_rows(X.shape[0], rank)])
     n, D = X.shape
     Xd = torch.from_numpy(X).to(dev)
     stream = torch.cuda.Stream(dev)
@@ -284,18 +284,10 @@ def run_ours(args, cfg):
                                    twomeans_iters=cfg["twomeans_iters"], seed=cfg["seed"],
                                    precision=PRECISIONS[prec])
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    barrier = replicas.barrier
 
     def max_over_ranks(v):
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([v], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            v = float(t.item())
-        return v
+        return replicas.max_over_ranks(v, dev)
 
     def timed(prec, sample_clocks):
         """steps whole builds on one stream, CUDA events, after warm-up."""
@@ -338,7 +330,7 @@ def run_ours(args, cfg):
 
     ms, st, clk, ids, dists, ms_k = timed(args.precision, True)
     launches = sum(v["launches_timed_run"] for v in st.values())
-    value = world * n * args.steps / (ms * 1e-3)
+    value = replicas.aggregate(n, args.steps, ms * 1e-3, world)
 
     # recall of the last graph on sampled rows, against exact lists
     smp = datagen.sample_rows(n, RECALL_SAMPLE, seed=3)
@@ -352,7 +344,8 @@ def run_ours(args, cfg):
     if args.precision != "fp32":
         ms32, st32, _, ids32, d32, _ = timed("fp32", False)
         r32 = knng.knng_recall(ids32, d32, gi, gd, smp_d)
-        fp32 = {"value": round(world * n * args.steps / (ms32 * 1e-3), 1), "ms_per_step": round(ms32 / args.steps, 3),
+        fp32 = {"value": round(replicas.aggregate(n, args.steps, ms32 * 1e-3, world), 1),
+                "ms_per_step": round(ms32 / args.steps, 3),
                 "recall_ids": round(r32[0], 5),
                 "graph_identical": bool(torch.equal(ids32, ids) and torch.equal(d32, dists))}
 
@@ -367,15 +360,13 @@ def run_ours(args, cfg):
     for _ in range(args.e2e_steps):
         knng.knng_build_ex(Xh, p, stream=stream, out=(oi, od))
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": round(world * n * args.e2e_steps / e2e_s, 1), "unit": "points/s",
+    e2e = {"value": round(replicas.aggregate(n, args.e2e_steps, e2e_s, world), 1), "unit": "points/s",
            "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(oi.numel() * 4 + od.numel() * 4),
            "steps": args.e2e_steps, "timer": "host wall clock around synchronous C-ABI calls"}
     same = bool(torch.equal(oi, ids.cpu()) and torch.equal(od, dists.cpu()))
 
     if rank != 0:
-        if world > 1:
-            import torch.distributed as dist
-            dist.destroy_process_group()
+        replicas.finish()
         return
     roof = roofline(st, clk, cfg["workload"], args.steps)
     roof["share_of_step"] = round(st[roof["kernel"]]["ms"] / ms_k, 4)
@@ -411,9 +402,7 @@ def run_ours(args, cfg):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    replicas.finish()
 
 
 def run_batched(args):
