@@ -130,6 +130,34 @@ typedef struct knng_instance {
 KNNG_API int knng_build_batched(int n_inst, const knng_instance *inst, const knng_params *p, void *stream);
 
 /*
+ * A build (as knng_build_ex: Sec. 3.1 / Alg. 1, then the refinement rounds of
+ * Sec. 1) recorded once into a CUDA graph and replayed at will.  The paper
+ * has no counterpart; recording removes the host's part of every launch.
+ * data, out_ids and out_dists must be device buffers; they are bound at
+ * creation, so a replay rebuilds the graph of whatever `data` then holds into
+ * the same outputs.  The plan owns its workspace (device memory for the whole
+ * build; the offer buffer is sized for one chunk per round up to 48 GB, since
+ * a graph cannot read offer counts back) until knng_plan_destroy.
+ * Recording makes no host reads of the data: every choice the host would make
+ * from it (the join kind, the chunk sizes) is made on the device instead, and
+ * the result equals knng_build_ex's bit for bit.
+ *   knng_plan_create: validates, allocates, records; *out_plan is NULL on error.
+ *   knng_plan_launch: enqueues one replay on `stream`.
+ *   knng_plan_check:  waits for `stream`, then reports the last replay's
+ *                     device status (KNNG_EINVAL for non-finite data, ...).
+ *   knng_plan_destroy: frees everything (NULL is ignored).
+ * Replays of one plan must not overlap in time (they share the workspace).
+ */
+typedef struct knng_plan knng_plan;
+KNNG_API int knng_plan_create(const float *data, int64_t n, int D, const knng_params *p, int32_t *out_ids,
+                              float *out_dists, void *stream, knng_plan **out_plan);
+KNNG_API int knng_plan_launch(knng_plan *plan, void *stream);
+/* Kernel launches one replay makes (the recorded graph's kernel nodes); -1 on error. */
+KNNG_API int64_t knng_plan_kernels(knng_plan *plan);
+KNNG_API int knng_plan_check(knng_plan *plan, void *stream);
+KNNG_API void knng_plan_destroy(knng_plan *plan);
+
+/*
  * Refinement only: p->refine_rounds local-join rounds (Jacobi: every offer of
  * a round comes from the graph as it stood before the round) applied to the
  * graph (ids_inout, dists_inout), which must satisfy the graph conventions and

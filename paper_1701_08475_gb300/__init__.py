@@ -18,6 +18,7 @@ from ._lib import (  # noqa: F401
     knng_build,
     knng_build_ex,
     knng_build_batched,
+    BuildPlan,
     knng_exact,
     knng_exact_noalloc,
     knng_leaf_update,

@@ -67,6 +67,11 @@ def load():
             "knng_build": (i32, [P, i64, i32, i32, i32, i32, u64, P, P]),
             "knng_build_ex": (i32, [P, i64, i32, PP, P, P, P]),
             "knng_build_batched": (i32, [i32, ctypes.POINTER(Instance), PP, P]),
+            "knng_plan_create": (i32, [P, i64, i32, PP, P, P, P, ctypes.POINTER(ctypes.c_void_p)]),
+            "knng_plan_launch": (i32, [P, P]),
+            "knng_plan_kernels": (i64, [P]),
+            "knng_plan_check": (i32, [P, P]),
+            "knng_plan_destroy": (None, [P]),
             "knng_refine": (i32, [P, i64, i32, PP, P, P, P]),
             "knng_partition": (i32, [P, i64, i32, i32, i32, u64, i32, P, P, P]),
             "knng_tree_depth": (i32, [i64, i32]),
@@ -213,6 +218,55 @@ def knng_build_batched(datas, params, leaf_maxes=None, stream=None):
     with _DeviceCtx(datas[0], stream) as s:
         _check(load().knng_build_batched(len(datas), arr, ctypes.byref(params), s))
     return outs
+
+
+class BuildPlan:
+    """A build recorded once into a CUDA graph (knng_plan_*): `launch()`
+    replays it on `data` into (ids, dists); `check()` waits and raises on a
+    device-reported error.  Device tensors only."""
+
+    def __init__(self, data, params, stream=None):
+        import torch
+        self.data = _contig(data, "float32")
+        n, D = self.data.shape
+        self.ids = torch.empty((n, params.k), dtype=torch.int32, device=self.data.device)
+        self.dists = torch.empty((n, params.k), dtype=torch.float32, device=self.data.device)
+        self._plan = ctypes.c_void_p()
+        self._stream = stream
+        with _DeviceCtx(self.data, stream) as s:
+            _check(load().knng_plan_create(_ptr(self.data), n, D, ctypes.byref(params), _ptr(self.ids),
+                                           _ptr(self.dists), s, ctypes.byref(self._plan)))
+
+    @property
+    def kernels(self):
+        """Kernel launches per replay."""
+        return int(load().knng_plan_kernels(self._plan))
+
+    def launch(self, stream=None):
+        with _DeviceCtx(self.data, stream if stream is not None else self._stream) as s:
+            _check(load().knng_plan_launch(self._plan, s))
+        return self.ids, self.dists
+
+    def check(self, stream=None):
+        with _DeviceCtx(self.data, stream if stream is not None else self._stream) as s:
+            _check(load().knng_plan_check(self._plan, s))
+
+    def close(self):
+        if self._plan:
+            load().knng_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def knng_refine(data, ids, dists, params, stream=None):

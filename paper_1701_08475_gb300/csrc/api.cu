@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -155,6 +156,12 @@ void record_bytes(const char* name, double bytes) {
     knng_kernel_stat& st = r.stats[name];
     if (st.name[0] == 0) snprintf(st.name, sizeof st.name, "%s", name);
     st.bytes += bytes;
+}
+
+void stats_set(bool on) {
+    StatRegistry& r = reg();
+    std::lock_guard<std::mutex> lk(r.mu);
+    r.on = on;
 }
 
 bool stats_on() {
@@ -432,6 +439,7 @@ struct Args {
     int64_t n;
     int D;
     knng_params p;
+    size_t offer_budget = 0;  // bytes for one chunk's offers; 0: offer_budget_bytes()
 };
 
 void validate_common(const void* data, int64_t n, int D, int k) {
@@ -492,6 +500,7 @@ struct BuildLayout {
 void quantize_for_join(const float* X, const Args& a, BuildLayout& b, cudaStream_t s) {
     if (!b.Xq) return;
     launch_quantize(X, a.n, a.D, nullptr, a.p.precision == KNNG_BF16, b.Xq, b.q_nrm, b.q_err, b.notexact, s);
+    if (b.jb.capture) return;  // a graph records no host reads
     // the kernels pick their path from the device flag; the host copy only
     // sizes the statistics' algorithmic bytes
     int f = 0;
@@ -556,7 +565,7 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         const bool rev = a.p.join_mode == KNNG_JOIN_FWD_REV;
         const int64_t m = rev ? 2 * k : k;
         const int64_t per_node = std::max<int64_t>(m * (m - 1), 1);
-        int64_t cap = (int64_t)(offer_budget_bytes() / 20);
+        int64_t cap = (int64_t)((a.offer_budget ? a.offer_budget : offer_budget_bytes()) / 20);
         cap = std::min<int64_t>(cap, per_node * n);
         cap = std::min<int64_t>(cap, ((int64_t)1 << 31) - 1);
         b.nodes_per_chunk = std::max<int64_t>(cap / per_node, 1);
@@ -643,7 +652,7 @@ void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& t
     const int k = a.p.k;
     launch_check_finite(X, n * (int64_t)a.D, b.status, s);
     launch_fill_empty(b.G, n * k, s);
-    if (a.p.tree_passes > 0)
+    if (a.p.tree_passes > 0 && !b.jb.capture)  // a captured build has its plan uploaded beforehand
         cuda_check(cudaMemcpyAsync(b.plan_dev, tp.host.data(), tp.host.size() * 4, cudaMemcpyHostToDevice, s),
                    "plan upload");
     const bool lp = lp_leaf(a, tp);
@@ -810,6 +819,118 @@ int knng_build_batched(int n_inst, const knng_instance* inst, const knng_params*
             offers_end(b);
         }
     });
+}
+
+}  // extern "C"
+
+// A build recorded into a CUDA graph: its workspace, plan image and graph.
+struct knng_plan {
+    Args a;
+    TreePlan tp;
+    Workspace ws;
+    BuildLayout b;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+int knng_plan_create(const float* data, int64_t n, int D, const knng_params* p, int32_t* out_ids, float* out_dists,
+                     void* stream, knng_plan** out_plan) {
+    return guarded([&] {
+        if (!out_plan) fail(KNNG_EINVAL, "out_plan is NULL");
+        *out_plan = nullptr;
+        if (!p) fail(KNNG_EINVAL, "params is NULL");
+        validate_common(data, n, D, p->k);
+        validate_params(p, n);
+        if (!out_ids || !out_dists) fail(KNNG_EINVAL, "output pointer is NULL");
+        if (!is_device_ptr(data) || !is_device_ptr(out_ids) || !is_device_ptr(out_dists))
+            fail(KNNG_EINVAL, "a recorded build needs device buffers (data and outputs)");
+        cudaStream_t s = (cudaStream_t)stream;
+        std::unique_ptr<knng_plan> pl(new knng_plan());
+        pl->a = Args{n, D, *p};
+        // one chunk per round when the worst case fits 48 GB: no host reads
+        // are possible in a graph, so the chunks are the worst case's size
+        const int64_t m = p->join_mode == KNNG_JOIN_FWD_REV ? 2 * p->k : p->k;
+        const double worst = (double)n * std::max<int64_t>(m * (m - 1), 1) * 20.0;
+        pl->a.offer_budget = (size_t)std::max<double>((double)offer_budget_bytes(), std::min(worst, 48e9));
+        if (p->tree_passes > 0) pl->tp.make(n, p->leaf_max);
+        for (int pass = 0; pass < 2; ++pass) {
+            pl->ws.used = 0;
+            carve(pl->ws, pl->b, pl->a, pl->tp, p->tree_passes > 0, p->refine_rounds > 0);
+            if (pass == 0) pl->ws.allocate(nullptr);  // freed on the default stream at destroy
+        }
+        cuda_check(cudaStreamSynchronize(nullptr), "workspace allocation");
+        if (p->tree_passes > 0) {
+            pl->tp.rebase(pl->b.plan_dev);
+            cuda_check(cudaMemcpy(pl->b.plan_dev, pl->tp.host.data(), pl->tp.host.size() * 4, cudaMemcpyHostToDevice),
+                       "plan upload");
+        }
+        pl->b.jb.capture = true;
+        pl->b.sb.capture = true;
+        // the recording stream: launch-time statistics stay off while recording
+        cudaStream_t cs;
+        cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream creation");
+        const bool stats_were = stats_on();
+        stats_set(false);
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            try {
+                cuda_check(cudaMemsetAsync(pl->b.status, 0, 4 * sizeof(int), cs), "status clear");
+                build_core(data, pl->a, pl->b, pl->tp, cs);
+                launch_unpack(pl->b.G, out_ids, out_dists, n * (int64_t)p->k, cs);
+            } catch (...) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(cs, &g);
+                if (g) cudaGraphDestroy(g);
+                cudaStreamDestroy(cs);
+                stats_set(stats_were);
+                throw;
+            }
+            e = cudaStreamEndCapture(cs, &pl->graph);
+        }
+        cudaStreamDestroy(cs);
+        stats_set(stats_were);
+        cuda_check(e, "stream capture");
+        cuda_check(cudaGraphInstantiate(&pl->exec, pl->graph, 0), "graph instantiation");
+        (void)s;
+        *out_plan = pl.release();
+    });
+}
+
+int64_t knng_plan_kernels(knng_plan* plan) {
+    if (!plan || !plan->graph) return -1;
+    size_t nn = 0;
+    if (cudaGraphGetNodes(plan->graph, nullptr, &nn) != cudaSuccess) return -1;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn && cudaGraphGetNodes(plan->graph, nodes.data(), &nn) != cudaSuccess) return -1;
+    int64_t kernels = 0;
+    for (cudaGraphNode_t v : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(v, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+    }
+    return kernels;
+}
+
+int knng_plan_launch(knng_plan* plan, void* stream) {
+    return guarded([&] {
+        if (!plan || !plan->exec) fail(KNNG_EINVAL, "no plan");
+        cuda_check(cudaGraphLaunch(plan->exec, (cudaStream_t)stream), "graph launch");
+    });
+}
+
+int knng_plan_check(knng_plan* plan, void* stream) {
+    return guarded([&] {
+        if (!plan) fail(KNNG_EINVAL, "no plan");
+        check_status(plan->b.status, (cudaStream_t)stream);
+    });
+}
+
+void knng_plan_destroy(knng_plan* plan) {
+    if (!plan) return;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    delete plan;
 }
 
 int knng_build(const float* data, int64_t n, int D, int k, int leaf_max, int rounds, uint64_t seed,

@@ -538,9 +538,11 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
                                                           int64_t cap, uint32_t* __restrict__ ptgt,
                                                           uint64_t* __restrict__ pkey,
                                                           int32_t* __restrict__ pcnt, int* __restrict__ status,
-                                                          const int* __restrict__ skip_if_exact) {
+                                                          const int* __restrict__ skip_if_exact,
+                                                          const int32_t* __restrict__ count_dev) {
     extern __shared__ float4 smem4[];
     if (*status & kStatusStop) return;
+    if (count_dev && (int64_t)*count_dev < node1) node1 = *count_dev;
     // the tensor-core join does this round when the 16-bit copy is exact
     if (skip_if_exact) {
         const int f = *skip_if_exact;
@@ -792,6 +794,14 @@ void join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_
     const double m_max = rev ? 2.0 * k : (double)k;
     // the 32-bit offer counter must not wrap, even in the worst case
     const int64_t wrap_nodes = (int64_t)(4294967295.0 / std::max(1.0, m_max * (m_max - 1)));
+    if (b.capture) {  // no host reads: worst-case chunks over every position
+        for (int64_t c0 = 0; c0 < count; c0 += nodes_per_chunk) {
+            const int64_t c1 = std::min(count, c0 + nodes_per_chunk);
+            launch_join_chunk(X, n, D, k, rev, Gold, b, tc, c0, c1, mcap, bpl, smem, status, s);
+            finish_chunk(n, k, Gnew, b, 0.0, status, s);
+        }
+        return;
+    }
     for (int64_t c0 = 0, c1 = 0; c0 < count; c0 = c1) {
         int64_t want = (int64_t)((double)b.cap / std::max(est, 1.0));
         want = std::max(nodes_per_chunk, std::min(want, wrap_nodes));
@@ -830,9 +840,14 @@ const char* launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev,
         cudaMemsetAsync(b.counter, 0, sizeof(uint32_t), s);
         if (tc && launch_join_tc(b.Xq, D, b.qnrm, k, rev, Gold, b.R, c0, c1, b, status, b.notexact, b.bf16, s))
             return "k5_join_tc";
+        // capture: the tensor-core join returns at once on the device unless
+        // the copy is exact, and the FP32 join below returns at once if it is
+        const bool tc_dev = b.capture && b.lp &&
+                            launch_join_tc(b.Xq, D, b.qnrm, k, rev, Gold, b.R, c0, c1, b, status, b.notexact,
+                                           b.bf16, s);
         // not exact: the tensor cores screen the pairs and canonical distances
         // decide (on request: it pays only when few pairs survive the screen)
-        if (!tc && b.lp && join_screen() &&
+        if (!tc && !b.capture && b.lp && join_screen() &&
             launch_join_tc(b.Xq, D, b.qnrm, k, rev, Gold, b.R, c0, c1, b, status, b.notexact, b.bf16, s, true, X))
             return "k5_join_tc_cert";
         {
@@ -845,7 +860,9 @@ const char* launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev,
         cudaFuncSetAttribute(k5_join<BPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
         k5_join<BPL><<<grid, 32 * kJoinWarps, smem, s>>>(X, D, k, rev ? 1 : 0, mcap, Gold, b.R, b.list,     \
                                                          b.fnew, b.rnew, c0, c1, b.counter, b.cap, b.ptgt,  \
-                                                         b.pkey, b.pcnt, status, nullptr);                  \
+                                                         b.pkey, b.pcnt, status,                            \
+                                                         tc_dev ? b.notexact : nullptr,                     \
+                                                         b.count_dev);                                      \
     } while (0)
             if (bpl <= 1) KNNG_JOIN(1);
             else if (bpl <= 2) KNNG_JOIN(2);
@@ -893,7 +910,7 @@ void run_refine(const float* X, int64_t n, int D, int k, bool rev, uint64_t*& G,
     double est = m_max * (m_max - 1) / 4;
     // the tensor-core join runs when the 16-bit copy is exact for this input
     bool tc = false;
-    if (b.lp) {
+    if (b.lp && !b.capture) {
         int f = 0;
         cudaMemcpyAsync(&f, b.notexact, sizeof f, cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
@@ -903,6 +920,7 @@ void run_refine(const float* X, int64_t n, int D, int k, bool rev, uint64_t*& G,
         if (rev) launch_reverse_lists(G, n, k, b, s);  // into b.R; b.R2 keeps the previous round's
         b.list = nullptr;
         b.fnew = b.rnew = nullptr;
+        b.count_dev = nullptr;
         int64_t count = n;
         if (r > 0) {
             // G2 still holds the previous round's G_old
@@ -917,14 +935,18 @@ void run_refine(const float* X, int64_t n, int D, int k, bool rev, uint64_t*& G,
                     k6_flags<1><<<grid, 32 * kFlagWarps, 0, s>>>(G, rev ? b.R : nullptr, G2, rev ? b.R2 : nullptr,
                                                                  n, k, b.fnew_buf, b.rnew_buf, b.active, b.nactive);
             }
-            int32_t h = 0;
-            cudaMemcpyAsync(&h, b.nactive, sizeof h, cudaMemcpyDeviceToHost, s);
-            cudaStreamSynchronize(s);
-            count = h;
+            if (b.capture) {
+                b.count_dev = b.nactive;  // the kernels read how many nodes are listed
+            } else {
+                int32_t h = 0;
+                cudaMemcpyAsync(&h, b.nactive, sizeof h, cudaMemcpyDeviceToHost, s);
+                cudaStreamSynchronize(s);
+                count = h;
+                record_items("k6_flags", (double)count);
+            }
             b.list = b.active;
             b.fnew = b.fnew_buf;
             b.rnew = rev ? b.rnew_buf : nullptr;
-            record_items("k6_flags", (double)count);
         }
         join_round(X, n, D, k, rev, G, G2, b, tc, count, nodes_per_chunk, est, status, s);
         std::swap(G, G2);

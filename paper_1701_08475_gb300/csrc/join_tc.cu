@@ -127,9 +127,11 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                                                          int32_t* __restrict__ pcnt, int* __restrict__ status,
                                                          const int* __restrict__ notexact, bool bf16,
                                                          const float* __restrict__ X, int D,
-                                                         const float* __restrict__ qerr) {
+                                                         const float* __restrict__ qerr,
+                                                         const int32_t* __restrict__ count_dev) {
     extern __shared__ uint8_t smem_raw[];
     if ((*status & kStatusStop) || (!CERT && !lp_exact_flag(*notexact))) return;
+    if (count_dev && (int64_t)*count_dev < node1) node1 = *count_dev;
     const JtSmem L = jt_smem(Dp, mcap, CERT);
     uint8_t* base = smem_raw + ((1024 - (tc::smem_addr(smem_raw) & 1023)) & 1023);
     float* priv = reinterpret_cast<float*>(base + L.priv);    // [mcap][128]: thread r's Gram row
@@ -379,12 +381,13 @@ bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev
         cudaFuncSetAttribute(k5_join_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k5_join_tc<true><<<grid, kThreads, smem, s>>>(Xq, Dp, nrm, k, rev ? 1 : 0, mcap, npc, Gold, R, b.list, b.fnew,
                                                       b.rnew, node0, node1, b.counter, b.cap, b.ptgt, b.pkey, b.pcnt,
-                                                      status, notexact, bf16, X, D, b.qerr);
+                                                      status, notexact, bf16, X, D, b.qerr, b.count_dev);
     } else {
         cudaFuncSetAttribute(k5_join_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k5_join_tc<false><<<grid, kThreads, smem, s>>>(Xq, Dp, nrm, k, rev ? 1 : 0, mcap, npc, Gold, R, b.list,
                                                        b.fnew, b.rnew, node0, node1, b.counter, b.cap, b.ptgt, b.pkey,
-                                                       b.pcnt, status, notexact, bf16, nullptr, 0, nullptr);
+                                                       b.pcnt, status, notexact, bf16, nullptr, 0, nullptr,
+                                                       b.count_dev);
     }
     return true;
 }

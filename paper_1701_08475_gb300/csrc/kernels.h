@@ -70,6 +70,7 @@ struct SplitBuffers {
     int Dq = 0, qtype = 0;  // qtype 1 = BF16, 2 = FP16
     const int* qflag = nullptr;
     bool q16_host = false;  // the host's copy of that decision (statistics only)
+    bool capture = false;   // recorded into a CUDA graph: the host knows nothing of the data
 };
 
 constexpr int kTile = 2048;         // positions per select/partition tile
@@ -135,6 +136,11 @@ struct JoinBuffers {
     const int32_t* list = nullptr;
     const uint64_t* fnew = nullptr;
     const uint64_t* rnew = nullptr;
+    // capture: no host reads (a CUDA graph records the build): chunks of the
+    // worst-case size over all positions, both joins launched with the choice
+    // made on the device, and `count_dev` (device) bounding the positions
+    bool capture = false;
+    const int32_t* count_dev = nullptr;
     // tensor-core join (16-bit copy in original order); used when lp is set
     // and, on the device, only when the copy's arithmetic is exact
     bool lp = false, bf16 = true;

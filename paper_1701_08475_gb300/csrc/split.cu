@@ -950,7 +950,9 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
         {
             LaunchScope ls("k1_sums", s, rows + n * 8, n * D);
             dim3 grid(lp.ntiles, dchunks);
-            if (vec && b.q16_host) {  // the staged sums pay off on the exact 16-bit copy
+            // the staged sums pay off on the exact 16-bit copy (when the host
+            // does not know, as in a captured build, they decide on the device)
+            if (vec && b.Xq && (b.q16_host || b.capture)) {
                 cudaFuncSetAttribute(k1_sums_async, cudaFuncAttributeMaxDynamicSharedMemorySize, kSuSmem);
                 k1_sums_async<<<lp.ntiles, kSuThreads, kSuSmem, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off,
                                                                      b.thr, lp.pos_bits, b.partial, b.status, b.Xq,

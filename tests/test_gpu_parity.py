@@ -402,3 +402,34 @@ def test_screening_join_matches_oracle(knng, monkeypatch, k, mode):
     assert knng.stats().get("k5_join_tc_cert", {}).get("launches", 0) > 0
     o_ids, o_d = oracle.build_graph(X, k, 128, passes=1, rounds=4, seed=5, mode=mode)
     _assert_graph_equal(ids, d, o_ids, o_d)
+
+
+# ---------------------------------------------------------------- recorded builds
+@pytest.mark.parametrize("precision,kind,mode", [("bf16", "integer", oracle.FWD_REV), ("fp32", "float", oracle.FWD_REV),
+                                                 ("bf16", "float", oracle.FWD), ("fp16", "integer", oracle.FWD)])
+def test_recorded_build_equals_direct_build(knng, precision, kind, mode):
+    # a build recorded into a CUDA graph makes every data-dependent choice on
+    # the device; replays equal direct builds, also after the data change kind
+    n, D, k = 6000, 64, 12
+    X = (datagen.sift_like(n, D=D, n_centres=60, seed=2) if kind == "integer"
+         else datagen.gaussian_mixture(n, D, 30, seed=2))
+    prec = {"fp32": knng.KNNG_FP32, "bf16": knng.KNNG_BF16, "fp16": knng.KNNG_FP16}[precision]
+    p = knng.default_params(k=k, leaf_max=64, tree_passes=2, refine_rounds=3, seed=3, precision=prec, join_mode=mode)
+    ids0, d0 = knng.knng_build_ex(_dev(X), p)
+    Xd = _dev(X)
+    with knng.BuildPlan(Xd, p) as plan:
+        for _ in range(2):
+            ids, d = plan.launch()
+            plan.check()
+            _assert_graph_equal(ids, d, _np(ids0), _np(d0))
+        X2 = (datagen.gaussian_mixture(n, D, 30, seed=7) if kind == "integer"
+              else datagen.sift_like(n, D=D, n_centres=60, seed=7))
+        Xd.copy_(torch.from_numpy(X2))
+        ids, d = plan.launch()
+        plan.check()
+        ids2, d2 = knng.knng_build_ex(_dev(X2), p)
+        _assert_graph_equal(ids, d, _np(ids2), _np(d2))
+        Xd[5, 3] = float("nan")
+        plan.launch()
+        with pytest.raises(knng.KnngError):
+            plan.check()
