@@ -198,6 +198,29 @@ __device__ __forceinline__ bool warp_merge_few(const uint64_t (&cand)[NC], uint6
     return true;
 }
 
+// warp_merge_few for more candidates than survive at once (a first pass
+// into an empty list): each lane sorts its NC candidates, the lanes' smallest
+// ones (one per lane) merge first, and the rest then face the new k-th entry.
+// Same contract and fallback as warp_merge_few.
+template <int NC>
+__device__ __forceinline__ bool warp_merge_many(uint64_t (&cand)[NC], uint64_t list, int k, uint64_t* scratch,
+                                                uint64_t& out, bool& changed) {
+    static_assert(NC >= 2, "one candidate per lane: use warp_merge_few");
+    const int lane = threadIdx.x & 31;
+    sort_regs<NC>(cand);
+    uint64_t first[1] = {cand[0]}, mid;
+    bool ch0;
+    if (!warp_merge_few<1>(first, list, k, scratch, mid, ch0)) return false;
+    mid = lane < k ? mid : kEmptyKey;
+    uint64_t rest[NC - 1];
+#pragma unroll
+    for (int s = 0; s < NC - 1; ++s) rest[s] = cand[s + 1];
+    bool ch1;
+    if (!warp_merge_few<NC - 1>(rest, mid, k, scratch, out, ch1)) return false;
+    changed = __any_sync(0xffffffffu, lane < k && out != list);
+    return true;
+}
+
 // canonical FP32 squared distance between rows xa and xb (dims ascending,
 // fmaf); vec: D % 4 == 0 and 16-byte aligned rows
 __device__ __forceinline__ float canon_dist(const float* __restrict__ xa, const float* __restrict__ xb, int D,

@@ -132,7 +132,15 @@ __global__ void __launch_bounds__(LeafCfg<MC>::NT) k2_leaf_fp32(const float* __r
                 bool changed;
 #pragma unroll
                 for (int s = 0; s < MC / 32; ++s) few[s] = cand[s];
-                if (warp_merge_few<MC / 32>(few, lane < k ? grow[lane] : kEmptyKey, k, wscratch, out, changed)) {
+                const uint64_t cur = lane < k ? grow[lane] : kEmptyKey;
+                if (warp_merge_few<MC / 32>(few, cur, k, wscratch, out, changed)) {
+                    if (changed && lane < k) grow[lane] = out;
+                    continue;
+                }
+                // many survive (the first pass): the lanes' smallest first
+#pragma unroll
+                for (int s = 0; s < MC / 32; ++s) few[s] = cand[s];
+                if (warp_merge_many<MC / 32>(few, cur, k, wscratch, out, changed)) {  // MC >= 64
                     if (changed && lane < k) grow[lane] = out;
                     continue;
                 }

@@ -353,6 +353,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
                     if (changed && lane < k) grow[lane] = out;
                     continue;
                 }
+                // many survive (the first pass): the lanes' smallest first
+#pragma unroll
+                for (int s = 0; s < NC; ++s) few[s] = cand[s];
+                if (warp_merge_many<NC>(few, old[0], k, wscratch, out, changed)) {
+                    if (changed && lane < k) grow[lane] = out;
+                    continue;
+                }
             }
 #pragma unroll
             for (int s = 0; s < NSG; ++s) cand[NC + s] = old[s];
