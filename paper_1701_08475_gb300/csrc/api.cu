@@ -558,6 +558,7 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.sb.ticket = ws.take<uint32_t>(nl);
         b.sb.nseg_large = nl;
         b.sb.partial = ws.take<double>((size_t)std::max(tp.nsweep_max, 1) * 2 * D);
+        b.sb.segsum = ws.take<double>((size_t)ns * D);
         b.sb.tile_left = ws.take<int32_t>(nt);
         b.sb.status = b.status;
     }

@@ -62,6 +62,7 @@ struct SplitBuffers {
     uint32_t* ticket;     // [nseg_large]: same
     int nseg_large;       // segments of the widest level that selects across CTAs
     double* partial;      // [nsweep_max][2][D]
+    double* segsum;       // [nseg_max][D] each segment's sum of rows (FP64)
     int32_t* tile_left;   // [ntiles_max]
     int* status;          // device status word
     // 16-bit copy of X (original order, rows of Dq); the sweeps read it

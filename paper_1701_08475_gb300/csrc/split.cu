@@ -537,7 +537,7 @@ template <bool VEC, int Q>
 __device__ __forceinline__ void sums_run(const float* __restrict__ X, int D, const uint16_t* __restrict__ Xq, int Dq,
                                          const int32_t* __restrict__ perm, const float* __restrict__ S, int a,
                                          uint64_t T, int pos_bits, int w0, int w1, int dbase, int* rows, float* hL,
-                                         float* lL, float* hR, float* lR) {
+                                         float* lL, float* hR, float* lR, bool left_only) {
     const int lane = threadIdx.x & 31;
     // ids and projections of the next 32 positions load while this chunk's
     // rows are summed
@@ -562,7 +562,7 @@ __device__ __forceinline__ void sums_run(const float* __restrict__ X, int D, con
         if (p < w1) rows[my_left ? before : nl + lane - before] = my_row;
         __syncwarp();
         sums_side<VEC, Q>(X, D, Xq, Dq, rows, nl, dbase, hL, lL);
-        sums_side<VEC, Q>(X, D, Xq, Dq, rows + nl, cnt - nl, dbase, hR, lR);
+        if (!left_only) sums_side<VEC, Q>(X, D, Xq, Dq, rows + nl, cnt - nl, dbase, hR, lR);
     }
 }
 
@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restri
                                                           double* __restrict__ partial,
                                                           const int* __restrict__ status,
                                                           const uint16_t* __restrict__ Xq, int Dq, int qtype,
-                                                          const int* __restrict__ qflag) {
+                                                          const int* __restrict__ qflag, int left_only) {
     __shared__ double red[kSumsWarps][2][128];
     __shared__ int rows[kSumsWarps][32];
     if (*status & kStatusStop) return;  // perm may hold unwritten slots
@@ -597,11 +597,14 @@ __global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restri
     float hL[4] = {0.f, 0.f, 0.f, 0.f}, lL[4] = {0.f, 0.f, 0.f, 0.f};
     float hR[4] = {0.f, 0.f, 0.f, 0.f}, lR[4] = {0.f, 0.f, 0.f, 0.f};
     if (q == 1)
-        sums_run<VEC, 1>(X, D, Xq, Dq, perm, S, a, T, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR, lR);
+        sums_run<VEC, 1>(X, D, Xq, Dq, perm, S, a, T, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR, lR,
+                         left_only != 0);
     else if (q == 2)
-        sums_run<VEC, 2>(X, D, Xq, Dq, perm, S, a, T, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR, lR);
+        sums_run<VEC, 2>(X, D, Xq, Dq, perm, S, a, T, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR, lR,
+                         left_only != 0);
     else
-        sums_run<VEC, 0>(X, D, Xq, Dq, perm, S, a, T, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR, lR);
+        sums_run<VEC, 0>(X, D, Xq, Dq, perm, S, a, T, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR, lR,
+                         left_only != 0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int dl = (VEC || q != 0) ? lane * 4 + j : lane + 32 * j;
@@ -622,16 +625,17 @@ __global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restri
 }
 
 // Centroid sums with rows staged like the projection's: a CTA takes one
-// select tile (up to kTile positions), stages 128-byte slabs of 256 rows by
-// cp.async (double-buffered), and each thread sums 4 dims of the slab over a
-// 1/G share of the rows, left and right apart.  Each chunk of 256 positions
-// is first ordered stably by side (left rows first), so that a warp's two row
-// groups are almost always on the same side.  Per thread the rows of a side
+// select tile (up to kTile positions) and first lists its rows by side (the
+// left rows in ascending positions, then the right ones).  The list is staged
+// in chunks of 256 rows, a 128-byte slab of each row at a time, by cp.async
+// (double-buffered), and each thread sums 4 dims of the slab over a 1/G share
+// of the chunk's rows, left and right apart.  Per thread the rows of a side
 // come in ascending positions; the G partial sums of a dim are combined in
-// FP64 in group order.
+// FP64 in group order.  With left_only the right rows are neither staged nor
+// summed: the right side's sum is then the segment's total minus the left's.
 constexpr int kSuThreads = 256;
-constexpr int kSuSmem = 2 * kPrRows * kPrStride + kTile * 4 + kTile * 2 + 8 * 4 + 2 * 1024 * 8;
-
+constexpr int kSuSmem = 2 * kPrRows * kPrStride + kTile * 4 + 8 * 4 + 2 * 1024 * 8;
+static_assert(kTile == 8 * kPrRows && kSuThreads == 256, "one warp lists each 256 positions of a tile");
 // Adds 4 dims (quad q) of one staged row to the sums (h, l).
 template <int Q>
 __device__ __forceinline__ void sums_add(const uint8_t* row, int q, float (&h)[4], float (&l)[4]) {
@@ -689,63 +693,73 @@ template <int Q>
 __device__ __forceinline__ void sums_async_tile(const float* __restrict__ X, int D, const uint16_t* __restrict__ Xq,
                                                 int Dq, const int32_t* __restrict__ perm,
                                                 const float* __restrict__ S, int a, uint64_t T, int pos_bits,
-                                                int begin, int end, double* __restrict__ part, uint8_t* smem) {
+                                                int begin, int end, bool left_only, double* __restrict__ part,
+                                                uint8_t* smem) {
     constexpr int SLAB = Q != 0 ? 64 : 32;  // dims per 128-byte slab
     constexpr int QUADS = SLAB / 4;         // threads per row
     constexpr int G = kSuThreads / QUADS;   // row groups
-    int* ids = reinterpret_cast<int*>(smem + 2 * kPrRows * kPrStride);  // [kTile] row ids by position
-    uint16_t* order = reinterpret_cast<uint16_t*>(ids + kTile);          // [kTile] positions by side
-    int* nleft = reinterpret_cast<int*>(order + kTile);                  // [8] left rows per chunk
+    int* ids = reinterpret_cast<int*>(smem + 2 * kPrRows * kPrStride);  // [kTile] row ids, left side first
+    int* nleft = ids + kTile;                                            // [8] left rows per 256 positions
     double* red = reinterpret_cast<double*>(nleft + 8);                  // [2][G][SLAB], G * SLAB = 1024
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m = end - begin, nchunk = (m + kPrRows - 1) / kPrRows;
-    for (int p = tid; p < m; p += kSuThreads) ids[p] = perm[begin + p];
-    // warp c orders chunk c: left rows first, each side by position
-    for (int c = warp; c < nchunk; c += kSuThreads / 32) {
-        unsigned bal[8];
-        int nl = 0;
+    const int m = end - begin;
+    // warp w lists positions 256 w .. 256 w + 255
+    unsigned bal[8];
+    int nlw = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int p = c * kPrRows + 32 * i + lane;
-            bal[i] = __ballot_sync(0xffffffffu, p < m && sel_key(S[begin + p], begin + p - a, pos_bits) < T);
-            nl += __popc(bal[i]);
-        }
-        int lb = 0;  // left rows before this group of 32
+    for (int i = 0; i < 8; ++i) {
+        const int p = warp * kPrRows + 32 * i + lane;
+        bal[i] = __ballot_sync(0xffffffffu, p < m && sel_key(S[begin + p], begin + p - a, pos_bits) < T);
+        nlw += __popc(bal[i]);
+    }
+    if (lane == 0) nleft[warp] = nlw;
+    __syncthreads();
+    int NL = 0, lb = 0;  // left rows of the tile; of the positions before this warp's
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int p = c * kPrRows + 32 * i + lane;
-            if (p < m) {
-                const int l_rank = lb + __popc(bal[i] & ((1u << lane) - 1u));
-                // rows before p: 32 i + lane, of which l_rank on the left
-                const int rank = (bal[i] >> lane) & 1u ? l_rank : nl + (32 * i + lane - l_rank);
-                order[c * kPrRows + rank] = (uint16_t)(32 * i + lane);
-            }
-            lb += __popc(bal[i]);
+    for (int w = 0; w < 8; ++w) {
+        const int v = nleft[w];
+        NL += v;
+        lb += w < warp ? v : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int p = warp * kPrRows + 32 * i + lane;
+        if (p < m) {
+            const int l_rank = lb + __popc(bal[i] & ((1u << lane) - 1u));  // left positions before p
+            const bool left = (bal[i] >> lane) & 1u;
+            if (left || !left_only) ids[left ? l_rank : NL + (p - l_rank)] = perm[begin + p];
         }
-        if (lane == 0) nleft[c] = nl;
+        lb += __popc(bal[i]);
     }
     __syncthreads();
+    const int mt = left_only ? NL : m;  // rows staged
+    const int nchunk = (mt + kPrRows - 1) / kPrRows;
+    if (nchunk == 0) {  // no left rows: zero sums
+        for (int d = tid; d < 2 * D; d += kSuThreads) part[d] = 0.0;
+        return;
+    }
     const int nslab = (D + SLAB - 1) / SLAB, nstage = nslab * nchunk;
     // stage st: dims (st / nchunk) * SLAB .., rows of chunk st % nchunk
     const int q = tid % QUADS, g = tid / QUADS;
     float hL[4] = {0.f, 0.f, 0.f, 0.f}, lL[4] = {0.f, 0.f, 0.f, 0.f};
     float hR[4] = {0.f, 0.f, 0.f, 0.f}, lR[4] = {0.f, 0.f, 0.f, 0.f};
-    if (nstage > 0) sums_issue<Q>(X, D, Xq, Dq, ids, m, nchunk, 0, smem);
+    sums_issue<Q>(X, D, Xq, Dq, ids, mt, nchunk, 0, smem);
     for (int st = 0; st < nstage; ++st) {
         if (st + 1 < nstage) {
-            sums_issue<Q>(X, D, Xq, Dq, ids, m, nchunk, st + 1, smem);
+            sums_issue<Q>(X, D, Xq, Dq, ids, mt, nchunk, st + 1, smem);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
         __syncthreads();
         const int sl = st / nchunk, c = st - sl * nchunk, d0 = sl * SLAB;
-        const int cnt = min(kPrRows, m - c * kPrRows), nl = nleft[c];
+        const int cnt = min(kPrRows, mt - c * kPrRows);
+        const int nl = min(max(NL - c * kPrRows, 0), cnt);  // the chunk's left rows come first
         const uint8_t* buf = smem + (st & 1) * (kPrRows * kPrStride);
         if (d0 + 4 * q < D) {
             int i = g;
-            for (; i < nl; i += G) sums_add<Q>(buf + order[c * kPrRows + i] * kPrStride, q, hL, lL);
-            for (; i < cnt; i += G) sums_add<Q>(buf + order[c * kPrRows + i] * kPrStride, q, hR, lR);
+            for (; i < nl; i += G) sums_add<Q>(buf + i * kPrStride, q, hL, lL);
+            for (; i < cnt; i += G) sums_add<Q>(buf + i * kPrStride, q, hR, lR);
         }
         if (c == nchunk - 1) {  // the slab's rows are all in: combine the groups
 #pragma unroll
@@ -777,7 +791,7 @@ __global__ void __launch_bounds__(kSuThreads) k1_sums_async(const float* __restr
                                                             double* __restrict__ partial,
                                                             const int* __restrict__ status,
                                                             const uint16_t* __restrict__ Xq, int Dq, int qtype,
-                                                            const int* __restrict__ qflag) {
+                                                            const int* __restrict__ qflag, int left_only) {
     extern __shared__ __align__(16) uint8_t su_smem[];
     if (*status & kStatusStop) return;  // perm may hold unwritten slots
     const int q = q16_usable(Xq, qflag) ? qtype : 0;
@@ -787,20 +801,26 @@ __global__ void __launch_bounds__(kSuThreads) k1_sums_async(const float* __restr
     const uint64_t T = thr[seg];
     double* part = partial + (int64_t)blockIdx.x * 2 * D;
     if (q == 1)
-        sums_async_tile<1>(X, D, Xq, Dq, perm, S, a, T, pos_bits, begin, end, part, su_smem);
+        sums_async_tile<1>(X, D, Xq, Dq, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
+                           su_smem);
     else if (q == 2)
-        sums_async_tile<2>(X, D, Xq, Dq, perm, S, a, T, pos_bits, begin, end, part, su_smem);
+        sums_async_tile<2>(X, D, Xq, Dq, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
+                           su_smem);
     else
-        sums_async_tile<0>(X, D, Xq, Dq, perm, S, a, T, pos_bits, begin, end, part, su_smem);
+        sums_async_tile<0>(X, D, Xq, Dq, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
+                           su_smem);
 }
 
 // New centroids of each segment from its tiles' partial sums (kCenGroups
 // interleaved groups of tiles, each summed in tile order, then added in group
-// order), FP64 mean rounded to FP32; stores w = c1 - c0.
+// order), FP64 mean rounded to FP32; stores w = c1 - c0.  A sweep of both
+// sides stores the segment's total (segsum); after a left-only sweep the
+// right sum is that total minus the left sum.
 constexpr int kCenGroups = 4;  // tile groups of k1_centroids (128 dims each)
 __global__ void __launch_bounds__(128 * kCenGroups) k1_centroids(const double* __restrict__ partial,
                                                                  const int32_t* __restrict__ seg_off,
                                                                  const int32_t* __restrict__ seg_tile0, int D,
+                                                                 double* __restrict__ segsum, int left_only,
                                                                  float* __restrict__ W) {
     __shared__ double red[kCenGroups][2][128];
     const int seg = blockIdx.x;
@@ -832,6 +852,10 @@ __global__ void __launch_bounds__(128 * kCenGroups) k1_centroids(const double* _
                 sL += red[q][0][dl];
                 sR += red[q][1][dl];
             }
+            if (left_only)
+                sR = segsum[(int64_t)seg * D + d] - sL;
+            else
+                segsum[(int64_t)seg * D + d] = sL + sR;
             const float c0 = (float)(sL / (double)K);
             const float c1 = (float)(sR / (double)(m - K));
             W[(int64_t)seg * D + d] = __fsub_rn(c1, c0);
@@ -947,8 +971,11 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
                 break;
             }
         }
+        // the first sweep sums both sides (and so each segment's total), the
+        // later ones the left side (floor(m / 2) rows) alone
+        const int left_only = it > 0;
         {
-            LaunchScope ls("k1_sums", s, rows + n * 8, n * D);
+            LaunchScope ls("k1_sums", s, (left_only ? rows * 0.5 : rows) + n * 8, n * D);
             dim3 grid(lp.ntiles, dchunks);
             // the staged sums pay off on the exact 16-bit copy (when the host
             // does not know, as in a captured build, they decide on the device)
@@ -956,19 +983,20 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
                 cudaFuncSetAttribute(k1_sums_async, cudaFuncAttributeMaxDynamicSharedMemorySize, kSuSmem);
                 k1_sums_async<<<lp.ntiles, kSuThreads, kSuSmem, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off,
                                                                      b.thr, lp.pos_bits, b.partial, b.status, b.Xq,
-                                                                     b.Dq, b.qtype, b.qflag);
+                                                                     b.Dq, b.qtype, b.qflag, left_only);
             } else if (vec)
                 k1_sums<true><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr,
                                                                lp.pos_bits, b.partial, b.status, b.Xq, b.Dq,
-                                                               b.qtype, b.qflag);
+                                                               b.qtype, b.qflag, left_only);
             else
                 k1_sums<false><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr,
                                                                 lp.pos_bits, b.partial, b.status, b.Xq, b.Dq,
-                                                                b.qtype, b.qflag);
+                                                                b.qtype, b.qflag, left_only);
         }
         {
             LaunchScope ls("k1_centroids", s, (double)lp.ntiles * 2 * D * 8 + (double)lp.nseg * D * 4, 0);
-            k1_centroids<<<lp.nseg, 128 * kCenGroups, 0, s>>>(b.partial, lp.seg_off, lp.seg_tile0, D, b.W);
+            k1_centroids<<<lp.nseg, 128 * kCenGroups, 0, s>>>(b.partial, lp.seg_off, lp.seg_tile0, D, b.segsum,
+                                                              left_only, b.W);
         }
     }
 }
