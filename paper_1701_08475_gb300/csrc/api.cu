@@ -493,7 +493,25 @@ struct BuildLayout {
     // tensor-core join
     uint16_t* Xq = nullptr;
     float *q_nrm = nullptr, *q_err = nullptr;
+    // byte copy for the tree sweeps
+    uint8_t* Xb = nullptr;
+    int* bflag = nullptr;
 };
+
+int byte_dim(int D) { return (D + 15) & ~15; }
+
+// Byte copy of X for the tree sweeps, used when every value is an integer in
+// [0, 255] (the kernels read the device flag; the host copy picks the sums
+// kernel and sizes the statistics' algorithmic bytes).
+void make_bytes(const float* X, const Args& a, BuildLayout& b, cudaStream_t s) {
+    if (!b.Xb) return;
+    launch_bytes(X, a.n, a.D, byte_dim(a.D), b.Xb, b.bflag, s);
+    if (b.jb.capture) return;  // a graph records no host reads
+    int f = 1;
+    cuda_check(cudaMemcpyAsync(&f, b.bflag, sizeof f, cudaMemcpyDeviceToHost, s), "flag read");
+    cuda_check(cudaStreamSynchronize(s), "stream synchronize");
+    b.sb.u8_host = f == 0;
+}
 
 // Original-order 16-bit copy for the tensor-core stages (also sets the
 // exactness flag); nothing in FP32.
@@ -545,6 +563,11 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.sb.qflag = b.notexact;
     }
     if (tree) {
+        b.Xb = ws.take<uint8_t>((size_t)n * byte_dim(D));
+        b.bflag = ws.take<int>(4);
+        b.sb.Xb = b.Xb;
+        b.sb.Db = byte_dim(D);
+        b.sb.bflag = b.bflag;
         b.perm_a = ws.take<int32_t>(n);
         b.perm_b = ws.take<int32_t>(n);
         b.plan_dev = ws.take<int32_t>(tp.host.size());
@@ -662,6 +685,7 @@ void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& t
     const int kp = std::min(63, k + std::max(k / 2, 8));
     if (b.notexact) cuda_check(cudaMemsetAsync(b.notexact, 0, sizeof(int), s), "flag clear");
     quantize_for_join(X, a, b, s);
+    make_bytes(X, a, b, s);
     for (int pass = 0; pass < a.p.tree_passes; ++pass) {
         int32_t* perm = run_partition(X, a, tp, b, pass, s);
         const int32_t* leaf_off = b.plan_dev + tp.leaf_off_at;
@@ -1035,6 +1059,7 @@ int knng_partition(const float* data, int64_t n, int D, int leaf_max, int twomea
         launch_check_finite(X.dev, n * (int64_t)D, b.status, s);
         cuda_check(cudaMemcpyAsync(b.plan_dev, tp.host.data(), tp.host.size() * 4, cudaMemcpyHostToDevice, s),
                    "plan upload");
+        make_bytes(X.dev, a, b, s);
         int32_t* perm = run_partition(X.dev, a, tp, b, pass, s);
         cuda_check(cudaMemcpyAsync(op.dev, perm, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s), "perm copy");
         download(op, s);

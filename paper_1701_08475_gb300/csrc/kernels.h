@@ -71,6 +71,13 @@ struct SplitBuffers {
     int Dq = 0, qtype = 0;  // qtype 1 = BF16, 2 = FP16
     const int* qflag = nullptr;
     bool q16_host = false;  // the host's copy of that decision (statistics only)
+    // byte copy of X (original order, rows of Db = D rounded up to 16 bytes);
+    // the staged sweeps read it first when *bflag == 0 (every value an
+    // integer in [0, 255])
+    const uint8_t* Xb = nullptr;
+    int Db = 0;
+    const int* bflag = nullptr;
+    bool u8_host = false;   // the host's copy of that decision
     bool capture = false;   // recorded into a CUDA graph: the host knows nothing of the data
 };
 
@@ -96,6 +103,9 @@ int lp_dim(int D);  // D rounded up to the 64-element rows of the swizzled tiles
 // Leaf-order 16-bit copy of X (perm: leaf order; NULL = identity), squared
 // norms and quantisation errors; *notexact |= 1 when the 16-bit arithmetic is
 // not exact for this input.
+// Byte copy of X (rows of Db bytes) and its flag: 0 when every value is an
+// integer in [0, 255].
+void launch_bytes(const float* X, int64_t n, int D, int Db, uint8_t* Xb, int* bflag, cudaStream_t s);
 void launch_quantize(const float* X, int64_t n, int D, const int32_t* perm, bool bf16, uint16_t* Xq, float* nrm,
                      float* qerr, int* notexact, cudaStream_t s);
 // Leaf-order gather of a 16-bit copy (with its norms and errors).

@@ -138,6 +138,41 @@ __device__ __forceinline__ float q16_to_float(uint32_t h) {
     return __half2float(__ushort_as_half((unsigned short)h));
 }
 
+// Byte copy: when every value of X is an integer in [0, 255] (flag from
+// k0_bytes), the staged sweeps read one byte per value instead of four (or
+// two).  Byte i of `word` as a float, exactly: the byte becomes the low
+// mantissa bits of 2^23, which the subtraction then removes.
+__device__ __forceinline__ bool u8_usable(const uint8_t* Xb, const int* bflag) {
+    return Xb != nullptr && *bflag == 0;
+}
+__device__ __forceinline__ float u8_to_float(uint32_t word, int i) {
+    return __fsub_rn(__uint_as_float(__byte_perm(word, 0x4B000000u, 0x7540u + (uint32_t)i)), 8388608.f);
+}
+
+// Writes the byte copy (rows of Db bytes, zero padded) and sets *bflag when
+// some value is not an integer in [0, 255]; once it is set, the remaining
+// CTAs return at once.  One warp per row, 4 values per lane and step.
+__global__ void __launch_bounds__(256) k0_bytes(const float* __restrict__ X, int64_t n, int D, int Db,
+                                                uint8_t* __restrict__ Xb, int* __restrict__ bflag) {
+    if (*(volatile int*)bflag) return;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= n) return;
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    for (int d0 = lane * 4; d0 < Db; d0 += 128) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int d = d0 + j;
+            const float x = d < D ? X[r * D + d] : 0.f;
+            ok &= x == rintf(x) && x >= 0.f && x <= 255.f;
+            word |= (uint32_t)(ok ? (int)x : 0) << (8 * j);
+        }
+        *reinterpret_cast<uint32_t*>(Xb + r * Db + d0) = word;
+    }
+    if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(bflag, 1);
+}
+
 // One sweep tile of the projection.  Q = 0 reads the FP32 rows of X (VEC2:
 // as float2), Q = 1 / 2 the BF16 / FP16 copy; every load of a 64-dim slab is
 // issued before any value is used.
@@ -226,7 +261,7 @@ __global__ void __launch_bounds__(256) k1_project(const float* __restrict__ X, i
 // banks once.  Needs 16-byte aligned rows of X (D a multiple of 4).
 constexpr int kPrRows = 256;
 constexpr int kPrStride = 144;
-constexpr int kPrSmem = 2 * kPrRows * kPrStride + 2 * 64 * 4 + kSweepTile * 4;
+constexpr int kPrSmem = 2 * kPrRows * kPrStride + 2 * 128 * 4 + kSweepTile * 4;
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -234,15 +269,16 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
                  : "memory");
 }
 
-template <int Q>
+template <int Q>  // 0 = FP32 rows of X, 1 / 2 = BF16 / FP16 copy, 3 = byte copy
 __device__ __forceinline__ void project_async_tile(const float* __restrict__ X, int D,
                                                    const uint16_t* __restrict__ Xq, int Dq,
+                                                   const uint8_t* __restrict__ Xb, int Db,
                                                    const int32_t* __restrict__ perm, int begin, int end,
                                                    const float* __restrict__ w, float* __restrict__ S,
                                                    uint8_t* smem) {
-    constexpr int SLAB = Q != 0 ? 64 : 32;  // dims per 128-byte slab
-    float* wsb = reinterpret_cast<float*>(smem + 2 * kPrRows * kPrStride);  // [2][64]
-    int* ids = reinterpret_cast<int*>(wsb + 2 * 64);                        // [kSweepTile]
+    constexpr int SLAB = Q == 3 ? 128 : Q != 0 ? 64 : 32;  // dims per 128-byte slab
+    float* wsb = reinterpret_cast<float*>(smem + 2 * kPrRows * kPrStride);  // [2][128]
+    int* ids = reinterpret_cast<int*>(wsb + 2 * 128);                       // [kSweepTile]
     const int tid = threadIdx.x;
     // the tile's row ids once, so that no copy waits on a global load
     for (int p = tid; p < end - begin; p += kPrRows) ids[p] = perm[begin + p];
@@ -258,13 +294,16 @@ __device__ __forceinline__ void project_async_tile(const float* __restrict__ X, 
             const int r = e >> 3, part = e & 7;
             if (r >= cnt) break;
             const int row = ids[base - begin + r];
-            if (Q != 0) {
+            if (Q == 3) {
+                if (d0 + part * 16 < Db)
+                    cp_async16(buf + r * kPrStride + part * 16, Xb + (int64_t)row * Db + d0 + part * 16);
+            } else if (Q != 0) {
                 cp_async16(buf + r * kPrStride + part * 16, Xq + (int64_t)row * Dq + d0 + part * 8);
             } else if (d0 + part * 4 < D) {
                 cp_async16(buf + r * kPrStride + part * 16, X + (int64_t)row * D + d0 + part * 4);
             }
         }
-        if (tid < SLAB) wsb[(st & 1) * 64 + tid] = d0 + tid < D ? w[d0 + tid] : 0.f;
+        if (tid < SLAB) wsb[(st & 1) * 128 + tid] = d0 + tid < D ? w[d0 + tid] : 0.f;
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
     if (nstage > 0) issue(0);
@@ -281,9 +320,19 @@ __device__ __forceinline__ void project_async_tile(const float* __restrict__ X, 
         const int base = begin + c * kPrRows, cnt = min(kPrRows, end - base);
         if (tid < cnt) {
             const uint8_t* rowp = smem + (st & 1) * (kPrRows * kPrStride) + tid * kPrStride;
-            const float* ws = wsb + (st & 1) * 64;
+            const float* ws = wsb + (st & 1) * 128;
             const int dl = min(SLAB, D - d0);
-            if (Q != 0) {
+            if (Q == 3) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (q * 16 >= dl) break;
+                    const uint4 h = *reinterpret_cast<const uint4*>(rowp + q * 16);
+                    const uint32_t hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                    for (int t = 0; t < 16; ++t)
+                        if (q * 16 + t < dl) acc = __fmaf_rn(u8_to_float(hv[t >> 2], t & 3), ws[q * 16 + t], acc);
+                }
+            } else if (Q != 0) {
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     if (q * 8 >= dl) break;
@@ -325,10 +374,12 @@ __global__ void __launch_bounds__(kPrRows) k1_project_async(const float* __restr
                                                             SelState* __restrict__ st,
                                                             const int* __restrict__ status,
                                                             const uint16_t* __restrict__ Xq, int Dq, int qtype,
-                                                            const int* __restrict__ qflag) {
+                                                            const int* __restrict__ qflag,
+                                                            const uint8_t* __restrict__ Xb, int Db,
+                                                            const int* __restrict__ bflag) {
     extern __shared__ __align__(16) uint8_t pr_smem[];
     if (*status & kStatusStop) return;  // perm may hold unwritten slots
-    const int q = q16_usable(Xq, qflag) ? qtype : 0;
+    const int q = u8_usable(Xb, bflag) ? 3 : q16_usable(Xq, qflag) ? qtype : 0;
     const int4 t = tiles[blockIdx.x];
     const int seg = t.x, begin = t.y, end = t.z;
     if (st != nullptr && t.w && threadIdx.x == 0) {
@@ -338,12 +389,14 @@ __global__ void __launch_bounds__(kPrRows) k1_project_async(const float* __restr
         st[seg].done = 0;  // set once the selection is done
     }
     const float* w = W + (int64_t)seg * D;
-    if (q == 1)
-        project_async_tile<1>(X, D, Xq, Dq, perm, begin, end, w, S, pr_smem);
+    if (q == 3)
+        project_async_tile<3>(X, D, Xq, Dq, Xb, Db, perm, begin, end, w, S, pr_smem);
+    else if (q == 1)
+        project_async_tile<1>(X, D, Xq, Dq, Xb, Db, perm, begin, end, w, S, pr_smem);
     else if (q == 2)
-        project_async_tile<2>(X, D, Xq, Dq, perm, begin, end, w, S, pr_smem);
+        project_async_tile<2>(X, D, Xq, Dq, Xb, Db, perm, begin, end, w, S, pr_smem);
     else
-        project_async_tile<0>(X, D, Xq, Dq, perm, begin, end, w, S, pr_smem);
+        project_async_tile<0>(X, D, Xq, Dq, Xb, Db, perm, begin, end, w, S, pr_smem);
 }
 
 // Small segments: one CTA per segment keeps all keys in shared memory,
@@ -640,7 +693,13 @@ static_assert(kTile == 8 * kPrRows && kSuThreads == 256, "one warp lists each 25
 template <int Q>
 __device__ __forceinline__ void sums_add(const uint8_t* row, int q, float (&h)[4], float (&l)[4]) {
     float v[4];
-    if (Q != 0) {
+    if (Q == 3) {
+        const uint32_t b = *reinterpret_cast<const uint32_t*>(row + q * 4);
+        // values up to 255, at most kTile / 8 of them per thread, dim and
+        // tile: FP32 sums are exact
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[j] = __fadd_rn(h[j], u8_to_float(b, j));
+    } else if (Q != 0) {
         const uint2 b = *reinterpret_cast<const uint2*>(row + q * 8);
         v[0] = q16_to_float<Q>(b.x & 0xFFFFu);
         v[1] = q16_to_float<Q>(b.x >> 16);
@@ -671,8 +730,9 @@ __device__ __forceinline__ void sums_add(const uint8_t* row, int q, float (&h)[4
 // of the rows of chunk st % nchunk, into buffer st & 1.
 template <int Q>
 __device__ __forceinline__ void sums_issue(const float* __restrict__ X, int D, const uint16_t* __restrict__ Xq,
-                                           int Dq, const int* ids, int m, int nchunk, int st, uint8_t* smem) {
-    constexpr int SLAB = Q != 0 ? 64 : 32;
+                                           int Dq, const uint8_t* __restrict__ Xb, int Db, const int* ids, int m,
+                                           int nchunk, int st, uint8_t* smem) {
+    constexpr int SLAB = Q == 3 ? 128 : Q != 0 ? 64 : 32;
     const int sl = st / nchunk, c = st - sl * nchunk, d0 = sl * SLAB;
     const int cnt = min(kPrRows, m - c * kPrRows);
     uint8_t* buf = smem + (st & 1) * (kPrRows * kPrStride);
@@ -680,7 +740,10 @@ __device__ __forceinline__ void sums_issue(const float* __restrict__ X, int D, c
         const int r = e >> 3, piece = e & 7;
         if (r >= cnt) break;
         const int row = ids[c * kPrRows + r];
-        if (Q != 0) {
+        if (Q == 3) {
+            if (d0 + piece * 16 < Db)
+                cp_async16(buf + r * kPrStride + piece * 16, Xb + (int64_t)row * Db + d0 + piece * 16);
+        } else if (Q != 0) {
             cp_async16(buf + r * kPrStride + piece * 16, Xq + (int64_t)row * Dq + d0 + piece * 8);
         } else if (d0 + piece * 4 < D) {
             cp_async16(buf + r * kPrStride + piece * 16, X + (int64_t)row * D + d0 + piece * 4);
@@ -691,16 +754,18 @@ __device__ __forceinline__ void sums_issue(const float* __restrict__ X, int D, c
 
 template <int Q>
 __device__ __forceinline__ void sums_async_tile(const float* __restrict__ X, int D, const uint16_t* __restrict__ Xq,
-                                                int Dq, const int32_t* __restrict__ perm,
+                                                int Dq, const uint8_t* __restrict__ Xb, int Db,
+                                                const int32_t* __restrict__ perm,
                                                 const float* __restrict__ S, int a, uint64_t T, int pos_bits,
                                                 int begin, int end, bool left_only, double* __restrict__ part,
                                                 uint8_t* smem) {
-    constexpr int SLAB = Q != 0 ? 64 : 32;  // dims per 128-byte slab
-    constexpr int QUADS = SLAB / 4;         // threads per row
-    constexpr int G = kSuThreads / QUADS;   // row groups
+    constexpr int SLAB = Q == 3 ? 128 : Q != 0 ? 64 : 32;  // dims per 128-byte slab
+    constexpr int QUADS = SLAB / 4;                        // threads per row
+    constexpr int G = kSuThreads / QUADS;                  // row groups
     int* ids = reinterpret_cast<int*>(smem + 2 * kPrRows * kPrStride);  // [kTile] row ids, left side first
     int* nleft = ids + kTile;                                            // [8] left rows per 256 positions
     double* red = reinterpret_cast<double*>(nleft + 8);                  // [2][G][SLAB], G * SLAB = 1024
+    static_assert(G * SLAB == 1024, "the combine buffer holds 2 x 1024 sums");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m = end - begin;
     // warp w lists positions 256 w .. 256 w + 255
@@ -743,10 +808,10 @@ __device__ __forceinline__ void sums_async_tile(const float* __restrict__ X, int
     const int q = tid % QUADS, g = tid / QUADS;
     float hL[4] = {0.f, 0.f, 0.f, 0.f}, lL[4] = {0.f, 0.f, 0.f, 0.f};
     float hR[4] = {0.f, 0.f, 0.f, 0.f}, lR[4] = {0.f, 0.f, 0.f, 0.f};
-    sums_issue<Q>(X, D, Xq, Dq, ids, mt, nchunk, 0, smem);
+    sums_issue<Q>(X, D, Xq, Dq, Xb, Db, ids, mt, nchunk, 0, smem);
     for (int st = 0; st < nstage; ++st) {
         if (st + 1 < nstage) {
-            sums_issue<Q>(X, D, Xq, Dq, ids, mt, nchunk, st + 1, smem);
+            sums_issue<Q>(X, D, Xq, Dq, Xb, Db, ids, mt, nchunk, st + 1, smem);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -791,23 +856,28 @@ __global__ void __launch_bounds__(kSuThreads) k1_sums_async(const float* __restr
                                                             double* __restrict__ partial,
                                                             const int* __restrict__ status,
                                                             const uint16_t* __restrict__ Xq, int Dq, int qtype,
-                                                            const int* __restrict__ qflag, int left_only) {
+                                                            const int* __restrict__ qflag,
+                                                            const uint8_t* __restrict__ Xb, int Db,
+                                                            const int* __restrict__ bflag, int left_only) {
     extern __shared__ __align__(16) uint8_t su_smem[];
     if (*status & kStatusStop) return;  // perm may hold unwritten slots
-    const int q = q16_usable(Xq, qflag) ? qtype : 0;
+    const int q = u8_usable(Xb, bflag) ? 3 : q16_usable(Xq, qflag) ? qtype : 0;
     const int4 t = tiles[blockIdx.x];
     const int seg = t.x, begin = t.y, end = t.z;
     const int a = seg_off[seg];
     const uint64_t T = thr[seg];
     double* part = partial + (int64_t)blockIdx.x * 2 * D;
-    if (q == 1)
-        sums_async_tile<1>(X, D, Xq, Dq, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
+    if (q == 3)
+        sums_async_tile<3>(X, D, Xq, Dq, Xb, Db, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
+                           su_smem);
+    else if (q == 1)
+        sums_async_tile<1>(X, D, Xq, Dq, Xb, Db, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
                            su_smem);
     else if (q == 2)
-        sums_async_tile<2>(X, D, Xq, Dq, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
+        sums_async_tile<2>(X, D, Xq, Dq, Xb, Db, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
                            su_smem);
     else
-        sums_async_tile<0>(X, D, Xq, Dq, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
+        sums_async_tile<0>(X, D, Xq, Dq, Xb, Db, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
                            su_smem);
 }
 
@@ -915,8 +985,10 @@ __global__ void __launch_bounds__(256) k1_part_scatter(const float* __restrict__
 void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint64_t pass_seed,
                      const int32_t* perm_in, int32_t* perm_out, const SplitBuffers& b, cudaStream_t s) {
     // algorithmic bytes: a sweep reads every row once plus its id and key
-    const double n = lp.n, rows = n * (b.q16_host ? b.Dq * 2.0 : D * 4.0);
-    const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    const double n = lp.n, rows = n * (b.u8_host ? b.Db * 1.0 : b.q16_host ? b.Dq * 2.0 : D * 4.0);
+    // the staged kernels read 16-byte pieces of rows: of X (vec) or of the
+    // byte copy, whose rows are padded (when the host knows it is usable)
+    const bool vec = ((D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0)) || b.u8_host;
     const bool vec2 = (D % 2 == 0) && ((reinterpret_cast<uintptr_t>(X) & 7) == 0);
     const int dchunks = (D + 127) / 128;
     // finished trees' leaves keep their place: the cut below writes only the
@@ -935,7 +1007,8 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
             if (vec) {
                 cudaFuncSetAttribute(k1_project_async, cudaFuncAttributeMaxDynamicSharedMemorySize, kPrSmem);
                 k1_project_async<<<lp.nsweep, kPrRows, kPrSmem, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S,
-                                                                     st, b.status, b.Xq, b.Dq, b.qtype, b.qflag);
+                                                                     st, b.status, b.Xq, b.Dq, b.qtype, b.qflag,
+                                                                     b.Xb, b.Db, b.bflag);
             } else if (vec2)
                 k1_project<true><<<lp.nsweep, 256, 0, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S, st,
                                                            b.status, b.Xq, b.Dq, b.qtype, b.qflag);
@@ -977,13 +1050,14 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
         {
             LaunchScope ls("k1_sums", s, (left_only ? rows * 0.5 : rows) + n * 8, n * D);
             dim3 grid(lp.ntiles, dchunks);
-            // the staged sums pay off on the exact 16-bit copy (when the host
+            // the staged sums pay off on an exact narrow copy (when the host
             // does not know, as in a captured build, they decide on the device)
-            if (vec && b.Xq && (b.q16_host || b.capture)) {
+            if (vec && (b.Xq || b.Xb) && (b.u8_host || b.q16_host || b.capture)) {
                 cudaFuncSetAttribute(k1_sums_async, cudaFuncAttributeMaxDynamicSharedMemorySize, kSuSmem);
                 k1_sums_async<<<lp.ntiles, kSuThreads, kSuSmem, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off,
                                                                      b.thr, lp.pos_bits, b.partial, b.status, b.Xq,
-                                                                     b.Dq, b.qtype, b.qflag, left_only);
+                                                                     b.Dq, b.qtype, b.qflag, b.Xb, b.Db, b.bflag,
+                                                                     left_only);
             } else if (vec)
                 k1_sums<true><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr,
                                                                lp.pos_bits, b.partial, b.status, b.Xq, b.Dq,
@@ -999,6 +1073,12 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
                                                               left_only, b.W);
         }
     }
+}
+
+void launch_bytes(const float* X, int64_t n, int D, int Db, uint8_t* Xb, int* bflag, cudaStream_t s) {
+    LaunchScope ls("k0_bytes", s, (double)n * (D * 4.0 + Db), 0);
+    cudaMemsetAsync(bflag, 0, sizeof(int), s);
+    k0_bytes<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(X, n, D, Db, Xb, bflag);
 }
 
 }  // namespace knng

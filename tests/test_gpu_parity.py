@@ -129,10 +129,18 @@ def test_low_precision_build_equals_fp32(knng, precision, kind, n, D, k, lm):
 
 
 # ---------------------------------------------------------------- partition
-@pytest.mark.parametrize("n,D,lm,iters", [(20000, 12, 64, 3), (5000, 7, 40, 4), (64, 5, 64, 4), (9000, 1, 100, 2)])
-def test_partition_matches_oracle_on_integer_data(knng, n, D, lm, iters):
-    # n = 20000 takes the multi-CTA selection at the top levels
+@pytest.mark.parametrize("n,D,lm,iters,top", [(20000, 12, 64, 3, 255), (5000, 7, 40, 4, 255), (64, 5, 64, 4, 255),
+                                               (9000, 1, 100, 2, 255), (20000, 200, 64, 3, 255),
+                                               (6000, 33, 50, 4, 255), (20000, 40, 64, 3, 256),
+                                               (6000, 33, 50, 4, 256)])
+def test_partition_matches_oracle_on_integer_data(knng, n, D, lm, iters, top):
+    # n = 20000 takes the multi-CTA selection at the top levels.  Values in
+    # [0, 255] take the byte copy (D = 200: two slabs, the second ragged; D
+    # not a multiple of 4: padded rows); one value of 256 sends the same data
+    # to the FP32 rows
     X = datagen.sift_like(n, D=D, n_centres=50, seed=n)
+    if top == 256:
+        X[n // 2, D // 2] = 256.0
     perm, off = knng.knng_partition(_dev(X), lm, twomeans_iters=iters, seed=77, pass_=1)
     o_perm, o_off = oracle.partition(X, lm, iters=iters, seed=77, pass_=1)
     assert np.array_equal(_np(off), o_off)
