@@ -458,6 +458,107 @@ __global__ void __launch_bounds__(1024) k1_select_small(const float* __restrict_
     }
 }
 
+// Ascending bitonic sort of the warp's 32 R keys (R per lane, element
+// lane * R + r): exchanges within a lane for distances below R, across lanes
+// by shuffles above.
+template <int R>
+__device__ __forceinline__ void warp_bitonic_sort(uint64_t (&v)[R]) {
+    const int lane = threadIdx.x & 31;
+    constexpr int LOG = 5 + (R >= 2) + (R >= 4) + (R >= 8) + (R >= 16) + (R >= 32);
+    static_assert((32 * R) == (1 << LOG), "R is a power of two up to 32");
+#pragma unroll
+    for (int lk = 1; lk <= LOG; ++lk) {
+#pragma unroll
+        for (int lj = LOG - 1; lj >= 0; --lj) {  // constant trip count: unrolls fully
+            const int k = 1 << lk, j = 1 << lj;
+            if (lj < lk && j >= R) {
+                const int lj2 = j / R;
+                // k > j >= R: the direction bit of the pair is a lane bit
+                const bool up = ((lane * R) & k) == 0;
+                const bool keep_min = ((lane & lj2) == 0) == up;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint64_t o = shfl_xor64(v[r], lj2);
+                    v[r] = keep_min ? (o < v[r] ? o : v[r]) : (o > v[r] ? o : v[r]);
+                }
+            } else if (lj < lk) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if ((r & j) == 0) {
+                        const bool up = ((lane * R + r) & k) == 0;
+                        const uint64_t x = v[r], y = v[r | j];
+                        const bool sw = (x > y) == up;
+                        v[r] = sw ? y : x;
+                        v[r | j] = sw ? x : y;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Segments of up to 32 R points: one warp per segment holds its keys in
+// registers, sorts them and takes the floor(m/2)-th smallest; on the final
+// cut it partitions the segment stably into perm_out (left positions first,
+// each side in position order), as k1_select_small does.
+template <int R>
+__global__ void __launch_bounds__(128) k1_select_warp(const float* __restrict__ S,
+                                                      const int32_t* __restrict__ seg_off,
+                                                      const int32_t* __restrict__ seg_tile0, int nseg,
+                                                      int pos_bits, uint64_t* __restrict__ thr,
+                                                      const int32_t* __restrict__ perm_in,
+                                                      int32_t* __restrict__ perm_out, int* __restrict__ status) {
+    const int seg = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (seg >= nseg || seg_tile0[seg + 1] == seg_tile0[seg]) return;  // past the end; a finished tree's leaf
+    const int a = seg_off[seg], m = seg_off[seg + 1] - a;
+    if (m > 32 * R) {  // the plan sized R from the level's largest segment
+        if (lane == 0) atomicOr(status, kStatusInternal);
+        return;
+    }
+    uint64_t v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int p = r * 32 + lane;
+        v[r] = p < m ? sel_key(S[a + p], p, pos_bits) : ~0ull;  // padding sorts last
+    }
+    warp_bitonic_sort<R>(v);
+    const int K = m / 2;
+    // element K: register K % R of lane K / R (a masked OR keeps v[] in
+    // registers, where a select by a run-time index would not)
+    uint64_t mine = 0;
+    const int kr = K % R;
+#pragma unroll
+    for (int r = 0; r < R; ++r) mine |= v[r] & (0ull - (uint64_t)(r == kr));
+    const uint64_t T = shfl64(mine, K / R);
+    if (perm_out == nullptr) {
+        if (lane == 0) thr[seg] = T;
+        return;
+    }
+    int lb = 0;  // left positions before this chunk
+    for (int base = 0; base < m; base += 32) {
+        const int p = base + lane;
+        const bool in = p < m;
+        const bool isl = in && sel_key(S[a + p], p, pos_bits) < T;
+        const unsigned bl = __ballot_sync(0xffffffffu, isl);
+        const int l_rank = lb + __popc(bl & ((1u << lane) - 1u));
+        if (in) {
+            const int np = isl ? l_rank : K + (p - l_rank);
+            if ((isl ? np < K : np < m) && np >= 0)
+                perm_out[a + np] = perm_in[a + p];
+            else
+                atomicOr(status, kStatusInternal);
+        }
+        lb += __popc(bl);
+    }
+}
+
+template <int R>
+void launch_select_warp(const LevelPlan& lp, const SplitBuffers& b, const int32_t* perm_in, int32_t* perm_out,
+                        cudaStream_t s) {
+    k1_select_warp<R><<<(lp.nseg + 3) / 4, 128, 0, s>>>(b.S, lp.seg_off, lp.seg_tile0, lp.nseg, lp.pos_bits, b.thr,
+                                                         perm_in, perm_out, b.status);
+}
+
 // Large segments: one radix pass over bits [hi-11, hi) of the keys.  Every
 // tile adds its histogram to the segment's global one; the last tile of the
 // segment to finish (ticket) picks the digit and clears the histogram.
@@ -1016,7 +1117,23 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
                 k1_project<false><<<lp.nsweep, 256, 0, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S, st,
                                                             b.status, b.Xq, b.Dq, b.qtype, b.qflag);
         }
-        if (lp.small) {
+        if (lp.small && lp.max_m <= kWarpSelectMax) {
+            LaunchScope ls("k1_select_warp", s, n * 4 + (last ? n * 8 : 0), 0);
+            int32_t* out = last ? perm_out : nullptr;
+            if (lp.max_m <= 32)
+                launch_select_warp<1>(lp, b, perm_in, out, s);
+            else if (lp.max_m <= 64)
+                launch_select_warp<2>(lp, b, perm_in, out, s);
+            else if (lp.max_m <= 128)
+                launch_select_warp<4>(lp, b, perm_in, out, s);
+            else if (lp.max_m <= 256)
+                launch_select_warp<8>(lp, b, perm_in, out, s);
+            else if (lp.max_m <= 512)
+                launch_select_warp<16>(lp, b, perm_in, out, s);
+            else
+                launch_select_warp<32>(lp, b, perm_in, out, s);
+            if (last) break;
+        } else if (lp.small) {
             const size_t smem = (size_t)lp.max_m * sizeof(uint64_t);
             // one thread per point up to 1024, at least 4 warps
             const int nt = std::min(1024, std::max(128, (lp.max_m + 31) & ~31));
