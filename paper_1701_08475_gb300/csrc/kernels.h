@@ -84,7 +84,7 @@ struct SplitBuffers {
 constexpr int kTile = 2048;         // positions per select/partition tile
 constexpr int kSweepTile = 512;     // positions per project/sums tile
 constexpr int kSmallMax = 8192;     // segments up to this size select in one CTA
-constexpr int kWarpSelectMax = 1024; // segments up to this size select in one warp
+constexpr int kSortSelectMax = 2048; // segments up to this size select by a sort in registers
 constexpr int kRadixBits = 11;
 
 // One level of the balanced two-means tree: T Lloyd iterations, then the

@@ -458,24 +458,40 @@ __global__ void __launch_bounds__(1024) k1_select_small(const float* __restrict_
     }
 }
 
-// Ascending bitonic sort of the warp's 32 R keys (R per lane, element
-// lane * R + r): exchanges within a lane for distances below R, across lanes
-// by shuffles above.
-template <int R>
-__device__ __forceinline__ void warp_bitonic_sort(uint64_t (&v)[R]) {
-    const int lane = threadIdx.x & 31;
-    constexpr int LOG = 5 + (R >= 2) + (R >= 4) + (R >= 8) + (R >= 16) + (R >= 32);
-    static_assert((32 * R) == (1 << LOG), "R is a power of two up to 32");
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
+
+// Ascending bitonic sort of 32 R NW keys held by NW warps (R per lane;
+// element e = 32 R warp + R lane + r): exchanges within a lane for distances
+// below R, across lanes by shuffles up to 32 R, across warps through shared
+// memory (xch: 32 R NW keys) above.
+template <int R, int NW>
+__device__ __forceinline__ void bitonic_sort_keys(uint64_t (&v)[R], uint64_t* xch) {
+    const int lane = threadIdx.x & 31, warp = NW > 1 ? (int)(threadIdx.x >> 5) : 0;
+    constexpr int LOG = ilog2c(32 * R * NW);
+    static_assert((32 * R * NW) == (1 << LOG), "R and NW are powers of two");
+    const int e0 = 32 * R * warp + R * lane;  // element of v[0]
 #pragma unroll
     for (int lk = 1; lk <= LOG; ++lk) {
 #pragma unroll
         for (int lj = LOG - 1; lj >= 0; --lj) {  // constant trip count: unrolls fully
             const int k = 1 << lk, j = 1 << lj;
-            if (lj < lk && j >= R) {
+            if (lj < lk && j >= 32 * R) {
+                const int wj = j / (32 * R);
+                // the direction bit and the pair are warp bits
+                const bool keep_min = ((warp & wj) == 0) == ((e0 & k) == 0);
+#pragma unroll
+                for (int r = 0; r < R; ++r) xch[r * 32 * NW + threadIdx.x] = v[r];
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint64_t o = xch[r * 32 * NW + (threadIdx.x ^ (32 * wj))];
+                    v[r] = keep_min ? (o < v[r] ? o : v[r]) : (o > v[r] ? o : v[r]);
+                }
+                __syncthreads();
+            } else if (lj < lk && j >= R) {
                 const int lj2 = j / R;
-                // k > j >= R: the direction bit of the pair is a lane bit
-                const bool up = ((lane * R) & k) == 0;
-                const bool keep_min = ((lane & lj2) == 0) == up;
+                // k > j >= R: the direction bit of the pair is a lane or warp bit
+                const bool keep_min = ((lane & lj2) == 0) == ((e0 & k) == 0);
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const uint64_t o = shfl_xor64(v[r], lj2);
@@ -485,7 +501,7 @@ __device__ __forceinline__ void warp_bitonic_sort(uint64_t (&v)[R]) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     if ((r & j) == 0) {
-                        const bool up = ((lane * R + r) & k) == 0;
+                        const bool up = ((e0 + r) & k) == 0;
                         const uint64_t x = v[r], y = v[r | j];
                         const bool sw = (x > y) == up;
                         v[r] = sw ? y : x;
@@ -497,66 +513,104 @@ __device__ __forceinline__ void warp_bitonic_sort(uint64_t (&v)[R]) {
     }
 }
 
-// Segments of up to 32 R points: one warp per segment holds its keys in
-// registers, sorts them and takes the floor(m/2)-th smallest; on the final
-// cut it partitions the segment stably into perm_out (left positions first,
-// each side in position order), as k1_select_small does.
-template <int R>
-__global__ void __launch_bounds__(128) k1_select_warp(const float* __restrict__ S,
-                                                      const int32_t* __restrict__ seg_off,
-                                                      const int32_t* __restrict__ seg_tile0, int nseg,
-                                                      int pos_bits, uint64_t* __restrict__ thr,
-                                                      const int32_t* __restrict__ perm_in,
-                                                      int32_t* __restrict__ perm_out, int* __restrict__ status) {
-    const int seg = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+// Segments of up to 32 R NW points: NW warps hold a segment's keys in
+// registers, sort them and take the floor(m/2)-th smallest.  NW = 1: four
+// segments per CTA, one per warp; NW > 1: one segment per CTA.  On the final
+// cut each thread takes R consecutive positions, and an exclusive scan of
+// the left counts gives every position its place in perm_out (left positions
+// first, each side in position order), as k1_select_small does.
+template <int R, int NW>
+__global__ void __launch_bounds__(NW > 1 ? 32 * NW : 128) k1_select_sort(const float* __restrict__ S,
+                                                                        const int32_t* __restrict__ seg_off,
+                                                                        const int32_t* __restrict__ seg_tile0,
+                                                                        int nseg, int pos_bits,
+                                                                        uint64_t* __restrict__ thr,
+                                                                        const int32_t* __restrict__ perm_in,
+                                                                        int32_t* __restrict__ perm_out,
+                                                                        int* __restrict__ status) {
+    constexpr int NK = 32 * R * NW;  // keys per segment
+    __shared__ uint64_t xch[NW > 1 ? NK : 1];
+    __shared__ uint64_t sh_T;
+    __shared__ int warp_tot[32];
+    const int lane = threadIdx.x & 31;
+    const int tid = NW > 1 ? (int)threadIdx.x : lane;  // thread within the segment's group
+    const int seg = NW > 1 ? (int)blockIdx.x : (int)(blockIdx.x * 4 + (threadIdx.x >> 5));
+    // segment-uniform exits (NW > 1: the whole CTA)
     if (seg >= nseg || seg_tile0[seg + 1] == seg_tile0[seg]) return;  // past the end; a finished tree's leaf
     const int a = seg_off[seg], m = seg_off[seg + 1] - a;
-    if (m > 32 * R) {  // the plan sized R from the level's largest segment
-        if (lane == 0) atomicOr(status, kStatusInternal);
+    if (m > NK) {  // the plan sized the kernel from the level's largest segment
+        if (tid == 0) atomicOr(status, kStatusInternal);
         return;
     }
     uint64_t v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int p = r * 32 + lane;
+        const int p = r * 32 * NW + tid;
         v[r] = p < m ? sel_key(S[a + p], p, pos_bits) : ~0ull;  // padding sorts last
     }
-    warp_bitonic_sort<R>(v);
-    const int K = m / 2;
-    // element K: register K % R of lane K / R (a masked OR keeps v[] in
+    bitonic_sort_keys<R, NW>(v, xch);
+    // element K: register K % R of thread K / R (a masked OR keeps v[] in
     // registers, where a select by a run-time index would not)
+    const int K = m / 2;
     uint64_t mine = 0;
-    const int kr = K % R;
 #pragma unroll
-    for (int r = 0; r < R; ++r) mine |= v[r] & (0ull - (uint64_t)(r == kr));
-    const uint64_t T = shfl64(mine, K / R);
+    for (int r = 0; r < R; ++r) mine |= v[r] & (0ull - (uint64_t)(r == K % R));
+    uint64_t T;
+    if (NW > 1) {
+        if (tid == K / R) sh_T = mine;
+        __syncthreads();
+        T = sh_T;
+    } else {
+        T = shfl64(mine, K / R);
+    }
     if (perm_out == nullptr) {
-        if (lane == 0) thr[seg] = T;
+        if (tid == 0) thr[seg] = T;
         return;
     }
-    int lb = 0;  // left positions before this chunk
-    for (int base = 0; base < m; base += 32) {
-        const int p = base + lane;
-        const bool in = p < m;
-        const bool isl = in && sel_key(S[a + p], p, pos_bits) < T;
-        const unsigned bl = __ballot_sync(0xffffffffu, isl);
-        const int l_rank = lb + __popc(bl & ((1u << lane) - 1u));
-        if (in) {
-            const int np = isl ? l_rank : K + (p - l_rank);
-            if ((isl ? np < K : np < m) && np >= 0)
-                perm_out[a + np] = perm_in[a + p];
+    const int p0 = tid * R;
+    bool isl[R];
+    int32_t id[R];
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int p = p0 + r;
+        isl[r] = p < m && sel_key(S[a + p], p, pos_bits) < T;
+        id[r] = p < m ? perm_in[a + p] : 0;
+        cnt += isl[r];
+    }
+    int lb;  // left positions before p0
+    if (NW > 1) {
+        int tot;
+        lb = block_excl_scan(cnt, warp_tot, &tot);
+    } else {
+        int x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        lb = x - cnt;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int p = p0 + r;
+        if (p < m) {
+            const int np = isl[r] ? lb : K + (p - lb);
+            if ((isl[r] ? np < K : np < m) && np >= 0)
+                perm_out[a + np] = id[r];
             else
                 atomicOr(status, kStatusInternal);
+            lb += isl[r];
         }
-        lb += __popc(bl);
     }
 }
 
-template <int R>
-void launch_select_warp(const LevelPlan& lp, const SplitBuffers& b, const int32_t* perm_in, int32_t* perm_out,
+template <int R, int NW>
+void launch_select_sort(const LevelPlan& lp, const SplitBuffers& b, const int32_t* perm_in, int32_t* perm_out,
                         cudaStream_t s) {
-    k1_select_warp<R><<<(lp.nseg + 3) / 4, 128, 0, s>>>(b.S, lp.seg_off, lp.seg_tile0, lp.nseg, lp.pos_bits, b.thr,
-                                                         perm_in, perm_out, b.status);
+    const int grid = NW > 1 ? lp.nseg : (lp.nseg + 3) / 4;
+    k1_select_sort<R, NW><<<grid, NW > 1 ? 32 * NW : 128, 0, s>>>(b.S, lp.seg_off, lp.seg_tile0, lp.nseg,
+                                                                  lp.pos_bits, b.thr, perm_in, perm_out, b.status);
 }
 
 // Large segments: one radix pass over bits [hi-11, hi) of the keys.  Every
@@ -982,57 +1036,115 @@ __global__ void __launch_bounds__(kSuThreads) k1_sums_async(const float* __restr
                            su_smem);
 }
 
-// New centroids of each segment from its tiles' partial sums (kCenGroups
-// interleaved groups of tiles, each summed in tile order, then added in group
-// order), FP64 mean rounded to FP32; stores w = c1 - c0.  A sweep of both
-// sides stores the segment's total (segsum); after a left-only sweep the
-// right sum is that total minus the left sum.
-constexpr int kCenGroups = 4;  // tile groups of k1_centroids (128 dims each)
-__global__ void __launch_bounds__(128 * kCenGroups) k1_centroids(const double* __restrict__ partial,
-                                                                 const int32_t* __restrict__ seg_off,
-                                                                 const int32_t* __restrict__ seg_tile0, int D,
-                                                                 double* __restrict__ segsum, int left_only,
-                                                                 float* __restrict__ W) {
-    __shared__ double red[kCenGroups][2][128];
+// s / b rounded to nearest (FP64) from inv = RN(1 / b): the FMA residual
+// r = s - q0 b of q0 = RN(s inv) is exact, and q0 + r inv rounds to RN(s / b)
+// (Markstein's correction).  For integer s and b < 2^52 the quotient is never
+// within the correction's error of a rounding boundary, so the result equals
+// FP64 division bit for bit; it costs three FP64 operations, where GB300
+// issues FP64 at a small fraction of its FP32 rate.
+__device__ __forceinline__ double div_by(double s, double b, double inv) {
+    const double q0 = __dmul_rn(s, inv);
+    const double r = __fma_rn(-q0, b, s);
+    return __fma_rn(r, inv, q0);
+}
+
+// c1 - c0 of one dim from the left and right sums (or, left_only, the left sum
+// and the segment's total): FP64 means rounded to FP32.
+__device__ __forceinline__ void store_w(double sL, double sR, int seg, int d, int D, int K, int m, double inv0,
+                                        double inv1, double* __restrict__ segsum, int left_only,
+                                        float* __restrict__ W) {
+    if (left_only)
+        sR = segsum[(int64_t)seg * D + d] - sL;
+    else
+        segsum[(int64_t)seg * D + d] = sL + sR;
+    const float c0 = (float)div_by(sL, (double)K, inv0);
+    const float c1 = (float)div_by(sR, (double)(m - K), inv1);
+    W[(int64_t)seg * D + d] = __fsub_rn(c1, c0);
+}
+
+// New centroids of each segment from its tiles' partial sums; stores
+// w = c1 - c0.  A CTA takes 32 dims of one segment; its G warps sum
+// interleaved tiles (warp g: tiles t0 + g, t0 + g + G, ... in order), then
+// the G sums are added in warp order.  A sweep of both sides stores the
+// segment's total (segsum); after a left-only sweep the right sum is that
+// total minus the left sum.
+template <int G>
+__global__ void __launch_bounds__(32 * G) k1_centroids(const double* __restrict__ partial,
+                                                       const int32_t* __restrict__ seg_off,
+                                                       const int32_t* __restrict__ seg_tile0, int D,
+                                                       double* __restrict__ segsum, int left_only,
+                                                       float* __restrict__ W) {
+    __shared__ double red[G][2][32];
+    __shared__ double inv[2];
     const int seg = blockIdx.x;
     const int m = seg_off[seg + 1] - seg_off[seg];
     const int K = m / 2;
     const int t0 = seg_tile0[seg], t1 = seg_tile0[seg + 1];
     if (t0 == t1) return;  // a finished tree's leaf: no centroids
-    const int dl = threadIdx.x & 127, g = threadIdx.x >> 7;
-    for (int db = 0; db < D; db += 128) {
-        const int d = db + dl;
-        // group g sums tiles t0 + g, t0 + g + kCenGroups, ...; the groups are
-        // then added in order
-        double sL = 0.0, sR = 0.0;
-        if (d < D) {
-#pragma unroll 4
-            for (int t = t0 + g; t < t1; t += kCenGroups) {
-                sL += partial[((int64_t)t * 2 + 0) * D + d];
-                sR += partial[((int64_t)t * 2 + 1) * D + d];
-            }
-        }
-        red[g][0][dl] = sL;
-        red[g][1][dl] = sR;
-        __syncthreads();
-        if (g == 0 && d < D) {
-            sL = red[0][0][dl];
-            sR = red[0][1][dl];
-#pragma unroll
-            for (int q = 1; q < kCenGroups; ++q) {
-                sL += red[q][0][dl];
-                sR += red[q][1][dl];
-            }
-            if (left_only)
-                sR = segsum[(int64_t)seg * D + d] - sL;
-            else
-                segsum[(int64_t)seg * D + d] = sL + sR;
-            const float c0 = (float)(sL / (double)K);
-            const float c1 = (float)(sR / (double)(m - K));
-            W[(int64_t)seg * D + d] = __fsub_rn(c1, c0);
-        }
-        __syncthreads();
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int d = blockIdx.y * 32 + lane;
+    if (threadIdx.x == 0) {
+        inv[0] = 1.0 / (double)K;
+        inv[1] = 1.0 / (double)(m - K);
     }
+    double sL = 0.0, sR = 0.0;
+    if (d < D) {
+#pragma unroll 4
+        for (int t = t0 + g; t < t1; t += G) {
+            sL += partial[((int64_t)t * 2 + 0) * D + d];
+            sR += partial[((int64_t)t * 2 + 1) * D + d];
+        }
+    }
+    red[g][0][lane] = sL;
+    red[g][1][lane] = sR;
+    __syncthreads();
+    if (g == 0 && d < D) {
+        sL = red[0][0][lane];
+        sR = red[0][1][lane];
+#pragma unroll
+        for (int q = 1; q < G; ++q) {
+            sL += red[q][0][lane];
+            sR += red[q][1][lane];
+        }
+        store_w(sL, sR, seg, d, D, K, m, inv[0], inv[1], segsum, left_only, W);
+    }
+}
+
+// Segments of one or two tiles: each warp takes 32 dims of one segment and
+// sums its tiles in order.
+__global__ void __launch_bounds__(256) k1_centroids_warp(const double* __restrict__ partial,
+                                                         const int32_t* __restrict__ seg_off,
+                                                         const int32_t* __restrict__ seg_tile0, int nseg, int D,
+                                                         double* __restrict__ segsum, int left_only,
+                                                         float* __restrict__ W) {
+    const int nch = (D + 31) / 32;
+    const int pair = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (pair >= nseg * nch) return;
+    const int seg = pair / nch, d = (pair - seg * nch) * 32 + lane;
+    const int t0 = seg_tile0[seg], t1 = seg_tile0[seg + 1];
+    if (t0 == t1) return;  // a finished tree's leaf: no centroids
+    const int m = seg_off[seg + 1] - seg_off[seg];
+    const int K = m / 2;
+    double inv0 = 0.0, inv1 = 0.0;
+    if (lane == 0) {
+        inv0 = 1.0 / (double)K;
+        inv1 = 1.0 / (double)(m - K);
+    }
+    inv0 = __shfl_sync(0xffffffffu, inv0, 0);
+    inv1 = __shfl_sync(0xffffffffu, inv1, 0);
+    if (d >= D) return;
+    double sL = 0.0, sR = 0.0;
+    for (int t = t0; t < t1; ++t) {
+        sL += partial[((int64_t)t * 2 + 0) * D + d];
+        sR += partial[((int64_t)t * 2 + 1) * D + d];
+    }
+    store_w(sL, sR, seg, d, D, K, m, inv0, inv1, segsum, left_only, W);
+}
+
+template <int G>
+void launch_centroids(const LevelPlan& lp, const SplitBuffers& b, int D, int left_only, cudaStream_t s) {
+    k1_centroids<G><<<dim3(lp.nseg, (D + 31) / 32), 32 * G, 0, s>>>(b.partial, lp.seg_off, lp.seg_tile0, D,
+                                                                     b.segsum, left_only, b.W);
 }
 
 __global__ void __launch_bounds__(256) k1_part_count(const float* __restrict__ S, const int4* __restrict__ tiles,
@@ -1117,21 +1229,23 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
                 k1_project<false><<<lp.nsweep, 256, 0, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S, st,
                                                             b.status, b.Xq, b.Dq, b.qtype, b.qflag);
         }
-        if (lp.small && lp.max_m <= kWarpSelectMax) {
-            LaunchScope ls("k1_select_warp", s, n * 4 + (last ? n * 8 : 0), 0);
+        if (lp.small && lp.max_m <= kSortSelectMax) {
+            LaunchScope ls("k1_select_sort", s, n * 4 + (last ? n * 8 : 0), 0);
             int32_t* out = last ? perm_out : nullptr;
             if (lp.max_m <= 32)
-                launch_select_warp<1>(lp, b, perm_in, out, s);
+                launch_select_sort<1, 1>(lp, b, perm_in, out, s);
             else if (lp.max_m <= 64)
-                launch_select_warp<2>(lp, b, perm_in, out, s);
+                launch_select_sort<2, 1>(lp, b, perm_in, out, s);
             else if (lp.max_m <= 128)
-                launch_select_warp<4>(lp, b, perm_in, out, s);
+                launch_select_sort<4, 1>(lp, b, perm_in, out, s);
             else if (lp.max_m <= 256)
-                launch_select_warp<8>(lp, b, perm_in, out, s);
+                launch_select_sort<8, 1>(lp, b, perm_in, out, s);
             else if (lp.max_m <= 512)
-                launch_select_warp<16>(lp, b, perm_in, out, s);
+                launch_select_sort<8, 2>(lp, b, perm_in, out, s);
+            else if (lp.max_m <= 1024)
+                launch_select_sort<8, 4>(lp, b, perm_in, out, s);
             else
-                launch_select_warp<32>(lp, b, perm_in, out, s);
+                launch_select_sort<8, 8>(lp, b, perm_in, out, s);
             if (last) break;
         } else if (lp.small) {
             const size_t smem = (size_t)lp.max_m * sizeof(uint64_t);
@@ -1186,8 +1300,16 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
         }
         {
             LaunchScope ls("k1_centroids", s, (double)lp.ntiles * 2 * D * 8 + (double)lp.nseg * D * 4, 0);
-            k1_centroids<<<lp.nseg, 128 * kCenGroups, 0, s>>>(b.partial, lp.seg_off, lp.seg_tile0, D, b.segsum,
-                                                              left_only, b.W);
+            // warps per CTA: about one per tile of the largest segment, up to 32
+            const int tiles = (lp.max_m + kTile - 1) / kTile + 1;
+            if (tiles <= 3) {
+                const int64_t pairs = (int64_t)lp.nseg * ((D + 31) / 32);
+                k1_centroids_warp<<<(unsigned)((pairs + 7) / 8), 256, 0, s>>>(b.partial, lp.seg_off, lp.seg_tile0,
+                                                                               lp.nseg, D, b.segsum, left_only, b.W);
+            } else if (tiles <= 8)
+                launch_centroids<8>(lp, b, D, left_only, s);
+            else
+                launch_centroids<32>(lp, b, D, left_only, s);
         }
     }
 }
