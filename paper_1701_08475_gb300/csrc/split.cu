@@ -145,6 +145,15 @@ __device__ __forceinline__ float q16_to_float(uint32_t h) {
 __device__ __forceinline__ bool u8_usable(const uint8_t* Xb, const int* bflag) {
     return Xb != nullptr && *bflag == 0;
 }
+__device__ __forceinline__ bool exact_ints(const uint16_t* Xq, const int* qflag, const uint8_t* Xb,
+                                          const int* bflag) {
+    return u8_usable(Xb, bflag) || q16_usable(Xq, qflag);
+}
+// Every value of X an integer of magnitude <= 2048 (one of the exact copies is
+// usable): then the sums of a tile are exact integers below 2^24 and travel
+// as int32 partials, and a segment's sums are int64.
+__device__ __forceinline__ bool exact_ints(const uint16_t* Xq, const int* qflag, const uint8_t* Xb,
+                                          const int* bflag);
 __device__ __forceinline__ float u8_to_float(uint32_t word, int i) {
     return __fsub_rn(__uint_as_float(__byte_perm(word, 0x4B000000u, 0x7540u + (uint32_t)i)), 8388608.f);
 }
@@ -784,11 +793,14 @@ __global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restri
                                                           double* __restrict__ partial,
                                                           const int* __restrict__ status,
                                                           const uint16_t* __restrict__ Xq, int Dq, int qtype,
-                                                          const int* __restrict__ qflag, int left_only) {
+                                                          const int* __restrict__ qflag,
+                                                          const uint8_t* __restrict__ Xb,
+                                                          const int* __restrict__ bflag, int left_only) {
     __shared__ double red[kSumsWarps][2][128];
     __shared__ int rows[kSumsWarps][32];
     if (*status & kStatusStop) return;  // perm may hold unwritten slots
     const int q = q16_usable(Xq, qflag) ? qtype : 0;  // then lane l owns dims 4l .. 4l+3
+    const bool exact = exact_ints(Xq, qflag, Xb, bflag);
     const int4 t = tiles[blockIdx.x];
     const int seg = t.x, begin = t.y, end = t.z;
     const int dbase = blockIdx.y * 128;
@@ -813,6 +825,28 @@ __global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restri
     else
         sums_run<VEC, 0>(X, D, Xq, Dq, perm, S, a, T, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR, lR,
                          left_only != 0);
+    if (exact) {  // integer sums below 2^24 per lane and 2^31 per tile: int32 partials
+        int(*ired)[2][128] = reinterpret_cast<int(*)[2][128]>(red);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int dl = (VEC || q != 0) ? lane * 4 + j : lane + 32 * j;
+            ired[warp][0][dl] = __float2int_rn(hL[j]);
+            ired[warp][1][dl] = __float2int_rn(hR[j]);
+        }
+        __syncthreads();
+        if (threadIdx.x < 128 && dbase + threadIdx.x < D) {
+            int sL = 0, sR = 0;
+#pragma unroll
+            for (int w = 0; w < kSumsWarps; ++w) {
+                sL += ired[w][0][threadIdx.x];
+                sR += ired[w][1][threadIdx.x];
+            }
+            int32_t* ip = reinterpret_cast<int32_t*>(partial);
+            ip[((int64_t)blockIdx.x * 2 + 0) * D + dbase + threadIdx.x] = sL;
+            ip[((int64_t)blockIdx.x * 2 + 1) * D + dbase + threadIdx.x] = sR;
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int dl = (VEC || q != 0) ? lane * 4 + j : lane + 32 * j;
@@ -913,7 +947,7 @@ __device__ __forceinline__ void sums_async_tile(const float* __restrict__ X, int
                                                 const int32_t* __restrict__ perm,
                                                 const float* __restrict__ S, int a, uint64_t T, int pos_bits,
                                                 int begin, int end, bool left_only, double* __restrict__ part,
-                                                uint8_t* smem) {
+                                                int32_t* __restrict__ ipart, uint8_t* smem) {
     constexpr int SLAB = Q == 3 ? 128 : Q != 0 ? 64 : 32;  // dims per 128-byte slab
     constexpr int QUADS = SLAB / 4;                        // threads per row
     constexpr int G = kSuThreads / QUADS;                  // row groups
@@ -955,7 +989,12 @@ __device__ __forceinline__ void sums_async_tile(const float* __restrict__ X, int
     const int mt = left_only ? NL : m;  // rows staged
     const int nchunk = (mt + kPrRows - 1) / kPrRows;
     if (nchunk == 0) {  // no left rows: zero sums
-        for (int d = tid; d < 2 * D; d += kSuThreads) part[d] = 0.0;
+        for (int d = tid; d < 2 * D; d += kSuThreads) {
+            if (Q != 0)
+                ipart[d] = 0;
+            else
+                part[d] = 0.0;
+        }
         return;
     }
     const int nslab = (D + SLAB - 1) / SLAB, nstage = nslab * nchunk;
@@ -981,7 +1020,24 @@ __device__ __forceinline__ void sums_async_tile(const float* __restrict__ X, int
             for (; i < nl; i += G) sums_add<Q>(buf + i * kPrStride, q, hL, lL);
             for (; i < cnt; i += G) sums_add<Q>(buf + i * kPrStride, q, hR, lR);
         }
-        if (c == nchunk - 1) {  // the slab's rows are all in: combine the groups
+        if (c == nchunk - 1 && Q != 0) {  // integer data: exact int32 sums of the slab's dims
+            int* ired = reinterpret_cast<int*>(red);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                ired[(0 * G + g) * SLAB + 4 * q + j] = __float2int_rn(hL[j]);
+                ired[(1 * G + g) * SLAB + 4 * q + j] = __float2int_rn(hR[j]);
+                hL[j] = hR[j] = 0.f;
+            }
+            __syncthreads();
+            if (tid < 2 * SLAB) {
+                const int side = tid / SLAB, dd = tid - side * SLAB;
+                if (d0 + dd < D) {
+                    int acc = 0;
+                    for (int gg = 0; gg < G; ++gg) acc += ired[(side * G + gg) * SLAB + dd];
+                    ipart[(int64_t)side * D + d0 + dd] = acc;
+                }
+            }
+        } else if (c == nchunk - 1) {  // the slab's rows are all in: combine the groups
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 red[(0 * G + g) * SLAB + 4 * q + j] = (double)hL[j] + (double)lL[j];
@@ -1021,19 +1077,21 @@ __global__ void __launch_bounds__(kSuThreads) k1_sums_async(const float* __restr
     const int seg = t.x, begin = t.y, end = t.z;
     const int a = seg_off[seg];
     const uint64_t T = thr[seg];
+    // this tile's sums: [2][D] FP64, or int32 for integer data (Q != 0)
     double* part = partial + (int64_t)blockIdx.x * 2 * D;
+    int32_t* ipart = reinterpret_cast<int32_t*>(partial) + (int64_t)blockIdx.x * 2 * D;
     if (q == 3)
         sums_async_tile<3>(X, D, Xq, Dq, Xb, Db, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
-                           su_smem);
+                           ipart, su_smem);
     else if (q == 1)
         sums_async_tile<1>(X, D, Xq, Dq, Xb, Db, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
-                           su_smem);
+                           ipart, su_smem);
     else if (q == 2)
         sums_async_tile<2>(X, D, Xq, Dq, Xb, Db, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
-                           su_smem);
+                           ipart, su_smem);
     else
         sums_async_tile<0>(X, D, Xq, Dq, Xb, Db, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
-                           su_smem);
+                           ipart, su_smem);
 }
 
 // s / b rounded to nearest (FP64) from inv = RN(1 / b): the FMA residual
@@ -1046,6 +1104,26 @@ __device__ __forceinline__ double div_by(double s, double b, double inv) {
     const double q0 = __dmul_rn(s, inv);
     const double r = __fma_rn(-q0, b, s);
     return __fma_rn(r, inv, q0);
+}
+
+// RN32(S / K) of an integer sum: FP32 division when S and K are exact in FP32
+// (no double rounding can separate it from RN32(RN64(S / K)) for K < 2^28:
+// the quotient is either an FP32 midpoint, which FP64 holds exactly, or
+// farther from one than FP64's rounding error), else FP64 division.
+__device__ __forceinline__ float mean_of_ints(long long S, int K) {
+    if (S > -16777216LL && S < 16777216LL && K < 16777216) return __fdiv_rn((float)S, (float)K);
+    return (float)((double)S / (double)K);
+}
+
+// c1 - c0 of one dim from integer sums (int64; segsum holds int64 totals).
+__device__ __forceinline__ void store_w_ints(long long sL, long long sR, int seg, int d, int D, int K, int m,
+                                             double* __restrict__ segsum, int left_only, float* __restrict__ W) {
+    long long* ss = reinterpret_cast<long long*>(segsum);
+    if (left_only)
+        sR = ss[(int64_t)seg * D + d] - sL;
+    else
+        ss[(int64_t)seg * D + d] = sL + sR;
+    W[(int64_t)seg * D + d] = __fsub_rn(mean_of_ints(sR, m - K), mean_of_ints(sL, K));
 }
 
 // c1 - c0 of one dim from the left and right sums (or, left_only, the left sum
@@ -1073,7 +1151,10 @@ __global__ void __launch_bounds__(32 * G) k1_centroids(const double* __restrict_
                                                        const int32_t* __restrict__ seg_off,
                                                        const int32_t* __restrict__ seg_tile0, int D,
                                                        double* __restrict__ segsum, int left_only,
-                                                       float* __restrict__ W) {
+                                                       float* __restrict__ W, const uint16_t* __restrict__ Xq,
+                                                       const int* __restrict__ qflag,
+                                                       const uint8_t* __restrict__ Xb,
+                                                       const int* __restrict__ bflag) {
     __shared__ double red[G][2][32];
     __shared__ double inv[2];
     const int seg = blockIdx.x;
@@ -1083,6 +1164,32 @@ __global__ void __launch_bounds__(32 * G) k1_centroids(const double* __restrict_
     if (t0 == t1) return;  // a finished tree's leaf: no centroids
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int d = blockIdx.y * 32 + lane;
+    if (exact_ints(Xq, qflag, Xb, bflag)) {  // int32 partials, int64 sums
+        const int32_t* ip = reinterpret_cast<const int32_t*>(partial);
+        long long iL = 0, iR = 0;
+        if (d < D) {
+#pragma unroll 4
+            for (int t = t0 + g; t < t1; t += G) {
+                iL += ip[((int64_t)t * 2 + 0) * D + d];
+                iR += ip[((int64_t)t * 2 + 1) * D + d];
+            }
+        }
+        long long(*ired)[2][32] = reinterpret_cast<long long(*)[2][32]>(red);
+        ired[g][0][lane] = iL;
+        ired[g][1][lane] = iR;
+        __syncthreads();
+        if (g == 0 && d < D) {
+            iL = ired[0][0][lane];
+            iR = ired[0][1][lane];
+#pragma unroll
+            for (int q = 1; q < G; ++q) {
+                iL += ired[q][0][lane];
+                iR += ired[q][1][lane];
+            }
+            store_w_ints(iL, iR, seg, d, D, K, m, segsum, left_only, W);
+        }
+        return;
+    }
     if (threadIdx.x == 0) {
         inv[0] = 1.0 / (double)K;
         inv[1] = 1.0 / (double)(m - K);
@@ -1116,7 +1223,10 @@ __global__ void __launch_bounds__(256) k1_centroids_warp(const double* __restric
                                                          const int32_t* __restrict__ seg_off,
                                                          const int32_t* __restrict__ seg_tile0, int nseg, int D,
                                                          double* __restrict__ segsum, int left_only,
-                                                         float* __restrict__ W) {
+                                                         float* __restrict__ W, const uint16_t* __restrict__ Xq,
+                                                         const int* __restrict__ qflag,
+                                                         const uint8_t* __restrict__ Xb,
+                                                         const int* __restrict__ bflag) {
     const int nch = (D + 31) / 32;
     const int pair = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (pair >= nseg * nch) return;
@@ -1125,6 +1235,17 @@ __global__ void __launch_bounds__(256) k1_centroids_warp(const double* __restric
     if (t0 == t1) return;  // a finished tree's leaf: no centroids
     const int m = seg_off[seg + 1] - seg_off[seg];
     const int K = m / 2;
+    if (exact_ints(Xq, qflag, Xb, bflag)) {  // int32 partials, int64 sums
+        if (d >= D) return;
+        const int32_t* ip = reinterpret_cast<const int32_t*>(partial);
+        long long iL = 0, iR = 0;
+        for (int t = t0; t < t1; ++t) {
+            iL += ip[((int64_t)t * 2 + 0) * D + d];
+            iR += ip[((int64_t)t * 2 + 1) * D + d];
+        }
+        store_w_ints(iL, iR, seg, d, D, K, m, segsum, left_only, W);
+        return;
+    }
     double inv0 = 0.0, inv1 = 0.0;
     if (lane == 0) {
         inv0 = 1.0 / (double)K;
@@ -1144,7 +1265,8 @@ __global__ void __launch_bounds__(256) k1_centroids_warp(const double* __restric
 template <int G>
 void launch_centroids(const LevelPlan& lp, const SplitBuffers& b, int D, int left_only, cudaStream_t s) {
     k1_centroids<G><<<dim3(lp.nseg, (D + 31) / 32), 32 * G, 0, s>>>(b.partial, lp.seg_off, lp.seg_tile0, D,
-                                                                     b.segsum, left_only, b.W);
+                                                                     b.segsum, left_only, b.W, b.Xq, b.qflag,
+                                                                     b.Xb, b.bflag);
 }
 
 __global__ void __launch_bounds__(256) k1_part_count(const float* __restrict__ S, const int4* __restrict__ tiles,
@@ -1292,11 +1414,11 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
             } else if (vec)
                 k1_sums<true><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr,
                                                                lp.pos_bits, b.partial, b.status, b.Xq, b.Dq,
-                                                               b.qtype, b.qflag, left_only);
+                                                               b.qtype, b.qflag, b.Xb, b.bflag, left_only);
             else
                 k1_sums<false><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr,
                                                                 lp.pos_bits, b.partial, b.status, b.Xq, b.Dq,
-                                                                b.qtype, b.qflag, left_only);
+                                                                b.qtype, b.qflag, b.Xb, b.bflag, left_only);
         }
         {
             LaunchScope ls("k1_centroids", s, (double)lp.ntiles * 2 * D * 8 + (double)lp.nseg * D * 4, 0);
@@ -1305,7 +1427,8 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
             if (tiles <= 3) {
                 const int64_t pairs = (int64_t)lp.nseg * ((D + 31) / 32);
                 k1_centroids_warp<<<(unsigned)((pairs + 7) / 8), 256, 0, s>>>(b.partial, lp.seg_off, lp.seg_tile0,
-                                                                               lp.nseg, D, b.segsum, left_only, b.W);
+                                                                               lp.nseg, D, b.segsum, left_only, b.W,
+                                                                               b.Xq, b.qflag, b.Xb, b.bflag);
             } else if (tiles <= 8)
                 launch_centroids<8>(lp, b, D, left_only, s);
             else
