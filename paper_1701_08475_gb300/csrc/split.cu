@@ -15,6 +15,9 @@
 // x . (c1 - c0) has the same order.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <cstdlib>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -263,14 +266,12 @@ __global__ void __launch_bounds__(256) k1_project(const float* __restrict__ X, i
         project_tile<VEC2, 0>(X, D, Xq, Dq, perm, begin, end, w, S, xs, ws);
 }
 
-// The projection with rows staged by cp.async and double-buffered: while one
-// 128-byte slab of 256 rows (64 dims of the 16-bit copy, or 32 dims of X) is
-// summed, the copies of the next slab are in flight.  Staged rows are 144
-// bytes apart, so the 16-byte reads of 8 consecutive threads cover all 32
-// banks once.  Needs 16-byte aligned rows of X (D a multiple of 4).
+// Rows staged by cp.async, a 128-byte slab at a time (128 dims of the byte
+// copy, 64 of the 16-bit copy, or 32 of X), 256 rows per stage.  Staged rows
+// are 144 bytes apart, so the 16-byte reads of 8 consecutive threads cover all
+// 32 banks once.  Reading X needs 16-byte aligned rows (D a multiple of 4).
 constexpr int kPrRows = 256;
 constexpr int kPrStride = 144;
-constexpr int kPrSmem = 2 * kPrRows * kPrStride + 2 * 128 * 4 + kSweepTile * 4;
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -278,60 +279,162 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
                  : "memory");
 }
 
+// Persistent, pipelined projection: CTA b walks the sweep tiles b, b + grid,
+// ...; each tile is a run of stages (256 rows by one 128-byte slab of each;
+// thread t sums the dims of row t in ascending order, one fmaf per dim, across
+// the slabs of its chunk) that flow through a ring of kPpBufs shared-memory
+// buffers, so that the copies of the next kPpBufs - 1 stages are in flight
+// while one is summed.  The row ids of a stage are loaded into registers one
+// iteration before its copies are issued, and the w slab travels with the
+// stage's copies.
+constexpr int kPpBufs = 3;
+constexpr int kPpSmem = kPpBufs * (kPrRows * kPrStride + 128 * 4);
+
+// Walks a CTA's stages: tile t (blockIdx.x + i gridDim.x), chunk c of 256
+// rows, slab sl.  Uniform across the CTA.
+struct PpIter {
+    int t, c, sl, nslab, ntiles;
+    int4 tl, tl_next;  // tiles[t], tiles[t + gridDim.x] (loaded ahead)
+    __device__ __forceinline__ void init(const int4* __restrict__ tiles, int ntiles_, int nslab_) {
+        ntiles = ntiles_;
+        nslab = nslab_;
+        t = blockIdx.x;
+        c = sl = 0;
+        tl = t < ntiles ? tiles[t] : make_int4(-1, 0, 0, 0);
+        tl_next = t + (int)gridDim.x < ntiles ? tiles[t + gridDim.x] : make_int4(-1, 0, 0, 0);
+    }
+    __device__ __forceinline__ bool valid() const { return t < ntiles; }
+    __device__ __forceinline__ int base() const { return tl.y + c * kPrRows; }
+    __device__ __forceinline__ int cnt() const { return min(kPrRows, tl.z - base()); }
+    __device__ __forceinline__ void next(const int4* __restrict__ tiles) {
+        if (++sl < nslab) return;
+        sl = 0;
+        if (tl.y + (++c) * kPrRows < tl.z) return;
+        c = 0;
+        t += gridDim.x;
+        tl = tl_next;
+        const int t2 = t + (int)gridDim.x;
+        tl_next = t2 < ntiles ? tiles[t2] : make_int4(-1, 0, 0, 0);
+    }
+};
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
 template <int Q>  // 0 = FP32 rows of X, 1 / 2 = BF16 / FP16 copy, 3 = byte copy
-__device__ __forceinline__ void project_async_tile(const float* __restrict__ X, int D,
-                                                   const uint16_t* __restrict__ Xq, int Dq,
-                                                   const uint8_t* __restrict__ Xb, int Db,
-                                                   const int32_t* __restrict__ perm, int begin, int end,
-                                                   const float* __restrict__ w, float* __restrict__ S,
-                                                   uint8_t* smem) {
+__device__ __forceinline__ void project_pipe(const float* __restrict__ X, int D, const uint16_t* __restrict__ Xq,
+                                             int Dq, const uint8_t* __restrict__ Xb, int Db,
+                                             const int32_t* __restrict__ perm, const int4* __restrict__ tiles,
+                                             int ntiles, const int32_t* __restrict__ seg_off,
+                                             const float* __restrict__ W, float* __restrict__ S,
+                                             SelState* __restrict__ st, uint8_t* smem) {
     constexpr int SLAB = Q == 3 ? 128 : Q != 0 ? 64 : 32;  // dims per 128-byte slab
-    float* wsb = reinterpret_cast<float*>(smem + 2 * kPrRows * kPrStride);  // [2][128]
-    int* ids = reinterpret_cast<int*>(wsb + 2 * 128);                       // [kSweepTile]
-    const int tid = threadIdx.x;
-    // the tile's row ids once, so that no copy waits on a global load
-    for (int p = tid; p < end - begin; p += kPrRows) ids[p] = perm[begin + p];
-    __syncthreads();
+    const int tid = threadIdx.x, piece = tid & 7;
     const int nslab = (D + SLAB - 1) / SLAB;
-    const int nstage = ((end - begin + kPrRows - 1) / kPrRows) * nslab;
-    // stage st: rows begin + (st / nslab) * 256 .., dims (st % nslab) * SLAB ..
-    auto issue = [&](int st) {
-        const int c = st / nslab, d0 = (st - c * nslab) * SLAB;
-        const int base = begin + c * kPrRows, cnt = min(kPrRows, end - base);
-        uint8_t* buf = smem + (st & 1) * (kPrRows * kPrStride);
-        for (int e = tid; e < kPrRows * 8; e += kPrRows) {
-            const int r = e >> 3, part = e & 7;
-            if (r >= cnt) break;
-            const int row = ids[base - begin + r];
-            if (Q == 3) {
-                if (d0 + part * 16 < Db)
-                    cp_async16(buf + r * kPrStride + part * 16, Xb + (int64_t)row * Db + d0 + part * 16);
-            } else if (Q != 0) {
-                cp_async16(buf + r * kPrStride + part * 16, Xq + (int64_t)row * Dq + d0 + part * 8);
-            } else if (d0 + part * 4 < D) {
-                cp_async16(buf + r * kPrStride + part * 16, X + (int64_t)row * D + d0 + part * 4);
+    // thread tid copies piece (tid & 7) of rows (tid >> 3) + 32 k, k < 8
+    int ids[8];
+    auto load_ids = [&](const PpIter& it) {
+        const int base = it.base(), cnt = it.cnt();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int r = (tid >> 3) + 32 * k;
+            ids[k] = r < cnt ? __ldg(perm + base + r) : 0;
+        }
+    };
+    auto issue = [&](const PpIter& it, int buf) {
+        if (it.valid()) {
+            const int cnt = it.cnt(), d0 = it.sl * SLAB, seg = it.tl.x;
+            uint8_t* b = smem + buf * (kPrRows * kPrStride);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int r = (tid >> 3) + 32 * k;
+                if (r >= cnt) break;
+                if (Q == 3) {
+                    if (d0 + piece * 16 < Db)
+                        cp_async16(b + r * kPrStride + piece * 16, Xb + (int64_t)ids[k] * Db + d0 + piece * 16);
+                } else if (Q != 0) {
+                    cp_async16(b + r * kPrStride + piece * 16, Xq + (int64_t)ids[k] * Dq + d0 + piece * 8);
+                } else if (d0 + piece * 4 < D) {
+                    cp_async16(b + r * kPrStride + piece * 16, X + (int64_t)ids[k] * D + d0 + piece * 4);
+                }
+            }
+            float* ws = reinterpret_cast<float*>(smem + kPpBufs * (kPrRows * kPrStride)) + buf * 128;
+            if (tid < SLAB) {
+                if (d0 + tid < D)
+                    cp_async4(ws + tid, W + (int64_t)seg * D + d0 + tid);
+                else
+                    ws[tid] = 0.f;
             }
         }
-        if (tid < SLAB) wsb[(st & 1) * 128 + tid] = d0 + tid < D ? w[d0 + tid] : 0.f;
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    if (nstage > 0) issue(0);
+    PpIter ic, ii;  // the stage to compute; the next stage to issue
+    ic.init(tiles, ntiles, nslab);
+    ii = ic;
+    // prologue: stages 0 .. kPpBufs - 2
+#pragma unroll
+    for (int k = 0; k < kPpBufs - 1; ++k) {
+        if (ii.valid()) load_ids(ii);
+        issue(ii, k);
+        if (ii.valid()) ii.next(tiles);
+    }
+    if (ii.valid()) load_ids(ii);
     float acc = 0.f;
-    for (int st = 0; st < nstage; ++st) {
-        if (st + 1 < nstage) {
-            issue(st + 1);
-            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    for (int s = 0; ic.valid(); ++s) {
+        issue(ii, (s + kPpBufs - 1) % kPpBufs);  // ids loaded one iteration ago
+        if (ii.valid()) {
+            ii.next(tiles);
+            if (ii.valid()) load_ids(ii);  // consumed by the next iteration's issue
         }
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kPpBufs - 1) : "memory");
         __syncthreads();
-        const int c = st / nslab, sl = st - c * nslab, d0 = sl * SLAB;
-        const int base = begin + c * kPrRows, cnt = min(kPrRows, end - base);
+        const int buf = s % kPpBufs, cnt = ic.cnt(), d0 = ic.sl * SLAB;
+        if (st != nullptr && ic.tl.w && ic.c == 0 && ic.sl == 0 && tid == 0) {  // a segment's first tile
+            const int seg = ic.tl.x, m = seg_off[seg + 1] - seg_off[seg];
+            st[seg].prefix = 0;
+            st[seg].krem = (uint32_t)(m / 2);
+            st[seg].done = 0;  // set once the selection is done
+        }
         if (tid < cnt) {
-            const uint8_t* rowp = smem + (st & 1) * (kPrRows * kPrStride) + tid * kPrStride;
-            const float* ws = wsb + (st & 1) * 128;
+            const uint8_t* rowp = smem + buf * (kPrRows * kPrStride) + tid * kPrStride;
+            const float* ws = reinterpret_cast<const float*>(smem + kPpBufs * (kPrRows * kPrStride)) + buf * 128;
             const int dl = min(SLAB, D - d0);
-            if (Q == 3) {
+            if (dl == SLAB) {  // a full slab: no per-dim guards, w four dims per load
+                const float4* w4 = reinterpret_cast<const float4*>(ws);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const uint4 h = *reinterpret_cast<const uint4*>(rowp + q * 16);
+                    const uint32_t hv[4] = {h.x, h.y, h.z, h.w};
+                    if (Q == 3) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float4 wv = w4[q * 4 + u];
+                            acc = __fmaf_rn(u8_to_float(hv[u], 0), wv.x, acc);
+                            acc = __fmaf_rn(u8_to_float(hv[u], 1), wv.y, acc);
+                            acc = __fmaf_rn(u8_to_float(hv[u], 2), wv.z, acc);
+                            acc = __fmaf_rn(u8_to_float(hv[u], 3), wv.w, acc);
+                        }
+                    } else if (Q != 0) {
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const float4 wv = w4[q * 2 + u];
+                            acc = __fmaf_rn(q16_to_float<Q>(hv[2 * u] & 0xFFFFu), wv.x, acc);
+                            acc = __fmaf_rn(q16_to_float<Q>(hv[2 * u] >> 16), wv.y, acc);
+                            acc = __fmaf_rn(q16_to_float<Q>(hv[2 * u + 1] & 0xFFFFu), wv.z, acc);
+                            acc = __fmaf_rn(q16_to_float<Q>(hv[2 * u + 1] >> 16), wv.w, acc);
+                        }
+                    } else {
+                        const float4 wv = w4[q];
+                        acc = __fmaf_rn(__uint_as_float(hv[0]), wv.x, acc);
+                        acc = __fmaf_rn(__uint_as_float(hv[1]), wv.y, acc);
+                        acc = __fmaf_rn(__uint_as_float(hv[2]), wv.z, acc);
+                        acc = __fmaf_rn(__uint_as_float(hv[3]), wv.w, acc);
+                    }
+                }
+            } else if (Q == 3) {
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     if (q * 16 >= dl) break;
@@ -366,46 +469,49 @@ __device__ __forceinline__ void project_async_tile(const float* __restrict__ X, 
                         if (q * 4 + t < dl) acc = __fmaf_rn(vv[t], ws[q * 4 + t], acc);
                 }
             }
-            if (sl == nslab - 1) {
-                S[base + tid] = __fadd_rn(acc, 0.f);  // -0 -> +0
+            if (ic.sl == nslab - 1) {
+                S[ic.base() + tid] = __fadd_rn(acc, 0.f);  // -0 -> +0
                 acc = 0.f;
             }
         }
-        __syncthreads();  // buffer st & 1 is refilled by the next issue
+        __syncthreads();  // buffer s % kPpBufs is refilled by the next issue
+        ic.next(tiles);
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-__global__ void __launch_bounds__(kPrRows) k1_project_async(const float* __restrict__ X, int D,
-                                                            const int32_t* __restrict__ perm,
-                                                            const int4* __restrict__ tiles,
-                                                            const int32_t* __restrict__ seg_off,
-                                                            const float* __restrict__ W, float* __restrict__ S,
-                                                            SelState* __restrict__ st,
-                                                            const int* __restrict__ status,
-                                                            const uint16_t* __restrict__ Xq, int Dq, int qtype,
-                                                            const int* __restrict__ qflag,
-                                                            const uint8_t* __restrict__ Xb, int Db,
-                                                            const int* __restrict__ bflag) {
-    extern __shared__ __align__(16) uint8_t pr_smem[];
+__global__ void __launch_bounds__(kPrRows, 2) k1_project_pipe(const float* __restrict__ X, int D,
+                                                              const int32_t* __restrict__ perm,
+                                                              const int4* __restrict__ tiles, int ntiles,
+                                                              const int32_t* __restrict__ seg_off,
+                                                              const float* __restrict__ W, float* __restrict__ S,
+                                                              SelState* __restrict__ st,
+                                                              const int* __restrict__ status,
+                                                              const uint16_t* __restrict__ Xq, int Dq, int qtype,
+                                                              const int* __restrict__ qflag,
+                                                              const uint8_t* __restrict__ Xb, int Db,
+                                                              const int* __restrict__ bflag) {
+    extern __shared__ __align__(16) uint8_t pp_smem[];
     if (*status & kStatusStop) return;  // perm may hold unwritten slots
     const int q = u8_usable(Xb, bflag) ? 3 : q16_usable(Xq, qflag) ? qtype : 0;
-    const int4 t = tiles[blockIdx.x];
-    const int seg = t.x, begin = t.y, end = t.z;
-    if (st != nullptr && t.w && threadIdx.x == 0) {
-        const int m = seg_off[seg + 1] - seg_off[seg];
-        st[seg].prefix = 0;
-        st[seg].krem = (uint32_t)(m / 2);
-        st[seg].done = 0;  // set once the selection is done
-    }
-    const float* w = W + (int64_t)seg * D;
     if (q == 3)
-        project_async_tile<3>(X, D, Xq, Dq, Xb, Db, perm, begin, end, w, S, pr_smem);
+        project_pipe<3>(X, D, Xq, Dq, Xb, Db, perm, tiles, ntiles, seg_off, W, S, st, pp_smem);
     else if (q == 1)
-        project_async_tile<1>(X, D, Xq, Dq, Xb, Db, perm, begin, end, w, S, pr_smem);
+        project_pipe<1>(X, D, Xq, Dq, Xb, Db, perm, tiles, ntiles, seg_off, W, S, st, pp_smem);
     else if (q == 2)
-        project_async_tile<2>(X, D, Xq, Dq, Xb, Db, perm, begin, end, w, S, pr_smem);
+        project_pipe<2>(X, D, Xq, Dq, Xb, Db, perm, tiles, ntiles, seg_off, W, S, st, pp_smem);
     else
-        project_async_tile<0>(X, D, Xq, Dq, Xb, Db, perm, begin, end, w, S, pr_smem);
+        project_pipe<0>(X, D, Xq, Dq, Xb, Db, perm, tiles, ntiles, seg_off, W, S, st, pp_smem);
+}
+
+int sm_count() {
+    static const int n = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
+    return n;
 }
 
 // Small segments: one CTA per segment keeps all keys in shared memory,
@@ -1340,10 +1446,11 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
             LaunchScope ls("k1_project", s, rows + n * 8, 2.0 * n * D);
             SelState* st = lp.small ? nullptr : b.st;
             if (vec) {
-                cudaFuncSetAttribute(k1_project_async, cudaFuncAttributeMaxDynamicSharedMemorySize, kPrSmem);
-                k1_project_async<<<lp.nsweep, kPrRows, kPrSmem, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S,
-                                                                     st, b.status, b.Xq, b.Dq, b.qtype, b.qflag,
-                                                                     b.Xb, b.Db, b.bflag);
+                cudaFuncSetAttribute(k1_project_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, kPpSmem);
+                const int grid = std::min(lp.nsweep, 2 * sm_count());
+                k1_project_pipe<<<grid, kPrRows, kPpSmem, s>>>(X, D, perm_in, lp.sweep, lp.nsweep, lp.seg_off, b.W,
+                                                               b.S, st, b.status, b.Xq, b.Dq, b.qtype, b.qflag,
+                                                               b.Xb, b.Db, b.bflag);
             } else if (vec2)
                 k1_project<true><<<lp.nsweep, 256, 0, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S, st,
                                                            b.status, b.Xq, b.Dq, b.qtype, b.qflag);
