@@ -576,12 +576,15 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.sb.W = ws.take<float>((size_t)ns * D);
         b.sb.S = ws.take<float>(n);
         b.sb.thr = ws.take<uint64_t>(ns);
+        b.sb.S2 = ws.take<float>(n);
+        b.sb.thr2 = ws.take<uint64_t>(ns);
         b.sb.st = ws.take<SelState>(ns);
         b.sb.ghist = ws.take<uint32_t>((size_t)nl << kRadixBits);
         b.sb.ticket = ws.take<uint32_t>(nl);
         b.sb.nseg_large = nl;
         b.sb.partial = ws.take<double>((size_t)std::max(tp.nsweep_max, 1) * 2 * D);
         b.sb.segsum = ws.take<double>((size_t)ns * D);
+        b.sb.segleft = ws.take<double>((size_t)ns * D);
         b.sb.tile_left = ws.take<int32_t>(nt);
         b.sb.status = b.status;
     }

@@ -55,14 +55,17 @@ struct LevelPlan {
 
 struct SplitBuffers {
     float* W;             // [nseg_max][D]  c1 - c0 per segment
-    float* S;             // [n] projections
+    float* S;             // [n] projections (even iterations of a level)
     uint64_t* thr;        // [nseg_max] selected key (first key of the right side)
+    float* S2;            // [n], [nseg_max]: the same for odd iterations
+    uint64_t* thr2;
     SelState* st;         // [nseg_max]
     uint32_t* ghist;      // [nseg_large][2048]: zeroed once per partition, left zero by each select
     uint32_t* ticket;     // [nseg_large]: same
     int nseg_large;       // segments of the widest level that selects across CTAs
     double* partial;      // [nsweep_max][2][D]
-    double* segsum;       // [nseg_max][D] each segment's sum of rows (FP64)
+    double* segsum;       // [nseg_max][D] each segment's sum of rows (FP64, or int64 for integer data)
+    double* segleft;      // [nseg_max][D] the same for its left side at the last cut
     int32_t* tile_left;   // [ntiles_max]
     int* status;          // device status word
     // 16-bit copy of X (original order, rows of Dq); the sweeps read it

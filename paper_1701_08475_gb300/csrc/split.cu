@@ -749,11 +749,22 @@ __global__ void __launch_bounds__(256) k1_select_pass(const float* __restrict__ 
     const int lo = digit_lo(hi, pos_bits), width = hi - lo, nb = 1 << width;
     const uint32_t mask = (uint32_t)nb - 1u;
     const uint64_t prefix = st[seg].prefix;
+    // the tile's projections first (all loads in flight at once), then the
+    // histogram
+    constexpr int PER = kTile / 256;
+    float sv[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int p = begin + (int)threadIdx.x + 256 * i;
+        sv[i] = p < end ? S[p] : 0.f;
+    }
     for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
     __syncthreads();
-    for (int p = begin + threadIdx.x; p < end; p += blockDim.x) {
-        const uint64_t kk = sel_key(S[p], p - a, pos_bits);
-        if ((kk >> hi) == (prefix >> hi)) atomicAdd(&hist[(uint32_t)(kk >> lo) & mask], 1u);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int p = begin + (int)threadIdx.x + 256 * i;
+        const uint64_t kk = sel_key(sv[i], p - a, pos_bits);
+        if (p < end && (kk >> hi) == (prefix >> hi)) atomicAdd(&hist[(uint32_t)(kk >> lo) & mask], 1u);
     }
     __syncthreads();
     uint32_t* gh = ghist + (size_t)seg * (1 << kRadixBits);
@@ -852,40 +863,57 @@ __device__ __forceinline__ void sums_side(const float* __restrict__ X, int D, co
     }
 }
 
-// Accumulates the warp's run [w0, w1) of one tile: each chunk of 32
-// positions is split by side (rows[]: the left rows, then the right ones,
-// both in position order) so that each side's sums take its rows in
-// ascending positions without per-row selects.
+// Accumulates the warp's run [w0, w1) of one tile into the sums of two
+// lists: full (Sp == nullptr): list 0 = the left positions, list 1 = the
+// right ones; delta: list 0 = the positions that moved to the left since the
+// previous iteration's cut (projections Sp, key Tp), list 1 = those that moved
+// to the right; the rest are not read.  Each chunk of 32 positions is
+// compacted by list (rows[]: list 0, then list 1, both in position order), so
+// that each list's sums take its rows in ascending positions without per-row
+// selects.
 template <bool VEC, int Q>
 __device__ __forceinline__ void sums_run(const float* __restrict__ X, int D, const uint16_t* __restrict__ Xq, int Dq,
-                                         const int32_t* __restrict__ perm, const float* __restrict__ S, int a,
-                                         uint64_t T, int pos_bits, int w0, int w1, int dbase, int* rows, float* hL,
-                                         float* lL, float* hR, float* lR, bool left_only) {
+                                         const int32_t* __restrict__ perm, const float* __restrict__ S,
+                                         const float* __restrict__ Sp, int a, uint64_t T, uint64_t Tp, int pos_bits,
+                                         int w0, int w1, int dbase, int* rows, float* hL, float* lL, float* hR,
+                                         float* lR) {
     const int lane = threadIdx.x & 31;
     // ids and projections of the next 32 positions load while this chunk's
     // rows are summed
     int next_row = 0;
-    float next_s = 0.f;
+    float next_s = 0.f, next_sp = 0.f;
     if (w0 + lane < w1) {
         next_row = perm[w0 + lane];
         next_s = S[w0 + lane];
+        if (Sp) next_sp = Sp[w0 + lane];
     }
     for (int c = w0; c < w1; c += 32) {
         const int p = c + lane;
         const int my_row = next_row;
-        const bool my_left = p < w1 && sel_key(next_s, p - a, pos_bits) < T;
+        const bool in = p < w1;
+        const bool now_left = in && sel_key(next_s, p - a, pos_bits) < T;
+        bool c0 = now_left, c1 = in && !now_left;
+        if (Sp) {
+            const bool was_left = in && sel_key(next_sp, p - a, pos_bits) < Tp;
+            c0 = now_left && !was_left;
+            c1 = in && !now_left && was_left;
+        }
         if (p + 32 < w1) {
             next_row = perm[p + 32];
             next_s = S[p + 32];
+            if (Sp) next_sp = Sp[p + 32];
         }
-        const int cnt = min(32, w1 - c);
-        const unsigned lb = __ballot_sync(0xffffffffu, my_left);
-        const int nl = __popc(lb), before = __popc(lb & ((1u << lane) - 1u));
+        const unsigned b0 = __ballot_sync(0xffffffffu, c0), b1 = __ballot_sync(0xffffffffu, c1);
+        const unsigned lt = (1u << lane) - 1u;
+        const int n0 = __popc(b0);
         __syncwarp();  // the previous chunk's reads of rows[] are done
-        if (p < w1) rows[my_left ? before : nl + lane - before] = my_row;
+        if (c0)
+            rows[__popc(b0 & lt)] = my_row;
+        else if (c1)
+            rows[n0 + __popc(b1 & lt)] = my_row;
         __syncwarp();
-        sums_side<VEC, Q>(X, D, Xq, Dq, rows, nl, dbase, hL, lL);
-        if (!left_only) sums_side<VEC, Q>(X, D, Xq, Dq, rows + nl, cnt - nl, dbase, hR, lR);
+        sums_side<VEC, Q>(X, D, Xq, Dq, rows, n0, dbase, hL, lL);
+        sums_side<VEC, Q>(X, D, Xq, Dq, rows + n0, __popc(b1), dbase, hR, lR);
     }
 }
 
@@ -901,7 +929,9 @@ __global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restri
                                                           const uint16_t* __restrict__ Xq, int Dq, int qtype,
                                                           const int* __restrict__ qflag,
                                                           const uint8_t* __restrict__ Xb,
-                                                          const int* __restrict__ bflag, int left_only) {
+                                                          const int* __restrict__ bflag,
+                                                          const float* __restrict__ Sp,
+                                                          const uint64_t* __restrict__ thrp) {
     __shared__ double red[kSumsWarps][2][128];
     __shared__ int rows[kSumsWarps][32];
     if (*status & kStatusStop) return;  // perm may hold unwritten slots
@@ -911,7 +941,7 @@ __global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restri
     const int seg = t.x, begin = t.y, end = t.z;
     const int dbase = blockIdx.y * 128;
     const int a = seg_off[seg];
-    const uint64_t T = thr[seg];
+    const uint64_t T = thr[seg], Tp = Sp ? thrp[seg] : 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per = (end - begin + kSumsWarps - 1) / kSumsWarps;
     const int w0 = begin + warp * per, w1 = min(end, w0 + per);
@@ -923,14 +953,14 @@ __global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restri
     float hL[4] = {0.f, 0.f, 0.f, 0.f}, lL[4] = {0.f, 0.f, 0.f, 0.f};
     float hR[4] = {0.f, 0.f, 0.f, 0.f}, lR[4] = {0.f, 0.f, 0.f, 0.f};
     if (q == 1)
-        sums_run<VEC, 1>(X, D, Xq, Dq, perm, S, a, T, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR, lR,
-                         left_only != 0);
+        sums_run<VEC, 1>(X, D, Xq, Dq, perm, S, Sp, a, T, Tp, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR,
+                         lR);
     else if (q == 2)
-        sums_run<VEC, 2>(X, D, Xq, Dq, perm, S, a, T, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR, lR,
-                         left_only != 0);
+        sums_run<VEC, 2>(X, D, Xq, Dq, perm, S, Sp, a, T, Tp, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR,
+                         lR);
     else
-        sums_run<VEC, 0>(X, D, Xq, Dq, perm, S, a, T, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR, lR,
-                         left_only != 0);
+        sums_run<VEC, 0>(X, D, Xq, Dq, perm, S, Sp, a, T, Tp, pos_bits, w0, w1, dbase, rows[warp], hL, lL, hR,
+                         lR);
     if (exact) {  // integer sums below 2^24 per lane and 2^31 per tile: int32 partials
         int(*ired)[2][128] = reinterpret_cast<int(*)[2][128]>(red);
 #pragma unroll
@@ -973,16 +1003,16 @@ __global__ void __launch_bounds__(32 * kSumsWarps) k1_sums(const float* __restri
 }
 
 // Centroid sums with rows staged like the projection's: a CTA takes one
-// select tile (up to kTile positions) and first lists its rows by side (the
-// left rows in ascending positions, then the right ones).  The list is staged
-// in chunks of 256 rows, a 128-byte slab of each row at a time, by cp.async
-// (double-buffered), and each thread sums 4 dims of the slab over a 1/G share
-// of the chunk's rows, left and right apart.  Per thread the rows of a side
-// come in ascending positions; the G partial sums of a dim are combined in
-// FP64 in group order.  With left_only the right rows are neither staged nor
-// summed: the right side's sum is then the segment's total minus the left's.
+// select tile (up to kTile positions) and first lists its rows (list 0 in
+// ascending positions, then list 1; the lists of sums_run: left and right, or
+// moved left and moved right).  The list is staged in chunks of 256 rows, a
+// 128-byte slab of each row at a time, by cp.async (double-buffered), and
+// each thread sums 4 dims of the slab over a 1/G share of the chunk's rows,
+// the two lists apart.  Per thread the rows of a list come in ascending
+// positions; the G partial sums of a dim are combined in group order (int32
+// for integer data, else FP64).
 constexpr int kSuThreads = 256;
-constexpr int kSuSmem = 2 * kPrRows * kPrStride + kTile * 4 + 8 * 4 + 2 * 1024 * 8;
+constexpr int kSuSmem = 2 * kPrRows * kPrStride + kTile * 4 + 16 * 4 + 2 * 1024 * 8;
 static_assert(kTile == 8 * kPrRows && kSuThreads == 256, "one warp lists each 256 positions of a tile");
 // Adds 4 dims (quad q) of one staged row to the sums (h, l).
 template <int Q>
@@ -1051,50 +1081,78 @@ template <int Q>
 __device__ __forceinline__ void sums_async_tile(const float* __restrict__ X, int D, const uint16_t* __restrict__ Xq,
                                                 int Dq, const uint8_t* __restrict__ Xb, int Db,
                                                 const int32_t* __restrict__ perm,
-                                                const float* __restrict__ S, int a, uint64_t T, int pos_bits,
-                                                int begin, int end, bool left_only, double* __restrict__ part,
-                                                int32_t* __restrict__ ipart, uint8_t* smem) {
+                                                const float* __restrict__ S, const float* __restrict__ Sp, int a,
+                                                uint64_t T, uint64_t Tp, int pos_bits, int begin, int end,
+                                                double* __restrict__ part, int32_t* __restrict__ ipart,
+                                                uint8_t* smem) {
     constexpr int SLAB = Q == 3 ? 128 : Q != 0 ? 64 : 32;  // dims per 128-byte slab
     constexpr int QUADS = SLAB / 4;                        // threads per row
     constexpr int G = kSuThreads / QUADS;                  // row groups
-    int* ids = reinterpret_cast<int*>(smem + 2 * kPrRows * kPrStride);  // [kTile] row ids, left side first
-    int* nleft = ids + kTile;                                            // [8] left rows per 256 positions
-    double* red = reinterpret_cast<double*>(nleft + 8);                  // [2][G][SLAB], G * SLAB = 1024
+    int* ids = reinterpret_cast<int*>(smem + 2 * kPrRows * kPrStride);  // [kTile] row ids, list 0 first
+    int* cnt0 = ids + kTile;                                             // [8] list-0 rows per 256 positions
+    int* cnt1 = cnt0 + 8;                                                // [8] list-1 rows
+    double* red = reinterpret_cast<double*>(cnt1 + 8);                   // [2][G][SLAB], G * SLAB = 1024
     static_assert(G * SLAB == 1024, "the combine buffer holds 2 x 1024 sums");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m = end - begin;
-    // warp w lists positions 256 w .. 256 w + 255
-    unsigned bal[8];
-    int nlw = 0;
+    // warp w lists positions 256 w .. 256 w + 255; their projections and ids
+    // load first, all in flight at once
+    float sv[8], spv[8];
+    int pv[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int p = warp * kPrRows + 32 * i + lane;
-        bal[i] = __ballot_sync(0xffffffffu, p < m && sel_key(S[begin + p], begin + p - a, pos_bits) < T);
-        nlw += __popc(bal[i]);
+        const bool in = p < m;
+        sv[i] = in ? S[begin + p] : 0.f;
+        spv[i] = in && Sp ? Sp[begin + p] : 0.f;
+        pv[i] = in ? perm[begin + p] : 0;
     }
-    if (lane == 0) nleft[warp] = nlw;
+    unsigned bal0[8], bal1[8];
+    int n0w = 0, n1w = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int p = warp * kPrRows + 32 * i + lane;
+        const bool in = p < m;
+        const bool now_left = in && sel_key(sv[i], begin + p - a, pos_bits) < T;
+        bool c0 = now_left, c1 = in && !now_left;
+        if (Sp) {
+            const bool was_left = in && sel_key(spv[i], begin + p - a, pos_bits) < Tp;
+            c0 = now_left && !was_left;
+            c1 = in && !now_left && was_left;
+        }
+        bal0[i] = __ballot_sync(0xffffffffu, c0);
+        bal1[i] = __ballot_sync(0xffffffffu, c1);
+        n0w += __popc(bal0[i]);
+        n1w += __popc(bal1[i]);
+    }
+    if (lane == 0) {
+        cnt0[warp] = n0w;
+        cnt1[warp] = n1w;
+    }
     __syncthreads();
-    int NL = 0, lb = 0;  // left rows of the tile; of the positions before this warp's
+    int NL = 0, N1 = 0, lb0 = 0, lb1 = 0;  // list sizes; list rows of the positions before this warp's
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
-        const int v = nleft[w];
-        NL += v;
-        lb += w < warp ? v : 0;
+        const int v0 = cnt0[w], v1 = cnt1[w];
+        NL += v0;
+        N1 += v1;
+        lb0 += w < warp ? v0 : 0;
+        lb1 += w < warp ? v1 : 0;
     }
+    const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const int p = warp * kPrRows + 32 * i + lane;
-        if (p < m) {
-            const int l_rank = lb + __popc(bal[i] & ((1u << lane) - 1u));  // left positions before p
-            const bool left = (bal[i] >> lane) & 1u;
-            if (left || !left_only) ids[left ? l_rank : NL + (p - l_rank)] = perm[begin + p];
-        }
-        lb += __popc(bal[i]);
+        if ((bal0[i] >> lane) & 1u)
+            ids[lb0 + __popc(bal0[i] & lt)] = pv[i];
+        else if ((bal1[i] >> lane) & 1u)
+            ids[NL + lb1 + __popc(bal1[i] & lt)] = pv[i];
+        lb0 += __popc(bal0[i]);
+        lb1 += __popc(bal1[i]);
     }
     __syncthreads();
-    const int mt = left_only ? NL : m;  // rows staged
+    const int mt = NL + N1;  // rows staged
     const int nchunk = (mt + kPrRows - 1) / kPrRows;
-    if (nchunk == 0) {  // no left rows: zero sums
+    if (nchunk == 0) {  // no rows: zero sums
         for (int d = tid; d < 2 * D; d += kSuThreads) {
             if (Q != 0)
                 ipart[d] = 0;
@@ -1119,7 +1177,7 @@ __device__ __forceinline__ void sums_async_tile(const float* __restrict__ X, int
         __syncthreads();
         const int sl = st / nchunk, c = st - sl * nchunk, d0 = sl * SLAB;
         const int cnt = min(kPrRows, mt - c * kPrRows);
-        const int nl = min(max(NL - c * kPrRows, 0), cnt);  // the chunk's left rows come first
+        const int nl = min(max(NL - c * kPrRows, 0), cnt);  // the chunk's list-0 rows come first
         const uint8_t* buf = smem + (st & 1) * (kPrRows * kPrStride);
         if (d0 + 4 * q < D) {
             int i = g;
@@ -1175,29 +1233,31 @@ __global__ void __launch_bounds__(kSuThreads) k1_sums_async(const float* __restr
                                                             const uint16_t* __restrict__ Xq, int Dq, int qtype,
                                                             const int* __restrict__ qflag,
                                                             const uint8_t* __restrict__ Xb, int Db,
-                                                            const int* __restrict__ bflag, int left_only) {
+                                                            const int* __restrict__ bflag,
+                                                            const float* __restrict__ Sp,
+                                                            const uint64_t* __restrict__ thrp) {
     extern __shared__ __align__(16) uint8_t su_smem[];
     if (*status & kStatusStop) return;  // perm may hold unwritten slots
     const int q = u8_usable(Xb, bflag) ? 3 : q16_usable(Xq, qflag) ? qtype : 0;
     const int4 t = tiles[blockIdx.x];
     const int seg = t.x, begin = t.y, end = t.z;
     const int a = seg_off[seg];
-    const uint64_t T = thr[seg];
+    const uint64_t T = thr[seg], Tp = Sp ? thrp[seg] : 0;
     // this tile's sums: [2][D] FP64, or int32 for integer data (Q != 0)
     double* part = partial + (int64_t)blockIdx.x * 2 * D;
     int32_t* ipart = reinterpret_cast<int32_t*>(partial) + (int64_t)blockIdx.x * 2 * D;
     if (q == 3)
-        sums_async_tile<3>(X, D, Xq, Dq, Xb, Db, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
-                           ipart, su_smem);
+        sums_async_tile<3>(X, D, Xq, Dq, Xb, Db, perm, S, Sp, a, T, Tp, pos_bits, begin, end, part, ipart,
+                           su_smem);
     else if (q == 1)
-        sums_async_tile<1>(X, D, Xq, Dq, Xb, Db, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
-                           ipart, su_smem);
+        sums_async_tile<1>(X, D, Xq, Dq, Xb, Db, perm, S, Sp, a, T, Tp, pos_bits, begin, end, part, ipart,
+                           su_smem);
     else if (q == 2)
-        sums_async_tile<2>(X, D, Xq, Dq, Xb, Db, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
-                           ipart, su_smem);
+        sums_async_tile<2>(X, D, Xq, Dq, Xb, Db, perm, S, Sp, a, T, Tp, pos_bits, begin, end, part, ipart,
+                           su_smem);
     else
-        sums_async_tile<0>(X, D, Xq, Dq, Xb, Db, perm, S, a, T, pos_bits, begin, end, left_only != 0, part,
-                           ipart, su_smem);
+        sums_async_tile<0>(X, D, Xq, Dq, Xb, Db, perm, S, Sp, a, T, Tp, pos_bits, begin, end, part, ipart,
+                           su_smem);
 }
 
 // s / b rounded to nearest (FP64) from inv = RN(1 / b): the FMA residual
@@ -1221,26 +1281,40 @@ __device__ __forceinline__ float mean_of_ints(long long S, int K) {
     return (float)((double)S / (double)K);
 }
 
-// c1 - c0 of one dim from integer sums (int64; segsum holds int64 totals).
-__device__ __forceinline__ void store_w_ints(long long sL, long long sR, int seg, int d, int D, int K, int m,
-                                             double* __restrict__ segsum, int left_only, float* __restrict__ W) {
-    long long* ss = reinterpret_cast<long long*>(segsum);
-    if (left_only)
-        sR = ss[(int64_t)seg * D + d] - sL;
-    else
-        ss[(int64_t)seg * D + d] = sL + sR;
+// c1 - c0 of one dim from integer sums (int64 in segsum and segleft).  Full
+// sweep: s0, s1 are the left and right sums; the segment's total and left sum
+// are kept.  Delta sweep: s0, s1 are the sums of the points that moved left
+// and right since the last cut, so left = kept left + s0 - s1.
+__device__ __forceinline__ void store_w_ints(long long s0, long long s1, int seg, int d, int D, int K, int m,
+                                             double* __restrict__ segsum, double* __restrict__ segleft, int delta,
+                                             float* __restrict__ W) {
+    long long* tot = reinterpret_cast<long long*>(segsum) + (int64_t)seg * D + d;
+    long long* lft = reinterpret_cast<long long*>(segleft) + (int64_t)seg * D + d;
+    long long sL = s0, sR = s1;
+    if (delta) {
+        sL = *lft + s0 - s1;
+        sR = *tot - sL;
+    } else {
+        *tot = sL + sR;
+    }
+    *lft = sL;
     W[(int64_t)seg * D + d] = __fsub_rn(mean_of_ints(sR, m - K), mean_of_ints(sL, K));
 }
 
-// c1 - c0 of one dim from the left and right sums (or, left_only, the left sum
-// and the segment's total): FP64 means rounded to FP32.
-__device__ __forceinline__ void store_w(double sL, double sR, int seg, int d, int D, int K, int m, double inv0,
-                                        double inv1, double* __restrict__ segsum, int left_only,
-                                        float* __restrict__ W) {
-    if (left_only)
-        sR = segsum[(int64_t)seg * D + d] - sL;
-    else
-        segsum[(int64_t)seg * D + d] = sL + sR;
+// The same from FP64 sums: FP64 means rounded to FP32.
+__device__ __forceinline__ void store_w(double s0, double s1, int seg, int d, int D, int K, int m, double inv0,
+                                        double inv1, double* __restrict__ segsum, double* __restrict__ segleft,
+                                        int delta, float* __restrict__ W) {
+    double* tot = segsum + (int64_t)seg * D + d;
+    double* lft = segleft + (int64_t)seg * D + d;
+    double sL = s0, sR = s1;
+    if (delta) {
+        sL = *lft + s0 - s1;
+        sR = *tot - sL;
+    } else {
+        *tot = sL + sR;
+    }
+    *lft = sL;
     const float c0 = (float)div_by(sL, (double)K, inv0);
     const float c1 = (float)div_by(sR, (double)(m - K), inv1);
     W[(int64_t)seg * D + d] = __fsub_rn(c1, c0);
@@ -1256,8 +1330,9 @@ template <int G>
 __global__ void __launch_bounds__(32 * G) k1_centroids(const double* __restrict__ partial,
                                                        const int32_t* __restrict__ seg_off,
                                                        const int32_t* __restrict__ seg_tile0, int D,
-                                                       double* __restrict__ segsum, int left_only,
-                                                       float* __restrict__ W, const uint16_t* __restrict__ Xq,
+                                                       double* __restrict__ segsum, double* __restrict__ segleft,
+                                                       int delta, float* __restrict__ W,
+                                                       const uint16_t* __restrict__ Xq,
                                                        const int* __restrict__ qflag,
                                                        const uint8_t* __restrict__ Xb,
                                                        const int* __restrict__ bflag) {
@@ -1292,7 +1367,7 @@ __global__ void __launch_bounds__(32 * G) k1_centroids(const double* __restrict_
                 iL += ired[q][0][lane];
                 iR += ired[q][1][lane];
             }
-            store_w_ints(iL, iR, seg, d, D, K, m, segsum, left_only, W);
+            store_w_ints(iL, iR, seg, d, D, K, m, segsum, segleft, delta, W);
         }
         return;
     }
@@ -1319,7 +1394,7 @@ __global__ void __launch_bounds__(32 * G) k1_centroids(const double* __restrict_
             sL += red[q][0][lane];
             sR += red[q][1][lane];
         }
-        store_w(sL, sR, seg, d, D, K, m, inv[0], inv[1], segsum, left_only, W);
+        store_w(sL, sR, seg, d, D, K, m, inv[0], inv[1], segsum, segleft, delta, W);
     }
 }
 
@@ -1328,8 +1403,9 @@ __global__ void __launch_bounds__(32 * G) k1_centroids(const double* __restrict_
 __global__ void __launch_bounds__(256) k1_centroids_warp(const double* __restrict__ partial,
                                                          const int32_t* __restrict__ seg_off,
                                                          const int32_t* __restrict__ seg_tile0, int nseg, int D,
-                                                         double* __restrict__ segsum, int left_only,
-                                                         float* __restrict__ W, const uint16_t* __restrict__ Xq,
+                                                         double* __restrict__ segsum, double* __restrict__ segleft,
+                                                         int delta, float* __restrict__ W,
+                                                         const uint16_t* __restrict__ Xq,
                                                          const int* __restrict__ qflag,
                                                          const uint8_t* __restrict__ Xb,
                                                          const int* __restrict__ bflag) {
@@ -1349,7 +1425,7 @@ __global__ void __launch_bounds__(256) k1_centroids_warp(const double* __restric
             iL += ip[((int64_t)t * 2 + 0) * D + d];
             iR += ip[((int64_t)t * 2 + 1) * D + d];
         }
-        store_w_ints(iL, iR, seg, d, D, K, m, segsum, left_only, W);
+        store_w_ints(iL, iR, seg, d, D, K, m, segsum, segleft, delta, W);
         return;
     }
     double inv0 = 0.0, inv1 = 0.0;
@@ -1365,14 +1441,14 @@ __global__ void __launch_bounds__(256) k1_centroids_warp(const double* __restric
         sL += partial[((int64_t)t * 2 + 0) * D + d];
         sR += partial[((int64_t)t * 2 + 1) * D + d];
     }
-    store_w(sL, sR, seg, d, D, K, m, inv0, inv1, segsum, left_only, W);
+    store_w(sL, sR, seg, d, D, K, m, inv0, inv1, segsum, segleft, delta, W);
 }
 
 template <int G>
-void launch_centroids(const LevelPlan& lp, const SplitBuffers& b, int D, int left_only, cudaStream_t s) {
+void launch_centroids(const LevelPlan& lp, const SplitBuffers& b, int D, int delta, cudaStream_t s) {
     k1_centroids<G><<<dim3(lp.nseg, (D + 31) / 32), 32 * G, 0, s>>>(b.partial, lp.seg_off, lp.seg_tile0, D,
-                                                                     b.segsum, left_only, b.W, b.Xq, b.qflag,
-                                                                     b.Xb, b.bflag);
+                                                                     b.segsum, b.segleft, delta, b.W, b.Xq,
+                                                                     b.qflag, b.Xb, b.bflag);
 }
 
 __global__ void __launch_bounds__(256) k1_part_count(const float* __restrict__ S, const int4* __restrict__ tiles,
@@ -1401,19 +1477,30 @@ __global__ void __launch_bounds__(256) k1_part_scatter(const float* __restrict__
     const int seg = t.x;
     const int a = seg_off[seg], m = seg_off[seg + 1] - a, K = m / 2;
     const uint64_t T = thr[seg];
+    // the tile's projections and ids first (all loads in flight at once)
+    constexpr int PER = kTile / 256;
+    float sv[PER];
+    int id[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int p = t.y + (int)threadIdx.x + 256 * i;
+        sv[i] = p < t.z ? S[p] : 0.f;
+        id[i] = p < t.z ? perm_in[p] : 0;
+    }
     int lb = 0;
     for (int q = seg_tile0[seg] + threadIdx.x; q < (int)blockIdx.x; q += blockDim.x) lb += tile_left[q];
     lb = block_sum(lb, warp_tot);
-    for (int base = t.y; base < t.z; base += blockDim.x) {
-        const int p = base + threadIdx.x;
-        const int isl = p < t.z && sel_key(S[p], p - a, pos_bits) < T;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int p = t.y + (int)threadIdx.x + 256 * i;
+        const int isl = p < t.z && sel_key(sv[i], p - a, pos_bits) < T;
         int tot;
         const int ex = block_excl_scan(isl, warp_tot, &tot);
         if (p < t.z) {
             const int l = lb + ex;
             const int np = isl ? l : K + (p - a - l);
             if ((isl ? np < K : np < m) && np >= 0)
-                perm_out[a + np] = perm_in[p];
+                perm_out[a + np] = id[i];
             else
                 atomicOr(status, kStatusInternal);
         }
@@ -1442,6 +1529,15 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
     }
     for (int it = 0; it <= iters; ++it) {
         const bool last = it == iters;
+        // projections and keys alternate between two buffers, so that a
+        // sweep can compare this iteration's cut with the previous one
+        SplitBuffers bi = b;
+        if (it & 1) {
+            bi.S = b.S2;
+            bi.thr = b.thr2;
+        }
+        const float* Sp = it > 0 ? ((it & 1) ? b.S : b.S2) : nullptr;
+        const uint64_t* Tp = it > 0 ? ((it & 1) ? b.thr : b.thr2) : nullptr;
         {
             LaunchScope ls("k1_project", s, rows + n * 8, 2.0 * n * D);
             SelState* st = lp.small ? nullptr : b.st;
@@ -1449,32 +1545,32 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
                 cudaFuncSetAttribute(k1_project_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, kPpSmem);
                 const int grid = std::min(lp.nsweep, 2 * sm_count());
                 k1_project_pipe<<<grid, kPrRows, kPpSmem, s>>>(X, D, perm_in, lp.sweep, lp.nsweep, lp.seg_off, b.W,
-                                                               b.S, st, b.status, b.Xq, b.Dq, b.qtype, b.qflag,
+                                                               bi.S, st, b.status, b.Xq, b.Dq, b.qtype, b.qflag,
                                                                b.Xb, b.Db, b.bflag);
             } else if (vec2)
-                k1_project<true><<<lp.nsweep, 256, 0, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S, st,
+                k1_project<true><<<lp.nsweep, 256, 0, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, bi.S, st,
                                                            b.status, b.Xq, b.Dq, b.qtype, b.qflag);
             else
-                k1_project<false><<<lp.nsweep, 256, 0, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, b.S, st,
+                k1_project<false><<<lp.nsweep, 256, 0, s>>>(X, D, perm_in, lp.sweep, lp.seg_off, b.W, bi.S, st,
                                                             b.status, b.Xq, b.Dq, b.qtype, b.qflag);
         }
         if (lp.small && lp.max_m <= kSortSelectMax) {
             LaunchScope ls("k1_select_sort", s, n * 4 + (last ? n * 8 : 0), 0);
             int32_t* out = last ? perm_out : nullptr;
             if (lp.max_m <= 32)
-                launch_select_sort<1, 1>(lp, b, perm_in, out, s);
+                launch_select_sort<1, 1>(lp, bi, perm_in, out, s);
             else if (lp.max_m <= 64)
-                launch_select_sort<2, 1>(lp, b, perm_in, out, s);
+                launch_select_sort<2, 1>(lp, bi, perm_in, out, s);
             else if (lp.max_m <= 128)
-                launch_select_sort<4, 1>(lp, b, perm_in, out, s);
+                launch_select_sort<4, 1>(lp, bi, perm_in, out, s);
             else if (lp.max_m <= 256)
-                launch_select_sort<8, 1>(lp, b, perm_in, out, s);
+                launch_select_sort<8, 1>(lp, bi, perm_in, out, s);
             else if (lp.max_m <= 512)
-                launch_select_sort<8, 2>(lp, b, perm_in, out, s);
+                launch_select_sort<8, 2>(lp, bi, perm_in, out, s);
             else if (lp.max_m <= 1024)
-                launch_select_sort<8, 4>(lp, b, perm_in, out, s);
+                launch_select_sort<8, 4>(lp, bi, perm_in, out, s);
             else
-                launch_select_sort<8, 8>(lp, b, perm_in, out, s);
+                launch_select_sort<8, 8>(lp, bi, perm_in, out, s);
             if (last) break;
         } else if (lp.small) {
             const size_t smem = (size_t)lp.max_m * sizeof(uint64_t);
@@ -1482,50 +1578,51 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
             const int nt = std::min(1024, std::max(128, (lp.max_m + 31) & ~31));
             LaunchScope ls("k1_select_small", s, n * 4 + (last ? n * 8 : 0), 0);
             cudaFuncSetAttribute(k1_select_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k1_select_small<<<lp.nseg, nt, smem, s>>>(b.S, lp.seg_off, lp.seg_tile0, lp.pos_bits, b.thr, perm_in,
+            k1_select_small<<<lp.nseg, nt, smem, s>>>(bi.S, lp.seg_off, lp.seg_tile0, lp.pos_bits, bi.thr, perm_in,
                                                       last ? perm_out : nullptr, b.status);
             if (last) break;
         } else {
             // every digit is launched; a segment whose key is known returns at once
             for (int hi = 32 + lp.pos_bits; hi > 0; hi = digit_lo(hi, lp.pos_bits)) {
                 LaunchScope ls("k1_select_pass", s, hi > lp.pos_bits ? n * 4 : 0, 0);
-                k1_select_pass<<<lp.ntiles, 256, 0, s>>>(b.S, lp.tiles, lp.seg_off, lp.seg_tile0, lp.pos_bits, hi,
-                                                         b.st, b.ghist, b.ticket, b.thr);
+                k1_select_pass<<<lp.ntiles, 256, 0, s>>>(bi.S, lp.tiles, lp.seg_off, lp.seg_tile0, lp.pos_bits, hi,
+                                                         b.st, b.ghist, b.ticket, bi.thr);
             }
             if (last) {
                 {
                     LaunchScope ls("k1_part_count", s, n * 4, 0);
-                    k1_part_count<<<lp.ntiles, 256, 0, s>>>(b.S, lp.tiles, lp.seg_off, b.thr, lp.pos_bits,
+                    k1_part_count<<<lp.ntiles, 256, 0, s>>>(bi.S, lp.tiles, lp.seg_off, bi.thr, lp.pos_bits,
                                                             b.tile_left);
                 }
                 LaunchScope ls("k1_part_scatter", s, n * 12, 0);
-                k1_part_scatter<<<lp.ntiles, 256, 0, s>>>(b.S, lp.tiles, lp.seg_off, lp.seg_tile0, b.thr,
+                k1_part_scatter<<<lp.ntiles, 256, 0, s>>>(bi.S, lp.tiles, lp.seg_off, lp.seg_tile0, bi.thr,
                                                           lp.pos_bits, b.tile_left, perm_in, perm_out, b.status);
                 break;
             }
         }
-        // the first sweep sums both sides (and so each segment's total), the
-        // later ones the left side (floor(m / 2) rows) alone
-        const int left_only = it > 0;
+        // the first sweep sums both sides (and so each segment's total); the
+        // later ones read only the points whose side changed at this cut
+        // (delta), which Lloyd's iterations make ever fewer
+        const int delta = it > 0;
         {
-            LaunchScope ls("k1_sums", s, (left_only ? rows * 0.5 : rows) + n * 8, n * D);
+            LaunchScope ls("k1_sums", s, delta ? n * 12 : rows + n * 8, n * D);
             dim3 grid(lp.ntiles, dchunks);
             // the staged sums pay off on an exact narrow copy (when the host
             // does not know, as in a captured build, they decide on the device)
             if (vec && (b.Xq || b.Xb) && (b.u8_host || b.q16_host || b.capture)) {
                 cudaFuncSetAttribute(k1_sums_async, cudaFuncAttributeMaxDynamicSharedMemorySize, kSuSmem);
-                k1_sums_async<<<lp.ntiles, kSuThreads, kSuSmem, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off,
-                                                                     b.thr, lp.pos_bits, b.partial, b.status, b.Xq,
-                                                                     b.Dq, b.qtype, b.qflag, b.Xb, b.Db, b.bflag,
-                                                                     left_only);
+                k1_sums_async<<<lp.ntiles, kSuThreads, kSuSmem, s>>>(X, D, perm_in, lp.tiles, bi.S, lp.seg_off,
+                                                                     bi.thr, lp.pos_bits, b.partial, b.status, b.Xq,
+                                                                     b.Dq, b.qtype, b.qflag, b.Xb, b.Db, b.bflag, Sp,
+                                                                     Tp);
             } else if (vec)
-                k1_sums<true><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr,
+                k1_sums<true><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, bi.S, lp.seg_off, bi.thr,
                                                                lp.pos_bits, b.partial, b.status, b.Xq, b.Dq,
-                                                               b.qtype, b.qflag, b.Xb, b.bflag, left_only);
+                                                               b.qtype, b.qflag, b.Xb, b.bflag, Sp, Tp);
             else
-                k1_sums<false><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, b.S, lp.seg_off, b.thr,
+                k1_sums<false><<<grid, 32 * kSumsWarps, 0, s>>>(X, D, perm_in, lp.tiles, bi.S, lp.seg_off, bi.thr,
                                                                 lp.pos_bits, b.partial, b.status, b.Xq, b.Dq,
-                                                                b.qtype, b.qflag, b.Xb, b.bflag, left_only);
+                                                                b.qtype, b.qflag, b.Xb, b.bflag, Sp, Tp);
         }
         {
             LaunchScope ls("k1_centroids", s, (double)lp.ntiles * 2 * D * 8 + (double)lp.nseg * D * 4, 0);
@@ -1534,12 +1631,13 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
             if (tiles <= 3) {
                 const int64_t pairs = (int64_t)lp.nseg * ((D + 31) / 32);
                 k1_centroids_warp<<<(unsigned)((pairs + 7) / 8), 256, 0, s>>>(b.partial, lp.seg_off, lp.seg_tile0,
-                                                                               lp.nseg, D, b.segsum, left_only, b.W,
+                                                                               lp.nseg, D, b.segsum, b.segleft, delta,
+                                                                               b.W,
                                                                                b.Xq, b.qflag, b.Xb, b.bflag);
             } else if (tiles <= 8)
-                launch_centroids<8>(lp, b, D, left_only, s);
+                launch_centroids<8>(lp, b, D, delta, s);
             else
-                launch_centroids<32>(lp, b, D, left_only, s);
+                launch_centroids<32>(lp, b, D, delta, s);
         }
     }
 }
