@@ -12,10 +12,14 @@
 // One CTA packs NPC nodes: node j's members N_i = G_old[i] (+ R[i]) occupy
 // tile rows j * mcap .. j * mcap + M_j - 1.  Their 16-bit rows are gathered
 // into the 128-byte-swizzled K-major layout with cp.async, one thread issues
-// the 128 x 128 x Dp Gram on the tensor cores, and in the epilogue the two
-// threads of tile row r (= tensor-memory lane r) evaluate an equal share of
-// the node's pairs {u, v}, offering each in both directions when the offer
-// beats the target's k-th entry.
+// the 128 x 128 x Dp Gram on the tensor cores, and in the epilogue each
+// node's 2 mcap threads evaluate its pairs.  A node with many pairs goes by
+// rows: the two threads of tile row r (= tensor-memory lane r, member s of
+// node j) decide the offers to that member, from every other member (half
+// each; an old member takes the new ones only), with the member's k-th entry
+// in a register and one count per target.  A node with few pairs (few new
+// members) deals its pairs {u, v} round-robin to its threads instead, each
+// pair decided in both directions.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -33,24 +37,19 @@ constexpr int kThreads = 256;  // two threads per tile row in the epilogue
 
 __device__ __forceinline__ bool lp_exact_flag(int f) { return (f & 1) == 0 && !((f & 2) && (f & 4)); }
 
-// pairs a thread evaluates per group at most: ceil of mcap (mcap - 1) / 2
-// pairs over 2 mcap threads
-__host__ __device__ inline int jt_iters(int mcap) { return (mcap - 1) / 4 + 1; }
-
-// The operand tile, reused after the product for the Gram rows (and, when
-// certifying, each thread's exact distances); then member ids, thresholds,
-// norms, errors and rounded-up norm roots, counts, the barrier, the slot.
+// The operand tile, reused after the product for the Gram rows (priv[t][r]:
+// row r's entry for member t of its node; an entry that makes an offer is
+// overwritten with the offer's distance); then member ids, thresholds, norms,
+// errors and rounded-up norm roots, counts, the barrier, the slot.
 struct JtSmem {
-    size_t tile, priv, dist, mem, thr, nrm, err, srt, cnt, bar, slot, total;
+    size_t tile, priv, mem, thr, nrm, err, srt, cnt, bar, slot, total;
 };
 __host__ __device__ inline JtSmem jt_smem(int Dp, int mcap, bool cert) {
     JtSmem L;
     L.tile = 0;
     L.priv = 0;  // the operand tile is dead once the MMA has completed
     const size_t tile = (size_t)(Dp / kKc) * kChunkBytes, pv = (size_t)mcap * kRows * 4;
-    const size_t ds = cert ? (size_t)kThreads * jt_iters(mcap) * 4 : 0;
-    L.dist = pv;
-    L.mem = tile > pv + ds ? tile : pv + ds;
+    L.mem = tile > pv ? tile : pv;
     L.thr = L.mem + kRows * 4;
     L.nrm = L.thr + kRows * 8;
     L.err = L.nrm + kRows * 4;
@@ -140,7 +139,6 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
     float* snrm = reinterpret_cast<float*>(base + L.nrm);
     float* serr = reinterpret_cast<float*>(base + L.err);  // CERT: quantisation errors
     float* srt = reinterpret_cast<float*>(base + L.srt);   // CERT: norm roots, rounded up
-    float* dist = reinterpret_cast<float*>(base + L.dist) + threadIdx.x * jt_iters(mcap);  // CERT
     int* mcount = reinterpret_cast<int*>(base + L.cnt);
     const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.slot);
@@ -275,42 +273,73 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
         }
         tc::fence_before_sync();
         __syncthreads();
-        // The pairs to evaluate: new x old (nn * no of them) and new x new
-        // (nn (nn - 1) / 2), flattened and dealt round-robin to the node's
-        // 2 * mcap threads.  Bit 2i (2i + 1) of `hit` says that the thread's
-        // i-th pair {a, b} offers b to a (a to b).
+        // Bit i of `hit`: by rows, member i is offered to member s; by pairs,
+        // the thread's (i / 2)-th pair {a, b} offers b to a (i even) or a to b.
+        // An entry of priv that makes an offer is overwritten with its
+        // distance (no other thread reads that entry).
         const int nn = j < npc ? mcount[16 + j] : 0, no = Mj - nn;
         const int P = nn * no + nn * (nn - 1) / 2;
+        const bool by_rows = 8 * P >= Mj * Mj;
         const int T = 2 * mcap, tix = 2 * s + h, base_row = j * mcap;
         const PairMap pm = pair_map(nn, no);
         uint64_t hit = 0;
-        for (int p = tix, i = 0; p < P; p += T, ++i) {
-            int a, b;
-            pm.decode(p, a, b);
-            const uint32_t ua = (uint32_t)mem[base_row + a], ub = (uint32_t)mem[base_row + b];
-            if (ua == ub) continue;
-            float d = __fadd_rn(__fsub_rn(__fadd_rn(snrm[base_row + a], snrm[base_row + b]),
-                                          __fmul_rn(2.f, priv[b * kRows + base_row + a])), 0.f);
-            const uint64_t ta = thr[base_row + a], tb = thr[base_row + b];
-            if (CERT) {
-                const float cD = (16.f * Dp + 8.f) * 5.9604644775390625e-8f;  // 2^-24
-                const float sn = __fadd_ru(srt[base_row + a], srt[base_row + b]);
-                const float eps = __fadd_ru(__fmul_ru(cD, __fmul_ru(sn, sn)), __fmul_ru(1.1920928955078125e-7f, fabsf(d)));
-                const float lo = __fsub_rd(d, eps);
-                float lb = 0.f;
-                if (lo > 0.f) {
-                    const float root = __fsub_rd(__fsub_rd(__fsqrt_rd(lo), serr[base_row + a]), serr[base_row + b]);
-                    if (root > 0.f) lb = __fmul_rd(root, root);
+        const uint32_t ua = mine ? (uint32_t)mem[r] : 0u;
+        if (by_rows && mine) {
+            const uint64_t ta = thr[r];
+            const float na = snrm[r];
+            const int bend = s < nn ? Mj : nn;
+            for (int b = h; b < bend; b += 2) {
+                const uint32_t ub = (uint32_t)mem[base_row + b];
+                if (b == s || ub == ua) continue;
+                float d = __fadd_rn(__fsub_rn(__fadd_rn(na, snrm[base_row + b]), __fmul_rn(2.f, priv[b * kRows + r])),
+                                    0.f);
+                if (CERT) {
+                    const float cD = (16.f * Dp + 8.f) * 5.9604644775390625e-8f;  // 2^-24
+                    const float sn = __fadd_ru(srt[r], srt[base_row + b]);
+                    const float eps = __fadd_ru(__fmul_ru(cD, __fmul_ru(sn, sn)), __fmul_ru(1.1920928955078125e-7f, fabsf(d)));
+                    const float lo = __fsub_rd(d, eps);
+                    float lb = 0.f;
+                    if (lo > 0.f) {
+                        const float root = __fsub_rd(__fsub_rd(__fsqrt_rd(lo), serr[r]), serr[base_row + b]);
+                        if (root > 0.f) lb = __fmul_rd(root, root);
+                    }
+                    // an empty slot's key accepts everything
+                    if (ta != kEmptyKey && lb > key_dist(ta)) continue;
+                    d = canon_dist(X + (int64_t)ua * D, X + (int64_t)ub * D, D, vec);
                 }
-                // an empty slot's key accepts everything
-                const bool na = ta == kEmptyKey || !(lb > key_dist(ta));
-                const bool nb = tb == kEmptyKey || !(lb > key_dist(tb));
-                if (!na && !nb) continue;
-                d = canon_dist(X + (int64_t)ua * D, X + (int64_t)ub * D, D, vec);
-                dist[i] = d;
+                if (make_key(d, ub) < ta) {
+                    hit |= 1ull << b;
+                    priv[b * kRows + r] = d;
+                }
             }
-            const bool oa = make_key(d, ub) < ta, ob = make_key(d, ua) < tb;
-            hit |= ((uint64_t)oa << (2 * i)) | ((uint64_t)ob << (2 * i + 1));
+        } else if (!by_rows) {
+            for (int p = tix, i = 0; p < P; p += T, ++i) {
+                int a, b;
+                pm.decode(p, a, b);
+                const uint32_t pa = (uint32_t)mem[base_row + a], pb = (uint32_t)mem[base_row + b];
+                if (pa == pb) continue;
+                float d = __fadd_rn(__fsub_rn(__fadd_rn(snrm[base_row + a], snrm[base_row + b]),
+                                              __fmul_rn(2.f, priv[a * kRows + base_row + b])), 0.f);
+                const uint64_t ta = thr[base_row + a], tb = thr[base_row + b];
+                if (CERT) {
+                    const float cD = (16.f * Dp + 8.f) * 5.9604644775390625e-8f;  // 2^-24
+                    const float sn = __fadd_ru(srt[base_row + a], srt[base_row + b]);
+                    const float eps = __fadd_ru(__fmul_ru(cD, __fmul_ru(sn, sn)), __fmul_ru(1.1920928955078125e-7f, fabsf(d)));
+                    const float lo = __fsub_rd(d, eps);
+                    float lb = 0.f;
+                    if (lo > 0.f) {
+                        const float root = __fsub_rd(__fsub_rd(__fsqrt_rd(lo), serr[base_row + a]), serr[base_row + b]);
+                        if (root > 0.f) lb = __fmul_rd(root, root);
+                    }
+                    const bool na = ta == kEmptyKey || !(lb > key_dist(ta));
+                    const bool nb = tb == kEmptyKey || !(lb > key_dist(tb));
+                    if (!na && !nb) continue;
+                    d = canon_dist(X + (int64_t)pa * D, X + (int64_t)pb * D, D, vec);
+                }
+                const bool oa = make_key(d, pb) < ta, ob = make_key(d, pa) < tb;
+                if (oa || ob) priv[a * kRows + base_row + b] = d;
+                hit |= ((uint64_t)oa << (2 * i)) | ((uint64_t)ob << (2 * i + 1));
+            }
         }
         // one slot range per warp, then the offers themselves
         const int cnt = __popcll(hit);
@@ -329,20 +358,29 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
             hit = 0;
         }
         uint32_t w = at + x - cnt;
-        while (hit != 0) {
-            const int bit = __ffsll((long long)hit) - 1;
-            hit &= hit - 1;
-            int a, b;
-            pm.decode(tix + (bit >> 1) * T, a, b);
-            const uint32_t ua = (uint32_t)mem[base_row + a], ub = (uint32_t)mem[base_row + b];
-            const float d = CERT ? dist[bit >> 1]
-                                 : __fadd_rn(__fsub_rn(__fadd_rn(snrm[base_row + a], snrm[base_row + b]),
-                                                       __fmul_rn(2.f, priv[b * kRows + base_row + a])), 0.f);
-            const uint32_t tgt = (bit & 1) ? ub : ua;
-            ptgt[w] = tgt;
-            pkey[w] = make_key(d, (bit & 1) ? ua : ub);
-            ++w;
-            atomicAdd(&pcnt[tgt], 1);
+        if (by_rows) {
+            if (hit) atomicAdd(&pcnt[ua], cnt);  // one count per target and thread
+            while (hit != 0) {
+                const int b = __ffsll((long long)hit) - 1;
+                hit &= hit - 1;
+                ptgt[w] = ua;
+                pkey[w] = make_key(priv[b * kRows + r], (uint32_t)mem[base_row + b]);
+                ++w;
+            }
+        } else {
+            while (hit != 0) {
+                const int bit = __ffsll((long long)hit) - 1;
+                hit &= hit - 1;
+                int a, b;
+                pm.decode(tix + (bit >> 1) * T, a, b);
+                const uint32_t pa = (uint32_t)mem[base_row + a], pb = (uint32_t)mem[base_row + b];
+                const float d = priv[a * kRows + base_row + b];
+                const uint32_t tgt = (bit & 1) ? pb : pa;
+                ptgt[w] = tgt;
+                pkey[w] = make_key(d, (bit & 1) ? pa : pb);
+                ++w;
+                atomicAdd(&pcnt[tgt], 1);
+            }
         }
         // all tensor-memory reads and shared-memory uses of this group done
         tc::fence_before_sync();
@@ -360,7 +398,7 @@ bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev
                     const int* notexact, bool bf16, cudaStream_t s, bool cert, const float* X) {
     const int Dp = lp_dim(D);
     const int mcap = ((rev ? 2 * k : k) + 7) & ~7;
-    if (Dp / kKc > 4 || mcap > kRows) return false;
+    if (Dp / kKc > 4 || mcap > 64) return false;  // a 64-bit mask of offers per tile row
     if (cert && (!X || !b.qerr)) return false;
     const int npc = kRows / mcap;
     const JtSmem L = jt_smem(Dp, mcap, cert);
