@@ -145,8 +145,17 @@ __host__ __device__ inline TcSmem tc_smem(int Dp, int MT) {
     const int smax = MT == 1 ? 4 : 2;
     L.stages = nk < smax ? nk : smax;
     L.stage_off = 0;
-    L.dt_off = (size_t)L.stages * kStageBytes * MT;
-    L.bar_off = L.dt_off + (size_t)kTcRows * (kTcRows * MT + 1) * 4;
+    const size_t stages = (size_t)L.stages * kStageBytes * MT;
+    if (MT == 1) {
+        // the d^ rows of half a tile at a time, over the stages (dead once
+        // the product is done): a smaller footprint, more CTAs per SM
+        L.dt_off = 0;
+        const size_t dt = (size_t)(kTcRows / 2) * (kTcRows + 1) * 4;
+        L.bar_off = ((stages > dt ? stages : dt) + 15) & ~(size_t)15;
+    } else {
+        L.dt_off = stages;
+        L.bar_off = L.dt_off + (size_t)kTcRows * (kTcRows * MT + 1) * 4;
+    }
     L.misc_off = L.bar_off + (size_t)(2 * L.stages + 1) * 8;
     L.scratch_off = L.misc_off + 16 + 4 * (size_t)kTcRows * MT * 4 + 16;
     L.total = L.scratch_off + (kTcThreads / 32) * 32 * 8;
@@ -305,10 +314,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
     const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     constexpr int NC = RW / 32;
     uint64_t* wscratch = reinterpret_cast<uint64_t*>(base + L.scratch_off) + warp * 32;
-    for (int t = 0; t < MT; ++t) {
-    // ---- this tile's d^ rows: thread = TMEM lane = row 128 t + warp * 32 + lane
-    {
-        const int rl = warp * 32 + lane, R = t * kTcRows + rl;
+    // Two phases: the two halves of the one row tile (MT = 1), or the two row
+    // tiles (MT = 2); dt holds the phase's d^ rows.  With MT = 1 dt lies over
+    // the operand stages, which the completed product has read through the
+    // async proxy.
+    if (MT == 1) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    for (int ph = 0; ph < 2; ++ph) {
+    const int t = MT == 1 ? 0 : ph;              // row tile
+    const int r0 = MT == 1 ? ph * (kTcRows / 2) : 0;  // the phase's first row in the tile
+    const int pr = MT == 1 ? kTcRows / 2 : kTcRows;   // rows per phase
+    // ---- the phase's d^ rows: thread = TMEM lane = row 128 t + warp * 32 + lane
+    if (MT != 1 || (warp >> 1) == ph) {
+        const int rl = warp * 32 + lane, R = t * kTcRows + rl, rd = rl - r0;
 #pragma unroll 1
         for (int cc = 0; cc < RW / 32; ++cc) {
             float v[32];
@@ -316,16 +333,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int col = cc * 32 + j;
-                dt[rl * DTS + col] = __fsub_rn(__fadd_rn(snrm[R], snrm[col]), __fmul_rn(2.f, v[j]));
+                dt[rd * DTS + col] = __fsub_rn(__fadd_rn(snrm[R], snrm[col]), __fmul_rn(2.f, v[j]));
             }
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (t == MT - 1 && warp == 0) tc::tmem_dealloc(tmem, kCols);
-    const int rows_t = min(kTcRows, m - t * kTcRows);
-    for (int r = warp; r < rows_t; r += kTcThreads / 32) {
-        const int R = t * kTcRows + r;  // the row in the leaf; r: its d^ row
+    if (ph == 1 && warp == 0) tc::tmem_dealloc(tmem, kCols);
+    const int rows_t = min(r0 + pr, min(kTcRows, m - t * kTcRows));
+    for (int r = r0 + warp; r < rows_t; r += kTcThreads / 32) {
+        const int R = t * kTcRows + r;  // the row in the leaf; rd: its d^ row
+        const int rd = r - r0;
         const int gi = sid[R];
         uint64_t* grow = G + (int64_t)gi * k;
         uint64_t old[NSG];
@@ -339,7 +357,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
 #pragma unroll
             for (int s = 0; s < NC; ++s) {
                 const int c = lane + 32 * s;
-                cand[s] = (c < m && c != R) ? make_key(__fadd_rn(dt[r * DTS + c], 0.f), (uint32_t)sid[c])
+                cand[s] = (c < m && c != R) ? make_key(__fadd_rn(dt[rd * DTS + c], 0.f), (uint32_t)sid[c])
                                             : kEmptyKey;
             }
             if (NSG == 1) {
@@ -382,7 +400,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
                     const int c = lane + 32 * s;
                     bool keep = c < m && c != R;
                     if (keep) {
-                        const float a = dt[r * DTS + c];
+                        const float a = dt[rd * DTS + c];
                         const float sn = __fadd_ru(srt[R], srt[c]);
                         const float eps = __fadd_ru(__fmul_ru(cD, __fmul_ru(sn, sn)), __fmul_ru(1.1920928955078125e-7f, fabsf(a)));
                         const float lo = __fsub_rd(a, eps);
@@ -423,7 +441,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
 #pragma unroll
             for (int s = 0; s < NC; ++s) {
                 const int c = lane + 32 * s;
-                apx[s] = (c < m && c != R) ? make_key(__fadd_rn(dt[r * DTS + c], 0.f), (uint32_t)sid[c])
+                apx[s] = (c < m && c != R) ? make_key(__fadd_rn(dt[rd * DTS + c], 0.f), (uint32_t)sid[c])
                                            : kEmptyKey;
             }
             sort_regs<NC>(apx);
@@ -490,7 +508,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
         for (int s = 0; s < NSG; ++s)
             if (lane + 32 * s < k) grow[lane + 32 * s] = res[s];
     }
-    __syncthreads();  // the next tile's d^ rows overwrite dt
+    __syncthreads();  // the next phase's d^ rows overwrite dt
     }
 }
 
