@@ -496,6 +496,8 @@ struct BuildLayout {
     // byte copy for the tree sweeps
     uint8_t* Xb = nullptr;
     int* bflag = nullptr;
+    // leaves of the last tree passes, for the join ([npass][n])
+    int32_t* lid = nullptr;
 };
 
 int byte_dim(int D) { return (D + 15) & ~15; }
@@ -561,6 +563,12 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.sb.Dq = lp_dim(D);
         b.sb.qtype = a.p.precision == KNNG_BF16 ? 1 : 2;
         b.sb.qflag = b.notexact;
+    }
+    if (tree && join) {
+        const int np = std::min(a.p.tree_passes, kMaxLeafPasses);
+        b.lid = ws.take<int32_t>((size_t)n * kMaxLeafPasses);
+        b.jb.leafid = b.lid;
+        b.jb.npass = np;
     }
     if (tree) {
         b.Xb = ws.take<uint8_t>((size_t)n * byte_dim(D));
@@ -700,6 +708,8 @@ void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& t
                                   bf16, b.G, b.status, b.notexact, s);
         }
         if (!done) launch_leaf_fp32(X, a.D, perm, leaf_off, nleaf, tp.max_leaf, k, b.G, b.status, s);
+        const int slot = pass - (a.p.tree_passes - b.jb.npass);
+        if (b.lid && slot >= 0) launch_leaf_ids(perm, leaf_off, nleaf, n, slot, b.lid, s);
     }
     run_refine(X, n, a.D, k, a.p.join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, b.jb, b.nodes_per_chunk,
                a.p.refine_rounds, b.status, s);

@@ -681,6 +681,18 @@ __global__ void __launch_bounds__(256) k4_merge(uint64_t* __restrict__ Gnew, con
     }
 }
 
+// One warp per leaf: slot `slot` of point perm[p]'s leaf ids = leaf, for the
+// leaf's positions p.
+__global__ void __launch_bounds__(256) k_leaf_ids(const int32_t* __restrict__ perm,
+                                                  const int32_t* __restrict__ leaf_off, int nleaf, int slot,
+                                                  int32_t* __restrict__ lid) {
+    const int lane = threadIdx.x & 31;
+    for (int l = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); l < nleaf;
+         l += (int)((gridDim.x * (int64_t)blockDim.x) >> 5))
+        for (int p = leaf_off[l] + lane; p < leaf_off[l + 1]; p += 32)
+            lid[(int64_t)perm[p] * kMaxLeafPasses + slot] = l;
+}
+
 inline int grid_for(int64_t count, int block) {
     int64_t g = (count + block - 1) / block;
     if (g > 152 * 32) g = 152 * 32;
@@ -701,6 +713,13 @@ void launch_scan(const int32_t* cnt, int32_t* off, int64_t n, int32_t* tmp, cuda
     k_scan_partial<<<nb, kScanBlock, 0, s>>>(cnt, n, tmp);
     k_scan_blocks<<<1, kScanBlock, 0, s>>>(tmp, nb);
     k_scan_final<<<nb, kScanBlock, 0, s>>>(cnt, n, tmp, off);
+}
+
+void launch_leaf_ids(const int32_t* perm, const int32_t* leaf_off, int nleaf, int64_t n, int slot, int32_t* lid,
+                     cudaStream_t s) {
+    if (nleaf <= 0) return;
+    LaunchScope ls("k_leaf_ids", s, n * 8.0 + nleaf * 4.0, 0);
+    k_leaf_ids<<<grid_for((int64_t)nleaf * 32, 256), 256, 0, s>>>(perm, leaf_off, nleaf, slot, lid);
 }
 
 void launch_fill_empty(uint64_t* G, int64_t count, cudaStream_t s) {

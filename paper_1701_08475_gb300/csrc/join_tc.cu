@@ -42,7 +42,7 @@ __device__ __forceinline__ bool lp_exact_flag(int f) { return (f & 1) == 0 && !(
 // overwritten with the offer's distance); then member ids, thresholds, norms,
 // errors and rounded-up norm roots, counts, the barrier, the slot.
 struct JtSmem {
-    size_t tile, priv, mem, thr, nrm, err, srt, cnt, bar, slot, total;
+    size_t tile, priv, mem, thr, nrm, err, srt, lid, cnt, bar, slot, total;
 };
 __host__ __device__ inline JtSmem jt_smem(int Dp, int mcap, bool cert) {
     JtSmem L;
@@ -54,7 +54,8 @@ __host__ __device__ inline JtSmem jt_smem(int Dp, int mcap, bool cert) {
     L.nrm = L.thr + kRows * 8;
     L.err = L.nrm + kRows * 4;
     L.srt = L.err + (cert ? kRows * 4 : 0);
-    L.cnt = L.srt + (cert ? kRows * 4 : 0);
+    L.lid = L.srt + (cert ? kRows * 4 : 0);
+    L.cnt = L.lid + kRows * 16;
     L.bar = L.cnt + 32 * 4;  // member counts, then new-member counts
     L.slot = L.bar + 8;
     L.total = L.slot + 8;
@@ -104,6 +105,13 @@ __device__ __forceinline__ PairMap pair_map(int nn, int no) {
     return m;
 }
 
+// Did tile rows x and y share a leaf in one of the remembered tree passes?
+__device__ __forceinline__ bool leaf_mates(const int4& a, const int4& b, int npass) {
+    static_assert(kMaxLeafPasses == 4, "one int4 of leaf ids per point");
+    return (npass > 0 && a.x == b.x) || (npass > 1 && a.y == b.y) || (npass > 2 && a.z == b.z) ||
+           (npass > 3 && a.w == b.w);
+}
+
 // Persistent: CTA b takes node groups b, b + gridDim.x, ...; tensor memory
 // and the barrier are set up once.
 //
@@ -127,7 +135,8 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                                                          const int* __restrict__ notexact, bool bf16,
                                                          const float* __restrict__ X, int D,
                                                          const float* __restrict__ qerr,
-                                                         const int32_t* __restrict__ count_dev) {
+                                                         const int32_t* __restrict__ count_dev,
+                                                         const int32_t* __restrict__ leafid, int npass) {
     extern __shared__ uint8_t smem_raw[];
     if ((*status & kStatusStop) || (!CERT && !lp_exact_flag(*notexact))) return;
     if (count_dev && (int64_t)*count_dev < node1) node1 = *count_dev;
@@ -140,6 +149,7 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
     float* serr = reinterpret_cast<float*>(base + L.err);  // CERT: quantisation errors
     float* srt = reinterpret_cast<float*>(base + L.srt);   // CERT: norm roots, rounded up
     int* mcount = reinterpret_cast<int*>(base + L.cnt);
+    int4* slid = reinterpret_cast<int4*>(base + L.lid);  // [kRows] the members' leaves (npass slots)
     const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.slot);
     const uint32_t done = tc::smem_addr(base + L.bar);
@@ -222,6 +232,8 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
             const int u = mem[r];
             thr[r] = u >= 0 ? Gold[(int64_t)u * k + k - 1] : 0ull;
             snrm[r] = u >= 0 ? nrm[u] : 0.f;
+            if (npass > 0)
+                slid[r] = u >= 0 ? __ldg(reinterpret_cast<const int4*>(leafid) + u) : make_int4(-1 - r, -1 - r, -1 - r, -1 - r);
             if (CERT) {
                 serr[r] = u >= 0 ? qerr[u] : 0.f;
                 srt[r] = u >= 0 ? __fsqrt_ru(nrm[u]) : 0.f;
@@ -288,6 +300,7 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
             const uint64_t ta = thr[r];
             const float na = snrm[r];
             const int bend = s < nn ? Mj : nn;
+            const int4 la = slid[r];
             for (int b = h; b < bend; b += 2) {
                 const uint32_t ub = (uint32_t)mem[base_row + b];
                 if (b == s || ub == ua) continue;
@@ -307,7 +320,8 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                     if (ta != kEmptyKey && lb > key_dist(ta)) continue;
                     d = canon_dist(X + (int64_t)ua * D, X + (int64_t)ub * D, D, vec);
                 }
-                if (make_key(d, ub) < ta) {
+                // leaf-mates were offered to each other in the leaf stage
+                if (make_key(d, ub) < ta && !leaf_mates(la, slid[base_row + b], npass)) {
                     hit |= 1ull << b;
                     priv[b * kRows + r] = d;
                 }
@@ -336,7 +350,8 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                     if (!na && !nb) continue;
                     d = canon_dist(X + (int64_t)pa * D, X + (int64_t)pb * D, D, vec);
                 }
-                const bool oa = make_key(d, pb) < ta, ob = make_key(d, pa) < tb;
+                bool oa = make_key(d, pb) < ta, ob = make_key(d, pa) < tb;
+                if ((oa || ob) && leaf_mates(slid[base_row + a], slid[base_row + b], npass)) oa = ob = false;
                 if (oa || ob) priv[a * kRows + base_row + b] = d;
                 hit |= ((uint64_t)oa << (2 * i)) | ((uint64_t)ob << (2 * i + 1));
             }
@@ -419,13 +434,14 @@ bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev
         cudaFuncSetAttribute(k5_join_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k5_join_tc<true><<<grid, kThreads, smem, s>>>(Xq, Dp, nrm, k, rev ? 1 : 0, mcap, npc, Gold, R, b.list, b.fnew,
                                                       b.rnew, node0, node1, b.counter, b.cap, b.ptgt, b.pkey, b.pcnt,
-                                                      status, notexact, bf16, X, D, b.qerr, b.count_dev);
+                                                      status, notexact, bf16, X, D, b.qerr, b.count_dev, b.leafid,
+                                                      b.npass);
     } else {
         cudaFuncSetAttribute(k5_join_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k5_join_tc<false><<<grid, kThreads, smem, s>>>(Xq, Dp, nrm, k, rev ? 1 : 0, mcap, npc, Gold, R, b.list,
                                                        b.fnew, b.rnew, node0, node1, b.counter, b.cap, b.ptgt, b.pkey,
                                                        b.pcnt, status, notexact, bf16, nullptr, 0, nullptr,
-                                                       b.count_dev);
+                                                       b.count_dev, b.leafid, b.npass);
     }
     return true;
 }

@@ -163,7 +163,20 @@ struct JoinBuffers {
     const float* qnrm = nullptr;
     const float* qerr = nullptr;
     const int* notexact = nullptr;
+    // the leaf of every point in the build's last tree passes ([n][4], slots
+    // 0 .. npass - 1 used; NULL: none).  Two points that shared a leaf were compared there, and
+    // each was offered to the other's list; lists only improve, so offering
+    // that pair again could not change either list, and the join skips it.
+    const int32_t* leafid = nullptr;
+    int npass = 0;
 };
+
+constexpr int kMaxLeafPasses = 4;  // tree passes whose leaves the join remembers
+
+// lid[perm[p] * kMaxLeafPasses + slot] = the leaf of position p (leaf_off:
+// nleaf + 1 offsets).
+void launch_leaf_ids(const int32_t* perm, const int32_t* leaf_off, int nleaf, int64_t n, int slot, int32_t* lid,
+                     cudaStream_t s);
 
 // The tensor-core local join of the nodes at positions [node0, node1) of
 // b.list (of all nodes when it is NULL); false (nothing launched) when the
