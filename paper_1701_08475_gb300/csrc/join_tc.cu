@@ -105,13 +105,6 @@ __device__ __forceinline__ PairMap pair_map(int nn, int no) {
     return m;
 }
 
-// Did tile rows x and y share a leaf in one of the remembered tree passes?
-__device__ __forceinline__ bool leaf_mates(const int4& a, const int4& b, int npass) {
-    static_assert(kMaxLeafPasses == 4, "one int4 of leaf ids per point");
-    return (npass > 0 && a.x == b.x) || (npass > 1 && a.y == b.y) || (npass > 2 && a.z == b.z) ||
-           (npass > 3 && a.w == b.w);
-}
-
 // Persistent: CTA b takes node groups b, b + gridDim.x, ...; tensor memory
 // and the barrier are set up once.
 //

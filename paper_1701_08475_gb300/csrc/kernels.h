@@ -173,6 +173,13 @@ struct JoinBuffers {
 
 constexpr int kMaxLeafPasses = 4;  // tree passes whose leaves the join remembers
 
+// Did two points with leaf ids a and b (npass slots used) share a leaf?
+__device__ __forceinline__ bool leaf_mates(const int4& a, const int4& b, int npass) {
+    static_assert(kMaxLeafPasses == 4, "one int4 of leaf ids per point");
+    return (npass > 0 && a.x == b.x) || (npass > 1 && a.y == b.y) || (npass > 2 && a.z == b.z) ||
+           (npass > 3 && a.w == b.w);
+}
+
 // lid[perm[p] * kMaxLeafPasses + slot] = the leaf of position p (leaf_off:
 // nleaf + 1 offsets).
 void launch_leaf_ids(const int32_t* perm, const int32_t* leaf_off, int nleaf, int64_t n, int slot, int32_t* lid,
