@@ -796,6 +796,93 @@ __global__ void __launch_bounds__(256) k1_select_pass(const float* __restrict__ 
     }
 }
 
+// Large segments, after the value digits: when the selected value v has ties
+// (krem > 0: the key is the krem-th of the keys with value v, in position
+// order), one pass finds its position.  Every tile counts its keys with value
+// v; the last tile of the segment to finish (ticket) finds the tile that holds
+// the krem-th of them from the counts, in tile order, and the position inside
+// that tile by ordered ballots.  A segment whose key is known returns at once.
+__global__ void __launch_bounds__(256) k1_select_pos(const float* __restrict__ S, const int4* __restrict__ tiles,
+                                                     const int32_t* __restrict__ seg_off,
+                                                     const int32_t* __restrict__ seg_tile0, int pos_bits,
+                                                     SelState* __restrict__ st, int32_t* __restrict__ tcount,
+                                                     uint32_t* __restrict__ ticket, uint64_t* __restrict__ thr) {
+    __shared__ int warp_tot[32];
+    __shared__ int sh_last, sh_tile, sh_before;
+    const int4 t = tiles[blockIdx.x];
+    const int seg = t.x, begin = t.y, end = t.z;
+    if (st[seg].done) return;
+    const int a = seg_off[seg];
+    const uint32_t v = (uint32_t)(st[seg].prefix >> pos_bits);
+    constexpr int PER = kTile / 256;
+    int c = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int p = begin + (int)threadIdx.x + 256 * i;
+        c += (p < end && ord32(S[p]) == v) ? 1 : 0;
+    }
+    c = block_sum(c, warp_tot);
+    if (threadIdx.x == 0) tcount[blockIdx.x] = c;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t ntile = (uint32_t)(seg_tile0[seg + 1] - seg_tile0[seg]);
+        sh_last = atomicAdd(&ticket[seg], 1u) == ntile - 1u;
+    }
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    const int krem = (int)st[seg].krem;
+    const int t0 = seg_tile0[seg], t1 = seg_tile0[seg + 1];
+    // the tile holding the krem-th tied key: warp 0 scans the counts in order
+    if (threadIdx.x == 0) sh_tile = -1;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int run = 0;
+        for (int q0 = t0; q0 < t1; q0 += 32) {
+            const int q = q0 + lane;
+            const int cq = q < t1 ? tcount[q] : 0;
+            int incl = cq;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int excl = run + incl - cq;
+            const unsigned hitb = __ballot_sync(0xffffffffu, q < t1 && excl <= krem && krem < excl + cq);
+            if (hitb) {
+                const int src = __ffs(hitb) - 1;
+                if (lane == src) {
+                    sh_tile = q;
+                    sh_before = excl;
+                }
+                break;
+            }
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+    __syncthreads();
+    if (sh_tile < 0) {  // cannot happen (value v has more than krem keys); the cut then reports it
+        if (threadIdx.x == 0) ticket[seg] = 0;
+        return;
+    }
+    const int4 tt = tiles[sh_tile];
+    int want = krem - sh_before;  // among the tile's tied keys, in position order
+    for (int base = tt.y; base < tt.z; base += 256) {
+        const int p = base + (int)threadIdx.x;
+        const int tied = (p < tt.z && ord32(S[p]) == v) ? 1 : 0;
+        int tot;
+        const int ex = block_excl_scan(tied, warp_tot, &tot);
+        if (tied && ex == want) {
+            thr[seg] = ((uint64_t)v << pos_bits) | (uint32_t)(p - a);
+            st[seg].done = 1;
+        }
+        want -= tot;
+        if (want < 0) break;  // uniform: tot is the block's
+    }
+    if (threadIdx.x == 0) ticket[seg] = 0;
+}
+
 // FP64 sums of the left and right points of each tile, 128 dims per CTA
 // (blockIdx.y).  Warp w owns a contiguous run of the tile's positions; order:
 // per warp ascending positions, then warps 0..15, then tiles.
@@ -1582,11 +1669,17 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
                                                       last ? perm_out : nullptr, b.status);
             if (last) break;
         } else {
-            // every digit is launched; a segment whose key is known returns at once
-            for (int hi = 32 + lp.pos_bits; hi > 0; hi = digit_lo(hi, lp.pos_bits)) {
-                LaunchScope ls("k1_select_pass", s, hi > lp.pos_bits ? n * 4 : 0, 0);
+            // every value digit is launched, then the position pass; a
+            // segment whose key is known returns at once
+            for (int hi = 32 + lp.pos_bits; hi > lp.pos_bits; hi = digit_lo(hi, lp.pos_bits)) {
+                LaunchScope ls("k1_select_pass", s, n * 4, 0);
                 k1_select_pass<<<lp.ntiles, 256, 0, s>>>(bi.S, lp.tiles, lp.seg_off, lp.seg_tile0, lp.pos_bits, hi,
                                                          b.st, b.ghist, b.ticket, bi.thr);
+            }
+            {
+                LaunchScope ls("k1_select_pos", s, n * 4, 0);
+                k1_select_pos<<<lp.ntiles, 256, 0, s>>>(bi.S, lp.tiles, lp.seg_off, lp.seg_tile0, lp.pos_bits, b.st,
+                                                        b.tile_left, b.ticket, bi.thr);
             }
             if (last) {
                 {
