@@ -141,7 +141,9 @@ KNNG_API int knng_build_batched(int n_inst, const knng_instance *inst, const knn
  * Recording makes no host reads of the data: every choice the host would make
  * from it (the join kind, the chunk sizes) is made on the device instead, and
  * the result equals knng_build_ex's bit for bit.
- *   knng_plan_create: validates, allocates, records; *out_plan is NULL on error.
+ *   knng_plan_create: validates, synchronizes `stream` (so that inputs queued
+ *                     on it are ready), allocates, records; *out_plan is NULL
+ *                     on error.
  *   knng_plan_launch: enqueues one replay on `stream`.
  *   knng_plan_check:  waits for `stream`, then reports the last replay's
  *                     device status (KNNG_EINVAL for non-finite data, ...).

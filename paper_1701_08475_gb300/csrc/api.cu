@@ -884,7 +884,8 @@ int knng_plan_create(const float* data, int64_t n, int D, const knng_params* p, 
         if (!out_ids || !out_dists) fail(KNNG_EINVAL, "output pointer is NULL");
         if (!is_device_ptr(data) || !is_device_ptr(out_ids) || !is_device_ptr(out_dists))
             fail(KNNG_EINVAL, "a recorded build needs device buffers (data and outputs)");
-        cudaStream_t s = (cudaStream_t)stream;
+        // work the caller queued on `stream` (its inputs) completes first
+        cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
         std::unique_ptr<knng_plan> pl(new knng_plan());
         pl->a = Args{n, D, *p};
         // one chunk per round when the worst case fits 48 GB: no host reads
@@ -931,7 +932,6 @@ int knng_plan_create(const float* data, int64_t n, int D, const knng_params* p, 
         stats_set(stats_were);
         cuda_check(e, "stream capture");
         cuda_check(cudaGraphInstantiate(&pl->exec, pl->graph, 0), "graph instantiation");
-        (void)s;
         *out_plan = pl.release();
     });
 }
