@@ -58,6 +58,7 @@ def _bind(lib):
         "orc_refine_round": (i32, [P, i64, i32, i32, i32, P, P]),
         "orc_build": (i32, [P, i64, i32, i32, i32, i32, i32, i32, i32, u64, P, P]),
         "orc_recall": (i32, [P, P, P, P, P, i64, i32, P, P]),
+        "orc_search": (i32, [P, i64, i32, P, i32, P, i64, P, i32, i32, i32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -238,3 +239,19 @@ def recall(ids, dists, gt_ids, gt_d, sample):
     _load().orc_recall(_p(ids), _p(dists), _p(gt_ids), _p(gt_d), _p(sample),
                        len(sample), k, ctypes.byref(ri), ctypes.byref(rt))
     return ri.value, rt.value
+
+
+def search(X, G, Q, S, t0, ks):
+    """Enhanced hill-climbing search (Sec. 3.2, Alg. 2) of queries Q (m x D)
+    over the graph G (n x k ids, -1 empty) from seeds S (m x s ids), t0
+    iterations, ks results per query: (ids m x ks, dists m x ks)."""
+    X, Q = _f32(X), _f32(Q)
+    G, S = _i32(G), _i32(S)
+    n, D = X.shape
+    m = Q.shape[0]
+    ids = np.empty((m, ks), np.int32)
+    d = np.empty((m, ks), np.float32)
+    rc = _load().orc_search(_p(X), n, D, _p(G), G.shape[1], _p(Q), m, _p(S), S.shape[1], t0, ks, _p(ids), _p(d))
+    if rc != 0:
+        raise ValueError("orc_search failed: %d" % rc)
+    return ids, d

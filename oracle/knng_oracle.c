@@ -3,7 +3,8 @@
  * partitioning, exhaustive comparison inside each cluster, and
  * neighbour-of-neighbour refinement (Zhao, Yang, Deng, "Scalable Nearest
  * Neighbor Search based on kNN Graph", arXiv 1701.08475, Sec. 3.1, Alg. 1;
- * refinement: the nearest-neighbour-descent prior art cited in Sec. 1).
+ * refinement: the nearest-neighbour-descent prior art cited in Sec. 1), and
+ * the enhanced hill-climbing search over the built graph (Sec. 3.2, Alg. 2).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
  * baseline leg of the benchmark load this library.  It shares no code,
@@ -424,5 +425,76 @@ int orc_recall(const int32_t *ids, const float *dists, const int32_t *gt_ids,
     }
     *recall_ids = s ? (double)hit / ((double)s * k) : 0.0;
     *recall_tie = s ? (double)tie / ((double)s * k) : 0.0;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Enhanced hill-climbing search over a kNN graph (Sec. 3.2, Alg. 2).  */
+/* For each query q (m x D) with seeds S[q] (s ids; ids outside [0, n) */
+/* are skipped): the rank list R starts as the seeds with d(q, seed);  */
+/* then, t0 times, every neighbour (in G, n x k ids, -1 = empty) of     */
+/* the ks first entries of R by (d, id) that has not been visited yet  */
+/* is visited and added to R.  Visited = its distance was computed     */
+/* (seeds included).  Output: the ks first entries of R by (d, id),    */
+/* empty slots id -1, d +inf.  d is the canonical FP32 distance.       */
+/* ------------------------------------------------------------------ */
+typedef struct { float d; int32_t id; } rank_t;
+
+static int rank_cmp(const void *a, const void *b)
+{
+    const rank_t *x = (const rank_t *)a, *y = (const rank_t *)b;
+    if (key_less(x->d, x->id, y->d, y->id)) return -1;
+    if (key_less(y->d, y->id, x->d, x->id)) return 1;
+    return 0;
+}
+
+int orc_search(const float *X, int64_t n, int D, const int32_t *G, int k,
+               const float *Q, int64_t m, const int32_t *S, int s, int t0, int ks,
+               int32_t *out_ids, float *out_d)
+{
+    if (n <= 0 || D <= 0 || k <= 0 || s < 0 || t0 < 0 || ks <= 0) return -1;
+    unsigned char *visited = (unsigned char *)malloc((size_t)n);
+    int32_t *top = (int32_t *)malloc(sizeof(int32_t) * (size_t)ks);
+    int64_t cap = (int64_t)s + (int64_t)t0 * ks * k;
+    rank_t *R = (rank_t *)malloc(sizeof(rank_t) * (size_t)(cap > 0 ? cap : 1));
+    if (!visited || !top || !R) { free(visited); free(top); free(R); return -2; }
+    for (int64_t qi = 0; qi < m; ++qi) {
+        const float *q = Q + qi * D;
+        memset(visited, 0, (size_t)n);
+        int64_t nr = 0;
+        for (int a = 0; a < s; ++a) {          /* R <- seeds */
+            int32_t id = S[qi * s + a];
+            if (id < 0 || id >= n || visited[id]) continue;
+            visited[id] = 1;
+            R[nr].d = orc_dist_f32(X + (int64_t)id * D, q, D);
+            R[nr].id = id;
+            ++nr;
+        }
+        for (int t = 0; t < t0; ++t) {
+            /* the ks first entries of R as it stands at the iteration's start */
+            qsort(R, (size_t)nr, sizeof(rank_t), rank_cmp);
+            int ntop = nr < ks ? (int)nr : ks;
+            for (int a = 0; a < ntop; ++a) top[a] = R[a].id;
+            for (int a = 0; a < ntop; ++a) {
+                const int32_t *row = G + (int64_t)top[a] * k;
+                for (int e = 0; e < k; ++e) {
+                    int32_t nb = row[e];
+                    if (nb < 0 || nb >= n || visited[nb]) continue;
+                    visited[nb] = 1;
+                    R[nr].d = orc_dist_f32(X + (int64_t)nb * D, q, D);
+                    R[nr].id = nb;
+                    ++nr;
+                }
+            }
+        }
+        qsort(R, (size_t)nr, sizeof(rank_t), rank_cmp);
+        for (int a = 0; a < ks; ++a) {
+            out_ids[qi * ks + a] = a < nr ? R[a].id : -1;
+            out_d[qi * ks + a] = a < nr ? R[a].d : INFINITY;
+        }
+    }
+    free(visited);
+    free(top);
+    free(R);
     return 0;
 }
