@@ -196,6 +196,24 @@ KNNG_API int knng_leaf_update(const float *data, int64_t n, int D, int k, const 
                      float *dists_inout, void *stream);
 
 /*
+ * The enhanced hill-climbing search of Sec. 3.2 (Alg. 2) over a kNN graph, for
+ * a batch of m queries.  For query q (row q of `queries`, m x D) the rank list
+ * R starts as its seeds (row q of `seeds`, m x s ids; ids outside [0, n) are
+ * skipped, repeats count once) with their distances; then, t0 times, every
+ * neighbour in `graph_ids` (n x k ids, -1 = empty; e.g. knng_build's output)
+ * of the ks first entries of R by (d, id), as R stands at the iteration's
+ * start, that has not been visited yet (its distance computed) is visited and
+ * added to R.  out_ids, out_dists (m x ks): the ks first entries of R by
+ * (d, id), canonical FP32 squared l2, empty slots id -1, d +inf.
+ * 1 <= ks <= 32; seeds are the caller's (random ones, as the paper's baseline
+ * draws, or any other choice).  Pointers host or device; KNNG_EINVAL on bad
+ * sizes or a non-finite input.
+ */
+KNNG_API int knng_search(const float *data, int64_t n, int D, const int32_t *graph_ids, int k,
+                         const float *queries, int64_t m, const int32_t *seeds, int s, int t0, int ks,
+                         int32_t *out_ids, float *out_dists, void *stream);
+
+/*
  * Exact k nearest neighbours (the problem statement of Sec. 1, each listed
  * point as a query against the other n - 1) of the s rows listed in `sample`
  * (all rows in order when sample is NULL, then s must equal n), canonical FP32

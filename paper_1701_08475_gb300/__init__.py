@@ -1,6 +1,7 @@
 """GB300 (sm_103a) kNN-graph construction by two-means trees
 (Zhao, Yang, Deng, arXiv 1701.08475, Sec. 3.1, Alg. 1) with neighbour-of-
-neighbour refinement.
+neighbour refinement, and the enhanced hill-climbing search over the graph
+(Sec. 3.2, Alg. 2).
 
 A thin binding of the C ABI declared in include/knng.h: every function has
 the name of its C entry point, marshals tensors to plain pointers and sizes,
@@ -20,6 +21,7 @@ from ._lib import (  # noqa: F401
     knng_build_batched,
     BuildPlan,
     knng_exact,
+    knng_search,
     knng_exact_noalloc,
     knng_leaf_update,
     knng_partition,

@@ -77,6 +77,7 @@ def load():
             "knng_tree_depth": (i32, [i64, i32]),
             "knng_leaf_update": (i32, [P, i64, i32, i32, P, P, i64, P, P, P]),
             "knng_exact": (i32, [P, i64, i32, i32, P, i64, P, P, P]),
+            "knng_search": (i32, [P, i64, i32, P, i32, P, i64, P, i32, i32, i32, P, P, P]),
             "knng_exact_noalloc": (i32, [P, i64, i32, i32, P, i64, P, P, P]),
             "knng_recall": (i32, [P, P, P, P, P, i64, i32, P, P, P]),
             "knng_last_error": (ctypes.c_char_p, []),
@@ -312,6 +313,24 @@ def knng_leaf_update(data, k, perm, leaf_offsets, ids, dists, stream=None):
         _check(load().knng_leaf_update(_ptr(data), n, D, k, _ptr(perm), _ptr(leaf_offsets), len(leaf_offsets) - 1,
                                        _ptr(ids), _ptr(dists), s))
     return ids, dists
+
+
+def knng_search(data, graph_ids, queries, seeds, t0, ks, stream=None):
+    """Enhanced hill-climbing search (Sec. 3.2, Alg. 2) of `queries` (m x D)
+    over the graph `graph_ids` (n x k ids) from `seeds` (m x s ids), t0
+    iterations: (ids, dists), m x ks each."""
+    data = _contig(data, "float32")
+    graph_ids = _contig(graph_ids, "int32")
+    queries = _contig(queries, "float32")
+    seeds = _contig(seeds, "int32")
+    n, D = data.shape
+    m = queries.shape[0]
+    ids = _empty_like_input(data, (m, ks), "int32")
+    d = _empty_like_input(data, (m, ks), "float32")
+    with _DeviceCtx(data, stream) as s:
+        _check(load().knng_search(_ptr(data), n, D, _ptr(graph_ids), graph_ids.shape[1], _ptr(queries), m,
+                                  _ptr(seeds), seeds.shape[1], t0, ks, _ptr(ids), _ptr(d), s))
+    return ids, d
 
 
 def knng_exact(data, k, sample=None, stream=None):

@@ -1148,6 +1148,56 @@ int knng_leaf_update(const float* data, int64_t n, int D, int k, const int32_t* 
     });
 }
 
+int knng_search(const float* data, int64_t n, int D, const int32_t* graph_ids, int k, const float* queries,
+                int64_t m, const int32_t* seeds, int s, int t0, int ks, int32_t* out_ids, float* out_dists,
+                void* stream) {
+    return guarded([&] {
+        if (!data || n < 1 || D < 1) fail(KNNG_EINVAL, "data, n or D invalid");
+        if (!graph_ids || k < 1) fail(KNNG_EINVAL, "graph_ids NULL or k < 1");
+        if (m < 0 || s < 0 || t0 < 0) fail(KNNG_EINVAL, "m, s or t0 negative");
+        if (ks < 1 || ks > 32) fail(KNNG_EINVAL, "ks = %d out of range [1, 32]", ks);
+        if ((size_t)4 * D * sizeof(float) > 200 * 1024) fail(KNNG_EINVAL, "D = %d too large for the search", D);
+        if (m == 0) return;
+        if (!queries || !out_ids || !out_dists || (s > 0 && !seeds)) fail(KNNG_EINVAL, "a pointer is NULL");
+        cudaStream_t st = (cudaStream_t)stream;
+        const int cl = search_cap_log2(s, t0, ks, k);
+        // queries per launch: their visited tables within 1 GiB
+        const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(m, ((int64_t)1 << 28) >> cl));
+        Workspace ws;
+        DevBuf<float> X, Qb;
+        DevBuf<int32_t> Gb, Sb, oi;
+        DevBuf<float> od;
+        int32_t* tab = nullptr;
+        int* status = nullptr;
+        for (int ps = 0; ps < 2; ++ps) {
+            ws.used = 0;
+            bind(ws, X, data, (size_t)n * D, ps);
+            bind(ws, Gb, graph_ids, (size_t)n * k, ps);
+            bind(ws, Qb, queries, (size_t)m * D, ps);
+            if (s > 0) bind(ws, Sb, seeds, (size_t)m * s, ps);
+            bind(ws, oi, out_ids, (size_t)m * ks, ps);
+            bind(ws, od, out_dists, (size_t)m * ks, ps);
+            tab = ws.take<int32_t>((size_t)chunk << cl);
+            status = ws.take<int>(4);
+            if (ps == 0) ws.allocate(st);
+        }
+        cuda_check(cudaMemsetAsync(status, 0, 4 * sizeof(int), st), "status clear");
+        upload(X, st);
+        upload(Gb, st);
+        upload(Qb, st);
+        if (s > 0) upload(Sb, st);
+        launch_check_finite(X.dev, n * (int64_t)D, status, st);
+        launch_check_finite(Qb.dev, m * (int64_t)D, status, st);
+        for (int64_t q0 = 0; q0 < m; q0 += chunk)
+            launch_search(X.dev, n, D, Gb.dev, k, Qb.dev, q0, std::min(m, q0 + chunk), s > 0 ? Sb.dev : nullptr, s,
+                          t0, ks, tab, cl, oi.dev, od.dev, st);
+        download(oi, st);
+        download(od, st);
+        cuda_check(cudaGetLastError(), "kernel launch");
+        check_status(status, st);
+    });
+}
+
 int knng_exact(const float* data, int64_t n, int D, int k, const int32_t* sample, int64_t s_rows, int32_t* out_ids,
                float* out_dists, void* stream) {
     return guarded([&] {

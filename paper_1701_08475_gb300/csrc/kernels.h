@@ -221,6 +221,14 @@ void launch_check_ids(const int32_t* ids, int64_t count, int64_t lo, int64_t hi,
 void launch_unpack(const uint64_t* G, int32_t* ids, float* d, int64_t count, cudaStream_t s, int64_t id_offset = 0);
 
 // ---------------------------------------------------------------- exact / recall (K7)
+// Enhanced hill-climbing search (search.cu): queries [q0, q1) of Q against
+// the graph G (n x k ids), seeds S (s per query), t0 iterations, ks <= 32
+// results per query; tab: (q1 - q0) << cap_log2 ints of visited tables.
+int search_cap_log2(int s, int t0, int ks, int k);
+void launch_search(const float* X, int64_t n, int D, const int32_t* G, int k, const float* Q, int64_t q0,
+                   int64_t q1, const int32_t* S, int s, int t0, int ks, int32_t* tab, int cap_log2, int32_t* out_ids,
+                   float* out_d, cudaStream_t st);
+
 void launch_exact(const float* X, int64_t n, int D, int k, const int32_t* sample, int64_t s_rows,
                   uint64_t* out, const int* status, cudaStream_t s);
 void launch_recall(const int32_t* ids, const float* d, const int32_t* gt_ids, const float* gt_d,
