@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-search", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16"])
     return ap.parse_args()
@@ -259,6 +260,53 @@ def run_reference(args, cfg):
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
 
 
+def search_measure(knng, X, Xd, G, dev, stream, m=10000, t0=12, ks=20, n_seeds=32, n_check=200):
+    """The enhanced hill-climbing search (Alg. 2) over the built graph: m
+    queries (input points moved by N(0, 4^2) noise, rounded and clipped for
+    integer data), timed with CUDA events; recall against float64 brute force
+    on n_check of them.  Seeds: random (the paper's baseline) and random plus
+    one point of the query's own cluster (a stand-in for the inverted-index
+    seeding of Sec. 4, which is not built)."""
+    import torch
+    n, D = X.shape
+    rng = np.random.default_rng(17)
+    base = rng.integers(0, n, size=m)
+    Q = X[base].astype(np.float64) + rng.normal(0.0, 4.0, size=(m, D))
+    if np.array_equal(X, np.rint(X)):
+        Q = np.clip(np.rint(Q), X.min(), X.max())
+    Q = Q.astype(np.float32)
+    S_rand = rng.integers(0, n, size=(m, n_seeds)).astype(np.int32)
+    S_near = S_rand.copy()
+    S_near[:, 0] = G[:, -1].cpu().numpy()[base]
+    Qd = torch.from_numpy(Q).to(dev)
+    check = np.sort(rng.choice(m, size=n_check, replace=False))
+    # ||x - q||^2 - ||q||^2 = ||x||^2 - 2 x.q, one float64 GEMM for all checked queries
+    Xd64 = Xd.double()
+    Qc = Qd[torch.from_numpy(check).to(dev)].double()
+    part = (Xd64 * Xd64).sum(1, keepdim=True) - 2.0 * (Xd64 @ Qc.T)
+    truth = torch.topk(part, ks, dim=0, largest=False).indices.T.cpu().numpy()
+    del Xd64, part
+    out = {"queries": m, "t0": t0, "ks": ks, "seeds_per_query": n_seeds,
+           "queries_from": "input points moved by N(0, 4^2) noise", "truth": "float64 brute force, %d queries" % n_check}
+    for name, S in (("random_seeds", S_rand), ("near_seed", S_near)):
+        Sd = torch.from_numpy(S).to(dev)
+        with torch.cuda.stream(stream):
+            knng.knng_search(Xd, G, Qd, Sd, t0, ks, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                ids, _d = knng.knng_search(Xd, G, Qd, Sd, t0, ks, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        got = ids.cpu().numpy()[check]
+        r1 = float(np.mean([got[i, 0] == truth[i][0] for i in range(n_check)]))
+        rk = float(np.mean([len(set(got[i].tolist()) & set(truth[i].tolist())) / ks for i in range(n_check)]))
+        out[name] = {"queries_per_s": round(m / (ms * 1e-3), 1), "ms": round(ms, 3), "recall_at_1": round(r1, 4),
+                     "recall_at_ks": round(rk, 4)}
+    return out
+
+
 def run_ours(args, cfg):
     import torch
     import paper_1701_08475_gb300 as knng
@@ -436,6 +484,8 @@ def run_ours(args, cfg):
                                  "note": "a second run of the same steps with CUDA events around every launch; "
                                          "the per-kernel times, shares and rooflines come from it"},
     }
+    if world == 1 and not args.no_search:
+        line["search"] = search_measure(knng, X, Xd, ids, dev, stream)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(line), flush=True)
