@@ -1,4 +1,6 @@
-"""CPU oracle for kNN-graph construction (arXiv 1701.08475, Sec. 3.1, Alg. 1).
+"""CPU oracle for kNN-graph construction (arXiv 1701.08475, Sec. 3.1, Alg. 1),
+the graph search (Sec. 3.2, Alg. 2) and its residue-quantisation inverted index
+(Sec. 4).
 
 TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` are the only callers.  The oracle shares no code
@@ -59,6 +61,11 @@ def _bind(lib):
         "orc_build": (i32, [P, i64, i32, i32, i32, i32, i32, i32, i32, u64, P, P]),
         "orc_recall": (i32, [P, P, P, P, P, i64, i32, P, P]),
         "orc_search": (i32, [P, i64, i32, P, i32, P, i64, P, i32, i32, i32, P, P]),
+        "orc_rvq_init_positions": (None, [i64, i32, u64, i32, P]),
+        "orc_rvq_assign": (i32, [P, i64, i32, P, i32, P]),
+        "orc_rvq_train": (i32, [P, i64, i32, i32, i32, i32, u64, P, P]),
+        "orc_rvq_index": (i32, [P, i64, i32, P, i32, P, i32, P, P, P]),
+        "orc_rvq_seeds": (i32, [P, i32, P, i32, i32, P, P, P, i64, i32, i32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -255,3 +262,62 @@ def search(X, G, Q, S, t0, ks):
     if rc != 0:
         raise ValueError("orc_search failed: %d" % rc)
     return ids, d
+
+
+def rvq_init_positions(N, W, seed, stage):
+    """Initial word positions of one stage (one SplitMix64 draw per stratum)."""
+    pos = np.empty(W, np.int64)
+    _load().orc_rvq_init_positions(N, W, seed & (2**64 - 1), stage, _p(pos))
+    return pos
+
+
+def rvq_assign(V, words):
+    """Nearest word of every row of V (canonical FP32, ties to the smaller index)."""
+    V, words = _f32(V), _f32(words)
+    codes = np.empty(V.shape[0], np.int32)
+    if _load().orc_rvq_assign(_p(V), V.shape[0], V.shape[1], _p(words), words.shape[0], _p(codes)) != 0:
+        raise ValueError("orc_rvq_assign: bad arguments")
+    return codes
+
+
+def rvq_train(X, W1=256, W2=256, iters=10, seed=0):
+    """Two-stage residue vector quantisation vocabularies (Sec. 4.1, Eqn. 1):
+    (w1 W1 x D, w2 W2 x D), Lloyd's k-means per stage."""
+    X = _f32(X)
+    n, D = X.shape
+    w1 = np.empty((W1, D), np.float32)
+    w2 = np.empty((W2, D), np.float32)
+    rc = _load().orc_rvq_train(_p(X), n, D, W1, W2, iters, seed & (2**64 - 1), _p(w1), _p(w2))
+    if rc != 0:
+        raise ValueError("orc_rvq_train failed: %d" % rc)
+    return w1, w2
+
+
+def rvq_index(X, w1, w2):
+    """Codes (n x 2: c1, c2) and the inverted lists (offsets W1*W2 + 1, ids n)
+    keyed by c1 * W2 + c2 (Sec. 4.2)."""
+    X, w1, w2 = _f32(X), _f32(w1), _f32(w2)
+    n, D = X.shape
+    W1, W2 = w1.shape[0], w2.shape[0]
+    codes = np.empty((n, 2), np.int32)
+    off = np.empty(W1 * W2 + 1, np.int32)
+    ids = np.empty(n, np.int32)
+    rc = _load().orc_rvq_index(_p(X), n, D, _p(w1), W1, _p(w2), W2, _p(codes), _p(off), _p(ids))
+    if rc != 0:
+        raise ValueError("orc_rvq_index failed: %d" % rc)
+    return codes, off, ids
+
+
+def rvq_seeds(w1, w2, offsets, ids, Q, probe1, s):
+    """Seeds of Alg. 2 from the inverted index (Sec. 4.2, Eqns. 2 and 3):
+    m x s ids, -1 padded."""
+    w1, w2, Q = _f32(w1), _f32(w2), _f32(Q)
+    offsets, ids = _i32(offsets), _i32(ids)
+    W1, D = w1.shape
+    W2 = w2.shape[0]
+    m = Q.shape[0]
+    S = np.empty((m, s), np.int32)
+    rc = _load().orc_rvq_seeds(_p(w1), W1, _p(w2), W2, D, _p(offsets), _p(ids), _p(Q), m, probe1, s, _p(S))
+    if rc != 0:
+        raise ValueError("orc_rvq_seeds failed: %d" % rc)
+    return S

@@ -4,7 +4,8 @@
  * neighbour-of-neighbour refinement (Zhao, Yang, Deng, "Scalable Nearest
  * Neighbor Search based on kNN Graph", arXiv 1701.08475, Sec. 3.1, Alg. 1;
  * refinement: the nearest-neighbour-descent prior art cited in Sec. 1), and
- * the enhanced hill-climbing search over the built graph (Sec. 3.2, Alg. 2).
+ * the enhanced hill-climbing search over the built graph (Sec. 3.2, Alg. 2),
+ * and the residue-quantisation inverted index that seeds it (Sec. 4).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
  * baseline leg of the benchmark load this library.  It shares no code,
@@ -496,5 +497,214 @@ int orc_search(const float *X, int64_t n, int D, const int32_t *G, int k,
     free(visited);
     free(top);
     free(R);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Residue vector quantisation (Sec. 4.1, Eqn. 1) and the inverted     */
+/* index with cascaded pruning (Sec. 4.2, Eqns. 2 and 3).  Two stages. */
+/*                                                                    */
+/* Readings (the paper names the steps but not these details):         */
+/*  - each stage's vocabulary is trained by Lloyd's k-means on that    */
+/*    stage's vectors: stage 1 on the points, stage 2 on the residues  */
+/*    r = x - w1[c1(x)] (FP32 subtraction), c1 the stage-1 code after  */
+/*    training;                                                        */
+/*  - initial word c is vector p_c, drawn by SplitMix64 inside the     */
+/*    c-th of W equal strata of the N vectors (N >= W);                */
+/*  - an iteration assigns every vector to its nearest word (canonical */
+/*    FP32 distance, ties to the smaller word index), then sets each   */
+/*    word with members to the FP64 mean of its members (summed in     */
+/*    ascending vector order), rounded to FP32; a word without members */
+/*    keeps its value;                                                 */
+/*  - the index key of a point is c1 * W2 + c2; a list holds its ids   */
+/*    in ascending order;                                              */
+/*  - query-to-key distance, in FP32 with this operation order:        */
+/*      term1(c1)     = fmaf(-2, q.w1, q.q) + |w1|^2                   */
+/*      term2(c1, c2) = fmaf(-2, q.w2, fmaf(2, w1.w2, |w2|^2))         */
+/*      d(q, I)       = term1 + term2                                  */
+/*    (Eqn. 3 prints the signs of |w1|^2 and of the two products with  */
+/*    w2 garbled; these are the terms of the expansion of Eqn. 2).     */
+/*    Dot products and norms are canonical: acc = fmaf(a_j, b_j, acc), */
+/*    j ascending, from 0.  -0 is normalised to +0;                    */
+/*  - cascaded pruning keeps the probe1 stage-1 words with the least   */
+/*    (term1, c1); their keys are ranked by (d, I); the seeds are the  */
+/*    ids of the lists in that order, ascending inside a list, the     */
+/*    first s of them; -1 pads a query whose lists hold fewer.         */
+/* ------------------------------------------------------------------ */
+static float dot_f32(const float *a, const float *b, int D)
+{
+    float acc = 0.0f;
+    for (int j = 0; j < D; ++j) acc = fmaf(a[j], b[j], acc);
+    return acc;
+}
+
+void orc_rvq_init_positions(int64_t N, int W, uint64_t seed, int stage, int64_t *pos)
+{
+    const uint64_t h0 = orc_splitmix64(seed ^ ((uint64_t)stage << 32));
+    for (int c = 0; c < W; ++c) {
+        int64_t lo = (int64_t)c * N / W, hi = (int64_t)(c + 1) * N / W;
+        uint64_t h = orc_splitmix64(h0 ^ (uint64_t)c);
+        pos[c] = lo + (int64_t)(h % (uint64_t)(hi - lo));
+    }
+}
+
+int orc_rvq_assign(const float *V, int64_t N, int D, const float *words, int W, int32_t *codes)
+{
+    if (N < 0 || D <= 0 || W <= 0) return -1;
+    for (int64_t i = 0; i < N; ++i) {
+        float best = INFINITY;
+        int32_t bc = 0;
+        for (int c = 0; c < W; ++c) {
+            float d = orc_dist_f32(V + i * D, words + (int64_t)c * D, D);
+            if (d < best) { best = d; bc = c; }
+        }
+        codes[i] = bc;
+    }
+    return 0;
+}
+
+/* Lloyd's k-means of one stage: W words from the N vectors V. */
+static int lloyd(const float *V, int64_t N, int D, int W, int iters, uint64_t seed, int stage,
+                 float *words, int32_t *codes)
+{
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)W);
+    double *acc = (double *)malloc(sizeof(double) * (size_t)W * D);
+    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)W);
+    if (!pos || !acc || !cnt) { free(pos); free(acc); free(cnt); return -2; }
+    orc_rvq_init_positions(N, W, seed, stage, pos);
+    for (int c = 0; c < W; ++c) memcpy(words + (int64_t)c * D, V + pos[c] * D, sizeof(float) * D);
+    for (int it = 0; it < iters; ++it) {
+        orc_rvq_assign(V, N, D, words, W, codes);
+        memset(acc, 0, sizeof(double) * (size_t)W * D);
+        memset(cnt, 0, sizeof(int64_t) * (size_t)W);
+        for (int64_t i = 0; i < N; ++i) {        /* ascending vector order */
+            double *a = acc + (int64_t)codes[i] * D;
+            for (int j = 0; j < D; ++j) a[j] += (double)V[i * D + j];
+            cnt[codes[i]] += 1;
+        }
+        for (int c = 0; c < W; ++c) {
+            if (cnt[c] == 0) continue;
+            for (int j = 0; j < D; ++j)
+                words[(int64_t)c * D + j] = (float)(acc[(int64_t)c * D + j] / (double)cnt[c]);
+        }
+    }
+    free(pos);
+    free(acc);
+    free(cnt);
+    return 0;
+}
+
+/* Stage-2 vectors: r_i = x_i - w1[c1_i], FP32. */
+static void residues(const float *X, int64_t n, int D, const float *w1, const int32_t *c1, float *R)
+{
+    for (int64_t i = 0; i < n; ++i)
+        for (int j = 0; j < D; ++j) R[i * D + j] = X[i * D + j] - w1[(int64_t)c1[i] * D + j];
+}
+
+int orc_rvq_train(const float *X, int64_t n, int D, int W1, int W2, int iters, uint64_t seed,
+                  float *w1, float *w2)
+{
+    if (n <= 0 || D <= 0 || W1 <= 0 || W2 <= 0 || W1 > n || W2 > n || iters < 0) return -1;
+    int32_t *codes = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    float *R = (float *)malloc(sizeof(float) * (size_t)n * D);
+    if (!codes || !R) { free(codes); free(R); return -2; }
+    int rc = lloyd(X, n, D, W1, iters, seed, 1, w1, codes);
+    if (rc == 0) {
+        orc_rvq_assign(X, n, D, w1, W1, codes);
+        residues(X, n, D, w1, codes, R);
+        rc = lloyd(R, n, D, W2, iters, seed, 2, w2, codes);
+    }
+    free(codes);
+    free(R);
+    return rc;
+}
+
+int orc_rvq_index(const float *X, int64_t n, int D, const float *w1, int W1, const float *w2, int W2,
+                  int32_t *codes, int32_t *offsets, int32_t *ids)
+{
+    if (n < 0 || D <= 0 || W1 <= 0 || W2 <= 0) return -1;
+    int32_t *c1 = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *c2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    float *R = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1) * D);
+    int64_t nk = (int64_t)W1 * W2;
+    int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)nk);
+    if (!c1 || !c2 || !R || !fill) { free(c1); free(c2); free(R); free(fill); return -2; }
+    orc_rvq_assign(X, n, D, w1, W1, c1);
+    residues(X, n, D, w1, c1, R);
+    orc_rvq_assign(R, n, D, w2, W2, c2);
+    memset(offsets, 0, sizeof(int32_t) * (size_t)(nk + 1));
+    for (int64_t i = 0; i < n; ++i) {
+        codes[2 * i] = c1[i];
+        codes[2 * i + 1] = c2[i];
+        offsets[(int64_t)c1[i] * W2 + c2[i] + 1] += 1;
+    }
+    for (int64_t key = 0; key < nk; ++key) offsets[key + 1] += offsets[key];
+    memcpy(fill, offsets, sizeof(int32_t) * (size_t)nk);
+    for (int64_t i = 0; i < n; ++i) ids[fill[(int64_t)c1[i] * W2 + c2[i]]++] = (int32_t)i;
+    free(c1);
+    free(c2);
+    free(R);
+    free(fill);
+    return 0;
+}
+
+typedef struct { float d; int32_t key; } keyd_t;
+
+static int keyd_cmp(const void *a, const void *b)
+{
+    const keyd_t *x = (const keyd_t *)a, *y = (const keyd_t *)b;
+    if (x->d < y->d) return -1;
+    if (x->d > y->d) return 1;
+    return (x->key > y->key) - (x->key < y->key);
+}
+
+int orc_rvq_seeds(const float *w1, int W1, const float *w2, int W2, int D, const int32_t *offsets,
+                  const int32_t *ids, const float *Q, int64_t m, int probe1, int s, int32_t *S)
+{
+    if (W1 <= 0 || W2 <= 0 || D <= 0 || m < 0 || probe1 <= 0 || s < 0) return -1;
+    const int p1 = probe1 < W1 ? probe1 : W1;
+    float *n1 = (float *)malloc(sizeof(float) * (size_t)W1);
+    float *n2 = (float *)malloc(sizeof(float) * (size_t)W2);
+    float *x12 = (float *)malloc(sizeof(float) * (size_t)W1 * W2);
+    float *qw2 = (float *)malloc(sizeof(float) * (size_t)W2);
+    keyd_t *t1 = (keyd_t *)malloc(sizeof(keyd_t) * (size_t)W1);
+    keyd_t *cand = (keyd_t *)malloc(sizeof(keyd_t) * (size_t)p1 * W2);
+    if (!n1 || !n2 || !x12 || !qw2 || !t1 || !cand) {
+        free(n1); free(n2); free(x12); free(qw2); free(t1); free(cand);
+        return -2;
+    }
+    for (int a = 0; a < W1; ++a) n1[a] = dot_f32(w1 + (int64_t)a * D, w1 + (int64_t)a * D, D);
+    for (int b = 0; b < W2; ++b) n2[b] = dot_f32(w2 + (int64_t)b * D, w2 + (int64_t)b * D, D);
+    for (int a = 0; a < W1; ++a)
+        for (int b = 0; b < W2; ++b)
+            x12[(int64_t)a * W2 + b] = dot_f32(w1 + (int64_t)a * D, w2 + (int64_t)b * D, D);
+    for (int64_t qi = 0; qi < m; ++qi) {
+        const float *q = Q + qi * D;
+        const float qq = dot_f32(q, q, D);
+        for (int a = 0; a < W1; ++a) {            /* Eqn. 3, term 1 */
+            float t = fmaf(-2.0f, dot_f32(q, w1 + (int64_t)a * D, D), qq);
+            t1[a].d = (t + n1[a]) + 0.0f;
+            t1[a].key = a;
+        }
+        qsort(t1, (size_t)W1, sizeof(keyd_t), keyd_cmp);
+        for (int b = 0; b < W2; ++b) qw2[b] = dot_f32(q, w2 + (int64_t)b * D, D);
+        int64_t nc = 0;
+        for (int r = 0; r < p1; ++r) {            /* the kept stage-1 words, term 2 */
+            const int a = t1[r].key;
+            for (int b = 0; b < W2; ++b) {
+                float t2 = fmaf(-2.0f, qw2[b], fmaf(2.0f, x12[(int64_t)a * W2 + b], n2[b]));
+                cand[nc].d = (t1[r].d + t2) + 0.0f;
+                cand[nc].key = a * W2 + b;
+                ++nc;
+            }
+        }
+        qsort(cand, (size_t)nc, sizeof(keyd_t), keyd_cmp);
+        int cnt = 0;
+        for (int64_t e = 0; e < nc && cnt < s; ++e)
+            for (int32_t t = offsets[cand[e].key]; t < offsets[cand[e].key + 1] && cnt < s; ++t)
+                S[qi * s + cnt++] = ids[t];
+        for (; cnt < s; ++cnt) S[qi * s + cnt] = -1;
+    }
+    free(n1); free(n2); free(x12); free(qw2); free(t1); free(cand);
     return 0;
 }

@@ -71,3 +71,65 @@ def test_planted_mistake_is_caught(name, old, new, tmp_path, monkeypatch):
             caught.append(getattr(pin, "__name__", "pin"))
             break
     assert caught, "no pin caught the planted mistake: " + name
+
+
+# the search (Alg. 2) and the residue-quantisation index (Sec. 4)
+from tests import test_oracle_rvq as V    # noqa: E402
+from tests import test_oracle_search as Sr  # noqa: E402
+
+PINS_SEARCH_RVQ = [
+    Sr.test_no_iterations_rank_the_seeds,
+    Sr.test_one_iteration_over_a_complete_graph_is_brute_force,
+    lambda: Sr.test_path_graph_frontier_moves_one_node_per_iteration(2, 3),
+    lambda: Sr.test_path_graph_frontier_moves_one_node_per_iteration(4, 40),
+    Sr.test_repeated_and_out_of_range_seeds_count_once,
+    Sr.test_rows_are_sorted_unique_and_carry_canonical_distances,
+    lambda: Sr.test_every_top_entry_is_expanded_not_only_the_first(2, [2, 0]),
+    V.test_init_positions_one_per_stratum,
+    V.test_assign_is_the_brute_force_argmin_with_ties_to_the_smaller_index,
+    V.test_one_iteration_from_separated_clusters_gives_their_means,
+    lambda: V.test_converged_training_is_a_fixed_point_of_both_stages(0),
+    V.test_quantisation_error_never_grows_over_iterations,
+    V.test_one_word_per_point_and_a_single_word,
+    V.test_index_is_a_stable_sort_by_key,
+    lambda: V.test_seeds_follow_eqn2_with_pruning_by_the_first_term(3, 40),
+    lambda: V.test_seeds_follow_eqn2_with_pruning_by_the_first_term(12, 300),
+    V.test_seeds_on_float_data_follow_the_direct_distance_up_to_rounding,
+]
+
+MUTATIONS_SEARCH_RVQ = [
+    ("search expands only the top entry", "int ntop = nr < ks ? (int)nr : ks;", "int ntop = nr < 1 ? (int)nr : 1;"),
+    ("search seeds not marked visited", "visited[id] = 1;\n            R[nr].d", "R[nr].d"),
+    ("search drops the last neighbour slot", "for (int e = 0; e < k; ++e) {\n                    int32_t nb",
+     "for (int e = 0; e + 1 < k; ++e) {\n                    int32_t nb"),
+    ("search expands the final order", "/* the ks first entries of R as it stands at the iteration's start */\n"
+     "            qsort(R, (size_t)nr, sizeof(rank_t), rank_cmp);", ""),
+    ("rvq ties to the larger word", "if (d < best) { best = d; bc = c; }", "if (d <= best) { best = d; bc = c; }"),
+    ("rvq residue sign", "R[i * D + j] = X[i * D + j] - w1[", "R[i * D + j] = X[i * D + j] + w1["),
+    ("rvq mean off by one", "/ (double)cnt[c]);", "/ (double)(cnt[c] + 1));"),
+    ("rvq stage 2 trained on the points", "rc = lloyd(R, n, D, W2", "rc = lloyd(X, n, D, W2"),
+    ("rvq draw outside its stratum", "pos[c] = lo + (int64_t)(h % (uint64_t)(hi - lo));",
+     "pos[c] = lo + (int64_t)(h % (uint64_t)(hi - lo + 1));"),
+    ("rvq term 2 cross-product sign", "fmaf(2.0f, x12[", "fmaf(-2.0f, x12["),
+    ("rvq pruning without the word norm", "t1[a].d = (t + n1[a]) + 0.0f;", "t1[a].d = t + 0.0f;"),
+    ("rvq lists in descending ids", "for (int64_t i = 0; i < n; ++i) ids[fill",
+     "for (int64_t i = n - 1; i >= 0; --i) ids[fill"),
+    ("rvq seeds skip a list's first id", "for (int32_t t = offsets[cand[e].key];",
+     "for (int32_t t = offsets[cand[e].key] + 1;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS_SEARCH_RVQ, ids=[m[0] for m in MUTATIONS_SEARCH_RVQ])
+def test_planted_mistake_in_search_or_index_is_caught(name, old, new, tmp_path, monkeypatch):
+    src = oracle.source_text()
+    assert src.count(old) == 1, "mutation anchor must occur once: " + name
+    lib = oracle.compile_variant(src.replace(old, new), str(tmp_path / "mutant.so"))
+    monkeypatch.setattr(oracle, "_lib", lib)
+    caught = False
+    for pin in PINS_SEARCH_RVQ:
+        try:
+            pin()
+        except Exception:
+            caught = True
+            break
+    assert caught, "no pin caught the planted mistake: " + name

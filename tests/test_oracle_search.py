@@ -93,3 +93,19 @@ def test_rows_are_sorted_unique_and_carry_canonical_distances():
         assert keys == sorted(keys)
         for i, dv in zip(ids[r][real], d[r][real]):
             assert dv == np.float32(_d64(X[i:i + 1], Q[r])[0])   # integer data: exact in FP32
+
+
+@pytest.mark.parametrize("ks,want", [(2, [2, 0]), (1, [0])])
+def test_every_top_entry_is_expanded_not_only_the_first(ks, want):
+    # Alg. 2 expands each of the top ks entries per iteration (the change from
+    # the original GNNS, which expands only the first).  1-D points, dyadic so
+    # every distance is exact: q = 10.5; seeds A = 10 (d 0.25) and B = 13
+    # (d 6.25); B's only neighbour C = 10.75 (d 0.0625) beats A, A's only
+    # neighbour E = 20 (d 90.25).  With ks = 2 one iteration finds C.
+    X = np.array([[10.0], [13.0], [10.75], [20.0]], np.float32)
+    G = np.array([[3], [2], [1], [0]], np.int32)
+    Q = np.array([[10.5]], np.float32)
+    S = np.array([[0, 1]], np.int32)
+    ids, d = oracle.search(X, G, Q, S, 1, ks)
+    assert ids[0].tolist() == want
+    assert d[0].tolist() == [{0: 0.25, 1: 6.25, 2: 0.0625, 3: 90.25}[i] for i in want]
