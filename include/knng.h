@@ -214,6 +214,56 @@ KNNG_API int knng_search(const float *data, int64_t n, int D, const int32_t *gra
                          int32_t *out_ids, float *out_dists, void *stream);
 
 /*
+ * Residue vector quantisation vocabularies (Sec. 4.1, Eqn. 1), two stages.
+ * Stage 1 (W1 words) is trained on the n points of `data` (n x D FP32,
+ * row-major), stage 2 (W2 words) on their residues x - w1[c1(x)] (FP32
+ * difference, c1 the nearest stage-1 word after training).  Each stage is
+ * Lloyd's k-means for `iters` iterations from W initial words: word c starts
+ * as vector p_c, p_c = lo_c + SplitMix64(SplitMix64(seed ^ (stage << 32)) ^ c)
+ * mod (hi_c - lo_c) inside the c-th of W equal strata [lo_c, hi_c) of the
+ * vectors.  An iteration assigns each vector to its nearest word (canonical
+ * FP32 squared l2: dims ascending, t = x - w, acc = fmaf(t, t, acc); ties to
+ * the smaller word index) and sets every word with members to the FP64 mean of
+ * its members summed in ascending vector order, rounded to FP32; a word
+ * without members keeps its value.  1 <= W1, W2 <= 256, both <= n; iters >= 0.
+ * Outputs words1 (W1 x D) and words2 (W2 x D), FP32.  Pointers host or
+ * device.  KNNG_EINVAL on bad sizes or non-finite data.
+ */
+KNNG_API int knng_rvq_train(const float *data, int64_t n, int D, int W1, int W2, int iters, uint64_t seed,
+                            float *words1, float *words2, void *stream);
+
+/*
+ * The inverted index of Sec. 4.2: each point's codes (c1 = nearest stage-1
+ * word, c2 = nearest stage-2 word to its residue; same distance and ties as
+ * knng_rvq_train) into `codes` (n x 2 int32: c1, c2), and the lists keyed by
+ * I = c1 * W2 + c2 as CSR: list I holds list_ids[list_offsets[I] ..
+ * list_offsets[I + 1]) in ascending id order (list_offsets: W1 * W2 + 1
+ * int32; list_ids: n int32).  1 <= W1, W2 <= 256.  Pointers host or device.
+ */
+KNNG_API int knng_rvq_index(const float *data, int64_t n, int D, const float *words1, int W1,
+                            const float *words2, int W2, int32_t *codes, int32_t *list_offsets,
+                            int32_t *list_ids, void *stream);
+
+/*
+ * Seeds of the graph search (Alg. 2) from the inverted index (Sec. 4.2,
+ * Eqns. 2 and 3), for m queries (m x D).  With canonical dot products
+ * (acc = fmaf(a_j, b_j, acc), dims ascending) in FP32:
+ *   term1(c1)     = fmaf(-2, q.w1, q.q) + |w1|^2
+ *   term2(c1, c2) = fmaf(-2, q.w2, fmaf(2, w1.w2, |w2|^2))
+ *   d(q, I)       = term1 + term2          (-0 normalised to +0)
+ * the probe1 stage-1 words with the least (term1, c1) are kept (the cascaded
+ * pruning), their W2 keys each are ranked by (d, I), and the seeds are the ids
+ * of those lists in that order (ascending inside a list), the first s; -1 pads
+ * a query whose lists hold fewer.  seeds: m x s int32.  list_offsets /
+ * list_ids as knng_rvq_index writes them, n = the number of list ids;
+ * offsets that are negative, decreasing or above n give KNNG_EINVAL.
+ * 1 <= probe1 <= W1, probe1 * W2 <= 8192.  Pointers host or device.
+ */
+KNNG_API int knng_rvq_seeds(const float *words1, int W1, const float *words2, int W2, int D,
+                            const int32_t *list_offsets, const int32_t *list_ids, int64_t n,
+                            const float *queries, int64_t m, int probe1, int s, int32_t *seeds, void *stream);
+
+/*
  * Exact k nearest neighbours (the problem statement of Sec. 1, each listed
  * point as a query against the other n - 1) of the s rows listed in `sample`
  * (all rows in order when sample is NULL, then s must equal n), canonical FP32

@@ -1,7 +1,8 @@
 """GB300 (sm_103a) kNN-graph construction by two-means trees
 (Zhao, Yang, Deng, arXiv 1701.08475, Sec. 3.1, Alg. 1) with neighbour-of-
-neighbour refinement, and the enhanced hill-climbing search over the graph
-(Sec. 3.2, Alg. 2).
+neighbour refinement, the enhanced hill-climbing search over the graph
+(Sec. 3.2, Alg. 2), and the residue-quantisation inverted index that seeds it
+(Sec. 4).
 
 A thin binding of the C ABI declared in include/knng.h: every function has
 the name of its C entry point, marshals tensors to plain pointers and sizes,
@@ -22,6 +23,9 @@ from ._lib import (  # noqa: F401
     BuildPlan,
     knng_exact,
     knng_search,
+    knng_rvq_train,
+    knng_rvq_index,
+    knng_rvq_seeds,
     knng_exact_noalloc,
     knng_leaf_update,
     knng_partition,

@@ -78,6 +78,9 @@ def load():
             "knng_leaf_update": (i32, [P, i64, i32, i32, P, P, i64, P, P, P]),
             "knng_exact": (i32, [P, i64, i32, i32, P, i64, P, P, P]),
             "knng_search": (i32, [P, i64, i32, P, i32, P, i64, P, i32, i32, i32, P, P, P]),
+            "knng_rvq_train": (i32, [P, i64, i32, i32, i32, i32, u64, P, P, P]),
+            "knng_rvq_index": (i32, [P, i64, i32, P, i32, P, i32, P, P, P, P]),
+            "knng_rvq_seeds": (i32, [P, i32, P, i32, i32, P, P, i64, P, i64, i32, i32, P, P]),
             "knng_exact_noalloc": (i32, [P, i64, i32, i32, P, i64, P, P, P]),
             "knng_recall": (i32, [P, P, P, P, P, i64, i32, P, P, P]),
             "knng_last_error": (ctypes.c_char_p, []),
@@ -331,6 +334,53 @@ def knng_search(data, graph_ids, queries, seeds, t0, ks, stream=None):
         _check(load().knng_search(_ptr(data), n, D, _ptr(graph_ids), graph_ids.shape[1], _ptr(queries), m,
                                   _ptr(seeds), seeds.shape[1], t0, ks, _ptr(ids), _ptr(d), s))
     return ids, d
+
+
+def knng_rvq_train(data, W1=256, W2=256, iters=10, seed=0, stream=None):
+    """Two-stage residue vector quantisation vocabularies (Sec. 4.1, Eqn. 1),
+    Lloyd's k-means per stage: (words1 W1 x D, words2 W2 x D)."""
+    data = _contig(data, "float32")
+    n, D = data.shape
+    w1 = _empty_like_input(data, (W1, D), "float32")
+    w2 = _empty_like_input(data, (W2, D), "float32")
+    with _DeviceCtx(data, stream) as s:
+        _check(load().knng_rvq_train(_ptr(data), n, D, W1, W2, iters, seed & (2**64 - 1), _ptr(w1), _ptr(w2), s))
+    return w1, w2
+
+
+def knng_rvq_index(data, words1, words2, stream=None):
+    """The inverted index of Sec. 4.2: (codes n x 2, list_offsets W1*W2 + 1,
+    list_ids n), lists keyed by c1 * W2 + c2, ids ascending."""
+    data = _contig(data, "float32")
+    words1 = _contig(words1, "float32")
+    words2 = _contig(words2, "float32")
+    n, D = data.shape
+    W1, W2 = words1.shape[0], words2.shape[0]
+    codes = _empty_like_input(data, (n, 2), "int32")
+    off = _empty_like_input(data, (W1 * W2 + 1,), "int32")
+    ids = _empty_like_input(data, (n,), "int32")
+    with _DeviceCtx(data, stream) as s:
+        _check(load().knng_rvq_index(_ptr(data), n, D, _ptr(words1), W1, _ptr(words2), W2, _ptr(codes), _ptr(off),
+                                     _ptr(ids), s))
+    return codes, off, ids
+
+
+def knng_rvq_seeds(words1, words2, list_offsets, list_ids, queries, probe1, s, stream=None):
+    """Seeds of Alg. 2 from the inverted index (Sec. 4.2, Eqns. 2 and 3, the
+    cascaded pruning keeping probe1 stage-1 words): m x s ids, -1 padded."""
+    words1 = _contig(words1, "float32")
+    words2 = _contig(words2, "float32")
+    list_offsets = _contig(list_offsets, "int32")
+    list_ids = _contig(list_ids, "int32")
+    queries = _contig(queries, "float32")
+    W1, D = words1.shape
+    W2 = words2.shape[0]
+    m = queries.shape[0]
+    out = _empty_like_input(queries, (m, s), "int32")
+    with _DeviceCtx(queries, stream) as st:
+        _check(load().knng_rvq_seeds(_ptr(words1), W1, _ptr(words2), W2, D, _ptr(list_offsets), _ptr(list_ids),
+                                     list_ids.shape[0], _ptr(queries), m, probe1, s, _ptr(out), st))
+    return out
 
 
 def knng_exact(data, k, sample=None, stream=None):

@@ -871,6 +871,35 @@ struct knng_plan {
     cudaGraphExec_t exec = nullptr;
 };
 
+namespace {
+// Validation shared by the three residue-quantisation entries.
+void validate_vocab(int W1, int W2, int D) {
+    if (D < 1) fail(KNNG_EINVAL, "D = %d < 1", D);
+    if (W1 < 1 || W1 > 256 || W2 < 1 || W2 > 256) fail(KNNG_EINVAL, "W1 = %d, W2 = %d outside [1, 256]", W1, W2);
+}
+
+// One stage of Lloyd's k-means on the device (Sec. 4.1): the vectors are the
+// points, or their residues against W1 (codes c1) when W1 is given.
+void rvq_lloyd(const float* X, int64_t N, int D, const float* W1, const int32_t* c1, int W, int iters,
+               uint64_t seed, int stage, float* words, int32_t* codes, int32_t* order, int32_t* hist, int32_t* gofs,
+               int32_t* scan_tmp, int64_t* dpos, std::vector<int64_t>& hpos, cudaStream_t s) {
+    const uint64_t h0 = splitmix64(seed ^ ((uint64_t)stage << 32));
+    hpos.assign(W, 0);
+    for (int c = 0; c < W; ++c) {
+        const int64_t lo = (int64_t)c * N / W, hi = (int64_t)(c + 1) * N / W;
+        hpos[c] = lo + (int64_t)(splitmix64(h0 ^ (uint64_t)c) % (uint64_t)(hi - lo));
+    }
+    cuda_check(cudaMemcpyAsync(dpos, hpos.data(), sizeof(int64_t) * W, cudaMemcpyHostToDevice, s), "positions");
+    launch_rvq_init(X, D, W1, c1, 1, dpos, W, words, s);
+    const int nb = digit_sort_blocks(N);
+    for (int it = 0; it < iters; ++it) {
+        launch_rvq_assign(X, N, D, W1, c1, 1, words, W, codes, 1, s);
+        launch_digit_sort(nullptr, N, codes, 1, order, hist, gofs, scan_tmp, s);
+        launch_rvq_update(X, N, D, W1, c1, 1, order, gofs, nb, W, words, s);
+    }
+}
+}  // namespace
+
 extern "C" {
 
 int knng_plan_create(const float* data, int64_t n, int D, const knng_params* p, int32_t* out_ids, float* out_dists,
@@ -1193,6 +1222,156 @@ int knng_search(const float* data, int64_t n, int D, const int32_t* graph_ids, i
                           t0, ks, tab, cl, oi.dev, od.dev, st);
         download(oi, st);
         download(od, st);
+        cuda_check(cudaGetLastError(), "kernel launch");
+        check_status(status, st);
+    });
+}
+
+int knng_rvq_train(const float* data, int64_t n, int D, int W1, int W2, int iters, uint64_t seed, float* words1,
+                   float* words2, void* stream) {
+    return guarded([&] {
+        validate_vocab(W1, W2, D);
+        if (!data || n < 1 || n > INT32_MAX) fail(KNNG_EINVAL, "data NULL or n out of range");
+        if (W1 > n || W2 > n) fail(KNNG_EINVAL, "more words than points");
+        if (iters < 0) fail(KNNG_EINVAL, "iters < 0");
+        if (!words1 || !words2) fail(KNNG_EINVAL, "an output pointer is NULL");
+        cudaStream_t st = (cudaStream_t)stream;
+        const size_t nh = digit_sort_hist_ints(n);
+        Workspace ws;
+        DevBuf<float> X, o1, o2;
+        int32_t *codes = nullptr, *c1 = nullptr, *order = nullptr, *hist = nullptr, *gofs = nullptr, *tmp = nullptr;
+        int64_t* pos = nullptr;
+        int* status = nullptr;
+        for (int ps = 0; ps < 2; ++ps) {
+            ws.used = 0;
+            bind(ws, X, data, (size_t)n * D, ps);
+            bind(ws, o1, (const float*)words1, (size_t)W1 * D, ps);
+            bind(ws, o2, (const float*)words2, (size_t)W2 * D, ps);
+            codes = ws.take<int32_t>(n);
+            c1 = ws.take<int32_t>(n);
+            order = ws.take<int32_t>(n);
+            hist = ws.take<int32_t>(nh);
+            gofs = ws.take<int32_t>(nh + 1);
+            tmp = ws.take<int32_t>(scan_tmp_ints((int64_t)nh));
+            pos = ws.take<int64_t>(256);
+            status = ws.take<int>(4);
+            if (ps == 0) ws.allocate(st);
+        }
+        cuda_check(cudaMemsetAsync(status, 0, 4 * sizeof(int), st), "status clear");
+        upload(X, st);
+        launch_check_finite(X.dev, n * (int64_t)D, status, st);
+        std::vector<int64_t> hpos;
+        rvq_lloyd(X.dev, n, D, nullptr, nullptr, W1, iters, seed, 1, o1.dev, codes, order, hist, gofs, tmp, pos, hpos,
+                  st);
+        launch_rvq_assign(X.dev, n, D, nullptr, nullptr, 1, o1.dev, W1, c1, 1, st);
+        rvq_lloyd(X.dev, n, D, o1.dev, c1, W2, iters, seed, 2, o2.dev, codes, order, hist, gofs, tmp, pos, hpos, st);
+        download(o1, st);
+        download(o2, st);
+        cuda_check(cudaGetLastError(), "kernel launch");
+        check_status(status, st);
+    });
+}
+
+int knng_rvq_index(const float* data, int64_t n, int D, const float* words1, int W1, const float* words2, int W2,
+                   int32_t* codes, int32_t* list_offsets, int32_t* list_ids, void* stream) {
+    return guarded([&] {
+        validate_vocab(W1, W2, D);
+        if (!data || n < 1 || n > INT32_MAX) fail(KNNG_EINVAL, "data NULL or n out of range");
+        if (!words1 || !words2 || !codes || !list_offsets || !list_ids) fail(KNNG_EINVAL, "a pointer is NULL");
+        cudaStream_t st = (cudaStream_t)stream;
+        const int64_t nk = (int64_t)W1 * W2;
+        const size_t nh = digit_sort_hist_ints(n);
+        Workspace ws;
+        DevBuf<float> X, w1, w2;
+        DevBuf<int32_t> cd, off, li;
+        int32_t *order = nullptr, *hist = nullptr, *gofs = nullptr, *tmp = nullptr, *cnt = nullptr;
+        int* status = nullptr;
+        for (int ps = 0; ps < 2; ++ps) {
+            ws.used = 0;
+            bind(ws, X, data, (size_t)n * D, ps);
+            bind(ws, w1, words1, (size_t)W1 * D, ps);
+            bind(ws, w2, words2, (size_t)W2 * D, ps);
+            bind(ws, cd, (const int32_t*)codes, (size_t)n * 2, ps);
+            bind(ws, off, (const int32_t*)list_offsets, (size_t)nk + 1, ps);
+            bind(ws, li, (const int32_t*)list_ids, (size_t)n, ps);
+            order = ws.take<int32_t>(n);
+            hist = ws.take<int32_t>(nh);
+            gofs = ws.take<int32_t>(nh + 1);
+            tmp = ws.take<int32_t>(std::max(scan_tmp_ints((int64_t)nh), scan_tmp_ints(nk)));
+            cnt = ws.take<int32_t>(nk);
+            status = ws.take<int>(4);
+            if (ps == 0) ws.allocate(st);
+        }
+        cuda_check(cudaMemsetAsync(status, 0, 4 * sizeof(int), st), "status clear");
+        upload(X, st);
+        upload(w1, st);
+        upload(w2, st);
+        launch_check_finite(X.dev, n * (int64_t)D, status, st);
+        launch_check_finite(w1.dev, (int64_t)W1 * D, status, st);
+        launch_check_finite(w2.dev, (int64_t)W2 * D, status, st);
+        launch_rvq_assign(X.dev, n, D, nullptr, nullptr, 2, w1.dev, W1, cd.dev, 2, st);
+        launch_rvq_assign(X.dev, n, D, w1.dev, cd.dev, 2, w2.dev, W2, cd.dev + 1, 2, st);
+        launch_digit_sort(nullptr, n, cd.dev + 1, 2, order, hist, gofs, tmp, st);   // by c2
+        launch_digit_sort(order, n, cd.dev, 2, li.dev, hist, gofs, tmp, st);        // then by c1, stable
+        cuda_check(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nk, st), "count clear");
+        launch_rvq_key_count(cd.dev, n, W2, cnt, st);
+        launch_scan(cnt, off.dev, nk, tmp, st);
+        download(cd, st);
+        download(off, st);
+        download(li, st);
+        cuda_check(cudaGetLastError(), "kernel launch");
+        check_status(status, st);
+    });
+}
+
+int knng_rvq_seeds(const float* words1, int W1, const float* words2, int W2, int D, const int32_t* list_offsets,
+                   const int32_t* list_ids, int64_t n, const float* queries, int64_t m, int probe1, int s,
+                   int32_t* seeds, void* stream) {
+    return guarded([&] {
+        validate_vocab(W1, W2, D);
+        if (n < 0 || n > INT32_MAX || m < 0 || s < 0) fail(KNNG_EINVAL, "n, m or s out of range");
+        if (probe1 < 1 || probe1 > W1) fail(KNNG_EINVAL, "probe1 = %d outside [1, W1]", probe1);
+        if (probe1 * W2 > 8192) fail(KNNG_EINVAL, "probe1 * W2 = %d above 8192", probe1 * W2);
+        if (rvq_seeds_smem(probe1, W2, D) > 200 * 1024) fail(KNNG_EINVAL, "D = %d too large for the seeds", D);
+        if (m == 0 || s == 0) return;
+        if (!words1 || !words2 || !list_offsets || (n > 0 && !list_ids) || !queries || !seeds)
+            fail(KNNG_EINVAL, "a pointer is NULL");
+        cudaStream_t st = (cudaStream_t)stream;
+        const int64_t nk = (int64_t)W1 * W2;
+        Workspace ws;
+        DevBuf<float> w1, w2, Qb;
+        DevBuf<int32_t> off, li, Sb;
+        float *n1 = nullptr, *n2 = nullptr, *x12 = nullptr, *w1T = nullptr, *w2T = nullptr;
+        int* status = nullptr;
+        for (int ps = 0; ps < 2; ++ps) {
+            ws.used = 0;
+            bind(ws, w1, words1, (size_t)W1 * D, ps);
+            bind(ws, w2, words2, (size_t)W2 * D, ps);
+            bind(ws, off, list_offsets, (size_t)nk + 1, ps);
+            bind(ws, li, list_ids, (size_t)n, ps);
+            bind(ws, Qb, queries, (size_t)m * D, ps);
+            bind(ws, Sb, (const int32_t*)seeds, (size_t)m * s, ps);
+            n1 = ws.take<float>(W1);
+            n2 = ws.take<float>(W2);
+            x12 = ws.take<float>((size_t)nk);
+            w1T = ws.take<float>((size_t)W1 * D);
+            w2T = ws.take<float>((size_t)W2 * D);
+            status = ws.take<int>(4);
+            if (ps == 0) ws.allocate(st);
+        }
+        cuda_check(cudaMemsetAsync(status, 0, 4 * sizeof(int), st), "status clear");
+        upload(w1, st);
+        upload(w2, st);
+        upload(off, st);
+        upload(li, st);
+        upload(Qb, st);
+        launch_check_finite(w1.dev, (int64_t)W1 * D, status, st);
+        launch_check_finite(w2.dev, (int64_t)W2 * D, status, st);
+        launch_check_finite(Qb.dev, m * (int64_t)D, status, st);
+        launch_check_offsets(off.dev, nk, n, status, st);
+        launch_rvq_tables(w1.dev, W1, w2.dev, W2, D, n1, n2, x12, w1T, w2T, st);
+        launch_rvq_seeds(w1T, W1, w2T, W2, D, n1, n2, x12, off.dev, li.dev, Qb.dev, m, probe1, s, Sb.dev, status, st);
+        download(Sb, st);
         cuda_check(cudaGetLastError(), "kernel launch");
         check_status(status, st);
     });

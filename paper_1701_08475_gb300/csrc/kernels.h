@@ -221,6 +221,34 @@ void launch_check_ids(const int32_t* ids, int64_t count, int64_t lo, int64_t hi,
 void launch_unpack(const uint64_t* G, int32_t* ids, float* d, int64_t count, cudaStream_t s, int64_t id_offset = 0);
 
 // ---------------------------------------------------------------- exact / recall (K7)
+// Residue vector quantisation and its inverted index (rvq.cu, Sec. 4).
+// codes of the N vectors v_i = X_i, or X_i - W1[c1[i * c1_stride]] when W1 is
+// given, against W <= 256 words: out[i * out_stride].
+void launch_rvq_assign(const float* X, int64_t N, int D, const float* W1, const int32_t* c1, int c1_stride,
+                       const float* words, int W, int32_t* out, int out_stride, cudaStream_t s);
+// Stable sort of the ids in[0..n) (0..n-1 when in is null) by the 8-bit digit
+// key[id * kstride] into out.  hist: digit_sort_hist_ints(n) ints; gofs: one
+// more; gofs[d * digit_sort_blocks(n)] is where digit d starts.
+int digit_sort_blocks(int64_t n);
+size_t digit_sort_hist_ints(int64_t n);
+void launch_digit_sort(const int32_t* in, int64_t n, const int32_t* key, int kstride, int32_t* out, int32_t* hist,
+                       int32_t* gofs, int32_t* scan_tmp, cudaStream_t s);
+// words[c] = FP64 mean (ascending vector order) of the vectors of word c, in
+// FP32; words without members keep their value.
+void launch_rvq_update(const float* X, int64_t N, int D, const float* W1, const int32_t* c1, int c1_stride,
+                       const int32_t* order, const int32_t* gofs, int nb, int W, float* words, cudaStream_t s);
+void launch_rvq_init(const float* X, int D, const float* W1, const int32_t* c1, int c1_stride, const int64_t* pos,
+                     int W, float* words, cudaStream_t s);
+void launch_rvq_key_count(const int32_t* codes, int64_t n, int W2, int32_t* cnt, cudaStream_t s);
+void launch_check_offsets(const int32_t* off, int64_t nk, int64_t n, int* status, cudaStream_t s);
+void launch_rvq_tables(const float* w1, int W1, const float* w2, int W2, int D, float* n1, float* n2, float* x12,
+                       float* w1T, float* w2T, cudaStream_t s);
+int rvq_seed_keys(int probe1, int W2);
+size_t rvq_seeds_smem(int probe1, int W2, int D);
+void launch_rvq_seeds(const float* w1T, int W1, const float* w2T, int W2, int D, const float* n1, const float* n2,
+                      const float* x12, const int32_t* off, const int32_t* ids, const float* Q, int64_t m, int probe1,
+                      int s_seeds, int32_t* S, const int* status, cudaStream_t s);
+
 // Enhanced hill-climbing search (search.cu): queries [q0, q1) of Q against
 // the graph G (n x k ids), seeds S (s per query), t0 iterations, ks <= 32
 // results per query; tab: (q1 - q0) << cap_log2 ints of visited tables.

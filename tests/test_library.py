@@ -78,3 +78,26 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
         knng.knng_build(X, k=3, leaf_max=7)        # leaf_max < 2(k+1)
     with pytest.raises(knng.KnngError):
         knng.knng_build_ex(X, knng.default_params(k=3, leaf_max=64, precision=7))
+
+
+def test_rvq_arguments_are_rejected_without_a_gpu(lib):
+    import numpy as np
+    import paper_1701_08475_gb300 as knng
+    assert {"knng_rvq_train", "knng_rvq_index", "knng_rvq_seeds", "knng_search"} <= set(_declared())
+    X = np.zeros((10, 4), np.float32)
+    for W1, W2 in ((0, 4), (300, 4), (11, 4), (4, 257)):
+        with pytest.raises(knng.KnngError) as e:
+            knng.knng_rvq_train(X, W1=W1, W2=W2)
+        assert e.value.code == -1
+    with pytest.raises(knng.KnngError):
+        knng.knng_rvq_train(X, W1=4, W2=4, iters=-1)
+    w = np.zeros((4, 4), np.float32)
+    off = np.zeros(17, np.int32)
+    ids = np.zeros(0, np.int32)
+    with pytest.raises(knng.KnngError):
+        knng.knng_rvq_seeds(w, w, off, ids, X, 5, 3)          # probe1 > W1
+    with pytest.raises(knng.KnngError):
+        knng.knng_rvq_seeds(w, w, off, ids, X, 0, 3)          # probe1 < 1
+    big = np.zeros((256, 4), np.float32)
+    with pytest.raises(knng.KnngError):
+        knng.knng_rvq_seeds(big, big, np.zeros(65537, np.int32), ids, X, 33, 3)   # 33 * 256 keys > 8192
