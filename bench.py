@@ -264,9 +264,9 @@ def search_measure(knng, X, Xd, G, dev, stream, m=10000, t0=12, ks=20, n_seeds=3
     """The enhanced hill-climbing search (Alg. 2) over the built graph: m
     queries (input points moved by N(0, 4^2) noise, rounded and clipped for
     integer data), timed with CUDA events; recall against float64 brute force
-    on n_check of them.  Seeds: random (the paper's baseline) and random plus
-    one point of the query's own cluster (a stand-in for the inverted-index
-    seeding of Sec. 4, which is not built)."""
+    on n_check of them.  Seeds: random (the paper's baseline); random plus one
+    point of the query's own cluster; and the inverted index of Sec. 4 (its
+    training, indexing and seeding timed too)."""
     import torch
     n, D = X.shape
     rng = np.random.default_rng(17)
@@ -288,8 +288,29 @@ def search_measure(knng, X, Xd, G, dev, stream, m=10000, t0=12, ks=20, n_seeds=3
     del Xd64, part
     out = {"queries": m, "t0": t0, "ks": ks, "seeds_per_query": n_seeds,
            "queries_from": "input points moved by N(0, 4^2) noise", "truth": "float64 brute force, %d queries" % n_check}
-    for name, S in (("random_seeds", S_rand), ("near_seed", S_near)):
-        Sd = torch.from_numpy(S).to(dev)
+
+    def timed(fn, reps=3):
+        with torch.cuda.stream(stream):
+            r = fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                r = fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / reps
+
+    # the inverted index of Sec. 4: vocabularies from a 100,000-row prefix,
+    # the whole input indexed, seeds from the lists (Eqns. 2-3)
+    n_train, W, iters, probe1 = min(n, 100000), 256, 8, 16
+    (w1, w2), train_ms = timed(lambda: knng.knng_rvq_train(Xd[:n_train], W, W, iters, seed=5, stream=stream), 1)
+    (_, off, lids), index_ms = timed(lambda: knng.knng_rvq_index(Xd, w1, w2, stream=stream), 1)
+    S_ivf, seeds_ms = timed(lambda: knng.knng_rvq_seeds(w1, w2, off, lids, Qd, probe1, n_seeds, stream=stream))
+    out["index"] = {"train_rows": n_train, "W1": W, "W2": W, "iters": iters, "probe1": probe1,
+                    "train_ms": round(train_ms, 3), "index_ms": round(index_ms, 3), "seeds_ms": round(seeds_ms, 3),
+                    "nonempty_lists": int((off[1:] > off[:-1]).sum().item())}
+    for name, S in (("random_seeds", S_rand), ("near_seed", S_near), ("ivf_seeds", S_ivf)):
+        Sd = torch.from_numpy(S).to(dev) if isinstance(S, np.ndarray) else S
         with torch.cuda.stream(stream):
             knng.knng_search(Xd, G, Qd, Sd, t0, ks, stream=stream)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -304,6 +325,8 @@ def search_measure(knng, X, Xd, G, dev, stream, m=10000, t0=12, ks=20, n_seeds=3
         rk = float(np.mean([len(set(got[i].tolist()) & set(truth[i].tolist())) / ks for i in range(n_check)]))
         out[name] = {"queries_per_s": round(m / (ms * 1e-3), 1), "ms": round(ms, 3), "recall_at_1": round(r1, 4),
                      "recall_at_ks": round(rk, 4)}
+        if name == "ivf_seeds":   # seeds and search together
+            out[name]["queries_per_s_with_seeds"] = round(m / ((ms + seeds_ms) * 1e-3), 1)
     return out
 
 

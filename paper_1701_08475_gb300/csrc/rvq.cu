@@ -357,8 +357,9 @@ __device__ int block_excl_scan(int v, int* wsum, int* total) {
 
 size_t seeds_smem(int P, int D) { return (size_t)P * 8 + 256 * 8 + (kSdT / 32 + 1) * 4 + 256 * 4 + (size_t)D * 4; }
 
-// One CTA per query.  P: the candidate keys (probe1 * W2) rounded up to a
-// power of two, at least kSdT.
+// One CTA per query.  P: room for the candidate keys (probe1 * W2 rounded up
+// to a power of two, at least kSdT); only those with a non-empty list are
+// ranked.
 __global__ void __launch_bounds__(kSdT) k9_seeds(const float* __restrict__ w1T, int W1,
                                                 const float* __restrict__ w2T, int W2, int D,
                                                 const float* __restrict__ n1, const float* __restrict__ n2,
@@ -395,38 +396,55 @@ __global__ void __launch_bounds__(kSdT) k9_seeds(const float* __restrict__ w1T, 
     }
     __syncthreads();
     block_bitonic(t1, 256);
-    // term 2 for the kept words' keys, d(q, I) = term 1 + term 2 (Eqn. 2)
+    // term 2 for the kept words' keys, d(q, I) = term 1 + term 2 (Eqn. 2).
+    // Keys of empty lists add no seed: only the others are kept (in any
+    // order, the sort below fixes it), with their list's start and length.
+    __shared__ int nkeep;
+    if (tid == 0) nkeep = 0;
+    __syncthreads();
     const int nc = p1 * W2;
-    for (int e = tid; e < P; e += kSdT) {
+    for (int e0 = 0; e0 < nc; e0 += kSdT) {
+        const int e = e0 + tid;
         uint64_t key = kEmptyKey;
         if (e < nc) {
             const int r = e / W2, b = e - r * W2;
             const uint64_t kk = t1[r];
-            const int a = (int)key_id(kk);
-            const float t2 =
-                __fmaf_rn(-2.f, qw2[b], __fmaf_rn(2.f, __ldg(x12 + (int64_t)a * W2 + b), __ldg(n2 + b)));
-            const float d = __fadd_rn(__fadd_rn(key_dist(kk), t2), 0.f);
-            key = make_key(d, (uint32_t)(a * W2 + b));
+            const int a = (int)key_id(kk), I = a * W2 + b;
+            if (__ldg(off + I + 1) > __ldg(off + I)) {
+                const float t2 =
+                    __fmaf_rn(-2.f, qw2[b], __fmaf_rn(2.f, __ldg(x12 + (int64_t)a * W2 + b), __ldg(n2 + b)));
+                const float d = __fadd_rn(__fadd_rn(key_dist(kk), t2), 0.f);
+                key = make_key(d, (uint32_t)I);
+            }
         }
-        cand[e] = key;
+        const unsigned ball = __ballot_sync(0xffffffffu, key != kEmptyKey);
+        int base = 0;
+        if ((tid & 31) == 0 && ball) base = atomicAdd(&nkeep, __popc(ball));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (key != kEmptyKey) cand[base + __popc(ball & ((1u << (tid & 31)) - 1u))] = key;
     }
     __syncthreads();
-    block_bitonic(cand, P);
+    const int nk = nkeep;
+    int Pk = 2;
+    while (Pk < nk) Pk <<= 1;
+    for (int e = nk + tid; e < Pk; e += kSdT) cand[e] = kEmptyKey;
+    __syncthreads();
+    block_bitonic(cand, Pk);
     // the lists in that order: thread t walks keys [t * per, (t + 1) * per)
-    const int per = P / kSdT;
+    const int per = (Pk + kSdT - 1) / kSdT;
     int mine = 0;
     for (int u = 0; u < per; ++u) {
-        const uint64_t kk = cand[tid * per + u];
-        if (kk == kEmptyKey) break;
-        const int I = (int)key_id(kk);
+        const int e = tid * per + u;
+        if (e >= nk) break;
+        const int I = (int)key_id(cand[e]);
         mine += __ldg(off + I + 1) - __ldg(off + I);
     }
     __shared__ int total;
     int pos = block_excl_scan(mine, wsum, &total);
     for (int u = 0; u < per && pos < s; ++u) {
-        const uint64_t kk = cand[tid * per + u];
-        if (kk == kEmptyKey) break;
-        const int I = (int)key_id(kk);
+        const int e = tid * per + u;
+        if (e >= nk) break;
+        const int I = (int)key_id(cand[e]);
         const int a0 = __ldg(off + I), a1 = __ldg(off + I + 1);
         for (int t = a0; t < a1 && pos < s; ++t) S[qi * s + pos++] = __ldg(ids + t);
     }

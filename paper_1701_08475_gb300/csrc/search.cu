@@ -37,9 +37,27 @@ __device__ __forceinline__ bool visit(int32_t* tab, int cap_log2, int32_t id) {
 }
 
 // Canonical FP32 squared l2 of row x against the query q (dims ascending,
-// t = x_j - q_j, acc = fmaf(t, t, acc)).
+// t = x_j - q_j, acc = fmaf(t, t, acc)).  V4: x and q 16-byte aligned and D a
+// multiple of 4, so both are read four dims at a time (the same chain).
+template <bool V4>
 __device__ __forceinline__ float dist_to_query(const float* __restrict__ x, const float* q, int D) {
     float acc = 0.f;
+    if (V4) {
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        const float4* q4 = reinterpret_cast<const float4*>(q);
+        for (int j = 0; j < D / 4; ++j) {
+            const float4 a = __ldg(x4 + j), b = q4[j];
+            float t = __fsub_rn(a.x, b.x);
+            acc = __fmaf_rn(t, t, acc);
+            t = __fsub_rn(a.y, b.y);
+            acc = __fmaf_rn(t, t, acc);
+            t = __fsub_rn(a.z, b.z);
+            acc = __fmaf_rn(t, t, acc);
+            t = __fsub_rn(a.w, b.w);
+            acc = __fmaf_rn(t, t, acc);
+        }
+        return acc;
+    }
     for (int j = 0; j < D; ++j) {
         const float t = __fsub_rn(__ldg(x + j), q[j]);
         acc = __fmaf_rn(t, t, acc);
@@ -47,6 +65,7 @@ __device__ __forceinline__ float dist_to_query(const float* __restrict__ x, cons
     return acc;
 }
 
+template <bool V4>
 __global__ void __launch_bounds__(32 * kSearchWarps) k8_search(const float* __restrict__ X, int64_t n, int D,
                                                               const int32_t* __restrict__ G, int k,
                                                               const float* __restrict__ Q, int64_t q0, int64_t q1,
@@ -54,7 +73,8 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k8_search(const float* __re
                                                               int32_t* __restrict__ tab, int cap_log2,
                                                               int32_t* __restrict__ out_ids,
                                                               float* __restrict__ out_d) {
-    extern __shared__ float qs[];  // [kSearchWarps][D]
+    extern __shared__ float4 qs4[];  // [kSearchWarps][D]
+    float* qs = reinterpret_cast<float*>(qs4);
     __shared__ uint64_t scratch[kSearchWarps][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t qi = q0 + (int64_t)blockIdx.x * kSearchWarps + w;
@@ -68,7 +88,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k8_search(const float* __re
     // every lane offers one id (or -1): the fresh ones are visited and merged
     auto offer = [&](int32_t id) {
         const bool fresh = id >= 0 && id < n && visit(T, cap_log2, id);
-        const uint64_t key = fresh ? make_key(dist_to_query(X + (int64_t)id * D, q, D), (uint32_t)id) : kEmptyKey;
+        const uint64_t key = fresh ? make_key(dist_to_query<V4>(X + (int64_t)id * D, q, D), (uint32_t)id) : kEmptyKey;
         uint64_t cand[1] = {key}, out;
         bool changed;
         if (!warp_merge_few<1>(cand, list, ks, sc, out, changed)) {
@@ -118,10 +138,16 @@ void launch_search(const float* X, int64_t n, int D, const int32_t* G, int k, co
     LaunchScope ls("k8_search", st, (double)m * (visits * (D * 4.0 + 8.0) + (double)t0 * ks * k * 4.0 + D * 4.0),
                    (double)m * visits * 3.0 * D);
     const size_t smem = (size_t)kSearchWarps * D * sizeof(float);
-    cudaFuncSetAttribute(k8_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t grid = (m + kSearchWarps - 1) / kSearchWarps;
-    k8_search<<<(unsigned)grid, 32 * kSearchWarps, smem, st>>>(X, n, D, G, k, Q, q0, q1, S, s, t0, ks, tab, cap_log2,
-                                                               out_ids, out_d);
+    if (D % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+        cudaFuncSetAttribute(k8_search<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k8_search<true><<<(unsigned)grid, 32 * kSearchWarps, smem, st>>>(X, n, D, G, k, Q, q0, q1, S, s, t0, ks, tab,
+                                                                         cap_log2, out_ids, out_d);
+    } else {
+        cudaFuncSetAttribute(k8_search<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k8_search<false><<<(unsigned)grid, 32 * kSearchWarps, smem, st>>>(X, n, D, G, k, Q, q0, q1, S, s, t0, ks,
+                                                                          tab, cap_log2, out_ids, out_d);
+    }
 }
 
 }  // namespace knng
