@@ -309,6 +309,20 @@ def search_measure(knng, X, Xd, G, dev, stream, m=10000, t0=12, ks=20, n_seeds=3
     out["index"] = {"train_rows": n_train, "W1": W, "W2": W, "iters": iters, "probe1": probe1,
                     "train_ms": round(train_ms, 3), "index_ms": round(index_ms, 3), "seeds_ms": round(seeds_ms, 3),
                     "nonempty_lists": int((off[1:] > off[:-1]).sum().item())}
+    # per-kernel device time of one training, indexing and seeding (events
+    # around every launch: a separate, slower run)
+    knng.stats_reset()
+    knng.stats_enable(True, timing=True)
+    with torch.cuda.stream(stream):
+        knng.knng_rvq_train(Xd[:n_train], W, W, iters, seed=5, stream=stream)
+        knng.knng_rvq_index(Xd, w1, w2, stream=stream)
+        knng.knng_rvq_seeds(w1, w2, off, lids, Qd, probe1, n_seeds, stream=stream)
+        knng.knng_search(Xd, G, Qd, S_ivf, t0, ks, stream=stream)
+    torch.cuda.synchronize()
+    knng.stats_enable(False)
+    st = knng.stats()
+    out["index"]["kernels_ms"] = {k: round(v["ms"], 3) for k, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])
+                                  if v["ms"] >= 0.05}
     for name, S in (("random_seeds", S_rand), ("near_seed", S_near), ("ivf_seeds", S_ivf)):
         Sd = torch.from_numpy(S).to(dev) if isinstance(S, np.ndarray) else S
         with torch.cuda.stream(stream):

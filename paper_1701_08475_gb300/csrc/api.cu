@@ -1241,10 +1241,12 @@ int knng_rvq_train(const float* data, int64_t n, int D, int W1, int W2, int iter
         DevBuf<float> X, o1, o2;
         int32_t *codes = nullptr, *c1 = nullptr, *order = nullptr, *hist = nullptr, *gofs = nullptr, *tmp = nullptr;
         int64_t* pos = nullptr;
+        float* R = nullptr;
         int* status = nullptr;
         for (int ps = 0; ps < 2; ++ps) {
             ws.used = 0;
             bind(ws, X, data, (size_t)n * D, ps);
+            R = ws.take<float>((size_t)n * D);
             bind(ws, o1, (const float*)words1, (size_t)W1 * D, ps);
             bind(ws, o2, (const float*)words2, (size_t)W2 * D, ps);
             codes = ws.take<int32_t>(n);
@@ -1264,7 +1266,8 @@ int knng_rvq_train(const float* data, int64_t n, int D, int W1, int W2, int iter
         rvq_lloyd(X.dev, n, D, nullptr, nullptr, W1, iters, seed, 1, o1.dev, codes, order, hist, gofs, tmp, pos, hpos,
                   st);
         launch_rvq_assign(X.dev, n, D, nullptr, nullptr, 1, o1.dev, W1, c1, 1, st);
-        rvq_lloyd(X.dev, n, D, o1.dev, c1, W2, iters, seed, 2, o2.dev, codes, order, hist, gofs, tmp, pos, hpos, st);
+        launch_rvq_residues(X.dev, n, D, o1.dev, c1, R, st);   // stage 2 trains on the residues
+        rvq_lloyd(R, n, D, nullptr, nullptr, W2, iters, seed, 2, o2.dev, codes, order, hist, gofs, tmp, pos, hpos, st);
         download(o1, st);
         download(o2, st);
         cuda_check(cudaGetLastError(), "kernel launch");

@@ -239,6 +239,9 @@ void launch_rvq_update(const float* X, int64_t N, int D, const float* W1, const 
                        const int32_t* order, const int32_t* gofs, int nb, int W, float* words, cudaStream_t s);
 void launch_rvq_init(const float* X, int D, const float* W1, const int32_t* c1, int c1_stride, const int64_t* pos,
                      int W, float* words, cudaStream_t s);
+// R = X - W1[c1] row by row (FP32): the stage-2 training vectors.
+void launch_rvq_residues(const float* X, int64_t N, int D, const float* W1, const int32_t* c1, float* R,
+                         cudaStream_t s);
 void launch_rvq_key_count(const int32_t* codes, int64_t n, int W2, int32_t* cnt, cudaStream_t s);
 void launch_check_offsets(const int32_t* off, int64_t nk, int64_t n, int* status, cudaStream_t s);
 void launch_rvq_tables(const float* w1, int W1, const float* w2, int W2, int D, float* n1, float* n2, float* x12,

@@ -217,8 +217,8 @@ __global__ void __launch_bounds__(kDsThreads) k9_digit_scatter(const int32_t* __
 // ---------------------------------------------------------------- word update
 // One warp per (word, 32 dims): the FP64 sum of the members in ascending
 // vector order (the sorted run order[gofs[c * nb] .. gofs[(c + 1) * nb])),
-// divided by the count, rounded to FP32.  Loads run four members ahead of the
-// additions; the additions keep their order.
+// divided by the count, rounded to FP32.  Loads run eight members ahead of
+// the additions; the additions keep their order.
 template <bool RES>
 __global__ void __launch_bounds__(128) k9_update(const float* __restrict__ X, int D, const float* __restrict__ W1,
                                                 const int32_t* __restrict__ c1, int c1_stride,
@@ -238,12 +238,12 @@ __global__ void __launch_bounds__(128) k9_update(const float* __restrict__ X, in
     };
     double acc = 0.0;
     int t = a;
-    for (; t + 4 <= b; t += 4) {
-        float v[4];
+    for (; t + 8 <= b; t += 8) {
+        float v[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = value(t + u);
+        for (int u = 0; u < 8; ++u) v[u] = value(t + u);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc = __dadd_rn(acc, (double)v[u]);
+        for (int u = 0; u < 8; ++u) acc = __dadd_rn(acc, (double)v[u]);
     }
     for (; t < b; ++t) acc = __dadd_rn(acc, (double)value(t));
     words[(int64_t)c * D + j] = __double2float_rn(__ddiv_rn(acc, (double)(b - a)));
@@ -261,6 +261,17 @@ __global__ void k9_init_words(const float* __restrict__ X, int D, const float* _
         float v = X[id * D + j];
         if (RES) v = __fsub_rn(v, W1[(int64_t)c1[id * c1_stride] * D + j]);
         words[e] = v;
+    }
+}
+
+// R_i = X_i - W1[c1[i]] (FP32), the stage-2 vectors, written once for all
+// of stage 2's iterations.
+__global__ void k9_residues(const float* __restrict__ X, int64_t N, int D, const float* __restrict__ W1,
+                            const int32_t* __restrict__ c1, float* __restrict__ R) {
+    const int64_t total = N * D;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / D;
+        R[e] = __fsub_rn(X[e], W1[(int64_t)c1[i] * D + (e - i * D)]);
     }
 }
 
@@ -510,6 +521,13 @@ void launch_rvq_init(const float* X, int D, const float* W1, const int32_t* c1, 
         k9_init_words<true><<<grid, 256, 0, s>>>(X, D, W1, c1, c1_stride, pos, W, words);
     else
         k9_init_words<false><<<grid, 256, 0, s>>>(X, D, nullptr, nullptr, 0, pos, W, words);
+}
+
+void launch_rvq_residues(const float* X, int64_t N, int D, const float* W1, const int32_t* c1, float* R,
+                         cudaStream_t s) {
+    if (N <= 0) return;
+    LaunchScope ls("k9_residues", s, (double)N * D * 12.0 + N * 4.0, (double)N * D);
+    k9_residues<<<grid_for_count(N * D), 256, 0, s>>>(X, N, D, W1, c1, R);
 }
 
 void launch_rvq_key_count(const int32_t* codes, int64_t n, int W2, int32_t* cnt, cudaStream_t s) {

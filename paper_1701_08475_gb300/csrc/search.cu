@@ -9,8 +9,10 @@
 // most visits the query can make, so probes stay short and never fill it).
 // An iteration takes the ks entries as they stand at its start, and every
 // neighbour of theirs not visited yet is visited: its canonical FP32 distance
-// is computed and its key merged into the list.  A key enters the list at
-// most once, so the merge order does not change the result.
+// is computed and its key merged into the list.  The entries' graph slots are
+// taken 32 at a time across entries, one per lane.  A key enters the list at
+// most once and the fresh ids of an iteration do not depend on the order the
+// slots are taken in, so the order does not change the result.
 #include <algorithm>
 
 #include "common.cuh"
@@ -102,12 +104,17 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k8_search(const float* __re
     };
     for (int a0 = 0; a0 < s; a0 += 32) offer(a0 + lane < s ? S[qi * s + a0 + lane] : -1);
     for (int t = 0; t < t0; ++t) {
-        const uint64_t snap = list;  // R's first ks at the iteration's start
-        for (int a = 0; a < ks; ++a) {
+        // R's first ks at the iteration's start: its real entries are a
+        // prefix; their nt * k graph slots are offered 32 at a time (slot
+        // u = entry u / k, neighbour u % k)
+        const uint64_t snap = list;
+        const int nt = __popc(__ballot_sync(0xffffffffu, snap != kEmptyKey));
+        const int slots = nt * k;
+        for (int u0 = 0; u0 < slots; u0 += 32) {
+            const int u = u0 + lane;
+            const int a = u < slots ? u / k : 0;
             const uint64_t e = shfl64(snap, a);
-            if (e == kEmptyKey) break;
-            const int64_t r = key_id(e);
-            for (int e0 = 0; e0 < k; e0 += 32) offer(e0 + lane < k ? G[r * k + e0 + lane] : -1);
+            offer(u < slots ? G[(int64_t)key_id(e) * k + (u - a * k)] : -1);
         }
     }
     if (lane < ks) {

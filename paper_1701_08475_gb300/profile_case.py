@@ -9,6 +9,9 @@ STAGE:
   leaf    the leaf stage on a random balanced partition made on the host
   refine  one refinement round on a random graph made on the host
   exact   exact lists of 1024 sampled rows
+  search  build the graph (BF16) and the RVQ index (2 x 256 words, 8
+          iterations on a 100,000-row prefix), then seed and search 10,000
+          queries near the data (t0 = 12, ks = 20, 32 seeds, probe1 = 16)
 """
 import argparse
 import os
@@ -41,7 +44,7 @@ def random_graph(n, k, seed):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("stage", choices=["build", "split", "leaf", "refine", "exact"])
+    ap.add_argument("stage", choices=["build", "split", "leaf", "refine", "exact", "search"])
     ap.add_argument("--workload", default="sift-like-1m-d128")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--repeat", type=int, default=1)
@@ -54,8 +57,21 @@ def main():
     n, D = X.shape
     k = w["k"]
     Xd = torch.from_numpy(X).cuda()
+    if a.stage == "search":
+        p = knng.default_params(k=k, leaf_max=w["leaf_max"], tree_passes=w["passes"], refine_rounds=w["rounds"],
+                                seed=w["seed"], precision=knng.KNNG_BF16)
+        G, _ = knng.knng_build_ex(Xd, p)
+        w1, w2 = knng.knng_rvq_train(Xd[:min(n, 100000)], 256, 256, 8, seed=5)
+        _, off, lids = knng.knng_rvq_index(Xd, w1, w2)
+        rng = np.random.default_rng(17)
+        Q = np.clip(np.rint(X[rng.integers(0, n, 10000)] + rng.normal(0, 4.0, size=(10000, D))), X.min(),
+                    X.max()).astype(np.float32)
+        Qd = torch.from_numpy(Q).cuda()
     for _ in range(a.repeat):
-        if a.stage == "build":
+        if a.stage == "search":
+            S = knng.knng_rvq_seeds(w1, w2, off, lids, Qd, 16, 32)
+            knng.knng_search(Xd, G, Qd, S, 12, 20)
+        elif a.stage == "build":
             p = knng.default_params(k=k, leaf_max=w["leaf_max"], tree_passes=w["passes"], refine_rounds=w["rounds"],
                                     seed=w["seed"], precision={"fp32": 0, "bf16": 1, "fp16": 2}[a.precision])
             knng.knng_build_ex(Xd, p)
