@@ -257,7 +257,8 @@ KNNG_API int knng_rvq_index(const float *data, int64_t n, int D, const float *wo
  * a query whose lists hold fewer.  seeds: m x s int32.  list_offsets /
  * list_ids as knng_rvq_index writes them, n = the number of list ids;
  * offsets that are negative, decreasing or above n give KNNG_EINVAL.
- * 1 <= probe1 <= W1, probe1 * W2 <= 8192.  Pointers host or device.
+ * 1 <= probe1 <= W1, probe1 * W2 <= 8192, m <= 2^31 - 1 (one CTA per
+ * query).  Pointers host or device.
  */
 KNNG_API int knng_rvq_seeds(const float *words1, int W1, const float *words2, int W2, int D,
                             const int32_t *list_offsets, const int32_t *list_ids, int64_t n,

@@ -1332,7 +1332,7 @@ int knng_rvq_seeds(const float* words1, int W1, const float* words2, int W2, int
                    int32_t* seeds, void* stream) {
     return guarded([&] {
         validate_vocab(W1, W2, D);
-        if (n < 0 || n > INT32_MAX || m < 0 || s < 0) fail(KNNG_EINVAL, "n, m or s out of range");
+        if (n < 0 || n > INT32_MAX || m < 0 || m > INT32_MAX || s < 0) fail(KNNG_EINVAL, "n, m or s out of range");
         if (probe1 < 1 || probe1 > W1) fail(KNNG_EINVAL, "probe1 = %d outside [1, W1]", probe1);
         if (probe1 * W2 > 8192) fail(KNNG_EINVAL, "probe1 * W2 = %d above 8192", probe1 * W2);
         if (rvq_seeds_smem(probe1, W2, D) > 200 * 1024) fail(KNNG_EINVAL, "D = %d too large for the seeds", D);
