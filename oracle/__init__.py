@@ -61,6 +61,8 @@ def _bind(lib):
         "orc_build": (i32, [P, i64, i32, i32, i32, i32, i32, i32, i32, u64, P, P]),
         "orc_recall": (i32, [P, P, P, P, P, i64, i32, P, P]),
         "orc_search": (i32, [P, i64, i32, P, i32, P, i64, P, i32, i32, i32, P, P]),
+        "orc_sample_prio": (u64, [u64, i32, i64, ctypes.c_int32]),
+        "orc_refine_sampled": (i64, [P, i64, i32, i32, i32, u64, i32, P, P, P]),
         "orc_rvq_init_positions": (None, [i64, i32, u64, i32, P]),
         "orc_rvq_assign": (i32, [P, i64, i32, P, i32, P]),
         "orc_rvq_train": (i32, [P, i64, i32, i32, i32, i32, u64, P, P]),
@@ -222,6 +224,27 @@ def refine_round(X, ids, dists, mode=FWD_REV):
     if _load().orc_refine_round(_p(X), n, D, k, mode, _p(ids), _p(dists)) != 0:
         raise MemoryError("orc_refine_round")
     return ids, dists
+
+
+def sample_prio(seed, round_, v, u):
+    """Sampling priority h(v, u) of the sampled refinement round."""
+    return int(_load().orc_sample_prio(seed & (2**64 - 1), round_, v, u))
+
+
+def refine_sampled(X, ids, dists, flags, ms, seed=0, round_=0):
+    """One sampled refinement round (nearest-neighbour descent with sampling,
+    ms samples per list): (ids, dists, flags, entries that entered a list).
+    flags: n x k uint8, 1 = new."""
+    X = _f32(X)
+    n, D = X.shape
+    ids = np.array(ids, np.int32, order="C", copy=True)
+    dists = np.array(dists, np.float32, order="C", copy=True)
+    flags = np.array(flags, np.uint8, order="C", copy=True)
+    k = ids.shape[1]
+    r = _load().orc_refine_sampled(_p(X), n, D, k, ms, seed & (2**64 - 1), round_, _p(ids), _p(dists), _p(flags))
+    if r < 0:
+        raise ValueError("orc_refine_sampled failed: %d" % r)
+    return ids, dists, flags, int(r)
 
 
 def build_graph(X, k, leaf_max, passes=1, rounds=0, iters=4, mode=FWD_REV, seed=0):

@@ -3,7 +3,8 @@
  * partitioning, exhaustive comparison inside each cluster, and
  * neighbour-of-neighbour refinement (Zhao, Yang, Deng, "Scalable Nearest
  * Neighbor Search based on kNN Graph", arXiv 1701.08475, Sec. 3.1, Alg. 1;
- * refinement: the nearest-neighbour-descent prior art cited in Sec. 1), and
+ * refinement: the nearest-neighbour-descent prior art cited in Sec. 1, also
+ * in its sampled form), and
  * the enhanced hill-climbing search over the built graph (Sec. 3.2, Alg. 2),
  * and the residue-quantisation inverted index that seeds it (Sec. 4).
  *
@@ -372,6 +373,163 @@ int orc_refine_round(const float *X, int64_t n, int D, int k, int mode,
     }
     free(old_ids); free(old_d); free(rev_ids); free(rev_d); free(memb);
     return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sampled refinement round: nearest-neighbour descent with sampling,  */
+/* the prior art Sec. 1 cites (Dong, Charikar and Li, WWW 2011), in    */
+/* Jacobi form.  flags[i*k + t] = 1 marks entry t of G[i] as new (not  */
+/* yet joined), 0 as old.                                             */
+/*  1. per node v: old[v] = its entries flagged old; new[v] = the ms    */
+/*     entries flagged new with the least priority h(v, u) (all of     */
+/*     them when fewer), which are then flagged old;                   */
+/*  2. reverse lists: rold[u] = {v : u in old[v]}, rnew[u] = {v : u in  */
+/*     new[v]}, each cut to the ms members with the least h(u, v);     */
+/*  3. per v: Nn = new[v] + rnew[v], No = old[v] + rold[v] without the  */
+/*     ids of Nn; every pair of Nn and every pair of Nn x No offers    */
+/*     each member to the other with the canonical distance;           */
+/*  4. G[u] becomes the first k unique of G[u] and its offers; an id   */
+/*     that was not in G[u] enters flagged new, the others keep their  */
+/*     flags.                                                          */
+/* h(v, u) = SplitMix64(SplitMix64(seed ^ round) ^ (v << 32 | u)), ties */
+/* by id.  Returns the entries that entered a list (NN-descent's       */
+/* update count), or < 0 on bad arguments.                             */
+/* ------------------------------------------------------------------ */
+uint64_t orc_sample_prio(uint64_t seed, int round, int64_t v, int32_t u)
+{
+    return orc_splitmix64(orc_splitmix64(seed ^ (uint64_t)(uint32_t)round) ^
+                          (((uint64_t)v << 32) | (uint32_t)u));
+}
+
+typedef struct { uint64_t h; int32_t id; } prio_t;
+
+static int prio_cmp(const void *a, const void *b)
+{
+    const prio_t *x = (const prio_t *)a, *y = (const prio_t *)b;
+    if (x->h != y->h) return x->h < y->h ? -1 : 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+/* Keep the ms members of ids[0..cnt) with the least h(owner, id). */
+static int sample_least(int32_t *ids, int cnt, int ms, uint64_t seed, int round, int64_t owner, prio_t *tmp)
+{
+    if (cnt <= ms) return cnt;
+    for (int a = 0; a < cnt; ++a) {
+        tmp[a].h = orc_sample_prio(seed, round, owner, ids[a]);
+        tmp[a].id = ids[a];
+    }
+    qsort(tmp, (size_t)cnt, sizeof(prio_t), prio_cmp);
+    for (int a = 0; a < ms; ++a) ids[a] = tmp[a].id;
+    return ms;
+}
+
+static int has_id(const int32_t *ids, int cnt, int32_t id)
+{
+    for (int a = 0; a < cnt; ++a)
+        if (ids[a] == id) return 1;
+    return 0;
+}
+
+int64_t orc_refine_sampled(const float *X, int64_t n, int D, int k, int ms, uint64_t seed, int round,
+                           int32_t *ids, float *dists, unsigned char *flags)
+{
+    if (n < 1 || D < 1 || k < 1 || ms < 0) return -1;
+    size_t nk = (size_t)n * (size_t)k;
+    int32_t *snap = malloc(sizeof(int32_t) * nk);           /* G before the round */
+    unsigned char *isnew = malloc(nk);                      /* 1: in new[v] (sampled) */
+    int64_t *co = calloc((size_t)n + 1, sizeof(int64_t)), *cn = calloc((size_t)n + 1, sizeof(int64_t));
+    int32_t *ro = malloc(sizeof(int32_t) * (nk > 0 ? nk : 1)), *rn = malloc(sizeof(int32_t) * (nk > 0 ? nk : 1));
+    int32_t *nn = malloc(sizeof(int32_t) * (size_t)(k + 2 * ms + 1)), *no = malloc(sizeof(int32_t) * (size_t)(k + ms + 1));
+    int32_t *buf = malloc(sizeof(int32_t) * (nk > 0 ? nk : 1));
+    prio_t *tmp = malloc(sizeof(prio_t) * (nk > 0 ? nk : 1));
+    int64_t *fo = malloc(sizeof(int64_t) * ((size_t)n + 1)), *fn = malloc(sizeof(int64_t) * ((size_t)n + 1));
+    if (!snap || !isnew || !co || !cn || !ro || !rn || !nn || !no || !buf || !tmp || !fo || !fn) {
+        free(snap); free(isnew); free(co); free(cn); free(ro); free(rn); free(nn); free(no); free(buf);
+        free(tmp); free(fo); free(fn);
+        return -2;
+    }
+    memcpy(snap, ids, sizeof(int32_t) * nk);
+    memset(isnew, 0, nk);
+    /* 1. samples of the new entries; old[v] = entries flagged old before */
+    for (int64_t v = 0; v < n; ++v) {
+        int cnt = 0;
+        for (int t = 0; t < k; ++t)
+            if (snap[v * k + t] >= 0 && flags[v * k + t]) buf[cnt++] = snap[v * k + t];
+        cnt = sample_least(buf, cnt, ms, seed, round, v, tmp);
+        for (int t = 0; t < k; ++t)
+            if (snap[v * k + t] >= 0 && flags[v * k + t] && has_id(buf, cnt, snap[v * k + t])) {
+                isnew[v * k + t] = 1;
+                flags[v * k + t] = 0;
+            }
+    }
+    /* 2. reverse lists (CSR; cut to ms per node below).  An entry is in
+     * new[v] when isnew is set, in old[v] when it is flagged old and was
+     * not sampled now, and in neither when it stays new unsampled. */
+    for (int64_t v = 0; v < n; ++v)
+        for (int t = 0; t < k; ++t) {
+            int32_t u = snap[v * k + t];
+            if (u < 0) continue;
+            if (isnew[v * k + t]) cn[u + 1]++;
+            else if (!flags[v * k + t]) co[u + 1]++;
+        }
+    for (int64_t u = 0; u < n; ++u) { co[u + 1] += co[u]; cn[u + 1] += cn[u]; }
+    memcpy(fo, co, sizeof(int64_t) * ((size_t)n + 1));
+    memcpy(fn, cn, sizeof(int64_t) * ((size_t)n + 1));
+    for (int64_t v = 0; v < n; ++v)
+        for (int t = 0; t < k; ++t) {
+            int32_t u = snap[v * k + t];
+            if (u < 0) continue;
+            if (isnew[v * k + t]) rn[fn[u]++] = (int32_t)v;
+            else if (!flags[v * k + t]) ro[fo[u]++] = (int32_t)v;
+        }
+    int64_t changed = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        /* 3. members */
+        int cn_ = 0, co_ = 0;
+        for (int t = 0; t < k; ++t)
+            if (isnew[v * k + t]) nn[cn_++] = snap[v * k + t];
+        int rc = (int)(cn[v + 1] - cn[v]);
+        memcpy(buf, rn + cn[v], sizeof(int32_t) * (size_t)rc);
+        rc = sample_least(buf, rc, ms, seed, round, v, tmp);
+        for (int a = 0; a < rc; ++a)
+            if (!has_id(nn, cn_, buf[a])) nn[cn_++] = buf[a];
+        for (int t = 0; t < k; ++t) {
+            int32_t u = snap[v * k + t];
+            if (u >= 0 && !isnew[v * k + t] && !flags[v * k + t] && !has_id(nn, cn_, u)) no[co_++] = u;
+        }
+        rc = (int)(co[v + 1] - co[v]);
+        memcpy(buf, ro + co[v], sizeof(int32_t) * (size_t)rc);
+        rc = sample_least(buf, rc, ms, seed, round, v, tmp);
+        for (int a = 0; a < rc; ++a)
+            if (!has_id(nn, cn_, buf[a]) && !has_id(no, co_, buf[a])) no[co_++] = buf[a];
+        for (int a = 0; a < cn_; ++a) {
+            int32_t u = nn[a];
+            for (int b = a + 1; b < cn_ + co_; ++b) {
+                int32_t w = b < cn_ ? nn[b] : no[b - cn_];
+                float d = orc_dist_f32(X + (int64_t)u * D, X + (int64_t)w * D, D);
+                orc_list_insert(ids + (int64_t)u * k, dists + (int64_t)u * k, k, d, w);
+                orc_list_insert(ids + (int64_t)w * k, dists + (int64_t)w * k, k, d, u);
+            }
+        }
+    }
+    /* 4. flags of the new lists */
+    memcpy(isnew, flags, nk);                   /* flags after the sampling, by snapshot slot */
+    for (int64_t u = 0; u < n; ++u)
+        for (int t = 0; t < k; ++t) {
+            int32_t id = ids[u * k + t];
+            unsigned char f = 0;
+            if (id >= 0) {
+                int found = -1;
+                for (int s2 = 0; s2 < k; ++s2)
+                    if (snap[u * k + s2] == id) { found = s2; break; }
+                if (found < 0) { f = 1; ++changed; }
+                else f = isnew[u * k + found];
+            }
+            flags[u * k + t] = f;
+        }
+    free(snap); free(isnew); free(co); free(cn); free(ro); free(rn); free(nn); free(no); free(buf);
+    free(tmp); free(fo); free(fn);
+    return changed;
 }
 
 /* ------------------------------------------------------------------ */

@@ -133,3 +133,46 @@ def test_planted_mistake_in_search_or_index_is_caught(name, old, new, tmp_path, 
             caught = True
             break
     assert caught, "no pin caught the planted mistake: " + name
+
+
+# the sampled refinement round (nearest-neighbour descent with sampling)
+from tests import test_oracle_sampled as Sm  # noqa: E402
+
+PINS_SAMPLED = [
+    Sm.test_priority_is_splitmix_of_the_stated_key,
+    Sm.test_no_samples_or_no_new_entries_change_nothing,
+    lambda: Sm.test_unlimited_sample_joins_every_new_pair(3),
+    lambda: Sm.test_limited_sample_joins_the_sampled_members(4, 2),
+    Sm.test_the_sample_is_the_least_priorities,
+    Sm.test_lists_only_improve_and_stay_canonical,
+]
+
+MUTATIONS_SAMPLED = [
+    ("sampled entries stay new", "isnew[v * k + t] = 1;\n                flags[v * k + t] = 0;",
+     "isnew[v * k + t] = 1;"),
+    ("new x old pairs skipped", "for (int b = a + 1; b < cn_ + co_; ++b) {", "for (int b = a + 1; b < cn_; ++b) {"),
+    ("inserted entries flagged old", "if (found < 0) { f = 1; ++changed; }", "if (found < 0) { f = 0; ++changed; }"),
+    ("reverse new lists ignored", "if (!has_id(nn, cn_, buf[a])) nn[cn_++] = buf[a];", ""),
+    ("sample keeps the greatest priorities", "if (x->h != y->h) return x->h < y->h ? -1 : 1;",
+     "if (x->h != y->h) return x->h > y->h ? -1 : 1;"),
+    ("priority ignores the round", "orc_splitmix64(seed ^ (uint64_t)(uint32_t)round)", "orc_splitmix64(seed)"),
+    ("old members drawn from unsampled new entries",
+     "if (u >= 0 && !isnew[v * k + t] && !flags[v * k + t] && !has_id(nn, cn_, u)) no[co_++] = u;",
+     "if (u >= 0 && !isnew[v * k + t] && !has_id(nn, cn_, u)) no[co_++] = u;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS_SAMPLED, ids=[m[0] for m in MUTATIONS_SAMPLED])
+def test_planted_mistake_in_the_sampled_round_is_caught(name, old, new, tmp_path, monkeypatch):
+    src = oracle.source_text()
+    assert src.count(old) == 1, "mutation anchor must occur once: " + name
+    lib = oracle.compile_variant(src.replace(old, new), str(tmp_path / "mutant.so"))
+    monkeypatch.setattr(oracle, "_lib", lib)
+    caught = False
+    for pin in PINS_SAMPLED:
+        try:
+            pin()
+        except Exception:
+            caught = True
+            break
+    assert caught, "no pin caught the planted mistake: " + name
