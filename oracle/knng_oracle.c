@@ -391,14 +391,17 @@ int orc_refine_round(const float *X, int64_t n, int D, int k, int mode,
 /*  4. G[u] becomes the first k unique of G[u] and its offers; an id   */
 /*     that was not in G[u] enters flagged new, the others keep their  */
 /*     flags.                                                          */
-/* h(v, u) = SplitMix64(SplitMix64(seed ^ round) ^ (v << 32 | u)), ties */
-/* by id.  Returns the entries that entered a list (NN-descent's       */
-/* update count), or < 0 on bad arguments.                             */
+/* Priority of member u of node v: the upper 32 bits of                */
+/* SplitMix64(SplitMix64(seed ^ round) ^ (v << 32 | u)) above the 32   */
+/* bits of u, so one 64-bit key orders by hash, then by id.  Returns   */
+/* the entries that entered a list (NN-descent's update count), or < 0 */
+/* on bad arguments.                                                   */
 /* ------------------------------------------------------------------ */
 uint64_t orc_sample_prio(uint64_t seed, int round, int64_t v, int32_t u)
 {
-    return orc_splitmix64(orc_splitmix64(seed ^ (uint64_t)(uint32_t)round) ^
-                          (((uint64_t)v << 32) | (uint32_t)u));
+    uint64_t h = orc_splitmix64(orc_splitmix64(seed ^ (uint64_t)(uint32_t)round) ^
+                                (((uint64_t)v << 32) | (uint32_t)u));
+    return (h & 0xFFFFFFFF00000000ull) | (uint32_t)u;
 }
 
 typedef struct { uint64_t h; int32_t id; } prio_t;

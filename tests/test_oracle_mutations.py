@@ -156,6 +156,8 @@ MUTATIONS_SAMPLED = [
     ("sample keeps the greatest priorities", "if (x->h != y->h) return x->h < y->h ? -1 : 1;",
      "if (x->h != y->h) return x->h > y->h ? -1 : 1;"),
     ("priority ignores the round", "orc_splitmix64(seed ^ (uint64_t)(uint32_t)round)", "orc_splitmix64(seed)"),
+    ("priority without the id bits", "return (h & 0xFFFFFFFF00000000ull) | (uint32_t)u;",
+     "return h & 0xFFFFFFFF00000000ull;"),
     ("old members drawn from unsampled new entries",
      "if (u >= 0 && !isnew[v * k + t] && !flags[v * k + t] && !has_id(nn, cn_, u)) no[co_++] = u;",
      "if (u >= 0 && !isnew[v * k + t] && !has_id(nn, cn_, u)) no[co_++] = u;"),

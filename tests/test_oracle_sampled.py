@@ -30,8 +30,8 @@ def _random_lists(X, k, seed):
 
 def test_priority_is_splitmix_of_the_stated_key():
     for seed, r, v, u in [(0, 0, 0, 0), (5, 3, 17, 4), (2**40 + 1, 7, 123456, 99)]:
-        want = oracle.splitmix64(oracle.splitmix64(seed ^ r) ^ ((v << 32) | u))
-        assert oracle.sample_prio(seed, r, v, u) == want
+        h = oracle.splitmix64(oracle.splitmix64(seed ^ r) ^ ((v << 32) | u))
+        assert oracle.sample_prio(seed, r, v, u) == (h & ~0xFFFFFFFF) | u     # hash bits above the id
     assert oracle.sample_prio(1, 0, 3, 4) != oracle.sample_prio(1, 1, 3, 4)
     assert oracle.sample_prio(1, 0, 3, 4) != oracle.sample_prio(1, 0, 4, 3)
 
