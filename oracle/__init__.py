@@ -62,6 +62,7 @@ def _bind(lib):
         "orc_recall": (i32, [P, P, P, P, P, i64, i32, P, P]),
         "orc_search": (i32, [P, i64, i32, P, i32, P, i64, P, i32, i32, i32, P, P]),
         "orc_sample_prio": (u64, [u64, i32, i64, ctypes.c_int32]),
+        "orc_build_sampled": (i32, [P, i64, i32, i32, i32, i32, i32, i32, i32, u64, P, P]),
         "orc_refine_sampled": (i64, [P, i64, i32, i32, i32, u64, i32, P, P, P]),
         "orc_rvq_init_positions": (None, [i64, i32, u64, i32, P]),
         "orc_rvq_assign": (i32, [P, i64, i32, P, i32, P]),
@@ -257,6 +258,21 @@ def build_graph(X, k, leaf_max, passes=1, rounds=0, iters=4, mode=FWD_REV, seed=
                           seed & (2**64 - 1), _p(ids), _p(d))
     if r != 0:
         raise ValueError("orc_build: bad arguments")
+    return ids, d
+
+
+def build_graph_sampled(X, k, leaf_max, passes=1, rounds=0, iters=4, ms=None, seed=0):
+    """The whole build with sampled refinement rounds (ms samples per list,
+    default k // 2), every entry flagged new before the first round."""
+    X = _f32(X)
+    n, D = X.shape
+    ms = k // 2 if ms is None else ms
+    ids = np.empty((n, k), np.int32)
+    d = np.empty((n, k), np.float32)
+    r = _load().orc_build_sampled(_p(X), n, D, k, leaf_max, passes, rounds, iters, ms, seed & (2**64 - 1),
+                                  _p(ids), _p(d))
+    if r != 0:
+        raise ValueError("orc_build_sampled: bad arguments")
     return ids, d
 
 

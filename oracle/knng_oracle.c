@@ -562,6 +562,24 @@ int orc_build(const float *X, int64_t n, int D, int k, int leaf_max, int passes,
     return 0;
 }
 
+/* Whole build with sampled refinement: the tree passes of orc_build,  */
+/* then `rounds` sampled rounds (round r uses priority round r and the */
+/* build seed), every entry flagged new before the first.              */
+int orc_build_sampled(const float *X, int64_t n, int D, int k, int leaf_max, int passes, int rounds,
+                      int iters, int ms, uint64_t seed, int32_t *out_ids, float *out_d)
+{
+    if (rounds < 0 || ms < 0) return -1;
+    int rc = orc_build(X, n, D, k, leaf_max, passes, 0, iters, 1, seed, out_ids, out_d);
+    if (rc != 0) return rc;
+    unsigned char *flags = malloc((size_t)n * (size_t)k);
+    if (!flags) return -2;
+    memset(flags, 1, (size_t)n * (size_t)k);
+    for (int r = 0; r < rounds && rc == 0; ++r)
+        if (orc_refine_sampled(X, n, D, k, ms, seed, r, out_ids, out_d, flags) < 0) rc = -2;
+    free(flags);
+    return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* Recall of a graph against exact lists on sampled rows.             */
 /* ids: n x k graph; gt_ids/gt_d: s x k exact lists of sample rows.   */

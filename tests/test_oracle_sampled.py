@@ -167,3 +167,18 @@ def test_sampled_rounds_approach_the_exact_graph():
     r1 = oracle.recall(ids, d, gi, gd, np.arange(400))[0]
     assert r0 < 0.2 and r1 > 0.9, (r0, r1)
     assert changes[-1] < changes[0]
+
+
+def test_sampled_build_is_the_passes_then_sampled_rounds():
+    rng = np.random.default_rng(12)
+    X = rng.integers(0, 40, size=(700, 8)).astype(np.float32)
+    k, ms, seed = 8, 3, 21
+    ids, d = oracle.build_graph_sampled(X, k, 32, passes=2, rounds=3, iters=3, ms=ms, seed=seed)
+    wi, wd = oracle.build_graph(X, k, 32, passes=2, rounds=0, iters=3, seed=seed)
+    flags = np.ones(wi.shape, np.uint8)
+    for r in range(3):
+        wi, wd, flags, _ = oracle.refine_sampled(X, wi, wd, flags, ms, seed=seed, round_=r)
+    assert np.array_equal(ids, wi) and np.array_equal(d, wd)
+    i0, _ = oracle.build_graph_sampled(X, k, 32, passes=2, rounds=0, iters=3, ms=ms, seed=seed)
+    b0, _ = oracle.build_graph(X, k, 32, passes=2, rounds=0, iters=3, seed=seed)
+    assert np.array_equal(i0, b0)
