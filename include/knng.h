@@ -56,7 +56,10 @@ extern "C" {
 
 enum knng_join_mode {
     KNNG_JOIN_FWD = 0,     /* N_i = G[i] */
-    KNNG_JOIN_FWD_REV = 1  /* N_i = G[i] + R[i], R[i] the k closest reverse neighbours */
+    KNNG_JOIN_FWD_REV = 1, /* N_i = G[i] + R[i], R[i] the k closest reverse neighbours */
+    KNNG_JOIN_SAMPLED = 2  /* nearest-neighbour descent with sampling (Dong, Charikar and Li 2011): per-entry
+                              new/old flags, knng_params.sample new entries per list and members per reverse
+                              list drawn by a counter-based priority, new x new and new x old pairs joined */
 };
 
 enum knng_precision {
@@ -77,10 +80,14 @@ typedef struct knng_params {
     int precision;       /* enum knng_precision */
     int twomeans_iters;  /* Lloyd iterations T per two-means split (>= 0) */
     uint64_t seed;       /* partition seed; pass p uses SplitMix64(seed ^ p) */
+    int sample;          /* KNNG_JOIN_SAMPLED only: samples per list, 1 <= sample <= k / 2;
+                            round r draws member u of node v by the upper 32 bits of
+                            SplitMix64(SplitMix64(seed ^ r) ^ (v << 32 | u)), least first, ties by u.
+                            Not taken by recorded or batched builds. */
 } knng_params;
 
 /* Defaults: k 10, leaf_max 64, tree_passes 1, refine_rounds 0,
- * join_mode FWD_REV, precision FP32, twomeans_iters 4, seed 0. */
+ * join_mode FWD_REV, precision FP32, twomeans_iters 4, seed 0, sample 0. */
 KNNG_API void knng_default_params(knng_params *p);
 
 /*

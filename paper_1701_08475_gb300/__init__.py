@@ -14,6 +14,7 @@ from ._lib import (  # noqa: F401
     KNNG_FP32,
     KNNG_JOIN_FWD,
     KNNG_JOIN_FWD_REV,
+    KNNG_JOIN_SAMPLED,
     KnngError,
     Params,
     default_params,

@@ -18,6 +18,7 @@ _lib = None
 
 KNNG_JOIN_FWD = 0
 KNNG_JOIN_FWD_REV = 1
+KNNG_JOIN_SAMPLED = 2
 KNNG_FP32 = 0
 KNNG_BF16 = 1
 KNNG_FP16 = 2
@@ -34,7 +35,7 @@ class KnngError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("leaf_max", ctypes.c_int), ("tree_passes", ctypes.c_int),
                 ("refine_rounds", ctypes.c_int), ("join_mode", ctypes.c_int), ("precision", ctypes.c_int),
-                ("twomeans_iters", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("twomeans_iters", ctypes.c_int), ("seed", ctypes.c_uint64), ("sample", ctypes.c_int)]
 
 
 class Instance(ctypes.Structure):

@@ -459,13 +459,15 @@ void validate_params(const knng_params* p, int64_t n) {
         fail(KNNG_EINVAL, "refine_rounds > 0 needs tree_passes >= 1");
     if (p->tree_passes > 0 && (p->leaf_max < 2 * (p->k + 1) || p->leaf_max > 256))
         fail(KNNG_EINVAL, "leaf_max = %d out of range [2(k+1) = %d, 256]", p->leaf_max, 2 * (p->k + 1));
-    if (p->join_mode != KNNG_JOIN_FWD && p->join_mode != KNNG_JOIN_FWD_REV)
+    if (p->join_mode != KNNG_JOIN_FWD && p->join_mode != KNNG_JOIN_FWD_REV && p->join_mode != KNNG_JOIN_SAMPLED)
         fail(KNNG_EINVAL, "join_mode = %d unknown", p->join_mode);
+    if (p->join_mode == KNNG_JOIN_SAMPLED && (p->sample < 1 || 2 * p->sample > p->k))
+        fail(KNNG_EINVAL, "sample = %d outside [1, k / 2] for the sampled join", p->sample);
     if (p->precision != KNNG_FP32 && p->precision != KNNG_BF16 && p->precision != KNNG_FP16)
         fail(KNNG_EINVAL, "precision = %d unknown", p->precision);
     if (p->twomeans_iters < 0 || p->twomeans_iters > 64)
         fail(KNNG_EINVAL, "twomeans_iters = %d out of range [0, 64]", p->twomeans_iters);
-    const int m = p->join_mode == KNNG_JOIN_FWD_REV ? 2 * p->k : p->k;
+    const int m = p->join_mode != KNNG_JOIN_FWD ? 2 * p->k : p->k;
     if (p->refine_rounds > 0 && m > 64) fail(KNNG_EINVAL, "refinement supports k <= 32 with reverse lists");
     (void)n;
 }
@@ -597,7 +599,7 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.sb.status = b.status;
     }
     if (join) {
-        const bool rev = a.p.join_mode == KNNG_JOIN_FWD_REV;
+        const bool rev = a.p.join_mode != KNNG_JOIN_FWD;
         const int64_t m = rev ? 2 * k : k;
         const int64_t per_node = std::max<int64_t>(m * (m - 1), 1);
         int64_t cap = (int64_t)((a.offer_budget ? a.offer_budget : offer_budget_bytes()) / 20);
@@ -628,6 +630,10 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.jb.counter = ws.take<uint32_t>(4);
         b.jb.scan_tmp = ws.take<int32_t>(scan_tmp_ints(n));
         b.jb.offers_total = ws.take<unsigned long long>(1);
+        if (a.p.join_mode == KNNG_JOIN_SAMPLED) {
+            b.jb.flags = ws.take<uint64_t>(n);
+            b.jb.flags_post = ws.take<uint64_t>(n);
+        }
     }
 }
 
@@ -711,8 +717,12 @@ void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& t
         const int slot = pass - (a.p.tree_passes - b.jb.npass);
         if (b.lid && slot >= 0) launch_leaf_ids(perm, leaf_off, nleaf, n, slot, b.lid, s);
     }
-    run_refine(X, n, a.D, k, a.p.join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, b.jb, b.nodes_per_chunk,
-               a.p.refine_rounds, b.status, s);
+    if (a.p.join_mode == KNNG_JOIN_SAMPLED)
+        run_refine_sampled(X, n, a.D, k, b.G, b.G2, b.jb, b.nodes_per_chunk, a.p.refine_rounds, a.p.sample,
+                           a.p.seed, b.status, s);
+    else
+        run_refine(X, n, a.D, k, a.p.join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, b.jb, b.nodes_per_chunk,
+                   a.p.refine_rounds, b.status, s);
 }
 
 }  // namespace
@@ -733,6 +743,7 @@ void knng_default_params(knng_params* p) {
     p->precision = KNNG_FP32;
     p->twomeans_iters = 4;
     p->seed = 0;
+    p->sample = 0;
 }
 
 const char* knng_last_error(void) { return g_last_error.c_str(); }
@@ -795,6 +806,8 @@ int knng_build_batched(int n_inst, const knng_instance* inst, const knng_params*
             try {
                 validate_common(in.data, in.n, in.D, q.k);
                 validate_params(&q, in.n);
+                if (q.join_mode == KNNG_JOIN_SAMPLED && q.refine_rounds > 0)
+                    fail(KNNG_EINVAL, "batched builds do not take the sampled join");
                 if (!in.out_ids || !in.out_dists) fail(KNNG_EINVAL, "output pointer is NULL");
             } catch (const Error& e) {
                 const std::string msg = g_last_error;
@@ -919,6 +932,8 @@ int knng_plan_create(const float* data, int64_t n, int D, const knng_params* p, 
         pl->a = Args{n, D, *p};
         // one chunk per round when the worst case fits 48 GB: no host reads
         // are possible in a graph, so the chunks are the worst case's size
+        if (p->join_mode == KNNG_JOIN_SAMPLED && p->refine_rounds > 0)
+            fail(KNNG_EINVAL, "a recorded build does not take the sampled join");
         const int64_t m = p->join_mode == KNNG_JOIN_FWD_REV ? 2 * p->k : p->k;
         const double worst = (double)n * std::max<int64_t>(m * (m - 1), 1) * 20.0;
         pl->a.offer_budget = (size_t)std::max<double>((double)offer_budget_bytes(), std::min(worst, 48e9));
@@ -1054,8 +1069,12 @@ int knng_refine(const float* data, int64_t n, int D, const knng_params* p, int32
         launch_pack(gi.dev, gd.dev, b.G, (int64_t)nk, n, b.status, s);
         if (b.notexact) cuda_check(cudaMemsetAsync(b.notexact, 0, sizeof(int), s), "flag clear");
         quantize_for_join(X.dev, a, b, s);
-        run_refine(X.dev, n, D, p->k, p->join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, b.jb, b.nodes_per_chunk,
-                   p->refine_rounds, b.status, s);
+        if (p->join_mode == KNNG_JOIN_SAMPLED)
+            run_refine_sampled(X.dev, n, D, p->k, b.G, b.G2, b.jb, b.nodes_per_chunk, p->refine_rounds, p->sample,
+                               p->seed, b.status, s);
+        else
+            run_refine(X.dev, n, D, p->k, p->join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, b.jb, b.nodes_per_chunk,
+                       p->refine_rounds, b.status, s);
         launch_unpack(b.G, gi.dev, gd.dev, (int64_t)nk, s);
         download(gi, s);
         download(gd, s);

@@ -803,10 +803,12 @@ bool join_screen() {
 // counter is read back; on an overflow the flag is cleared and the join
 // re-runs on a smaller chunk (no target list has been touched yet).  `tc`:
 // the tensor-core join does the work.
+// `Gbase`, when given, is the list Gnew starts from and Gold only the
+// members' view (the sampled round); thresholds come from Gold either way.
 void join_round(const float* X, int64_t n, int D, int k, bool rev, const uint64_t* Gold, uint64_t* Gnew,
                 const JoinBuffers& b, bool tc, int64_t count, int64_t nodes_per_chunk, double& est, int* status,
-                cudaStream_t s) {
-    cudaMemcpyAsync(Gnew, Gold, sizeof(uint64_t) * n * k, cudaMemcpyDeviceToDevice, s);
+                cudaStream_t s, const uint64_t* Gbase = nullptr) {
+    cudaMemcpyAsync(Gnew, Gbase ? Gbase : Gold, sizeof(uint64_t) * n * k, cudaMemcpyDeviceToDevice, s);
     const int mcap = ((rev ? 2 * k : k) + 3) & ~3;
     const int bpl = join_blocks_per_lane(mcap);
     const size_t smem = join_smem_bytes(D, mcap);
@@ -970,6 +972,33 @@ void run_refine(const float* X, int64_t n, int D, int k, bool rev, uint64_t*& G,
         join_round(X, n, D, k, rev, G, G2, b, tc, count, nodes_per_chunk, est, status, s);
         std::swap(G, G2);
         if (rev) std::swap(b.R, b.R2);
+    }
+}
+
+void run_refine_sampled(const float* X, int64_t n, int D, int k, uint64_t*& G, uint64_t*& G2, const JoinBuffers& jb,
+                        int64_t nodes_per_chunk, int rounds, int ms, uint64_t seed, int* status, cudaStream_t s) {
+    JoinBuffers b = jb;
+    double est = 2.0 * k * (2.0 * k - 1) / 4;
+    bool tc = false;
+    if (b.lp) {
+        int f = 0;
+        cudaMemcpyAsync(&f, b.notexact, sizeof f, cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        tc = (f & 1) == 0 && !((f & 2) && (f & 4));
+    }
+    cudaMemsetAsync(b.flags, 0xFF, sizeof(uint64_t) * n, s);  // every entry new before the first round
+    for (int r = 0; r < rounds; ++r) {
+        const uint64_t h0 = splitmix64(seed ^ (uint64_t)(uint32_t)r);
+        // member view in R2, sampled-new mask in fnew_buf, reverse samples in R
+        launch_sampled_prepare(G, b.flags, n, k, ms, h0, b.R2, b.fnew_buf, b.flags_post, b.deg, b.roff, b.cur,
+                               b.scan_tmp, b.rbuf, b.R, b.rnew_buf, s);
+        b.list = nullptr;
+        b.count_dev = nullptr;
+        b.fnew = b.fnew_buf;
+        b.rnew = b.rnew_buf;
+        join_round(X, n, D, k, true, b.R2, G2, b, tc, n, nodes_per_chunk, est, status, s, G);
+        launch_sampled_flags(G2, G, b.flags_post, n, k, b.flags, nullptr, s);
+        std::swap(G, G2);
     }
 }
 

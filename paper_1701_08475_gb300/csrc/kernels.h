@@ -169,6 +169,10 @@ struct JoinBuffers {
     // that pair again could not change either list, and the join skips it.
     const int32_t* leafid = nullptr;
     int npass = 0;
+    // sampled rounds: per node a flag mask (bit e: entry e of the list is
+    // new) and the mask after this round's sample (NULL: full rounds)
+    uint64_t* flags = nullptr;
+    uint64_t* flags_post = nullptr;
 };
 
 constexpr int kMaxLeafPasses = 4;  // tree passes whose leaves the join remembers
@@ -205,6 +209,11 @@ void launch_reverse_lists(const uint64_t* G, int64_t n, int k, const JoinBuffers
 // the previous round already offered.
 void run_refine(const float* X, int64_t n, int D, int k, bool rev, uint64_t*& G, uint64_t*& G2,
                 const JoinBuffers& b, int64_t nodes_per_chunk, int rounds, int* status, cudaStream_t s);
+// `rounds` sampled refinement rounds (nearest-neighbour descent with ms
+// samples per list, every entry new before the first): b.flags and
+// b.flags_post hold the masks; round r draws with SplitMix64(seed ^ r).
+void run_refine_sampled(const float* X, int64_t n, int D, int k, uint64_t*& G, uint64_t*& G2, const JoinBuffers& b,
+                        int64_t nodes_per_chunk, int rounds, int ms, uint64_t seed, int* status, cudaStream_t s);
 
 // Exclusive scan of cnt[0..n) into off[0..n], off[n] = total.
 void launch_scan(const int32_t* cnt, int32_t* off, int64_t n, int32_t* tmp, cudaStream_t s);
@@ -221,6 +230,16 @@ void launch_check_ids(const int32_t* ids, int64_t count, int64_t lo, int64_t hi,
 void launch_unpack(const uint64_t* G, int32_t* ids, float* d, int64_t count, cudaStream_t s, int64_t id_offset = 0);
 
 // ---------------------------------------------------------------- exact / recall (K7)
+// Sampled refinement round (sampled.cu): the sample of every list and of the
+// reverse lists, the member view Gm, the masks fm (sampled) and Fp (flags
+// after the sample), the sampled reverse rows R with their new-mask rm; and
+// the flags after the merge.
+void launch_sampled_prepare(const uint64_t* G, uint64_t* F, int64_t n, int k, int ms, uint64_t h0, uint64_t* Gm,
+                            uint64_t* fm, uint64_t* Fp, int32_t* deg, int32_t* roff, int32_t* cur, int32_t* scan_tmp,
+                            uint64_t* rbuf, uint64_t* R, uint64_t* rm, cudaStream_t s);
+void launch_sampled_flags(const uint64_t* Gnew, const uint64_t* Gold, const uint64_t* Fp, int64_t n, int k,
+                          uint64_t* F, unsigned long long* entered, cudaStream_t s);
+
 // Residue vector quantisation and its inverted index (rvq.cu, Sec. 4).
 // codes of the N vectors v_i = X_i, or X_i - W1[c1[i * c1_stride]] when W1 is
 // given, against W <= 256 words: out[i * out_stride].

@@ -101,3 +101,19 @@ def test_rvq_arguments_are_rejected_without_a_gpu(lib):
     big = np.zeros((256, 4), np.float32)
     with pytest.raises(knng.KnngError):
         knng.knng_rvq_seeds(big, big, np.zeros(65537, np.int32), ids, X, 33, 3)   # 33 * 256 keys > 8192
+
+
+def test_sampled_join_parameters_without_a_gpu(lib):
+    import numpy as np
+    import paper_1701_08475_gb300 as knng
+    p = knng.default_params()
+    assert p.sample == 0 and knng.KNNG_JOIN_SAMPLED == 2
+    X = np.zeros((500, 4), np.float32)
+    for sample in (0, 5, -1):                           # outside [1, k / 2] for k = 8
+        q = knng.default_params(k=8, leaf_max=64, refine_rounds=1, join_mode=knng.KNNG_JOIN_SAMPLED, sample=sample)
+        with pytest.raises(knng.KnngError) as e:
+            knng.knng_build_ex(X, q)
+        assert e.value.code == -1
+    q = knng.default_params(k=8, leaf_max=64, refine_rounds=1, join_mode=3)
+    with pytest.raises(knng.KnngError):
+        knng.knng_build_ex(X, q)
