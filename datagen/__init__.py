@@ -25,6 +25,22 @@ def gaussian_mixture(n, D, n_centres, seed, lo=-10.0, hi=10.0, sigma=1.0):
     return np.ascontiguousarray(X, dtype=np.float32)
 
 
+def _chunks(n, chunk, fill):
+    """Runs fill(a, b, rng) over the row ranges [a, b) of `chunk` rows in
+    parallel threads; chunk c draws from its own stream, seeded by the
+    caller's seed material and c, so the result does not depend on the
+    number of threads (numpy's generators release the GIL in bulk draws)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+    starts = list(range(0, n, chunk))
+    if len(starts) <= 1:
+        for c, a in enumerate(starts):
+            fill(a, min(n, a + chunk), c)
+        return
+    with ThreadPoolExecutor(max_workers=min(len(starts), os.cpu_count() or 4, 32)) as ex:
+        list(ex.map(lambda ca: fill(ca[1], min(n, ca[1] + chunk), ca[0]), enumerate(starts)))
+
+
 def sift_like(n, D=128, n_centres=1000, seed=0, zero_frac=0.3, spread=25.0, latent_dim=16, noise=4.0,
               chunk=1 << 18):
     """Non-negative integers 0..255 stored as FP32, clustered, low intrinsic dimension.
@@ -47,25 +63,28 @@ def sift_like(n, D=128, n_centres=1000, seed=0, zero_frac=0.3, spread=25.0, late
         basis = rng.standard_normal(size=(n_centres, latent_dim, D), dtype=np.float32)
         basis *= np.float32(spread / np.sqrt(latent_dim))
     X = np.empty((n, D), np.float32)
-    for a in range(0, n, chunk):
-        b = min(n, a + chunk)
+
+    def fill(a, b, c):
+        r = np.random.default_rng([seed, c + 1])
         lb = lab[a:b]
         if latent_dim:
-            z = rng.standard_normal(size=(b - a, latent_dim), dtype=np.float32)
-            v = rng.standard_normal(size=(b - a, D), dtype=np.float32) * np.float32(noise)
+            z = r.standard_normal(size=(b - a, latent_dim), dtype=np.float32)
+            v = r.standard_normal(size=(b - a, D), dtype=np.float32) * np.float32(noise)
             order = np.argsort(lb, kind="stable")
             bounds = np.searchsorted(lb[order], np.arange(n_centres + 1))
-            for c in range(n_centres):
-                rows = order[bounds[c]:bounds[c + 1]]
+            for ci in range(n_centres):
+                rows = order[bounds[ci]:bounds[ci + 1]]
                 if len(rows):
-                    v[rows] += z[rows] @ basis[c]
+                    v[rows] += z[rows] @ basis[ci]
         else:
-            v = rng.standard_normal(size=(b - a, D), dtype=np.float32) * np.float32(spread)
+            v = r.standard_normal(size=(b - a, D), dtype=np.float32) * np.float32(spread)
         v += centres[lb]
         v *= keep[lb]
         np.clip(v, 0.0, 255.0, out=v)
         np.rint(v, out=v)
-        X[a:b] = v.astype(np.float32, copy=False)
+        X[a:b] = v
+
+    _chunks(n, chunk, fill)
     return X
 
 
@@ -84,29 +103,35 @@ def gist_like(n, D=960, n_centres=1000, seed=0, block=32, alpha=0.3, conc=50.0, 
     prof = prof.reshape(n_centres, D)
     lab = rng.integers(0, n_centres, size=n)
     X = np.empty((n, D), np.float32)
-    for a in range(0, n, chunk):
-        b = min(n, a + chunk)
-        v = rng.gamma(conc * prof[lab[a:b]] + np.float32(1e-3)).astype(np.float32)
+
+    def fill(a, b, c):
+        r = np.random.default_rng([seed, c + 1])
+        v = r.gamma(conc * prof[lab[a:b]] + np.float32(1e-3)).astype(np.float32)
         v = v.reshape(b - a, D // block, block)
         v /= np.maximum(v.sum(axis=2, keepdims=True), np.float32(1e-30))
         X[a:b] = v.reshape(b - a, D)
+
+    _chunks(n, chunk, fill)
     return X
 
 
-def unit_mixture(n, D=96, n_centres=10000, seed=0, sigma=0.1, chunk=1 << 20):
+def unit_mixture(n, D=96, n_centres=10000, seed=0, sigma=0.1, chunk=1 << 18):
     """Unit-normalised mixture: centres ~ N(0, I) normalised; point = centre + N(0, sigma^2), normalised."""
     rng = np.random.default_rng(seed)
-    c = rng.standard_normal(size=(n_centres, D), dtype=np.float32)
-    c /= np.linalg.norm(c, axis=1, keepdims=True)
+    cen = rng.standard_normal(size=(n_centres, D), dtype=np.float32)
+    cen /= np.linalg.norm(cen, axis=1, keepdims=True)
     lab = rng.integers(0, n_centres, size=n)
     X = np.empty((n, D), np.float32)
-    for a in range(0, n, chunk):
-        b = min(n, a + chunk)
-        v = rng.standard_normal(size=(b - a, D), dtype=np.float32)
+
+    def fill(a, b, c):
+        r = np.random.default_rng([seed, c + 1])
+        v = r.standard_normal(size=(b - a, D), dtype=np.float32)
         v *= np.float32(sigma)
-        v += c[lab[a:b]]
+        v += cen[lab[a:b]]
         v /= np.linalg.norm(v, axis=1, keepdims=True)
         X[a:b] = v
+
+    _chunks(n, chunk, fill)
     return X
 
 

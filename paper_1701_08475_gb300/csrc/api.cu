@@ -170,6 +170,8 @@ bool stats_on() {
     return r.on;
 }
 
+void stats_flush() { reg().flush(); }
+
 LaunchScope::~LaunchScope() {
     StatRegistry& r = reg();
     std::lock_guard<std::mutex> lk(r.mu);

@@ -19,6 +19,9 @@ struct LaunchScope {
     double bytes_, flops_;
     int slot_;
 };
+// Reads the event times of the launches timed since the last flush into the
+// statistics; call after the stream has been synchronised.
+void stats_flush();
 
 // ---------------------------------------------------------------- prepare (K0)
 // Sets *status |= kStatusNonFinite if any of the n*D values is not finite.

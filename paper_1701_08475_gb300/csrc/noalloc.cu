@@ -9,6 +9,7 @@
 // packed lists and a status word) lives in the file-scope device arrays
 // below, which every GPU that loads the library holds until the process
 // exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -31,19 +32,65 @@ static __device__ __align__(256) int g_noalloc_status;
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 bool g_ready[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};
 uint64_t* g_keys_addr[kMaxDevices] = {};
 int* g_status_addr[kMaxDevices] = {};
 
-// Device addresses of the scratch arrays on the current device, looked up
-// once per device (the first call on a device does it).
+// The unique id of the current context (cuCtxGetId through the runtime's
+// driver entry points, so the library needs no link to libcuda).  A device
+// reset destroys the context and the next runtime call makes a new one with
+// a new id, into which the module (and so the scratch) is loaded afresh.
+bool current_context_id(unsigned long long* id) {
+    typedef CUresult (*get_current_fn)(CUcontext*);
+    typedef CUresult (*get_id_fn)(CUcontext, unsigned long long*);
+    static get_current_fn get_current = nullptr;
+    static get_id_fn get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<get_current_fn>(f1);
+            get_id = reinterpret_cast<get_id_fn>(f2);
+        }
+        cudaGetLastError();
+        looked = true;
+    }
+    if (!get_current || !get_id) return false;
+    CUcontext c = nullptr;
+    return get_current(&c) == CUDA_SUCCESS && c != nullptr && get_id(c, id) == CUDA_SUCCESS;
+}
+
+// Device addresses of the scratch arrays in the current device's context.
+// The set-up (cudaGetSymbolAddress with the device current) runs on the
+// first call on a device, and again on the first call after that device's
+// context was replaced (cudaDeviceReset), whose module holds a new copy of
+// the arrays; otherwise the cached addresses serve.
 bool scratch_for_current_device(uint64_t** keys, int** status, const char** why) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
         *why = "no usable current CUDA device";
         return false;
     }
+    // makes the device's primary context current (creating it after a
+    // reset), so that its id can be read
+    if (cudaSetDevice(dev) != cudaSuccess) {
+        cudaGetLastError();
+        *why = "the device's context could not be made current";
+        return false;
+    }
+    unsigned long long ctx = 0;
+    if (!current_context_id(&ctx)) {
+        *why = "the current context's id could not be read";
+        return false;
+    }
     std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_ready[dev]) {
+    if (!g_ready[dev] || g_ctx_id[dev] != ctx) {
+        g_ready[dev] = false;
         void* k = nullptr;
         void* s = nullptr;
         if (cudaGetSymbolAddress(&k, g_noalloc_keys) != cudaSuccess ||
@@ -54,6 +101,7 @@ bool scratch_for_current_device(uint64_t** keys, int** status, const char** why)
         }
         g_keys_addr[dev] = static_cast<uint64_t*>(k);
         g_status_addr[dev] = static_cast<int*>(s);
+        g_ctx_id[dev] = ctx;
         g_ready[dev] = true;
     }
     *keys = g_keys_addr[dev];
@@ -103,12 +151,18 @@ extern "C" KNNG_API int knng_exact_noalloc(const float* data, int64_t n, int D, 
     launch_check_ids(sample, s, 0, n, status, st);
     launch_exact(data, n, D, k, sample, s, keys, status, st);
     launch_unpack(keys, out_ids, out_dists, s * (int64_t)k, st);
+    // a launch the runtime refused (for example the dynamic shared memory of
+    // the exact kernel) leaves the outputs unwritten: report it before the
+    // status word, which would read zero
+    const cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) return fail(KNNG_ECUDA, cudaGetErrorString(le));
     int hs = 0;
     if (cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         cudaError_t e = cudaGetLastError();
         return fail(KNNG_ECUDA, cudaGetErrorString(e));
     }
+    stats_flush();
     if (hs & kStatusNonFinite) return fail(KNNG_EINVAL, "data holds a non-finite value");
     if (hs & kStatusBadInput) return fail(KNNG_EINVAL, "a sampled row index is out of range");
     return KNNG_OK;

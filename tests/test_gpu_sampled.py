@@ -9,8 +9,7 @@ import datagen
 import oracle
 
 torch = pytest.importorskip("torch")
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="written without a GPU run; enabled once run on a GB300")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
