@@ -42,8 +42,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-search", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads' measurements")
+    ap.add_argument("--config-steps", type=int, default=2, help="timed steps per form of the other workloads")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16", "fp8"])
     return ap.parse_args()
 
 
@@ -54,11 +56,14 @@ def dist_env():
     return rank, world, local
 
 
-def workload_config(name):
+def workload_config(name, precision="fp32"):
     w = dict(datagen.WORKLOADS[name])
+    X_mb = w["n"] * w["D"] * 4 / 1e6
     return dict(workload=name, n=w["n"], D=w["D"], k=w["k"], leaf_max=w["leaf_max"], tree_passes=w["passes"],
-                refine_rounds=w["rounds"], join_mode="fwd_rev", twomeans_iters=4, precision="fp32",
-                generator=w["gen"], seed=w["seed"])
+                refine_rounds=w["rounds"], join_mode="fwd_rev", twomeans_iters=4, precision=precision,
+                generator=w["gen"], seed=w["seed"],
+                l2="inputs larger than L2: X is %.0f MB (L2 129 MB)" % X_mb if X_mb > 129 else
+                   "X is %.1f MB, smaller than L2 (129 MB): a latency case" % X_mb)
 
 
 # ---------------------------------------------------------------- clocks
@@ -217,22 +222,47 @@ def distance_error(X, ids, dists, rows):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_build_seconds(cfg, n_s):
+def oracle_build_seconds(cfg, n_s, X=None):
     import oracle
-    X = datagen.make(cfg["workload"], n_s)
+    if X is None:
+        X = datagen.make(cfg["workload"], n_s)
     t = time.perf_counter()
     oracle.build_graph(X, cfg["k"], cfg["leaf_max"], passes=cfg["tree_passes"], rounds=cfg["refine_rounds"],
                        iters=cfg["twomeans_iters"], mode=oracle.FWD_REV, seed=cfg["seed"])
     return time.perf_counter() - t
 
 
-def cpu_baseline(cfg):
-    n_s = CPU_BASELINE_N
+def oracle_all_cores(cfg, n_s, cores=None):
+    """The single-threaded oracle run as `cores` independent builds at once
+    (one host thread each; the C code runs without the GIL), each on its own
+    draw of the recipe: whole-host throughput of the oracle as it stands."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    cores = cores or os.cpu_count() or 1
+    oracle.build()
+    draws = [datagen.make(cfg["workload"], n_s) if i == 0 else None for i in range(cores)]
+    # other draws: the same recipe at another seed (the generators take the seed)
+    w = datagen.WORKLOADS[cfg["workload"]]
+    for i in range(1, cores):
+        draws[i] = datagen.make_seeded(cfg["workload"], n_s, w["seed"] + 1000 * i)
+    t = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda X: oracle_build_seconds(cfg, n_s, X), draws))
+    sec = time.perf_counter() - t
+    return cores * n_s / sec, sec, cores
+
+
+def cpu_baseline(cfg, n_s=None):
+    n_s = n_s or CPU_BASELINE_N
     sec = oracle_build_seconds(cfg, n_s)
+    multi, msec, cores = oracle_all_cores(cfg, n_s)
     return {"value": round(n_s / sec, 1), "unit": "points/s", "cores": 1, "kind": "oracle",
             "sample": "whole build (same k, leaf_max, passes, rounds, iters) of the first recipe draw at "
                       "n=%d instead of %d points; %.1f s single-threaded" % (n_s, cfg["n"], sec),
-            "host_cpus": os.cpu_count()}
+            "host_cpus": os.cpu_count(),
+            "all_cores": {"value": round(multi, 1), "unit": "points/s", "cores": cores,
+                          "sample": "%d independent whole builds of n=%d draws of the recipe at once, one host "
+                                    "thread each; %.1f s wall" % (cores, n_s, msec)}}
 
 
 def run_reference(args, cfg):
@@ -257,7 +287,7 @@ def run_reference(args, cfg):
 
 
 # ---------------------------------------------------------------- our arm
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "fp8": 3}
 
 
 def search_measure(knng, X, Xd, G, dev, stream, m=10000, t0=12, ks=20, n_seeds=32, n_check=200):
@@ -341,6 +371,115 @@ def search_measure(knng, X, Xd, G, dev, stream, m=10000, t0=12, ks=20, n_seeds=3
                      "recall_at_ks": round(rk, 4)}
         if name == "ivf_seeds":   # seeds and search together
             out[name]["queries_per_s_with_seeds"] = round(m / ((ms + seeds_ms) * 1e-3), 1)
+    return out
+
+
+def event_time(stream, fn, reps):
+    """CUDA-event time (ms) of `reps` calls of fn on `stream` (after the caller's warm-up)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def sampled_measure(knng, Xd, cfg, base_params, gi, gd, smp_d, stream, steps, full):
+    """The sampled refinement round (nearest-neighbour descent with sampling,
+    the prior art Sec. 1 cites) in place of the full local join: the same
+    build with ms = k/2 and k/4 samples per list, direct knng_build_ex calls
+    timed with CUDA events; `full` = the full round's direct form."""
+    import torch
+    n, k = Xd.shape[0], cfg["k"]
+    out = {"full_fwd_rev": full, "how": "knng_build_ex per step, join_mode KNNG_JOIN_SAMPLED, same passes, rounds, "
+                                        "seed and precision as the headline"}
+    ids = torch.empty((n, k), dtype=torch.int32, device=Xd.device)
+    dists = torch.empty((n, k), dtype=torch.float32, device=Xd.device)
+    for ms in sorted({max(1, k // 2), max(1, k // 4)}, reverse=True):
+        p = knng.default_params(**{f: getattr(base_params, f) for f, _ in base_params._fields_})
+        p.join_mode = knng.KNNG_JOIN_SAMPLED
+        p.sample = ms
+        with torch.cuda.stream(stream):
+            knng.knng_build_ex(Xd, p, stream=stream, out=(ids, dists))
+        ms_t = event_time(stream, lambda: knng.knng_build_ex(Xd, p, stream=stream, out=(ids, dists)), steps)
+        r_ids, r_tie = knng.knng_recall(ids, dists, gi, gd, smp_d)
+        out["ms_%d" % ms] = {"value": round(n * steps / (ms_t * 1e-3), 1), "ms_per_step": round(ms_t / steps, 3),
+                             "recall_ids": round(r_ids, 5), "recall_tie": round(r_tie, 5)}
+    return out
+
+
+# Every other workload of the scope table, measured in the same run: its
+# forms (low precision first), event-timed steps, and the oracle's sample
+# size for its single-threaded CPU baseline.
+OTHER_CONFIGS = [
+    ("gmm-10k-d32", ["fp32"], 10_000),
+    ("gist-like-1m-d960", ["fp16", "fp32"], 1_500),
+    ("unit-10m-d96", ["fp8", "bf16", "fp32"], 10_000),
+]
+
+
+def measure_config(knng, name, forms, cpu_n, steps, dev, stream, recall_rows=2000):
+    """One workload: for each form, `steps` direct builds timed with CUDA
+    events after one warm-up, a further build with events around every launch
+    (per-kernel times, the dominant kernel's roofline, the certificate's
+    fallback rows), recall@k against exact lists on sampled rows and the
+    distance error against FP64; the graphs of the forms compared; the oracle
+    timed single-threaded on a bounded draw of the same recipe."""
+    import torch
+    cfg = workload_config(name, forms[0])
+    t0 = time.perf_counter()
+    X = datagen.make(name)
+    gen_s = time.perf_counter() - t0
+    n, D = X.shape
+    k = cfg["k"]
+    Xd = torch.from_numpy(X).to(dev)
+    smp = datagen.sample_rows(n, recall_rows, seed=3)
+    smp_d = torch.from_numpy(smp).to(dev)
+    gi, gd = knng.knng_exact(Xd, k, smp_d)
+    out = {"n": n, "D": D, "k": k, "leaf_max": cfg["leaf_max"], "tree_passes": cfg["tree_passes"],
+           "refine_rounds": cfg["refine_rounds"], "generator": cfg["generator"], "seed": cfg["seed"],
+           "l2": cfg["l2"], "steps": steps, "forms": {}, "datagen_s": round(gen_s, 1)}
+    first = None
+    for prec in forms:
+        p = knng.default_params(k=k, leaf_max=cfg["leaf_max"], tree_passes=cfg["tree_passes"],
+                                refine_rounds=cfg["refine_rounds"], join_mode=knng.KNNG_JOIN_FWD_REV,
+                                twomeans_iters=cfg["twomeans_iters"], seed=cfg["seed"], precision=PRECISIONS[prec])
+        ids = torch.empty((n, k), dtype=torch.int32, device=dev)
+        dists = torch.empty((n, k), dtype=torch.float32, device=dev)
+        with torch.cuda.stream(stream):
+            knng.knng_build_ex(Xd, p, stream=stream, out=(ids, dists))
+        ms = event_time(stream, lambda: knng.knng_build_ex(Xd, p, stream=stream, out=(ids, dists)), steps)
+        knng.stats_reset()
+        knng.stats_enable(True, timing=True)
+        ms_k = event_time(stream, lambda: knng.knng_build_ex(Xd, p, stream=stream, out=(ids, dists)), 1)
+        knng.stats_enable(False)
+        st = knng.stats()
+        roof = roofline(st, None, name, 1)
+        roof["share_of_step"] = round(st[roof["kernel"]]["ms"] / ms_k, 4)
+        leaf = [v for key, v in st.items() if key.startswith("k2_leaf_") and key != "k2_leaf_fp32"]
+        r_ids, r_tie = knng.knng_recall(ids, dists, gi, gd, smp_d)
+        form = {"value": round(n * steps / (ms * 1e-3), 1), "unit": "points/s", "ms_per_step": round(ms / steps, 3),
+                "recall_ids": round(r_ids, 5), "recall_tie": round(r_tie, 5), "recall_rows": int(len(smp)),
+                "distance_error": distance_error(X, ids, dists, smp[:500]),
+                "roofline": roof,
+                "kernels_ms": {key: round(v["ms"], 3) for key, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])[:6]}}
+        if leaf:
+            form["certificate_fallback_rows"] = {"rows": int(leaf[0]["items"]), "of": n * cfg["tree_passes"],
+                                                 "rate": round(leaf[0]["items"] / (n * cfg["tree_passes"]), 4)}
+        out["forms"][prec] = form
+        if first is None:
+            first = (ids, dists)
+        else:
+            form["graph_identical_to_%s" % forms[0]] = bool(torch.equal(first[0], ids) and torch.equal(first[1], dists))
+    sec = oracle_build_seconds(cfg, cpu_n)
+    out["cpu_baseline"] = {"value": round(cpu_n / sec, 1), "unit": "points/s", "cores": 1, "kind": "oracle",
+                           "sample": "whole build (same parameters) of an n=%d draw of the recipe; %.1f s" % (cpu_n, sec)}
+    del Xd, first
+    torch.cuda.empty_cache()
     return out
 
 
@@ -469,6 +608,12 @@ def run_ours(args, cfg):
               "graph_identical": graph_same,
               "how": "knng_build_ex per step (the host launches every kernel and reads offer counts back)"}
 
+    sampled = None
+    if world == 1:
+        sampled = sampled_measure(knng, Xd, cfg, params(args.precision), gi, gd, smp_d, stream, args.steps,
+                                  {"value": direct["value"], "ms_per_step": direct["ms_per_step"],
+                                   "recall_ids": round(rec_ids, 5), "recall_tie": round(rec_tie, 5)})
+
     # end to end: host buffers through the C ABI, copies inside the timed region
     p = params(args.precision)
     Xh = torch.from_numpy(X).pin_memory()
@@ -500,8 +645,6 @@ def run_ours(args, cfg):
         others.append({key: r_[key] for key in ("kernel", "bound", "achieved", "peak", "unit", "frac",
                                                  "share_of_step", "traffic")})
     cfg_out = dict(cfg)
-    cfg_out["precision"] = args.precision
-    cfg_out["l2"] = "inputs larger than L2: X is %.0f MB (L2 129 MB)" % (X.nbytes / 1e6)
     line = {
         "metric": "kNN-graph build points/s at recall@k vs exact", "value": round(value, 1), "unit": "points/s",
         "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 3),
@@ -521,52 +664,69 @@ def run_ours(args, cfg):
                                  "note": "a second run of the same steps with CUDA events around every launch; "
                                          "the per-kernel times, shares and rooflines come from it"},
     }
+    if sampled is not None:
+        line["sampled"] = sampled
     if world == 1 and not args.no_search:
         line["search"] = search_measure(knng, X, Xd, ids, dev, stream)
+    if world == 1 and not args.no_configs:
+        del Xd, Xh
+        torch.cuda.empty_cache()
+        configs = {}
+        for name, forms, cpu_n in OTHER_CONFIGS:
+            configs[name] = measure_config(knng, name, forms, cpu_n, args.config_steps, dev, stream)
+        configs[datagen.BATCHED["name"]] = batched_measure(knng, args.config_steps, 1, "bf16")
+        line["configs"] = configs
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(line), flush=True)
     replicas.finish()
 
 
-def run_batched(args):
-    """The batched workload: 64 independent instances in one knng_build_batched
-    call per step, leaf_max per D from the autotuner (time not counted)."""
+def batched_measure(knng, steps, warmup, precision, local=0):
+    """The batched workload: 64 independent instances recorded once into a
+    CUDA graph (knng_plan_create_batched) and replayed once per step, each D
+    group's leaf tile shape (leaf_max) and split schedule (twomeans_iters)
+    from the autotuner (its time not counted); the low-precision form against
+    FP32, graphs compared; direct knng_build_batched calls timed beside."""
     import torch
-    import paper_1701_08475_gb300 as knng
-    from paper_1701_08475_gb300.autotune import autotune_leaf_max
+    from paper_1701_08475_gb300.autotune import autotune
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     w = datagen.BATCHED
-    datas = datagen.batched_mixtures(n_inst=w["n_inst"], seed=w["seed"] + rank)
+    datas = datagen.batched_mixtures(n_inst=w["n_inst"], seed=w["seed"] + local)
     n_tot = sum(x.shape[0] for x in datas)
     dev = [torch.from_numpy(x).cuda() for x in datas]
-    prec = PRECISIONS[args.precision]
+    prec = PRECISIONS[precision]
     p = knng.default_params(k=w["k"], leaf_max=128, tree_passes=w["passes"], refine_rounds=w["rounds"],
                             join_mode=knng.KNNG_JOIN_FWD_REV, seed=w["seed"], precision=prec)
-    leafs, report = autotune_leaf_max(dev, p)
+    leafs, iters, report = autotune(dev, p)
     stream = torch.cuda.Stream()
 
-    def timed(q):
+    def replayed(q):
+        plan = knng.BatchedPlan(dev, q, leaf_maxes=leafs, twomeans_iters=iters, stream=stream)
         with torch.cuda.stream(stream):
-            for _ in range(max(3, args.warmup)):
-                outs = knng.knng_build_batched(dev, q, leaf_maxes=leafs, stream=stream)
-        torch.cuda.synchronize()
+            for _ in range(max(1, warmup)):
+                plan.launch()
+        plan.check()
+        ms = event_time(stream, plan.launch, steps)
+        plan.check()
+        outs = [(a.clone(), b.clone()) for a, b in plan.outs]
+        kernels = plan.kernels
+        plan.close()
+        return ms, outs, kernels
+
+    def direct(q):
+        with torch.cuda.stream(stream):
+            outs = knng.knng_build_batched(dev, q, leaf_maxes=leafs, twomeans_iters=iters, stream=stream)
         knng.stats_reset()
         knng.stats_enable(True, timing=False)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-            for _ in range(args.steps):
-                outs = knng.knng_build_batched(dev, q, leaf_maxes=leafs, stream=stream)
-            e1.record(stream)
-        torch.cuda.synchronize()
+        ms = event_time(stream, lambda: knng.knng_build_batched(dev, q, leaf_maxes=leafs, twomeans_iters=iters,
+                                                                 stream=stream), steps)
         launches = sum(v["launches"] for v in knng.stats().values())
         knng.stats_enable(False)
-        return e0.elapsed_time(e1), outs, launches
+        return ms, launches
 
-    ms, outs, launches = timed(p)
+    ms, outs, kernels = replayed(p)
+    ms_d, launches_d = direct(p)
     # recall on 200 sampled rows of every instance
     hit = tot = 0
     for x, (ids, d) in zip(dev, outs):
@@ -577,22 +737,40 @@ def run_batched(args):
         tot += len(smp)
     q32 = knng.default_params(k=w["k"], leaf_max=128, tree_passes=w["passes"], refine_rounds=w["rounds"],
                               join_mode=knng.KNNG_JOIN_FWD_REV, seed=w["seed"], precision=knng.KNNG_FP32)
-    ms32, outs32, _ = timed(q32)
+    ms32, outs32, _ = replayed(q32)
     same = all(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) for a, b in zip(outs, outs32))
-    line = {
-        "metric": "kNN-graph build points/s at recall@k vs exact", "value": round(n_tot * args.steps / (ms * 1e-3), 1),
-        "unit": "points/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
-        "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else args.precision + "+f32", "data": "synthetic",
+    return {
+        "value": round(n_tot * steps / (ms * 1e-3), 1), "unit": "points/s", "steps": steps,
+        "ms_per_step": round(ms / steps, 3),
+        "dtype": "f32" if precision == "fp32" else precision + "+f32",
         "config": {"workload": w["name"], "instances": len(datas), "points": int(n_tot), "k": w["k"],
-                   "tree_passes": w["passes"], "refine_rounds": w["rounds"], "precision": args.precision,
+                   "tree_passes": w["passes"], "refine_rounds": w["rounds"], "precision": precision,
                    "leaf_max_by_D": {str(x.shape[1]): l for x, l in zip(datas, leafs)},
+                   "twomeans_iters_by_D": {str(x.shape[1]): t for x, t in zip(datas, iters)},
                    "autotune": {str(D): rows for D, rows in report.items()}},
         "recall_at_k": {"ids": round(hit / tot, 5), "sample_rows": int(tot)},
-        "fp32_form": {"value": round(n_tot * args.steps / (ms32 * 1e-3), 1), "ms_per_step": round(ms32 / args.steps, 3),
+        "fp32_form": {"value": round(n_tot * steps / (ms32 * 1e-3), 1), "ms_per_step": round(ms32 / steps, 3),
                       "graph_identical": bool(same)},
-        "gpu_launches": int(launches),
+        "direct_form": {"value": round(n_tot * steps / (ms_d * 1e-3), 1), "ms_per_step": round(ms_d / steps, 3),
+                        "gpu_launches": int(launches_d), "how": "knng_build_batched per step"},
+        "gpu_launches": int(kernels * steps),
+        "timed": "CUDA-graph replays of the recorded batched build (knng_plan_create_batched, knng_plan_launch)",
     }
+
+
+def run_batched(args):
+    import torch
+    import paper_1701_08475_gb300 as knng
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    knng.load()
+    m = batched_measure(knng, args.steps, args.warmup, args.precision, local=rank)
+    line = {"metric": "kNN-graph build points/s at recall@k vs exact", "value": m["value"], "unit": "points/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": m["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": m["dtype"],
+            "data": "synthetic", "config": m["config"], "recall_at_k": m["recall_at_k"],
+            "fp32_form": m["fp32_form"], "gpu_launches": m["gpu_launches"]}
     print(json.dumps(line), flush=True)
 
 
@@ -605,7 +783,7 @@ def main():
             return
         run_batched(args)
         return
-    cfg = workload_config(args.workload)
+    cfg = workload_config(args.workload, args.precision)
     if args.impl == "reference":
         run_reference(args, cfg)
     else:

@@ -11,7 +11,7 @@ and clustered structure.  No item of either dataset is reproduced.
 import numpy as np
 
 __all__ = ["gaussian_mixture", "sift_like", "gist_like", "unit_mixture", "batched_mixtures",
-           "WORKLOADS", "BATCHED", "make", "sample_rows"]
+           "WORKLOADS", "BATCHED", "make", "make_seeded", "sample_rows"]
 
 
 def gaussian_mixture(n, D, n_centres, seed, lo=-10.0, hi=10.0, sigma=1.0):
@@ -168,17 +168,23 @@ def batched_mixtures(n_inst=64, seed=1238, n_lo=2000, n_hi=200000, dims=(64, 128
 
 def make(name, n=None):
     """Draw the input of workload `name` (optionally only its first `n` rows' recipe at size n)."""
+    return make_seeded(name, n, WORKLOADS[name]["seed"])
+
+
+def make_seeded(name, n=None, seed=None):
+    """The recipe of workload `name` at size n (default: its own) and another seed (default: its own)."""
     w = dict(WORKLOADS[name])
     n = w["n"] if n is None else n
+    seed = w["seed"] if seed is None else seed
     g = w["gen"]
     if g == "gaussian_mixture":
-        return gaussian_mixture(n, w["D"], w["n_centres"], w["seed"])
+        return gaussian_mixture(n, w["D"], w["n_centres"], seed)
     if g == "sift_like":
-        return sift_like(n, w["D"], w["n_centres"], w["seed"])
+        return sift_like(n, w["D"], w["n_centres"], seed)
     if g == "gist_like":
-        return gist_like(n, w["D"], w["n_centres"], w["seed"])
+        return gist_like(n, w["D"], w["n_centres"], seed)
     if g == "unit_mixture":
-        return unit_mixture(n, w["D"], w["n_centres"], w["seed"])
+        return unit_mixture(n, w["D"], w["n_centres"], seed)
     raise KeyError(g)
 
 

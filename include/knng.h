@@ -65,7 +65,8 @@ enum knng_join_mode {
 enum knng_precision {
     KNNG_FP32 = 0,         /* canonical FP32 everywhere */
     KNNG_BF16 = 1,         /* leaf Gram on tensor cores from a BF16 copy, certified FP32 re-rank */
-    KNNG_FP16 = 2          /* the same from an FP16 copy */
+    KNNG_FP16 = 2,         /* the same from an FP16 copy */
+    KNNG_FP8 = 3           /* the same from an FP8 E4M3 copy, each row scaled by max|x| / 448 */
     /* With BF16/FP16 the graph is identical to the FP32 one: every row whose
      * low-precision selection cannot be certified by the error bound is
      * recomputed in FP32.  Leaves above 128 points use the FP32 leaf kernel. */
@@ -120,6 +121,8 @@ typedef struct knng_instance {
     int leaf_max;        /* this instance's cluster bound; 0: p->leaf_max */
     int32_t *out_ids;    /* n x k, ids local to the instance */
     float *out_dists;    /* n x k */
+    int twomeans_iters;  /* this instance's Lloyd iterations per split; 0: p->twomeans_iters.  Instances of
+                            one D must agree (KNNG_EINVAL otherwise): they share one forest */
 } knng_instance;
 
 /*
@@ -160,6 +163,15 @@ KNNG_API int knng_build_batched(int n_inst, const knng_instance *inst, const knn
 typedef struct knng_plan knng_plan;
 KNNG_API int knng_plan_create(const float *data, int64_t n, int D, const knng_params *p, int32_t *out_ids,
                               float *out_dists, void *stream, knng_plan **out_plan);
+/*
+ * The batched form (as knng_build_batched) recorded the same way: one graph
+ * for every instance, all instances' data and outputs device buffers bound at
+ * creation (the instance array itself is read only while recording).  One
+ * replay equals one knng_build_batched call on the same buffers, bit for bit.
+ * The offer buffers of the D groups share the 48 GB equally.
+ */
+KNNG_API int knng_plan_create_batched(int n_inst, const knng_instance *inst, const knng_params *p, void *stream,
+                                      knng_plan **out_plan);
 KNNG_API int knng_plan_launch(knng_plan *plan, void *stream);
 /* Kernel launches one replay makes (the recorded graph's kernel nodes); -1 on error. */
 KNNG_API int64_t knng_plan_kernels(knng_plan *plan);
@@ -190,6 +202,25 @@ KNNG_API int knng_partition(const float *data, int64_t n, int D, int leaf_max, i
 
 /* Depth L of the balanced tree for n points and threshold leaf_max (-1 if invalid). */
 KNNG_API int knng_tree_depth(int64_t n, int leaf_max);
+
+/*
+ * Parity hook of the low-precision leaf stage (Alg. 1's pairwise distances
+ * inside one cluster, computed from a low-precision copy): for the m points
+ * of `data` (m x D, one cluster of 2..256 points, row-major FP32), the
+ * approximate squared distances d^ (out_dhat, m x m row-major FP32, diagonal
+ * included) exactly as the tensor-core leaf kernel forms them for
+ * `precision` (KNNG_BF16, KNNG_FP16 or KNNG_FP8), and the quantised copy they
+ * come from: out_q (m x D FP32) holds the 16-bit values, or for FP8 the
+ * unscaled E4M3 values q; out_scale (m) the row scales s (x~ = s q; 1 for the
+ * 16-bit forms); out_nrm (m) the FP32 squared norms ||x~||^2 the kernel uses;
+ * out_err (m) the upper bounds e >= ||x - x~|| of the certificate.  For
+ * tests of the certificate's error bound against the hardware's arithmetic.
+ * Pointers host or device (all caller-owned).  KNNG_EINVAL for m outside
+ * [2, 256], a non-finite value, or a precision without a low-precision copy;
+ * KNNG_ECUDA when the tensor-core kernel cannot run for this D.
+ */
+KNNG_API int knng_leaf_dhat(const float *data, int64_t m, int D, int precision, float *out_dhat,
+                            float *out_q, float *out_scale, float *out_nrm, float *out_err, void *stream);
 
 /*
  * The leaf stage of Alg. 1 on a given partition: for every cluster and every

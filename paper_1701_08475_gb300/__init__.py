@@ -12,6 +12,7 @@ from ._lib import (  # noqa: F401
     KNNG_BF16,
     KNNG_FP16,
     KNNG_FP32,
+    KNNG_FP8,
     KNNG_JOIN_FWD,
     KNNG_JOIN_FWD_REV,
     KNNG_JOIN_SAMPLED,
@@ -22,12 +23,14 @@ from ._lib import (  # noqa: F401
     knng_build_ex,
     knng_build_batched,
     BuildPlan,
+    BatchedPlan,
     knng_exact,
     knng_search,
     knng_rvq_train,
     knng_rvq_index,
     knng_rvq_seeds,
     knng_exact_noalloc,
+    knng_leaf_dhat,
     knng_leaf_update,
     knng_partition,
     knng_recall,

@@ -22,6 +22,7 @@ KNNG_JOIN_SAMPLED = 2
 KNNG_FP32 = 0
 KNNG_BF16 = 1
 KNNG_FP16 = 2
+KNNG_FP8 = 3
 
 _CODES = {-1: "KNNG_EINVAL", -2: "KNNG_ENOMEM", -3: "KNNG_ECUDA", -4: "KNNG_ETIMEOUT"}
 
@@ -40,7 +41,7 @@ class Params(ctypes.Structure):
 
 class Instance(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("n", ctypes.c_int64), ("D", ctypes.c_int), ("leaf_max", ctypes.c_int),
-                ("out_ids", ctypes.c_void_p), ("out_dists", ctypes.c_void_p)]
+                ("out_ids", ctypes.c_void_p), ("out_dists", ctypes.c_void_p), ("twomeans_iters", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -69,6 +70,7 @@ def load():
             "knng_build_ex": (i32, [P, i64, i32, PP, P, P, P]),
             "knng_build_batched": (i32, [i32, ctypes.POINTER(Instance), PP, P]),
             "knng_plan_create": (i32, [P, i64, i32, PP, P, P, P, ctypes.POINTER(ctypes.c_void_p)]),
+            "knng_plan_create_batched": (i32, [i32, ctypes.POINTER(Instance), PP, P, ctypes.POINTER(ctypes.c_void_p)]),
             "knng_plan_launch": (i32, [P, P]),
             "knng_plan_kernels": (i64, [P]),
             "knng_plan_check": (i32, [P, P]),
@@ -77,6 +79,7 @@ def load():
             "knng_partition": (i32, [P, i64, i32, i32, i32, u64, i32, P, P, P]),
             "knng_tree_depth": (i32, [i64, i32]),
             "knng_leaf_update": (i32, [P, i64, i32, i32, P, P, i64, P, P, P]),
+            "knng_leaf_dhat": (i32, [P, i64, i32, i32, P, P, P, P, P, P]),
             "knng_exact": (i32, [P, i64, i32, i32, P, i64, P, P, P]),
             "knng_search": (i32, [P, i64, i32, P, i32, P, i64, P, i32, i32, i32, P, P, P]),
             "knng_rvq_train": (i32, [P, i64, i32, i32, i32, i32, u64, P, P, P]),
@@ -204,12 +207,7 @@ def knng_build_ex(data, params, stream=None, out=None):
     return ids, d
 
 
-def knng_build_batched(datas, params, leaf_maxes=None, stream=None):
-    """Independent graphs of several inputs in one build; returns a list of
-    (ids, dists), ids local to each input.  leaf_maxes: per input (0: params')."""
-    datas = [_contig(x, "float32") for x in datas]
-    leaf_maxes = leaf_maxes or [0] * len(datas)
-    k = params.k
+def _instances(datas, k, leaf_maxes, iters=None):
     outs = [(_empty_like_input(x, (x.shape[0], k), "int32"), _empty_like_input(x, (x.shape[0], k), "float32"))
             for x in datas]
     arr = (Instance * len(datas))()
@@ -220,6 +218,16 @@ def knng_build_batched(datas, params, leaf_maxes=None, stream=None):
         arr[i].leaf_max = int(leaf_maxes[i])
         arr[i].out_ids = _ptr(ids).value
         arr[i].out_dists = _ptr(d).value
+        arr[i].twomeans_iters = int(iters[i]) if iters is not None else 0
+    return arr, outs
+
+
+def knng_build_batched(datas, params, leaf_maxes=None, stream=None, twomeans_iters=None):
+    """Independent graphs of several inputs in one build; returns a list of
+    (ids, dists), ids local to each input.  leaf_maxes, twomeans_iters: per
+    input (0: params')."""
+    datas = [_contig(x, "float32") for x in datas]
+    arr, outs = _instances(datas, params.k, leaf_maxes or [0] * len(datas), twomeans_iters)
     with _DeviceCtx(datas[0], stream) as s:
         _check(load().knng_build_batched(len(datas), arr, ctypes.byref(params), s))
     return outs
@@ -274,6 +282,27 @@ class BuildPlan:
         self.close()
 
 
+class BatchedPlan(BuildPlan):
+    """knng_build_batched recorded once into a CUDA graph
+    (knng_plan_create_batched): `launch()` replays it on the instances'
+    tensors into `outs` (a list of (ids, dists)).  Device tensors only."""
+
+    def __init__(self, datas, params, leaf_maxes=None, stream=None, twomeans_iters=None):
+        self.datas = [_contig(x, "float32") for x in datas]
+        self.data = self.datas[0]
+        arr, self.outs = _instances(self.datas, params.k, leaf_maxes or [0] * len(self.datas), twomeans_iters)
+        self._plan = ctypes.c_void_p()
+        self._stream = stream
+        with _DeviceCtx(self.data, stream) as s:
+            _check(load().knng_plan_create_batched(len(self.datas), arr, ctypes.byref(params), s,
+                                                   ctypes.byref(self._plan)))
+
+    def launch(self, stream=None):
+        with _DeviceCtx(self.data, stream if stream is not None else self._stream) as s:
+            _check(load().knng_plan_launch(self._plan, s))
+        return self.outs
+
+
 def knng_refine(data, ids, dists, params, stream=None):
     """Refinement rounds on (ids, dists), in place; returns them."""
     data = _contig(data, "float32")
@@ -317,6 +346,19 @@ def knng_leaf_update(data, k, perm, leaf_offsets, ids, dists, stream=None):
         _check(load().knng_leaf_update(_ptr(data), n, D, k, _ptr(perm), _ptr(leaf_offsets), len(leaf_offsets) - 1,
                                        _ptr(ids), _ptr(dists), s))
     return ids, dists
+
+
+def knng_leaf_dhat(data, precision, stream=None):
+    """Parity hook of the low-precision leaf stage for one cluster (m <= 256
+    points): (d^ m x m, q m x D, scales m, squared norms m, error bounds m)."""
+    data = _contig(data, "float32")
+    m, D = data.shape
+    outs = (_empty_like_input(data, (m, m), "float32"), _empty_like_input(data, (m, D), "float32"),
+            _empty_like_input(data, (m,), "float32"), _empty_like_input(data, (m,), "float32"),
+            _empty_like_input(data, (m,), "float32"))
+    with _DeviceCtx(data, stream) as s:
+        _check(load().knng_leaf_dhat(_ptr(data), m, D, precision, *[_ptr(o) for o in outs], s))
+    return outs
 
 
 def knng_search(data, graph_ids, queries, seeds, t0, ks, stream=None):

@@ -51,10 +51,50 @@ void cuda_check(cudaError_t e, const char* what) {
 // Sets the message knng_last_error returns (for entry points outside this file).
 void record_error(const char* msg) { g_last_error = msg; }
 
+// ---------------------------------------------------------------- fault injection
+// KNNG_FAULT=alloc|launch makes the next calls fail on the host, for tests of
+// the error paths (no device fault is ever made): "alloc" fails the workspace
+// allocation as if the pool were out of memory (KNNG_ENOMEM); "launch" adds,
+// before the call's first kernel, one launch the runtime refuses on the host
+// (more threads per block than any GPU allows), which the call's launch check
+// reports (KNNG_ECUDA).  The variable is read at the start of every call.
+namespace {
+thread_local int g_fault = 0;  // 0 none, 1 alloc, 2 launch
+thread_local bool g_fault_fired = false;
+// The first launch error of the current call, taken right after the launch:
+// later runtime calls of the same call may clear the runtime's own record.
+thread_local cudaError_t g_launch_error = cudaSuccess;
+
+__global__ void k_refused() {}
+}  // namespace
+
+void fault_begin() {
+    const char* e = getenv("KNNG_FAULT");
+    g_fault = !e ? 0 : strcmp(e, "alloc") == 0 ? 1 : strcmp(e, "launch") == 0 ? 2 : 0;
+    g_fault_fired = false;
+    g_launch_error = cudaSuccess;
+}
+
+cudaError_t launch_error() {
+    const cudaError_t last = cudaGetLastError();
+    return g_launch_error != cudaSuccess ? g_launch_error : last;
+}
+
+bool fault_alloc() { return g_fault == 1; }
+
+void fault_launch_point(cudaStream_t s) {
+    if (g_fault != 2 || g_fault_fired) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    g_fault_fired = true;
+    k_refused<<<1, 2048, 0, s>>>();
+}
+
 namespace {
 template <class F>
 int guarded(F&& f) {
     g_last_error.clear();
+    fault_begin();
     try {
         f();
         return KNNG_OK;
@@ -122,6 +162,7 @@ bool launch_log() {
 
 LaunchScope::LaunchScope(const char* name, cudaStream_t s, double bytes, double flops, int kernels)
     : name_(name), s_(s), bytes_(bytes), flops_(flops), slot_(-1) {
+    fault_launch_point(s);
     if (launch_log()) fprintf(stderr, "launch %s %.0f %.0f\n", name, bytes, flops);
     StatRegistry& r = reg();
     std::lock_guard<std::mutex> lk(r.mu);
@@ -173,6 +214,8 @@ bool stats_on() {
 void stats_flush() { reg().flush(); }
 
 LaunchScope::~LaunchScope() {
+    const cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess && g_launch_error == cudaSuccess) g_launch_error = e;
     StatRegistry& r = reg();
     std::lock_guard<std::mutex> lk(r.mu);
     if (slot_ >= 0 && slot_ < (int)r.pending.size()) cudaEventRecord(r.pending[slot_].b, s_);
@@ -220,6 +263,7 @@ struct Workspace {
         size = used;
         used = 0;
         if (size == 0) return;
+        if (fault_alloc()) fail(KNNG_ENOMEM, "workspace allocation: injected fault (KNNG_FAULT=alloc)");
         void* p = nullptr;
         cuda_check(cudaMallocFromPoolAsync(&p, size, device_pool(), s), "workspace allocation");
         base = static_cast<char*>(p);
@@ -275,6 +319,16 @@ void download(DevBuf<T>& b, cudaStream_t s) {
 __global__ void k_iota(int32_t* p, int64_t n) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
         p[e] = (int32_t)e;
+}
+
+__global__ void k_fill_f32(float* p, int64_t n, float v) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        p[e] = v;
+}
+
+void launch_fill_value(float* p, int64_t n, float v, cudaStream_t s) {
+    LaunchScope ls("k_fill_f32", s, n * 4.0, 0);
+    k_fill_f32<<<(int)std::min<int64_t>((n + 255) / 256 + 1, 152 * 16), 256, 0, s>>>(p, n, v);
 }
 }  // namespace
 
@@ -465,7 +519,8 @@ void validate_params(const knng_params* p, int64_t n) {
         fail(KNNG_EINVAL, "join_mode = %d unknown", p->join_mode);
     if (p->join_mode == KNNG_JOIN_SAMPLED && (p->sample < 1 || 2 * p->sample > p->k))
         fail(KNNG_EINVAL, "sample = %d outside [1, k / 2] for the sampled join", p->sample);
-    if (p->precision != KNNG_FP32 && p->precision != KNNG_BF16 && p->precision != KNNG_FP16)
+    if (p->precision != KNNG_FP32 && p->precision != KNNG_BF16 && p->precision != KNNG_FP16 &&
+        p->precision != KNNG_FP8)
         fail(KNNG_EINVAL, "precision = %d unknown", p->precision);
     if (p->twomeans_iters < 0 || p->twomeans_iters > 64)
         fail(KNNG_EINVAL, "twomeans_iters = %d out of range [0, 64]", p->twomeans_iters);
@@ -492,11 +547,11 @@ struct BuildLayout {
     int64_t nodes_per_chunk = 0;
     // low-precision leaf stage
     uint16_t* Xl = nullptr;
-    float *lp_nrm = nullptr, *lp_err = nullptr;
+    float *lp_nrm = nullptr, *lp_err = nullptr, *lp_scale = nullptr;
     int* notexact = nullptr;
     // tensor-core join
     uint16_t* Xq = nullptr;
-    float *q_nrm = nullptr, *q_err = nullptr;
+    float *q_nrm = nullptr, *q_err = nullptr, *q_scale = nullptr;
     // byte copy for the tree sweeps
     uint8_t* Xb = nullptr;
     int* bflag = nullptr;
@@ -519,11 +574,18 @@ void make_bytes(const float* X, const Args& a, BuildLayout& b, cudaStream_t s) {
     b.sb.u8_host = f == 0;
 }
 
+// Quantisation type of the low-precision copy for a precision (0 FP16, 1
+// BF16, 2 FP8 E4M3) and the name of its leaf kernel.
+int qtype(int precision) { return precision == KNNG_BF16 ? 1 : precision == KNNG_FP16 ? 0 : 2; }
+const char* leaf_kernel_name(int precision) {
+    return precision == KNNG_BF16 ? "k2_leaf_bf16" : precision == KNNG_FP16 ? "k2_leaf_fp16" : "k2_leaf_fp8";
+}
+
 // Original-order 16-bit copy for the tensor-core stages (also sets the
 // exactness flag); nothing in FP32.
 void quantize_for_join(const float* X, const Args& a, BuildLayout& b, cudaStream_t s) {
     if (!b.Xq) return;
-    launch_quantize(X, a.n, a.D, nullptr, a.p.precision == KNNG_BF16, b.Xq, b.q_nrm, b.q_err, b.notexact, s);
+    launch_quantize(X, a.n, a.D, nullptr, qtype(a.p.precision), b.Xq, b.q_nrm, b.q_err, b.q_scale, b.notexact, s);
     if (b.jb.capture) return;  // a graph records no host reads
     // the kernels pick their path from the device flag; the host copy only
     // sizes the statistics' algorithmic bytes
@@ -542,18 +604,25 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
     const int k = a.p.k, D = a.D;
     b.status = ws.take<int>(4);
     b.G = ws.take<uint64_t>((size_t)n * k);
-    const bool lp_any = a.p.precision != KNNG_FP32;
+    bool lp_any = a.p.precision != KNNG_FP32;
     if (lp_any) b.notexact = ws.take<int>(4);
+    const int qt = qtype(a.p.precision);
+    const size_t row_halves = (size_t)lp_row_bytes(D, qt) / 2;
     if (tree && lp_leaf(a, tp)) {
-        b.Xl = ws.take<uint16_t>((size_t)n * lp_dim(D));
+        b.Xl = ws.take<uint16_t>((size_t)n * row_halves);
         b.lp_nrm = ws.take<float>(n);
         b.lp_err = ws.take<float>(n);
+        if (qt == 2) b.lp_scale = ws.take<float>(n);
     }
-    if (lp_any && (join || tree)) {  // original-order 16-bit copy
-        b.Xq = ws.take<uint16_t>((size_t)n * lp_dim(D));
+    if (lp_any && (join || tree)) {  // original-order low-precision copy
+        b.Xq = ws.take<uint16_t>((size_t)n * row_halves);
         b.q_nrm = ws.take<float>(n);
         b.q_err = ws.take<float>(n);
+        if (qt == 2) b.q_scale = ws.take<float>(n);
     }
+    // the tensor-core join and the tree sweeps read a 16-bit copy when it is
+    // exact; an FP8 copy never is
+    lp_any = lp_any && qt != 2;
     if (join && lp_any) {  // the tensor-core join reads the original-order copy
         b.jb.lp = true;
         b.jb.bf16 = a.p.precision == KNNG_BF16;
@@ -699,7 +768,7 @@ void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& t
         cuda_check(cudaMemcpyAsync(b.plan_dev, tp.host.data(), tp.host.size() * 4, cudaMemcpyHostToDevice, s),
                    "plan upload");
     const bool lp = lp_leaf(a, tp);
-    const bool bf16 = a.p.precision == KNNG_BF16;
+    const int qt = qtype(a.p.precision);
     // re-ranked candidates per row: k plus a margin, at most 63
     const int kp = std::min(63, k + std::max(k / 2, 8));
     if (b.notexact) cuda_check(cudaMemsetAsync(b.notexact, 0, sizeof(int), s), "flag clear");
@@ -711,9 +780,10 @@ void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& t
         const int nleaf = (int)(tp.off[tp.L].size() - 1);
         bool done = false;
         if (lp) {
-            launch_permute16(b.Xq, b.q_nrm, b.q_err, n, a.D, perm, b.Xl, b.lp_nrm, b.lp_err, s);
-            done = launch_leaf_tc(b.Xl, n, X, a.D, perm, leaf_off, nleaf, tp.max_leaf, b.lp_nrm, b.lp_err, k, kp,
-                                  bf16, b.G, b.status, b.notexact, s);
+            launch_permute16(b.Xq, b.q_nrm, b.q_err, b.q_scale, n, lp_row_bytes(a.D, qt), perm, b.Xl, b.lp_nrm,
+                             b.lp_err, b.lp_scale, s);
+            done = launch_leaf_tc(b.Xl, n, X, a.D, perm, leaf_off, nleaf, tp.max_leaf, b.lp_nrm, b.lp_err,
+                                  b.lp_scale, k, kp, qt, b.G, b.status, b.notexact, s);
         }
         if (!done) launch_leaf_fp32(X, a.D, perm, leaf_off, nleaf, tp.max_leaf, k, b.G, b.status, s);
         const int slot = pass - (a.p.tree_passes - b.jb.npass);
@@ -788,100 +858,143 @@ int knng_build_ex(const float* data, int64_t n, int D, const knng_params* p, int
         launch_unpack(b.G, oi.dev, od.dev, (int64_t)nk, s);
         download(oi, s);
         download(od, s);
-        cuda_check(cudaGetLastError(), "kernel launch");
+        cuda_check(launch_error(), "kernel launch");
         check_status(b.status, s,
-                     lp_leaf(a, tp) ? (p->precision == KNNG_BF16 ? "k2_leaf_bf16" : "k2_leaf_fp16") : nullptr);
+                     lp_leaf(a, tp) ? leaf_kernel_name(p->precision) : nullptr);
         offers_end(b);
     });
 }
 
+}  // extern "C"
+
+namespace {
+// One group of batched instances (those of one D), concatenated into one
+// forest: its parameters, tree plan, workspace, layout and where each
+// instance's rows and lists lie.
+struct Group {
+    Args a;
+    TreePlan tp;
+    Workspace ws;
+    BuildLayout b;
+    float* X = nullptr;  // the instances' rows, concatenated
+    int32_t* oi = nullptr;
+    float* od = nullptr;
+    std::vector<int> inst;
+    std::vector<int64_t> first, sizes;
+};
+
+// Checks every instance before any device work; returns the instance
+// indices grouped by D.
+std::map<int, std::vector<int>> validate_batch(int n_inst, const knng_instance* inst, const knng_params* p) {
+    if (!p) fail(KNNG_EINVAL, "params is NULL");
+    if (n_inst < 1 || !inst) fail(KNNG_EINVAL, "n_inst = %d (need >= 1 and an instance array)", n_inst);
+    std::map<int, std::vector<int>> by_dim;
+    for (int i = 0; i < n_inst; ++i) {
+        const knng_instance& in = inst[i];
+        knng_params q = *p;
+        if (in.leaf_max > 0) q.leaf_max = in.leaf_max;
+        if (in.twomeans_iters > 0) q.twomeans_iters = in.twomeans_iters;
+        try {
+            if (in.twomeans_iters < 0) fail(KNNG_EINVAL, "twomeans_iters = %d < 0", in.twomeans_iters);
+            validate_common(in.data, in.n, in.D, q.k);
+            validate_params(&q, in.n);
+            if (q.join_mode == KNNG_JOIN_SAMPLED && q.refine_rounds > 0)
+                fail(KNNG_EINVAL, "batched builds do not take the sampled join");
+            if (!in.out_ids || !in.out_dists) fail(KNNG_EINVAL, "output pointer is NULL");
+        } catch (const Error& e) {
+            const std::string msg = g_last_error;
+            fail(e.code, "instance %d: %s", i, msg.c_str());
+        }
+        by_dim[in.D].push_back(i);
+    }
+    for (const auto& grp : by_dim) {  // one forest per D: one Lloyd schedule
+        const int t0 = inst[grp.second[0]].twomeans_iters;
+        for (int i : grp.second)
+            if (inst[i].twomeans_iters != t0)
+                fail(KNNG_EINVAL, "instances of D = %d differ in twomeans_iters (%d, %d)", grp.first, t0,
+                     inst[i].twomeans_iters);
+    }
+    return by_dim;
+}
+
+// Sizes, tree plan and workspace of one group (offer budget: `budget`
+// bytes, 0 = the default).
+void setup_group(Group& g, int D, const std::vector<int>& ids, const knng_instance* inst, const knng_params* p,
+                 size_t budget, cudaStream_t s) {
+    const int k = p->k;
+    std::vector<int> leafs;
+    int64_t n = 0;
+    g.inst = ids;
+    for (int i : ids) {
+        g.first.push_back(n);
+        g.sizes.push_back(inst[i].n);
+        leafs.push_back(inst[i].leaf_max > 0 ? inst[i].leaf_max : p->leaf_max);
+        n += inst[i].n;
+    }
+    if (n >= ((int64_t)1 << 31) || n * (int64_t)k >= ((int64_t)1 << 31))
+        fail(KNNG_EINVAL, "the instances of D = %d hold %lld points together (must stay below 2^31, "
+             "and n * k too)", D, (long long)n);
+    g.a = Args{n, D, *p};
+    if (inst[ids[0]].twomeans_iters > 0) g.a.p.twomeans_iters = inst[ids[0]].twomeans_iters;
+    g.a.offer_budget = budget;
+    if (p->tree_passes > 0) g.tp.make_forest(g.sizes, leafs);
+    const size_t nk = (size_t)n * k;
+    for (int pass = 0; pass < 2; ++pass) {  // layout, then real pointers
+        g.ws.used = 0;
+        g.X = g.ws.take<float>((size_t)n * D);
+        g.oi = g.ws.take<int32_t>(nk);
+        g.od = g.ws.take<float>(nk);
+        carve(g.ws, g.b, g.a, g.tp, p->tree_passes > 0, p->refine_rounds > 0);
+        if (pass == 0) g.ws.allocate(s);
+    }
+    if (p->tree_passes > 0) g.tp.rebase(g.b.plan_dev);
+}
+
+// The group's device work: instance rows in, one forest build, every
+// instance's lists (local ids) out.
+void run_group(Group& g, const knng_instance* inst, cudaStream_t s) {
+    const int k = g.a.p.k, D = g.a.D;
+    cuda_check(cudaMemsetAsync(g.b.status, 0, 4 * sizeof(int), s), "status clear");
+    for (size_t t = 0; t < g.inst.size(); ++t)
+        cuda_check(cudaMemcpyAsync(g.X + g.first[t] * D, inst[g.inst[t]].data, sizeof(float) * g.sizes[t] * D,
+                                   cudaMemcpyDefault, s),
+                   "instance copy");
+    build_core(g.X, g.a, g.b, g.tp, s);
+    for (size_t t = 0; t < g.inst.size(); ++t) {
+        const knng_instance& in = inst[g.inst[t]];
+        const size_t off = (size_t)g.first[t] * k, cnt = (size_t)g.sizes[t] * k;
+        launch_unpack(g.b.G + off, g.oi + off, g.od + off, (int64_t)cnt, s, g.first[t]);
+        cuda_check(cudaMemcpyAsync(in.out_ids, g.oi + off, cnt * 4, cudaMemcpyDefault, s), "ids copy");
+        cuda_check(cudaMemcpyAsync(in.out_dists, g.od + off, cnt * 4, cudaMemcpyDefault, s), "dists copy");
+    }
+}
+}  // namespace
+
+extern "C" {
+
 int knng_build_batched(int n_inst, const knng_instance* inst, const knng_params* p, void* stream) {
     return guarded([&] {
-        if (!p) fail(KNNG_EINVAL, "params is NULL");
-        if (n_inst < 1 || !inst) fail(KNNG_EINVAL, "n_inst = %d (need >= 1 and an instance array)", n_inst);
-        // every instance is checked before any device work
-        std::map<int, std::vector<int>> by_dim;
-        for (int i = 0; i < n_inst; ++i) {
-            const knng_instance& in = inst[i];
-            knng_params q = *p;
-            if (in.leaf_max > 0) q.leaf_max = in.leaf_max;
-            try {
-                validate_common(in.data, in.n, in.D, q.k);
-                validate_params(&q, in.n);
-                if (q.join_mode == KNNG_JOIN_SAMPLED && q.refine_rounds > 0)
-                    fail(KNNG_EINVAL, "batched builds do not take the sampled join");
-                if (!in.out_ids || !in.out_dists) fail(KNNG_EINVAL, "output pointer is NULL");
-            } catch (const Error& e) {
-                const std::string msg = g_last_error;
-                fail(e.code, "instance %d: %s", i, msg.c_str());
-            }
-            by_dim[in.D].push_back(i);
-        }
+        const std::map<int, std::vector<int>> by_dim = validate_batch(n_inst, inst, p);
         cudaStream_t s = (cudaStream_t)stream;
-        const int k = p->k;
         for (const auto& grp : by_dim) {
-            const int D = grp.first;
-            const std::vector<int>& ids = grp.second;
-            std::vector<int64_t> sizes, first;
-            std::vector<int> leafs;
-            int64_t n = 0;
-            for (int i : ids) {
-                first.push_back(n);
-                sizes.push_back(inst[i].n);
-                leafs.push_back(inst[i].leaf_max > 0 ? inst[i].leaf_max : p->leaf_max);
-                n += inst[i].n;
-            }
-            if (n >= ((int64_t)1 << 31) || n * (int64_t)k >= ((int64_t)1 << 31))
-                fail(KNNG_EINVAL, "the instances of D = %d hold %lld points together (must stay below 2^31, "
-                     "and n * k too)", D, (long long)n);
-            Args a{n, D, *p};
-            TreePlan tp;
-            if (p->tree_passes > 0) tp.make_forest(sizes, leafs);
-            Workspace ws;
-            BuildLayout b;
-            float* X = nullptr;
-            int32_t* oi = nullptr;
-            float* od = nullptr;
-            const size_t nk = (size_t)n * k;
-            for (int pass = 0; pass < 2; ++pass) {  // layout, then real pointers
-                ws.used = 0;
-                X = ws.take<float>((size_t)n * D);
-                oi = ws.take<int32_t>(nk);
-                od = ws.take<float>(nk);
-                carve(ws, b, a, tp, p->tree_passes > 0, p->refine_rounds > 0);
-                if (pass == 0) ws.allocate(s);
-            }
-            if (p->tree_passes > 0) tp.rebase(b.plan_dev);
-            cuda_check(cudaMemsetAsync(b.status, 0, 4 * sizeof(int), s), "status clear");
-            offers_begin(b, s);
-            for (size_t t = 0; t < ids.size(); ++t)
-                cuda_check(cudaMemcpyAsync(X + first[t] * D, inst[ids[t]].data, sizeof(float) * sizes[t] * D,
-                                           cudaMemcpyDefault, s),
-                           "instance copy");
-            build_core(X, a, b, tp, s);
-            for (size_t t = 0; t < ids.size(); ++t) {
-                const knng_instance& in = inst[ids[t]];
-                const size_t off = (size_t)first[t] * k, cnt = (size_t)sizes[t] * k;
-                launch_unpack(b.G + off, oi + off, od + off, (int64_t)cnt, s, first[t]);
-                cuda_check(cudaMemcpyAsync(in.out_ids, oi + off, cnt * 4, cudaMemcpyDefault, s), "ids copy");
-                cuda_check(cudaMemcpyAsync(in.out_dists, od + off, cnt * 4, cudaMemcpyDefault, s), "dists copy");
-            }
-            cuda_check(cudaGetLastError(), "kernel launch");
-            check_status(b.status, s,
-                         lp_leaf(a, tp) ? (p->precision == KNNG_BF16 ? "k2_leaf_bf16" : "k2_leaf_fp16") : nullptr);
-            offers_end(b);
+            Group g;
+            setup_group(g, grp.first, grp.second, inst, p, 0, s);
+            offers_begin(g.b, s);
+            run_group(g, inst, s);
+            cuda_check(launch_error(), "kernel launch");
+            check_status(g.b.status, s, lp_leaf(g.a, g.tp) ? leaf_kernel_name(p->precision) : nullptr);
+            offers_end(g.b);
         }
     });
 }
 
 }  // extern "C"
 
-// A build recorded into a CUDA graph: its workspace, plan image and graph.
+// A build recorded into a CUDA graph: its groups (one for a single build,
+// one per D for a batch), each with its workspace and plan image, and the
+// graph.
 struct knng_plan {
-    Args a;
-    TreePlan tp;
-    Workspace ws;
-    BuildLayout b;
+    std::vector<std::unique_ptr<Group>> groups;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -915,6 +1028,57 @@ void rvq_lloyd(const float* X, int64_t N, int D, const float* W1, const int32_t*
 }
 }  // namespace
 
+namespace {
+// Offer buffer of a recorded build: no host reads are possible in a graph,
+// so the chunks are the worst case's size; one chunk per round when the
+// worst case fits `cap` bytes.
+size_t recorded_offer_budget(int64_t n, const knng_params* p, double cap) {
+    const int64_t m = p->join_mode == KNNG_JOIN_FWD_REV ? 2 * p->k : p->k;
+    const double worst = (double)n * std::max<int64_t>(m * (m - 1), 1) * 20.0;
+    return (size_t)std::max<double>((double)offer_budget_bytes(), std::min(worst, cap));
+}
+
+// Records body(stream) into the plan's graph on a stream of its own, with
+// the launch-time statistics off, and instantiates it.
+template <class F>
+void record_plan(knng_plan* pl, F&& body) {
+    cudaStream_t cs;
+    cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream creation");
+    const bool stats_were = stats_on();
+    stats_set(false);
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        try {
+            body(cs);
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            stats_set(stats_were);
+            throw;
+        }
+        e = cudaStreamEndCapture(cs, &pl->graph);
+    }
+    cudaStreamDestroy(cs);
+    stats_set(stats_were);
+    cuda_check(e, "stream capture");
+    cuda_check(cudaGraphInstantiate(&pl->exec, pl->graph, 0), "graph instantiation");
+}
+
+// A group's workspace is allocated on the default stream (freed there at
+// destroy); its tree plan is uploaded before recording; its kernels make
+// every data-dependent choice on the device.
+void prepare_recorded(Group& g) {
+    cuda_check(cudaStreamSynchronize(nullptr), "workspace allocation");
+    if (g.a.p.tree_passes > 0)
+        cuda_check(cudaMemcpy(g.b.plan_dev, g.tp.host.data(), g.tp.host.size() * 4, cudaMemcpyHostToDevice),
+                   "plan upload");
+    g.b.jb.capture = true;
+    g.b.sb.capture = true;
+}
+}  // namespace
+
 extern "C" {
 
 int knng_plan_create(const float* data, int64_t n, int D, const knng_params* p, int32_t* out_ids, float* out_dists,
@@ -928,56 +1092,58 @@ int knng_plan_create(const float* data, int64_t n, int D, const knng_params* p, 
         if (!out_ids || !out_dists) fail(KNNG_EINVAL, "output pointer is NULL");
         if (!is_device_ptr(data) || !is_device_ptr(out_ids) || !is_device_ptr(out_dists))
             fail(KNNG_EINVAL, "a recorded build needs device buffers (data and outputs)");
+        if (p->join_mode == KNNG_JOIN_SAMPLED && p->refine_rounds > 0)
+            fail(KNNG_EINVAL, "a recorded build does not take the sampled join");
         // work the caller queued on `stream` (its inputs) completes first
         cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
         std::unique_ptr<knng_plan> pl(new knng_plan());
-        pl->a = Args{n, D, *p};
-        // one chunk per round when the worst case fits 48 GB: no host reads
-        // are possible in a graph, so the chunks are the worst case's size
-        if (p->join_mode == KNNG_JOIN_SAMPLED && p->refine_rounds > 0)
-            fail(KNNG_EINVAL, "a recorded build does not take the sampled join");
-        const int64_t m = p->join_mode == KNNG_JOIN_FWD_REV ? 2 * p->k : p->k;
-        const double worst = (double)n * std::max<int64_t>(m * (m - 1), 1) * 20.0;
-        pl->a.offer_budget = (size_t)std::max<double>((double)offer_budget_bytes(), std::min(worst, 48e9));
-        if (p->tree_passes > 0) pl->tp.make(n, p->leaf_max);
+        pl->groups.emplace_back(new Group());
+        Group& g = *pl->groups[0];
+        g.a = Args{n, D, *p};
+        g.a.offer_budget = recorded_offer_budget(n, p, 48e9);
+        if (p->tree_passes > 0) g.tp.make(n, p->leaf_max);
         for (int pass = 0; pass < 2; ++pass) {
-            pl->ws.used = 0;
-            carve(pl->ws, pl->b, pl->a, pl->tp, p->tree_passes > 0, p->refine_rounds > 0);
-            if (pass == 0) pl->ws.allocate(nullptr);  // freed on the default stream at destroy
+            g.ws.used = 0;
+            carve(g.ws, g.b, g.a, g.tp, p->tree_passes > 0, p->refine_rounds > 0);
+            if (pass == 0) g.ws.allocate(nullptr);
         }
-        cuda_check(cudaStreamSynchronize(nullptr), "workspace allocation");
-        if (p->tree_passes > 0) {
-            pl->tp.rebase(pl->b.plan_dev);
-            cuda_check(cudaMemcpy(pl->b.plan_dev, pl->tp.host.data(), pl->tp.host.size() * 4, cudaMemcpyHostToDevice),
-                       "plan upload");
+        if (p->tree_passes > 0) g.tp.rebase(g.b.plan_dev);
+        prepare_recorded(g);
+        record_plan(pl.get(), [&](cudaStream_t cs) {
+            cuda_check(cudaMemsetAsync(g.b.status, 0, 4 * sizeof(int), cs), "status clear");
+            build_core(data, g.a, g.b, g.tp, cs);
+            launch_unpack(g.b.G, out_ids, out_dists, n * (int64_t)p->k, cs);
+        });
+        *out_plan = pl.release();
+    });
+}
+
+int knng_plan_create_batched(int n_inst, const knng_instance* inst, const knng_params* p, void* stream,
+                             knng_plan** out_plan) {
+    return guarded([&] {
+        if (!out_plan) fail(KNNG_EINVAL, "out_plan is NULL");
+        *out_plan = nullptr;
+        const std::map<int, std::vector<int>> by_dim = validate_batch(n_inst, inst, p);
+        for (int i = 0; i < n_inst; ++i)
+            if (!is_device_ptr(inst[i].data) || !is_device_ptr(inst[i].out_ids) || !is_device_ptr(inst[i].out_dists))
+                fail(KNNG_EINVAL, "instance %d: a recorded build needs device buffers (data and outputs)", i);
+        cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
+        std::unique_ptr<knng_plan> pl(new knng_plan());
+        // the groups run one after another: each holds an equal share of the
+        // 48 GB a recorded build may give its offers
+        const double cap = 48e9 / (double)by_dim.size();
+        for (const auto& grp : by_dim) {
+            pl->groups.emplace_back(new Group());
+            Group& g = *pl->groups.back();
+            int64_t n = 0;
+            for (int i : grp.second) n += inst[i].n;
+            setup_group(g, grp.first, grp.second, inst, p, recorded_offer_budget(n, p, cap), nullptr);
+            prepare_recorded(g);
         }
-        pl->b.jb.capture = true;
-        pl->b.sb.capture = true;
-        // the recording stream: launch-time statistics stay off while recording
-        cudaStream_t cs;
-        cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream creation");
-        const bool stats_were = stats_on();
-        stats_set(false);
-        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            try {
-                cuda_check(cudaMemsetAsync(pl->b.status, 0, 4 * sizeof(int), cs), "status clear");
-                build_core(data, pl->a, pl->b, pl->tp, cs);
-                launch_unpack(pl->b.G, out_ids, out_dists, n * (int64_t)p->k, cs);
-            } catch (...) {
-                cudaGraph_t g = nullptr;
-                cudaStreamEndCapture(cs, &g);
-                if (g) cudaGraphDestroy(g);
-                cudaStreamDestroy(cs);
-                stats_set(stats_were);
-                throw;
-            }
-            e = cudaStreamEndCapture(cs, &pl->graph);
-        }
-        cudaStreamDestroy(cs);
-        stats_set(stats_were);
-        cuda_check(e, "stream capture");
-        cuda_check(cudaGraphInstantiate(&pl->exec, pl->graph, 0), "graph instantiation");
+        // the instance array is read while recording only
+        record_plan(pl.get(), [&](cudaStream_t cs) {
+            for (auto& g : pl->groups) run_group(*g, inst, cs);
+        });
         *out_plan = pl.release();
     });
 }
@@ -1006,7 +1172,7 @@ int knng_plan_launch(knng_plan* plan, void* stream) {
 int knng_plan_check(knng_plan* plan, void* stream) {
     return guarded([&] {
         if (!plan) fail(KNNG_EINVAL, "no plan");
-        check_status(plan->b.status, (cudaStream_t)stream);
+        for (auto& g : plan->groups) check_status(g->b.status, (cudaStream_t)stream);
     });
 }
 
@@ -1080,7 +1246,7 @@ int knng_refine(const float* data, int64_t n, int D, const knng_params* p, int32
         launch_unpack(b.G, gi.dev, gd.dev, (int64_t)nk, s);
         download(gi, s);
         download(gd, s);
-        cuda_check(cudaGetLastError(), "kernel launch");
+        cuda_check(launch_error(), "kernel launch");
         check_status(b.status, s);
         offers_end(b);
     });
@@ -1132,8 +1298,67 @@ int knng_partition(const float* data, int64_t n, int D, int leaf_max, int twomea
                        "offsets copy");
         else
             memcpy(out_leaf_offsets, off.data(), noff * 8);
-        cuda_check(cudaGetLastError(), "kernel launch");
+        cuda_check(launch_error(), "kernel launch");
         check_status(b.status, s);
+    });
+}
+
+int knng_leaf_dhat(const float* data, int64_t m, int D, int precision, float* out_dhat, float* out_q,
+                   float* out_scale, float* out_nrm, float* out_err, void* stream) {
+    return guarded([&] {
+        if (!data || !out_dhat || !out_q || !out_scale || !out_nrm || !out_err) fail(KNNG_EINVAL, "NULL pointer");
+        if (m < 2 || m > 256) fail(KNNG_EINVAL, "m = %lld outside [2, 256]", (long long)m);
+        if (D < 1 || D > 4096) fail(KNNG_EINVAL, "D = %d out of range [1, 4096]", D);
+        if (precision != KNNG_BF16 && precision != KNNG_FP16 && precision != KNNG_FP8)
+            fail(KNNG_EINVAL, "precision = %d is not a low-precision form", precision);
+        const int qt = qtype(precision);
+        cudaStream_t s = (cudaStream_t)stream;
+        Workspace ws;
+        DevBuf<float> X, dh, q, sc, nr, er;
+        uint16_t* Xq = nullptr;
+        int32_t *perm = nullptr, *off = nullptr;
+        int *status = nullptr, *notexact = nullptr;
+        uint64_t* G = nullptr;
+        for (int ps = 0; ps < 2; ++ps) {
+            ws.used = 0;
+            bind(ws, X, data, (size_t)m * D, ps);
+            bind(ws, dh, out_dhat, (size_t)m * m, ps);
+            bind(ws, q, out_q, (size_t)m * D, ps);
+            bind(ws, sc, out_scale, (size_t)m, ps);
+            bind(ws, nr, out_nrm, (size_t)m, ps);
+            bind(ws, er, out_err, (size_t)m, ps);
+            Xq = ws.take<uint16_t>((size_t)m * lp_row_bytes(D, qt) / 2);
+            perm = ws.take<int32_t>(m);
+            off = ws.take<int32_t>(2);
+            status = ws.take<int>(4);
+            notexact = ws.take<int>(4);
+            G = ws.take<uint64_t>(m);
+            if (ps == 0) ws.allocate(s);
+        }
+        cuda_check(cudaMemsetAsync(status, 0, 4 * sizeof(int), s), "status clear");
+        cuda_check(cudaMemsetAsync(notexact, 0, 4 * sizeof(int), s), "flag clear");
+        const int32_t hoff[2] = {0, (int32_t)m};
+        cuda_check(cudaMemcpyAsync(off, hoff, sizeof hoff, cudaMemcpyHostToDevice, s), "offsets");
+        upload(X, s);
+        launch_check_finite(X.dev, m * (int64_t)D, status, s);
+        {
+            LaunchScope ls("k_iota", s, m * 4.0, 0);
+            k_iota<<<1, 256, 0, s>>>(perm, m);
+        }
+        // scales: FP8 writes them; 16-bit copies have none (1)
+        if (qt != 2) launch_fill_value(sc.dev, m, 1.f, s);
+        launch_quantize(X.dev, m, D, nullptr, qt, Xq, nr.dev, er.dev, qt == 2 ? sc.dev : nullptr, notexact, s);
+        if (!launch_leaf_tc(Xq, m, X.dev, D, perm, off, 1, (int)m, nr.dev, er.dev, qt == 2 ? sc.dev : nullptr, 1, 1,
+                            qt, G, status, notexact, s, dh.dev))
+            fail(KNNG_ECUDA, "the tensor-core leaf kernel cannot run for D = %d", D);
+        launch_lp_to_float(Xq, m, D, qt, q.dev, s);
+        download(dh, s);
+        download(q, s);
+        download(sc, s);
+        download(nr, s);
+        download(er, s);
+        cuda_check(launch_error(), "kernel launch");
+        check_status(status, s);
     });
 }
 
@@ -1193,7 +1418,7 @@ int knng_leaf_update(const float* data, int64_t n, int D, int k, const int32_t* 
         launch_unpack(G, gi.dev, gd.dev, (int64_t)nk, s);
         download(gi, s);
         download(gd, s);
-        cuda_check(cudaGetLastError(), "kernel launch");
+        cuda_check(launch_error(), "kernel launch");
         check_status(status, s);
     });
 }
@@ -1243,7 +1468,7 @@ int knng_search(const float* data, int64_t n, int D, const int32_t* graph_ids, i
                           t0, ks, tab, cl, oi.dev, od.dev, st);
         download(oi, st);
         download(od, st);
-        cuda_check(cudaGetLastError(), "kernel launch");
+        cuda_check(launch_error(), "kernel launch");
         check_status(status, st);
     });
 }
@@ -1291,7 +1516,7 @@ int knng_rvq_train(const float* data, int64_t n, int D, int W1, int W2, int iter
         rvq_lloyd(R, n, D, nullptr, nullptr, W2, iters, seed, 2, o2.dev, codes, order, hist, gofs, tmp, pos, hpos, st);
         download(o1, st);
         download(o2, st);
-        cuda_check(cudaGetLastError(), "kernel launch");
+        cuda_check(launch_error(), "kernel launch");
         check_status(status, st);
     });
 }
@@ -1343,7 +1568,7 @@ int knng_rvq_index(const float* data, int64_t n, int D, const float* words1, int
         download(cd, st);
         download(off, st);
         download(li, st);
-        cuda_check(cudaGetLastError(), "kernel launch");
+        cuda_check(launch_error(), "kernel launch");
         check_status(status, st);
     });
 }
@@ -1396,7 +1621,7 @@ int knng_rvq_seeds(const float* words1, int W1, const float* words2, int W2, int
         launch_rvq_tables(w1.dev, W1, w2.dev, W2, D, n1, n2, x12, w1T, w2T, st);
         launch_rvq_seeds(w1T, W1, w2T, W2, D, n1, n2, x12, off.dev, li.dev, Qb.dev, m, probe1, s, Sb.dev, status, st);
         download(Sb, st);
-        cuda_check(cudaGetLastError(), "kernel launch");
+        cuda_check(launch_error(), "kernel launch");
         check_status(status, st);
     });
 }
@@ -1438,7 +1663,7 @@ int knng_exact(const float* data, int64_t n, int D, int k, const int32_t* sample
         }
         download(oi, s);
         download(od, s);
-        cuda_check(cudaGetLastError(), "kernel launch");
+        cuda_check(launch_error(), "kernel launch");
         check_status(status, s);
     });
 }
@@ -1507,7 +1732,7 @@ int knng_recall(const int32_t* ids, const float* dists, const int32_t* gt_ids, c
         launch_recall(di.dev, dd.dev, gi.dev, gd.dev, smp.dev, s_rows, k, counts, s);
         unsigned long long hc[2] = {0, 0};
         cuda_check(cudaMemcpyAsync(hc, counts, sizeof hc, cudaMemcpyDeviceToHost, s), "counts read");
-        cuda_check(cudaGetLastError(), "kernel launch");
+        cuda_check(launch_error(), "kernel launch");
         cuda_check(cudaStreamSynchronize(s), "stream synchronize");
         reg().flush();
         const double denom = (double)s_rows * k;

@@ -22,6 +22,16 @@ struct LaunchScope {
 // Reads the event times of the launches timed since the last flush into the
 // statistics; call after the stream has been synchronised.
 void stats_flush();
+// Host-side fault injection for tests (KNNG_FAULT=alloc|launch, read by
+// fault_begin at the start of each call): fault_alloc() tells an allocation
+// to fail; fault_launch_point(s) issues, once per call, a launch the runtime
+// refuses on the host (never on a capturing stream).
+void fault_begin();
+bool fault_alloc();
+void fault_launch_point(cudaStream_t s);
+// The first error of a launch made in this call (LaunchScope records it right
+// after each launch), else the runtime's last error; both are cleared.
+cudaError_t launch_error();
 
 // ---------------------------------------------------------------- prepare (K0)
 // Sets *status |= kStatusNonFinite if any of the n*D values is not finite.
@@ -107,23 +117,35 @@ void launch_leaf_fp32(const float* X, int D, const int32_t* perm, const int32_t*
 
 // ---------------------------------------------------------------- low precision (K0, K2 tensor cores, K3)
 int lp_dim(int D);  // D rounded up to the 64-element rows of the swizzled tiles
-// Leaf-order 16-bit copy of X (perm: leaf order; NULL = identity), squared
-// norms and quantisation errors; *notexact |= 1 when the 16-bit arithmetic is
-// not exact for this input.
+// Quantisation types of the low-precision copy: 0 FP16, 1 BF16, 2 FP8 E4M3
+// with a scale per row.  Bytes per row of the copy (a multiple of 128).
+int lp_row_bytes(int D, int qt);
+// The leaf certificate's coefficient of (||x^_i|| + ||x^_j||)^2.
+float lp_cert_coeff(int D, int qt);
 // Byte copy of X (rows of Db bytes) and its flag: 0 when every value is an
 // integer in [0, 255].
 void launch_bytes(const float* X, int64_t n, int D, int Db, uint8_t* Xb, int* bflag, cudaStream_t s);
-void launch_quantize(const float* X, int64_t n, int D, const int32_t* perm, bool bf16, uint16_t* Xq, float* nrm,
-                     float* qerr, int* notexact, cudaStream_t s);
-// Leaf-order gather of a 16-bit copy (with its norms and errors).
-void launch_permute16(const uint16_t* Xq, const float* nrm, const float* qerr, int64_t n, int D,
-                      const int32_t* perm, uint16_t* Xl, float* lnrm, float* lerr, cudaStream_t s);
+// Low-precision copy of X (perm: row order; NULL = identity), squared norms
+// of the copy, quantisation errors and (FP8) row scales; *notexact |= 1 when
+// the low-precision arithmetic is not exact for this input (always for FP8).
+void launch_quantize(const float* X, int64_t n, int D, const int32_t* perm, int qt, void* Xq, float* nrm,
+                     float* qerr, float* scale, int* notexact, cudaStream_t s);
+// Leaf-order gather of a low-precision copy (with its norms, errors and
+// scales; scale may be NULL).
+void launch_permute16(const void* Xq, const float* nrm, const float* qerr, const float* scale, int64_t n,
+                      int row_bytes, const int32_t* perm, void* Xl, float* lnrm, float* lerr, float* lscale,
+                      cudaStream_t s);
 // Leaf stage on tcgen05 from the leaf-order copy; false when it cannot run
-// (leaf above 128 points, no tensor-map encoder) and nothing was launched.
-// status[1] counts the rows that fell back to exact recomputation.
-bool launch_leaf_tc(const uint16_t* Xl, int64_t n, const float* X, int D, const int32_t* perm,
-                    const int32_t* leaf_off, int nleaf, int max_leaf, const float* nrm, const float* qerr, int k,
-                    int kp, bool bf16, uint64_t* G, int* status, const int* notexact, cudaStream_t s);
+// (leaf above 256 points, no tensor-map encoder) and nothing was launched.
+// status[1] counts the rows whose first batch of exact evaluations did not
+// settle them.  dump (a parity hook, one leaf of m points): the m x m
+// approximate distances are written there and nothing is selected.
+// The values of a low-precision copy as FP32 (m x D; FP8: the unscaled q).
+void launch_lp_to_float(const void* Xq, int64_t m, int D, int qt, float* out, cudaStream_t s);
+bool launch_leaf_tc(const void* Xl, int64_t n, const float* X, int D, const int32_t* perm,
+                    const int32_t* leaf_off, int nleaf, int max_leaf, const float* nrm, const float* qerr,
+                    const float* scale, int k, int kp, int qt, uint64_t* G, int* status, const int* notexact,
+                    cudaStream_t s, float* dump = nullptr);
 
 // ---------------------------------------------------------------- refinement (K4-K6)
 struct JoinBuffers {

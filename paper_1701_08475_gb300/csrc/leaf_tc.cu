@@ -19,6 +19,17 @@
 // below 2^23, products and sums are exact integers in FP32, d^ is the
 // canonical distance itself and no re-rank is needed.
 //
+// FP8 E4M3 form: each row is scaled first, x~ = s q with s = max|x| / 448 and
+// q the E4M3 rounding (nearest even, saturating) of x / s; the tensor cores
+// form q_i . q_j (kind::f8f6f4, FP32 accumulation), and
+// d^ = ||x~_i||^2 + ||x~_j||^2 - 2 s_i s_j (q_i . q_j).  The bound below then
+// holds with x~ in place of x^ and the FP8 accumulation term c8 added to c_D:
+// the PTX ISA does not state how many bits the FP8 path keeps while it sums,
+// so the certificate assumes at least a 14-bit significand with truncation,
+// c8 = D 2^-13 (a previous generation's FP8 path was reported to keep about
+// 14 bits); the Gram error the hardware actually makes is measured against
+// this assumption by the tests.
+//
 // Error bound of d^ against the exact distance d of the FP32 points (per row
 // i, against every candidate j of the leaf):
 //   |sqrt(d) - sqrt(d~)| <= e_i + e_j            (d~: exact distance of x^)
@@ -31,6 +42,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -103,14 +115,61 @@ __global__ void __launch_bounds__(256) k0_quantize(const float* __restrict__ X, 
     }
 }
 
+// FP8 E4M3 copy with a scale per row (one warp per output row p, dims padded
+// with zeros to Dp): s = max|x| / 448 (1 for a row of zeros), q = E4M3(x / s)
+// rounded to nearest even and saturated, ||x~||^2 = s^2 sum q^2 and an upper
+// bound of e = ||x - s q||.  The FP8 arithmetic is never taken as exact
+// (*notexact |= 1).
+__global__ void __launch_bounds__(256) k0_quantize_e4m3(const float* __restrict__ X, int64_t n, int D, int Dp,
+                                                        const int32_t* __restrict__ perm, uint8_t* __restrict__ Xq,
+                                                        float* __restrict__ nrm, float* __restrict__ qerr,
+                                                        float* __restrict__ scale, int* __restrict__ notexact) {
+    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (p >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = perm ? perm[p] : p;
+    float amax = 0.f;
+    for (int d = lane; d < D; d += 32) amax = fmaxf(amax, fabsf(X[i * D + d]));
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, m));
+    // a row whose largest value is tiny keeps the scale 1 (its values round to
+    // zero or to subnormals, and e then covers them)
+    const float sc = amax >= 1e-30f ? __fdiv_rn(amax, 448.f) : 1.f;
+    float sq = 0.f, e2 = 0.f;
+    for (int d = lane; d < Dp; d += 32) {
+        const float x = d < D ? X[i * D + d] : 0.f;
+        const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(__fdiv_rn(x, sc), __NV_SATFINITE, __NV_E4M3);
+        Xq[p * Dp + d] = (uint8_t)q;
+        const float qf = __half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3)));
+        sq = __fmaf_rn(qf, qf, sq);                // products exact: 4-bit significands
+        const float t = __fmaf_rn(-sc, qf, x);      // x - s q, rounded once
+        e2 = __fmaf_rn(t, t, e2);
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+        sq += __shfl_xor_sync(0xffffffffu, sq, m);
+        e2 += __shfl_xor_sync(0xffffffffu, e2, m);
+    }
+    if (lane == 0) {
+        nrm[p] = __fmul_rn(__fmul_rn(sc, sc), sq);
+        scale[p] = sc;
+        // upper bound: the rounding of each difference (1 + u)^2, the FP32 sum
+        // of Dp squares (Dp + 2) u (Higham, Ch. 3), the square root rounded up
+        qerr[p] = e2 > 0.f ? __fsqrt_ru(__fmul_ru(e2, 1.f + (float)(Dp + 16) * 5.9604645e-8f)) : 0.f;
+        if (p == 0) atomicOr(notexact, 1);
+    }
+}
+
 __device__ __forceinline__ bool lp_exact(int f) { return (f & 1) == 0 && !((f & 2) && (f & 4)); }
 
 // Leaf-order copy gathered from the original-order one: row p of the output
-// is row perm[p] of the input (16-byte pieces), with its norm and error.
+// is row perm[p] of the input (16-byte pieces), with its norm, error and
+// (FP8 only) scale.
 __global__ void __launch_bounds__(256) k0_permute16(const uint4* __restrict__ Xq, const float* __restrict__ nrm,
-                                                    const float* __restrict__ qerr, int64_t n, int q_per_row,
-                                                    const int32_t* __restrict__ perm, uint4* __restrict__ Xl,
-                                                    float* __restrict__ lnrm, float* __restrict__ lerr) {
+                                                    const float* __restrict__ qerr, const float* __restrict__ scale,
+                                                    int64_t n, int q_per_row, const int32_t* __restrict__ perm,
+                                                    uint4* __restrict__ Xl, float* __restrict__ lnrm,
+                                                    float* __restrict__ lerr, float* __restrict__ lscale) {
     const int64_t total = n * q_per_row;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = e / q_per_row;
@@ -120,6 +179,7 @@ __global__ void __launch_bounds__(256) k0_permute16(const uint4* __restrict__ Xq
         if (q == 0) {
             lnrm[p] = nrm[i];
             lerr[p] = qerr[i];
+            if (scale) lscale[p] = scale[i];
         }
     }
 }
@@ -127,7 +187,8 @@ __global__ void __launch_bounds__(256) k0_permute16(const uint4* __restrict__ Xq
 // ---------------------------------------------------------------- K2/K3
 constexpr int kTcRows = 128;             // M = N = 128 tile: leaves up to 128 points
 constexpr int kTcK = 64;                 // 16-bit elements per 128-byte swizzled row
-constexpr int kStageBytes = kTcRows * kTcK * 2;
+constexpr int kRowChunk = 128;           // bytes of a row per K chunk (one swizzle span)
+constexpr int kStageBytes = kTcRows * kRowChunk;
 constexpr int kTcThreads = 128;
 
 struct TcSmem {
@@ -137,11 +198,11 @@ struct TcSmem {
 
 // MT row tiles of 128 (leaves up to 128 MT points): stages of MT boxes, the
 // d^ rows of one tile, barriers, then misc: tmem address, abort flag,
-// ids / norms / errors / rounded-up sqrt norms [128 MT] each, two maxima; then
-// 32 keys of merge scratch per warp
-__host__ __device__ inline TcSmem tc_smem(int Dp, int MT) {
+// ids / norms / errors / rounded-up sqrt norms / scales [128 MT] each, two
+// maxima; then 32 keys of merge scratch per warp.  Dpb: bytes per row.
+__host__ __device__ inline TcSmem tc_smem(int Dpb, int MT) {
     TcSmem L;
-    const int nk = Dp / kTcK;
+    const int nk = Dpb / kRowChunk;
     const int smax = MT == 1 ? 4 : 2;
     L.stages = nk < smax ? nk : smax;
     L.stage_off = 0;
@@ -157,7 +218,7 @@ __host__ __device__ inline TcSmem tc_smem(int Dp, int MT) {
         L.bar_off = L.dt_off + (size_t)kTcRows * (kTcRows * MT + 1) * 4;
     }
     L.misc_off = L.bar_off + (size_t)(2 * L.stages + 1) * 8;
-    L.scratch_off = L.misc_off + 16 + 4 * (size_t)kTcRows * MT * 4 + 16;
+    L.scratch_off = L.misc_off + 16 + 5 * (size_t)kTcRows * MT * 4 + 16;
     L.total = L.scratch_off + (kTcThreads / 32) * 32 * 8;
     return L;
 }
@@ -175,21 +236,27 @@ __device__ __forceinline__ uint64_t list_at(const uint64_t (&v)[NO], int r) {
     return shfl64(mine, r & 31);
 }
 
-template <bool BF16, int NSG, int MT>
-__global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constant__ CUtensorMap tmap, int Dp,
-                                                           const float* __restrict__ X, int D,
+// QT: 0 FP16, 1 BF16 (kind::f16), 2 FP8 E4M3 (kind::f8f6f4, scaled rows).
+// Dpb: bytes per row of the copy; cD: the certificate's coefficient of
+// (||x^_i|| + ||x^_j||)^2.  dump (a parity hook; one leaf): the d^ rows are
+// written to dump (m x m) and nothing is selected.
+template <int QT, int NSG, int MT>
+__global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constant__ CUtensorMap tmap, int Dpb,
+                                                           float cD, const float* __restrict__ X, int D,
                                                            const int32_t* __restrict__ perm,
                                                            const int32_t* __restrict__ leaf_off,
                                                            const float* __restrict__ nrm,
-                                                           const float* __restrict__ qerr, int k, int kp,
+                                                           const float* __restrict__ qerr,
+                                                           const float* __restrict__ scale, int k, int kp,
                                                            uint64_t* __restrict__ G, int* __restrict__ status,
-                                                           const int* __restrict__ notexact) {
+                                                           const int* __restrict__ notexact,
+                                                           float* __restrict__ dump) {
     constexpr int RW = kTcRows * MT;      // leaf rows (and Gram columns) held
     constexpr int DTS = RW + 1;           // d^ row stride
     constexpr int SB = kStageBytes * MT;  // one K chunk of all rows
     extern __shared__ uint8_t smem_raw[];
     if (*status & kStatusStop) return;  // whole CTA, before any barrier or tensor memory
-    const TcSmem L = tc_smem(Dp, MT);
+    const TcSmem L = tc_smem(Dpb, MT);
     uint8_t* base = smem_raw + ((1024 - (tc::smem_addr(smem_raw) & 1023)) & 1023);
     float* dt = reinterpret_cast<float*>(base + L.dt_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bar_off);
@@ -199,9 +266,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
     float* snrm = reinterpret_cast<float*>(sid + RW);
     float* serr = snrm + RW;
     float* srt = serr + RW;   // ||x^|| rounded up
-    float* smax = srt + RW;   // [0] max ||x^||, [1] max e
+    float* sscl = srt + RW;   // row scales (FP8; 1 otherwise)
+    float* smax = sscl + RW;  // [0] max ||x^||, [1] max e
 
-    const int S = L.stages, nk = Dp / kTcK;
+    const int S = L.stages, nk = Dpb / kRowChunk;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int leaf = blockIdx.x;
     const int a = leaf_off[leaf];
@@ -227,6 +295,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
         sid[r] = in ? perm[a + r] : 0;
         snrm[r] = in ? nrm[a + r] : 0.f;
         serr[r] = in ? qerr[a + r] : 0.f;
+        sscl[r] = (in && QT == 2) ? scale[a + r] : 1.f;
     }
     __syncthreads();
     tc::fence_after_sync();
@@ -236,15 +305,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
     // Gram is A = rows 128 t .., B = all RW rows (N = RW), into columns t RW ..
     if (tid == 0) {
         bool ok = true;
-        const uint32_t idesc = tc::idesc_f16(BF16, kTcRows, RW);
+        const uint32_t idesc = QT == 2 ? tc::idesc_e4m3(kTcRows, RW) : tc::idesc_f16(QT == 1, kTcRows, RW);
         int issued = 0, consumed = 0;
         auto load_stage = [&](int s, int c) {
             const uint32_t fb = full0 + 8 * s;
             tc::mbar_expect_tx(fb, SB);
 #pragma unroll
             for (int t = 0; t < MT; ++t)
-                tc::tma_load_2d(tc::smem_addr(base + (size_t)s * SB + (size_t)t * kStageBytes), &tmap, c * kTcK,
-                                a + t * kTcRows, fb);
+                tc::tma_load_2d(tc::smem_addr(base + (size_t)s * SB + (size_t)t * kStageBytes), &tmap,
+                                c * (QT == 2 ? kRowChunk : kTcK), a + t * kTcRows, fb);
         };
         for (; issued < S && issued < nk; ++issued) load_stage(issued, issued);
         for (int c = 0; c < nk; ++c) {
@@ -258,9 +327,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
 #pragma unroll
             for (int t = 0; t < MT; ++t)
 #pragma unroll
-                for (int kk = 0; kk < kTcK / 16; ++kk)  // K = 16 per instruction: 32 bytes along the row
-                    tc::mma_f16(tmem + (uint32_t)(t * RW), d0 + (uint64_t)(t * (kStageBytes >> 4)) + 2 * kk,
-                                d0 + 2 * kk, idesc, (c | kk) != 0);
+                for (int kk = 0; kk < kRowChunk / 32; ++kk) {  // 32 bytes along the row per instruction
+                    // (K = 16 16-bit or K = 32 FP8 elements)
+                    if (QT == 2)
+                        tc::mma_f8(tmem + (uint32_t)(t * RW), d0 + (uint64_t)(t * (kStageBytes >> 4)) + 2 * kk,
+                                   d0 + 2 * kk, idesc, (c | kk) != 0);
+                    else
+                        tc::mma_f16(tmem + (uint32_t)(t * RW), d0 + (uint64_t)(t * (kStageBytes >> 4)) + 2 * kk,
+                                    d0 + 2 * kk, idesc, (c | kk) != 0);
+                }
             tc::mma_commit(empty0 + 8 * s);
             if (c + S < nk) {
                 if (!tc::mbar_wait(empty0 + 8 * s, (uint32_t)((c / S) & 1), status)) {
@@ -330,10 +405,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
         for (int cc = 0; cc < RW / 32; ++cc) {
             float v[32];
             tc::tmem_ld_32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * RW + cc * 32), v);
+            if (QT == 2) {
+                const float s2 = __fmul_rn(2.f, sscl[R]);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int col = cc * 32 + j;
-                dt[rd * DTS + col] = __fsub_rn(__fadd_rn(snrm[R], snrm[col]), __fmul_rn(2.f, v[j]));
+                for (int j = 0; j < 32; ++j) {
+                    const int col = cc * 32 + j;
+                    dt[rd * DTS + col] =
+                        __fsub_rn(__fadd_rn(snrm[R], snrm[col]), __fmul_rn(__fmul_rn(s2, sscl[col]), v[j]));
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = cc * 32 + j;
+                    dt[rd * DTS + col] = __fsub_rn(__fadd_rn(snrm[R], snrm[col]), __fmul_rn(2.f, v[j]));
+                }
             }
         }
     }
@@ -341,6 +426,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
     __syncthreads();
     if (ph == 1 && warp == 0) tc::tmem_dealloc(tmem, kCols);
     const int rows_t = min(r0 + pr, min(kTcRows, m - t * kTcRows));
+    if (dump) {  // the parity hook: the phase's d^ rows, nothing selected
+        for (int e = tid; e < pr * m; e += kTcThreads) {
+            const int r = r0 + e / m, col = e - (e / m) * m;
+            if (r < rows_t) dump[(int64_t)(t * kTcRows + r) * m + col] = dt[(r - r0) * DTS + col];
+        }
+        __syncthreads();
+        continue;
+    }
     for (int r = r0 + warp; r < rows_t; r += kTcThreads / 32) {
         const int R = t * kTcRows + r;  // the row in the leaf; rd: its d^ row
         const int rd = r - r0;
@@ -385,56 +478,104 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
             warp_select_unique<NC + NSG, NSG>(cand, k, res);
             done_row = true;
         } else if (m - 1 > 0) {
-            if (NSG == 1 && lane_key(old[0], k - 1) != kEmptyKey) {
-                // After the first pass: a candidate whose exact distance provably
-                // exceeds the row's k-th entry cannot enter.  With the bound of
-                // the certificate below, per candidate and rounded so that it
-                // stays a lower bound: d >= (sqrt(a - eps) - e_i - e_j)^2.  The
-                // rest (usually a few) get canonical distances and one merge.
-                const float tau = key_dist(lane_key(old[0], k - 1));
-                const float cD = (16.f * Dp + 8.f) * 5.9604644775390625e-8f;
-                unsigned bal[NC];
-                int total = 0;
+            if (NSG == 1) {
+                // Pruned exact re-rank (k <= 32).  With the bound above,
+                // evaluated per candidate and rounded so that it stays a lower
+                // bound, lb_c = (sqrt(a_c - eps_c) - e_i - e_c)^2 <= d_c; a
+                // candidate with lb_c above the row's k-th exact key tau
+                // cannot enter.  Batches of the 32 live candidates of least
+                // approximate value get canonical distances and merge into the
+                // row, which lowers tau; the rest are pruned against it; when
+                // at most 32 remain they are evaluated at once.  The row ends
+                // as the k best of its list and every candidate, the FP32
+                // form's result.
+                const uint64_t kth0 = lane_key(old[0], k - 1);
+                float tau = kth0 == kEmptyKey ? __int_as_float(0x7f800000) : key_dist(kth0);
+                float lbv[NC];
+                uint64_t apx[NC];
+                bool alive[NC];
 #pragma unroll
                 for (int s = 0; s < NC; ++s) {
                     const int c = lane + 32 * s;
-                    bool keep = c < m && c != R;
-                    if (keep) {
-                        const float a = dt[rd * DTS + c];
+                    const bool valid = c < m && c != R;
+                    apx[s] = kEmptyKey;
+                    lbv[s] = __int_as_float(0x7f800000);
+                    if (valid) {
+                        const float av = dt[rd * DTS + c];
+                        apx[s] = make_key(__fadd_rn(av, 0.f), (uint32_t)sid[c]);
                         const float sn = __fadd_ru(srt[R], srt[c]);
-                        const float eps = __fadd_ru(__fmul_ru(cD, __fmul_ru(sn, sn)), __fmul_ru(1.1920928955078125e-7f, fabsf(a)));
-                        const float lo = __fsub_rd(a, eps);
+                        const float eps =
+                            __fadd_ru(__fmul_ru(cD, __fmul_ru(sn, sn)), __fmul_ru(1.1920928955078125e-7f, fabsf(av)));
+                        const float lo = __fsub_rd(av, eps);
+                        float lb = 0.f;
                         if (lo > 0.f) {
                             const float root = __fsub_rd(__fsub_rd(__fsqrt_rd(lo), serr[R]), serr[c]);
-                            if (root > 0.f && __fmul_rd(root, root) > tau) keep = false;
+                            if (root > 0.f) lb = __fmul_rd(root, root);
                         }
+                        lbv[s] = lb;
                     }
-                    bal[s] = __ballot_sync(0xffffffffu, keep);
-                    total += __popc(bal[s]);
+                    alive[s] = valid && lbv[s] <= tau;
                 }
-                if (total <= 32) {
-                    // survivors' columns to lanes, then their canonical keys
-                    int* cols = reinterpret_cast<int*>(wscratch);
-                    int at = 0;
+                uint64_t list = old[0];
+                int batches = 0;
+                for (int it = 0; it <= NC; ++it) {
+                    unsigned bal[NC];
+                    int total = 0;
 #pragma unroll
                     for (int s = 0; s < NC; ++s) {
-                        if ((bal[s] >> lane) & 1u) cols[at + __popc(bal[s] & ((1u << lane) - 1u))] = lane + 32 * s;
-                        at += __popc(bal[s]);
+                        bal[s] = __ballot_sync(0xffffffffu, alive[s]);
+                        total += __popc(bal[s]);
                     }
-                    __syncwarp();
-                    const int c = lane < total ? cols[lane] : -1;
-                    __syncwarp();
+                    if (total == 0) break;
+                    // into an empty list the first batch is k wide (its k-th
+                    // exact key is the first finite tau); later batches 32
+                    const int B = (it == 0 && kth0 == kEmptyKey) ? k : 32;
+                    uint64_t pick = kEmptyKey;  // this lane's candidate of the batch
+                    if (total <= B) {
+                        int at = 0;
+#pragma unroll
+                        for (int s = 0; s < NC; ++s) {
+                            if (alive[s]) wscratch[at + __popc(bal[s] & ((1u << lane) - 1u))] = apx[s];
+                            at += __popc(bal[s]);
+                        }
+                        __syncwarp();
+                        pick = lane < total ? wscratch[lane] : kEmptyKey;
+                        __syncwarp();
+                    } else {
+                        uint64_t tmp[NC], top[1];
+#pragma unroll
+                        for (int s = 0; s < NC; ++s) tmp[s] = alive[s] ? apx[s] : kEmptyKey;
+                        sort_regs<NC>(tmp);
+                        warp_select_unique<NC, 1>(tmp, B, top);
+                        pick = top[0];
+                    }
+                    const uint64_t last = lane_key(pick, B - 1);  // the batch's largest key (lanes below B hold one)
                     uint64_t one[1] = {kEmptyKey};
-                    if (c >= 0)
-                        one[0] = make_key(canon_dist(X + (int64_t)gi * D, X + (int64_t)sid[c] * D, D, vec),
-                                          (uint32_t)sid[c]);
+                    if (pick != kEmptyKey) {
+                        const uint32_t cid = key_id(pick);
+                        one[0] = make_key(canon_dist(X + (int64_t)gi * D, X + (int64_t)cid * D, D, vec), cid);
+                    }
                     uint64_t out;
                     bool changed;
-                    if (warp_merge_few<1>(one, old[0], k, wscratch, out, changed)) {
-                        if (changed && lane < k) grow[lane] = out;
-                        continue;
+                    if (!warp_merge_few<1>(one, list, k, wscratch, out, changed)) {
+                        uint64_t both[2] = {one[0], list};
+                        uint64_t res1[1];
+                        sort_regs<2>(both);
+                        warp_select_unique<2, 1>(both, k, res1);
+                        out = res1[0];
                     }
+                    list = lane < k ? out : kEmptyKey;
+                    ++batches;
+                    if (total <= B) break;
+                    const uint64_t kth = lane_key(list, k - 1);
+                    if (kth != kEmptyKey) tau = key_dist(kth);
+#pragma unroll
+                    for (int s = 0; s < NC; ++s) alive[s] = alive[s] && apx[s] > last && lbv[s] <= tau;
                 }
+                if (batches > (kth0 == kEmptyKey ? 2 : 1) && lane == 0)
+                    atomicAdd(status + 1, 1);  // rows the approximate order did not settle at once
+                if (__any_sync(0xffffffffu, list != old[0]) && lane < k) grow[lane] = list;
+                continue;
             }
             // the kp + 1 best approximate candidates (keys unique: distinct ids)
             uint64_t apx[NC];
@@ -477,8 +618,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
                     const double astar = (double)key_dist(astar_key);
                     const double tau = (double)key_dist(tau_key);
                     const double ni = sqrt((double)snrm[R]);
-                    const double cD = (16.0 * Dp + 8.0) * 5.9604644775390625e-8;  // 2^-24
-                    const double eps = cD * (ni + smax[0]) * (ni + smax[0]) + 1.1920928955078125e-7 * fabs(astar);
+                    const double eps = (double)cD * (ni + smax[0]) * (ni + smax[0]) + 1.1920928955078125e-7 * fabs(astar);
                     const double lo = astar - eps;
                     double root = lo > 0.0 ? sqrt(lo) : 0.0;
                     root -= (double)serr[R] + (double)smax[1];
@@ -512,6 +652,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
     }
 }
 
+// The values held by a low-precision copy as FP32, m x D: the 16-bit values
+// themselves, or the unscaled E4M3 values q (a parity hook's output).
+__global__ void k_lp_to_float(const uint8_t* __restrict__ Xq, int64_t m, int D, int row_bytes, int qt,
+                              float* __restrict__ out) {
+    const int64_t total = m * D;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / D;
+        const int d = (int)(e - r * D);
+        const uint8_t* row = Xq + r * row_bytes;
+        float v;
+        if (qt == 2) {
+            v = __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)row[d], __NV_E4M3)));
+        } else {
+            const uint16_t h = reinterpret_cast<const uint16_t*>(row)[d];
+            v = qt == 1 ? __bfloat162float(__ushort_as_bfloat16(h)) : __half2float(__ushort_as_half(h));
+        }
+        out[e] = v;
+    }
+}
+
 // ---------------------------------------------------------------- host
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -535,70 +695,101 @@ EncodeTiledFn encode_fn() {
 
 int lp_dim(int D) { return (D + kTcK - 1) / kTcK * kTcK; }
 
-void launch_quantize(const float* X, int64_t n, int D, const int32_t* perm, bool bf16, uint16_t* Xq, float* nrm,
-                     float* qerr, int* notexact, cudaStream_t s) {
+int lp_row_bytes(int D, int qt) { return qt == 2 ? (D + kRowChunk - 1) / kRowChunk * kRowChunk : 2 * lp_dim(D); }
+
+float lp_cert_coeff(int D, int qt) {
+    const int Dp = qt == 2 ? lp_row_bytes(D, qt) : lp_dim(D);
+    const double c16 = (16.0 * Dp + 8.0) * 5.9604644775390625e-8;  // 2^-24
+    const double c8 = qt == 2 ? Dp * 1.220703125e-4 : 0.0;          // 2^-13: the FP8 accumulation assumption
+    return (float)((c16 + c8) * (1.0 + 1e-6));
+}
+
+void launch_quantize(const float* X, int64_t n, int D, const int32_t* perm, int qt, void* Xq, float* nrm,
+                     float* qerr, float* scale, int* notexact, cudaStream_t s) {
+    const int Dpb = lp_row_bytes(D, qt);
+    const int grid = (int)((n * 32 + 255) / 256);
+    if (qt == 2) {
+        LaunchScope ls("k0_quantize", s, (double)n * (D * 4.0 + Dpb + 12.0), 0);
+        k0_quantize_e4m3<<<grid, 256, 0, s>>>(X, n, D, Dpb, perm, static_cast<uint8_t*>(Xq), nrm, qerr, scale,
+                                              notexact);
+        return;
+    }
     const int Dp = lp_dim(D);
     LaunchScope ls("k0_quantize", s, (double)n * (D * 4.0 + Dp * 2.0 + 8.0), 0);
-    const int grid = (int)((n * 32 + 255) / 256);
-    if (bf16)
-        k0_quantize<true><<<grid, 256, 0, s>>>(X, n, D, Dp, perm, Xq, nrm, qerr, notexact);
+    if (qt == 1)
+        k0_quantize<true><<<grid, 256, 0, s>>>(X, n, D, Dp, perm, static_cast<uint16_t*>(Xq), nrm, qerr, notexact);
     else
-        k0_quantize<false><<<grid, 256, 0, s>>>(X, n, D, Dp, perm, Xq, nrm, qerr, notexact);
+        k0_quantize<false><<<grid, 256, 0, s>>>(X, n, D, Dp, perm, static_cast<uint16_t*>(Xq), nrm, qerr, notexact);
 }
 
-void launch_permute16(const uint16_t* Xq, const float* nrm, const float* qerr, int64_t n, int D,
-                      const int32_t* perm, uint16_t* Xl, float* lnrm, float* lerr, cudaStream_t s) {
-    const int Dp = lp_dim(D);
-    const int q = Dp / 8;
-    LaunchScope ls("k0_permute16", s, (double)n * (Dp * 4.0 + 16.0), 0);
+void launch_permute16(const void* Xq, const float* nrm, const float* qerr, const float* scale, int64_t n,
+                      int row_bytes, const int32_t* perm, void* Xl, float* lnrm, float* lerr, float* lscale,
+                      cudaStream_t s) {
+    const int q = row_bytes / 16;
+    LaunchScope ls("k0_permute16", s, (double)n * (row_bytes * 2.0 + (scale ? 24.0 : 16.0)), 0);
     int64_t g = (n * q + 255) / 256;
     if (g > 152 * 32) g = 152 * 32;
-    k0_permute16<<<(int)g, 256, 0, s>>>(reinterpret_cast<const uint4*>(Xq), nrm, qerr, n, q, perm,
-                                        reinterpret_cast<uint4*>(Xl), lnrm, lerr);
+    k0_permute16<<<(int)g, 256, 0, s>>>(static_cast<const uint4*>(Xq), nrm, qerr, scale, n, q, perm,
+                                        static_cast<uint4*>(Xl), lnrm, lerr, lscale);
 }
 
-bool launch_leaf_tc(const uint16_t* Xl, int64_t n, const float* X, int D, const int32_t* perm,
-                    const int32_t* leaf_off, int nleaf, int max_leaf, const float* nrm, const float* qerr, int k,
-                    int kp, bool bf16, uint64_t* G, int* status, const int* notexact, cudaStream_t s) {
+void launch_lp_to_float(const void* Xq, int64_t m, int D, int qt, float* out, cudaStream_t s) {
+    LaunchScope ls("k_lp_to_float", s, (double)m * (lp_row_bytes(D, qt) + D * 4.0), 0);
+    int64_t g = (m * D + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    k_lp_to_float<<<(int)(g < 1 ? 1 : g), 256, 0, s>>>(static_cast<const uint8_t*>(Xq), m, D, lp_row_bytes(D, qt), qt,
+                                                       out);
+}
+
+bool launch_leaf_tc(const void* Xl, int64_t n, const float* X, int D, const int32_t* perm,
+                    const int32_t* leaf_off, int nleaf, int max_leaf, const float* nrm, const float* qerr,
+                    const float* scale, int k, int kp, int qt, uint64_t* G, int* status, const int* notexact,
+                    cudaStream_t s, float* dump) {
     if (max_leaf > 2 * kTcRows) return false;
     const int MT = max_leaf > kTcRows ? 2 : 1;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
-    const int Dp = lp_dim(D);
+    const int Dpb = lp_row_bytes(D, qt);
     CUtensorMap tmap;
-    const cuuint64_t gdim[2] = {(cuuint64_t)Dp, (cuuint64_t)n};
-    const cuuint64_t gstride[1] = {(cuuint64_t)Dp * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTcRows};
+    const cuuint64_t gdim[2] = {(cuuint64_t)(qt == 2 ? Dpb : Dpb / 2), (cuuint64_t)n};
+    const cuuint64_t gstride[1] = {(cuuint64_t)Dpb};
+    const cuuint32_t box[2] = {(cuuint32_t)(qt == 2 ? kRowChunk : kTcK), (cuuint32_t)kTcRows};
     const cuuint32_t estride[2] = {1, 1};
-    if (enc(&tmap, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
-            const_cast<uint16_t*>(Xl), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    const CUtensorMapDataType dtype = qt == 2   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                      : qt == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    if (enc(&tmap, dtype, 2, const_cast<void*>(Xl), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
-    const TcSmem L = tc_smem(Dp, MT);
+    const TcSmem L = tc_smem(Dpb, MT);
     const size_t smem = L.total + 1024;
     if (smem > 227 * 1024) return false;
+    const float cD = lp_cert_coeff(D, qt);
     const double mm = (double)max_leaf, rw = 128.0 * MT;
-    LaunchScope ls(bf16 ? "k2_leaf_bf16" : "k2_leaf_fp16", s, (double)nleaf * mm * (Dp * 2.0 + 2 * 8.0 * k),
-                   (double)nleaf * rw * rw * 2.0 * Dp);
-#define KNNG_LEAF_TC(B, NS, T)                                                                                  \
+    const double elems = qt == 2 ? Dpb : Dpb / 2;
+    static const char* names[3] = {"k2_leaf_fp16", "k2_leaf_bf16", "k2_leaf_fp8"};
+    LaunchScope ls(names[qt], s, (double)nleaf * mm * (Dpb + 2 * 8.0 * k), (double)nleaf * rw * rw * 2.0 * elems);
+#define KNNG_LEAF_TC(Q, NS, T)                                                                                  \
     do {                                                                                                        \
-        cudaFuncSetAttribute(k2_leaf_tc<B, NS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
-        k2_leaf_tc<B, NS, T><<<nleaf, kTcThreads, smem, s>>>(tmap, Dp, X, D, perm, leaf_off, nrm, qerr, k, kp, \
-                                                             G, status, notexact);                              \
+        cudaFuncSetAttribute(k2_leaf_tc<Q, NS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+        k2_leaf_tc<Q, NS, T><<<nleaf, kTcThreads, smem, s>>>(tmap, Dpb, cD, X, D, perm, leaf_off, nrm, qerr,  \
+                                                             scale, k, kp, G, status, notexact, dump);          \
     } while (0)
-#define KNNG_LEAF_TC_K(B, T)              \
+#define KNNG_LEAF_TC_K(Q, T)               \
+    do {                                   \
+        if (k > 32) KNNG_LEAF_TC(Q, 2, T); \
+        else KNNG_LEAF_TC(Q, 1, T);        \
+    } while (0)
+#define KNNG_LEAF_TC_T(Q)                 \
     do {                                  \
-        if (k > 32) KNNG_LEAF_TC(B, 2, T); \
-        else KNNG_LEAF_TC(B, 1, T);        \
+        if (MT == 2) KNNG_LEAF_TC_K(Q, 2); \
+        else KNNG_LEAF_TC_K(Q, 1);         \
     } while (0)
-    if (bf16) {
-        if (MT == 2) KNNG_LEAF_TC_K(true, 2);
-        else KNNG_LEAF_TC_K(true, 1);
-    } else {
-        if (MT == 2) KNNG_LEAF_TC_K(false, 2);
-        else KNNG_LEAF_TC_K(false, 1);
-    }
+    if (qt == 2) KNNG_LEAF_TC_T(2);
+    else if (qt == 1) KNNG_LEAF_TC_T(1);
+    else KNNG_LEAF_TC_T(0);
+#undef KNNG_LEAF_TC_T
 #undef KNNG_LEAF_TC_K
 #undef KNNG_LEAF_TC
     return true;

@@ -131,6 +131,7 @@ using namespace knng;
 extern "C" KNNG_API int knng_exact_noalloc(const float* data, int64_t n, int D, int k, const int32_t* sample,
                                            int64_t s, int32_t* out_ids, float* out_dists, void* stream) {
     record_error("");
+    fault_begin();
     if (!data || !sample || !out_ids || !out_dists) return fail(KNNG_EINVAL, "NULL pointer");
     if (D < 1 || D > 4096) return fail(KNNG_EINVAL, "D out of range [1, 4096]");
     if (k < 1 || k > 64) return fail(KNNG_EINVAL, "k out of range [1, 64]");
@@ -154,7 +155,7 @@ extern "C" KNNG_API int knng_exact_noalloc(const float* data, int64_t n, int D, 
     // a launch the runtime refused (for example the dynamic shared memory of
     // the exact kernel) leaves the outputs unwritten: report it before the
     // status word, which would read zero
-    const cudaError_t le = cudaGetLastError();
+    const cudaError_t le = launch_error();
     if (le != cudaSuccess) return fail(KNNG_ECUDA, cudaGetErrorString(le));
     int hs = 0;
     if (cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

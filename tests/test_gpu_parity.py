@@ -365,6 +365,42 @@ def test_batched_build_equals_single_builds(knng, precision):
         _assert_graph_equal(ids, d, _np(ids1), _np(d1))
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_batched_plan_equals_direct_batched(knng, precision):
+    # the batched build recorded into one CUDA graph: every replay equals a
+    # direct knng_build_batched call, also after the instances' data change
+    specs = [(2000, 64, 64, 3), (5003, 64, 128, 3), (777, 128, 40, 2), (3000, 128, 128, 2), (150, 32, 40, 4)]
+    k = 12
+    datas = [_dev(datagen.gaussian_mixture(n, D, 20, seed=n + D) if i % 2 else
+                  datagen.sift_like(n, D=D, n_centres=30, seed=n)) for i, (n, D, _, _) in enumerate(specs)]
+    prec = {"fp32": knng.KNNG_FP32, "bf16": knng.KNNG_BF16}[precision]
+    p = knng.default_params(k=k, leaf_max=64, tree_passes=2, refine_rounds=3, seed=21, precision=prec)
+    lms, its = [lm for _, _, lm, _ in specs], [t for _, _, _, t in specs]
+    want = knng.knng_build_batched(datas, p, leaf_maxes=lms, twomeans_iters=its)
+    with knng.BatchedPlan(datas, p, leaf_maxes=lms, twomeans_iters=its) as plan:
+        assert plan.kernels > 0
+        for _ in range(2):
+            outs = plan.launch()
+            plan.check()
+            for (ids, d), (wi, wd) in zip(outs, want):
+                _assert_graph_equal(ids, d, _np(wi), _np(wd))
+        for i, (n, D, _, _) in enumerate(specs):
+            datas[i].copy_(torch.from_numpy(datagen.gaussian_mixture(n, D, 25, seed=7 * n + D)))
+        want2 = knng.knng_build_batched(datas, p, leaf_maxes=lms, twomeans_iters=its)
+        outs = plan.launch()
+        plan.check()
+        for (ids, d), (wi, wd) in zip(outs, want2):
+            _assert_graph_equal(ids, d, _np(wi), _np(wd))
+    # one instance alone, with its own schedule, gives the same lists
+    n, D, lm, t = specs[1]
+    q = knng.default_params(k=k, leaf_max=lm, tree_passes=2, refine_rounds=3, seed=21, precision=prec,
+                            twomeans_iters=t)
+    ids1, d1 = knng.knng_build_ex(datas[1], q)
+    _assert_graph_equal(want2[1][0], want2[1][1], _np(ids1), _np(d1))
+    with pytest.raises(knng.KnngError):   # instances of one D must share the schedule
+        knng.knng_build_batched(datas[:2], p, twomeans_iters=[2, 3])
+
+
 def test_batched_build_host_buffers_and_errors(knng):
     X1 = datagen.gaussian_mixture(1000, 16, 10, seed=1)
     X2 = datagen.gaussian_mixture(1500, 16, 10, seed=2)
@@ -375,6 +411,22 @@ def test_batched_build_host_buffers_and_errors(knng):
         _assert_graph_equal(ids, d, _np(ids1), _np(d1))
     with pytest.raises(knng.KnngError):
         knng.knng_build_batched([X1, X2[:5]], p)      # second instance: n <= k
+
+
+def test_autotune_picks_a_measured_tile_and_schedule(knng):
+    from paper_1701_08475_gb300.autotune import autotune
+    datas = [_dev(datagen.gaussian_mixture(6000, 32, 30, seed=1)), _dev(datagen.gaussian_mixture(3000, 64, 30, seed=2))]
+    p = knng.default_params(k=10, tree_passes=1, refine_rounds=1, seed=4)
+    leafs, iters, report = autotune(datas, p, iters_candidates=(1, 3), pilot_rows=4000, sample_rows=200)
+    assert set(report) == {32, 64}
+    for i, D in enumerate((32, 64)):
+        rows = report[D]
+        assert [(r[0], r[1]) for r in rows] == [(64, 1), (64, 3), (128, 1), (128, 3), (256, 1), (256, 3)]
+        assert all(r[2] > 0 and 0 <= r[3] <= 1 for r in rows)
+        best = max(r[3] for r in rows)
+        pick = [r for r in rows if (r[0], r[1]) == (leafs[i], iters[i])][0]
+        assert pick[3] >= best - 0.002
+        assert pick[2] == min(r[2] for r in rows if r[3] >= best - 0.002)
 
 
 def test_autotune_leaf_max_picks_a_measured_candidate(knng):
