@@ -127,7 +127,7 @@ KERNEL_SOURCES = {"k1_": "split.cu", "k2_leaf_fp32": "leaf.cu", "k2_": "leaf_tc.
                   "k5_join_tc": "join_tc.cu", "k5_": "join.cu", "k6_": "join.cu", "k7_": "exact.cu",
                   "k0_": "leaf_tc.cu"}
 ALU_KERNELS = ("k5_join", "k2_leaf_fp32", "k7_exact")
-TENSOR_KERNELS = ("k2_leaf_bf16", "k2_leaf_fp16")
+TENSOR_KERNELS = ("k2_leaf_bf16", "k2_leaf_fp16", "k2_leaf_fp8")
 
 
 def kernel_source_hash(kernel):
@@ -182,11 +182,15 @@ def roofline(stats, clocks, workload, steps, name=None):
                "unit": "Top/s", "frac": round(achieved / peak, 4),
                "peak_source": "derived: 152 SMs x 128 FP32 lanes x median SM clock %.0f MHz" % sm_mhz}
     elif name in TENSOR_KERNELS:
-        # dense 16-bit tensor rate; timed inside a long step: the sustained peak
+        # dense tensor rate; timed inside a long step: the sustained peak.
+        # FP16 runs at the BF16 rate; FP8 at twice it (the nominal 4.5 / 2.25
+        # PFLOP/s ratio applied to the measured BF16 figure)
         achieved = st["flops"] / st["launches"] / (avg_ms * 1e-3) / 1e12
-        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
+        ratio = 2.0 if name == "k2_leaf_fp8" else 1.0
+        peak = ratio * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
         out = {"kernel": name, "bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
-               "frac": round(achieved / peak, 4), "peak_source": "%s bf16_tflops_sustained" % kind}
+               "frac": round(achieved / peak, 4),
+               "peak_source": "%s bf16_tflops_sustained%s" % (kind, " x 2 (nominal FP8 / BF16)" if ratio != 1 else "")}
     else:
         achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
         peak = float(peaks["hbm_gbs"])

@@ -561,6 +561,255 @@ __global__ void __launch_bounds__(32 * kJoinWarps) k5_join(const float* __restri
                        pkey, pcnt, status, xs, thr, mem, dch, stride);
 }
 
+// ---------------------------------------------------------------- K5, CTA-wide
+// The FP32 local join with the pairs of several nodes spread over one CTA.
+// A node's member pairs are cut into the 4 x 4 blocks of the upper triangle
+// of its (mcap / 4)-group member grid: NB = RGN (RGN + 1) / 2 blocks, RGN =
+// mcap / 4; a CTA of 256 threads takes G = 256 / NB nodes at a time and
+// thread t computes block t % NB of node t / NB, so a warp's lanes stay busy
+// whatever NB is (one node per warp leaves lanes idle when NB is not a
+// multiple of 32).  Block (rg, cg) holds members {4 rg + a} x {4 cg + b};
+// member m of a node sits in shared-memory row (m % 4) RGN + m / 4, so lanes
+// of consecutive cg read consecutive rows (an odd float4 stride puts them in
+// different banks) and lanes of one rg read the same row.  Members are new
+// first, so blocks whose two groups hold only old members are skipped whole.
+// Offers as in k5_join; a pair of members that shared a leaf in one of the
+// build's last tree passes makes none (the leaf stage offered it already).
+constexpr int kJ2Threads = 256;
+
+struct J2Layout {
+    int RGN, NB, G, dch, stride;
+    size_t thr, lid, rows, mem, cnt, total;
+};
+
+__host__ __device__ inline J2Layout j2_layout(int D, int mcap, bool leafids) {
+    J2Layout L;
+    L.RGN = mcap / 4;
+    L.NB = L.RGN * (L.RGN + 1) / 2;
+    L.G = L.NB > kJ2Threads ? 1 : kJ2Threads / L.NB;
+    const int slots = L.G * mcap;
+    const int d4 = (D + 3) & ~3;
+    int cap = (44 * 1024 / (slots * 4) - 4) & ~3;
+    if (cap < 4) cap = 4;
+    const int nch = (d4 + cap - 1) / cap;
+    L.dch = ((d4 + nch - 1) / nch + 3) & ~3;
+    L.stride = ((L.dch / 4) & 1) ? L.dch : L.dch + 4;
+    L.thr = 0;
+    L.lid = L.thr + (size_t)slots * 8;
+    L.rows = L.lid + (leafids ? (size_t)slots * 16 : 0);
+    L.mem = L.rows + (size_t)slots * L.stride * 4;
+    L.cnt = L.mem + (size_t)slots * 4;
+    L.total = L.cnt + (size_t)L.G * 2 * 4;
+    return L;
+}
+
+__device__ __forceinline__ int j2_slot(int m, int RGN) { return (m & 3) * RGN + (m >> 2); }
+
+__global__ void __launch_bounds__(kJ2Threads, 4) k5_join_cta(const float* __restrict__ X, int D, int k, int rev,
+                                                         int mcap, const uint64_t* __restrict__ Gold,
+                                                         const uint64_t* __restrict__ R,
+                                                         const int32_t* __restrict__ list,
+                                                         const uint64_t* __restrict__ fnew,
+                                                         const uint64_t* __restrict__ rnew, int64_t node0,
+                                                         int64_t node1, uint32_t* __restrict__ counter, int64_t cap,
+                                                         uint32_t* __restrict__ ptgt, uint64_t* __restrict__ pkey,
+                                                         int32_t* __restrict__ pcnt, int* __restrict__ status,
+                                                         const int* __restrict__ skip_if_exact,
+                                                         const int32_t* __restrict__ count_dev,
+                                                         const int32_t* __restrict__ leafid, int npass) {
+    extern __shared__ float4 smem4[];
+    if (*status & kStatusStop) return;
+    if (count_dev && (int64_t)*count_dev < node1) node1 = *count_dev;
+    if (skip_if_exact) {  // the tensor-core join does this round when the 16-bit copy is exact
+        const int f = *skip_if_exact;
+        if ((f & 1) == 0 && !((f & 2) && (f & 4))) return;
+    }
+    const bool lids = leafid != nullptr && npass > 0;
+    const J2Layout L = j2_layout(D, mcap, lids);
+    char* base = reinterpret_cast<char*>(smem4);
+    uint64_t* thr = reinterpret_cast<uint64_t*>(base + L.thr);  // [G][mcap] by slot
+    int4* slid = reinterpret_cast<int4*>(base + L.lid);         // [G][mcap] by slot
+    float* rows = reinterpret_cast<float*>(base + L.rows);      // [G][mcap][stride] by slot
+    int32_t* mem = reinterpret_cast<int32_t*>(base + L.mem);    // [G][mcap] by member index
+    int* cnt = reinterpret_cast<int*>(base + L.cnt);            // [G] members, then [G] new members
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int RGN = L.RGN, NB = L.NB, G = L.G, dch = L.dch, stride = L.stride;
+    // this thread's block, fixed for the launch
+    const int jn = tid / NB, bk = tid - jn * NB;
+    int rg = 0, cg = 0;
+    {
+        int b = bk;
+        while (b >= RGN - rg) {
+            b -= RGN - rg;
+            ++rg;
+        }
+        cg = rg + b;
+    }
+    const bool vec = (D % 4 == 0);
+    const int64_t ngroups = (node1 - node0 + G - 1) / G;
+    for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int64_t first = node0 + grp * G;
+        // members of the group's nodes (warp w collects nodes w, w + 8, ...):
+        // the new ones first, then the old ones; each takes ids of G_old[i],
+        // then of R[i]
+        for (int j = warp; j < G; j += kJ2Threads / 32) {
+            const int64_t pos = first + j;
+            int M = 0, nn = 0;
+            if (pos < node1) {
+                const int64_t i = list ? (int64_t)list[pos] : pos;
+                const uint64_t fbits = fnew ? fnew[i] : ~0ull, rbits = rnew ? rnew[i] : ~0ull;
+                for (int want = 1; want >= 0; --want) {
+                    for (int src = 0; src < (rev ? 2 : 1); ++src) {
+                        const uint64_t* row = (src == 0 ? Gold : R) + i * k;
+                        const uint64_t bits = src == 0 ? fbits : rbits;
+                        for (int e0 = 0; e0 < k; e0 += 32) {
+                            const int e = e0 + lane;
+                            const uint64_t key = e < k ? row[e] : kEmptyKey;
+                            const bool take = key != kEmptyKey && (int)((bits >> e) & 1ull) == want;
+                            const unsigned bal = __ballot_sync(0xffffffffu, take);
+                            if (take) {
+                                const int m = M + __popc(bal & ((1u << lane) - 1u));
+                                const uint32_t u = key_id(key);
+                                const int sl = j * mcap + j2_slot(m, RGN);
+                                mem[j * mcap + m] = (int32_t)u;
+                                thr[sl] = Gold[(int64_t)u * k + k - 1];
+                                if (lids) slid[sl] = __ldg(reinterpret_cast<const int4*>(leafid) + u);
+                            }
+                            M += __popc(bal);
+                        }
+                    }
+                    if (want == 1) nn = M;
+                }
+            }
+            if (lane == 0) {
+                cnt[j] = M;
+                cnt[G + j] = nn;
+            }
+        }
+        __syncthreads();
+        const int Mj = jn < G ? cnt[jn] : 0, nnj = jn < G ? cnt[G + jn] : 0;
+        // a block with a live pair: both groups hold members, one holds a new one
+        const bool live = jn < G && 4 * rg < Mj && 4 * cg < Mj && (4 * rg < nnj || 4 * cg < nnj);
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+        const int q4 = dch >> 2;
+        for (int d0 = 0; d0 < D; d0 += dch) {
+            const int dl = min(dch, D - d0);
+            // gather dims [d0, d0 + dch) of every member slot (zeros past
+            // the members and past D)
+            if (vec) {
+                for (int e = tid; e < G * mcap * q4; e += kJ2Threads) {
+                    const int sl = e / q4, c4 = e - sl * q4;
+                    const int j = sl / mcap, s = sl - j * mcap;
+                    const int m = (s % RGN) * 4 + s / RGN;  // the member stored in slot s
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (m < cnt[j] && c4 * 4 < dl)
+                        v = __ldg(reinterpret_cast<const float4*>(X + (int64_t)mem[j * mcap + m] * D + d0) + c4);
+                    *reinterpret_cast<float4*>(rows + (size_t)sl * stride + c4 * 4) = v;
+                }
+            } else {
+                for (int e = tid; e < G * mcap * dch; e += kJ2Threads) {
+                    const int sl = e / dch, c = e - sl * dch;
+                    const int j = sl / mcap, s = sl - j * mcap;
+                    const int m = (s % RGN) * 4 + s / RGN;
+                    rows[(size_t)sl * stride + c] =
+                        (m < cnt[j] && c < dl) ? __ldg(X + (int64_t)mem[j * mcap + m] * D + d0 + c) : 0.f;
+                }
+            }
+            __syncthreads();
+            if (live) {
+                const float* rp = rows + (size_t)(jn * mcap + rg) * stride;
+                const float* cp = rows + (size_t)(jn * mcap + cg) * stride;
+                const int step = RGN * stride;  // member 4 g + a sits a RGN rows below member 4 g
+                for (int dq = 0; dq < dch; dq += 4) {
+                    float4 rv[4], cv[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) rv[a] = *reinterpret_cast<const float4*>(rp + a * step + dq);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) cv[b] = *reinterpret_cast<const float4*>(cp + b * step + dq);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            float t = __fsub_rn(rv[a].x, cv[b].x);
+                            acc[a][b] = __fmaf_rn(t, t, acc[a][b]);
+                            t = __fsub_rn(rv[a].y, cv[b].y);
+                            acc[a][b] = __fmaf_rn(t, t, acc[a][b]);
+                            t = __fsub_rn(rv[a].z, cv[b].z);
+                            acc[a][b] = __fmaf_rn(t, t, acc[a][b]);
+                            t = __fsub_rn(rv[a].w, cv[b].w);
+                            acc[a][b] = __fmaf_rn(t, t, acc[a][b]);
+                        }
+                }
+            }
+            __syncthreads();  // the next chunk overwrites the rows
+        }
+        // offers: count, reserve (one atomic per warp), write
+        int c = 0;
+        if (live) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int ia = 4 * rg + a, ib = 4 * cg + b;
+                    if (ia < Mj && ib < Mj && (ia < nnj || ib < nnj) && (rg < cg || a < b)) {
+                        const uint32_t u = (uint32_t)mem[jn * mcap + ia], v = (uint32_t)mem[jn * mcap + ib];
+                        if (u != v) {
+                            const int sa = jn * mcap + a * RGN + rg, sb = jn * mcap + b * RGN + cg;
+                            const bool ou = make_key(acc[a][b], v) < thr[sa];
+                            const bool ov = make_key(acc[a][b], u) < thr[sb];
+                            if ((ou || ov) && !(lids && leaf_mates(slid[sa], slid[sb], npass))) c += ou + ov;
+                        }
+                    }
+                }
+        }
+        const int incl = warp_incl_scan(c);
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total > 0) {
+            uint32_t at = 0;
+            if (lane == 31) at = atomicAdd(counter, (uint32_t)total);
+            at = __shfl_sync(0xffffffffu, at, 31);
+            if ((int64_t)at + total > cap) {
+                if (lane == 0) atomicOr(status, kStatusOverflow);
+            } else if (c > 0) {
+                uint32_t w = at + incl - c;
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int ia = 4 * rg + a, ib = 4 * cg + b;
+                        if (ia < Mj && ib < Mj && (ia < nnj || ib < nnj) && (rg < cg || a < b)) {
+                            const uint32_t u = (uint32_t)mem[jn * mcap + ia], v = (uint32_t)mem[jn * mcap + ib];
+                            if (u != v) {
+                                const int sa = jn * mcap + a * RGN + rg, sb = jn * mcap + b * RGN + cg;
+                                const uint64_t ku = make_key(acc[a][b], v), kv = make_key(acc[a][b], u);
+                                const bool ou = ku < thr[sa], ov = kv < thr[sb];
+                                if ((ou || ov) && !(lids && leaf_mates(slid[sa], slid[sb], npass))) {
+                                    if (ou) {
+                                        ptgt[w] = u;
+                                        pkey[w] = ku;
+                                        ++w;
+                                        atomicAdd(&pcnt[u], 1);
+                                    }
+                                    if (ov) {
+                                        ptgt[w] = v;
+                                        pkey[w] = kv;
+                                        ++w;
+                                        atomicAdd(&pcnt[v], 1);
+                                    }
+                                }
+                            }
+                        }
+                    }
+            }
+        }
+        __syncthreads();  // the next group overwrites members, thresholds and counts
+    }
+}
+
 __global__ void k5_scatter(const uint32_t* __restrict__ ptgt, const uint64_t* __restrict__ pkey,
                            const uint32_t* __restrict__ counter, int64_t cap, const int32_t* __restrict__ poff,
                            int32_t* __restrict__ pcur, uint64_t* __restrict__ grouped,
@@ -875,6 +1124,26 @@ const char* launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev,
             const double m = rev ? 2.0 * k : (double)k;
             LaunchScope ls("k5_join", s, (double)(c1 - c0) * (m * D * 4.0 + 2 * k * 8.0 + m * 8.0),
                            (double)(c1 - c0) * m * (m - 1) / 2 * 3.0 * D);
+            const bool lids = b.leafid != nullptr && b.npass > 0;
+            const J2Layout L2 = j2_layout(D, mcap, lids);
+            // the CTA-wide kernel when it keeps clearly more lanes busy than
+            // one node per warp (whose lanes idle when the block count is not
+            // a multiple of 32)
+            const double warp_eff = (double)L2.NB / (32.0 * ((L2.NB + 31) / 32));
+            const double cta_eff = (double)(L2.G * L2.NB) / kJ2Threads;
+            if (cta_eff >= warp_eff + 0.1) {
+                cudaFuncSetAttribute(k5_join_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L2.total);
+                int per_sm = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k5_join_cta, kJ2Threads, L2.total);
+                if (per_sm < 1) per_sm = 1;
+                const int64_t groups = (c1 - c0 + L2.G - 1) / L2.G;
+                const int grid2 = (int)std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)152 * per_sm));
+                k5_join_cta<<<grid2, kJ2Threads, L2.total, s>>>(X, D, k, rev ? 1 : 0, mcap, Gold, b.R, b.list, b.fnew,
+                                                               b.rnew, c0, c1, b.counter, b.cap, b.ptgt, b.pkey,
+                                                               b.pcnt, status, tc_dev ? b.notexact : nullptr,
+                                                               b.count_dev, lids ? b.leafid : nullptr, b.npass);
+                return "k5_join";
+            }
             const int grid = (int)std::min<int64_t>((c1 - c0 + kJoinWarps - 1) / kJoinWarps, 152 * 32);
 #define KNNG_JOIN(BPL)                                                                                     \
     do {                                                                                                   \

@@ -297,6 +297,9 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
             for (int b = h; b < bend; b += 2) {
                 const uint32_t ub = (uint32_t)mem[base_row + b];
                 if (b == s || ub == ua) continue;
+                // leaf-mates were offered to each other in the leaf stage (with
+                // CERT, no canonical distance is needed for them either)
+                if (CERT && leaf_mates(la, slid[base_row + b], npass)) continue;
                 float d = __fadd_rn(__fsub_rn(__fadd_rn(na, snrm[base_row + b]), __fmul_rn(2.f, priv[b * kRows + r])),
                                     0.f);
                 if (CERT) {
@@ -313,8 +316,7 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                     if (ta != kEmptyKey && lb > key_dist(ta)) continue;
                     d = canon_dist(X + (int64_t)ua * D, X + (int64_t)ub * D, D, vec);
                 }
-                // leaf-mates were offered to each other in the leaf stage
-                if (make_key(d, ub) < ta && !leaf_mates(la, slid[base_row + b], npass)) {
+                if (make_key(d, ub) < ta && (CERT || !leaf_mates(la, slid[base_row + b], npass))) {
                     hit |= 1ull << b;
                     priv[b * kRows + r] = d;
                 }
@@ -325,6 +327,7 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                 pm.decode(p, a, b);
                 const uint32_t pa = (uint32_t)mem[base_row + a], pb = (uint32_t)mem[base_row + b];
                 if (pa == pb) continue;
+                if (CERT && leaf_mates(slid[base_row + a], slid[base_row + b], npass)) continue;
                 float d = __fadd_rn(__fsub_rn(__fadd_rn(snrm[base_row + a], snrm[base_row + b]),
                                               __fmul_rn(2.f, priv[a * kRows + base_row + b])), 0.f);
                 const uint64_t ta = thr[base_row + a], tb = thr[base_row + b];

@@ -207,16 +207,11 @@ __host__ __device__ inline TcSmem tc_smem(int Dpb, int MT) {
     L.stages = nk < smax ? nk : smax;
     L.stage_off = 0;
     const size_t stages = (size_t)L.stages * kStageBytes * MT;
-    if (MT == 1) {
-        // the d^ rows of half a tile at a time, over the stages (dead once
-        // the product is done): a smaller footprint, more CTAs per SM
-        L.dt_off = 0;
-        const size_t dt = (size_t)(kTcRows / 2) * (kTcRows + 1) * 4;
-        L.bar_off = ((stages > dt ? stages : dt) + 15) & ~(size_t)15;
-    } else {
-        L.dt_off = stages;
-        L.bar_off = L.dt_off + (size_t)kTcRows * (kTcRows * MT + 1) * 4;
-    }
+    // the d^ rows of half a row tile at a time, over the stages (dead once
+    // the product is done): a smaller footprint, more CTAs per SM
+    L.dt_off = 0;
+    const size_t dt = (size_t)(kTcRows / 2) * (kTcRows * MT + 1) * 4;
+    L.bar_off = ((stages > dt ? stages : dt) + 15) & ~(size_t)15;
     L.misc_off = L.bar_off + (size_t)(2 * L.stages + 1) * 8;
     L.scratch_off = L.misc_off + 16 + 5 * (size_t)kTcRows * MT * 4 + 16;
     L.total = L.scratch_off + (kTcThreads / 32) * 32 * 8;
@@ -271,11 +266,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
 
     const int S = L.stages, nk = Dpb / kRowChunk;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int leaf = blockIdx.x;
+    // MT = 2: two CTAs per leaf, CTA `tile` takes the leaf's rows
+    // 128 tile .. 128 tile + 127 against all of its (up to 256) columns
+    const int leaf = blockIdx.x / MT, tile = MT == 1 ? 0 : (int)(blockIdx.x % MT);
     const int a = leaf_off[leaf];
     const int m = leaf_off[leaf + 1] - a;
+    if (tile * kTcRows >= m) return;  // a leaf of one tile: nothing for the second CTA
     const uint32_t full0 = tc::smem_addr(bars), empty0 = full0 + 8 * S, done = full0 + 16 * S;
-    constexpr uint32_t kCols = kTcRows * MT * MT;  // tensor-memory columns: MT tiles of RW
+    constexpr uint32_t kCols = kTcRows * MT;  // tensor-memory columns: one row tile against RW columns
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
@@ -301,8 +299,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    // ---- producer + MMA issue (one thread): per K chunk, row tile t of the
-    // Gram is A = rows 128 t .., B = all RW rows (N = RW), into columns t RW ..
+    // ---- producer + MMA issue (one thread): per K chunk, the CTA's row tile
+    // of the Gram, A = rows 128 tile .., B = all RW rows (N = RW)
     if (tid == 0) {
         bool ok = true;
         const uint32_t idesc = QT == 2 ? tc::idesc_e4m3(kTcRows, RW) : tc::idesc_f16(QT == 1, kTcRows, RW);
@@ -324,18 +322,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
             }
             consumed = c + 1;
             const uint64_t d0 = tc::sdesc_k128(tc::smem_addr(base + (size_t)s * SB));
+            const uint64_t da = d0 + (uint64_t)(tile * (kStageBytes >> 4));
 #pragma unroll
-            for (int t = 0; t < MT; ++t)
-#pragma unroll
-                for (int kk = 0; kk < kRowChunk / 32; ++kk) {  // 32 bytes along the row per instruction
-                    // (K = 16 16-bit or K = 32 FP8 elements)
-                    if (QT == 2)
-                        tc::mma_f8(tmem + (uint32_t)(t * RW), d0 + (uint64_t)(t * (kStageBytes >> 4)) + 2 * kk,
-                                   d0 + 2 * kk, idesc, (c | kk) != 0);
-                    else
-                        tc::mma_f16(tmem + (uint32_t)(t * RW), d0 + (uint64_t)(t * (kStageBytes >> 4)) + 2 * kk,
-                                    d0 + 2 * kk, idesc, (c | kk) != 0);
-                }
+            for (int kk = 0; kk < kRowChunk / 32; ++kk) {  // 32 bytes along the row per instruction
+                // (K = 16 16-bit or K = 32 FP8 elements)
+                if (QT == 2)
+                    tc::mma_f8(tmem, da + 2 * kk, d0 + 2 * kk, idesc, (c | kk) != 0);
+                else
+                    tc::mma_f16(tmem, da + 2 * kk, d0 + 2 * kk, idesc, (c | kk) != 0);
+            }
             tc::mma_commit(empty0 + 8 * s);
             if (c + S < nk) {
                 if (!tc::mbar_wait(empty0 + 8 * s, (uint32_t)((c / S) & 1), status)) {
@@ -389,22 +384,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k2_leaf_tc(const __grid_constan
     const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     constexpr int NC = RW / 32;
     uint64_t* wscratch = reinterpret_cast<uint64_t*>(base + L.scratch_off) + warp * 32;
-    // Two phases: the two halves of the one row tile (MT = 1), or the two row
-    // tiles (MT = 2); dt holds the phase's d^ rows.  With MT = 1 dt lies over
-    // the operand stages, which the completed product has read through the
-    // async proxy.
-    if (MT == 1) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    // Two phases: the two halves of the CTA's row tile; dt holds the phase's
+    // d^ rows.  dt lies over the operand stages, which the completed product
+    // has read through the async proxy.
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     for (int ph = 0; ph < 2; ++ph) {
-    const int t = MT == 1 ? 0 : ph;              // row tile
-    const int r0 = MT == 1 ? ph * (kTcRows / 2) : 0;  // the phase's first row in the tile
-    const int pr = MT == 1 ? kTcRows / 2 : kTcRows;   // rows per phase
+    const int t = tile;                // row tile
+    const int r0 = ph * (kTcRows / 2);  // the phase's first row in the tile
+    const int pr = kTcRows / 2;         // rows per phase
     // ---- the phase's d^ rows: thread = TMEM lane = row 128 t + warp * 32 + lane
-    if (MT != 1 || (warp >> 1) == ph) {
+    if ((warp >> 1) == ph) {
         const int rl = warp * 32 + lane, R = t * kTcRows + rl, rd = rl - r0;
 #pragma unroll 1
         for (int cc = 0; cc < RW / 32; ++cc) {
             float v[32];
-            tc::tmem_ld_32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * RW + cc * 32), v);
+            tc::tmem_ld_32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
             if (QT == 2) {
                 const float s2 = __fmul_rn(2.f, sscl[R]);
 #pragma unroll
@@ -773,8 +767,8 @@ bool launch_leaf_tc(const void* Xl, int64_t n, const float* X, int D, const int3
 #define KNNG_LEAF_TC(Q, NS, T)                                                                                  \
     do {                                                                                                        \
         cudaFuncSetAttribute(k2_leaf_tc<Q, NS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
-        k2_leaf_tc<Q, NS, T><<<nleaf, kTcThreads, smem, s>>>(tmap, Dpb, cD, X, D, perm, leaf_off, nrm, qerr,  \
-                                                             scale, k, kp, G, status, notexact, dump);          \
+        k2_leaf_tc<Q, NS, T><<<nleaf * T, kTcThreads, smem, s>>>(tmap, Dpb, cD, X, D, perm, leaf_off, nrm,   \
+                                                             qerr, scale, k, kp, G, status, notexact, dump);    \
     } while (0)
 #define KNNG_LEAF_TC_K(Q, T)               \
     do {                                   \

@@ -5,6 +5,7 @@ it, so that a profiler can capture that stage's kernels.
 
 STAGE:
   build   the whole build (passes + rounds) of the workload
+  sampled the whole build with the sampled refinement round (ms = k / 2)
   split   one tree pass's partition (the K1 kernels)
   leaf    the leaf stage on a random balanced partition made on the host
   refine  one refinement round on a random graph made on the host
@@ -44,11 +45,11 @@ def random_graph(n, k, seed):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("stage", choices=["build", "split", "leaf", "refine", "exact", "search"])
+    ap.add_argument("stage", choices=["build", "sampled", "split", "leaf", "refine", "exact", "search"])
     ap.add_argument("--workload", default="sift-like-1m-d128")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--repeat", type=int, default=1)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp8"])
     a = ap.parse_args()
     import torch
 
@@ -71,9 +72,12 @@ def main():
         if a.stage == "search":
             S = knng.knng_rvq_seeds(w1, w2, off, lids, Qd, 16, 32)
             knng.knng_search(Xd, G, Qd, S, 12, 20)
-        elif a.stage == "build":
+        elif a.stage in ("build", "sampled"):
             p = knng.default_params(k=k, leaf_max=w["leaf_max"], tree_passes=w["passes"], refine_rounds=w["rounds"],
-                                    seed=w["seed"], precision={"fp32": 0, "bf16": 1, "fp16": 2}[a.precision])
+                                    seed=w["seed"], precision={"fp32": 0, "bf16": 1, "fp16": 2, "fp8": 3}[a.precision])
+            if a.stage == "sampled":
+                p.join_mode = knng.KNNG_JOIN_SAMPLED
+                p.sample = k // 2
             knng.knng_build_ex(Xd, p)
         elif a.stage == "split":
             knng.knng_partition(Xd, w["leaf_max"], seed=w["seed"])
