@@ -557,6 +557,22 @@ struct BuildLayout {
     int* bflag = nullptr;
     // leaves of the last tree passes, for the join ([npass][n])
     int32_t* lid = nullptr;
+    // the tree passes' partitions are independent and run concurrently, each
+    // on its own stream with its own permutations and split buffers (slot 0:
+    // perm_a, perm_b and sb above; slots 1 ..: these); the leaf stages follow
+    // in pass order on the caller's stream
+    struct PartSlot {
+        int32_t *perm_a = nullptr, *perm_b = nullptr;
+        float *W = nullptr, *S = nullptr, *S2 = nullptr;
+        uint64_t *thr = nullptr, *thr2 = nullptr;
+        SelState* st = nullptr;
+        uint32_t *ghist = nullptr, *ticket = nullptr;
+        double *partial = nullptr, *segsum = nullptr, *segleft = nullptr;
+        int32_t* tile_left = nullptr;
+    };
+    static constexpr int kPartSlots = 3;
+    int nslots = 1;
+    PartSlot slot[kPartSlots];
 };
 
 int byte_dim(int D) { return (D + 15) & ~15; }
@@ -649,24 +665,42 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.sb.Xb = b.Xb;
         b.sb.Db = byte_dim(D);
         b.sb.bflag = b.bflag;
-        b.perm_a = ws.take<int32_t>(n);
-        b.perm_b = ws.take<int32_t>(n);
         b.plan_dev = ws.take<int32_t>(tp.host.size());
         const int ns = std::max(tp.nseg_max, 1), nt = std::max(tp.ntiles_max, 1);
         const int nl = std::max(tp.nseg_large_max, 1);
-        b.sb.W = ws.take<float>((size_t)ns * D);
-        b.sb.S = ws.take<float>(n);
-        b.sb.thr = ws.take<uint64_t>(ns);
-        b.sb.S2 = ws.take<float>(n);
-        b.sb.thr2 = ws.take<uint64_t>(ns);
-        b.sb.st = ws.take<SelState>(ns);
-        b.sb.ghist = ws.take<uint32_t>((size_t)nl << kRadixBits);
-        b.sb.ticket = ws.take<uint32_t>(nl);
+        b.nslots = std::max(1, std::min(a.p.tree_passes, (int)BuildLayout::kPartSlots));
+        for (int q = 0; q < b.nslots; ++q) {
+            BuildLayout::PartSlot& ps = b.slot[q];
+            ps.perm_a = ws.take<int32_t>(n);
+            ps.perm_b = ws.take<int32_t>(n);
+            ps.W = ws.take<float>((size_t)ns * D);
+            ps.S = ws.take<float>(n);
+            ps.thr = ws.take<uint64_t>(ns);
+            ps.S2 = ws.take<float>(n);
+            ps.thr2 = ws.take<uint64_t>(ns);
+            ps.st = ws.take<SelState>(ns);
+            ps.ghist = ws.take<uint32_t>((size_t)nl << kRadixBits);
+            ps.ticket = ws.take<uint32_t>(nl);
+            ps.partial = ws.take<double>((size_t)std::max(tp.nsweep_max, 1) * 2 * D);
+            ps.segsum = ws.take<double>((size_t)ns * D);
+            ps.segleft = ws.take<double>((size_t)ns * D);
+            ps.tile_left = ws.take<int32_t>(nt);
+        }
+        b.perm_a = b.slot[0].perm_a;
+        b.perm_b = b.slot[0].perm_b;
+        b.sb.W = b.slot[0].W;
+        b.sb.S = b.slot[0].S;
+        b.sb.thr = b.slot[0].thr;
+        b.sb.S2 = b.slot[0].S2;
+        b.sb.thr2 = b.slot[0].thr2;
+        b.sb.st = b.slot[0].st;
+        b.sb.ghist = b.slot[0].ghist;
+        b.sb.ticket = b.slot[0].ticket;
         b.sb.nseg_large = nl;
-        b.sb.partial = ws.take<double>((size_t)std::max(tp.nsweep_max, 1) * 2 * D);
-        b.sb.segsum = ws.take<double>((size_t)ns * D);
-        b.sb.segleft = ws.take<double>((size_t)ns * D);
-        b.sb.tile_left = ws.take<int32_t>(nt);
+        b.sb.partial = b.slot[0].partial;
+        b.sb.segsum = b.slot[0].segsum;
+        b.sb.segleft = b.slot[0].segleft;
+        b.sb.tile_left = b.slot[0].tile_left;
         b.sb.status = b.status;
     }
     if (join) {
@@ -740,26 +774,65 @@ void offers_end(BuildLayout& b) {
 
 // Partition of one pass into perm_a (leaves contiguous).  Returns the buffer
 // holding the result.
-int32_t* run_partition(const float* X, const Args& a, const TreePlan& tp, BuildLayout& b, int pass, cudaStream_t s) {
+int32_t* run_partition(const float* X, const Args& a, const TreePlan& tp, BuildLayout& b, int pass, cudaStream_t s,
+                       int q = 0) {
     const uint64_t ps = splitmix64(a.p.seed ^ (uint64_t)pass);
-    int32_t* pin = b.perm_a;
-    int32_t* pout = b.perm_b;
+    const BuildLayout::PartSlot& sl = b.slot[q];
+    // slot q's private buffers, the rest (copies of X, flags, status) shared
+    SplitBuffers sb = b.sb;
+    sb.W = sl.W;
+    sb.S = sl.S;
+    sb.thr = sl.thr;
+    sb.S2 = sl.S2;
+    sb.thr2 = sl.thr2;
+    sb.st = sl.st;
+    sb.ghist = sl.ghist;
+    sb.ticket = sl.ticket;
+    sb.partial = sl.partial;
+    sb.segsum = sl.segsum;
+    sb.segleft = sl.segleft;
+    sb.tile_left = sl.tile_left;
+    int32_t* pin = sl.perm_a;
+    int32_t* pout = sl.perm_b;
     // the cross-CTA selection accumulates into these and leaves them zero
-    cuda_check(cudaMemsetAsync(b.sb.ghist, 0, sizeof(uint32_t) * ((size_t)b.sb.nseg_large << kRadixBits), s),
+    cuda_check(cudaMemsetAsync(sb.ghist, 0, sizeof(uint32_t) * ((size_t)sb.nseg_large << kRadixBits), s),
                "histogram clear");
-    cuda_check(cudaMemsetAsync(b.sb.ticket, 0, sizeof(uint32_t) * b.sb.nseg_large, s), "ticket clear");
+    cuda_check(cudaMemsetAsync(sb.ticket, 0, sizeof(uint32_t) * sb.nseg_large, s), "ticket clear");
     {
         LaunchScope ls("k_iota", s, a.n * 4.0, 0);
         k_iota<<<grid_1d(a.n), 256, 0, s>>>(pin, a.n);
     }
     for (int l = 0; l < tp.L; ++l) {
-        run_split_level(X, a.D, tp.levels[l], a.p.twomeans_iters, ps, pin, pout, b.sb, s);
+        run_split_level(X, a.D, tp.levels[l], a.p.twomeans_iters, ps, pin, pout, sb, s);
         std::swap(pin, pout);
     }
     return pin;
 }
 
-void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& tp, cudaStream_t s) {
+// Helper streams and events of one call (created and destroyed with it).
+struct SideStreams {
+    cudaStream_t h[BuildLayout::kPartSlots] = {};
+    std::vector<cudaEvent_t> ev;
+    int nh = 0;
+    cudaEvent_t event() {
+        cudaEvent_t e;
+        cuda_check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event creation");
+        ev.push_back(e);
+        return e;
+    }
+    void make(int count) {
+        for (; nh < count; ++nh) cuda_check(cudaStreamCreateWithFlags(&h[nh], cudaStreamNonBlocking), "stream creation");
+    }
+    ~SideStreams() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (int i = 0; i < nh; ++i) cudaStreamDestroy(h[i]);
+    }
+};
+
+// side: helper streams that outlive the call's stream capture (a recorded
+// build); NULL: made here for this call.
+void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& tp, cudaStream_t s,
+                SideStreams* side_in = nullptr) {
     const int64_t n = a.n;
     const int k = a.p.k;
     launch_check_finite(X, n * (int64_t)a.D, b.status, s);
@@ -774,8 +847,36 @@ void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& t
     if (b.notexact) cuda_check(cudaMemsetAsync(b.notexact, 0, sizeof(int), s), "flag clear");
     quantize_for_join(X, a, b, s);
     make_bytes(X, a, b, s);
-    for (int pass = 0; pass < a.p.tree_passes; ++pass) {
-        int32_t* perm = run_partition(X, a, tp, b, pass, s);
+    // partitions: pass p on slot p % nslots (slot 0 on the caller's stream,
+    // slot q > 0 on helper stream q - 1, forked from the caller's stream); a
+    // slot's next partition waits for the leaf stage that read its last one
+    SideStreams side_local;
+    SideStreams& side = side_in ? *side_in : side_local;
+    const int P = a.p.tree_passes, Q = b.nslots;
+    std::vector<int32_t*> perms((size_t)std::max(P, 0), nullptr);
+    std::vector<cudaEvent_t> part_done((size_t)std::max(P, 0), nullptr), leaf_done((size_t)std::max(P, 0), nullptr);
+    if (Q > 1 && P > 1) {
+        side.make(Q - 1);
+        cudaEvent_t fork = side.event();
+        cuda_check(cudaEventRecord(fork, s), "event record");
+        for (int q = 1; q < Q; ++q) cuda_check(cudaStreamWaitEvent(side.h[q - 1], fork, 0), "stream wait");
+    }
+    auto launch_partition = [&](int pass) {
+        const int q = pass % Q;
+        cudaStream_t ps = q == 0 ? s : side.h[q - 1];
+        if (pass >= Q && q > 0) cuda_check(cudaStreamWaitEvent(ps, leaf_done[pass - Q], 0), "stream wait");
+        perms[pass] = run_partition(X, a, tp, b, pass, ps, q);
+        if (q > 0) {
+            part_done[pass] = side.event();
+            cuda_check(cudaEventRecord(part_done[pass], ps), "event record");
+        }
+    };
+    for (int pass = 0; pass < std::min(P, Q); ++pass)
+        if (pass % Q != 0) launch_partition(pass);
+    for (int pass = 0; pass < P; ++pass) {
+        if (pass % Q == 0) launch_partition(pass);  // slot 0: in order on the caller's stream
+        else cuda_check(cudaStreamWaitEvent(s, part_done[pass], 0), "stream wait");
+        int32_t* perm = perms[pass];
         const int32_t* leaf_off = b.plan_dev + tp.leaf_off_at;
         const int nleaf = (int)(tp.off[tp.L].size() - 1);
         bool done = false;
@@ -788,6 +889,12 @@ void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& t
         if (!done) launch_leaf_fp32(X, a.D, perm, leaf_off, nleaf, tp.max_leaf, k, b.G, b.status, s);
         const int slot = pass - (a.p.tree_passes - b.jb.npass);
         if (b.lid && slot >= 0) launch_leaf_ids(perm, leaf_off, nleaf, n, slot, b.lid, s);
+        // the next partition on this pass's slot may reuse its permutations
+        if (pass + Q < P && (pass + Q) % Q != 0) {
+            leaf_done[pass] = side.event();
+            cuda_check(cudaEventRecord(leaf_done[pass], s), "event record");
+            launch_partition(pass + Q);
+        }
     }
     if (a.p.join_mode == KNNG_JOIN_SAMPLED)
         run_refine_sampled(X, n, a.D, k, b.G, b.G2, b.jb, b.nodes_per_chunk, a.p.refine_rounds, a.p.sample,
@@ -952,14 +1059,14 @@ void setup_group(Group& g, int D, const std::vector<int>& ids, const knng_instan
 
 // The group's device work: instance rows in, one forest build, every
 // instance's lists (local ids) out.
-void run_group(Group& g, const knng_instance* inst, cudaStream_t s) {
+void run_group(Group& g, const knng_instance* inst, cudaStream_t s, SideStreams* side = nullptr) {
     const int k = g.a.p.k, D = g.a.D;
     cuda_check(cudaMemsetAsync(g.b.status, 0, 4 * sizeof(int), s), "status clear");
     for (size_t t = 0; t < g.inst.size(); ++t)
         cuda_check(cudaMemcpyAsync(g.X + g.first[t] * D, inst[g.inst[t]].data, sizeof(float) * g.sizes[t] * D,
                                    cudaMemcpyDefault, s),
                    "instance copy");
-    build_core(g.X, g.a, g.b, g.tp, s);
+    build_core(g.X, g.a, g.b, g.tp, s, side);
     for (size_t t = 0; t < g.inst.size(); ++t) {
         const knng_instance& in = inst[g.inst[t]];
         const size_t off = (size_t)g.first[t] * k, cnt = (size_t)g.sizes[t] * k;
@@ -1042,6 +1149,10 @@ size_t recorded_offer_budget(int64_t n, const knng_params* p, double cap) {
 // the launch-time statistics off, and instantiates it.
 template <class F>
 void record_plan(knng_plan* pl, F&& body) {
+    // helper streams for the concurrent partitions: made before and destroyed
+    // after the capture they join
+    SideStreams side;
+    side.make(BuildLayout::kPartSlots - 1);
     cudaStream_t cs;
     cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream creation");
     const bool stats_were = stats_on();
@@ -1049,7 +1160,7 @@ void record_plan(knng_plan* pl, F&& body) {
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         try {
-            body(cs);
+            body(cs, &side);
         } catch (...) {
             cudaGraph_t g = nullptr;
             cudaStreamEndCapture(cs, &g);
@@ -1109,9 +1220,9 @@ int knng_plan_create(const float* data, int64_t n, int D, const knng_params* p, 
         }
         if (p->tree_passes > 0) g.tp.rebase(g.b.plan_dev);
         prepare_recorded(g);
-        record_plan(pl.get(), [&](cudaStream_t cs) {
+        record_plan(pl.get(), [&](cudaStream_t cs, SideStreams* side) {
             cuda_check(cudaMemsetAsync(g.b.status, 0, 4 * sizeof(int), cs), "status clear");
-            build_core(data, g.a, g.b, g.tp, cs);
+            build_core(data, g.a, g.b, g.tp, cs, side);
             launch_unpack(g.b.G, out_ids, out_dists, n * (int64_t)p->k, cs);
         });
         *out_plan = pl.release();
@@ -1141,8 +1252,8 @@ int knng_plan_create_batched(int n_inst, const knng_instance* inst, const knng_p
             prepare_recorded(g);
         }
         // the instance array is read while recording only
-        record_plan(pl.get(), [&](cudaStream_t cs) {
-            for (auto& g : pl->groups) run_group(*g, inst, cs);
+        record_plan(pl.get(), [&](cudaStream_t cs, SideStreams* side) {
+            for (auto& g : pl->groups) run_group(*g, inst, cs, side);
         });
         *out_plan = pl.release();
     });
