@@ -291,10 +291,38 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
         const uint32_t ua = mine ? (uint32_t)mem[r] : 0u;
         if (by_rows && mine) {
             const uint64_t ta = thr[r];
+            // the threshold key as (distance, id): an offer (d, ub) is below it
+            // when d < ta_d, or d == ta_d and ub < ta_id (d >= 0, never NaN);
+            // an empty slot takes everything
+            const float ta_d = ta == kEmptyKey ? __int_as_float(0x7f800000) : key_dist(ta);
+            const uint32_t ta_id = ta == kEmptyKey ? 0xFFFFFFFFu : key_id(ta);
             const float na = snrm[r];
             const int bend = s < nn ? Mj : nn;
             const int4 la = slid[r];
-            for (int b = h; b < bend; b += 2) {
+            int b0 = h;
+            if (!CERT) {
+                // two members per step: independent chains for the scheduler
+                auto below = [&](int b, uint32_t ub, float d) {
+                    return b != s && ub != ua && (d < ta_d || (d == ta_d && ub < ta_id));
+                };
+                for (; b0 + 2 < bend; b0 += 4) {
+                    const int b1 = b0 + 2;
+                    const uint32_t u0 = (uint32_t)mem[base_row + b0], u1 = (uint32_t)mem[base_row + b1];
+                    const float d0 = __fadd_rn(__fsub_rn(__fadd_rn(na, snrm[base_row + b0]),
+                                                         __fmul_rn(2.f, priv[b0 * kRows + r])), 0.f);
+                    const float d1 = __fadd_rn(__fsub_rn(__fadd_rn(na, snrm[base_row + b1]),
+                                                         __fmul_rn(2.f, priv[b1 * kRows + r])), 0.f);
+                    if (below(b0, u0, d0) && !leaf_mates(la, slid[base_row + b0], npass)) {
+                        hit |= 1ull << b0;
+                        priv[b0 * kRows + r] = d0;
+                    }
+                    if (below(b1, u1, d1) && !leaf_mates(la, slid[base_row + b1], npass)) {
+                        hit |= 1ull << b1;
+                        priv[b1 * kRows + r] = d1;
+                    }
+                }
+            }
+            for (int b = b0; b < bend; b += 2) {
                 const uint32_t ub = (uint32_t)mem[base_row + b];
                 if (b == s || ub == ua) continue;
                 // leaf-mates were offered to each other in the leaf stage (with
@@ -313,10 +341,10 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                         if (root > 0.f) lb = __fmul_rd(root, root);
                     }
                     // an empty slot's key accepts everything
-                    if (ta != kEmptyKey && lb > key_dist(ta)) continue;
+                    if (lb > ta_d) continue;
                     d = canon_dist(X + (int64_t)ua * D, X + (int64_t)ub * D, D, vec);
                 }
-                if (make_key(d, ub) < ta && (CERT || !leaf_mates(la, slid[base_row + b], npass))) {
+                if ((d < ta_d || (d == ta_d && ub < ta_id)) && (CERT || !leaf_mates(la, slid[base_row + b], npass))) {
                     hit |= 1ull << b;
                     priv[b * kRows + r] = d;
                 }
