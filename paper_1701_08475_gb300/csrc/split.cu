@@ -101,6 +101,30 @@ __device__ __forceinline__ void find_digit(const uint32_t* hist, int nb, uint32_
     }
 }
 
+// find_digit with the whole CTA: thread t sums bins [t per, (t + 1) per), one
+// block scan, and the thread whose range holds rank krem walks its bins.
+// Called by every thread of the CTA (it synchronises).
+__device__ __forceinline__ void block_find_digit(const uint32_t* hist, int nb, uint32_t krem, int* warp_tot,
+                                                 int* out_digit, uint32_t* out_below) {
+    const int per = nb >= (int)blockDim.x ? nb / (int)blockDim.x : 1;
+    const int b0 = (int)threadIdx.x * per;
+    uint32_t sum = 0;
+    for (int b = b0; b < b0 + per && b < nb; ++b) sum += hist[b];
+    int total;
+    const uint32_t excl = (uint32_t)block_excl_scan((int)sum, warp_tot, &total);
+    if (sum > 0 && excl <= krem && krem < excl + sum) {
+        uint32_t run = excl;
+        for (int b = b0; b < b0 + per && b < nb; ++b) {
+            if (krem < run + hist[b]) {
+                *out_digit = b;
+                *out_below = run;
+                break;
+            }
+            run += hist[b];
+        }
+    }
+}
+
 __global__ void k1_init(const float* __restrict__ X, int D, const int32_t* __restrict__ perm,
                         const int32_t* __restrict__ seg_off, const int32_t* __restrict__ seg_tile0,
                         const int32_t* __restrict__ seg_local, int level, uint64_t pass_seed,
@@ -742,6 +766,7 @@ __global__ void __launch_bounds__(256) k1_select_pass(const float* __restrict__ 
     __shared__ uint32_t hist[1 << kRadixBits];
     __shared__ int sh_last, sh_digit;
     __shared__ uint32_t sh_below;
+    __shared__ int warp_tot[32];
     const int4 t = tiles[blockIdx.x];
     const int seg = t.x, begin = t.y, end = t.z;
     if (st[seg].done) return;  // selected already (value digits, no tie to the left)
@@ -781,7 +806,7 @@ __global__ void __launch_bounds__(256) k1_select_pass(const float* __restrict__ 
     __threadfence();
     for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = atomicExch(&gh[b], 0u);
     __syncthreads();
-    if (threadIdx.x < 32) find_digit(hist, nb, st[seg].krem, &sh_digit, &sh_below);
+    block_find_digit(hist, nb, st[seg].krem, warp_tot, &sh_digit, &sh_below);
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint64_t np = prefix | ((uint64_t)sh_digit << lo);
