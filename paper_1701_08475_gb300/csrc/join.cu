@@ -1041,7 +1041,13 @@ void finish_chunk(int64_t n, int k, uint64_t* Gnew, const JoinBuffers& b, double
 // KNNG_JOIN_SCREEN=1: with a 16-bit copy that is not exact, the join screens
 // pairs on the tensor cores and computes canonical distances only for those
 // the screen cannot exclude (k5_join_tc_cert) instead of running the FP32 join.
-bool join_screen() {
+// The screen runs on request (KNNG_JOIN_SCREEN=1): on every measured float
+// workload the FP32 join was faster (unit-sphere D = 96: 934 against 730 ms;
+// GIST-like D = 960: 434 against 285 ms), its canonical distances of the
+// surviving pairs (a thread per pair over two FP32 rows) costing more than the
+// pairs it saves.
+bool join_screen(int D) {
+    (void)D;
     const char* e = getenv("KNNG_JOIN_SCREEN");
     return e && e[0] == '1';
 }
@@ -1116,8 +1122,10 @@ const char* launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev,
                             launch_join_tc(b.Xq, D, b.qnrm, k, rev, Gold, b.R, c0, c1, b, status, b.notexact,
                                            b.bf16, s);
         // not exact: the tensor cores screen the pairs and canonical distances
-        // decide (on request: it pays only when few pairs survive the screen)
-        if (!tc && !b.capture && b.lp && join_screen() &&
+        // decide (on request).  In a capture the screening join returns at
+        // once on the device when the copy is exact (the exact join above has
+        // run), so no FP32 join is needed
+        if ((!tc || b.capture) && b.lp && join_screen(D) &&
             launch_join_tc(b.Xq, D, b.qnrm, k, rev, Gold, b.R, c0, c1, b, status, b.notexact, b.bf16, s, true, X))
             return "k5_join_tc_cert";
         {

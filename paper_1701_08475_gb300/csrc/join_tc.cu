@@ -34,6 +34,8 @@ constexpr int kRows = 128;
 constexpr int kKc = 64;                  // 16-bit elements per swizzled row
 constexpr int kChunkBytes = kRows * kKc * 2;
 constexpr int kThreads = 256;  // two threads per tile row in the epilogue
+constexpr int kResident = 4;   // chunks of a row (64 16-bit dims each) held at once
+constexpr int kRing = 2;       // chunk buffers for wider rows
 
 __device__ __forceinline__ bool lp_exact_flag(int f) { return (f & 1) == 0 && !((f & 2) && (f & 4)); }
 
@@ -48,7 +50,10 @@ __host__ __device__ inline JtSmem jt_smem(int Dp, int mcap, bool cert) {
     JtSmem L;
     L.tile = 0;
     L.priv = 0;  // the operand tile is dead once the MMA has completed
-    const size_t tile = (size_t)(Dp / kKc) * kChunkBytes, pv = (size_t)mcap * kRows * 4;
+    // rows of up to kResident chunks stay whole in shared memory; wider rows
+    // stream through a ring of kRing chunk buffers
+    const int nk = Dp / kKc;
+    const size_t tile = (size_t)(nk <= kResident ? nk : kRing) * kChunkBytes, pv = (size_t)mcap * kRows * 4;
     L.mem = tile > pv ? tile : pv;
     L.thr = L.mem + kRows * 4;
     L.nrm = L.thr + kRows * 8;
@@ -57,7 +62,7 @@ __host__ __device__ inline JtSmem jt_smem(int Dp, int mcap, bool cert) {
     L.lid = L.srt + (cert ? kRows * 4 : 0);
     L.cnt = L.lid + kRows * 16;
     L.bar = L.cnt + 32 * 4;  // member counts, then new-member counts
-    L.slot = L.bar + 8;
+    L.slot = L.bar + 8 * (1 + kRing);  // the product's barrier, then one per ring buffer
     L.total = L.slot + 8;
     return L;
 }
@@ -131,7 +136,9 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                                                          const int32_t* __restrict__ count_dev,
                                                          const int32_t* __restrict__ leafid, int npass) {
     extern __shared__ uint8_t smem_raw[];
-    if ((*status & kStatusStop) || (!CERT && !lp_exact_flag(*notexact))) return;
+    // the exact form runs when the 16-bit copy is exact, the screening form
+    // (CERT) when it is not; each returns at once otherwise
+    if ((*status & kStatusStop) || (CERT == lp_exact_flag(*notexact))) return;
     if (count_dev && (int64_t)*count_dev < node1) node1 = *count_dev;
     const JtSmem L = jt_smem(Dp, mcap, CERT);
     uint8_t* base = smem_raw + ((1024 - (tc::smem_addr(smem_raw) & 1023)) & 1023);
@@ -150,10 +157,13 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
     const int nk = Dp / kKc;
     const int64_t ngroups = (node1 - node0 + npc - 1) / npc;
 
+    const bool ring = nk > kResident;
     if (tid == 0) {
         tc::mbar_init(done, 1);
+        for (int q = 0; q < kRing; ++q) tc::mbar_init(done + 8 * (1 + q), 1);
         tc::mbar_fence_init();
     }
+    int uses[kRing] = {0, 0};  // products committed to each ring buffer's barrier so far
     if (warp == 0) {
         tc::tmem_alloc(tc::smem_addr(tmem_slot), kRows);
         tc::tmem_relinquish();
@@ -200,7 +210,8 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
         __syncthreads();
         // gather the member rows (16-byte pieces) into the swizzled K-major tile;
         // the thresholds and norms below load while these copies are in flight
-        const int q_per_row = Dp / 8;
+        // (wide rows: only the first chunk here, the rest in the ring below)
+        const int q_per_row = ring ? kKc / 8 : Dp / 8;
         // piece e = tid + i * kThreads is (row r, piece q); stepped without a division
         const int r_step = kThreads / q_per_row, q_step = kThreads - r_step * q_per_row;
         for (int r = tid / q_per_row, q = tid - (tid / q_per_row) * q_per_row; r < kRows;) {
@@ -232,24 +243,76 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                 srt[r] = u >= 0 ? __fsqrt_ru(nrm[u]) : 0.f;
             }
         }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
-        // the tensor cores read shared memory through the async proxy
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        tc::fence_after_sync();
-        if (tid == 0) {
-            for (int c = 0; c < nk; ++c) {
-                const uint64_t d0 = tc::sdesc_k128(tc::smem_addr(base + (size_t)c * kChunkBytes));
+        if (!ring) {
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            // the tensor cores read shared memory through the async proxy
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncthreads();
+            tc::fence_after_sync();
+            if (tid == 0) {
+                for (int c = 0; c < nk; ++c) {
+                    const uint64_t d0 = tc::sdesc_k128(tc::smem_addr(base + (size_t)c * kChunkBytes));
 #pragma unroll
-                for (int kk = 0; kk < kKc / 16; ++kk)
-                    tc::mma_f16(tmem, d0 + 2 * kk, d0 + 2 * kk, idesc, (c | kk) != 0);
+                    for (int kk = 0; kk < kKc / 16; ++kk)
+                        tc::mma_f16(tmem, d0 + 2 * kk, d0 + 2 * kk, idesc, (c | kk) != 0);
+                }
+                tc::mma_commit(done);
             }
-            tc::mma_commit(done);
+        } else {
+            // chunk c in ring buffer c % kRing: the copies of chunk c + 1 are
+            // in flight while the tensor cores take chunk c; a buffer is
+            // refilled only after the product that read it has completed
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            for (int c = 0; c < nk && ok; ++c) {
+                if (c + 1 < nk) {
+                    const int q1 = (c + 1) % kRing;
+                    if (uses[q1] > 0 && !tc::mbar_wait(done + 8 * (1 + q1), (uint32_t)((uses[q1] - 1) & 1), status))
+                        ok = false;
+                    // pieces of chunk c + 1: row r = e / 8, piece e % 8, 4 per thread
+                    for (int e = tid; e < kRows * 8; e += kThreads) {
+                        const int r = e >> 3, c16 = e & 7;
+                        uint8_t* dst = base + (size_t)q1 * kChunkBytes + r * 128 + ((c16 ^ (r & 7)) << 4);
+                        const int u = mem[r];
+                        if (u >= 0) {
+                            const uint16_t* src = Xq + (int64_t)u * Dp + (c + 1) * kKc + c16 * 8;
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::smem_addr(dst)),
+                                         "l"(src)
+                                         : "memory");
+                        } else {
+                            *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+                        }
+                    }
+                    asm volatile("cp.async.commit_group;\n" ::: "memory");
+                    asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // chunk c has landed
+                } else {
+                    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+                }
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                ok = __syncthreads_and(ok);
+                tc::fence_after_sync();
+                if (!ok) break;
+                const int q0 = c % kRing;
+                if (tid == 0) {
+                    const uint64_t d0 = tc::sdesc_k128(tc::smem_addr(base + (size_t)q0 * kChunkBytes));
+#pragma unroll
+                    for (int kk = 0; kk < kKc / 16; ++kk)
+                        tc::mma_f16(tmem, d0 + 2 * kk, d0 + 2 * kk, idesc, (c | kk) != 0);
+                    tc::mma_commit(done + 8 * (1 + q0));
+                }
+                ++uses[q0];
+            }
+            if (!ok) {
+                // copies still in flight land before anything is reused; the
+                // products issued so far complete before the CTA frees its
+                // tensor memory (below, after the bounded wait on `done`)
+                asm volatile("cp.async.wait_all;\n" ::: "memory");
+            }
+            if (tid == 0) tc::mma_commit(done);
         }
         __syncwarp();
         // one thread watches the barrier; the others sleep in __syncthreads
         const int mma_ok = tid == 0 ? (tc::mbar_wait(done, (uint32_t)(iter & 1), status) ? 1 : 0) : 1;
-        ok = __syncthreads_and(mma_ok);
+        ok = __syncthreads_and(mma_ok && ok);
         tc::fence_after_sync();
         if (!ok) break;
 
@@ -437,7 +500,7 @@ bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev
                     const int* notexact, bool bf16, cudaStream_t s, bool cert, const float* X) {
     const int Dp = lp_dim(D);
     const int mcap = ((rev ? 2 * k : k) + 7) & ~7;
-    if (Dp / kKc > 4 || mcap > 64) return false;  // a 64-bit mask of offers per tile row
+    if (mcap > 64) return false;  // a 64-bit mask of offers per tile row
     if (cert && (!X || !b.qerr)) return false;
     const int npc = kRows / mcap;
     const JtSmem L = jt_smem(Dp, mcap, cert);

@@ -464,6 +464,40 @@ def test_screening_join_matches_oracle(knng, monkeypatch, k, mode):
     _assert_graph_equal(ids, d, o_ids, o_d)
 
 
+@pytest.mark.parametrize("kind,precision", [("float", "fp16"), ("float", "bf16"), ("integer", "bf16")])
+def test_wide_rows_join_matches_oracle(knng, monkeypatch, kind, precision):
+    # rows wider than four 64-dim chunks stream through the tensor-core join's
+    # chunk ring: exact integers (the exact join) and float data (the
+    # screening join, requested) both equal the FP32 build (and the oracle)
+    monkeypatch.setenv("KNNG_JOIN_SCREEN", "1")
+    n, D, k = 2500, 600, 12
+    rng = np.random.default_rng(D + k)
+    X = (rng.integers(0, 60, size=(n, D)).astype(np.float32) if kind == "integer"
+         else datagen.gaussian_mixture(n, D, 25, seed=11))
+    prec = {"bf16": knng.KNNG_BF16, "fp16": knng.KNNG_FP16}[precision]
+    common = dict(k=k, leaf_max=64, tree_passes=2, refine_rounds=3, seed=5, join_mode=oracle.FWD_REV)
+    knng.stats_reset()
+    knng.stats_enable(True, False)
+    try:
+        ids, d = knng.knng_build_ex(_dev(X), knng.default_params(precision=prec, **common))
+    finally:
+        knng.stats_enable(False)
+    joins = knng.stats()
+    assert joins.get("k5_join_tc" if kind == "integer" else "k5_join_tc_cert", {}).get("launches", 0) > 0
+    assert joins.get("k5_join", {}).get("launches", 0) == 0
+    f_ids, f_d = knng.knng_build_ex(_dev(X), knng.default_params(precision=knng.KNNG_FP32, **common))
+    _assert_graph_equal(ids, d, _np(f_ids), _np(f_d))
+    if kind == "integer":
+        o_ids, o_d = oracle.build_graph(X, k, 64, passes=2, rounds=3, seed=5, mode=oracle.FWD_REV)
+        _assert_graph_equal(ids, d, o_ids, o_d)
+    # the recorded build takes the same joins on the device
+    Xd = _dev(X)
+    with knng.BuildPlan(Xd, knng.default_params(precision=prec, **common)) as plan:
+        pi, pd = plan.launch()
+        plan.check()
+        _assert_graph_equal(pi, pd, _np(f_ids), _np(f_d))
+
+
 # ---------------------------------------------------------------- recorded builds
 @pytest.mark.parametrize("precision,kind,mode", [("bf16", "integer", oracle.FWD_REV), ("fp32", "float", oracle.FWD_REV),
                                                  ("bf16", "float", oracle.FWD), ("fp16", "integer", oracle.FWD)])
