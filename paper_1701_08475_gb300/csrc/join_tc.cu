@@ -39,10 +39,16 @@ constexpr int kRing = 2;       // chunk buffers for wider rows
 
 __device__ __forceinline__ bool lp_exact_flag(int f) { return (f & 1) == 0 && !((f & 2) && (f & 4)); }
 
-// The operand tile, reused after the product for the Gram rows (priv[t][r]:
-// row r's entry for member t of its node; an entry that makes an offer is
-// overwritten with the offer's distance); then member ids, thresholds, norms,
-// errors and rounded-up norm roots, counts, the barrier, the slot.
+// Row stride (floats) of the Gram rows in shared memory: mcap + 4 is 4 mod 8
+// (mcap is a multiple of 8), so the 16-byte accesses of any 8 consecutive
+// rows fall in distinct bank quads.
+__host__ __device__ __forceinline__ int priv_stride(int mcap) { return mcap + 4; }
+
+// The operand tile, reused after the product for the Gram rows (priv[r][t]:
+// row r's entry for member t of its node, row stride priv_stride(mcap); an
+// entry that makes an offer is overwritten with the offer's distance); then
+// member ids, thresholds, norms, errors and rounded-up norm roots, counts, the
+// barrier, the slot.
 struct JtSmem {
     size_t tile, priv, mem, thr, nrm, err, srt, lid, cnt, bar, slot, total;
 };
@@ -53,7 +59,8 @@ __host__ __device__ inline JtSmem jt_smem(int Dp, int mcap, bool cert) {
     // rows of up to kResident chunks stay whole in shared memory; wider rows
     // stream through a ring of kRing chunk buffers
     const int nk = Dp / kKc;
-    const size_t tile = (size_t)(nk <= kResident ? nk : kRing) * kChunkBytes, pv = (size_t)mcap * kRows * 4;
+    const size_t tile = (size_t)(nk <= kResident ? nk : kRing) * kChunkBytes,
+                 pv = (size_t)priv_stride(mcap) * kRows * 4;
     L.mem = tile > pv ? tile : pv;
     L.thr = L.mem + kRows * 4;
     L.nrm = L.thr + kRows * 8;
@@ -142,7 +149,8 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
     if (count_dev && (int64_t)*count_dev < node1) node1 = *count_dev;
     const JtSmem L = jt_smem(Dp, mcap, CERT);
     uint8_t* base = smem_raw + ((1024 - (tc::smem_addr(smem_raw) & 1023)) & 1023);
-    float* priv = reinterpret_cast<float*>(base + L.priv);    // [mcap][128]: thread r's Gram row
+    float* priv = reinterpret_cast<float*>(base + L.priv);    // [128][PS]: row r's Gram entries
+    const int PS = priv_stride(mcap);
     int32_t* mem = reinterpret_cast<int32_t*>(base + L.mem);
     uint64_t* thr = reinterpret_cast<uint64_t*>(base + L.thr);
     float* snrm = reinterpret_cast<float*>(base + L.nrm);
@@ -186,19 +194,24 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
             if (pos < node1) {
                 const int64_t i = list ? (int64_t)list[pos] : pos;
                 const uint64_t fb = fnew ? fnew[i] : ~0ull, rb = rnew ? rnew[i] : ~0ull;
+                // at most 64 entries: G[i] then R[i] (k <= 32), or G[i] in two
+                // halves; both loaded at once, then taken new first, old after
+                const uint64_t* row1 = rev ? R + i * k : Gold + i * k + 32;
+                const int lim1 = rev ? k : k - 32;
+                const uint64_t key0 = lane < k ? Gold[i * k + lane] : kEmptyKey;
+                const uint64_t key1 = lane < lim1 ? row1[lane] : kEmptyKey;
+                const bool new0 = ((fb >> lane) & 1ull) != 0;
+                const bool new1 = (((rev ? rb : fb >> 32) >> lane) & 1ull) != 0;
+                const unsigned below = (1u << lane) - 1u;
                 for (int want = 1; want >= 0; --want) {
-                    for (int src = 0; src < (rev ? 2 : 1); ++src) {
-                        const uint64_t* row = (src == 0 ? Gold : R) + i * k;
-                        const uint64_t bits = src == 0 ? fb : rb;
-                        for (int e0 = 0; e0 < k; e0 += 32) {
-                            const int e = e0 + lane;
-                            const uint64_t key = e < k ? row[e] : kEmptyKey;
-                            const bool take = key != kEmptyKey && (int)((bits >> e) & 1ull) == want;
-                            const unsigned bal = __ballot_sync(0xffffffffu, take);
-                            if (take) mem[j * mcap + M + __popc(bal & ((1u << lane) - 1u))] = (int32_t)key_id(key);
-                            M += __popc(bal);
-                        }
-                    }
+                    const bool t0 = key0 != kEmptyKey && new0 == (want == 1);
+                    const unsigned b0 = __ballot_sync(0xffffffffu, t0);
+                    if (t0) mem[j * mcap + M + __popc(b0 & below)] = (int32_t)key_id(key0);
+                    M += __popc(b0);
+                    const bool t1 = key1 != kEmptyKey && new1 == (want == 1);
+                    const unsigned b1 = __ballot_sync(0xffffffffu, t1);
+                    if (t1) mem[j * mcap + M + __popc(b1 & below)] = (int32_t)key_id(key1);
+                    M += __popc(b1);
                     if (want == 1) nn = M;
                 }
             }
@@ -318,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
 
         // ---- epilogue: row r of the tile is member s of node j.  Threads r
         // and r + 128 (warps w and w + 4 read the same tensor-memory lanes)
-        // share the row: each copies half of its Gram values to priv[t][r].
+        // share the row: each copies half of its Gram values to priv[r][t].
         const int r = tid & (kRows - 1), h = tid >> 7;
         const int j = r / mcap, s = r - j * mcap;
         const int Mj = j < npc ? mcount[j] : 0;
@@ -332,10 +345,14 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
             float g[32];
             tc::tmem_ld_32(tmem + ((uint32_t)wr0 << 16) + (uint32_t)(cc * 32), g);
             if (mine) {
+                // in aligned quads: j * mcap and cc * 32 are multiples of 8, and
+                // a quad that starts below Mj ends below PS
 #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) {
-                    const int t = cc * 32 + jj - j * mcap;
-                    if ((unsigned)t < (unsigned)Mj) priv[t * kRows + r] = g[jj];
+                for (int qd = 0; qd < 8; ++qd) {
+                    const int t = cc * 32 + 4 * qd - j * mcap;
+                    if ((unsigned)t < (unsigned)Mj)
+                        *reinterpret_cast<float4*>(priv + r * PS + t) =
+                            make_float4(g[4 * qd], g[4 * qd + 1], g[4 * qd + 2], g[4 * qd + 3]);
                 }
             }
         }
@@ -362,37 +379,38 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
             const float na = snrm[r];
             const int bend = s < nn ? Mj : nn;
             const int4 la = slid[r];
-            int b0 = h;
+            float* prow = priv + r * PS;
             if (!CERT) {
-                // two members per step: independent chains for the scheduler
-                auto below = [&](int b, uint32_t ub, float d) {
-                    return b != s && ub != ua && (d < ta_d || (d == ta_d && ub < ta_id));
-                };
-                for (; b0 + 2 < bend; b0 += 4) {
-                    const int b1 = b0 + 2;
-                    const uint32_t u0 = (uint32_t)mem[base_row + b0], u1 = (uint32_t)mem[base_row + b1];
-                    const float d0 = __fadd_rn(__fsub_rn(__fadd_rn(na, snrm[base_row + b0]),
-                                                         __fmul_rn(2.f, priv[b0 * kRows + r])), 0.f);
-                    const float d1 = __fadd_rn(__fsub_rn(__fadd_rn(na, snrm[base_row + b1]),
-                                                         __fmul_rn(2.f, priv[b1 * kRows + r])), 0.f);
-                    if (below(b0, u0, d0) && !leaf_mates(la, slid[base_row + b0], npass)) {
-                        hit |= 1ull << b0;
-                        priv[b0 * kRows + r] = d0;
-                    }
-                    if (below(b1, u1, d1) && !leaf_mates(la, slid[base_row + b1], npass)) {
-                        hit |= 1ull << b1;
-                        priv[b1 * kRows + r] = d1;
+                // quads of members, alternately to h = 0 and h = 1: one 16-byte
+                // load each of Gram entries, member ids and norms.  Exact
+                // arithmetic: s - 2g is an integer below 2^24 however it is
+                // rounded, never -0, so its key orders like the distance.
+#pragma unroll 1
+                for (int b4 = 4 * h; b4 < bend; b4 += 8) {
+                    const float4 g4 = *reinterpret_cast<const float4*>(prow + b4);
+                    const int4 u4 = *reinterpret_cast<const int4*>(mem + base_row + b4);
+                    const float4 n4 = *reinterpret_cast<const float4*>(snrm + base_row + b4);
+                    const float gq[4] = {g4.x, g4.y, g4.z, g4.w}, nq[4] = {n4.x, n4.y, n4.z, n4.w};
+                    const uint32_t uq[4] = {(uint32_t)u4.x, (uint32_t)u4.y, (uint32_t)u4.z, (uint32_t)u4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int b = b4 + e;
+                        const float d = __fmaf_rn(-2.f, gq[e], __fadd_rn(na, nq[e]));
+                        if (b < bend && b != s && uq[e] != ua && make_key(d, uq[e]) < ta &&
+                            !leaf_mates(la, slid[base_row + b], npass)) {
+                            hit |= 1ull << b;
+                            prow[b] = d;
+                        }
                     }
                 }
             }
-            for (int b = b0; b < bend; b += 2) {
+            for (int b = h; CERT && b < bend; b += 2) {
                 const uint32_t ub = (uint32_t)mem[base_row + b];
                 if (b == s || ub == ua) continue;
                 // leaf-mates were offered to each other in the leaf stage (with
                 // CERT, no canonical distance is needed for them either)
                 if (CERT && leaf_mates(la, slid[base_row + b], npass)) continue;
-                float d = __fadd_rn(__fsub_rn(__fadd_rn(na, snrm[base_row + b]), __fmul_rn(2.f, priv[b * kRows + r])),
-                                    0.f);
+                float d = __fadd_rn(__fsub_rn(__fadd_rn(na, snrm[base_row + b]), __fmul_rn(2.f, prow[b])), 0.f);
                 if (CERT) {
                     const float cD = (16.f * Dp + 8.f) * 5.9604644775390625e-8f;  // 2^-24
                     const float sn = __fadd_ru(srt[r], srt[base_row + b]);
@@ -407,9 +425,9 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                     if (lb > ta_d) continue;
                     d = canon_dist(X + (int64_t)ua * D, X + (int64_t)ub * D, D, vec);
                 }
-                if ((d < ta_d || (d == ta_d && ub < ta_id)) && (CERT || !leaf_mates(la, slid[base_row + b], npass))) {
+                if (d < ta_d || (d == ta_d && ub < ta_id)) {
                     hit |= 1ull << b;
-                    priv[b * kRows + r] = d;
+                    prow[b] = d;
                 }
             }
         } else if (!by_rows) {
@@ -420,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                 if (pa == pb) continue;
                 if (CERT && leaf_mates(slid[base_row + a], slid[base_row + b], npass)) continue;
                 float d = __fadd_rn(__fsub_rn(__fadd_rn(snrm[base_row + a], snrm[base_row + b]),
-                                              __fmul_rn(2.f, priv[a * kRows + base_row + b])), 0.f);
+                                              __fmul_rn(2.f, priv[(base_row + b) * PS + a])), 0.f);
                 const uint64_t ta = thr[base_row + a], tb = thr[base_row + b];
                 if (CERT) {
                     const float cD = (16.f * Dp + 8.f) * 5.9604644775390625e-8f;  // 2^-24
@@ -439,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                 }
                 bool oa = make_key(d, pb) < ta, ob = make_key(d, pa) < tb;
                 if ((oa || ob) && leaf_mates(slid[base_row + a], slid[base_row + b], npass)) oa = ob = false;
-                if (oa || ob) priv[a * kRows + base_row + b] = d;
+                if (oa || ob) priv[(base_row + b) * PS + a] = d;
                 hit |= ((uint64_t)oa << (2 * i)) | ((uint64_t)ob << (2 * i + 1));
             }
         }
@@ -466,7 +484,7 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                 const int b = __ffsll((long long)hit) - 1;
                 hit &= hit - 1;
                 ptgt[w] = ua;
-                pkey[w] = make_key(priv[b * kRows + r], (uint32_t)mem[base_row + b]);
+                pkey[w] = make_key(priv[r * PS + b], (uint32_t)mem[base_row + b]);
                 ++w;
             }
         } else {
@@ -476,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                 int a, b;
                 pm.decode(tix + (bit >> 1) * T, a, b);
                 const uint32_t pa = (uint32_t)mem[base_row + a], pb = (uint32_t)mem[base_row + b];
-                const float d = priv[a * kRows + base_row + b];
+                const float d = priv[(base_row + b) * PS + a];
                 const uint32_t tgt = (bit & 1) ? pb : pa;
                 ptgt[w] = tgt;
                 pkey[w] = make_key(d, (bit & 1) ? pa : pb);
