@@ -62,13 +62,13 @@ __host__ __device__ inline JtSmem jt_smem(int Dp, int mcap, bool cert) {
     const size_t tile = (size_t)(nk <= kResident ? nk : kRing) * kChunkBytes,
                  pv = (size_t)priv_stride(mcap) * kRows * 4;
     L.mem = tile > pv ? tile : pv;
-    L.thr = L.mem + kRows * 4;
+    L.thr = L.mem + 2 * kRows * 4;  // two member buffers: this group's and the next one's
     L.nrm = L.thr + kRows * 8;
     L.err = L.nrm + kRows * 4;
     L.srt = L.err + (cert ? kRows * 4 : 0);
     L.lid = L.srt + (cert ? kRows * 4 : 0);
     L.cnt = L.lid + kRows * 16;
-    L.bar = L.cnt + 32 * 4;  // member counts, then new-member counts
+    L.bar = L.cnt + 2 * 32 * 4;  // member counts, then new-member counts (two buffers)
     L.slot = L.bar + 8 * (1 + kRing);  // the product's barrier, then one per ring buffer
     L.total = L.slot + 8;
     return L;
@@ -151,12 +151,12 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
     uint8_t* base = smem_raw + ((1024 - (tc::smem_addr(smem_raw) & 1023)) & 1023);
     float* priv = reinterpret_cast<float*>(base + L.priv);    // [128][PS]: row r's Gram entries
     const int PS = priv_stride(mcap);
-    int32_t* mem = reinterpret_cast<int32_t*>(base + L.mem);
+    int32_t* mem_buf = reinterpret_cast<int32_t*>(base + L.mem);  // [2][kRows]
     uint64_t* thr = reinterpret_cast<uint64_t*>(base + L.thr);
     float* snrm = reinterpret_cast<float*>(base + L.nrm);
     float* serr = reinterpret_cast<float*>(base + L.err);  // CERT: quantisation errors
     float* srt = reinterpret_cast<float*>(base + L.srt);   // CERT: norm roots, rounded up
-    int* mcount = reinterpret_cast<int*>(base + L.cnt);
+    int* cnt_buf = reinterpret_cast<int*>(base + L.cnt);  // [2][32]
     int4* slid = reinterpret_cast<int4*>(base + L.lid);  // [kRows] the members' leaves (npass slots)
     const bool vec = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.slot);
@@ -182,12 +182,12 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
     const uint32_t idesc = tc::idesc_f16(bf16, kRows, kRows);
     int iter = 0;
     bool ok = true;
-    for (int64_t grp = blockIdx.x; grp < ngroups && ok; grp += gridDim.x, ++iter) {
-        const int64_t first = node0 + grp * npc;
-        for (int r = tid; r < kRows; r += kThreads) mem[r] = -1;
-        __syncthreads();
-        // members of the group's nodes (warp j collects node j): the new ones
-        // first, then the old ones (flags from the previous round; none = all new)
+    const float rmcap = 1.f / (float)mcap;
+    // Members of the nodes of the group that starts at position `first`, into
+    // mb (member ids; a node's unused slots -1) and cb (member counts, then
+    // new-member counts): warp j collects node j, the new members first, then
+    // the old ones (flags from the previous round; none = all new).
+    auto collect = [&](int64_t first, int32_t* mb, int* cb) {
         for (int j = warp; j < npc; j += kThreads / 32) {
             const int64_t pos = first + j;
             int M = 0, nn = 0;
@@ -206,31 +206,38 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                 for (int want = 1; want >= 0; --want) {
                     const bool t0 = key0 != kEmptyKey && new0 == (want == 1);
                     const unsigned b0 = __ballot_sync(0xffffffffu, t0);
-                    if (t0) mem[j * mcap + M + __popc(b0 & below)] = (int32_t)key_id(key0);
+                    if (t0) mb[j * mcap + M + __popc(b0 & below)] = (int32_t)key_id(key0);
                     M += __popc(b0);
                     const bool t1 = key1 != kEmptyKey && new1 == (want == 1);
                     const unsigned b1 = __ballot_sync(0xffffffffu, t1);
-                    if (t1) mem[j * mcap + M + __popc(b1 & below)] = (int32_t)key_id(key1);
+                    if (t1) mb[j * mcap + M + __popc(b1 & below)] = (int32_t)key_id(key1);
                     M += __popc(b1);
                     if (want == 1) nn = M;
                 }
             }
+            for (int t = M + lane; t < mcap; t += 32) mb[j * mcap + t] = -1;
             if (lane == 0) {
-                mcount[j] = M;
-                mcount[16 + j] = nn;
+                cb[j] = M;
+                cb[16 + j] = nn;
             }
         }
-        __syncthreads();
+    };
+    // slots past the last node's never hold a member
+    for (int r = tid; r < 2 * kRows; r += kThreads) mem_buf[r] = -1;
+    __syncthreads();
+    if ((int64_t)blockIdx.x < ngroups) collect(node0 + (int64_t)blockIdx.x * npc, mem_buf, cnt_buf);
+    __syncthreads();
+    for (int64_t grp = blockIdx.x; grp < ngroups && ok; grp += gridDim.x, ++iter) {
+        // this group's members (collected before the previous group's offers)
+        int32_t* mem = mem_buf + (iter & 1) * kRows;
+        const int* mcount = cnt_buf + (iter & 1) * 32;
         // gather the member rows (16-byte pieces) into the swizzled K-major tile;
         // the thresholds and norms below load while these copies are in flight
         // (wide rows: only the first chunk here, the rest in the ring below)
         const int q_per_row = ring ? kKc / 8 : Dp / 8;
-        // piece e = tid + i * kThreads is (row r, piece q); stepped without a division
-        const int r_step = kThreads / q_per_row, q_step = kThreads - r_step * q_per_row;
-        for (int r = tid / q_per_row, q = tid - (tid / q_per_row) * q_per_row; r < kRows;) {
-            const int kc = q >> 3, c16 = q & 7;
-            uint8_t* dst = base + (size_t)kc * kChunkBytes + r * 128 + ((c16 ^ (r & 7)) << 4);
-            const int u = mem[r];
+        // piece (r, q) goes to chunk q / 8, row r, 16-byte slot (q % 8) ^ (r % 8)
+        auto piece = [&](int r, int q, int u) {
+            uint8_t* dst = base + (size_t)(q >> 3) * kChunkBytes + r * 128 + (((q & 7) ^ (r & 7)) << 4);
             if (u >= 0) {
                 const uint16_t* src = Xq + (int64_t)u * Dp + q * 8;
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::smem_addr(dst)), "l"(src)
@@ -238,26 +245,54 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
             } else {
                 *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
             }
-            r += r_step;
-            q += q_step;
-            if (q >= q_per_row) {
-                q -= q_per_row;
-                ++r;
+        };
+        if ((kThreads % q_per_row) == 0) {
+            // a power of two: each thread copies piece q of rows r0, r0 + rs, ...
+            const int sh = __ffs(q_per_row) - 1;
+            const int q = tid & (q_per_row - 1), rs = kThreads >> sh;
+#pragma unroll 4
+            for (int r = tid >> sh; r < kRows; r += rs) piece(r, q, mem[r]);
+        } else {
+            // piece e = tid + i * kThreads is (row r, piece q); stepped without a division
+            const int r_step = kThreads / q_per_row, q_step = kThreads - r_step * q_per_row;
+            for (int r = tid / q_per_row, q = tid - (tid / q_per_row) * q_per_row; r < kRows;) {
+                piece(r, q, mem[r]);
+                r += r_step;
+                q += q_step;
+                if (q >= q_per_row) {
+                    q -= q_per_row;
+                    ++r;
+                }
             }
         }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        // the members' thresholds, norms and leaves: copies of their own,
+        // awaited only before the epilogue
         for (int r = tid; r < kRows; r += kThreads) {
             const int u = mem[r];
-            thr[r] = u >= 0 ? Gold[(int64_t)u * k + k - 1] : 0ull;
-            snrm[r] = u >= 0 ? nrm[u] : 0.f;
-            if (npass > 0)
-                slid[r] = u >= 0 ? __ldg(reinterpret_cast<const int4*>(leafid) + u) : make_int4(-1 - r, -1 - r, -1 - r, -1 - r);
+            if (u >= 0) {
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(tc::smem_addr(thr + r)),
+                             "l"(Gold + (int64_t)u * k + k - 1)
+                             : "memory");
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(tc::smem_addr(snrm + r)), "l"(nrm + u)
+                             : "memory");
+                if (npass > 0)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::smem_addr(slid + r)),
+                                 "l"(reinterpret_cast<const int4*>(leafid) + u)
+                                 : "memory");
+            } else {
+                thr[r] = 0ull;
+                snrm[r] = 0.f;
+                if (npass > 0) slid[r] = make_int4(-1 - r, -1 - r, -1 - r, -1 - r);
+            }
             if (CERT) {
                 serr[r] = u >= 0 ? qerr[u] : 0.f;
                 srt[r] = u >= 0 ? __fsqrt_ru(nrm[u]) : 0.f;
             }
         }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
         if (!ring) {
-            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // the tile (the side copies may fly on)
             // the tensor cores read shared memory through the async proxy
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncthreads();
@@ -274,8 +309,8 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
         } else {
             // chunk c in ring buffer c % kRing: the copies of chunk c + 1 are
             // in flight while the tensor cores take chunk c; a buffer is
-            // refilled only after the product that read it has completed
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            // refilled only after the product that read it has completed (the
+            // first wait also covers the side copies, committed after chunk 0)
             for (int c = 0; c < nk && ok; ++c) {
                 if (c + 1 < nk) {
                     const int q1 = (c + 1) % kRing;
@@ -325,6 +360,7 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
         __syncwarp();
         // one thread watches the barrier; the others sleep in __syncthreads
         const int mma_ok = tid == 0 ? (tc::mbar_wait(done, (uint32_t)(iter & 1), status) ? 1 : 0) : 1;
+        asm volatile("cp.async.wait_all;\n" ::: "memory");  // the side copies
         ok = __syncthreads_and(mma_ok && ok);
         tc::fence_after_sync();
         if (!ok) break;
@@ -333,13 +369,14 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
         // and r + 128 (warps w and w + 4 read the same tensor-memory lanes)
         // share the row: each copies half of its Gram values to priv[r][t].
         const int r = tid & (kRows - 1), h = tid >> 7;
-        const int j = r / mcap, s = r - j * mcap;
+        const int j = small_div(r, mcap, rmcap), s = r - j * mcap;
         const int Mj = j < npc ? mcount[j] : 0;
         const bool mine = s < Mj;
         // the 32-column chunks that hold the windows of this warp's rows (its
         // first and last row's nodes), alternately to h = 0 and h = 1
         const int wr0 = (warp & 3) * 32;
-        const int cmin = (wr0 / mcap) * mcap, cmax = min(((wr0 + 31) / mcap + 1) * mcap, kRows);
+        const int cmin = small_div(wr0, mcap, rmcap) * mcap,
+                  cmax = min((small_div(wr0 + 31, mcap, rmcap) + 1) * mcap, kRows);
 #pragma unroll 1
         for (int cc = (cmin >> 5) + h; cc * 32 < cmax; cc += 2) {
             float g[32];
@@ -396,7 +433,8 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                     for (int e = 0; e < 4; ++e) {
                         const int b = b4 + e;
                         const float d = __fmaf_rn(-2.f, gq[e], __fadd_rn(na, nq[e]));
-                        if (b < bend && b != s && uq[e] != ua && make_key(d, uq[e]) < ta &&
+                        // member s itself has id ua: the id test skips it
+                        if (b < bend && uq[e] != ua && make_key(d, uq[e]) < ta &&
                             !leaf_mates(la, slid[base_row + b], npass)) {
                             hit |= 1ull << b;
                             prow[b] = d;
@@ -472,6 +510,11 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
         const int total = __shfl_sync(0xffffffffu, x, 31);
         uint32_t at = 0;
         if (lane == 31 && total > 0) at = atomicAdd(counter, (uint32_t)total);
+        // the next group's members are collected (into the other buffers)
+        // while the slot range is on its way
+        const int64_t nxt = grp + gridDim.x;
+        if (nxt < ngroups)
+            collect(node0 + nxt * npc, mem_buf + ((iter + 1) & 1) * kRows, cnt_buf + ((iter + 1) & 1) * 32);
         at = __shfl_sync(0xffffffffu, at, 31);
         if (total > 0 && (int64_t)at + total > cap) {
             if (lane == 0) atomicOr(status, kStatusOverflow);
