@@ -204,8 +204,12 @@ __global__ void __launch_bounds__(256) k6_select(const uint64_t* __restrict__ rb
     const int beg = roff[i], deg = roff[i + 1] - beg;
     if (deg <= 32) {
         // the usual case: every candidate fits a lane; the keys are distinct
-        // (one per source list), so the sorted run's first k are the list
-        const uint64_t v = warp_sort32(lane < deg ? rbuf[beg + lane] : kEmptyKey);
+        // (one per source list), so the sorted run's first k are the list.
+        // With k <= 32 the list's order is not used (the flags look ids up
+        // in a hash set and the join takes members in any order): up to k
+        // candidates are the list as they come.
+        uint64_t v = lane < deg ? rbuf[beg + lane] : kEmptyKey;
+        if (NO > 1 || deg > k) v = warp_sort32(v);
 #pragma unroll
         for (int o = 0; o < NO; ++o) {
             const int e = lane + 32 * o;
@@ -261,26 +265,63 @@ __global__ void __launch_bounds__(32 * kFlagWarps) k6_flags(const uint64_t* __re
     const int64_t i = (int64_t)blockIdx.x * kFlagWarps + w;
     int on = 0;
     if (i < n) {
-        uint64_t* pg = prev[w][0];
-        uint64_t* pr = prev[w][1];
-#pragma unroll
-        for (int o = 0; o < NO; ++o) {
-            const int e = lane + 32 * o;
-            pg[e] = e < k ? Gprev[i * k + e] : kEmptyKey;
-            pr[e] = (Rprev && e < k) ? Rprev[i * k + e] : kEmptyKey;
-        }
-        __syncwarp();
         uint64_t fb = 0, rb = 0;
+        if (NO == 1) {
+            // k <= 32: by id (a pair always has the same canonical distance,
+            // the same both ways), in a hash set of the previous members'
+            // ids (at most 64 in 128 slots, linear probing); no list needs
+            // to be sorted
+            uint32_t* tab = reinterpret_cast<uint32_t*>(prev[w]);
+            constexpr uint32_t kFree = 0xFFFFFFFFu;
+            const uint64_t gk = lane < k ? Gcur[i * k + lane] : kEmptyKey;
+            const uint64_t rk = (Rcur && lane < k) ? Rcur[i * k + lane] : kEmptyKey;
+            const uint64_t pgk = lane < k ? Gprev[i * k + lane] : kEmptyKey;
+            const uint64_t prk = (Rprev && lane < k) ? Rprev[i * k + lane] : kEmptyKey;
+            for (int t = lane; t < 128; t += 32) tab[t] = kFree;
+            __syncwarp();
+            auto home = [](uint32_t id) { return (id * 2654435761u) >> 25; };
+            for (int src = 0; src < 2; ++src) {
+                const uint64_t key = src == 0 ? pgk : prk;
+                if (key == kEmptyKey) continue;
+                const uint32_t id = key_id(key);
+                for (uint32_t h = home(id), t = 0; t < 128; ++t, h = (h + 1) & 127) {
+                    const uint32_t old = atomicCAS(&tab[h], kFree, id);
+                    if (old == kFree || old == id) break;
+                }
+            }
+            __syncwarp();
+            auto seen = [&](uint64_t key) {
+                const uint32_t id = key_id(key);
+                for (uint32_t h = home(id), t = 0; t < 128; ++t, h = (h + 1) & 127) {
+                    const uint32_t v = tab[h];
+                    if (v == id) return true;
+                    if (v == kFree) return false;
+                }
+                return false;
+            };
+            fb = __ballot_sync(0xffffffffu, gk != kEmptyKey && !seen(gk));
+            if (Rcur) rb = __ballot_sync(0xffffffffu, rk != kEmptyKey && !seen(rk));
+        } else {
+            uint64_t* pg = prev[w][0];
+            uint64_t* pr = prev[w][1];
 #pragma unroll
-        for (int o = 0; o < NO; ++o) {
-            const int e = lane + 32 * o;
-            uint64_t key = e < k ? Gcur[i * k + e] : kEmptyKey;
-            bool nw = key != kEmptyKey && !sorted_has(pg, k, key) && !(Rprev && sorted_has(pr, k, key));
-            fb |= (uint64_t)__ballot_sync(0xffffffffu, nw) << (32 * o);
-            if (Rcur) {
-                key = e < k ? Rcur[i * k + e] : kEmptyKey;
-                nw = key != kEmptyKey && !sorted_has(pg, k, key) && !(Rprev && sorted_has(pr, k, key));
-                rb |= (uint64_t)__ballot_sync(0xffffffffu, nw) << (32 * o);
+            for (int o = 0; o < NO; ++o) {
+                const int e = lane + 32 * o;
+                pg[e] = e < k ? Gprev[i * k + e] : kEmptyKey;
+                pr[e] = (Rprev && e < k) ? Rprev[i * k + e] : kEmptyKey;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int o = 0; o < NO; ++o) {
+                const int e = lane + 32 * o;
+                uint64_t key = e < k ? Gcur[i * k + e] : kEmptyKey;
+                bool nw = key != kEmptyKey && !sorted_has(pg, k, key) && !(Rprev && sorted_has(pr, k, key));
+                fb |= (uint64_t)__ballot_sync(0xffffffffu, nw) << (32 * o);
+                if (Rcur) {
+                    key = e < k ? Rcur[i * k + e] : kEmptyKey;
+                    nw = key != kEmptyKey && !sorted_has(pg, k, key) && !(Rprev && sorted_has(pr, k, key));
+                    rb |= (uint64_t)__ballot_sync(0xffffffffu, nw) << (32 * o);
+                }
             }
         }
         if (lane == 0) {
