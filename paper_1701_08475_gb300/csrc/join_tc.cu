@@ -421,37 +421,27 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
             const int4 la = slid[r];
             float* prow = priv + r * PS;
             if (!CERT) {
-                // Pass 1, without branches: member b is a candidate when its
-                // distance is at most row s's k-th (quads alternately to h = 0
-                // and h = 1, one 16-byte load each of Gram entries and norms).
-                // Exact arithmetic: s - 2g is an integer below 2^24 however it
-                // is rounded, never -0, so its key orders like the distance.
-                uint64_t cand = 0;
+                // quads of members, alternately to h = 0 and h = 1: one 16-byte
+                // load each of Gram entries, member ids and norms.  Exact
+                // arithmetic: s - 2g is an integer below 2^24 however it is
+                // rounded, never -0, so its key orders like the distance.
+#pragma unroll 1
+                for (int b4 = 4 * h; b4 < bend; b4 += 8) {
+                    const float4 g4 = *reinterpret_cast<const float4*>(prow + b4);
+                    const int4 u4 = *reinterpret_cast<const int4*>(mem + base_row + b4);
+                    const float4 n4 = *reinterpret_cast<const float4*>(snrm + base_row + b4);
+                    const float gq[4] = {g4.x, g4.y, g4.z, g4.w}, nq[4] = {n4.x, n4.y, n4.z, n4.w};
+                    const uint32_t uq[4] = {(uint32_t)u4.x, (uint32_t)u4.y, (uint32_t)u4.z, (uint32_t)u4.w};
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int b4 = 4 * h + 8 * i;
-                    if (b4 < bend) {
-                        const float4 g4 = *reinterpret_cast<const float4*>(prow + b4);
-                        const float4 n4 = *reinterpret_cast<const float4*>(snrm + base_row + b4);
-                        const uint32_t nib = (uint32_t)(__fmaf_rn(-2.f, g4.x, __fadd_rn(na, n4.x)) <= ta_d) |
-                                             (uint32_t)(__fmaf_rn(-2.f, g4.y, __fadd_rn(na, n4.y)) <= ta_d) << 1 |
-                                             (uint32_t)(__fmaf_rn(-2.f, g4.z, __fadd_rn(na, n4.z)) <= ta_d) << 2 |
-                                             (uint32_t)(__fmaf_rn(-2.f, g4.w, __fadd_rn(na, n4.w)) <= ta_d) << 3;
-                        cand |= (uint64_t)nib << (8 * i);
-                    }
-                }
-                // members below bend only, never s itself
-                cand = (cand << (4 * h)) & (bend >= 64 ? ~0ull : (1ull << bend) - 1ull) & ~(1ull << s);
-                // pass 2: the candidates' keys (ties by id), duplicates of s's
-                // id and leaf-mates
-                while (cand != 0) {
-                    const int b = __ffsll((long long)cand) - 1;
-                    cand &= cand - 1;
-                    const uint32_t ub = (uint32_t)mem[base_row + b];
-                    const float d = __fmaf_rn(-2.f, prow[b], __fadd_rn(na, snrm[base_row + b]));
-                    if (ub != ua && make_key(d, ub) < ta && !leaf_mates(la, slid[base_row + b], npass)) {
-                        hit |= 1ull << b;
-                        prow[b] = d;
+                    for (int e = 0; e < 4; ++e) {
+                        const int b = b4 + e;
+                        const float d = __fmaf_rn(-2.f, gq[e], __fadd_rn(na, nq[e]));
+                        // member s itself has id ua: the id test skips it
+                        if (b < bend && uq[e] != ua && make_key(d, uq[e]) < ta &&
+                            !leaf_mates(la, slid[base_row + b], npass)) {
+                            hit |= 1ull << b;
+                            prow[b] = d;
+                        }
                     }
                 }
             }
