@@ -144,8 +144,11 @@ def profiled_traffic(kernel, workload):
     kernel, or None when there is none or the kernel source changed since."""
     import glob
     path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
-    if not os.path.exists(path):   # a capture of a smaller case of the same recipe
-        cands = sorted(glob.glob(os.path.join(ROOT, "profiles", "%s_*.md" % kernel)))
+    if not os.path.exists(path):
+        # a capture of a smaller case of the same recipe: the kernel's exact
+        # name, then the recipe's name (the workload's up to its size)
+        recipe = workload.split("-")[0]
+        cands = sorted(glob.glob(os.path.join(ROOT, "profiles", "%s_%s-*.md" % (kernel, recipe))))
         if not cands:
             return None
         path = cands[0]
