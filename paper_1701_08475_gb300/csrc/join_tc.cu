@@ -15,11 +15,16 @@
 // the 128 x 128 x Dp Gram on the tensor cores, and in the epilogue each
 // node's 2 mcap threads evaluate its pairs.  A node with many pairs goes by
 // rows: the two threads of tile row r (= tensor-memory lane r, member s of
-// node j) decide the offers to that member, from every other member (half
-// each; an old member takes the new ones only), with the member's k-th entry
-// in a register and one count per target.  A node with few pairs (few new
-// members) deals its pairs {u, v} round-robin to its threads instead, each
-// pair decided in both directions.
+// node j) decide the offers to that member, from every other member (quads of
+// members alternately; an old member takes the new ones only), with the
+// member's k-th entry in a register and one count per target.  A node with
+// few pairs (few new members) deals its pairs {u, v} round-robin to its
+// threads instead, each pair decided in both directions.
+//
+// Inside a CTA the groups overlap where they can: the members' thresholds,
+// norms and leaf ids travel on cp.async beside the gather and are awaited only
+// before the epilogue, and the member lists are double-buffered so that the
+// next group's collection runs while this group's offer slots are fetched.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
