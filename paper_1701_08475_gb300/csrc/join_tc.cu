@@ -441,12 +441,12 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                     for (int e = 0; e < 4; ++e) {
                         const int b = b4 + e;
                         const float d = __fmaf_rn(-2.f, gq[e], __fadd_rn(na, nq[e]));
+                        const int4 lb = slid[base_row + b];
                         // member s itself has id ua: the id test skips it
-                        if (b < bend && uq[e] != ua && make_key(d, uq[e]) < ta &&
-                            !leaf_mates(la, slid[base_row + b], npass)) {
-                            hit |= 1ull << b;
-                            prow[b] = d;
-                        }
+                        const bool off = (b < bend) & (uq[e] != ua) & (make_key(d, uq[e]) < ta) &
+                                         !leaf_mates(la, lb, npass);
+                        hit |= (uint64_t)off << b;
+                        if (off) prow[b] = d;
                     }
                 }
             }
@@ -481,8 +481,7 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                 int a, b;
                 pm.decode(p, a, b);
                 const uint32_t pa = (uint32_t)mem[base_row + a], pb = (uint32_t)mem[base_row + b];
-                if (pa == pb) continue;
-                if (CERT && leaf_mates(slid[base_row + a], slid[base_row + b], npass)) continue;
+                if (CERT && (pa == pb || leaf_mates(slid[base_row + a], slid[base_row + b], npass))) continue;
                 float d = __fadd_rn(__fsub_rn(__fadd_rn(snrm[base_row + a], snrm[base_row + b]),
                                               __fmul_rn(2.f, priv[(base_row + b) * PS + a])), 0.f);
                 const uint64_t ta = thr[base_row + a], tb = thr[base_row + b];
@@ -501,9 +500,10 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                     if (!na && !nb) continue;
                     d = canon_dist(X + (int64_t)pa * D, X + (int64_t)pb * D, D, vec);
                 }
-                bool oa = make_key(d, pb) < ta, ob = make_key(d, pa) < tb;
-                if ((oa || ob) && leaf_mates(slid[base_row + a], slid[base_row + b], npass)) oa = ob = false;
-                if (oa || ob) priv[(base_row + b) * PS + a] = d;
+                // without branches: duplicates of one id and leaf-mates make no offer
+                const bool keep = (pa != pb) & !leaf_mates(slid[base_row + a], slid[base_row + b], npass);
+                const bool oa = keep & (make_key(d, pb) < ta), ob = keep & (make_key(d, pa) < tb);
+                if (oa | ob) priv[(base_row + b) * PS + a] = d;
                 hit |= ((uint64_t)oa << (2 * i)) | ((uint64_t)ob << (2 * i + 1));
             }
         }
