@@ -247,7 +247,10 @@ def test_refine_rounds_skipping_old_pairs_match_oracle(knng, mode, k, start):
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 @pytest.mark.parametrize("k,mode,kind", [(20, oracle.FWD_REV, "integer"), (12, oracle.FWD, "integer"),
                                          (48, oracle.FWD, "integer"), (16, oracle.FWD_REV, "float"),
-                                         (24, oracle.FWD, "float")])
+                                         (24, oracle.FWD, "float"),
+                                         # 16 nodes of 8 member slots per tile (a warp collects two)
+                                         (4, oracle.FWD_REV, "integer"), (8, oracle.FWD, "integer"),
+                                         (5, oracle.FWD_REV, "integer")])
 def test_low_precision_rounds_match_oracle(knng, precision, k, mode, kind):
     # the tensor-core join over four rounds (member flags from the second on):
     # exact on integer data; screening plus canonical distances on float data
@@ -259,6 +262,18 @@ def test_low_precision_rounds_match_oracle(knng, precision, k, mode, kind):
     lp_ids, lp_d = knng.knng_build_ex(_dev(X), knng.default_params(precision=prec, **common))
     o_ids, o_d = oracle.build_graph(X, k, 128, passes=1, rounds=4, seed=3, mode=mode)
     _assert_graph_equal(lp_ids, lp_d, o_ids, o_d)
+
+
+@pytest.mark.parametrize("k", [4, 20])
+def test_exact_join_three_passes_matches_oracle(knng, k):
+    # the tensor-core join with three passes' leaf ids (leaf-mate offers
+    # dropped), 3 and 16 nodes per tile, four rounds
+    n = 6000
+    X = datagen.sift_like(n, D=64, n_centres=50, seed=20 + k)
+    common = dict(k=k, leaf_max=64, tree_passes=3, refine_rounds=4, seed=5, join_mode=oracle.FWD_REV)
+    ids, d = knng.knng_build_ex(_dev(X), knng.default_params(precision=knng.KNNG_BF16, **common))
+    o_ids, o_d = oracle.build_graph(X, k, 64, passes=3, rounds=4, seed=5, mode=oracle.FWD_REV)
+    _assert_graph_equal(ids, d, o_ids, o_d)
 
 
 def test_refine_small_offer_budget_retries_chunks(knng, monkeypatch):
