@@ -884,12 +884,32 @@ __device__ __forceinline__ bool offer_useful(uint64_t key, const uint64_t* row, 
     return row[lo] != key;
 }
 
+// Inserts id into a warp's open-addressing set of kSeenSlots ids (linear
+// probing); true when it was not there.  The callers insert fewer ids than
+// there are slots, so a probe always ends.
+constexpr int kSeenSlots = 256;
+constexpr int kSeenOffers = 160;  // offers per node taken through the set (with at most 32 list ids)
+__device__ __forceinline__ bool seen_insert(uint32_t* tab, uint32_t id) {
+    for (uint32_t h = (id * 2654435761u) >> 24, t = 0; t < kSeenSlots; ++t, h = (h + 1) & (kSeenSlots - 1)) {
+        const uint32_t old = atomicCAS(&tab[h], 0xFFFFFFFFu, id);
+        if (old == 0xFFFFFFFFu) return true;
+        if (old == id) return false;
+    }
+    return false;
+}
+
 // Merges one node's offers into its list: the list sits in shared memory;
 // every lane drops the offers that cannot change it, and only the rest go
-// through the warp selection.
+// through the warp selection.  For k <= 32 and at most kSeenOffers offers the
+// drop is by id in the warp's set `seen` (a pair always has the same canonical
+// distance): the list's ids first, then each offer below the k-th key enters
+// once, so the survivors are distinct and new and usually one bitonic merge
+// takes them; a repeat of an offer that did not make the list cannot make it
+// later either (the k-th key only falls).
 template <int NO>
 __device__ __forceinline__ void merge_node(uint64_t* __restrict__ Gnew, const uint64_t* __restrict__ grouped,
-                                           int64_t u, int beg, int end, int k, uint64_t* srow, uint64_t* scratch) {
+                                           int64_t u, int beg, int end, int k, uint64_t* srow, uint64_t* scratch,
+                                           uint32_t* seen) {
     const int lane = threadIdx.x & 31;
     uint64_t* row = Gnew + u * k;
     uint64_t run[NO];
@@ -901,14 +921,24 @@ __device__ __forceinline__ void merge_node(uint64_t* __restrict__ Gnew, const ui
     __syncwarp();
     constexpr int NC = 4;
     bool changed = false;
+    const bool hashed = NO == 1 && end - beg <= kSeenOffers;
+    if (hashed) {
+        for (int t = lane; t < kSeenSlots; t += 32) seen[t] = 0xFFFFFFFFu;
+        __syncwarp();
+        if (run[0] != kEmptyKey) seen_insert(seen, key_id(run[0]));
+        __syncwarp();
+    }
     for (int c = beg; c < end; c += 32 * NC) {
         uint64_t a[NC + NO];
         bool any = false;
+        const uint64_t kth = hashed ? shfl64(run[0], k - 1) : kEmptyKey;
 #pragma unroll
         for (int s = 0; s < NC; ++s) {
             const int e = c + lane + 32 * s;
             a[s] = (e < end) ? grouped[e] : kEmptyKey;
-            if (a[s] != kEmptyKey && !offer_useful(a[s], srow, k)) a[s] = kEmptyKey;
+            if (a[s] != kEmptyKey &&
+                !(hashed ? (a[s] < kth && seen_insert(seen, key_id(a[s]))) : offer_useful(a[s], srow, k)))
+                a[s] = kEmptyKey;
             any |= a[s] != kEmptyKey;
         }
         if (!__any_sync(0xffffffffu, any)) continue;
@@ -954,6 +984,7 @@ __global__ void __launch_bounds__(256) k4_merge(uint64_t* __restrict__ Gnew, con
                                                 const int* __restrict__ status) {
     __shared__ uint64_t rows[8][32 * NO];
     __shared__ uint64_t scratch[8][32];
+    __shared__ uint32_t seen[8][NO == 1 ? kSeenSlots : 1];
     if (*status & kStatusStop) return;
     const int lane = threadIdx.x & 31;
     uint64_t* srow = rows[threadIdx.x >> 5];
@@ -966,7 +997,8 @@ __global__ void __launch_bounds__(256) k4_merge(uint64_t* __restrict__ Gnew, con
             const int src = __ffs(todo) - 1;
             todo &= todo - 1;
             merge_node<NO>(Gnew, grouped, g0 + src, __shfl_sync(0xffffffffu, beg, src),
-                           __shfl_sync(0xffffffffu, end, src), k, srow, scratch[threadIdx.x >> 5]);
+                           __shfl_sync(0xffffffffu, end, src), k, srow, scratch[threadIdx.x >> 5],
+                           seen[threadIdx.x >> 5]);
         }
     }
 }
