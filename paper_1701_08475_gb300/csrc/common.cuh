@@ -67,6 +67,39 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
     const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(v >> 32), src);
     return ((uint64_t)hi << 32) | lo;
 }
+// The candidate members of node i for one warp (all 32 lanes call it):
+// lane e holds entry e of G_old[i] (key0, new0) and entry e of R[i] (with
+// reverse lists, k <= 32) or entry 32 + e of G_old[i] (without, k <= 64) in
+// key1, new1; fb / rb hold the entries' new flags.  A reverse entry that is a
+// forward one too (a mutual neighbour: the same pair, so the same key) is
+// one member: it is dropped from key1, and the forward copy is new if either
+// copy is (its pairs then cover what the two copies gave).  G_old[i] is sorted,
+// so a branch-free binary search over its lanes finds the copy.
+__device__ __forceinline__ void member_keys(const uint64_t* __restrict__ Gold, const uint64_t* __restrict__ R,
+                                            int64_t i, int k, bool rev, uint64_t fb, uint64_t rb, uint64_t& key0,
+                                            uint64_t& key1, bool& new0, bool& new1) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t* row1 = rev ? R + i * k : Gold + i * k + 32;
+    const int lim1 = rev ? k : k - 32;
+    key0 = lane < k ? Gold[i * k + lane] : kEmptyKey;
+    key1 = lane < lim1 ? row1[lane] : kEmptyKey;
+    new0 = ((fb >> lane) & 1ull) != 0;
+    new1 = (((rev ? rb : fb >> 32) >> lane) & 1ull) != 0;
+    if (!rev) return;
+    int lo = 0;  // entries of G_old[i] below key1 (every lane shuffles: the probes differ)
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int probe = lo + step - 1;  // at most 30
+        const uint64_t v = shfl64(key0, probe);
+        if (probe < k && v < key1) lo += step;
+    }
+    const uint64_t at = shfl64(key0, lo);  // lo <= 31
+    const bool dup = key1 != kEmptyKey && lo < k && at == key1;
+    const unsigned promote = __reduce_or_sync(0xffffffffu, (dup && new1) ? (1u << lo) : 0u);
+    new0 = new0 || ((promote >> lane) & 1u) != 0;
+    if (dup) key1 = kEmptyKey;
+}
+
 __device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) {

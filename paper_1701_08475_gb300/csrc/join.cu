@@ -389,25 +389,39 @@ __device__ __forceinline__ void join_node(const float* __restrict__ X, int D, in
     // all new), then the old ones; each takes ids of G_old[i], then of R[i]
     int M = 0, nn = 0;
     const uint64_t fbits = fnew ? fnew[i] : ~0ull, rbits = rnew ? rnew[i] : ~0ull;
-    for (int want = 1; want >= 0; --want) {
-        for (int src = 0; src < (rev ? 2 : 1); ++src) {
-            const uint64_t* row = (src == 0 ? Gold : R) + i * k;
-            const uint64_t bits = src == 0 ? fbits : rbits;
-            for (int e0 = 0; e0 < k; e0 += 32) {
-                const int e = e0 + lane;
-                const uint64_t key = e < k ? row[e] : kEmptyKey;
-                const bool take = key != kEmptyKey && (int)((bits >> e) & 1ull) == want;
-                const unsigned bal = __ballot_sync(0xffffffffu, take);
-                if (take) {
-                    const int at = M + __popc(bal & ((1u << lane) - 1u));
-                    const uint32_t u = key_id(key);
-                    mem[at] = (int32_t)u;
-                    thr[at] = Gold[(int64_t)u * k + k - 1];
-                }
-                M += __popc(bal);
-            }
+    auto take_member = [&](uint64_t key, bool take) {
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        if (take) {
+            const int at = M + __popc(bal & ((1u << lane) - 1u));
+            const uint32_t u = key_id(key);
+            mem[at] = (int32_t)u;
+            thr[at] = Gold[(int64_t)u * k + k - 1];
         }
-        if (want == 1) nn = M;
+        M += __popc(bal);
+    };
+    if (!(rev && k > 32)) {
+        // at most 64 entries, a mutual neighbour once
+        uint64_t key0, key1;
+        bool new0, new1;
+        member_keys(Gold, R, i, k, rev != 0, fbits, rbits, key0, key1, new0, new1);
+        for (int want = 1; want >= 0; --want) {
+            take_member(key0, key0 != kEmptyKey && new0 == (want == 1));
+            take_member(key1, key1 != kEmptyKey && new1 == (want == 1));
+            if (want == 1) nn = M;
+        }
+    } else {
+        for (int want = 1; want >= 0; --want) {
+            for (int src = 0; src < 2; ++src) {
+                const uint64_t* row = (src == 0 ? Gold : R) + i * k;
+                const uint64_t bits = src == 0 ? fbits : rbits;
+                for (int e0 = 0; e0 < k; e0 += 32) {
+                    const int e = e0 + lane;
+                    const uint64_t key = e < k ? row[e] : kEmptyKey;
+                    take_member(key, key != kEmptyKey && (int)((bits >> e) & 1ull) == want);
+                }
+            }
+            if (want == 1) nn = M;
+        }
     }
     __syncwarp();
     if (M < 2 || nn == 0) return;
@@ -699,27 +713,41 @@ __global__ void __launch_bounds__(kJ2Threads, 4) k5_join_cta(const float* __rest
             if (pos < node1) {
                 const int64_t i = list ? (int64_t)list[pos] : pos;
                 const uint64_t fbits = fnew ? fnew[i] : ~0ull, rbits = rnew ? rnew[i] : ~0ull;
-                for (int want = 1; want >= 0; --want) {
-                    for (int src = 0; src < (rev ? 2 : 1); ++src) {
-                        const uint64_t* row = (src == 0 ? Gold : R) + i * k;
-                        const uint64_t bits = src == 0 ? fbits : rbits;
-                        for (int e0 = 0; e0 < k; e0 += 32) {
-                            const int e = e0 + lane;
-                            const uint64_t key = e < k ? row[e] : kEmptyKey;
-                            const bool take = key != kEmptyKey && (int)((bits >> e) & 1ull) == want;
-                            const unsigned bal = __ballot_sync(0xffffffffu, take);
-                            if (take) {
-                                const int m = M + __popc(bal & ((1u << lane) - 1u));
-                                const uint32_t u = key_id(key);
-                                const int sl = j * mcap + j2_slot(m, RGN);
-                                mem[j * mcap + m] = (int32_t)u;
-                                thr[sl] = Gold[(int64_t)u * k + k - 1];
-                                if (lids) slid[sl] = __ldg(reinterpret_cast<const int4*>(leafid) + u);
-                            }
-                            M += __popc(bal);
-                        }
+                auto take_member = [&](uint64_t key, bool take) {
+                    const unsigned bal = __ballot_sync(0xffffffffu, take);
+                    if (take) {
+                        const int m = M + __popc(bal & ((1u << lane) - 1u));
+                        const uint32_t u = key_id(key);
+                        const int sl = j * mcap + j2_slot(m, RGN);
+                        mem[j * mcap + m] = (int32_t)u;
+                        thr[sl] = Gold[(int64_t)u * k + k - 1];
+                        if (lids) slid[sl] = __ldg(reinterpret_cast<const int4*>(leafid) + u);
                     }
-                    if (want == 1) nn = M;
+                    M += __popc(bal);
+                };
+                if (!(rev && k > 32)) {
+                    // at most 64 entries, a mutual neighbour once
+                    uint64_t key0, key1;
+                    bool new0, new1;
+                    member_keys(Gold, R, i, k, rev != 0, fbits, rbits, key0, key1, new0, new1);
+                    for (int want = 1; want >= 0; --want) {
+                        take_member(key0, key0 != kEmptyKey && new0 == (want == 1));
+                        take_member(key1, key1 != kEmptyKey && new1 == (want == 1));
+                        if (want == 1) nn = M;
+                    }
+                } else {
+                    for (int want = 1; want >= 0; --want) {
+                        for (int src = 0; src < 2; ++src) {
+                            const uint64_t* row = (src == 0 ? Gold : R) + i * k;
+                            const uint64_t bits = src == 0 ? fbits : rbits;
+                            for (int e0 = 0; e0 < k; e0 += 32) {
+                                const int e = e0 + lane;
+                                const uint64_t key = e < k ? row[e] : kEmptyKey;
+                                take_member(key, key != kEmptyKey && (int)((bits >> e) & 1ull) == want);
+                            }
+                        }
+                        if (want == 1) nn = M;
+                    }
                 }
             }
             if (lane == 0) {

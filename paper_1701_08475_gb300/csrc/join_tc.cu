@@ -202,12 +202,9 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                 const uint64_t fb = fnew ? fnew[i] : ~0ull, rb = rnew ? rnew[i] : ~0ull;
                 // at most 64 entries: G[i] then R[i] (k <= 32), or G[i] in two
                 // halves; both loaded at once, then taken new first, old after
-                const uint64_t* row1 = rev ? R + i * k : Gold + i * k + 32;
-                const int lim1 = rev ? k : k - 32;
-                const uint64_t key0 = lane < k ? Gold[i * k + lane] : kEmptyKey;
-                const uint64_t key1 = lane < lim1 ? row1[lane] : kEmptyKey;
-                const bool new0 = ((fb >> lane) & 1ull) != 0;
-                const bool new1 = (((rev ? rb : fb >> 32) >> lane) & 1ull) != 0;
+                uint64_t key0, key1;
+                bool new0, new1;
+                member_keys(Gold, R, i, k, rev, fb, rb, key0, key1, new0, new1);
                 const unsigned below = (1u << lane) - 1u;
                 for (int want = 1; want >= 0; --want) {
                     const bool t0 = key0 != kEmptyKey && new0 == (want == 1);
