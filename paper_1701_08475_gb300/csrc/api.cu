@@ -725,6 +725,10 @@ void carve(Workspace& ws, BuildLayout& b, const Args& a, const TreePlan& tp, boo
         b.jb.fnew_buf = ws.take<uint64_t>(n);
         b.jb.active = ws.take<int32_t>(n);
         b.jb.nactive = ws.take<int32_t>(4);
+        if (rev) {
+            b.jb.ovf_list = ws.take<int32_t>(n);
+            b.jb.ovf_count = ws.take<int32_t>(4);
+        }
         b.jb.pcnt = ws.take<int32_t>(n + 1);
         b.jb.poff = ws.take<int32_t>(n + 1);
         b.jb.pcur = ws.take<int32_t>(n);

@@ -27,6 +27,8 @@
 // next group's collection runs while this group's offer slots are fetched.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tc.cuh"
@@ -146,7 +148,9 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                                                          const float* __restrict__ X, int D,
                                                          const float* __restrict__ qerr,
                                                          const int32_t* __restrict__ count_dev,
-                                                         const int32_t* __restrict__ leafid, int npass) {
+                                                         const int32_t* __restrict__ leafid, int npass,
+                                                         int32_t* __restrict__ ovf_list,
+                                                         int32_t* __restrict__ ovf_count) {
     extern __shared__ uint8_t smem_raw[];
     // the exact form runs when the 16-bit copy is exact, the screening form
     // (CERT) when it is not; each returns at once otherwise
@@ -206,6 +210,14 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
                 bool new0, new1;
                 member_keys(Gold, R, i, k, rev, fb, rb, key0, key1, new0, new1);
                 const unsigned below = (1u << lane) - 1u;
+                // more members than the slot holds (slots smaller than 2k): the
+                // node goes to the overflow list, for the launch with full slots
+                const int all = __popc(__ballot_sync(0xffffffffu, key0 != kEmptyKey)) +
+                                __popc(__ballot_sync(0xffffffffu, key1 != kEmptyKey));
+                if (all > mcap) {
+                    if (lane == 0) ovf_list[atomicAdd(ovf_count, 1)] = (int32_t)i;
+                    key0 = key1 = kEmptyKey;
+                }
                 for (int want = 1; want >= 0; --want) {
                     const bool t0 = key0 != kEmptyKey && new0 == (want == 1);
                     const unsigned b0 = __ballot_sync(0xffffffffu, t0);
@@ -564,13 +576,13 @@ __global__ void __launch_bounds__(kThreads, 4) k5_join_tc(const uint16_t* __rest
 
 }  // namespace
 
-bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev, const uint64_t* Gold,
-                    const uint64_t* R, int64_t node0, int64_t node1, const JoinBuffers& b, int* status,
-                    const int* notexact, bool bf16, cudaStream_t s, bool cert, const float* X) {
-    const int Dp = lp_dim(D);
-    const int mcap = ((rev ? 2 * k : k) + 7) & ~7;
-    if (mcap > 64) return false;  // a 64-bit mask of offers per tile row
-    if (cert && (!X || !b.qerr)) return false;
+namespace {
+// One launch of the tensor-core join with member slots of mcap rows (ovf:
+// nodes with more members go to b.ovf_list); bytes: its algorithmic bytes.
+void join_tc_once(const uint16_t* Xq, int Dp, const float* nrm, int k, bool rev, int mcap, const uint64_t* Gold,
+                  const uint64_t* R, int64_t node0, int64_t node1, const JoinBuffers& b, int* status,
+                  const int* notexact, bool bf16, cudaStream_t s, bool cert, const float* X, int D, bool ovf,
+                  double bytes) {
     const int npc = kRows / mcap;
     const JtSmem L = jt_smem(Dp, mcap, cert);
     // at least 56 KB per CTA: at most 4 CTAs (512 tensor-memory columns) per SM
@@ -579,26 +591,59 @@ bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev
     const int64_t nodes = node1 - node0;
     const int64_t groups = (nodes + npc - 1) / npc;
     const int per_sm = (int)((227 * 1024) / smem) < 4 ? (int)((227 * 1024) / smem) : 4;
-    const int grid = (int)(groups < (int64_t)152 * per_sm ? groups : (int64_t)152 * per_sm);
-    const double m = rev ? 2.0 * k : (double)k;
+    const int grid = (int)std::max<int64_t>(1, groups < (int64_t)152 * per_sm ? groups : (int64_t)152 * per_sm);
     // certifying: the canonical distances' rows of X are counted per offer
     // written (record_bytes), not here
-    LaunchScope ls(cert ? "k5_join_tc_cert" : "k5_join_tc", s,
-                   (double)nodes * (m * Dp * 2.0 + 2 * k * 8.0 + m * (cert ? 20.0 : 12.0)),
-                   (double)groups * kRows * kRows * 2.0 * Dp);
+    LaunchScope ls(cert ? "k5_join_tc_cert" : "k5_join_tc", s, bytes, bytes > 0 ? (double)groups * kRows * kRows * 2.0 * Dp : 0.0);
+    int32_t* ol = ovf ? b.ovf_list : nullptr;
+    int32_t* oc = ovf ? b.ovf_count : nullptr;
     if (cert) {
         cudaFuncSetAttribute(k5_join_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k5_join_tc<true><<<grid, kThreads, smem, s>>>(Xq, Dp, nrm, k, rev ? 1 : 0, mcap, npc, Gold, R, b.list, b.fnew,
                                                       b.rnew, node0, node1, b.counter, b.cap, b.ptgt, b.pkey, b.pcnt,
                                                       status, notexact, bf16, X, D, b.qerr, b.count_dev, b.leafid,
-                                                      b.npass);
+                                                      b.npass, ol, oc);
     } else {
         cudaFuncSetAttribute(k5_join_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k5_join_tc<false><<<grid, kThreads, smem, s>>>(Xq, Dp, nrm, k, rev ? 1 : 0, mcap, npc, Gold, R, b.list,
                                                        b.fnew, b.rnew, node0, node1, b.counter, b.cap, b.ptgt, b.pkey,
                                                        b.pcnt, status, notexact, bf16, nullptr, 0, nullptr,
-                                                       b.count_dev, b.leafid, b.npass);
+                                                       b.count_dev, b.leafid, b.npass, ol, oc);
     }
+}
+}  // namespace
+
+bool launch_join_tc(const uint16_t* Xq, int D, const float* nrm, int k, bool rev, const uint64_t* Gold,
+                    const uint64_t* R, int64_t node0, int64_t node1, const JoinBuffers& b, int* status,
+                    const int* notexact, bool bf16, cudaStream_t s, bool cert, const float* X) {
+    const int Dp = lp_dim(D);
+    const int mcap = ((rev ? 2 * k : k) + 7) & ~7;
+    if (mcap > 64) return false;  // a 64-bit mask of offers per tile row
+    if (cert && (!X || !b.qerr)) return false;
+    const double m = rev ? 2.0 * k : (double)k;
+    const double bytes = (double)(node1 - node0) * (m * Dp * 2.0 + 2 * k * 8.0 + m * (cert ? 20.0 : 12.0));
+    // With reverse lists a mutual neighbour is one member, so most nodes
+    // have far fewer than 2k: slots of four fifths of 2k (rounded to 8) when
+    // that packs more nodes into a tile, the nodes that do not fit joined
+    // after them with full slots (their count read on the device)
+    int small = mcap;
+    if (rev && b.ovf_list && b.ovf_count) {
+        const int m2 = (mcap * 4 / 5 + 7) & ~7;
+        if (m2 >= 8 && kRows / m2 > kRows / mcap) small = m2;
+    }
+    if (small == mcap) {
+        join_tc_once(Xq, Dp, nrm, k, rev, mcap, Gold, R, node0, node1, b, status, notexact, bf16, s, cert, X, D,
+                     false, bytes);
+        return true;
+    }
+    cudaMemsetAsync(b.ovf_count, 0, sizeof(int32_t), s);
+    join_tc_once(Xq, Dp, nrm, k, rev, small, Gold, R, node0, node1, b, status, notexact, bf16, s, cert, X, D, true,
+                 bytes);
+    JoinBuffers b2 = b;
+    b2.list = b.ovf_list;
+    b2.count_dev = b.ovf_count;
+    join_tc_once(Xq, Dp, nrm, k, rev, mcap, Gold, R, 0, node1 - node0, b2, status, notexact, bf16, s, cert, X, D,
+                 false, 0.0);
     return true;
 }
 

@@ -194,6 +194,12 @@ struct JoinBuffers {
     // that pair again could not change either list, and the join skips it.
     const int32_t* leafid = nullptr;
     int npass = 0;
+    // the tensor-core join with reverse lists first packs nodes into slots
+    // smaller than 2k members (a mutual neighbour is one member, so most
+    // nodes have far fewer); a node that does not fit is listed here and joined
+    // by a second launch with full slots
+    int32_t* ovf_list = nullptr;   // [n]
+    int32_t* ovf_count = nullptr;  // [1]
     // sampled rounds: per node a flag mask (bit e: entry e of the list is
     // new) and the mask after this round's sample (NULL: full rounds)
     uint64_t* flags = nullptr;

@@ -276,6 +276,19 @@ def test_exact_join_three_passes_matches_oracle(knng, k):
     _assert_graph_equal(ids, d, o_ids, o_d)
 
 
+@pytest.mark.parametrize("k", [20, 24])
+def test_exact_join_overflow_slots_match_oracle(knng, k):
+    # nearly uniform integer data: few mutual neighbours, so many nodes have
+    # more members than the tensor-core join's smaller first-launch slot and
+    # go through the second launch with full slots
+    n = 4000
+    X = datagen.sift_like(n, D=48, n_centres=n, seed=31 + k)
+    common = dict(k=k, leaf_max=64, tree_passes=2, refine_rounds=3, seed=9, join_mode=oracle.FWD_REV)
+    ids, d = knng.knng_build_ex(_dev(X), knng.default_params(precision=knng.KNNG_BF16, **common))
+    o_ids, o_d = oracle.build_graph(X, k, 64, passes=2, rounds=3, seed=9, mode=oracle.FWD_REV)
+    _assert_graph_equal(ids, d, o_ids, o_d)
+
+
 def test_refine_small_offer_budget_retries_chunks(knng, monkeypatch):
     # a 1 MB offer buffer: chunks sized from the offer estimate overflow and
     # are re-run smaller; the result must not change
