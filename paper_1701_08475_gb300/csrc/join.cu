@@ -671,7 +671,9 @@ __global__ void __launch_bounds__(kJ2Threads, 4) k5_join_cta(const float* __rest
                                                          int32_t* __restrict__ pcnt, int* __restrict__ status,
                                                          const int* __restrict__ skip_if_exact,
                                                          const int32_t* __restrict__ count_dev,
-                                                         const int32_t* __restrict__ leafid, int npass) {
+                                                         const int32_t* __restrict__ leafid, int npass,
+                                                         int32_t* __restrict__ ovf_list,
+                                                         int32_t* __restrict__ ovf_count) {
     extern __shared__ float4 smem4[];
     if (*status & kStatusStop) return;
     if (count_dev && (int64_t)*count_dev < node1) node1 = *count_dev;
@@ -730,6 +732,14 @@ __global__ void __launch_bounds__(kJ2Threads, 4) k5_join_cta(const float* __rest
                     uint64_t key0, key1;
                     bool new0, new1;
                     member_keys(Gold, R, i, k, rev != 0, fbits, rbits, key0, key1, new0, new1);
+                    // more members than the slot holds (slots smaller than 2k):
+                    // the node goes to the overflow list, for the full-slot launch
+                    const int all = __popc(__ballot_sync(0xffffffffu, key0 != kEmptyKey)) +
+                                    __popc(__ballot_sync(0xffffffffu, key1 != kEmptyKey));
+                    if (all > mcap) {
+                        if (lane == 0) ovf_list[atomicAdd(ovf_count, 1)] = (int32_t)i;
+                        key0 = key1 = kEmptyKey;
+                    }
                     for (int want = 1; want >= 0; --want) {
                         take_member(key0, key0 != kEmptyKey && new0 == (want == 1));
                         take_member(key1, key1 != kEmptyKey && new1 == (want == 1));
@@ -1231,8 +1241,6 @@ const char* launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev,
             return "k5_join_tc_cert";
         {
             const double m = rev ? 2.0 * k : (double)k;
-            LaunchScope ls("k5_join", s, (double)(c1 - c0) * (m * D * 4.0 + 2 * k * 8.0 + m * 8.0),
-                           (double)(c1 - c0) * m * (m - 1) / 2 * 3.0 * D);
             const bool lids = b.leafid != nullptr && b.npass > 0;
             const J2Layout L2 = j2_layout(D, mcap, lids);
             // the CTA-wide kernel when it keeps clearly more lanes busy than
@@ -1240,17 +1248,38 @@ const char* launch_join_chunk(const float* X, int64_t n, int D, int k, bool rev,
             // a multiple of 32)
             const double warp_eff = (double)L2.NB / (32.0 * ((L2.NB + 31) / 32));
             const double cta_eff = (double)(L2.G * L2.NB) / kJ2Threads;
-            if (cta_eff >= warp_eff + 0.1) {
-                cudaFuncSetAttribute(k5_join_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L2.total);
-                int per_sm = 0;
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k5_join_cta, kJ2Threads, L2.total);
-                if (per_sm < 1) per_sm = 1;
-                const int64_t groups = (c1 - c0 + L2.G - 1) / L2.G;
-                const int grid2 = (int)std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)152 * per_sm));
-                k5_join_cta<<<grid2, kJ2Threads, L2.total, s>>>(X, D, k, rev ? 1 : 0, mcap, Gold, b.R, b.list, b.fnew,
-                                                               b.rnew, c0, c1, b.counter, b.cap, b.ptgt, b.pkey,
-                                                               b.pcnt, status, tc_dev ? b.notexact : nullptr,
-                                                               b.count_dev, lids ? b.leafid : nullptr, b.npass);
+            const bool cta = cta_eff >= warp_eff + 0.1;
+            // With reverse lists a mutual neighbour is one member: slots of
+            // three quarters of 2k when that packs more nodes into a CTA, the
+            // nodes that overflow joined after them with full slots (their
+            // count read on the device)
+            const int small = (mcap * 3 / 4 + 3) & ~3;
+            const bool packed = cta && rev && k <= 32 && b.ovf_list && b.ovf_count && small >= 4 &&
+                                j2_layout(D, small, lids).G > L2.G;
+            LaunchScope ls("k5_join", s, (double)(c1 - c0) * (m * D * 4.0 + 2 * k * 8.0 + m * 8.0),
+                           (double)(c1 - c0) * m * (m - 1) / 2 * 3.0 * D, packed ? 2 : 1);
+            if (cta) {
+                auto cta_launch = [&](int mc, const int32_t* lst, const int32_t* cnt_dev, int64_t n0, int64_t n1,
+                                      bool ovf) {
+                    const J2Layout Lc = j2_layout(D, mc, lids);
+                    cudaFuncSetAttribute(k5_join_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lc.total);
+                    int per_sm = 0;
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k5_join_cta, kJ2Threads, Lc.total);
+                    if (per_sm < 1) per_sm = 1;
+                    const int64_t groups = (n1 - n0 + Lc.G - 1) / Lc.G;
+                    const int grid2 = (int)std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)152 * per_sm));
+                    k5_join_cta<<<grid2, kJ2Threads, Lc.total, s>>>(
+                        X, D, k, rev ? 1 : 0, mc, Gold, b.R, lst, b.fnew, b.rnew, n0, n1, b.counter, b.cap, b.ptgt,
+                        b.pkey, b.pcnt, status, tc_dev ? b.notexact : nullptr, cnt_dev, lids ? b.leafid : nullptr,
+                        b.npass, ovf ? b.ovf_list : nullptr, ovf ? b.ovf_count : nullptr);
+                };
+                if (packed) {
+                    cudaMemsetAsync(b.ovf_count, 0, sizeof(int32_t), s);
+                    cta_launch(small, b.list, b.count_dev, c0, c1, true);
+                    cta_launch(mcap, b.ovf_list, b.ovf_count, 0, c1 - c0, false);
+                } else {
+                    cta_launch(mcap, b.list, b.count_dev, c0, c1, false);
+                }
                 return "k5_join";
             }
             const int grid = (int)std::min<int64_t>((c1 - c0 + kJoinWarps - 1) / kJoinWarps, 152 * 32);

@@ -289,6 +289,19 @@ def test_exact_join_overflow_slots_match_oracle(knng, k):
     _assert_graph_equal(ids, d, o_ids, o_d)
 
 
+@pytest.mark.parametrize("k,D", [(16, 40), (12, 96)])
+def test_fp32_join_overflow_slots_match_oracle(knng, k, D):
+    # the CTA-wide FP32 join packs nodes in slots of three quarters of 2k;
+    # nearly uniform float data leaves many nodes more members than that, and
+    # the second launch with full slots joins them
+    n = 4000
+    X = datagen.gaussian_mixture(n, D, n, seed=41 + k)
+    common = dict(k=k, leaf_max=64, tree_passes=2, refine_rounds=3, seed=13, join_mode=oracle.FWD_REV)
+    ids, d = knng.knng_build_ex(_dev(X), knng.default_params(precision=knng.KNNG_FP32, **common))
+    o_ids, o_d = oracle.build_graph(X, k, 64, passes=2, rounds=3, seed=13, mode=oracle.FWD_REV)
+    _assert_graph_equal(ids, d, o_ids, o_d)
+
+
 def test_refine_small_offer_budget_retries_chunks(knng, monkeypatch):
     # a 1 MB offer buffer: chunks sized from the offer estimate overflow and
     # are re-run smaller; the result must not change
