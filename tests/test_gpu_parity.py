@@ -289,11 +289,12 @@ def test_exact_join_overflow_slots_match_oracle(knng, k):
     _assert_graph_equal(ids, d, o_ids, o_d)
 
 
-@pytest.mark.parametrize("k,D", [(16, 40), (12, 96)])
+@pytest.mark.parametrize("k,D", [(16, 40), (12, 96), (20, 64)])
 def test_fp32_join_overflow_slots_match_oracle(knng, k, D):
-    # the CTA-wide FP32 join packs nodes in slots of three quarters of 2k;
-    # nearly uniform float data leaves many nodes more members than that, and
-    # the second launch with full slots joins them
+    # the CTA-wide FP32 join (k = 16 and 12) packs nodes in slots of three
+    # quarters of 2k; nearly uniform float data leaves many nodes more members
+    # than that, and the second launch with full slots joins them (k = 20: the
+    # warp-per-node kernel, on the same data)
     n = 4000
     X = datagen.gaussian_mixture(n, D, n, seed=41 + k)
     common = dict(k=k, leaf_max=64, tree_passes=2, refine_rounds=3, seed=13, join_mode=oracle.FWD_REV)
