@@ -143,11 +143,16 @@ KNNG_API int knng_build_batched(int n_inst, const knng_instance *inst, const knn
  * A build (as knng_build_ex: Sec. 3.1 / Alg. 1, then the refinement rounds of
  * Sec. 1) recorded once into a CUDA graph and replayed at will.  The paper
  * has no counterpart; recording removes the host's part of every launch.
- * data, out_ids and out_dists must be device buffers; they are bound at
- * creation, so a replay rebuilds the graph of whatever `data` then holds into
- * the same outputs.  The plan owns its workspace (device memory for the whole
- * build; the offer buffer is sized for one chunk per round up to 48 GB, since
- * a graph cannot read offer counts back) until knng_plan_destroy.
+ * data, out_ids and out_dists are device buffers or page-locked host buffers
+ * (cudaHostAlloc, cudaMallocHost, cudaHostRegister; pageable memory is refused
+ * with KNNG_EINVAL); they are bound at creation, so a replay rebuilds the
+ * graph of whatever `data` then holds into the same outputs.  A host buffer
+ * gets a workspace copy: each replay copies data in at its start and the lists
+ * out at its end, inside the graph, so a replay followed by a wait on the
+ * stream leaves the lists in host memory.  The plan owns its workspace
+ * (device memory for the whole build; the offer buffer is sized for one chunk
+ * per round up to 48 GB, since a graph cannot read offer counts back) until
+ * knng_plan_destroy.
  * Recording makes no host reads of the data: every choice the host would make
  * from it (the join kind, the chunk sizes) is made on the device instead, and
  * the result equals knng_build_ex's bit for bit.

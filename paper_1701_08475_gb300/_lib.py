@@ -236,14 +236,20 @@ def knng_build_batched(datas, params, leaf_maxes=None, stream=None, twomeans_ite
 class BuildPlan:
     """A build recorded once into a CUDA graph (knng_plan_*): `launch()`
     replays it on `data` into (ids, dists); `check()` waits and raises on a
-    device-reported error.  Device tensors only."""
+    device-reported error.  Torch tensors on the device, or page-locked
+    host tensors (`pin_memory()`): then every replay copies `data` in and the
+    lists out, and the outputs made here are page-locked too."""
 
-    def __init__(self, data, params, stream=None):
+    def __init__(self, data, params, stream=None, out=None):
         import torch
         self.data = _contig(data, "float32")
         n, D = self.data.shape
-        self.ids = torch.empty((n, params.k), dtype=torch.int32, device=self.data.device)
-        self.dists = torch.empty((n, params.k), dtype=torch.float32, device=self.data.device)
+        if out is not None:
+            self.ids, self.dists = out
+        else:
+            pin = not self.data.is_cuda
+            self.ids = torch.empty((n, params.k), dtype=torch.int32, device=self.data.device, pin_memory=pin)
+            self.dists = torch.empty((n, params.k), dtype=torch.float32, device=self.data.device, pin_memory=pin)
         self._plan = ctypes.c_void_p()
         self._stream = stream
         with _DeviceCtx(self.data, stream) as s:

@@ -283,6 +283,18 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Page-locked host memory (cudaHostAlloc, cudaMallocHost or cudaHostRegister):
+// the only host memory a recorded copy may name.
+bool is_pinned_host_ptr(const void* p) {
+    if (p == nullptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 // A caller buffer as the kernels see it: the caller's device pointer, or a
 // workspace copy of a host buffer.
 template <class T>
@@ -1205,8 +1217,10 @@ int knng_plan_create(const float* data, int64_t n, int D, const knng_params* p, 
         validate_common(data, n, D, p->k);
         validate_params(p, n);
         if (!out_ids || !out_dists) fail(KNNG_EINVAL, "output pointer is NULL");
-        if (!is_device_ptr(data) || !is_device_ptr(out_ids) || !is_device_ptr(out_dists))
-            fail(KNNG_EINVAL, "a recorded build needs device buffers (data and outputs)");
+        const void* bufs[3] = {data, out_ids, out_dists};
+        for (const void* q : bufs)
+            if (!is_device_ptr(q) && !is_pinned_host_ptr(q))
+                fail(KNNG_EINVAL, "a recorded build needs device or page-locked host buffers (data and outputs)");
         if (p->join_mode == KNNG_JOIN_SAMPLED && p->refine_rounds > 0)
             fail(KNNG_EINVAL, "a recorded build does not take the sampled join");
         // work the caller queued on `stream` (its inputs) completes first
@@ -1217,8 +1231,16 @@ int knng_plan_create(const float* data, int64_t n, int D, const knng_params* p, 
         g.a = Args{n, D, *p};
         g.a.offer_budget = recorded_offer_budget(n, p, 48e9);
         if (p->tree_passes > 0) g.tp.make(n, p->leaf_max);
+        // host buffers get workspace copies; the graph copies in and out
+        DevBuf<float> X;
+        DevBuf<int32_t> oi;
+        DevBuf<float> od;
+        const size_t nk = (size_t)n * p->k;
         for (int pass = 0; pass < 2; ++pass) {
             g.ws.used = 0;
+            bind(g.ws, X, data, (size_t)n * D, pass);
+            bind(g.ws, oi, out_ids, nk, pass);
+            bind(g.ws, od, out_dists, nk, pass);
             carve(g.ws, g.b, g.a, g.tp, p->tree_passes > 0, p->refine_rounds > 0);
             if (pass == 0) g.ws.allocate(nullptr);
         }
@@ -1226,8 +1248,11 @@ int knng_plan_create(const float* data, int64_t n, int D, const knng_params* p, 
         prepare_recorded(g);
         record_plan(pl.get(), [&](cudaStream_t cs, SideStreams* side) {
             cuda_check(cudaMemsetAsync(g.b.status, 0, 4 * sizeof(int), cs), "status clear");
-            build_core(data, g.a, g.b, g.tp, cs, side);
-            launch_unpack(g.b.G, out_ids, out_dists, n * (int64_t)p->k, cs);
+            upload(X, cs);
+            build_core(X.dev, g.a, g.b, g.tp, cs, side);
+            launch_unpack(g.b.G, oi.dev, od.dev, (int64_t)nk, cs);
+            download(oi, cs);
+            download(od, cs);
         });
         *out_plan = pl.release();
     });

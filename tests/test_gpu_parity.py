@@ -569,3 +569,32 @@ def test_recorded_build_equals_direct_build(knng, precision, kind, mode):
         plan.launch()
         with pytest.raises(knng.KnngError):
             plan.check()
+
+
+def test_recorded_build_from_pinned_host_buffers(knng):
+    # page-locked host data and outputs: each replay copies the rows in and
+    # the lists out inside the graph; the lists equal the device build's
+    n, D, k = 5000, 48, 10
+    X = datagen.sift_like(n, D=D, n_centres=50, seed=4)
+    p = knng.default_params(k=k, leaf_max=64, tree_passes=2, refine_rounds=2, seed=8,
+                            precision=knng.KNNG_BF16, join_mode=oracle.FWD_REV)
+    ids0, d0 = knng.knng_build_ex(_dev(X), p)
+    o_ids, o_d = oracle.build_graph(X, k, 64, passes=2, rounds=2, seed=8, mode=oracle.FWD_REV)
+    _assert_graph_equal(ids0, d0, o_ids, o_d)
+    Xh = torch.from_numpy(X).pin_memory()
+    with knng.BuildPlan(Xh, p) as plan:
+        assert not plan.ids.is_cuda and plan.ids.is_pinned() and plan.dists.is_pinned()
+        for _ in range(2):
+            plan.ids.fill_(-7)
+            ids, d = plan.launch()
+            plan.check()  # waits for the stream: the lists are in host memory
+            _assert_graph_equal(ids, d, o_ids, o_d)
+        X2 = datagen.sift_like(n, D=D, n_centres=50, seed=9)
+        Xh.copy_(torch.from_numpy(X2))
+        ids, d = plan.launch()
+        plan.check()
+        ids2, d2 = knng.knng_build_ex(_dev(X2), p)
+        _assert_graph_equal(ids, d, _np(ids2), _np(d2))
+    # pageable host memory cannot be named by a recorded copy
+    with pytest.raises(knng.KnngError):
+        knng.BuildPlan(torch.from_numpy(X), p)
