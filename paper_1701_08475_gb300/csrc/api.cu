@@ -594,6 +594,7 @@ int byte_dim(int D) { return (D + 15) & ~15; }
 // kernel and sizes the statistics' algorithmic bytes).
 void make_bytes(const float* X, const Args& a, BuildLayout& b, cudaStream_t s) {
     if (!b.Xb) return;
+    cuda_check(cudaMemsetAsync(b.bflag, 0, sizeof(int), s), "flag clear");
     launch_bytes(X, a.n, a.D, byte_dim(a.D), b.Xb, b.bflag, s);
     if (b.jb.capture) return;  // a graph records no host reads
     int f = 1;
@@ -845,13 +846,31 @@ struct SideStreams {
     }
 };
 
+// The device work that reads X before the tree passes, over rows
+// [r0, r0 + rows): the finiteness check, the original-order low-precision copy
+// (norms, errors, exactness flag) and the byte copy (its flag).  The flags are
+// cleared once, before the first piece.
+void prepare_rows(const float* X, int64_t r0, int64_t rows, const Args& a, BuildLayout& b, cudaStream_t s) {
+    const int D = a.D;
+    launch_check_finite(X + r0 * D, rows * D, b.status, s);
+    if (b.Xq) {
+        const int qt = qtype(a.p.precision);
+        launch_quantize(X + r0 * D, rows, D, nullptr, qt,
+                        reinterpret_cast<uint8_t*>(b.Xq) + r0 * (int64_t)lp_row_bytes(D, qt), b.q_nrm + r0,
+                        b.q_err + r0, b.q_scale ? b.q_scale + r0 : nullptr, b.notexact, s);
+    }
+    if (b.Xb) launch_bytes(X + r0 * D, rows, D, byte_dim(D), b.Xb + r0 * byte_dim(D), b.bflag, s);
+}
+
 // side: helper streams that outlive the call's stream capture (a recorded
-// build); NULL: made here for this call.
+// build); NULL: made here for this call.  up: the caller's rows when they are
+// in host memory (up->dev is X): they are copied in pieces on a helper stream
+// while the caller's stream prepares the pieces already in, so the work of
+// prepare_rows hides under the copy, which the host link bounds.
 void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& tp, cudaStream_t s,
-                SideStreams* side_in = nullptr) {
+                SideStreams* side_in = nullptr, const DevBuf<float>* up = nullptr) {
     const int64_t n = a.n;
     const int k = a.p.k;
-    launch_check_finite(X, n * (int64_t)a.D, b.status, s);
     launch_fill_empty(b.G, n * k, s);
     if (a.p.tree_passes > 0 && !b.jb.capture)  // a captured build has its plan uploaded beforehand
         cuda_check(cudaMemcpyAsync(b.plan_dev, tp.host.data(), tp.host.size() * 4, cudaMemcpyHostToDevice, s),
@@ -861,13 +880,44 @@ void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& t
     // re-ranked candidates per row: k plus a margin, at most 63
     const int kp = std::min(63, k + std::max(k / 2, 8));
     if (b.notexact) cuda_check(cudaMemsetAsync(b.notexact, 0, sizeof(int), s), "flag clear");
-    quantize_for_join(X, a, b, s);
-    make_bytes(X, a, b, s);
+    if (b.Xb) cuda_check(cudaMemsetAsync(b.bflag, 0, sizeof(int), s), "flag clear");
+    SideStreams side_local;
+    SideStreams& side = side_in ? *side_in : side_local;
+    if (up && up->host && up->count) {
+        side.make(1);
+        cudaStream_t cp = side.h[0];
+        cudaEvent_t fork = side.event();
+        cuda_check(cudaEventRecord(fork, s), "event record");
+        cuda_check(cudaStreamWaitEvent(cp, fork, 0), "stream wait");
+        // eight pieces of a multiple of 4 rows (16-byte aligned starts)
+        const int64_t piece = std::max<int64_t>(4, ((n + 7) / 8 + 3) & ~(int64_t)3);
+        for (int64_t r0 = 0; r0 < n; r0 += piece) {
+            const int64_t rows = std::min(piece, n - r0);
+            cuda_check(cudaMemcpyAsync(up->dev + r0 * a.D, up->host + r0 * a.D, (size_t)rows * a.D * sizeof(float),
+                                       cudaMemcpyHostToDevice, cp),
+                       "H2D copy");
+            cudaEvent_t in = side.event();
+            cuda_check(cudaEventRecord(in, cp), "event record");
+            cuda_check(cudaStreamWaitEvent(s, in, 0), "stream wait");
+            prepare_rows(X, r0, rows, a, b, s);
+        }
+    } else {
+        if (up) upload(*const_cast<DevBuf<float>*>(up), s);
+        prepare_rows(X, 0, n, a, b, s);
+    }
+    if (!b.jb.capture && (b.Xq || b.Xb)) {  // a graph records no host reads
+        // the kernels pick their paths from the device flags; the host copies
+        // pick the sums kernel and size the statistics' algorithmic bytes
+        int f[2] = {0, 1};
+        if (b.Xq) cuda_check(cudaMemcpyAsync(&f[0], b.notexact, sizeof(int), cudaMemcpyDeviceToHost, s), "flag read");
+        if (b.Xb) cuda_check(cudaMemcpyAsync(&f[1], b.bflag, sizeof(int), cudaMemcpyDeviceToHost, s), "flag read");
+        cuda_check(cudaStreamSynchronize(s), "stream synchronize");
+        if (b.Xq) b.sb.q16_host = b.sb.Xq != nullptr && (f[0] & 1) == 0 && !((f[0] & 2) && (f[0] & 4));
+        if (b.Xb) b.sb.u8_host = f[1] == 0;
+    }
     // partitions: pass p on slot p % nslots (slot 0 on the caller's stream,
     // slot q > 0 on helper stream q - 1, forked from the caller's stream); a
     // slot's next partition waits for the leaf stage that read its last one
-    SideStreams side_local;
-    SideStreams& side = side_in ? *side_in : side_local;
     const int P = a.p.tree_passes, Q = b.nslots;
     std::vector<int32_t*> perms((size_t)std::max(P, 0), nullptr);
     std::vector<cudaEvent_t> part_done((size_t)std::max(P, 0), nullptr), leaf_done((size_t)std::max(P, 0), nullptr);
@@ -976,8 +1026,7 @@ int knng_build_ex(const float* data, int64_t n, int D, const knng_params* p, int
         if (p->tree_passes > 0) tp.rebase(b.plan_dev);
         cuda_check(cudaMemsetAsync(b.status, 0, 4 * sizeof(int), s), "status clear");
         offers_begin(b, s);
-        upload(X, s);
-        build_core(X.dev, a, b, tp, s);
+        build_core(X.dev, a, b, tp, s, nullptr, &X);
         launch_unpack(b.G, oi.dev, od.dev, (int64_t)nk, s);
         download(oi, s);
         download(od, s);
@@ -1248,8 +1297,7 @@ int knng_plan_create(const float* data, int64_t n, int D, const knng_params* p, 
         prepare_recorded(g);
         record_plan(pl.get(), [&](cudaStream_t cs, SideStreams* side) {
             cuda_check(cudaMemsetAsync(g.b.status, 0, 4 * sizeof(int), cs), "status clear");
-            upload(X, cs);
-            build_core(X.dev, g.a, g.b, g.tp, cs, side);
+            build_core(X.dev, g.a, g.b, g.tp, cs, side, &X);
             launch_unpack(g.b.G, oi.dev, od.dev, (int64_t)nk, cs);
             download(oi, cs);
             download(od, cs);

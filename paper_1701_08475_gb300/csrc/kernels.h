@@ -123,7 +123,8 @@ int lp_row_bytes(int D, int qt);
 // The leaf certificate's coefficient of (||x^_i|| + ||x^_j||)^2.
 float lp_cert_coeff(int D, int qt);
 // Byte copy of X (rows of Db bytes) and its flag: 0 when every value is an
-// integer in [0, 255].
+// integer in [0, 255].  The caller clears *bflag; launches over several row
+// ranges accumulate into it.
 void launch_bytes(const float* X, int64_t n, int D, int Db, uint8_t* Xb, int* bflag, cudaStream_t s);
 // Low-precision copy of X (perm: row order; NULL = identity), squared norms
 // of the copy, quantisation errors and (FP8) row scales; *notexact |= 1 when

@@ -1762,7 +1762,6 @@ void run_split_level(const float* X, int D, const LevelPlan& lp, int iters, uint
 
 void launch_bytes(const float* X, int64_t n, int D, int Db, uint8_t* Xb, int* bflag, cudaStream_t s) {
     LaunchScope ls("k0_bytes", s, (double)n * (D * 4.0 + Db), 0);
-    cudaMemsetAsync(bflag, 0, sizeof(int), s);
     k0_bytes<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(X, n, D, Db, Xb, bflag);
 }
 
