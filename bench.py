@@ -36,7 +36,7 @@ RECALL_SAMPLE = 10_000
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-search", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--config-steps", type=int, default=2, help="timed steps per form of the other workloads")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16", "fp8"])
     return ap.parse_args()
 

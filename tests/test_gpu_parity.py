@@ -89,13 +89,27 @@ def test_plain_build_entry_point(knng):
     _assert_graph_equal(ids, d, o_ids, o_d)
 
 
-def test_host_pointers_give_the_same_graph(knng):
-    X = datagen.sift_like(1200, D=20, n_centres=15, seed=5)
-    p = knng.default_params(k=6, leaf_max=32, tree_passes=2, refine_rounds=1, seed=8)
+@pytest.mark.parametrize("n,D,precision,kind", [(1200, 20, "fp32", "integer"), (1003, 7, "bf16", "integer"),
+                                                 (2051, 33, "fp16", "float"), (9, 3, "fp32", "float")])
+def test_host_pointers_give_the_same_graph(knng, n, D, precision, kind):
+    # host rows come in eight pieces of a multiple of 4 rows (the last one
+    # ragged), each checked and converted as it lands; the lists equal the
+    # device-buffer build's, and a NaN in the last piece is still refused
+    X = (datagen.sift_like(n, D=D, n_centres=15, seed=5) if kind == "integer"
+         else datagen.gaussian_mixture(n, D, 10, seed=5))
+    prec = {"fp32": knng.KNNG_FP32, "bf16": knng.KNNG_BF16, "fp16": knng.KNNG_FP16}[precision]
+    p = knng.default_params(k=6, leaf_max=32, tree_passes=2, refine_rounds=1, seed=8, precision=prec)
     hi, hd = knng.knng_build_ex(X, p)                        # numpy in, numpy out
     di, dd = knng.knng_build_ex(_dev(X), p)
     assert isinstance(hi, np.ndarray)
     _assert_graph_equal(di, dd, hi, hd)
+    Xp = torch.from_numpy(X).pin_memory()                    # page-locked host rows
+    pi, pd = knng.knng_build_ex(Xp, p)
+    _assert_graph_equal(di, dd, _np(pi), _np(pd))
+    Xn = X.copy()
+    Xn[-1, -1] = np.nan
+    with pytest.raises(knng.KnngError):
+        knng.knng_build_ex(Xn, p)
 
 
 # ---------------------------------------------------------------- low precision
