@@ -109,6 +109,63 @@ def test_sift_like_1m_d128_bf16(knng):
     _full_build(knng, "sift-like-1m-d128", knng.KNNG_BF16, 0.98)   # reaches 0.992
 
 
+def _holders(ids, n):
+    """For every id t, the nodes whose list holds t (CSR: order, start, end)."""
+    k = ids.shape[1]
+    tgt = ids.ravel().astype(np.int64)
+    src = np.repeat(np.arange(n, dtype=np.int64), k)
+    keep = tgt >= 0
+    tgt, src = tgt[keep], src[keep]
+    order = np.argsort(tgt, kind="stable")
+    tgt, src = tgt[order], src[order]
+    ids_ = np.arange(n)
+    return src, np.searchsorted(tgt, ids_), np.searchsorted(tgt, ids_, side="right")
+
+
+def _check_round_on_sampled_nodes(X, ids0, d0, ids1, d1, rows):
+    """One refinement round (Jacobi, forward and reverse lists) on sampled
+    nodes against its definition, with the oracle's reverse lists, canonical
+    distances and list insertion: node v's new list is its old list offered
+    every member u != v of every node i whose members (G_old[i] and R[i])
+    hold v."""
+    n, k = ids0.shape
+    rid, rd = oracle.reverse_lists(ids0, d0)
+    g_src, g_lo, g_hi = _holders(ids0, n)   # i with v in G_old[i]
+    r_src, r_lo, r_hi = _holders(rid, n)    # i with v in R[i]
+    for v in rows:
+        joins = set(g_src[g_lo[v]:g_hi[v]].tolist()) | set(r_src[r_lo[v]:r_hi[v]].tolist())
+        cand = set()
+        for i in joins:
+            m = set(ids0[i][ids0[i] >= 0].tolist()) | set(rid[i][rid[i] >= 0].tolist())
+            assert v in m
+            cand |= m
+        cand.discard(int(v))
+        e_ids, e_d = ids0[v].copy(), d0[v].copy()
+        for u in sorted(cand):
+            oracle.list_insert(e_ids, e_d, oracle.dist_f32(X[v], X[u]), u)
+        assert np.array_equal(ids1[v], e_ids), "node %d ids" % v
+        assert np.array_equal(d1[v].view(np.uint32), e_d.view(np.uint32)), "node %d distances" % v
+
+
+def test_sift_like_1m_rounds_on_sampled_nodes(knng):
+    # the first round (every member new) and the last one (old pairs and leaf
+    # mates skipped, nodes without a new member not joined) of the bench's
+    # build, each from the graph the build reached before it
+    name = "sift-like-1m-d128"
+    w = datagen.WORKLOADS[name]
+    X = datagen.make(name)
+    Xd = _dev(X)
+    graphs = {}
+    for r in (0, 1, w["rounds"] - 1, w["rounds"]):
+        p = knng.default_params(k=w["k"], leaf_max=w["leaf_max"], tree_passes=w["passes"], refine_rounds=r,
+                                seed=w["seed"], precision=knng.KNNG_BF16, join_mode=knng.KNNG_JOIN_FWD_REV)
+        ids, d = knng.knng_build_ex(Xd, p)
+        graphs[r] = (_np(ids), _np(d))
+    rows = datagen.sample_rows(X.shape[0], 150, seed=13)
+    for r in (1, w["rounds"]):
+        _check_round_on_sampled_nodes(X, *graphs[r - 1], *graphs[r], rows)
+
+
 def test_gist_like_1m_d960_fp16(knng):
     _full_build(knng, "gist-like-1m-d960", knng.KNNG_FP16, 0.90, check_leaves=False)   # reaches 0.926
 
