@@ -208,6 +208,46 @@ def roofline(stats, clocks, workload, steps, name=None):
     return out
 
 
+def kernel_roofline_ms(name, st, clocks, peaks):
+    """Roofline time of all of a kernel's launches, in ms: the larger of its
+    algorithmic bytes at the measured HBM bandwidth and its arithmetic at the
+    peak of its kind (tensor kernels: the sustained dense rate, FP8 at twice
+    BF16; the FP32 kernels: the derived FFMA issue rate, two issue slots per
+    pair and dim as in roofline()).  Returns (ms, bound)."""
+    t_mem = st["bytes"] / (float(peaks["hbm_gbs"]) * 1e9)
+    t_cmp, kind = 0.0, "hbm"
+    if name in TENSOR_KERNELS:
+        ratio = 2.0 if name == "k2_leaf_fp8" else 1.0
+        peak = ratio * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))) * 1e12
+        t_cmp, kind = st["flops"] / peak, "tensor"
+    elif name in ALU_KERNELS:
+        sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        t_cmp, kind = st["flops"] * 2.0 / 3.0 / (152 * 128 * sm_mhz * 1e6), "alu"
+    if t_cmp > t_mem:
+        return t_cmp * 1e3, kind
+    return t_mem * 1e3, "hbm"
+
+
+def whole_build_roofline(stats, clocks, builds, ms_per_step):
+    """The whole build against its roofline: the sum over kernels of each
+    kernel's roofline time (kernel_roofline_ms) per build, divided by the
+    measured time of one build.  `stats` covers `builds` builds."""
+    peaks, kind = measured_peaks()
+    by = {"hbm": 0.0, "tensor": 0.0, "alu": 0.0}
+    for name, st in stats.items():
+        if st["launches"] == 0:
+            continue
+        t, bound = kernel_roofline_ms(name, st, clocks, peaks)
+        by[bound] += t / builds
+    ideal = sum(by.values())
+    return {"roofline_ms_per_step": round(ideal, 3), "ms_per_step": round(ms_per_step, 3),
+            "frac": round(ideal / ms_per_step, 4) if ms_per_step > 0 else None,
+            "roofline_ms_by_bound": {b: round(v, 3) for b, v in by.items()},
+            "peak_source": "%s peaks" % kind,
+            "how": "sum over kernels of max(algorithmic bytes / HBM peak, arithmetic / peak of its kind) per "
+                   "build, divided by the timed step"}
+
+
 def distance_error(X, ids, dists, rows):
     """max |d - d64| / d64 over the stored entries of sampled rows, d64 the
     squared distance in FP64 (numpy, on the host)."""
@@ -490,6 +530,7 @@ def measure_config(knng, name, forms, cpu_n, steps, dev, stream, recall_rows=200
                 "recall_ids": round(r_ids, 5), "recall_tie": round(r_tie, 5), "recall_rows": int(len(smp)),
                 "distance_error": distance_error(X, ids, dists, smp[:500]),
                 "roofline": roof,
+                "whole_build_roofline": whole_build_roofline(st, None, 1, ms / steps),
                 "kernels_ms": {key: round(v["ms"], 3) for key, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])[:6]}}
         if leaf:
             form["certificate_fallback_rows"] = {"rows": int(leaf[0]["items"]), "of": n * cfg["tree_passes"],
@@ -688,6 +729,7 @@ def run_ours(args, cfg):
         replicas.finish()
         return
     roof = roofline(st, clk, cfg["workload"], args.steps)
+    whole = whole_build_roofline(st, clk, args.steps, ms / args.steps)
     roof["share_of_step"] = round(st[roof["kernel"]]["ms"] / ms_k, 4)
     # the same figures for the other kernels above 2 % of the step
     others = []
@@ -710,7 +752,8 @@ def run_ours(args, cfg):
         "timed": "CUDA-graph replays of the recorded build (knng_plan_launch), inputs resident in HBM",
         "direct_form": direct,
         "fp32_form": fp32,
-        "roofline": roof, "roofline_other_kernels": others, "distance_error": dist_err, "e2e": e2e, "e2e_graph_equals_device_graph": same, "gpu_launches": int(launches),
+        "roofline": roof, "roofline_other_kernels": others, "whole_build_roofline": whole,
+        "distance_error": dist_err, "e2e": e2e, "e2e_graph_equals_device_graph": same, "gpu_launches": int(launches),
         "clocks": clk,
         "kernels": {k_: {"ms_per_step": round(v["ms"] / args.steps, 3), "launches_per_step": v["launches"] / args.steps}
                     for k_, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])[:10]},

@@ -1,0 +1,65 @@
+"""Host-side arithmetic of bench.py's whole-build roofline (no GPU).
+
+The whole build's roofline time is the sum over kernels of each kernel's
+roofline time: the larger of its algorithmic bytes at the measured HBM
+bandwidth and its arithmetic at the peak of its kind.
+"""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _st(launches, bytes_, flops=0.0, ms=1.0):
+    return {"launches": launches, "ms": ms, "bytes": bytes_, "flops": flops, "items": 0.0}
+
+
+def test_hbm_kernel_at_peak_is_one(bench):
+    peaks, _ = bench.measured_peaks()
+    bw = float(peaks["hbm_gbs"]) * 1e9
+    # two builds, each moving exactly 1 ms worth of bytes at the measured bandwidth
+    stats = {"k4_merge": _st(8, 2 * bw * 1e-3)}
+    r = bench.whole_build_roofline(stats, None, 2, 1.0)
+    assert r["roofline_ms_per_step"] == pytest.approx(1.0, rel=1e-6)
+    assert r["frac"] == pytest.approx(1.0, rel=1e-6)
+    assert r["roofline_ms_by_bound"]["hbm"] == pytest.approx(1.0, rel=1e-6)
+    # the same kernel measured at four times its roofline time
+    assert bench.whole_build_roofline(stats, None, 2, 4.0)["frac"] == pytest.approx(0.25, rel=1e-6)
+
+
+def test_kernel_takes_the_larger_of_bytes_and_arithmetic(bench):
+    peaks, _ = bench.measured_peaks()
+    bw = float(peaks["hbm_gbs"]) * 1e9
+    tc = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))) * 1e12
+    # a tensor kernel whose arithmetic takes 3 ms and whose bytes take 1 ms
+    t, bound = bench.kernel_roofline_ms("k2_leaf_bf16", _st(1, bw * 1e-3, 3e-3 * tc), None, peaks)
+    assert bound == "tensor" and t == pytest.approx(3.0, rel=1e-6)
+    # FP8 runs at twice the BF16 rate
+    t8, _ = bench.kernel_roofline_ms("k2_leaf_fp8", _st(1, bw * 1e-3, 3e-3 * tc), None, peaks)
+    assert t8 == pytest.approx(1.5, rel=1e-6)
+    # bytes dominate: the same kernel with 5 ms of bytes
+    t, bound = bench.kernel_roofline_ms("k2_leaf_bf16", _st(1, 5 * bw * 1e-3, 3e-3 * tc), None, peaks)
+    assert bound == "hbm" and t == pytest.approx(5.0, rel=1e-6)
+    # an FP32 kernel: flops are counted 3 per pair and dim, two issue slots
+    ops = 152 * 128 * 2000e6  # issue slots per second at 2000 MHz
+    t, bound = bench.kernel_roofline_ms("k5_join", _st(1, 0.0, 1.5 * ops * 2e-3), {"sm_mhz": 2000.0}, peaks)
+    assert bound == "alu" and t == pytest.approx(2.0, rel=1e-6)
+
+
+def test_sum_over_kernels_and_unlaunched_kernels(bench):
+    peaks, _ = bench.measured_peaks()
+    bw = float(peaks["hbm_gbs"]) * 1e9
+    stats = {"k1_project": _st(65, bw * 2e-3), "k5_join_tc": _st(8, bw * 3e-3), "k6_fill": _st(0, 1e12)}
+    r = bench.whole_build_roofline(stats, None, 1, 10.0)
+    assert r["roofline_ms_per_step"] == pytest.approx(5.0, rel=1e-6)
+    assert r["frac"] == pytest.approx(0.5, rel=1e-6)
