@@ -123,19 +123,24 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-KERNEL_SOURCES = {"k1_": "split.cu", "k2_leaf_fp32": "leaf.cu", "k2_": "leaf_tc.cu", "k4_": "join.cu",
-                  "k5_join_tc": "join_tc.cu", "k5_": "join.cu", "k6_": "join.cu", "k7_": "exact.cu",
-                  "k0_": "leaf_tc.cu"}
+# the sources whose change makes a kernel's committed counters stale: its own
+# file, and for the tensor-core join also join.cu, which sets the order in
+# which it takes the nodes (and so its DRAM traffic)
+KERNEL_SOURCES = {"k1_": ("split.cu",), "k2_leaf_fp32": ("leaf.cu",), "k2_": ("leaf_tc.cu",), "k4_": ("join.cu",),
+                  "k5_join_tc": ("join_tc.cu", "join.cu"), "k5_": ("join.cu",), "k6_": ("join.cu",),
+                  "k7_": ("exact.cu",), "k0_": ("leaf_tc.cu",)}
 ALU_KERNELS = ("k5_join", "k2_leaf_fp32", "k7_exact")
 TENSOR_KERNELS = ("k2_leaf_bf16", "k2_leaf_fp16", "k2_leaf_fp8")
 
 
 def kernel_source_hash(kernel):
-    for pre, f in KERNEL_SOURCES.items():
+    for pre, files in KERNEL_SOURCES.items():
         if kernel.startswith(pre):
-            path = os.path.join(ROOT, "paper_1701_08475_gb300", "csrc", f)
-            with open(path, "rb") as fh:
-                return hashlib.sha256(fh.read()).hexdigest()[:16]
+            h = hashlib.sha256()
+            for f in files:
+                with open(os.path.join(ROOT, "paper_1701_08475_gb300", "csrc", f), "rb") as fh:
+                    h.update(fh.read())
+            return h.hexdigest()[:16]
     return None
 
 

@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(32 * kFlagWarps) k6_flags(const uint64_t* __re
         }
         on = (fb | rb) != 0;
     }
+    if (active == nullptr) return;  // the nodes are listed by k6_active (uniform over the CTA)
     if (lane == 0) act[w] = on;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -343,6 +344,41 @@ __global__ void __launch_bounds__(32 * kFlagWarps) k6_flags(const uint64_t* __re
         for (int q = 0; q < kFlagWarps; ++q)
             if (act[q]) active[at++] = (int32_t)((int64_t)blockIdx.x * kFlagWarps + q);
     }
+}
+
+// The nodes with a new member listed in the order of `order` (position p
+// listed when node order[p] has a new member in fnew / rnew, as k6_flags
+// wrote them): positions keep their order inside a CTA, one atomic per CTA.
+__global__ void __launch_bounds__(256) k6_active(const int32_t* __restrict__ order,
+                                                 const uint64_t* __restrict__ fnew,
+                                                 const uint64_t* __restrict__ rnew, int64_t n,
+                                                 int32_t* __restrict__ active, int32_t* __restrict__ nactive) {
+    __shared__ int wbefore[8];
+    __shared__ int base;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    int32_t i = 0;
+    bool on = false;
+    if (p < n) {
+        i = order[p];
+        // a permutation of the nodes; a stray id (a failed partition, which
+        // the status word reports) lists nothing
+        on = i >= 0 && i < n && (fnew[i] | (rnew ? rnew[i] : 0ull)) != 0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) wbefore[w] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int q = 0; q < 8; ++q) {
+            const int t = wbefore[q];
+            wbefore[q] = c;
+            c += t;
+        }
+        base = c > 0 ? atomicAdd(nactive, c) : 0;
+    }
+    __syncthreads();
+    if (on) active[base + wbefore[w] + __popc(bal & ((1u << lane) - 1u))] = i;
 }
 
 // ---------------------------------------------------------------- K5
@@ -1346,7 +1382,7 @@ void run_refine(const float* X, int64_t n, int D, int k, bool rev, uint64_t*& G,
     }
     for (int r = 0; r < rounds; ++r) {
         if (rev) launch_reverse_lists(G, n, k, b, s);  // into b.R; b.R2 keeps the previous round's
-        b.list = nullptr;
+        b.list = b.order;  // every node (in the last tree pass's leaf order when it is known)
         b.fnew = b.rnew = nullptr;
         b.count_dev = nullptr;
         int64_t count = n;
@@ -1356,12 +1392,20 @@ void run_refine(const float* X, int64_t n, int D, int k, bool rev, uint64_t*& G,
             {
                 LaunchScope ls("k6_flags", s, n * k * 8.0 * (rev ? 4.0 : 2.0) + n * 20.0, 0);
                 const int grid = (int)((n + kFlagWarps - 1) / kFlagWarps);
+                // with an order, k6_active lists the nodes after the flags
+                int32_t* act = b.order ? nullptr : b.active;
                 if (k > 32)
                     k6_flags<2><<<grid, 32 * kFlagWarps, 0, s>>>(G, rev ? b.R : nullptr, G2, rev ? b.R2 : nullptr,
-                                                                 n, k, b.fnew_buf, b.rnew_buf, b.active, b.nactive);
+                                                                 n, k, b.fnew_buf, b.rnew_buf, act, b.nactive);
                 else
                     k6_flags<1><<<grid, 32 * kFlagWarps, 0, s>>>(G, rev ? b.R : nullptr, G2, rev ? b.R2 : nullptr,
-                                                                 n, k, b.fnew_buf, b.rnew_buf, b.active, b.nactive);
+                                                                 n, k, b.fnew_buf, b.rnew_buf, act, b.nactive);
+            }
+            if (b.order) {
+                // the order (4 B), the flags of each node (8 or 16 B), the list written (4 B)
+                LaunchScope ls("k6_active", s, n * (rev ? 24.0 : 16.0), 0);
+                k6_active<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(b.order, b.fnew_buf, rev ? b.rnew_buf : nullptr,
+                                                                     n, b.active, b.nactive);
             }
             if (b.capture) {
                 b.count_dev = b.nactive;  // the kernels read how many nodes are listed
