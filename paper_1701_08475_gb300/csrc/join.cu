@@ -248,7 +248,8 @@ __device__ __forceinline__ bool sorted_has(const uint64_t* list, int k, uint64_t
 // or beaten by the target's k-th entry (which never gets worse), so the join
 // may skip the pair without changing the result.  One warp per node; bit e of
 // fnew[i] (rnew[i]) marks entry e of G_old[i] (R[i]) new; nodes with a new
-// member are appended to `active` (one atomic per block).
+// member are appended to `active` (one atomic per block), unless `active` is
+// NULL: then k6_active lists them afterwards in a given order.
 constexpr int kFlagWarps = 16;
 template <int NO>
 __global__ void __launch_bounds__(32 * kFlagWarps) k6_flags(const uint64_t* __restrict__ Gcur,
