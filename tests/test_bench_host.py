@@ -63,3 +63,28 @@ def test_sum_over_kernels_and_unlaunched_kernels(bench):
     r = bench.whole_build_roofline(stats, None, 1, 10.0)
     assert r["roofline_ms_per_step"] == pytest.approx(5.0, rel=1e-6)
     assert r["frac"] == pytest.approx(0.5, rel=1e-6)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` times the CPU oracle on the headline's
+    recipe and prints one JSON line with the same metric, unit and config as
+    the GPU arm would, its sample stated in cpu_baseline."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    spec = importlib.util.spec_from_file_location("bench_cfg", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    assert line["impl"] == "reference"
+    assert line["metric"] == "kNN-graph build points/s at recall@k vs exact" and line["unit"] == "points/s"
+    assert line["higher_is_better"] is True and line["steps"] == 1
+    # the GPU arm's default precision is BF16: the two lines carry one config
+    assert line["config"] == mod.workload_config(mod.DEFAULT_WORKLOAD, "bf16")
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
