@@ -62,6 +62,22 @@ def test_init_positions_distinct_and_in_range():
             assert 0 <= h < m and 0 <= h2 < m and h != h2
 
 
+def test_init_positions_depend_on_segment_level_and_seed():
+    # The first position is a hash of (pass seed, level, segment): over 200
+    # segments (levels, seeds) of 1,000 points it takes well over 100 values
+    # (a uniform draw takes about 181 on average).
+    ps = oracle.pass_seed(1234, 0)
+    assert len({oracle.init_positions(ps, 3, seg, 1000)[0] for seg in range(200)}) > 150
+    assert len({oracle.init_positions(ps, lev, 5, 1000)[0] for lev in range(200)}) > 150
+    assert len({oracle.init_positions(oracle.pass_seed(s, 0), 3, 5, 1000)[0] for s in range(200)}) > 150
+    # and the second one, given the first, varies too
+    seconds = {}
+    for seg in range(2000):
+        h, h2 = oracle.init_positions(ps, 3, seg, 50)
+        seconds.setdefault(h, set()).add(h2)
+    assert max(len(v) for v in seconds.values()) > 10
+
+
 # ---------------------------------------------------------------- distances
 def test_dist_symmetric_bitwise():
     rng = np.random.default_rng(0)
@@ -227,6 +243,64 @@ def test_partition_of_points_on_a_line_is_contiguous_runs():
     for a, b in zip(off[:-1], off[1:]):
         ts = np.sort(t[perm[a:b]])
         assert np.all(np.diff(ts) == 1.0)
+
+
+def test_partition_of_identical_points_is_by_ascending_id():
+    # Every point the same: every projection is the same key, so each balanced
+    # cut takes the floor(m/2) smallest ids of its segment (ties by position,
+    # positions ascending ids): the leaves are consecutive id ranges in order,
+    # and the permutation is the identity.
+    for n, leaf_max in ((1000, 40), (777, 64), (64, 2)):
+        X = np.full((n, 3), 2.5, np.float32)
+        perm, off = oracle.partition(X, leaf_max, iters=3, seed=9)
+        assert np.array_equal(perm, np.arange(n, dtype=np.int32))
+        L = oracle.tree_depth(n, leaf_max)
+        sizes = np.diff(off)
+        assert sizes.min() >= n // (1 << L) and sizes.max() <= -(-n // (1 << L))
+
+
+def _offset_pairs_data():
+    """2,051 points in 2-D, ids shuffled: b = -1 (825 points), 0 (400), +1
+    (826); a = B = 1023 + 37/1024 except that 724 of the b = -1 points carry
+    B +- 1/2 and every b = 0 point B +- 2^-10, + and - alternating in id
+    order.  Every a is an FP32 number and every sum below is exact in FP64;
+    1025 B and 1026 B are not FP32 numbers."""
+    m, n_neg, n_neg_b, n0 = 2051, 825, 101, 400
+    rng = np.random.default_rng(31)
+    b = np.array([-1.0] * n_neg + [0.0] * n0 + [1.0] * (m - n_neg - n0), np.float32)
+    rng.shuffle(b)
+    B = np.float32(1023 + 37 / 1024)
+    a = np.full(m, B, np.float32)
+    alt = np.flatnonzero(b == -1)[:n_neg - n_neg_b]
+    a[alt[0::2]] = B + np.float32(0.5)
+    a[alt[1::2]] = B - np.float32(0.5)
+    zeros = np.flatnonzero(b == 0)
+    a[zeros[0::2]] = B + np.float32(2.0 ** -10)
+    a[zeros[1::2]] = B - np.float32(2.0 ** -10)
+    return np.stack([a, b], 1), a, b, zeros
+
+
+def test_partition_centroids_are_fp64_means_rounded_to_fp32():
+    # With a pass seed whose initial points are a b = -1 and a b = +1 point of
+    # equal a, the first cut is by b: all b = -1 points, then the b = 0 points
+    # by ascending id up to floor(m/2) = 1025.  Both sides then have the exact
+    # mean B in a (the +- pairs cancel), so the FP64 means rounded to FP32 are
+    # equal, the projection ignores a, every b = 0 point ties and the same cut
+    # repeats: a closed form.  Means that are not the FP64 mean rounded once
+    # (sums accumulated in FP32, or the sum rounded to FP32 before the division)
+    # differ in a between the sides (by construction of B, 1025 and 1026), and
+    # the cut inside the b = 0 points then follows a, not the ids.
+    X, a, b, zeros = _offset_pairs_data()
+    m = X.shape[0]
+    K = m // 2
+    seed = next(s for s in range(3000)
+                for h, h2 in [oracle.init_positions(oracle.pass_seed(s, 0), 0, 0, m)]
+                if b[h] == -1 and b[h2] == 1 and a[h] == a[h2])
+    perm, off = oracle.partition(X, K + 1, iters=3, seed=seed)
+    left = np.sort(np.concatenate([np.flatnonzero(b == -1), zeros[:K - 825]]))
+    assert np.array_equal(off, [0, K, m])
+    assert np.array_equal(perm[:K], left)
+    assert np.array_equal(perm[K:], np.setdiff1d(np.arange(m), left))
 
 
 def test_partition_orientation_one_dimension():

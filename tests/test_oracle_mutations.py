@@ -24,6 +24,9 @@ PINS = [
     T.test_partition_orientation_one_dimension,
     T.test_partition_separates_two_far_clusters,
     T.test_partition_split_is_lloyd_fixed_point,
+    T.test_partition_of_identical_points_is_by_ascending_id,
+    T.test_partition_centroids_are_fp64_means_rounded_to_fp32,
+    T.test_init_positions_depend_on_segment_level_and_seed,
     T.test_one_leaf_build_is_exact_graph,
     T.test_leaf_update_is_exact_within_each_leaf,
     lambda: T.test_refine_round_matches_pull_formulation(oracle.FWD),
@@ -54,6 +57,17 @@ MUTATIONS = [
     ("reverse list stores wrong id", "dists[j * k + t], (int32_t)j);", "dists[j * k + t], (int32_t)i);"),
     ("join ignores reverse lists", "if (rev_ids[i * k + t] >= 0) memb[cnt++] = rev_ids[i * k + t];", ""),
     ("recall tie bound strict", "if (dists[i * k + a] <= kth) ++tie;", "if (dists[i * k + a] < kth) ++tie;"),
+    ("centroid sums in FP32", "for (int j = 0; j < D; ++j) acc[j] += (double)X[(int64_t)ids[t] * D + j];",
+     "for (int j = 0; j < D; ++j) acc[j] = (double)((float)acc[j] + X[(int64_t)ids[t] * D + j]);"),
+    ("mean divided in FP32", "for (int j = 0; j < D; ++j) c[j] = (float)(acc[j] / (double)cnt);",
+     "for (int j = 0; j < D; ++j) c[j] = (float)acc[j] / (float)cnt;"),
+    ("sum rounded to FP32 before the division", "for (int j = 0; j < D; ++j) c[j] = (float)(acc[j] / (double)cnt);",
+     "for (int j = 0; j < D; ++j) c[j] = (float)((float)acc[j] / (double)cnt);"),
+    ("projection ties by descending id", "    return (x->id > y->id) - (x->id < y->id);\n}\n\nstatic int id_cmp",
+     "    return (x->id < y->id) - (x->id > y->id);\n}\n\nstatic int id_cmp"),
+    ("first position ignores the segment",
+     "orc_splitmix64(orc_splitmix64(orc_splitmix64(pass_seed) ^ (uint64_t)level) ^ (uint64_t)seg)",
+     "orc_splitmix64(orc_splitmix64(orc_splitmix64(pass_seed) ^ (uint64_t)level))"),
 ]
 
 
