@@ -100,6 +100,8 @@ PINS_SEARCH_RVQ = [
     Sr.test_rows_are_sorted_unique_and_carry_canonical_distances,
     lambda: Sr.test_every_top_entry_is_expanded_not_only_the_first(2, [2, 0]),
     V.test_init_positions_one_per_stratum,
+    V.test_zero_iterations_give_each_stage_its_drawn_vectors,
+    V.test_a_word_without_members_keeps_its_value,
     V.test_assign_is_the_brute_force_argmin_with_ties_to_the_smaller_index,
     V.test_one_iteration_from_separated_clusters_gives_their_means,
     lambda: V.test_converged_training_is_a_fixed_point_of_both_stages(0),
@@ -130,6 +132,10 @@ MUTATIONS_SEARCH_RVQ = [
      "for (int64_t i = n - 1; i >= 0; --i) ids[fill"),
     ("rvq seeds skip a list's first id", "for (int32_t t = offsets[cand[e].key];",
      "for (int32_t t = offsets[cand[e].key] + 1;"),
+    ("rvq empty word reset to zero", "            if (cnt[c] == 0) continue;\n",
+     "            if (cnt[c] == 0) { for (int j = 0; j < D; ++j) words[(int64_t)c * D + j] = 0.0f; continue; }\n"),
+    ("rvq stage 2 drawn like stage 1", "rc = lloyd(R, n, D, W2, iters, seed, 2, w2, codes);",
+     "rc = lloyd(R, n, D, W2, iters, seed, 1, w2, codes);"),
 ]
 
 

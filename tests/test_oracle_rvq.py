@@ -35,6 +35,31 @@ def test_init_positions_one_per_stratum():
     assert not np.array_equal(a, oracle.rvq_init_positions(100000, 64, 12, 1))
 
 
+def test_zero_iterations_give_each_stage_its_drawn_vectors():
+    # With no Lloyd iteration each stage's words are its own draws: stage 1 the
+    # points at the stage-1 positions; stage 2 the residues (x - w1[c1], c1 the
+    # brute-force nearest stage-1 word on integer data) at the stage-2 positions.
+    rng = np.random.default_rng(7)
+    X = rng.integers(-50, 51, size=(3000, 6)).astype(np.float32)
+    W1, W2, seed = 24, 16, 9
+    w1, w2 = oracle.rvq_train(X, W1, W2, iters=0, seed=seed)
+    p1 = oracle.rvq_init_positions(3000, W1, seed, 1)
+    p2 = oracle.rvq_init_positions(3000, W2, seed, 2)
+    assert np.array_equal(w1, X[p1])
+    c1 = np.argmin(_sq64(X, w1), axis=1)
+    assert np.array_equal(w2, (X - w1[c1])[p2])
+
+
+def test_a_word_without_members_keeps_its_value():
+    # Identical points: every draw is the same vector, every vector goes to
+    # word 0 (ties to the smaller index), the other words have no member and
+    # keep their value, so every word of stage 1 is the point (stage 2: zero).
+    X = np.tile(np.array([[3.0, -1.5, 7.25]], np.float32), (500, 1))
+    w1, w2 = oracle.rvq_train(X, 8, 4, iters=3, seed=2)
+    assert np.array_equal(w1, np.tile(X[:1], (8, 1)))
+    assert not w2.any()
+
+
 def test_assign_is_the_brute_force_argmin_with_ties_to_the_smaller_index():
     rng = np.random.default_rng(1)
     V = rng.integers(0, 4, size=(2000, 5)).astype(np.float32)        # many exact ties
