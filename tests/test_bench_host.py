@@ -88,3 +88,25 @@ def test_reference_arm_prints_the_contract_line():
     assert line["config"] == mod.workload_config(mod.DEFAULT_WORKLOAD, "bf16")
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_profiled_traffic_only_for_the_same_sources(bench, tmp_path, monkeypatch):
+    """The committed ncu summary gives a kernel's DRAM bytes per algorithmic
+    byte only while the sources it was captured on are unchanged; for the
+    tensor-core join those are join_tc.cu and join.cu (which sets its node
+    order)."""
+    import hashlib
+    csrc = tmp_path / "paper_1701_08475_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "join_tc.cu").write_text("// kernel\n")
+    (csrc / "join.cu").write_text("// order\n")
+    h = hashlib.sha256(b"// kernel\n// order\n").hexdigest()[:16]
+    (tmp_path / "profiles" / "k5_join_tc_sift-like-300k.md").write_text(
+        "# summary\n\n- source_sha256_16: `%s`\n- dram_bytes_per_alg_byte: 0.25\n" % h)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # a smaller case of the same recipe stands in for the full-size workload
+    assert bench.profiled_traffic("k5_join_tc", "sift-like-1m-d128") == 0.25
+    (csrc / "join.cu").write_text("// another order\n")
+    assert bench.profiled_traffic("k5_join_tc", "sift-like-1m-d128") is None
+    assert bench.profiled_traffic("k4_merge", "sift-like-1m-d128") is None   # no summary at all
