@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["autotune", "autotune_leaf_max"]
+__all__ = ["autotune", "autotune_leaf_max", "pick"]
 
 
 def _timed_build(pilot, q, repeats):
@@ -33,6 +33,14 @@ def _timed_build(pilot, q, repeats):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     return ids, d, float(np.median(times))
+
+
+def pick(rows, recall_slack):
+    """The fastest of rows (leaf_max, twomeans_iters, ms, recall) whose recall
+    is within recall_slack of the best; the first of equally fast ones."""
+    best = max(r[3] for r in rows)
+    ok = [r for r in rows if r[3] >= best - recall_slack]
+    return min(ok, key=lambda r: r[2])
 
 
 def autotune(datas, params, leaf_candidates=(64, 128, 256), iters_candidates=(2, 3, 4), pilot_rows=20000,
@@ -72,10 +80,8 @@ def autotune(datas, params, leaf_candidates=(64, 128, 256), iters_candidates=(2,
                 ids, d, ms = _timed_build(pilot, q, repeats)
                 rec = L.knng_recall(ids, d, gi, gd, smp)[0]
                 rows.append((c, t, ms, float(rec)))
-        best = max(r[3] for r in rows)
-        ok = [r for r in rows if r[3] >= best - recall_slack]
-        pick = min(ok, key=lambda r: r[2])
-        choice[D] = (pick[0], pick[1])
+        chosen = pick(rows, recall_slack)
+        choice[D] = (chosen[0], chosen[1])
         report[D] = rows
     return ([choice[int(x.shape[1])][0] for x in datas], [choice[int(x.shape[1])][1] for x in datas], report)
 

@@ -110,3 +110,16 @@ def test_profiled_traffic_only_for_the_same_sources(bench, tmp_path, monkeypatch
     (csrc / "join.cu").write_text("// another order\n")
     assert bench.profiled_traffic("k5_join_tc", "sift-like-1m-d128") is None
     assert bench.profiled_traffic("k4_merge", "sift-like-1m-d128") is None   # no summary at all
+
+
+def test_autotuner_keeps_the_fastest_within_the_recall_slack():
+    from paper_1701_08475_gb300.autotune import pick
+    rows = [(64, 2, 4.8, 0.9917), (128, 2, 4.5, 0.9947), (128, 3, 5.1, 0.9945), (256, 2, 4.1, 0.9920),
+            (256, 4, 3.9, 0.9900)]
+    # best recall 0.9947: within 0.002 are the rows of recall >= 0.9927, the fastest of them (128, 2)
+    assert pick(rows, 0.002)[:2] == (128, 2)
+    # a looser slack admits (256, 2) at 4.1 ms and (256, 4) at 3.9 ms
+    assert pick(rows, 0.003)[:2] == (256, 2)
+    assert pick(rows, 0.005)[:2] == (256, 4)
+    # equal times: the first row wins
+    assert pick([(64, 2, 1.0, 0.5), (128, 2, 1.0, 0.5)], 0.0)[:2] == (64, 2)
