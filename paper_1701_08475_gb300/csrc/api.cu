@@ -962,16 +962,15 @@ void build_core(const float* X, const Args& a, BuildLayout& b, const TreePlan& t
             launch_partition(pass + Q);
         }
     }
+    // the rounds take the nodes in the last tree pass's leaf order
+    JoinBuffers jb = b.jb;
+    jb.order = P > 0 ? perms[P - 1] : nullptr;
     if (a.p.join_mode == KNNG_JOIN_SAMPLED)
-        run_refine_sampled(X, n, a.D, k, b.G, b.G2, b.jb, b.nodes_per_chunk, a.p.refine_rounds, a.p.sample,
+        run_refine_sampled(X, n, a.D, k, b.G, b.G2, jb, b.nodes_per_chunk, a.p.refine_rounds, a.p.sample,
                            a.p.seed, b.status, s);
-    else {
-        // the rounds take the nodes in the last tree pass's leaf order
-        JoinBuffers jb = b.jb;
-        jb.order = P > 0 ? perms[P - 1] : nullptr;
+    else
         run_refine(X, n, a.D, k, a.p.join_mode == KNNG_JOIN_FWD_REV, b.G, b.G2, jb, b.nodes_per_chunk,
                    a.p.refine_rounds, b.status, s);
-    }
 }
 
 }  // namespace

@@ -1444,7 +1444,7 @@ void run_refine_sampled(const float* X, int64_t n, int D, int k, uint64_t*& G, u
         // member view in R2, sampled-new mask in fnew_buf, reverse samples in R
         launch_sampled_prepare(G, b.flags, n, k, ms, h0, b.R2, b.fnew_buf, b.flags_post, b.deg, b.roff, b.cur,
                                b.scan_tmp, b.rbuf, b.R, b.rnew_buf, s);
-        b.list = nullptr;
+        b.list = b.order;  // every node (in the last tree pass's leaf order when it is known)
         b.count_dev = nullptr;
         b.fnew = b.fnew_buf;
         b.rnew = b.rnew_buf;

@@ -205,7 +205,7 @@ struct JoinBuffers {
     // new) and the mask after this round's sample (NULL: full rounds)
     uint64_t* flags = nullptr;
     uint64_t* flags_post = nullptr;
-    // the order in which the full rounds take the nodes: the ids in the leaf
+    // the order in which the rounds take the nodes: the ids in the leaf
     // order of the build's last tree pass (NULL: id order).  Neighbouring
     // nodes of a leaf share most of their members, so taken together their
     // member rows are read once from DRAM and then from L2.  A round's result
