@@ -110,6 +110,8 @@ PINS_SEARCH_RVQ = [
     V.test_index_is_a_stable_sort_by_key,
     lambda: V.test_seeds_follow_eqn2_with_pruning_by_the_first_term(3, 40),
     lambda: V.test_seeds_follow_eqn2_with_pruning_by_the_first_term(12, 300),
+    lambda: V.test_seeds_follow_eqn2_with_pruning_by_the_first_term(12, 5000),
+    V.test_seeds_tie_by_key_when_the_query_norm_absorbs_the_differences,
     V.test_seeds_on_float_data_follow_the_direct_distance_up_to_rounding,
 ]
 
@@ -136,6 +138,9 @@ MUTATIONS_SEARCH_RVQ = [
      "            if (cnt[c] == 0) { for (int j = 0; j < D; ++j) words[(int64_t)c * D + j] = 0.0f; continue; }\n"),
     ("rvq stage 2 drawn like stage 1", "rc = lloyd(R, n, D, W2, iters, seed, 2, w2, codes);",
      "rc = lloyd(R, n, D, W2, iters, seed, 1, w2, codes);"),
+    ("rvq term 1 without the query norm", "float t = fmaf(-2.0f, dot_f32(q, w1 + (int64_t)a * D, D), qq);",
+     "float t = fmaf(-2.0f, dot_f32(q, w1 + (int64_t)a * D, D), 0.0f);"),
+    ("rvq seeds padded with 0", "for (; cnt < s; ++cnt) S[qi * s + cnt] = -1;", "for (; cnt < s; ++cnt) S[qi * s + cnt] = 0;"),
 ]
 
 

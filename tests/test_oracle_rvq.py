@@ -214,6 +214,24 @@ def test_seeds_follow_eqn2_with_pruning_by_the_first_term(p1, s):
         assert S[r].tolist() == _seeds_by_eqn2(w1, w2, off, ids, Q[r], p1, s), r
 
 
+def test_seeds_tie_by_key_when_the_query_norm_absorbs_the_differences():
+    # Eqn. 3's first term is evaluated in FP32 with the query's squared norm
+    # in it: for q = (2^14, 0) every stage-1 word (0, u) with u^2 < 16 gets
+    # term1 = fl(2^28 + u^2) = 2^28 (the spacing of FP32 there is 32), so every
+    # key ties and the seeds come by ascending key: point a is word a's only
+    # member, so the seeds are 0, 1, ..., W1 - 1, then -1 padding.
+    # word a = (0, u_a, a / 4): |w|^2 <= 9 + 49/16 < 16; the third coordinate,
+    # which q does not see, keeps words with the same u apart
+    u = np.array([3, 0, 2, 1, 3, 2, 0, 1], np.float32)
+    w1 = np.stack([np.zeros(8, np.float32), u, np.arange(8, dtype=np.float32) / 4], 1)
+    w2 = np.zeros((1, 3), np.float32)
+    codes, off, ids = oracle.rvq_index(w1, w1, w2)
+    assert np.array_equal(codes[:, 0], np.arange(8))
+    Q = np.array([[2.0 ** 14, 0.0, 0.0]], np.float32)
+    S = oracle.rvq_seeds(w1, w2, off, ids, Q, 8, 10)
+    assert S[0].tolist() == list(range(8)) + [-1, -1]
+
+
 def test_seeds_on_float_data_follow_the_direct_distance_up_to_rounding():
     rng = np.random.default_rng(9)
     X = rng.standard_normal((3000, 10)).astype(np.float32)
