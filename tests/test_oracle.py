@@ -536,3 +536,13 @@ def test_recall_hand_example():
     d2 = np.array([[1, np.inf], [1, 1], [4, 1]], np.float32)
     ri, rt = oracle.recall(ids2, d2, gt_ids, gt_d, np.array([0, 1], np.int32))
     assert ri == 0.75 and rt == 0.75
+    # a sample that skips a row: ground-truth row r belongs to graph row sample[r]
+    gt3_ids = np.array([[0, 1]], np.int32)       # row 2's exact neighbours
+    gt3_d = np.array([[1, 4]], np.float32)
+    ids3 = np.array([[1, 2], [0, 2], [1, 0]], np.int32)
+    d3 = np.array([[1, 4], [1, 1], [4, 1]], np.float32)
+    ri, rt = oracle.recall(ids3, d3, gt3_ids, gt3_d, np.array([2], np.int32))
+    assert ri == 1.0 and rt == 1.0
+    # the same ground truth given as row 0's: row 0 holds 1 and 2, one of the two
+    ri, rt = oracle.recall(ids3, d3, gt3_ids, gt3_d, np.array([0], np.int32))
+    assert ri == 0.5

@@ -18,6 +18,7 @@ PINS = [
     lambda: T.test_exact_golden_hand_worked("square_ties_k2.txt"),
     lambda: T.test_exact_golden_hand_worked("tiny_1d_k2.txt"),
     T.test_exact_integer_ties_broken_by_id,
+    T.test_exact_sample_rows_equal_full_rows,
     T.test_tree_depth_closed_form,
     lambda: T.test_partition_invariants(777, 3, 40),
     T.test_partition_of_points_on_a_line_is_contiguous_runs,
@@ -65,6 +66,9 @@ MUTATIONS = [
      "for (int j = 0; j < D; ++j) c[j] = (float)((float)acc[j] / (double)cnt);"),
     ("projection ties by descending id", "    return (x->id > y->id) - (x->id < y->id);\n}\n\nstatic int id_cmp",
      "    return (x->id < y->id) - (x->id > y->id);\n}\n\nstatic int id_cmp"),
+    ("exact sample rows ignored", "        int64_t i = sample ? sample[r] : r;\n        int32_t *li = out_ids + r * k;\n        float *ld",
+     "        int64_t i = r;\n        int32_t *li = out_ids + r * k;\n        float *ld"),
+    ("recall reads graph rows by sample position", "            int32_t g = ids[i * k + a];", "            int32_t g = ids[r * k + a];"),
     ("first position ignores the segment",
      "orc_splitmix64(orc_splitmix64(orc_splitmix64(pass_seed) ^ (uint64_t)level) ^ (uint64_t)seg)",
      "orc_splitmix64(orc_splitmix64(orc_splitmix64(pass_seed) ^ (uint64_t)level))"),
