@@ -508,6 +508,27 @@ def test_build_invariants_and_recall_small_gmm():
             assert d[i, t] == oracle.dist_f32(X[i], X[ids[i, t]])
 
 
+@pytest.mark.parametrize("mode", [oracle.FWD, oracle.FWD_REV])
+def test_build_is_its_passes_then_its_rounds(mode):
+    # Alg. 1's loop: pass p partitions with the pass-p seed and updates G from
+    # its leaves, passes 0 .. I_0 - 1 in order; then the refinement rounds, each
+    # from the previous one's graph.  The whole build equals that composition of
+    # the stages pinned above.
+    X = datagen.gaussian_mixture(1200, 8, 12, seed=23)
+    k, leaf_max, passes, rounds = 6, 32, 3, 2
+    ids, d = oracle.new_graph(1200, k)
+    for p in range(passes):
+        perm, off = oracle.partition(X, leaf_max, iters=4, seed=5, pass_=p)
+        ids, d = oracle.leaf_update(X, k, perm, off, ids, d)
+    for _ in range(rounds):
+        ids, d = oracle.refine_round(X, ids, d, mode=mode)
+    bi, bd = oracle.build_graph(X, k, leaf_max, passes=passes, rounds=rounds, iters=4, mode=mode, seed=5)
+    assert np.array_equal(bi, ids) and np.array_equal(bd, d)
+    # and the rounds change the graph here (two passes overlap the leaves)
+    pi, _ = oracle.build_graph(X, k, leaf_max, passes=passes, rounds=rounds - 1, iters=4, mode=mode, seed=5)
+    assert not np.array_equal(pi, bi)
+
+
 def test_tree_pass_beats_random_partition():
     # The two-means partition puts true neighbours together far more often than
     # a random partition with the same leaf sizes (Sec. 3.1's motivation).

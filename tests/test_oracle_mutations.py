@@ -34,6 +34,8 @@ PINS = [
     lambda: T.test_refine_round_matches_pull_formulation(oracle.FWD_REV),
     T.test_reverse_lists_match_brute_force,
     T.test_recall_hand_example,
+    T.test_partition_depends_on_pass_seed_only_through_init,
+    lambda: T.test_build_is_its_passes_then_its_rounds(oracle.FWD_REV),
 ]
 
 # (name, text in the oracle source, planted replacement)
@@ -69,6 +71,13 @@ MUTATIONS = [
     ("exact sample rows ignored", "        int64_t i = sample ? sample[r] : r;\n        int32_t *li = out_ids + r * k;\n        float *ld",
      "        int64_t i = r;\n        int32_t *li = out_ids + r * k;\n        float *ld"),
     ("recall reads graph rows by sample position", "            int32_t g = ids[i * k + a];", "            int32_t g = ids[r * k + a];"),
+    ("build repeats pass 0", "        if (orc_partition(X, n, D, leaf_max, iters, seed, p, perm, off) < 0) {",
+     "        if (orc_partition(X, n, D, leaf_max, iters, seed, 0, perm, off) < 0) {"),
+    ("build one round fewer", "    for (int r = 0; r < rounds; ++r)\n        if (orc_refine_round",
+     "    for (int r = 1; r < rounds; ++r)\n        if (orc_refine_round"),
+    ("build rounds in forward mode only", "if (orc_refine_round(X, n, D, k, mode, out_ids, out_d) != 0) return -1;",
+     "if (orc_refine_round(X, n, D, k, 0, out_ids, out_d) != 0) return -1;"),
+    ("pass seed ignores the pass", "return orc_splitmix64(seed ^ (uint64_t)pass);", "return orc_splitmix64(seed);"),
     ("first position ignores the segment",
      "orc_splitmix64(orc_splitmix64(orc_splitmix64(pass_seed) ^ (uint64_t)level) ^ (uint64_t)seg)",
      "orc_splitmix64(orc_splitmix64(orc_splitmix64(pass_seed) ^ (uint64_t)level))"),
